@@ -1,0 +1,178 @@
+/*
+ * irk.h -- C ABI of the GB300 Gauss-IRK nonlinear stage solver.
+ *
+ * Problem (Sec. 1.1, Eq. problem):  M u'(t) = N(u, t),  u(0) = u0,
+ * advanced by an s-stage Gauss Runge-Kutta method (Eq. update, Eq. stages):
+ *     u_{n+1} = u_n + dt * sum_i b_i k_i,
+ *     0 = M k_i - N(u_n + dt * sum_j a_ij k_j, t_n + c_i dt),   i = 1..s.
+ * For the vorticity-streamfunction DAE (Sec. 6, Eq. dae / dae_stage) the state
+ * is (omega, psi), M = diag(I, 0) and the second row of N is the constraint
+ * G(omega, psi) = -L psi - omega; psi_{n+1} = psi_n + dt sum_i b_i l_i.
+ *
+ * Each step solves the stage equations by the Newton-like iteration of
+ * Algorithm 1 (Sec. 5): the stage block is transformed by the real Schur
+ * vectors of A0^{-1} (Sec. 3.1), the 1x1 and 2x2 diagonal blocks D_i of
+ * Eq. diag_blocks are solved by flexible GMRES preconditioned by the block
+ * lower-triangular L_P of Eq. Lprec with gamma* (Eq. gamma*), and the inner
+ * inverses (gamma M - dt L)^{-1} are one geometric-multigrid V-cycle each.
+ * N and its Jacobian are built-in periodic finite-difference stencils chosen
+ * by `op`; they are not callbacks (device kernels cannot call host code).
+ *
+ * Conventions
+ *  - All floating-point data are IEEE binary64.
+ *  - A state vector holds ncomp * n^dim values, component-major; a 2D field is
+ *    row-major [y][x] (x fastest).  ncomp = 1 for the 1D operators, 2 for
+ *    Burgers-2D (u, v) and VSF (omega, psi).  A stage block holds s states,
+ *    stage-major.
+ *  - `*_on_device` = 1 means the pointer is CUDA device memory on the current
+ *    device (e.g. a torch tensor's data_ptr()); 0 means host memory.
+ *  - The caller owns every buffer it passes; the library copies in and out.
+ *    The handle owns all device memory it allocates (one arena, sized at
+ *    irk_create) and releases it in irk_destroy.
+ *  - Work is issued on the stream given to irk_create (NULL = a stream the
+ *    library creates).  Calls return after their results are complete.
+ *  - Every call returns a status.  A failed irk_step leaves the state at the
+ *    last accepted step.  irk_last_error() describes the most recent failure.
+ *  - Calls on one handle must not overlap; distinct handles are independent.
+ */
+#ifndef IRK_H
+#define IRK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct irk_handle irk_handle;
+
+typedef enum {
+  IRK_OK = 0,
+  IRK_ERR_INVALID = 1,          /* bad argument or unsupported configuration */
+  IRK_ERR_NOMEM = 2,            /* device or host allocation failed */
+  IRK_ERR_CUDA = 3,             /* a CUDA runtime call failed */
+  IRK_ERR_NEWTON_DIVERGED = 4,  /* non-finite or growing stage residual */
+  IRK_ERR_NEWTON_MAXIT = 5,     /* residual tolerance not met in newton_maxit */
+  IRK_ERR_KRYLOV_BREAKDOWN = 6, /* FGMRES lost its basis or did not converge */
+  IRK_ERR_TIMEOUT = 7,          /* a bounded device wait gave up */
+  IRK_ERR_NO_DEVICE = 8         /* no CUDA device is available */
+} irk_status;
+
+typedef enum { IRK_GAUSS = 0 } irk_family;
+
+typedef enum {
+  IRK_OP_DIFFUSION_1D = 0, /* N = nu D2 u                       (linear test)   */
+  IRK_OP_BURGERS_1D = 1,   /* N = -(u_{i+1}^2 - u_{i-1}^2)/(4h) + nu D2 u        */
+  IRK_OP_BURGERS_2D = 2,   /* N = (-u Dx u - v Dy u + nu L u, same for v)        */
+  IRK_OP_VSF_2D = 3        /* N = (J_A(psi, omega) + nu L omega, -L psi - omega) */
+} irk_op;
+
+typedef enum { IRK_MASS_IDENTITY = 0, IRK_MASS_DAE = 1 } irk_mass;
+
+typedef enum { IRK_MG_FP64 = 0, IRK_MG_FP32 = 1, IRK_MG_BF16 = 2 } irk_mg_precision;
+
+typedef struct {
+  int family;        /* irk_family; only IRK_GAUSS */
+  int stages;        /* s, 1..5 */
+  int op;            /* irk_op */
+  int mass;          /* irk_mass; must be IRK_MASS_DAE exactly for IRK_OP_VSF_2D */
+  int n;             /* grid points per dimension, power of two, 8..8192 */
+  double length;     /* periodic domain [0, length)^dim */
+  double nu;         /* viscosity (1/Re for VSF), > 0 */
+  int forcing;       /* 0, or 1 = manufactured source of the 1D operators */
+  double newton_rtol;   /* stop at ||F(k)|| <= newton_rtol ||F(0)||; default 1e-10 */
+  int newton_maxit;     /* default 20 */
+  double krylov_rtol;   /* loosest FGMRES relative tolerance per block; default 1e-3 */
+  int krylov_restart;   /* FGMRES(m) restart length m, 1..64; default 30 */
+  int krylov_maxit;     /* total FGMRES iterations per block solve; default 200 */
+  int nonlinear_variant;/* Newton-like variant of Sec. 3.2: 2 or 3; default 3 */
+  int gamma_mode;       /* 0: gamma* = eta + beta^2/eta (Eq. gamma*), 1: gamma = eta */
+  int mg_precision;     /* irk_mg_precision of the V-cycle preconditioner */
+  int mg_levels;        /* 0 = coarsen down to the coarsest size below */
+  int mg_pre, mg_post;  /* damped-Jacobi sweeps per level; default 2, 2 */
+  int mg_coarse_sweeps; /* sweeps on the coarsest level; default 40 */
+  double mg_omega;      /* Jacobi damping; 0 = default (0.8 in 2D, 2/3 in 1D) */
+  int profile;          /* 1 = time each kernel class with CUDA events */
+} irk_config;
+
+typedef struct {
+  int steps;            /* accepted steps in this call */
+  int newton_its;       /* Newton iterations (summed over steps) */
+  int krylov_its;       /* FGMRES iterations (summed over blocks and steps) */
+  int prec_apps;        /* preconditioner applications: 1 per 1x1 and 2 per 2x2
+                           Krylov iteration (counting rule of Sec. 7.1.1) */
+  int vcycles;          /* V-cycles applied */
+  int max_newton_its;   /* worst step */
+  double final_rel_res; /* ||F|| / ||F(0)|| at acceptance of the last step */
+} irk_stats;
+
+typedef struct {
+  char name[32];        /* kernel class */
+  long long launches;
+  double ms;            /* summed CUDA-event time of its launches */
+  double bytes;         /* summed algorithmic DRAM bytes (minimum traffic) */
+  double flops;         /* summed algorithmic floating-point operations */
+} irk_kernel_stat;
+
+/* Fill *cfg with the defaults listed above (Gauss s=2, Burgers-1D n=256). */
+void irk_config_default(irk_config* cfg);
+
+/* Create a solver for cfg with initial state u0 (ncomp*n^dim values).
+ * For IRK_OP_VSF_2D only omega is read from u0 (first n^2 values); psi is
+ * made consistent by solving -L psi = omega (zero mean) on the device.
+ * cuda_stream: a cudaStream_t, or NULL.  Validation (Assumption 1, Sec. 2.2):
+ * rejects s outside 1..5, n not a power of two, nu <= 0, a mass that does not
+ * match op.  On success *out owns the device arena. */
+irk_status irk_create(const irk_config* cfg, const double* u0, int u0_on_device,
+                      void* cuda_stream, irk_handle** out);
+
+/* Advance nsteps steps of size dt from time t_n (Algorithm 1 per step).
+ * stats may be NULL. */
+irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats* stats);
+
+/* Copy the current state out / in (ncomp*n^dim values; VSF: omega then psi). */
+irk_status irk_get_state(irk_handle* h, double* dst, int dst_on_device);
+irk_status irk_set_state(irk_handle* h, const double* src, int src_on_device);
+
+/* Stage vectors k_1..k_s of the last accepted step (s*ncomp*n^dim values). */
+irk_status irk_get_stages(irk_handle* h, double* dst, int dst_on_device);
+
+/* Stage residual F_i = M k_i - N(u + dt sum_j a_ij k_j, t_n + c_i dt)
+ * (Eq. stages) of a caller-given stage block K about the current state.
+ * K and F hold s*ncomp*n^dim values. */
+irk_status irk_stage_residual(irk_handle* h, double t_n, double dt, const double* K,
+                              double* F, int on_device);
+
+/* Jacobian-vector product of the stage equations (Eq. k0):
+ * (J V)_i = M v_i - dt N'(Y_i) sum_j a_ij v_j with Y_i the stage states of K. */
+irk_status irk_stage_jacobian_apply(irk_handle* h, double dt, const double* K,
+                                    const double* V, double* JV, int on_device);
+
+/* Host-only: tableau of `family` with s stages and the standardized real Schur
+ * form A0^{-1} = Q0 R0 Q0^T (Sec. 3.1).  A, Q0, R0 are s*s row-major; b, c
+ * length s; block_sizes receives the diagonal block sizes (1 or 2) in order,
+ * *nblocks their count.  Needs no GPU. */
+irk_status irk_tableau(int family, int s, double* A, double* b, double* c,
+                       double* Q0, double* R0, int* block_sizes, int* nblocks);
+
+/* Per-kernel-class timing gathered while cfg.profile = 1 (CUDA events on the
+ * handle's stream).  Writes up to max entries, *count = entries written. */
+irk_status irk_kernel_stats(irk_handle* h, irk_kernel_stat* out, int max, int* count);
+irk_status irk_reset_kernel_stats(irk_handle* h);
+
+/* Device bytes held by the handle's arena. */
+size_t irk_device_bytes(const irk_handle* h);
+
+/* Human-readable text of the last failure on h (valid until the next call on
+ * h), or of a failure in irk_create when h is NULL. */
+const char* irk_last_error(const irk_handle* h);
+const char* irk_status_string(irk_status st);
+
+/* Release the handle and its device memory.  NULL-safe. */
+void irk_destroy(irk_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IRK_H */

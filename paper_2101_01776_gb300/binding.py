@@ -1,0 +1,282 @@
+"""ctypes binding of the C ABI in include/irk.h (argument marshalling only).
+
+Every function below calls the entry point of the same name in libirk.so;
+all numerical work runs in the library's CUDA kernels.  Arrays may be NumPy
+arrays (host memory) or torch tensors (host or CUDA memory); they must be
+float64 and contiguous.  Importing this module raises if the library has not
+been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+_LIB_PATH = _build.LIB
+
+IRK_OK = 0
+IRK_ERR_INVALID = 1
+IRK_ERR_NOMEM = 2
+IRK_ERR_CUDA = 3
+IRK_ERR_NEWTON_DIVERGED = 4
+IRK_ERR_NEWTON_MAXIT = 5
+IRK_ERR_KRYLOV_BREAKDOWN = 6
+IRK_ERR_TIMEOUT = 7
+IRK_ERR_NO_DEVICE = 8
+
+IRK_GAUSS = 0
+IRK_OP_DIFFUSION_1D, IRK_OP_BURGERS_1D, IRK_OP_BURGERS_2D, IRK_OP_VSF_2D = 0, 1, 2, 3
+IRK_MASS_IDENTITY, IRK_MASS_DAE = 0, 1
+IRK_MG_FP64, IRK_MG_FP32, IRK_MG_BF16 = 0, 1, 2
+
+OP_NAMES = {"diffusion1d": IRK_OP_DIFFUSION_1D, "burgers1d": IRK_OP_BURGERS_1D,
+            "burgers2d": IRK_OP_BURGERS_2D, "vsf": IRK_OP_VSF_2D}
+
+
+class IrkConfig(C.Structure):
+    _fields_ = [
+        ("family", C.c_int), ("stages", C.c_int), ("op", C.c_int), ("mass", C.c_int),
+        ("n", C.c_int), ("length", C.c_double), ("nu", C.c_double), ("forcing", C.c_int),
+        ("newton_rtol", C.c_double), ("newton_maxit", C.c_int),
+        ("krylov_rtol", C.c_double), ("krylov_restart", C.c_int), ("krylov_maxit", C.c_int),
+        ("nonlinear_variant", C.c_int), ("gamma_mode", C.c_int),
+        ("mg_precision", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
+        ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double),
+        ("profile", C.c_int),
+    ]
+
+
+class IrkStats(C.Structure):
+    _fields_ = [
+        ("steps", C.c_int), ("newton_its", C.c_int), ("krylov_its", C.c_int),
+        ("prec_apps", C.c_int), ("vcycles", C.c_int), ("max_newton_its", C.c_int),
+        ("final_rel_res", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class IrkKernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_longlong), ("ms", C.c_double),
+                ("bytes", C.c_double), ("flops", C.c_double)]
+
+
+class IrkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                          "`python -m paper_2101_01776_gb300.build` (needs nvcc)")
+    lib = C.CDLL(_LIB_PATH)
+    vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    P = C.POINTER
+    sig = {
+        "irk_config_default": (None, [P(IrkConfig)]),
+        "irk_create": (i, [P(IrkConfig), vp, i, vp, P(vp)]),
+        "irk_step": (i, [vp, d, d, i, P(IrkStats)]),
+        "irk_get_state": (i, [vp, vp, i]),
+        "irk_set_state": (i, [vp, vp, i]),
+        "irk_get_stages": (i, [vp, vp, i]),
+        "irk_stage_residual": (i, [vp, d, d, vp, vp, i]),
+        "irk_stage_jacobian_apply": (i, [vp, d, vp, vp, vp, i]),
+        "irk_tableau": (i, [i, i, vp, vp, vp, vp, vp, vp, vp]),
+        "irk_kernel_stats": (i, [vp, P(IrkKernelStat), i, P(i)]),
+        "irk_reset_kernel_stats": (i, [vp]),
+        "irk_device_bytes": (sz, [vp]),
+        "irk_last_error": (C.c_char_p, [vp]),
+        "irk_status_string": (C.c_char_p, [i]),
+        "irk_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+EXPORTED = (
+    "irk_config_default", "irk_create", "irk_step", "irk_get_state", "irk_set_state",
+    "irk_get_stages", "irk_stage_residual", "irk_stage_jacobian_apply", "irk_tableau",
+    "irk_kernel_stats", "irk_reset_kernel_stats", "irk_device_bytes", "irk_last_error",
+    "irk_status_string", "irk_destroy",
+)
+
+
+def status_string(st: int) -> str:
+    return LIB.irk_status_string(st).decode()
+
+
+def irk_config_default(**overrides) -> IrkConfig:
+    cfg = IrkConfig()
+    LIB.irk_config_default(C.byref(cfg))
+    for k, v in overrides.items():
+        if k == "op" and isinstance(v, str):
+            v = OP_NAMES[v]
+        setattr(cfg, k, v)
+    if "op" in overrides and "mass" not in overrides:
+        cfg.mass = IRK_MASS_DAE if cfg.op == IRK_OP_VSF_2D else IRK_MASS_IDENTITY
+    return cfg
+
+
+def _ptr(x):
+    """(address, on_device) of a contiguous float64 NumPy array or torch tensor."""
+    if hasattr(x, "data_ptr"):  # torch tensor
+        if not x.is_contiguous() or str(x.dtype) != "torch.float64":
+            raise ValueError("tensor must be contiguous float64")
+        return C.c_void_p(x.data_ptr()), int(x.is_cuda)
+    import numpy as np
+    if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+        raise ValueError("array must be a contiguous float64 numpy array")
+    return C.c_void_p(x.ctypes.data), 0
+
+
+def _check(st: int, handle=None):
+    if st != IRK_OK:
+        msg = LIB.irk_last_error(handle).decode(errors="replace")
+        raise IrkError(st, msg)
+
+
+def irk_create(cfg: IrkConfig, u0, stream=None):
+    """Return an opaque handle (c_void_p).  stream: torch.cuda.Stream, raw handle or None."""
+    h = C.c_void_p()
+    p, dev = _ptr(u0)
+    sp = None
+    if stream is not None:
+        sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(LIB.irk_create(C.byref(cfg), p, dev, sp, C.byref(h)))
+    return h
+
+
+def irk_step(h, t_n: float, dt: float, nsteps: int = 1) -> IrkStats:
+    st = IrkStats()
+    _check(LIB.irk_step(h, t_n, dt, nsteps, C.byref(st)), h)
+    return st
+
+
+def irk_get_state(h, dst):
+    p, dev = _ptr(dst)
+    _check(LIB.irk_get_state(h, p, dev), h)
+    return dst
+
+
+def irk_set_state(h, src):
+    p, dev = _ptr(src)
+    _check(LIB.irk_set_state(h, p, dev), h)
+
+
+def irk_get_stages(h, dst):
+    p, dev = _ptr(dst)
+    _check(LIB.irk_get_stages(h, p, dev), h)
+    return dst
+
+
+def irk_stage_residual(h, t_n: float, dt: float, K, F):
+    pk, dk = _ptr(K)
+    pf, df = _ptr(F)
+    if dk != df:
+        raise ValueError("K and F must live in the same memory space")
+    _check(LIB.irk_stage_residual(h, t_n, dt, pk, pf, dk), h)
+    return F
+
+
+def irk_stage_jacobian_apply(h, dt: float, K, V, JV):
+    (pk, dk), (pv, dv), (pj, dj) = _ptr(K), _ptr(V), _ptr(JV)
+    if not (dk == dv == dj):
+        raise ValueError("K, V and JV must live in the same memory space")
+    _check(LIB.irk_stage_jacobian_apply(h, dt, pk, pv, pj, dk), h)
+    return JV
+
+
+def irk_tableau(s: int, family: int = IRK_GAUSS):
+    """Host-only tableau and real Schur form: dict of numpy arrays."""
+    import numpy as np
+    A, Q, R = (np.zeros((s, s)) for _ in range(3))
+    b, c = np.zeros(s), np.zeros(s)
+    bs = np.zeros(s, dtype=np.int32)
+    nb = C.c_int()
+    _check(LIB.irk_tableau(family, s, A.ctypes.data, b.ctypes.data, c.ctypes.data,
+                           Q.ctypes.data, R.ctypes.data, bs.ctypes.data, C.byref(nb)))
+    return {"A": A, "b": b, "c": c, "Q0": Q, "R0": R, "block_sizes": list(bs[:nb.value])}
+
+
+def irk_kernel_stats(h):
+    arr = (IrkKernelStat * 64)()
+    n = C.c_int()
+    _check(LIB.irk_kernel_stats(h, arr, 64, C.byref(n)), h)
+    return [{"name": arr[k].name.decode(), "launches": arr[k].launches, "ms": arr[k].ms,
+             "bytes": arr[k].bytes, "flops": arr[k].flops} for k in range(n.value)]
+
+
+def irk_reset_kernel_stats(h):
+    _check(LIB.irk_reset_kernel_stats(h), h)
+
+
+def irk_device_bytes(h) -> int:
+    return int(LIB.irk_device_bytes(h))
+
+
+def irk_last_error(h=None) -> str:
+    return LIB.irk_last_error(h).decode(errors="replace")
+
+
+def irk_destroy(h):
+    LIB.irk_destroy(h)
+
+
+class IrkSolver:
+    """Owning wrapper around one handle (marshalling only)."""
+
+    def __init__(self, u0, stream=None, **cfg):
+        self.cfg = irk_config_default(**cfg)
+        self.h = irk_create(self.cfg, u0, stream)
+
+    @property
+    def ncomp(self):
+        return 2 if self.cfg.op in (IRK_OP_BURGERS_2D, IRK_OP_VSF_2D) else 1
+
+    @property
+    def shape(self):
+        d = 2 if self.cfg.op in (IRK_OP_BURGERS_2D, IRK_OP_VSF_2D) else 1
+        return (self.ncomp,) + (self.cfg.n,) * d
+
+    def step(self, t_n, dt, nsteps=1):
+        return irk_step(self.h, t_n, dt, nsteps)
+
+    def state(self, out=None):
+        import numpy as np
+        if out is None:
+            out = np.empty(self.shape)
+        return irk_get_state(self.h, out)
+
+    def set_state(self, src):
+        irk_set_state(self.h, src)
+
+    def stages(self, out=None):
+        import numpy as np
+        if out is None:
+            out = np.empty((self.cfg.stages,) + self.shape)
+        return irk_get_stages(self.h, out)
+
+    def close(self):
+        if self.h is not None:
+            irk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,151 @@
+// Internal declarations shared by the solver's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/irk.h"
+
+#define IRK_MAXS 5
+#define IRK_MAX_TERMS 5
+#define IRK_MAX_LEVELS 16
+#define IRK_BLAS_THREADS 256
+
+namespace irk {
+
+struct HostTableau {
+  int s;
+  double A[IRK_MAXS * IRK_MAXS], b[IRK_MAXS], c[IRK_MAXS];
+  double Ainv[IRK_MAXS * IRK_MAXS], Q[IRK_MAXS * IRK_MAXS], R[IRK_MAXS * IRK_MAXS];
+  double QR[IRK_MAXS * IRK_MAXS];  // Q0 R0: back-transform of Algorithm 1
+  int nblk, bstart[IRK_MAXS], bsize[IRK_MAXS];
+  double eta[IRK_MAXS], beta2[IRK_MAXS], gamma_star[IRK_MAXS];
+};
+
+int build_tableau(int family, int s, HostTableau* t, char* err, size_t errlen);
+
+// ---------------------------------------------------------------------------
+// Grid and operator description passed to every stencil kernel.
+struct GridDesc {
+  int dim;       // 1 or 2
+  int n;         // points per dimension (power of two)
+  int logn;
+  int npts;      // n^dim
+  int ncomp;     // state components
+  int op;        // irk_op
+  double h, inv2h, inv4h, invh2, inv12h2;
+  double nu;
+};
+
+// Pointwise stage states and combined fields (steps a2 + a7 setup):
+//   Y_i = u + dt sum_j A_ij K_j ;  Ybar_q = sum_m D_qm Y_m
+struct StageStateArgs {
+  int s, ncombo;
+  long long L;           // ncomp * npts
+  double dt;
+  double A[IRK_MAXS * IRK_MAXS];
+  double D[IRK_MAXS * (IRK_MAXS + 1) / 2 * IRK_MAXS];  // ncombo x s
+  const double* u;       // may be null (treated as 0)
+  const double* K;       // s * L
+  double* Y;             // s * L (may be null)
+  double* combos;        // ncombo * L (may be null)
+};
+
+// Stage residual (step a3) with the Algorithm-1 RHS transform (step a5):
+//   F_i = M K_i - N(Y_i, t_n + c_i dt);  rhs_k = -sum_i Q0_{ik} F_i ; partial ||F||^2
+struct ResidualArgs {
+  int s;
+  double Q[IRK_MAXS * IRK_MAXS];
+  double tstage[IRK_MAXS];
+  int forcing;
+  const double* Y;       // s * L
+  const double* K;       // s * L
+  double* rhs;           // s * L, may be null
+  double* Fraw;          // s * L, may be null (untransformed residual)
+  double* partials;      // one per block
+};
+
+// Generic block operator (steps a6, a7, a9 coupling):
+//   y_r = alpha * base_r + sigma * sum_t [ m_t M x_t - dt ( Jadv(Ybar_t) x_t + lin_t Jlin x_t ) ]
+struct OpTerm {
+  const double* x;       // ncomp * npts
+  const double* combo;   // ncomp * npts or null (no advective part)
+  double m;              // mass coefficient
+  double lin;            // coefficient of the state-independent linear part
+};
+struct OpRow {
+  double* y;
+  const double* base;    // may be null
+  double alpha, sigma;
+  int nterm;
+  OpTerm t[IRK_MAX_TERMS];
+};
+struct StageOpArgs {
+  int nrow;
+  double dt;
+  OpRow row[2];
+  double* copy_dst;      // optional: copy_src -> copy_dst (ncomp*npts*copy_rows)
+  const double* copy_src;
+  long long copy_len;
+};
+
+// ---------------------------------------------------------------------------
+// Multigrid level (one scalar-operator hierarchy, all state components).
+struct MGLevelDesc {
+  int n, logn, npts;
+  double h;
+};
+
+enum MGKind { MG_ADVECTIVE = 0, MG_CONSERVATIVE_1D = 1, MG_DIFFUSION = 2 };
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the .cu files).
+void launch_stage_states(const GridDesc& g, const StageStateArgs& a, cudaStream_t st);
+int residual_blocks(const GridDesc& g);
+void launch_residual(const GridDesc& g, const ResidualArgs& a, cudaStream_t st);
+void launch_stage_op(const GridDesc& g, const StageOpArgs& a, cudaStream_t st);
+void launch_stage_update(long long L, int s, const double* QR, const double* yhat, double* K,
+                         cudaStream_t st);
+void launch_u_update(long long L, int s, const double* b, double dt, const double* K, double* u,
+                     cudaStream_t st);
+void launch_velocity_from_combo(const GridDesc& g, const double* combo, void* vel, int prec,
+                                cudaStream_t st);
+void launch_remove_mean(long long npts, int nfields, long long stride, double* x, double* scratch,
+                        cudaStream_t st);
+
+// BLAS-1 for FGMRES (FP64, deterministic reductions)
+int blas_blocks(long long L);
+void launch_multi_dot(const double* V, long long ldv, int nv, const double* w, long long L,
+                      double* partials, cudaStream_t st);
+void launch_update_dot(const double* V, long long ldv, int nv, const double* hdev, double* w,
+                       long long L, int with_dots, double* partials, cudaStream_t st);
+void launch_reduce(const double* partials, int nblk, int stride, int nvals, double* out,
+                   cudaStream_t st);
+void launch_scale_copy(const double* w, double scale, double* v, double* v2, long long L,
+                       cudaStream_t st);
+void launch_lincomb(double* x, const double* Z, long long ldz, int k, const double* y,
+                    long long L, cudaStream_t st);
+void launch_norm2(const double* x, long long L, double* partials, cudaStream_t st);
+void launch_axpby(double* y, double a, const double* x, double b, long long L, cudaStream_t st);
+
+// Multigrid (templated on the storage precision; prec = irk_mg_precision)
+void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
+                      double cadv, double cdiff, double omega, const void* vel, const void* b,
+                      const void* w_in, void* w_out, int first, cudaStream_t st);
+void launch_mg_residual(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp,
+                        double sigma, double cadv, double cdiff, const void* vel, const void* b,
+                        const void* w, void* r, cudaStream_t st);
+void launch_mg_restrict(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* rf,
+                        void* bc, cudaStream_t st);
+void launch_mg_prolong_add(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* wc,
+                           void* wf, cudaStream_t st);
+void launch_mg_coarse(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
+                      double cadv, double cdiff, double omega, int sweeps, int project_mean,
+                      const void* vel, const void* b, void* w, cudaStream_t st);
+void launch_mg_convert_in(int prec, const double* src, void* dst, long long len, cudaStream_t st);
+void launch_mg_convert_out(int prec, const void* src, double* dst, long long len,
+                           cudaStream_t st);
+size_t mg_elem_size(int prec);
+
+}  // namespace irk

@@ -1,0 +1,368 @@
+// Geometric multigrid V-cycle kernels (steps a9/a10): one V-cycle stands in
+// for each inner inverse (gamma M - dt L)^{-1} of the block preconditioner
+// L_P (Eq. Lprec; inexact inner inverses as in Sec. 4).
+//
+// Scalar operator per state component on a periodic grid with spacing h:
+//   A w = sigma w + cadv * adv(a, w) - cdiff * L_h w
+//   MG_ADVECTIVE        adv = a_x Dx w + a_y Dy w   (central; 2D or 1D)
+//   MG_CONSERVATIVE_1D  adv = (a_E w_E - a_W w_W) / (2h)
+//   MG_DIFFUSION        adv = 0 (cadv ignored)
+// The velocity a is the frozen combined field of the block row, restricted
+// to every level by full weighting; coarse operators are rediscretised at 2h.
+// Smoother: damped Jacobi; transfers: full weighting and (bi)linear
+// interpolation on vertex-centred grids (coarse point I = fine point 2I);
+// coarsest level: Jacobi sweeps in one CTA out of shared memory.
+//
+// Storage precision: double (FP64), float (FP32) or bf16 with float
+// arithmetic (BF16-stored data, FP32 accumulation).
+#include <cuda_bf16.h>
+
+#include "irk_internal.h"
+
+namespace irk {
+
+template <typename TS> struct Cmp { typedef float T; };
+template <> struct Cmp<double> { typedef double T; };
+
+template <typename TS>
+__device__ __forceinline__ typename Cmp<TS>::T ldv(const TS* p) { return *p; }
+template <>
+__device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+template <typename TS, typename TC>
+__device__ __forceinline__ void stv(TS* p, TC v) { *p = (TS)v; }
+template <>
+__device__ __forceinline__ void stv<__nv_bfloat16, float>(__nv_bfloat16* p, float v) {
+  *p = __float2bfloat16_rn(v);
+}
+
+struct LvIdx {
+  int c, e, w, n, s;
+};
+
+template <int DIM>
+__device__ __forceinline__ LvIdx lv_nbr(const MGLevelDesc& lv, int p) {
+  LvIdx r;
+  r.c = p;
+  const int m = lv.n - 1;
+  if (DIM == 1) {
+    r.e = (p + 1) & m;
+    r.w = (p - 1) & m;
+    r.n = r.s = p;
+  } else {
+    const int i = p & m, j = p >> lv.logn;
+    r.e = (j << lv.logn) + ((i + 1) & m);
+    r.w = (j << lv.logn) + ((i - 1) & m);
+    r.n = (((j + 1) & m) << lv.logn) + i;
+    r.s = (((j - 1) & m) << lv.logn) + i;
+  }
+  return r;
+}
+
+// (A w)(p) for one component; w points at that component's field.
+template <typename TS, int DIM, int KIND>
+__device__ __forceinline__ typename Cmp<TS>::T apply_A(const LvIdx& q, const TS* __restrict__ w,
+                                                       const TS* __restrict__ vel, int npts,
+                                                       typename Cmp<TS>::T sigma,
+                                                       typename Cmp<TS>::T cadv,
+                                                       typename Cmp<TS>::T cdiff,
+                                                       typename Cmp<TS>::T inv2h,
+                                                       typename Cmp<TS>::T invh2) {
+  typedef typename Cmp<TS>::T TC;
+  const TC wc = ldv(w + q.c), we = ldv(w + q.e), ww = ldv(w + q.w);
+  TC lap, adv = 0;
+  if (DIM == 1) {
+    lap = (we + ww - TC(2) * wc) * invh2;
+  } else {
+    const TC wn = ldv(w + q.n), ws = ldv(w + q.s);
+    lap = (we + ww + wn + ws - TC(4) * wc) * invh2;
+    if (KIND == MG_ADVECTIVE)
+      adv = (ldv(vel + q.c) * (we - ww) + ldv(vel + npts + q.c) * (wn - ws)) * inv2h;
+  }
+  if (DIM == 1 && KIND == MG_ADVECTIVE) adv = ldv(vel + q.c) * (we - ww) * inv2h;
+  if (KIND == MG_CONSERVATIVE_1D) adv = (ldv(vel + q.e) * we - ldv(vel + q.w) * ww) * inv2h;
+  return sigma * wc + cadv * adv - cdiff * lap;
+}
+
+template <typename TS, int DIM, int KIND>
+__global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, double sigma_,
+                                                   double cadv_, double cdiff_, double omega_,
+                                                   const TS* __restrict__ vel,
+                                                   const TS* __restrict__ b,
+                                                   const TS* __restrict__ w_in,
+                                                   TS* __restrict__ w_out, int first) {
+  typedef typename Cmp<TS>::T TC;
+  const TC sigma = sigma_, cadv = cadv_, cdiff = cdiff_, omega = omega_;
+  const TC inv2h = TC(0.5 / lv.h), invh2 = TC(1.0 / (lv.h * lv.h));
+  const TC dinv = omega / (sigma + cdiff * TC(2 * DIM) * invh2);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lv.npts; p += gridDim.x * blockDim.x) {
+    const LvIdx q = lv_nbr<DIM>(lv, p);
+    for (int c = 0; c < ncomp; ++c) {
+      const long long off = (long long)c * lv.npts;
+      const TC bc = ldv(b + off + p);
+      TC out;
+      if (first) {
+        out = dinv * bc;
+      } else {
+        const TC aw = apply_A<TS, DIM, KIND>(q, w_in + off, vel, lv.npts, sigma, cadv, cdiff,
+                                             inv2h, invh2);
+        out = ldv(w_in + off + p) + dinv * (bc - aw);
+      }
+      stv<TS, TC>(w_out + off + p, out);
+    }
+  }
+}
+
+template <typename TS, int DIM, int KIND>
+__global__ void __launch_bounds__(256) k_mg_residual(MGLevelDesc lv, int ncomp, double sigma_,
+                                                     double cadv_, double cdiff_,
+                                                     const TS* __restrict__ vel,
+                                                     const TS* __restrict__ b,
+                                                     const TS* __restrict__ w, TS* __restrict__ r) {
+  typedef typename Cmp<TS>::T TC;
+  const TC sigma = sigma_, cadv = cadv_, cdiff = cdiff_;
+  const TC inv2h = TC(0.5 / lv.h), invh2 = TC(1.0 / (lv.h * lv.h));
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lv.npts; p += gridDim.x * blockDim.x) {
+    const LvIdx q = lv_nbr<DIM>(lv, p);
+    for (int c = 0; c < ncomp; ++c) {
+      const long long off = (long long)c * lv.npts;
+      const TC aw = apply_A<TS, DIM, KIND>(q, w + off, vel, lv.npts, sigma, cadv, cdiff, inv2h,
+                                           invh2);
+      stv<TS, TC>(r + off + p, ldv(b + off + p) - aw);
+    }
+  }
+}
+
+// Full weighting: fine -> coarse (coarse n = fine n / 2), all components.
+template <typename TS, int DIM>
+__global__ void __launch_bounds__(256) k_mg_restrict(MGLevelDesc fine, int ncomp,
+                                                     const TS* __restrict__ rf,
+                                                     TS* __restrict__ bc) {
+  typedef typename Cmp<TS>::T TC;
+  const int nc = fine.n >> 1, logc = fine.logn - 1, m = fine.n - 1;
+  const int ncpts = (DIM == 1) ? nc : nc * nc;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < ncpts; p += gridDim.x * blockDim.x) {
+    for (int c = 0; c < ncomp; ++c) {
+      const TS* f = rf + (long long)c * fine.npts;
+      TC v;
+      if (DIM == 1) {
+        const int i = 2 * p;
+        v = (ldv(f + ((i - 1) & m)) + TC(2) * ldv(f + i) + ldv(f + ((i + 1) & m))) * TC(0.25);
+      } else {
+        const int I = p & (nc - 1), J = p >> logc;
+        const int i = 2 * I, j = 2 * J;
+        const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
+        const int lf = fine.logn;
+        const TC centre = ldv(f + (j << lf) + i);
+        const TC edges = ldv(f + (j << lf) + ip) + ldv(f + (j << lf) + im) +
+                         ldv(f + (jp << lf) + i) + ldv(f + (jm << lf) + i);
+        const TC corners = ldv(f + (jp << lf) + ip) + ldv(f + (jp << lf) + im) +
+                           ldv(f + (jm << lf) + ip) + ldv(f + (jm << lf) + im);
+        v = (TC(4) * centre + TC(2) * edges + corners) * TC(0.0625);
+      }
+      stv<TS, TC>(bc + (long long)c * ncpts + p, v);
+    }
+  }
+}
+
+// Bilinear (linear in 1D) interpolation of the coarse correction, added to w.
+template <typename TS, int DIM>
+__global__ void __launch_bounds__(256) k_mg_prolong_add(MGLevelDesc fine, int ncomp,
+                                                        const TS* __restrict__ wc,
+                                                        TS* __restrict__ wf) {
+  typedef typename Cmp<TS>::T TC;
+  const int nc = fine.n >> 1, logc = fine.logn - 1, mc = nc - 1;
+  const int ncpts = (DIM == 1) ? nc : nc * nc;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < fine.npts; p += gridDim.x * blockDim.x) {
+    for (int c = 0; c < ncomp; ++c) {
+      const TS* g = wc + (long long)c * ncpts;
+      TC e;
+      if (DIM == 1) {
+        const int I = p >> 1;
+        e = (p & 1) ? TC(0.5) * (ldv(g + I) + ldv(g + ((I + 1) & mc))) : ldv(g + I);
+      } else {
+        const int i = p & (fine.n - 1), j = p >> fine.logn;
+        const int I = i >> 1, J = j >> 1, I1 = (I + 1) & mc, J1 = (J + 1) & mc;
+        const TC c00 = ldv(g + (J << logc) + I);
+        if (!(i & 1) && !(j & 1)) e = c00;
+        else if ((i & 1) && !(j & 1)) e = TC(0.5) * (c00 + ldv(g + (J << logc) + I1));
+        else if (!(i & 1) && (j & 1)) e = TC(0.5) * (c00 + ldv(g + (J1 << logc) + I));
+        else
+          e = TC(0.25) * (c00 + ldv(g + (J << logc) + I1) + ldv(g + (J1 << logc) + I) +
+                          ldv(g + (J1 << logc) + I1));
+      }
+      TS* dst = wf + (long long)c * fine.npts + p;
+      stv<TS, TC>(dst, ldv(dst) + e);
+    }
+  }
+}
+
+// Coarsest level in one CTA: w = 0, `sweeps` damped-Jacobi sweeps from shared
+// memory.  project_mean removes the constant null mode of a pure Laplacian.
+template <typename TS, int DIM, int KIND>
+__global__ void k_mg_coarse(MGLevelDesc lv, int ncomp, double sigma_, double cadv_, double cdiff_,
+                            double omega_, int sweeps, int project_mean,
+                            const TS* __restrict__ vel, const TS* __restrict__ b,
+                            TS* __restrict__ w) {
+  typedef typename Cmp<TS>::T TC;
+  extern __shared__ unsigned char smem_raw[];
+  TC* sw = reinterpret_cast<TC*>(smem_raw);          // ncomp * npts
+  TC* sw2 = sw + ncomp * lv.npts;                    // ncomp * npts
+  TC* sb = sw2 + ncomp * lv.npts;                    // ncomp * npts
+  TC* sv = sb + ncomp * lv.npts;                     // DIM * npts
+  __shared__ TC red[32];
+  const TC sigma = sigma_, cadv = cadv_, cdiff = cdiff_, omega = omega_;
+  const TC inv2h = TC(0.5 / lv.h), invh2 = TC(1.0 / (lv.h * lv.h));
+  const TC dinv = omega / (sigma + cdiff * TC(2 * DIM) * invh2);
+  const int tot = ncomp * lv.npts;
+  for (int k = threadIdx.x; k < tot; k += blockDim.x) {
+    sb[k] = ldv(b + k);
+    sw[k] = 0;
+  }
+  for (int k = threadIdx.x; k < DIM * lv.npts; k += blockDim.x) sv[k] = vel ? ldv(vel + k) : TC(0);
+  __syncthreads();
+  auto remove_mean = [&](TC* f) {
+    for (int c = 0; c < ncomp; ++c) {
+      if (threadIdx.x == 0) {
+        TC s = 0;
+        for (int k = 0; k < lv.npts; ++k) s += f[c * lv.npts + k];
+        red[0] = s / TC(lv.npts);
+      }
+      __syncthreads();
+      const TC mean = red[0];
+      for (int k = threadIdx.x; k < lv.npts; k += blockDim.x) f[c * lv.npts + k] -= mean;
+      __syncthreads();
+    }
+  };
+  if (project_mean) remove_mean(sb);
+  for (int it = 0; it < sweeps; ++it) {
+    for (int k = threadIdx.x; k < tot; k += blockDim.x) {
+      const int c = k / lv.npts, p = k - c * lv.npts;
+      const LvIdx q = lv_nbr<DIM>(lv, p);
+      const TC* f = sw + c * lv.npts;
+      const TC wc = f[q.c], we = f[q.e], ww = f[q.w];
+      TC lap, adv = 0;
+      if (DIM == 1) {
+        lap = (we + ww - TC(2) * wc) * invh2;
+        if (KIND == MG_ADVECTIVE) adv = sv[q.c] * (we - ww) * inv2h;
+        if (KIND == MG_CONSERVATIVE_1D) adv = (sv[q.e] * we - sv[q.w] * ww) * inv2h;
+      } else {
+        const TC wn = f[q.n], ws = f[q.s];
+        lap = (we + ww + wn + ws - TC(4) * wc) * invh2;
+        if (KIND == MG_ADVECTIVE) adv = (sv[q.c] * (we - ww) + sv[lv.npts + q.c] * (wn - ws)) * inv2h;
+      }
+      const TC aw = sigma * wc + cadv * adv - cdiff * lap;
+      sw2[k] = wc + dinv * (sb[k] - aw);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < tot; k += blockDim.x) sw[k] = sw2[k];
+    __syncthreads();
+  }
+  if (project_mean) remove_mean(sw);
+  for (int k = threadIdx.x; k < tot; k += blockDim.x) stv<TS, TC>(w + k, sw[k]);
+}
+
+template <typename TS>
+__global__ void k_convert_in(const double* __restrict__ src, TS* __restrict__ dst, long long n) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x)
+    stv<TS, typename Cmp<TS>::T>(dst + p, (typename Cmp<TS>::T)src[p]);
+}
+
+template <typename TS>
+__global__ void k_convert_out(const TS* __restrict__ src, double* __restrict__ dst, long long n) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x)
+    dst[p] = (double)ldv(src + p);
+}
+
+// ---------------------------------------------------------------------------
+static int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+size_t mg_elem_size(int prec) {
+  return prec == IRK_MG_FP64 ? sizeof(double) : (prec == IRK_MG_FP32 ? sizeof(float) : 2);
+}
+
+#define IRK_DISPATCH_PREC(prec, ...)                                    \
+  do {                                                                  \
+    if ((prec) == IRK_MG_FP64) { typedef double TS; __VA_ARGS__; }      \
+    else if ((prec) == IRK_MG_FP32) { typedef float TS; __VA_ARGS__; }  \
+    else { typedef __nv_bfloat16 TS; __VA_ARGS__; }                     \
+  } while (0)
+
+#define IRK_DISPATCH_DK(dim, kind, ...)                                                  \
+  do {                                                                                    \
+    if ((dim) == 1) {                                                                     \
+      if ((kind) == MG_ADVECTIVE) { constexpr int DIM = 1, KIND = MG_ADVECTIVE; __VA_ARGS__; }   \
+      else if ((kind) == MG_CONSERVATIVE_1D) { constexpr int DIM = 1, KIND = MG_CONSERVATIVE_1D; __VA_ARGS__; } \
+      else { constexpr int DIM = 1, KIND = MG_DIFFUSION; __VA_ARGS__; }                          \
+    } else {                                                                              \
+      if ((kind) == MG_ADVECTIVE) { constexpr int DIM = 2, KIND = MG_ADVECTIVE; __VA_ARGS__; }   \
+      else { constexpr int DIM = 2, KIND = MG_DIFFUSION; __VA_ARGS__; }                          \
+    }                                                                                     \
+  } while (0)
+
+void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
+                      double cadv, double cdiff, double omega, const void* vel, const void* b,
+                      const void* w_in, void* w_out, int first, cudaStream_t st) {
+  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_smooth<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
+      lv, ncomp, sigma, cadv, cdiff, omega, (const TS*)vel, (const TS*)b, (const TS*)w_in,
+      (TS*)w_out, first))));
+}
+
+void launch_mg_residual(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp,
+                        double sigma, double cadv, double cdiff, const void* vel, const void* b,
+                        const void* w, void* r, cudaStream_t st) {
+  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_residual<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
+      lv, ncomp, sigma, cadv, cdiff, (const TS*)vel, (const TS*)b, (const TS*)w, (TS*)r))));
+}
+
+void launch_mg_restrict(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* rf,
+                        void* bc, cudaStream_t st) {
+  const long long nc = dim == 1 ? fine.n / 2 : (long long)(fine.n / 2) * (fine.n / 2);
+  IRK_DISPATCH_PREC(prec, {
+    if (dim == 1)
+      k_mg_restrict<TS, 1><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)rf, (TS*)bc);
+    else
+      k_mg_restrict<TS, 2><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)rf, (TS*)bc);
+  });
+}
+
+void launch_mg_prolong_add(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* wc,
+                           void* wf, cudaStream_t st) {
+  IRK_DISPATCH_PREC(prec, {
+    if (dim == 1)
+      k_mg_prolong_add<TS, 1><<<grid_for(fine.npts), 256, 0, st>>>(fine, ncomp, (const TS*)wc, (TS*)wf);
+    else
+      k_mg_prolong_add<TS, 2><<<grid_for(fine.npts), 256, 0, st>>>(fine, ncomp, (const TS*)wc, (TS*)wf);
+  });
+}
+
+void launch_mg_coarse(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
+                      double cadv, double cdiff, double omega, int sweeps, int project_mean,
+                      const void* vel, const void* b, void* w, cudaStream_t st) {
+  IRK_DISPATCH_PREC(prec, {
+    typedef typename Cmp<TS>::T TC;
+    const size_t smem = sizeof(TC) * ((size_t)3 * ncomp * lv.npts + (size_t)dim * lv.npts);
+    IRK_DISPATCH_DK(dim, kind, (k_mg_coarse<TS, DIM, KIND><<<1, 256, smem, st>>>(
+        lv, ncomp, sigma, cadv, cdiff, omega, sweeps, project_mean, (const TS*)vel,
+        (const TS*)b, (TS*)w)));
+  });
+}
+
+void launch_mg_convert_in(int prec, const double* src, void* dst, long long len, cudaStream_t st) {
+  IRK_DISPATCH_PREC(prec, (k_convert_in<TS><<<grid_for(len), 256, 0, st>>>(src, (TS*)dst, len)));
+}
+
+void launch_mg_convert_out(int prec, const void* src, double* dst, long long len,
+                           cudaStream_t st) {
+  IRK_DISPATCH_PREC(prec, (k_convert_out<TS><<<grid_for(len), 256, 0, st>>>((const TS*)src, dst, len)));
+}
+
+}  // namespace irk

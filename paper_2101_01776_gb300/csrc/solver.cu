@@ -1,0 +1,1145 @@
+// Host driver of the Gauss-IRK stage solve and the C ABI (include/irk.h).
+//
+// One IRK step (Algorithm 1, Sec. 5):
+//   k = 0; loop:
+//     Y_i, combined fields      k_stage_states           (Eq. stages, Eq. Q0approx)
+//     F, rhs = -(Q0^T (x) I) F   k_residual               (Eq. stages, Algorithm 1)
+//     stop when ||F|| <= newton_rtol ||F(0)||
+//     for the diagonal blocks from last to first:
+//       z = rhs_i - sum_{j>i} U_ij dk_hat_j              (Eq. D+U)
+//       dk_hat_i = FGMRES(D_i, z, L_P_i)                (Eq. diag_blocks, Eq. Lprec)
+//     k += (Q0 R0 (x) I) dk_hat
+//   u += dt sum_i b_i k_i                                (Eq. update)
+// L_P_i applies one V-cycle for (eta M - dt L_aa) and one for (gamma M - dt L_bb)
+// with gamma = gamma* = eta + beta^2/eta (Eq. gamma*) by default.
+//
+// The Newton-like variant 3 of Sec. 3.2 keeps every d_{k,l} L term inside the
+// block upper-triangular pattern of R0 (x) I (exact Newton for s = 2);
+// variant 2 keeps only the diagonal terms d_{k,k} L.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "irk_internal.h"
+
+using namespace irk;
+
+namespace {
+
+enum ProfClass {
+  P_STAGE = 0, P_RESID, P_STAGEOP, P_UPDATE, P_MG_SMOOTH, P_MG_RESID, P_MG_RESTRICT,
+  P_MG_PROLONG, P_MG_COARSE, P_MG_CONVERT, P_MG_SETUP, P_GS_DOT, P_GS_UPDATE, P_REDUCE,
+  P_SCALE, P_LINCOMB, P_NORM, P_AXPBY, P_MEAN, P_NCLASS
+};
+const char* kProfNames[P_NCLASS] = {
+  "stage_states", "residual", "stage_op", "stage_update", "mg_smooth", "mg_residual",
+  "mg_restrict", "mg_prolong", "mg_coarse", "mg_convert", "mg_setup", "gs_multi_dot",
+  "gs_update_dot", "reduce", "scale_copy", "lincomb", "norm2", "axpby", "remove_mean"};
+
+struct PendingEvent {
+  int cls;
+  int a, b;  // indices into the event pool
+  double bytes, flops;
+};
+
+struct MGLevel {
+  MGLevelDesc d;
+  void *w, *w2, *b, *r;
+};
+
+}  // namespace
+
+struct irk_handle {
+  irk_config cfg;
+  HostTableau tab;
+  GridDesc g;
+  int s = 0, C = 0, dim = 0, npts = 0;
+  long long L = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int device = 0;
+
+  char* arena = nullptr;
+  size_t arena_bytes = 0, arena_used = 0;
+
+  double *u = nullptr, *u_save = nullptr, *K = nullptr, *Y = nullptr, *rhs = nullptr,
+         *yhat = nullptr, *combos = nullptr, *zbuf = nullptr, *tmp = nullptr, *tmp2 = nullptr;
+  int ncombo = 0;
+  int combo_of[IRK_MAXS][IRK_MAXS];
+  double Dq[IRK_MAXS * (IRK_MAXS + 1) / 2 * IRK_MAXS];
+  int blk_of[IRK_MAXS];
+
+  // FGMRES
+  int m = 0;
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *partials = nullptr, *dscal = nullptr;
+  double* hbuf = nullptr;  // pinned host
+  int nparts = 0;
+
+  // multigrid
+  int prec = 0, nlev = 0, mg_kind = 0;
+  size_t esz = 8;
+  MGLevel lev[IRK_MAX_LEVELS];
+  void* vel[IRK_MAXS][IRK_MAX_LEVELS];
+  double mg_omega = 0.8;
+
+  irk_stats stats;
+  std::string err;
+
+  // profiling
+  std::vector<cudaEvent_t> evpool;
+  int ev_used = 0;
+  std::vector<PendingEvent> pending;
+  irk_kernel_stat prof[P_NCLASS];
+};
+
+static std::string g_create_error;
+
+namespace {
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess) {                                                              \
+      h->err = std::string("CUDA error: ") + cudaGetErrorString(_e) + " at " #call;       \
+      return IRK_ERR_CUDA;                                                                \
+    }                                                                                     \
+  } while (0)
+
+#define TRY(expr)                   \
+  do {                              \
+    irk_status _s = (expr);         \
+    if (_s != IRK_OK) return _s;    \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// profiling: CUDA events around kernel launches on the handle's stream
+int prof_begin(irk_handle* h) {
+  if (!h->cfg.profile) return -1;
+  if (h->ev_used + 2 > (int)h->evpool.size()) return -1;
+  int a = h->ev_used++;
+  cudaEventRecord(h->evpool[a], h->st);
+  return a;
+}
+
+void prof_end(irk_handle* h, int a, int cls, double bytes, double flops) {
+  if (a < 0) return;
+  int b = h->ev_used++;
+  cudaEventRecord(h->evpool[b], h->st);
+  h->pending.push_back({cls, a, b, bytes, flops});
+}
+
+void prof_harvest(irk_handle* h) {
+  if (h->pending.empty()) { h->ev_used = 0; return; }
+  cudaStreamSynchronize(h->st);
+  for (auto& pe : h->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->evpool[pe.a], h->evpool[pe.b]);
+    irk_kernel_stat& ks = h->prof[pe.cls];
+    ks.launches += 1;
+    ks.ms += ms;
+    ks.bytes += pe.bytes;
+    ks.flops += pe.flops;
+  }
+  h->pending.clear();
+  h->ev_used = 0;
+}
+
+void prof_maybe_flush(irk_handle* h) {
+  if (h->cfg.profile && h->ev_used + 64 > (int)h->evpool.size()) prof_harvest(h);
+}
+
+struct ProfScope {
+  irk_handle* h;
+  int a, cls;
+  double bytes, flops;
+  ProfScope(irk_handle* h_, int cls_, double bytes_, double flops_)
+      : h(h_), a(-1), cls(cls_), bytes(bytes_), flops(flops_) {
+    prof_maybe_flush(h);
+    a = prof_begin(h);
+  }
+  ~ProfScope() { prof_end(h, a, cls, bytes, flops); }
+};
+
+// FP64 flops per grid point of the operators (counted from the stencils)
+double n_flops_per_point(int op) {
+  switch (op) {
+    case IRK_OP_DIFFUSION_1D: return 5;
+    case IRK_OP_BURGERS_1D: return 11;
+    case IRK_OP_BURGERS_2D: return 2 * 16;
+    default: return 40 + 12 + 6;  // Arakawa + Laplacian + constraint row
+  }
+}
+double jadv_flops_per_point(int op) {
+  switch (op) {
+    case IRK_OP_DIFFUSION_1D: return 0;
+    case IRK_OP_BURGERS_1D: return 4;
+    case IRK_OP_BURGERS_2D: return 2 * 12 + 8;
+    default: return 2 * 40;
+  }
+}
+double jlin_flops_per_point(int op) {
+  switch (op) {
+    case IRK_OP_DIFFUSION_1D: case IRK_OP_BURGERS_1D: return 5;
+    case IRK_OP_BURGERS_2D: return 2 * 7;
+    default: return 7 + 8;
+  }
+}
+
+// ---------------------------------------------------------------------------
+void* arena_take(irk_handle* h, size_t bytes) {
+  size_t off = (h->arena_used + 255) & ~(size_t)255;
+  if (off + bytes > h->arena_bytes) return nullptr;
+  h->arena_used = off + bytes;
+  return h->arena + off;
+}
+
+irk_status sync_read(irk_handle* h, const double* dsrc, int count) {
+  CK(cudaMemcpyAsync(h->hbuf, dsrc, sizeof(double) * count, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
+
+// ||x||_2 of a device vector (blocking)
+irk_status dev_norm(irk_handle* h, const double* x, long long len, double* out) {
+  const int nb = blas_blocks(len);
+  {
+    ProfScope ps(h, P_NORM, 8.0 * len, 2.0 * len);
+    launch_norm2(x, len, h->partials, h->st);
+  }
+  {
+    ProfScope ps(h, P_REDUCE, 8.0 * nb, nb);
+    launch_reduce(h->partials, nb, 1, 1, h->dscal + 200, h->st);
+  }
+  TRY(sync_read(h, h->dscal + 200, 1));
+  *out = std::sqrt(h->hbuf[0]);
+  return IRK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Row operators of the transformed Jacobian (Eq. D+U, Eq. diag_blocks).
+const double* combo_ptr(irk_handle* h, int r, int q) {
+  const int idx = h->combo_of[r][q];
+  return idx < 0 ? nullptr : h->combos + (long long)idx * h->L;
+}
+
+double stage_op_bytes(irk_handle* h, const StageOpArgs& a) {
+  double words = 0;
+  for (int r = 0; r < a.nrow; ++r) {
+    words += h->L * (1 + (a.row[r].base ? 1 : 0));
+    for (int t = 0; t < a.row[r].nterm; ++t) words += h->L * (1 + (a.row[r].t[t].combo ? 1 : 0));
+  }
+  words += a.copy_len * 2.0;
+  return words * 8.0;
+}
+
+double stage_op_flops(irk_handle* h, const StageOpArgs& a) {
+  double f = 0;
+  for (int r = 0; r < a.nrow; ++r)
+    for (int t = 0; t < a.row[r].nterm; ++t)
+      f += h->npts * (2.0 * h->C + (a.row[r].t[t].combo ? jadv_flops_per_point(h->g.op) : 0) +
+                      (a.row[r].t[t].lin != 0 ? jlin_flops_per_point(h->g.op) : 0));
+  return f;
+}
+
+void run_stage_op(irk_handle* h, const StageOpArgs& a) {
+  ProfScope ps(h, P_STAGEOP, stage_op_bytes(h, a), stage_op_flops(h, a));
+  launch_stage_op(h->g, a, h->st);
+}
+
+bool keep_coupling(irk_handle* h, int r, int q) {
+  return h->cfg.nonlinear_variant >= 3 || r == q;
+}
+
+// y = D_blk x (Eq. diag_blocks); x, y are block vectors of bsize rows of length L
+void block_matvec_dt(irk_handle* h, double dt, int blk, const double* x, double* y,
+                     const double* copy_src, double* copy_dst) {
+  const int a0 = h->tab.bstart[blk], bs = h->tab.bsize[blk], s = h->s;
+  StageOpArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nrow = bs;
+  a.dt = dt;
+  for (int rr = 0; rr < bs; ++rr) {
+    const int r = a0 + rr;
+    OpRow& row = a.row[rr];
+    row.y = y + (long long)rr * h->L;
+    row.sigma = 1;
+    for (int qq = 0; qq < bs; ++qq) {
+      const int q = a0 + qq;
+      OpTerm& t = row.t[row.nterm++];
+      t.x = x + (long long)qq * h->L;
+      t.combo = keep_coupling(h, r, q) ? combo_ptr(h, r, q) : nullptr;
+      t.m = h->tab.R[r * s + q];
+      t.lin = (r == q) ? 1.0 : 0.0;
+    }
+  }
+  a.copy_dst = copy_dst;
+  a.copy_src = copy_src;
+  a.copy_len = copy_dst ? (long long)bs * h->L : 0;
+  run_stage_op(h, a);
+}
+
+// z_rows(blk) = rhs_rows(blk) - sum_{l beyond blk} U_{r,l} yhat_l
+void upper_coupling(irk_handle* h, double dt, int blk, double* z) {
+  const int a0 = h->tab.bstart[blk], bs = h->tab.bsize[blk], s = h->s;
+  const int first_later = a0 + bs;
+  StageOpArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nrow = bs;
+  a.dt = dt;
+  for (int rr = 0; rr < bs; ++rr) {
+    const int r = a0 + rr;
+    OpRow& row = a.row[rr];
+    row.y = z + (long long)rr * h->L;
+    row.base = h->rhs + (long long)r * h->L;
+    row.alpha = 1;
+    row.sigma = -1;
+    for (int l = first_later; l < s; ++l) {
+      OpTerm& t = row.t[row.nterm++];
+      t.x = h->yhat + (long long)l * h->L;
+      t.combo = keep_coupling(h, r, l) ? combo_ptr(h, r, l) : nullptr;
+      t.m = h->tab.R[r * s + l];
+      t.lin = 0;
+    }
+  }
+  run_stage_op(h, a);
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid
+double mg_level_bytes(irk_handle* h, int l, double fields) {
+  return fields * h->lev[l].d.npts * (double)h->esz;
+}
+
+void mg_setup(irk_handle* h) {
+  // coefficient (velocity) hierarchy of every diagonal row from combo (k,k)
+  if (h->g.op == IRK_OP_DIFFUSION_1D) return;
+  for (int k = 0; k < h->s; ++k) {
+    {
+      ProfScope ps(h, P_MG_SETUP, 8.0 * h->L + mg_level_bytes(h, 0, h->dim), 0);
+      launch_velocity_from_combo(h->g, combo_ptr(h, k, k), h->vel[k][0], h->prec, h->st);
+    }
+    for (int l = 0; l + 1 < h->nlev; ++l) {
+      ProfScope ps(h, P_MG_SETUP, mg_level_bytes(h, l, h->dim) * 1.25, 0);
+      launch_mg_restrict(h->prec, h->dim, h->lev[l].d, h->dim, h->vel[k][l], h->vel[k][l + 1],
+                         h->st);
+    }
+  }
+}
+
+// One V-cycle for A = sigma I + cadv adv(vel_k) - cdiff L on ncomp fields.
+// in/out: double, ncomp * npts_fine.
+void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double cadv, double cdiff,
+            int project_mean, const double* in, double* out) {
+  const int nl = h->nlev, prec = h->prec, dim = h->dim;
+  const double om = h->mg_omega;
+  const void* vrow[IRK_MAX_LEVELS];
+  for (int l = 0; l < nl; ++l) vrow[l] = (row >= 0) ? h->vel[row][l] : nullptr;
+  const long long n0 = (long long)ncomp * h->lev[0].d.npts;
+  {
+    ProfScope ps(h, P_MG_CONVERT, n0 * (8.0 + h->esz), 0);
+    launch_mg_convert_in(prec, in, h->lev[0].b, n0, h->st);
+  }
+  void* cur[IRK_MAX_LEVELS];
+  void* alt[IRK_MAX_LEVELS];
+  const int velf = (kind == MG_DIFFUSION) ? 0 : (kind == MG_CONSERVATIVE_1D ? 1 : dim);
+  const double smooth_flops_pp = 2.0 * (4 * dim + 6);
+  for (int l = 0; l + 1 < nl; ++l) {
+    MGLevel& lv = h->lev[l];
+    cur[l] = lv.w;
+    alt[l] = lv.w2;
+    for (int sw = 0; sw < h->cfg.mg_pre; ++sw) {
+      const int first = (sw == 0);
+      ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, l, first ? 2.0 * ncomp : 3.0 * ncomp + velf),
+                   (double)ncomp * lv.d.npts * (first ? 1 : smooth_flops_pp));
+      launch_mg_smooth(prec, dim, kind, lv.d, ncomp, sigma, cadv, cdiff, om, vrow[l], lv.b,
+                       cur[l], first ? cur[l] : alt[l], first, h->st);
+      if (!first) std::swap(cur[l], alt[l]);
+    }
+    {
+      ProfScope ps(h, P_MG_RESID, mg_level_bytes(h, l, 3.0 * ncomp + velf),
+                   (double)ncomp * lv.d.npts * smooth_flops_pp);
+      launch_mg_residual(prec, dim, kind, lv.d, ncomp, sigma, cadv, cdiff, vrow[l], lv.b, cur[l],
+                         lv.r, h->st);
+    }
+    {
+      ProfScope ps(h, P_MG_RESTRICT, mg_level_bytes(h, l, ncomp) * (1.0 + 1.0 / (1 << dim)),
+                   (double)ncomp * lv.d.npts / (1 << dim) * (dim == 1 ? 4 : 12));
+      launch_mg_restrict(prec, dim, lv.d, ncomp, lv.r, h->lev[l + 1].b, h->st);
+    }
+  }
+  {
+    MGLevel& lc = h->lev[nl - 1];
+    ProfScope ps(h, P_MG_COARSE, mg_level_bytes(h, nl - 1, 2.0 * ncomp + velf),
+                 (double)ncomp * lc.d.npts * smooth_flops_pp * h->cfg.mg_coarse_sweeps);
+    launch_mg_coarse(prec, dim, kind, lc.d, ncomp, sigma, cadv, cdiff, om, h->cfg.mg_coarse_sweeps,
+                     project_mean, vrow[nl - 1], lc.b, lc.w, h->st);
+    cur[nl - 1] = lc.w;
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    MGLevel& lv = h->lev[l];
+    {
+      ProfScope ps(h, P_MG_PROLONG, mg_level_bytes(h, l, 2.0 * ncomp + (double)ncomp / (1 << dim)),
+                   (double)ncomp * lv.d.npts * 3);
+      launch_mg_prolong_add(prec, dim, lv.d, ncomp, cur[l + 1], cur[l], h->st);
+    }
+    for (int sw = 0; sw < h->cfg.mg_post; ++sw) {
+      ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, l, 3.0 * ncomp + velf),
+                   (double)ncomp * lv.d.npts * smooth_flops_pp);
+      launch_mg_smooth(prec, dim, kind, lv.d, ncomp, sigma, cadv, cdiff, om, vrow[l], lv.b,
+                       cur[l], alt[l], 0, h->st);
+      std::swap(cur[l], alt[l]);
+    }
+  }
+  {
+    ProfScope ps(h, P_MG_CONVERT, n0 * (8.0 + h->esz), 0);
+    launch_mg_convert_out(prec, cur[0], out, n0, h->st);
+  }
+  h->stats.vcycles += 1;
+}
+
+// Inner inverse (sigma M - dt L_kk)^{-1} of one block row, approximated by MG.
+void row_prec(irk_handle* h, double dt, int row, double sigma, const double* in, double* out) {
+  const int op = h->g.op;
+  if (op == IRK_OP_VSF_2D) {
+    // Picard-type lower-triangular solve of the (omega, psi) row (Eq. vsf-system-1):
+    // omega: sigma - dt (J_A(psibar, .) + nu L); psi: (-L) z_psi = z_omega - r_psi / dt
+    vcycle(h, row, MG_ADVECTIVE, 1, sigma, dt, dt * h->g.nu, 0, in, out);
+    {
+      ProfScope ps(h, P_AXPBY, 24.0 * h->npts, 2.0 * h->npts);
+      launch_axpby(h->tmp2, 1.0, out, 0.0, h->npts, h->st);
+      launch_axpby(h->tmp2, -1.0 / dt, in + h->npts, 1.0, h->npts, h->st);
+    }
+    vcycle(h, -1, MG_DIFFUSION, 1, 0.0, 0.0, 1.0, 1, h->tmp2, out + h->npts);
+    return;
+  }
+  const int kind = (op == IRK_OP_BURGERS_1D) ? MG_CONSERVATIVE_1D
+                   : (op == IRK_OP_BURGERS_2D) ? MG_ADVECTIVE : MG_DIFFUSION;
+  vcycle(h, row, kind, h->C, sigma, dt, dt * h->g.nu, 0, in, out);
+}
+
+// z = L_P(v) for block blk (Eq. Lprec with the (2,1) block of Eq. diag_blocks)
+void block_prec(irk_handle* h, double dt, int blk, const double* v, double* z) {
+  const int a = h->tab.bstart[blk], bs = h->tab.bsize[blk], s = h->s;
+  const double eta = h->tab.eta[blk];
+  row_prec(h, dt, a, eta, v, z);
+  if (bs == 1) return;
+  const int b = a + 1;
+  StageOpArgs op;
+  memset(&op, 0, sizeof(op));
+  op.nrow = 1;
+  op.dt = dt;
+  OpRow& row = op.row[0];
+  row.y = h->tmp;
+  row.base = v + h->L;
+  row.alpha = 1;
+  row.sigma = -1;
+  row.nterm = 1;
+  row.t[0].x = z;
+  row.t[0].combo = keep_coupling(h, b, a) ? combo_ptr(h, b, a) : nullptr;
+  row.t[0].m = h->tab.R[b * s + a];
+  row.t[0].lin = 0;
+  run_stage_op(h, op);
+  const double gamma = (h->cfg.gamma_mode == 1) ? eta : h->tab.gamma_star[blk];
+  row_prec(h, dt, b, gamma, h->tmp, z + h->L);
+}
+
+// ---------------------------------------------------------------------------
+// Flexible GMRES(m), right preconditioned, CGS2 (step a8).
+irk_status fgmres(irk_handle* h, double dt, int blk, const double* b, double* x, double rtol,
+                  int* its_out, double* relres_out) {
+  const int bs = h->tab.bsize[blk];
+  const long long Lb = (long long)bs * h->L;
+  const int m = h->m;
+  const long long ldv = Lb;
+  double beta;
+  TRY(dev_norm(h, b, Lb, &beta));
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * Lb, h->st));
+  *its_out = 0;
+  *relres_out = 0;
+  if (!(beta > 0)) {
+    if (!std::isfinite(beta)) { h->err = "non-finite right-hand side in FGMRES"; return IRK_ERR_NEWTON_DIVERGED; }
+    return IRK_OK;
+  }
+  const double target = rtol * beta;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  const double* r = b;
+  double rnorm = beta;
+  int total = 0;
+  const int nb = blas_blocks(Lb);
+  double* dh1 = h->dscal;        // [0, 64)
+  double* dh2 = h->dscal + 64;   // [64, 129)
+  double* dnr = h->dscal + 130;  // [130]
+  while (true) {
+    {
+      ProfScope ps(h, P_SCALE, 16.0 * Lb, (double)Lb);
+      launch_scale_copy(r, 1.0 / rnorm, h->V, nullptr, Lb, h->st);
+    }
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = rnorm;
+    int jlast = -1;
+    double res = rnorm;
+    for (int j = 0; j < m; ++j) {
+      double* vj = h->V + (long long)j * ldv;
+      double* zj = h->Z + (long long)j * ldv;
+      block_prec(h, dt, blk, vj, zj);
+      block_matvec_dt(h, dt, blk, zj, h->w, nullptr, nullptr);
+      const int nv = j + 1;
+      {
+        ProfScope ps(h, P_GS_DOT, 8.0 * Lb * (nv + 1), 2.0 * Lb * nv);
+        launch_multi_dot(h->V, ldv, nv, h->w, Lb, h->partials, h->st);
+      }
+      {
+        ProfScope ps(h, P_REDUCE, 8.0 * nb * nv, (double)nb * nv);
+        launch_reduce(h->partials, nb, nv, nv, dh1, h->st);
+      }
+      {
+        ProfScope ps(h, P_GS_UPDATE, 8.0 * Lb * (nv + 2), 4.0 * Lb * nv + 2.0 * Lb);
+        launch_update_dot(h->V, ldv, nv, dh1, h->w, Lb, 1, h->partials, h->st);
+      }
+      {
+        ProfScope ps(h, P_REDUCE, 8.0 * nb * (nv + 1), (double)nb * (nv + 1));
+        launch_reduce(h->partials, nb, nv + 1, nv, dh2, h->st);
+      }
+      {
+        ProfScope ps(h, P_GS_UPDATE, 8.0 * Lb * (nv + 2), 2.0 * Lb * nv + 2.0 * Lb);
+        launch_update_dot(h->V, ldv, nv, dh2, h->w, Lb, 0, h->partials, h->st);
+      }
+      {
+        ProfScope ps(h, P_REDUCE, 8.0 * nb, (double)nb);
+        launch_reduce(h->partials + nv, nb, nv + 1, 1, dnr, h->st);
+      }
+      CK(cudaMemcpyAsync(h->hbuf, h->dscal, sizeof(double) * 131, cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      const double* hh1 = h->hbuf;
+      const double* hh2 = h->hbuf + 64;
+      const double nrm2 = h->hbuf[130];
+      for (int i = 0; i < nv; ++i) H[i * m + j] = hh1[i] + hh2[i];
+      const double hn = std::sqrt(std::max(nrm2, 0.0));
+      if (!std::isfinite(hn)) { h->err = "non-finite Krylov vector"; return IRK_ERR_KRYLOV_BREAKDOWN; }
+      // apply the previous rotations to column j, then a new one
+      for (int i = 0; i < j; ++i) {
+        const double t0 = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        const double t1 = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t0;
+        H[(i + 1) * m + j] = t1;
+      }
+      const double hjj = H[j * m + j];
+      const double den = std::hypot(hjj, hn);
+      cs[j] = den > 0 ? hjj / den : 1.0;
+      sn[j] = den > 0 ? hn / den : 0.0;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      res = std::fabs(gv[j + 1]);
+      ++total;
+      jlast = j;
+      h->stats.krylov_its += 1;
+      h->stats.prec_apps += bs;
+      if (res <= target || hn <= 1e-300 || total >= h->cfg.krylov_maxit) break;
+      {
+        ProfScope ps(h, P_SCALE, 16.0 * Lb, (double)Lb);
+        launch_scale_copy(h->w, 1.0 / hn, h->V + (long long)(j + 1) * ldv, nullptr, Lb, h->st);
+      }
+    }
+    // y = H^{-1} g on the leading (jlast+1) block, x += Z y
+    const int k = jlast + 1;
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int q = i + 1; q < k; ++q) acc -= H[i * m + q] * y[q];
+      y[i] = acc / H[i * m + i];
+    }
+    {
+      ProfScope ps(h, P_LINCOMB, 8.0 * Lb * (k + 2), 2.0 * Lb * k);
+      launch_lincomb(x, h->Z, ldv, k, y.data(), Lb, h->st);
+    }
+    *its_out = total;
+    if (res <= target) { *relres_out = res / beta; return IRK_OK; }
+    if (total >= h->cfg.krylov_maxit) { *relres_out = res / beta; return IRK_OK; }
+    // restart: r = b - D x
+    block_matvec_dt(h, dt, blk, x, h->w, nullptr, nullptr);
+    {
+      ProfScope ps(h, P_AXPBY, 24.0 * Lb, 2.0 * Lb);
+      launch_axpby(h->w, 1.0, b, -1.0, Lb, h->st);
+    }
+    r = h->w;
+    TRY(dev_norm(h, r, Lb, &rnorm));
+    if (!(rnorm > 0)) return IRK_OK;
+  }
+}
+
+// ---------------------------------------------------------------------------
+void set_stage_args(irk_handle* h, StageStateArgs& a, double dt, const double* u,
+                    const double* K, double* Y, double* combos) {
+  memset(&a, 0, sizeof(a));
+  a.s = h->s;
+  a.ncombo = combos ? h->ncombo : 0;
+  a.L = h->L;
+  a.dt = dt;
+  for (int i = 0; i < h->s * h->s; ++i) a.A[i] = h->tab.A[i];
+  for (int i = 0; i < h->ncombo * h->s; ++i) a.D[i] = h->Dq[i];
+  a.u = u;
+  a.K = K;
+  a.Y = Y;
+  a.combos = combos;
+}
+
+// stage states + residual + ||F|| (blocking read of the norm)
+irk_status eval_residual(irk_handle* h, double t_n, double dt, const double* K, double* rhs,
+                         double* Fraw, bool combos, double* fnorm) {
+  StageStateArgs sa;
+  set_stage_args(h, sa, dt, h->u, K, h->Y, combos ? h->combos : nullptr);
+  {
+    const double w = h->L * (1.0 + h->s + h->s + (combos ? h->ncombo : 0));
+    ProfScope ps(h, P_STAGE, 8.0 * w, h->L * 2.0 * h->s * (h->s + (combos ? h->ncombo : 0)));
+    launch_stage_states(h->g, sa, h->st);
+  }
+  ResidualArgs ra;
+  memset(&ra, 0, sizeof(ra));
+  ra.s = h->s;
+  for (int i = 0; i < h->s * h->s; ++i) ra.Q[i] = h->tab.Q[i];
+  for (int i = 0; i < h->s; ++i) ra.tstage[i] = t_n + h->tab.c[i] * dt;
+  ra.forcing = h->cfg.forcing;
+  ra.Y = h->Y;
+  ra.K = K;
+  ra.rhs = rhs;
+  ra.Fraw = Fraw;
+  ra.partials = h->partials;
+  const int nb = residual_blocks(h->g);
+  {
+    const double w = h->L * (2.0 * h->s + (rhs ? h->s : 0) + (Fraw ? h->s : 0));
+    ProfScope ps(h, P_RESID, 8.0 * w,
+                 h->npts * h->s * (n_flops_per_point(h->g.op) + 4.0 * h->C + (rhs ? 2.0 * h->s * h->C : 0)));
+    launch_residual(h->g, ra, h->st);
+  }
+  {
+    ProfScope ps(h, P_REDUCE, 8.0 * nb, nb);
+    launch_reduce(h->partials, nb, 1, 1, h->dscal + 201, h->st);
+  }
+  TRY(sync_read(h, h->dscal + 201, 1));
+  *fnorm = std::sqrt(h->hbuf[0]);
+  return IRK_OK;
+}
+
+irk_status newton_step(irk_handle* h, double t_n, double dt) {
+  const int s = h->s;
+  CK(cudaMemsetAsync(h->K, 0, sizeof(double) * s * h->L, h->st));
+  double f0 = 0, fn = 0, prev = 0;
+  int it = 0;
+  for (;; ++it) {
+    TRY(eval_residual(h, t_n, dt, h->K, h->rhs, nullptr, true, &fn));
+    if (!std::isfinite(fn)) { h->err = "non-finite stage residual"; return IRK_ERR_NEWTON_DIVERGED; }
+    if (it == 0) f0 = fn;
+    const double rel = (f0 > 0) ? fn / f0 : 0.0;
+    h->stats.final_rel_res = rel;
+    if (f0 == 0 || rel <= h->cfg.newton_rtol) break;
+    if (it >= h->cfg.newton_maxit) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "Newton did not reach rtol %.1e in %d iterations (rel %.3e)",
+               h->cfg.newton_rtol, it, rel);
+      h->err = buf;
+      return IRK_ERR_NEWTON_MAXIT;
+    }
+    if (it > 0 && rel > 1e3) { h->err = "Newton residual grew by 1e3"; return IRK_ERR_NEWTON_DIVERGED; }
+    // inexact-Newton forcing term: tighten with the residual, never oversolve the last step
+    double eta_lin = std::min(h->cfg.krylov_rtol, rel);
+    if (it > 0 && prev > 0 && fn > 0.5 * prev) eta_lin = std::min(eta_lin, 1e-3 * rel);
+    eta_lin = std::max(eta_lin, 0.2 * h->cfg.newton_rtol / rel);
+    eta_lin = std::max(eta_lin, 1e-13);
+    prev = fn;
+    mg_setup(h);
+    for (int blk = h->tab.nblk - 1; blk >= 0; --blk) {
+      const int a0 = h->tab.bstart[blk];
+      const double* z = h->rhs + (long long)a0 * h->L;
+      if (blk < h->tab.nblk - 1) {
+        upper_coupling(h, dt, blk, h->zbuf);
+        z = h->zbuf;
+      }
+      int its = 0;
+      double rr = 0;
+      TRY(fgmres(h, dt, blk, z, h->yhat + (long long)a0 * h->L, eta_lin, &its, &rr));
+    }
+    {
+      ProfScope ps(h, P_UPDATE, 8.0 * h->L * 3 * s, 2.0 * h->L * s * s);
+      launch_stage_update(h->L, s, h->tab.QR, h->yhat, h->K, h->st);
+    }
+    if (h->g.op == IRK_OP_VSF_2D) {
+      ProfScope ps(h, P_MEAN, 16.0 * h->npts * s, 2.0 * h->npts * s);
+      launch_remove_mean(h->npts, s, h->L, h->K + h->npts, h->partials, h->st);
+    }
+    h->stats.newton_its += 1;
+  }
+  h->stats.max_newton_its = std::max(h->stats.max_newton_its, it);
+  {
+    ProfScope ps(h, P_UPDATE, 8.0 * h->L * (2 + s), 2.0 * h->L * s);
+    launch_u_update(h->L, s, h->tab.b, dt, h->K, h->u, h->st);
+  }
+  return IRK_OK;
+}
+
+// ---------------------------------------------------------------------------
+irk_status validate(const irk_config* c, std::string& err) {
+  if (!c) { err = "null config"; return IRK_ERR_INVALID; }
+  if (c->family != IRK_GAUSS) { err = "family must be IRK_GAUSS"; return IRK_ERR_INVALID; }
+  if (c->stages < 1 || c->stages > IRK_MAXS) { err = "stages must be in 1..5"; return IRK_ERR_INVALID; }
+  if (c->op < IRK_OP_DIFFUSION_1D || c->op > IRK_OP_VSF_2D) { err = "unknown op"; return IRK_ERR_INVALID; }
+  const int want_mass = (c->op == IRK_OP_VSF_2D) ? IRK_MASS_DAE : IRK_MASS_IDENTITY;
+  if (c->mass != want_mass) { err = "mass does not match op (DAE mass exactly for VSF)"; return IRK_ERR_INVALID; }
+  if (c->n < 8 || c->n > 8192 || (c->n & (c->n - 1))) { err = "n must be a power of two in 8..8192"; return IRK_ERR_INVALID; }
+  if (!(c->nu > 0) || !std::isfinite(c->nu)) { err = "nu must be positive"; return IRK_ERR_INVALID; }
+  if (!(c->length > 0)) { err = "length must be positive"; return IRK_ERR_INVALID; }
+  if (c->forcing != 0 && c->forcing != 1) { err = "forcing must be 0 or 1"; return IRK_ERR_INVALID; }
+  if (c->forcing == 1 && !(c->op == IRK_OP_BURGERS_1D || c->op == IRK_OP_DIFFUSION_1D)) { err = "forcing 1 is defined for the 1D operators"; return IRK_ERR_INVALID; }
+  if (c->forcing == 1 && c->length != 1.0) { err = "forcing 1 needs length 1"; return IRK_ERR_INVALID; }
+  if (!(c->newton_rtol > 0) || c->newton_maxit < 1) { err = "bad Newton tolerance"; return IRK_ERR_INVALID; }
+  if (!(c->krylov_rtol > 0) || c->krylov_restart < 1 || c->krylov_restart > 64 || c->krylov_maxit < 1) { err = "bad Krylov settings"; return IRK_ERR_INVALID; }
+  if (c->nonlinear_variant != 2 && c->nonlinear_variant != 3) { err = "nonlinear_variant must be 2 or 3"; return IRK_ERR_INVALID; }
+  if (c->gamma_mode != 0 && c->gamma_mode != 1) { err = "gamma_mode must be 0 or 1"; return IRK_ERR_INVALID; }
+  if (c->mg_precision < 0 || c->mg_precision > 2) { err = "mg_precision must be 0..2"; return IRK_ERR_INVALID; }
+  if (c->mg_pre < 1 || c->mg_post < 0 || c->mg_pre > 8 || c->mg_post > 8) { err = "mg sweeps out of range"; return IRK_ERR_INVALID; }
+  if (c->mg_coarse_sweeps < 1 || c->mg_coarse_sweeps > 1000) { err = "mg_coarse_sweeps out of range"; return IRK_ERR_INVALID; }
+  if (c->mg_levels < 0 || c->mg_levels > IRK_MAX_LEVELS) { err = "mg_levels out of range"; return IRK_ERR_INVALID; }
+  return IRK_OK;
+}
+
+irk_status build(irk_handle* h, const double* u0, int u0_on_device) {
+  const irk_config& c = h->cfg;
+  char ebuf[256] = {0};
+  if (build_tableau(c.family, c.stages, &h->tab, ebuf, sizeof ebuf)) { h->err = ebuf; return IRK_ERR_INVALID; }
+  const int s = h->s = c.stages;
+  h->dim = (c.op == IRK_OP_BURGERS_2D || c.op == IRK_OP_VSF_2D) ? 2 : 1;
+  h->C = (h->dim == 2) ? 2 : 1;
+  h->npts = (h->dim == 2) ? c.n * c.n : c.n;
+  h->L = (long long)h->C * h->npts;
+  GridDesc& g = h->g;
+  g.dim = h->dim;
+  g.n = c.n;
+  g.logn = 0;
+  while ((1 << g.logn) < c.n) ++g.logn;
+  g.npts = h->npts;
+  g.ncomp = h->C;
+  g.op = c.op;
+  g.h = c.length / c.n;
+  g.inv2h = 0.5 / g.h;
+  g.inv4h = 0.25 / g.h;
+  g.invh2 = 1.0 / (g.h * g.h);
+  g.inv12h2 = 1.0 / (12.0 * g.h * g.h);
+  g.nu = c.nu;
+  for (int k = 0; k < h->tab.nblk; ++k)
+    for (int i = 0; i < h->tab.bsize[k]; ++i) h->blk_of[h->tab.bstart[k] + i] = k;
+  // combined fields needed by the kept pattern
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) h->combo_of[i][j] = -1;
+  h->ncombo = 0;
+  for (int k = 0; k < s; ++k)
+    for (int l = k; l < s; ++l) {
+      if (!(k == l || (c.nonlinear_variant >= 3 && h->blk_of[k] <= h->blk_of[l]))) continue;
+      double dmax = 0;
+      for (int mm = 0; mm < s; ++mm) dmax = std::max(dmax, std::fabs(h->tab.Q[mm * s + k] * h->tab.Q[mm * s + l]));
+      if (k != l && dmax < 1e-15) continue;
+      const int q = h->ncombo++;
+      for (int mm = 0; mm < s; ++mm) h->Dq[q * s + mm] = h->tab.Q[mm * s + k] * h->tab.Q[mm * s + l];
+      h->combo_of[k][l] = h->combo_of[l][k] = q;
+    }
+  // multigrid levels
+  h->prec = c.mg_precision;
+  h->esz = mg_elem_size(h->prec);
+  h->mg_omega = c.mg_omega > 0 ? c.mg_omega : (h->dim == 2 ? 0.8 : 2.0 / 3.0);
+  h->mg_kind = 0;
+  {
+    int n = c.n, l = 0;
+    const int coarsest = 8;
+    while (true) {
+      MGLevel& lv = h->lev[l];
+      lv.d.n = n;
+      lv.d.logn = 0;
+      while ((1 << lv.d.logn) < n) ++lv.d.logn;
+      lv.d.npts = (h->dim == 2) ? n * n : n;
+      lv.d.h = c.length / n;
+      ++l;
+      if (n <= coarsest || l == IRK_MAX_LEVELS || (c.mg_levels > 0 && l == c.mg_levels)) break;
+      n >>= 1;
+    }
+    h->nlev = l;
+  }
+  h->m = c.krylov_restart;
+  // arena size
+  const int maxbs = 2;
+  const long long Lb = maxbs * h->L;
+  size_t bytes = 0;
+  auto add = [&](size_t b) { bytes += (b + 255) & ~(size_t)255; };
+  add(8 * h->L);                 // u
+  add(8 * h->L);                 // u_save
+  add(8 * h->L * s);             // K
+  add(8 * h->L * s);             // Y
+  add(8 * h->L * s);             // rhs
+  add(8 * h->L * s);             // yhat
+  add(8 * h->L * std::max(h->ncombo, 1));  // combos
+  add(8 * Lb);                   // zbuf
+  add(8 * h->L);                 // tmp
+  add(8 * h->L);                 // tmp2
+  add(8 * Lb * (h->m + 1));      // V
+  add(8 * Lb * h->m);            // Z
+  add(8 * Lb);                   // w
+  h->nparts = std::max(blas_blocks(Lb) * 70, residual_blocks(g)) + 1024;
+  add(8 * (size_t)h->nparts);    // partials
+  add(8 * 512);                  // device scalars
+  for (int l = 0; l < h->nlev; ++l) {
+    const size_t f = h->esz * (size_t)h->lev[l].d.npts;
+    add(f * h->C); add(f * h->C); add(f * h->C); add(f * h->C);
+    for (int k = 0; k < s; ++k) add(f * h->dim);
+  }
+  h->arena_bytes = bytes + 4096;
+  cudaError_t e = cudaMalloc((void**)&h->arena, h->arena_bytes);
+  if (e != cudaSuccess) {
+    h->arena = nullptr;
+    h->err = std::string("device arena allocation failed: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return IRK_ERR_NOMEM;
+  }
+  auto take = [&](size_t b) { return arena_take(h, b); };
+  h->u = (double*)take(8 * h->L);
+  h->u_save = (double*)take(8 * h->L);
+  h->K = (double*)take(8 * h->L * s);
+  h->Y = (double*)take(8 * h->L * s);
+  h->rhs = (double*)take(8 * h->L * s);
+  h->yhat = (double*)take(8 * h->L * s);
+  h->combos = (double*)take(8 * h->L * std::max(h->ncombo, 1));
+  h->zbuf = (double*)take(8 * Lb);
+  h->tmp = (double*)take(8 * h->L);
+  h->tmp2 = (double*)take(8 * h->L);
+  h->V = (double*)take(8 * Lb * (h->m + 1));
+  h->Z = (double*)take(8 * Lb * h->m);
+  h->w = (double*)take(8 * Lb);
+  h->partials = (double*)take(8 * (size_t)h->nparts);
+  h->dscal = (double*)take(8 * 512);
+  for (int l = 0; l < h->nlev; ++l) {
+    const size_t f = h->esz * (size_t)h->lev[l].d.npts;
+    h->lev[l].w = take(f * h->C);
+    h->lev[l].w2 = take(f * h->C);
+    h->lev[l].b = take(f * h->C);
+    h->lev[l].r = take(f * h->C);
+    for (int k = 0; k < s; ++k) h->vel[k][l] = take(f * h->dim);
+  }
+  for (int k = s; k < IRK_MAXS; ++k)
+    for (int l = 0; l < IRK_MAX_LEVELS; ++l) h->vel[k][l] = nullptr;
+  if (!h->dscal) { h->err = "arena layout overflow"; return IRK_ERR_NOMEM; }
+  CK(cudaMemsetAsync(h->arena, 0, h->arena_used, h->st));
+  CK(cudaMallocHost((void**)&h->hbuf, 4096));
+  if (c.profile) {
+    h->evpool.resize(8192);
+    for (auto& ev : h->evpool) CK(cudaEventCreate(&ev));
+  }
+  for (int k = 0; k < P_NCLASS; ++k) {
+    memset(&h->prof[k], 0, sizeof(irk_kernel_stat));
+    snprintf(h->prof[k].name, sizeof h->prof[k].name, "%s", kProfNames[k]);
+  }
+  // initial state
+  CK(cudaMemcpyAsync(h->u, u0, sizeof(double) * (c.op == IRK_OP_VSF_2D ? h->npts : h->L),
+                     u0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  if (c.op == IRK_OP_VSF_2D) {
+    // consistent psi: -L psi = omega (zero mean) by MG-preconditioned FGMRES-free
+    // defect correction with the Poisson V-cycle, to a relative residual of 1e-14
+    launch_remove_mean(h->npts, 1, h->npts, h->u, h->partials, h->st);
+    double* psi = h->u + h->npts;
+    CK(cudaMemsetAsync(psi, 0, sizeof(double) * h->npts, h->st));
+    double bnorm = 0;
+    TRY(dev_norm(h, h->u, h->npts, &bnorm));
+    const int save_prec = h->prec;
+    for (int it = 0; it < 200 && bnorm > 0; ++it) {
+      // defect d = omega - (-L psi) in tmp; via the row operator with x = (0, psi)
+      StageOpArgs a;
+      memset(&a, 0, sizeof(a));
+      a.nrow = 1;
+      a.dt = 1.0;
+      // Jlin of VSF on x = (0, psi): psi row = -(0) - L psi; row scaled by -dt -> L psi ... use tmp2 as zeros
+      CK(cudaMemsetAsync(h->zbuf, 0, sizeof(double) * h->npts, h->st));
+      CK(cudaMemcpyAsync(h->zbuf + h->npts, psi, sizeof(double) * h->npts, cudaMemcpyDeviceToDevice, h->st));
+      a.row[0].y = h->w;
+      a.row[0].sigma = 1;
+      a.row[0].nterm = 1;
+      a.row[0].t[0].x = h->zbuf;
+      a.row[0].t[0].combo = nullptr;
+      a.row[0].t[0].m = 0;
+      a.row[0].t[0].lin = 1;
+      run_stage_op(h, a);  // w_psi = -dt * (-L psi) = L psi
+      // defect = omega + L psi  (since -L psi should equal omega)
+      launch_axpby(h->w + h->npts, 1.0, h->u, 1.0, h->npts, h->st);
+      double dn = 0;
+      TRY(dev_norm(h, h->w + h->npts, h->npts, &dn));
+      if (dn <= 1e-14 * bnorm) break;
+      h->prec = IRK_MG_FP64;
+      vcycle(h, -1, MG_DIFFUSION, 1, 0.0, 0.0, 1.0, 1, h->w + h->npts, h->tmp);
+      h->prec = save_prec;
+      launch_axpby(psi, 1.0, h->tmp, 1.0, h->npts, h->st);
+    }
+    h->prec = save_prec;
+    h->stats.vcycles = 0;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+extern "C" {
+
+void irk_config_default(irk_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->family = IRK_GAUSS;
+  c->stages = 2;
+  c->op = IRK_OP_BURGERS_1D;
+  c->mass = IRK_MASS_IDENTITY;
+  c->n = 256;
+  c->length = 1.0;
+  c->nu = 0.01;
+  c->forcing = 0;
+  c->newton_rtol = 1e-10;
+  c->newton_maxit = 20;
+  c->krylov_rtol = 1e-3;
+  c->krylov_restart = 30;
+  c->krylov_maxit = 200;
+  c->nonlinear_variant = 3;
+  c->gamma_mode = 0;
+  c->mg_precision = IRK_MG_FP64;
+  c->mg_levels = 0;
+  c->mg_pre = 2;
+  c->mg_post = 2;
+  c->mg_coarse_sweeps = 40;
+  c->mg_omega = 0.0;
+  c->profile = 0;
+}
+
+const char* irk_status_string(irk_status st) {
+  switch (st) {
+    case IRK_OK: return "ok";
+    case IRK_ERR_INVALID: return "invalid argument";
+    case IRK_ERR_NOMEM: return "out of memory";
+    case IRK_ERR_CUDA: return "CUDA error";
+    case IRK_ERR_NEWTON_DIVERGED: return "Newton diverged";
+    case IRK_ERR_NEWTON_MAXIT: return "Newton iteration limit";
+    case IRK_ERR_KRYLOV_BREAKDOWN: return "Krylov breakdown";
+    case IRK_ERR_TIMEOUT: return "device wait timed out";
+    case IRK_ERR_NO_DEVICE: return "no CUDA device";
+  }
+  return "unknown status";
+}
+
+irk_status irk_tableau(int family, int s, double* A, double* b, double* c, double* Q0, double* R0,
+                       int* block_sizes, int* nblocks) {
+  HostTableau t;
+  char ebuf[256];
+  if (build_tableau(family, s, &t, ebuf, sizeof ebuf)) return IRK_ERR_INVALID;
+  for (int i = 0; i < s * s; ++i) {
+    if (A) A[i] = t.A[i];
+    if (Q0) Q0[i] = t.Q[i];
+    if (R0) R0[i] = t.R[i];
+  }
+  for (int i = 0; i < s; ++i) {
+    if (b) b[i] = t.b[i];
+    if (c) c[i] = t.c[i];
+  }
+  if (block_sizes)
+    for (int k = 0; k < t.nblk; ++k) block_sizes[k] = t.bsize[k];
+  if (nblocks) *nblocks = t.nblk;
+  return IRK_OK;
+}
+
+irk_status irk_create(const irk_config* cfg, const double* u0, int u0_on_device, void* cuda_stream,
+                      irk_handle** out) {
+  if (!out) { g_create_error = "null output handle"; return IRK_ERR_INVALID; }
+  *out = nullptr;
+  std::string verr;
+  irk_status vs = validate(cfg, verr);
+  if (vs != IRK_OK) { g_create_error = verr; return vs; }
+  if (!u0) { g_create_error = "null initial state"; return IRK_ERR_INVALID; }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    g_create_error = "no CUDA device";
+    return IRK_ERR_NO_DEVICE;
+  }
+  irk_handle* h = new (std::nothrow) irk_handle();
+  if (!h) { g_create_error = "host allocation failed"; return IRK_ERR_NOMEM; }
+  h->cfg = *cfg;
+  memset(&h->stats, 0, sizeof(h->stats));
+  cudaGetDevice(&h->device);
+  if (cuda_stream) {
+    h->st = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess) {
+      g_create_error = "stream creation failed";
+      delete h;
+      return IRK_ERR_CUDA;
+    }
+    h->own_stream = true;
+  }
+  irk_status st = build(h, u0, u0_on_device);
+  if (st != IRK_OK) {
+    g_create_error = h->err;
+    irk_destroy(h);
+    return st;
+  }
+  *out = h;
+  return IRK_OK;
+}
+
+irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats* stats) {
+  if (!h) return IRK_ERR_INVALID;
+  if (!(dt > 0) || !std::isfinite(dt) || nsteps < 0 || !std::isfinite(t_n)) {
+    h->err = "dt must be positive and finite, nsteps >= 0";
+    return IRK_ERR_INVALID;
+  }
+  memset(&h->stats, 0, sizeof(h->stats));
+  irk_status st = IRK_OK;
+  double t = t_n;
+  for (int k = 0; k < nsteps; ++k) {
+    cudaError_t e = cudaMemcpyAsync(h->u_save, h->u, sizeof(double) * h->L,
+                                    cudaMemcpyDeviceToDevice, h->st);
+    if (e != cudaSuccess) { h->err = cudaGetErrorString(e); st = IRK_ERR_CUDA; break; }
+    st = newton_step(h, t, dt);
+    if (st != IRK_OK) {
+      cudaMemcpyAsync(h->u, h->u_save, sizeof(double) * h->L, cudaMemcpyDeviceToDevice, h->st);
+      cudaStreamSynchronize(h->st);
+      break;
+    }
+    h->stats.steps += 1;
+    t += dt;
+  }
+  if (st == IRK_OK) {
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) { h->err = cudaGetErrorString(e); st = IRK_ERR_CUDA; }
+  }
+  prof_harvest(h);
+  if (stats) *stats = h->stats;
+  return st;
+}
+
+irk_status irk_get_state(irk_handle* h, double* dst, int dst_on_device) {
+  if (!h || !dst) return IRK_ERR_INVALID;
+  CK(cudaMemcpyAsync(dst, h->u, sizeof(double) * h->L,
+                     dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
+
+irk_status irk_set_state(irk_handle* h, const double* src, int src_on_device) {
+  if (!h || !src) return IRK_ERR_INVALID;
+  CK(cudaMemcpyAsync(h->u, src, sizeof(double) * h->L,
+                     src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
+
+irk_status irk_get_stages(irk_handle* h, double* dst, int dst_on_device) {
+  if (!h || !dst) return IRK_ERR_INVALID;
+  CK(cudaMemcpyAsync(dst, h->K, sizeof(double) * h->L * h->s,
+                     dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
+
+irk_status irk_stage_residual(irk_handle* h, double t_n, double dt, const double* K, double* F,
+                              int on_device) {
+  if (!h || !K || !F) return IRK_ERR_INVALID;
+  const size_t bytes = sizeof(double) * h->L * h->s;
+  // stage the input in yhat (free between steps) and the output in rhs
+  CK(cudaMemcpyAsync(h->yhat, K, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  double fn = 0;
+  TRY(eval_residual(h, t_n, dt, h->yhat, nullptr, h->rhs, false, &fn));
+  CK(cudaMemcpyAsync(F, h->rhs, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  prof_harvest(h);
+  return IRK_OK;
+}
+
+irk_status irk_stage_jacobian_apply(irk_handle* h, double dt, const double* K, const double* V,
+                                    double* JV, int on_device) {
+  if (!h || !K || !V || !JV) return IRK_ERR_INVALID;
+  const int s = h->s;
+  const size_t bytes = sizeof(double) * h->L * s;
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // K -> yhat, V -> V-basis scratch, W_i = sum_j a_ij v_j -> combos region is not used here
+  double* Kd = h->yhat;
+  double* Vd = h->V;
+  double* Wd = h->V + (long long)s * h->L;
+  double* Out = h->rhs;
+  if ((long long)2 * s * h->L > (long long)2 * h->L * (h->m + 1)) { h->err = "restart too small for the Jacobian scratch"; return IRK_ERR_INVALID; }
+  CK(cudaMemcpyAsync(Kd, K, bytes, kin, h->st));
+  CK(cudaMemcpyAsync(Vd, V, bytes, kin, h->st));
+  StageStateArgs sa;
+  set_stage_args(h, sa, dt, h->u, Kd, h->Y, nullptr);
+  launch_stage_states(h->g, sa, h->st);
+  StageStateArgs wa;
+  set_stage_args(h, wa, 1.0, nullptr, Vd, Wd, nullptr);
+  launch_stage_states(h->g, wa, h->st);
+  for (int i = 0; i < s; ++i) {
+    StageOpArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nrow = 1;
+    a.dt = dt;
+    OpRow& row = a.row[0];
+    row.y = Out + (long long)i * h->L;
+    row.sigma = 1;
+    row.nterm = 2;
+    row.t[0].x = Vd + (long long)i * h->L;
+    row.t[0].combo = nullptr;
+    row.t[0].m = 1.0;
+    row.t[0].lin = 0.0;
+    row.t[1].x = Wd + (long long)i * h->L;
+    row.t[1].combo = h->Y + (long long)i * h->L;
+    row.t[1].m = 0.0;
+    row.t[1].lin = 1.0;
+    run_stage_op(h, a);
+  }
+  CK(cudaMemcpyAsync(JV, Out, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  prof_harvest(h);
+  return IRK_OK;
+}
+
+irk_status irk_kernel_stats(irk_handle* h, irk_kernel_stat* out, int max, int* count) {
+  if (!h || !out || !count) return IRK_ERR_INVALID;
+  prof_harvest(h);
+  int n = 0;
+  for (int k = 0; k < P_NCLASS && n < max; ++k)
+    if (h->prof[k].launches > 0) out[n++] = h->prof[k];
+  *count = n;
+  return IRK_OK;
+}
+
+irk_status irk_reset_kernel_stats(irk_handle* h) {
+  if (!h) return IRK_ERR_INVALID;
+  prof_harvest(h);
+  for (int k = 0; k < P_NCLASS; ++k) {
+    h->prof[k].launches = 0;
+    h->prof[k].ms = h->prof[k].bytes = h->prof[k].flops = 0;
+  }
+  return IRK_OK;
+}
+
+size_t irk_device_bytes(const irk_handle* h) { return h ? h->arena_bytes : 0; }
+
+const char* irk_last_error(const irk_handle* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+void irk_destroy(irk_handle* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  for (auto& ev : h->evpool) cudaEventDestroy(ev);
+  if (h->hbuf) cudaFreeHost(h->hbuf);
+  if (h->arena) cudaFree(h->arena);
+  if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+  delete h;
+}
+
+}  // extern "C"

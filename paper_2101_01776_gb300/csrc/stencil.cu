@@ -1,0 +1,513 @@
+// Matrix-free FP64 stencil kernels of the stage solve.
+//
+//  k_stage_states   Y_i = u_n + dt sum_j a_ij k_j (Eq. stages) and the combined
+//                   fields Ybar_q = sum_m (d_q)_m Y_m that carry the s x s
+//                   transform of Eq. Q0approx into every later stencil.
+//  k_residual       F_i = M k_i - N(Y_i, t_n + c_i dt) (Eq. stages, Eq. dae_stage),
+//                   the Algorithm-1 right-hand side -(Q0^T (x) I) F and the
+//                   per-block partial sums of ||F||^2.
+//  k_stage_op       Generic row operator of the transformed Jacobian:
+//                   y_r = alpha base_r + sigma sum_t [m_t M x_t - dt (Jadv(Ybar_t) x_t
+//                   + lin_t Jlin x_t)], used for the diagonal blocks D_i
+//                   (Eq. diag_blocks), the upper coupling U (Eq. D+U) and the
+//                   coupling row of L_P (Eq. Lprec).  Every N here is bilinear
+//                   in the state, so sum_m d_m N'(Y_m) = Jadv(sum_m d_m Y_m) +
+//                   (sum_m d_m) Jlin: the transform costs one combined field.
+//  k_stage_update   k += (Q0 R0 (x) I) dk_hat (Algorithm 1 back-transform).
+//  k_u_update       u_{n+1} = u_n + dt sum_i b_i k_i (Eq. update).
+//
+// Discretisations (periodic, h = length/n, 2D fields [y][x]):
+//  Burgers-1D  N = -(u_E^2 - u_W^2)/(4h) + nu (u_E - 2u + u_W)/h^2
+//  Burgers-2D  N = (-u Dx u - v Dy u + nu L u, -u Dx v - v Dy v + nu L v)
+//  VSF         N = (J_A(psi, w) + nu L w, -L psi - w), M = diag(I, 0);
+//              J_A is Arakawa's average of the three central Jacobians.
+#include <cuda_bf16.h>
+
+#include "irk_internal.h"
+
+namespace irk {
+
+__device__ __forceinline__ int wrapn(int i, int n) { return i & (n - 1); }
+
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(256) k_stage_states(StageStateArgs a) {
+  const long long L = a.L;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    double k[S], y[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) k[j] = a.K[j * L + p];
+    const double u = a.u ? a.u[p] : 0.0;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < S; ++j) acc = fma(a.A[i * S + j], k[j], acc);
+      y[i] = fma(a.dt, acc, u);
+    }
+    if (a.Y) {
+#pragma unroll
+      for (int i = 0; i < S; ++i) a.Y[i * L + p] = y[i];
+    }
+    if (a.combos) {
+      for (int q = 0; q < a.ncombo; ++q) {
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < S; ++m) acc = fma(a.D[q * S + m], y[m], acc);
+        a.combos[q * L + p] = acc;
+      }
+    }
+  }
+}
+
+void launch_stage_states(const GridDesc& g, const StageStateArgs& a, cudaStream_t st) {
+  const long long L = a.L;
+  int blocks = (int)((L + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  switch (a.s) {
+    case 1: k_stage_states<1><<<blocks, 256, 0, st>>>(a); break;
+    case 2: k_stage_states<2><<<blocks, 256, 0, st>>>(a); break;
+    case 3: k_stage_states<3><<<blocks, 256, 0, st>>>(a); break;
+    case 4: k_stage_states<4><<<blocks, 256, 0, st>>>(a); break;
+    case 5: k_stage_states<5><<<blocks, 256, 0, st>>>(a); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Neighbourhood access.
+struct Nbr {
+  int c, e, w, n, s;              // centre, x+1, x-1, y+1, y-1
+  int ne, nw, se, sw;             // diagonals (2D)
+};
+
+__device__ __forceinline__ Nbr neighbours(const GridDesc& g, int p) {
+  Nbr r;
+  r.c = p;
+  if (g.dim == 1) {
+    r.e = wrapn(p + 1, g.n);
+    r.w = wrapn(p - 1, g.n);
+    r.n = r.s = r.ne = r.nw = r.se = r.sw = p;
+  } else {
+    const int i = p & (g.n - 1), j = p >> g.logn;
+    const int ip = wrapn(i + 1, g.n), im = wrapn(i - 1, g.n);
+    const int jp = wrapn(j + 1, g.n), jm = wrapn(j - 1, g.n);
+    r.e = (j << g.logn) + ip;
+    r.w = (j << g.logn) + im;
+    r.n = (jp << g.logn) + i;
+    r.s = (jm << g.logn) + i;
+    r.ne = (jp << g.logn) + ip;
+    r.nw = (jp << g.logn) + im;
+    r.se = (jm << g.logn) + ip;
+    r.sw = (jm << g.logn) + im;
+  }
+  return r;
+}
+
+// 3x3 neighbourhood f[dy+1][dx+1]
+__device__ __forceinline__ void load9(const double* __restrict__ f, const Nbr& nb, double v[3][3]) {
+  v[0][0] = __ldg(f + nb.sw); v[0][1] = __ldg(f + nb.s); v[0][2] = __ldg(f + nb.se);
+  v[1][0] = __ldg(f + nb.w);  v[1][1] = __ldg(f + nb.c); v[1][2] = __ldg(f + nb.e);
+  v[2][0] = __ldg(f + nb.nw); v[2][1] = __ldg(f + nb.n); v[2][2] = __ldg(f + nb.ne);
+}
+
+// Arakawa Jacobian J_A(a, b) * 12 h^2 from 3x3 neighbourhoods.
+__device__ __forceinline__ double arakawa12(const double a[3][3], const double b[3][3]) {
+  const double jpp = (a[1][2] - a[1][0]) * (b[2][1] - b[0][1]) - (a[2][1] - a[0][1]) * (b[1][2] - b[1][0]);
+  const double jpx = a[1][2] * (b[2][2] - b[0][2]) - a[1][0] * (b[2][0] - b[0][0])
+                   - a[2][1] * (b[2][2] - b[2][0]) + a[0][1] * (b[0][2] - b[0][0]);
+  const double jxp = b[2][1] * (a[2][2] - a[2][0]) - b[0][1] * (a[0][2] - a[0][0])
+                   - b[1][2] * (a[2][2] - a[0][2]) + b[1][0] * (a[2][0] - a[0][0]);
+  return jpp + jpx + jxp;
+}
+
+__device__ __forceinline__ double lap5(const double* __restrict__ f, const Nbr& nb, int dim,
+                                       double invh2) {
+  if (dim == 1) return (__ldg(f + nb.e) - 2.0 * __ldg(f + nb.c) + __ldg(f + nb.w)) * invh2;
+  return (__ldg(f + nb.e) + __ldg(f + nb.w) + __ldg(f + nb.n) + __ldg(f + nb.s) -
+          4.0 * __ldg(f + nb.c)) * invh2;
+}
+
+// Manufactured source of the 1D operators (forcing 1):
+// u*(x,t) = sin(2 pi x)(1 + 0.5 sin t) + 0.25 cos(4 pi x) cos 2t,  f = u*_t - N_h(u*).
+__device__ double manufactured_source(const GridDesc& g, int p, double t) {
+  const double twopi = 6.283185307179586476925286766559;
+  auto ustar = [&](int q) {
+    const double x = q * g.h;
+    return sin(twopi * x) * (1.0 + 0.5 * sin(t)) + 0.25 * cos(2.0 * twopi * x) * cos(2.0 * t);
+  };
+  const double x = p * g.h;
+  const double ut = 0.5 * sin(twopi * x) * cos(t) - 0.5 * cos(2.0 * twopi * x) * sin(2.0 * t);
+  const double uc = ustar(p), ue = ustar(p + 1), uw = ustar(p - 1);
+  double nh = g.nu * (ue - 2.0 * uc + uw) * g.invh2;
+  if (g.op == IRK_OP_BURGERS_1D) nh -= (ue * ue - uw * uw) * g.inv4h;
+  return ut - nh;
+}
+
+// N(Y) at point p for all components (ncomp <= 2).
+template <int OP>
+__device__ __forceinline__ void eval_N(const GridDesc& g, const double* __restrict__ Y, const Nbr& nb,
+                                       double out[2]) {
+  if (OP == IRK_OP_DIFFUSION_1D) {
+    out[0] = g.nu * lap5(Y, nb, 1, g.invh2);
+  } else if (OP == IRK_OP_BURGERS_1D) {
+    const double ue = __ldg(Y + nb.e), uw = __ldg(Y + nb.w), uc = __ldg(Y + nb.c);
+    out[0] = -(ue * ue - uw * uw) * g.inv4h + g.nu * (ue - 2.0 * uc + uw) * g.invh2;
+  } else if (OP == IRK_OP_BURGERS_2D) {
+    const double* u = Y;
+    const double* v = Y + g.npts;
+    const double uc = __ldg(u + nb.c), vc = __ldg(v + nb.c);
+    const double ue = __ldg(u + nb.e), uw = __ldg(u + nb.w), un = __ldg(u + nb.n), us = __ldg(u + nb.s);
+    const double ve = __ldg(v + nb.e), vw = __ldg(v + nb.w), vn = __ldg(v + nb.n), vs = __ldg(v + nb.s);
+    const double ux = (ue - uw) * g.inv2h, uy = (un - us) * g.inv2h;
+    const double vx = (ve - vw) * g.inv2h, vy = (vn - vs) * g.inv2h;
+    const double lu = (ue + uw + un + us - 4.0 * uc) * g.invh2;
+    const double lv = (ve + vw + vn + vs - 4.0 * vc) * g.invh2;
+    out[0] = -uc * ux - vc * uy + g.nu * lu;
+    out[1] = -uc * vx - vc * vy + g.nu * lv;
+  } else {  // VSF
+    double w9[3][3], p9[3][3];
+    load9(Y, nb, w9);
+    load9(Y + g.npts, nb, p9);
+    const double lw = (w9[1][2] + w9[1][0] + w9[2][1] + w9[0][1] - 4.0 * w9[1][1]) * g.invh2;
+    const double lp = (p9[1][2] + p9[1][0] + p9[2][1] + p9[0][1] - 4.0 * p9[1][1]) * g.invh2;
+    out[0] = arakawa12(p9, w9) * g.inv12h2 + g.nu * lw;
+    out[1] = -lp - w9[1][1];
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < nw; ++k) r += sh[k];
+  }
+  return r;
+}
+
+template <int OP, int S>
+__global__ void __launch_bounds__(256) k_residual(GridDesc g, ResidualArgs a) {
+  __shared__ double sh[32];
+  constexpr int C = (OP == IRK_OP_BURGERS_2D || OP == IRK_OP_VSF_2D) ? 2 : 1;
+  const long long L = (long long)C * g.npts;
+  double sq = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npts; p += gridDim.x * blockDim.x) {
+    const Nbr nb = neighbours(g, p);
+    double F[S][C];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      double nv[2];
+      eval_N<OP>(g, a.Y + i * L, nb, nv);
+      if (a.forcing) nv[0] += manufactured_source(g, p, a.tstage[i]);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const double mass = (OP == IRK_OP_VSF_2D && c == 1) ? 0.0 : 1.0;
+        const double k = a.K[i * L + c * (long long)g.npts + p];
+        F[i][c] = mass * k - nv[c];
+        sq = fma(F[i][c], F[i][c], sq);
+      }
+    }
+    if (a.Fraw) {
+#pragma unroll
+      for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int c = 0; c < C; ++c) a.Fraw[i * L + c * (long long)g.npts + p] = F[i][c];
+    }
+    if (a.rhs) {
+#pragma unroll
+      for (int k = 0; k < S; ++k)
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          double acc = 0.0;
+#pragma unroll
+          for (int i = 0; i < S; ++i) acc = fma(a.Q[i * S + k], F[i][c], acc);
+          a.rhs[k * L + c * (long long)g.npts + p] = -acc;
+        }
+    }
+  }
+  const double tot = block_sum(sq, sh);
+  if (threadIdx.x == 0 && a.partials) a.partials[blockIdx.x] = tot;
+}
+
+int residual_blocks(const GridDesc& g) {
+  int blocks = (g.npts + 255) / 256;
+  if (blocks > 152 * 4) blocks = 152 * 4;
+  return blocks;
+}
+
+template <int OP>
+static void launch_residual_op(const GridDesc& g, const ResidualArgs& a, cudaStream_t st) {
+  const int blocks = residual_blocks(g);
+  switch (a.s) {
+    case 1: k_residual<OP, 1><<<blocks, 256, 0, st>>>(g, a); break;
+    case 2: k_residual<OP, 2><<<blocks, 256, 0, st>>>(g, a); break;
+    case 3: k_residual<OP, 3><<<blocks, 256, 0, st>>>(g, a); break;
+    case 4: k_residual<OP, 4><<<blocks, 256, 0, st>>>(g, a); break;
+    case 5: k_residual<OP, 5><<<blocks, 256, 0, st>>>(g, a); break;
+  }
+}
+
+void launch_residual(const GridDesc& g, const ResidualArgs& a, cudaStream_t st) {
+  switch (g.op) {
+    case IRK_OP_DIFFUSION_1D: launch_residual_op<IRK_OP_DIFFUSION_1D>(g, a, st); break;
+    case IRK_OP_BURGERS_1D: launch_residual_op<IRK_OP_BURGERS_1D>(g, a, st); break;
+    case IRK_OP_BURGERS_2D: launch_residual_op<IRK_OP_BURGERS_2D>(g, a, st); break;
+    case IRK_OP_VSF_2D: launch_residual_op<IRK_OP_VSF_2D>(g, a, st); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One term of the row operator at point p, accumulated into acc[c]:
+//   m M x - dt (Jadv(Ybar) x + lin Jlin x)
+template <int OP>
+__device__ __forceinline__ void term_apply(const GridDesc& g, const OpTerm& t, const Nbr& nb,
+                                           double dt, double acc[2]) {
+  const int npts = g.npts;
+  if (OP == IRK_OP_DIFFUSION_1D || OP == IRK_OP_BURGERS_1D) {
+    const double* x = t.x;
+    const double xc = __ldg(x + nb.c), xe = __ldg(x + nb.e), xw = __ldg(x + nb.w);
+    double op = 0.0;
+    if (OP == IRK_OP_BURGERS_1D && t.combo)
+      op = -(__ldg(t.combo + nb.e) * xe - __ldg(t.combo + nb.w) * xw) * g.inv2h;
+    if (t.lin != 0.0) op = fma(t.lin * g.nu, (xe - 2.0 * xc + xw) * g.invh2, op);
+    acc[0] += t.m * xc - dt * op;
+  } else if (OP == IRK_OP_BURGERS_2D) {
+    const double* xu = t.x;
+    const double* xv = t.x + npts;
+    const double uc = __ldg(xu + nb.c), ue = __ldg(xu + nb.e), uw = __ldg(xu + nb.w),
+                 un = __ldg(xu + nb.n), us = __ldg(xu + nb.s);
+    const double vc = __ldg(xv + nb.c), ve = __ldg(xv + nb.e), vw = __ldg(xv + nb.w),
+                 vn = __ldg(xv + nb.n), vs = __ldg(xv + nb.s);
+    double opu = 0.0, opv = 0.0;
+    if (t.combo) {
+      const double* bu = t.combo;
+      const double* bv = t.combo + npts;
+      const double buc = __ldg(bu + nb.c), bvc = __ldg(bv + nb.c);
+      const double bux = (__ldg(bu + nb.e) - __ldg(bu + nb.w)) * g.inv2h;
+      const double buy = (__ldg(bu + nb.n) - __ldg(bu + nb.s)) * g.inv2h;
+      const double bvx = (__ldg(bv + nb.e) - __ldg(bv + nb.w)) * g.inv2h;
+      const double bvy = (__ldg(bv + nb.n) - __ldg(bv + nb.s)) * g.inv2h;
+      const double xux = (ue - uw) * g.inv2h, xuy = (un - us) * g.inv2h;
+      const double xvx = (ve - vw) * g.inv2h, xvy = (vn - vs) * g.inv2h;
+      opu = -(uc * bux + buc * xux + vc * buy + bvc * xuy);
+      opv = -(uc * bvx + buc * xvx + vc * bvy + bvc * xvy);
+    }
+    if (t.lin != 0.0) {
+      const double k = t.lin * g.nu * g.invh2;
+      opu = fma(k, ue + uw + un + us - 4.0 * uc, opu);
+      opv = fma(k, ve + vw + vn + vs - 4.0 * vc, opv);
+    }
+    acc[0] += t.m * uc - dt * opu;
+    acc[1] += t.m * vc - dt * opv;
+  } else {  // VSF: state (w, psi), M = diag(1, 0)
+    double xw9[3][3], xp9[3][3];
+    load9(t.x, nb, xw9);
+    load9(t.x + npts, nb, xp9);
+    double opw = 0.0, opp = 0.0;
+    if (t.combo) {
+      double bw9[3][3], bp9[3][3];
+      load9(t.combo, nb, bw9);
+      load9(t.combo + npts, nb, bp9);
+      opw = (arakawa12(bp9, xw9) + arakawa12(xp9, bw9)) * g.inv12h2;
+    }
+    if (t.lin != 0.0) {
+      const double lw = (xw9[1][2] + xw9[1][0] + xw9[2][1] + xw9[0][1] - 4.0 * xw9[1][1]) * g.invh2;
+      const double lp = (xp9[1][2] + xp9[1][0] + xp9[2][1] + xp9[0][1] - 4.0 * xp9[1][1]) * g.invh2;
+      opw = fma(t.lin * g.nu, lw, opw);
+      opp = t.lin * (-xw9[1][1] - lp);
+    }
+    acc[0] += t.m * xw9[1][1] - dt * opw;
+    acc[1] += -dt * opp;
+  }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(256) k_stage_op(GridDesc g, StageOpArgs a) {
+  constexpr int C = (OP == IRK_OP_BURGERS_2D || OP == IRK_OP_VSF_2D) ? 2 : 1;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npts; p += gridDim.x * blockDim.x) {
+    const Nbr nb = neighbours(g, p);
+    for (int r = 0; r < a.nrow; ++r) {
+      const OpRow& row = a.row[r];
+      double acc[2] = {0.0, 0.0};
+      for (int k = 0; k < row.nterm; ++k) term_apply<OP>(g, row.t[k], nb, a.dt, acc);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const long long idx = (long long)c * g.npts + p;
+        double y = row.sigma * acc[c];
+        if (row.base) y = fma(row.alpha, row.base[idx], y);
+        row.y[idx] = y;
+      }
+    }
+    if (a.copy_dst)
+      for (long long q = p; q < a.copy_len; q += g.npts) a.copy_dst[q] = a.copy_src[q];
+  }
+}
+
+void launch_stage_op(const GridDesc& g, const StageOpArgs& a, cudaStream_t st) {
+  int blocks = (g.npts + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  switch (g.op) {
+    case IRK_OP_DIFFUSION_1D: k_stage_op<IRK_OP_DIFFUSION_1D><<<blocks, 256, 0, st>>>(g, a); break;
+    case IRK_OP_BURGERS_1D: k_stage_op<IRK_OP_BURGERS_1D><<<blocks, 256, 0, st>>>(g, a); break;
+    case IRK_OP_BURGERS_2D: k_stage_op<IRK_OP_BURGERS_2D><<<blocks, 256, 0, st>>>(g, a); break;
+    case IRK_OP_VSF_2D: k_stage_op<IRK_OP_VSF_2D><<<blocks, 256, 0, st>>>(g, a); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+struct SmallMat {
+  double m[IRK_MAXS * IRK_MAXS];
+};
+
+template <int S>
+__global__ void __launch_bounds__(256) k_stage_update(long long L, SmallMat T, const double* __restrict__ yhat,
+                                                      double* __restrict__ K) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    double y[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) y[k] = yhat[k * L + p];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      double acc = K[i * L + p];
+#pragma unroll
+      for (int k = 0; k < S; ++k) acc = fma(T.m[i * S + k], y[k], acc);
+      K[i * L + p] = acc;
+    }
+  }
+}
+
+void launch_stage_update(long long L, int s, const double* QR, const double* yhat, double* K,
+                         cudaStream_t st) {
+  SmallMat T;
+  for (int i = 0; i < s * s; ++i) T.m[i] = QR[i];
+  int blocks = (int)((L + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  switch (s) {
+    case 1: k_stage_update<1><<<blocks, 256, 0, st>>>(L, T, yhat, K); break;
+    case 2: k_stage_update<2><<<blocks, 256, 0, st>>>(L, T, yhat, K); break;
+    case 3: k_stage_update<3><<<blocks, 256, 0, st>>>(L, T, yhat, K); break;
+    case 4: k_stage_update<4><<<blocks, 256, 0, st>>>(L, T, yhat, K); break;
+    case 5: k_stage_update<5><<<blocks, 256, 0, st>>>(L, T, yhat, K); break;
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) k_u_update(long long L, SmallMat bw, const double* __restrict__ K,
+                                                  double* __restrict__ u) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < S; ++i) acc = fma(bw.m[i], K[i * L + p], acc);
+    u[p] = fma(bw.m[IRK_MAXS], acc, u[p]);
+  }
+}
+
+void launch_u_update(long long L, int s, const double* b, double dt, const double* K, double* u,
+                     cudaStream_t st) {
+  SmallMat bw;
+  for (int i = 0; i < s; ++i) bw.m[i] = b[i];
+  bw.m[IRK_MAXS] = dt;
+  int blocks = (int)((L + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  switch (s) {
+    case 1: k_u_update<1><<<blocks, 256, 0, st>>>(L, bw, K, u); break;
+    case 2: k_u_update<2><<<blocks, 256, 0, st>>>(L, bw, K, u); break;
+    case 3: k_u_update<3><<<blocks, 256, 0, st>>>(L, bw, K, u); break;
+    case 4: k_u_update<4><<<blocks, 256, 0, st>>>(L, bw, K, u); break;
+    case 5: k_u_update<5><<<blocks, 256, 0, st>>>(L, bw, K, u); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid coefficient field of a diagonal block row: the advecting
+// velocity of the frozen-coefficient operator.  Burgers: the combined state
+// itself; VSF: (Dy psibar, -Dx psibar).  Written in the MG storage precision.
+template <typename T>
+__device__ __forceinline__ void store_as(T* p, double v);
+template <>
+__device__ __forceinline__ void store_as<double>(double* p, double v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_as<float>(float* p, double v) { *p = (float)v; }
+template <>
+__device__ __forceinline__ void store_as<__nv_bfloat16>(__nv_bfloat16* p, double v) {
+  *p = __double2bfloat16(v);
+}
+
+template <typename T>
+__global__ void k_velocity(GridDesc g, const double* __restrict__ combo, T* __restrict__ vel) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npts; p += gridDim.x * blockDim.x) {
+    if (g.op == IRK_OP_VSF_2D) {
+      const Nbr nb = neighbours(g, p);
+      const double* psi = combo + g.npts;
+      store_as<T>(vel + p, (__ldg(psi + nb.n) - __ldg(psi + nb.s)) * g.inv2h);
+      store_as<T>(vel + g.npts + p, -(__ldg(psi + nb.e) - __ldg(psi + nb.w)) * g.inv2h);
+    } else if (g.op == IRK_OP_BURGERS_2D) {
+      store_as<T>(vel + p, combo[p]);
+      store_as<T>(vel + g.npts + p, combo[g.npts + p]);
+    } else if (g.op == IRK_OP_BURGERS_1D) {
+      store_as<T>(vel + p, combo[p]);
+    } else {
+      store_as<T>(vel + p, 0.0);
+    }
+  }
+}
+
+void launch_velocity_from_combo(const GridDesc& g, const double* combo, void* vel, int prec,
+                                cudaStream_t st) {
+  int blocks = (g.npts + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (prec == IRK_MG_FP64)
+    k_velocity<double><<<blocks, 256, 0, st>>>(g, combo, (double*)vel);
+  else if (prec == IRK_MG_FP32)
+    k_velocity<float><<<blocks, 256, 0, st>>>(g, combo, (float*)vel);
+  else
+    k_velocity<__nv_bfloat16><<<blocks, 256, 0, st>>>(g, combo, (__nv_bfloat16*)vel);
+}
+
+// ---------------------------------------------------------------------------
+// Zero-mean projection of periodic fields (the psi null space of the DAE).
+__global__ void k_field_sums(long long npts, long long stride, const double* __restrict__ x,
+                             double* __restrict__ partials) {
+  __shared__ double sh[32];
+  const double* f = x + blockIdx.y * stride;
+  double acc = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npts;
+       p += (long long)gridDim.x * blockDim.x)
+    acc += f[p];
+  const double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+}
+
+__global__ void k_field_sub_mean(long long npts, long long stride, int nblk,
+                                 const double* __restrict__ partials, double* __restrict__ x) {
+  __shared__ double mean;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partials[blockIdx.y * nblk + b];
+    mean = s / (double)npts;
+  }
+  __syncthreads();
+  double* f = x + blockIdx.y * stride;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npts;
+       p += (long long)gridDim.x * blockDim.x)
+    f[p] -= mean;
+}
+
+void launch_remove_mean(long long npts, int nfields, long long stride, double* x, double* scratch,
+                        cudaStream_t st) {
+  int nblk = (int)((npts + 255) / 256);
+  if (nblk > 152) nblk = 152;
+  dim3 grid(nblk, nfields);
+  k_field_sums<<<grid, 256, 0, st>>>(npts, stride, x, scratch);
+  k_field_sub_mean<<<grid, 256, 0, st>>>(npts, stride, nblk, scratch, x);
+}
+
+}  // namespace irk

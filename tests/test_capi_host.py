@@ -1,0 +1,98 @@
+"""Host-side checks of the C-ABI library (no GPU compute).
+
+The library must load, export every function include/irk.h declares, reject
+invalid configurations before touching a device, and compute the same
+tableau and real Schur form as the oracle (up to the non-unique parts of a
+Schur basis).
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2101_01776_gb300 import build
+    build.build()
+    from paper_2101_01776_gb300 import binding
+    return binding
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "irk.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(irk_[a-z_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol(B):
+    names = declared_functions()
+    assert len(names) >= 12
+    lib = ctypes.CDLL(B._LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(B.EXPORTED)
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 5])
+def test_host_tableau_matches_oracle(B, s):
+    from oracle import tableau as tab
+    t = B.irk_tableau(s)
+    A, b, c = tab.gauss(s)
+    np.testing.assert_allclose(t["A"], A, atol=1e-15)
+    np.testing.assert_allclose(t["b"], b, atol=1e-15)
+    np.testing.assert_allclose(t["c"], c, atol=1e-15)
+    Ainv = np.linalg.inv(A)
+    Q, R = t["Q0"], t["R0"]
+    np.testing.assert_allclose(Q @ Q.T, np.eye(s), atol=1e-14)
+    np.testing.assert_allclose(Q @ R @ Q.T, Ainv, atol=1e-12)
+    # eta, beta^2 and gamma* per block agree with the oracle's Schur form
+    Qo, Ro, blocks_o = tab.real_schur(Ainv)
+    ours, k = [], 0
+    for m in t["block_sizes"]:
+        if m == 1:
+            ours.append((round(R[k, k], 9), 0.0))
+        else:
+            assert abs(R[k, k] - R[k + 1, k + 1]) < 1e-13
+            assert np.all(np.abs(R[k + 2:, k:k + 2]) == 0)
+            ours.append((round(R[k, k], 9), round(-R[k, k + 1] * R[k + 1, k], 8)))
+        k += m
+    theirs = []
+    for bc in tab.block_constants(Ro, blocks_o):
+        theirs.append((round(bc["eta"], 9), round(bc["beta"] ** 2, 8)))
+    assert sorted(ours) == sorted(theirs)
+
+
+def test_gauss2_schur_basis_is_identity(B):
+    """Eq. Gauss4Radau3_example: A0^{-1} of 2-stage Gauss is already in
+    standardized form, so the block is exactly Newton (P-hat block diagonal)."""
+    t = B.irk_tableau(2)
+    np.testing.assert_array_equal(t["Q0"], np.eye(2))
+
+
+def test_invalid_configs_rejected_before_device(B):
+    u0 = np.zeros(256)
+    bad = [dict(stages=0), dict(stages=6), dict(n=100), dict(nu=0.0), dict(nu=-1.0),
+           dict(op="vsf", mass=0), dict(op="burgers1d", mass=1), dict(family=3),
+           dict(krylov_restart=0), dict(krylov_restart=65), dict(nonlinear_variant=1),
+           dict(mg_precision=3), dict(forcing=1, op="burgers2d")]
+    for kw in bad:
+        cfg = B.irk_config_default(**kw)
+        with pytest.raises(B.IrkError) as ei:
+            B.irk_create(cfg, u0)
+        assert ei.value.status == B.IRK_ERR_INVALID, kw
+
+
+def test_no_device_reported_cleanly(B):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    cfg = B.irk_config_default()
+    with pytest.raises(B.IrkError) as ei:
+        B.irk_create(cfg, np.zeros(256))
+    assert ei.value.status == B.IRK_ERR_NO_DEVICE

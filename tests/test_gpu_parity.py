@@ -1,0 +1,276 @@
+"""CUDA path vs the FP64 oracle, through the C ABI.
+
+Tolerances (spec contract): per step, starting from the oracle's u_n,
+the GPU u_{n+1} matches the oracle within 1e-9 relative L2 at Newton relative
+residual 1e-10; over a full run within 1e-8.  Operator kernels (residual,
+Jacobian-vector product) are compared element by element at 1e-12 relative
+to the largest entry (differences are rounding order only).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import irk as orc
+from oracle import tableau as tab
+from oracle import vsf as ovsf
+from oracle.operators import Problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-9
+RUN_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_01776_gb300 import build
+    build.build()
+    from paper_2101_01776_gb300 import binding
+    return binding
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def make_problem(op, n, nu, s):
+    length = 2 * math.pi if op == "vsf" else 1.0
+    return Problem(op, n, nu, length), length
+
+
+def initial(op, n, seed):
+    if op == "burgers1d" or op == "diffusion1d":
+        return workloads.burgers1d_initial(n, seed=seed)[None]
+    if op == "burgers2d":
+        return workloads.random_fourier_2d(n, seed=seed)
+    w0 = workloads.double_shear_layer_vorticity(n, seed=seed)
+    return ovsf.initial_state(w0, 2 * math.pi / n)
+
+
+def oracle_step(p, s, u, t, dt):
+    if p.op == "vsf":
+        return ovsf.reduced_step(p, s, u, t, dt)
+    linear = "direct" if p.size * s <= 40000 else "gmres"
+    return orc.step(p, s, u, t, dt, linear=linear)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("op,n,s", [("diffusion1d", 64, 2), ("burgers1d", 64, 2), ("burgers1d", 64, 5),
+                                    ("burgers2d", 32, 2), ("burgers2d", 16, 3), ("vsf", 32, 3),
+                                    ("vsf", 16, 5)])
+def test_stage_residual_matches_oracle(B, op, n, s):
+    nu = 0.013
+    p, length = make_problem(op, n, nu, s)
+    rng = np.random.default_rng(11)
+    u = rng.standard_normal(p.shape)
+    K = rng.standard_normal((s,) + p.shape)
+    dt, t = 3e-3, 0.25
+    A, b, c = tab.gauss(s)
+    want = orc.stage_residual(p, u, K, t, dt, A, c)
+    with B.IrkSolver(u, op=op, n=n, stages=s, nu=nu, length=length) as sol:
+        sol.set_state(u)
+        got = B.irk_stage_residual(sol.h, t, dt, K, np.empty_like(K))
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_stage_residual_with_manufactured_forcing(B):
+    n, s, nu = 64, 3, 0.02
+    p = Problem("burgers1d", n, nu, forcing=1)
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal(p.shape)
+    K = rng.standard_normal((s,) + p.shape)
+    A, b, c = tab.gauss(s)
+    want = orc.stage_residual(p, u, K, 0.7, 0.05, A, c)
+    with B.IrkSolver(u, op="burgers1d", n=n, stages=s, nu=nu, forcing=1) as sol:
+        got = B.irk_stage_residual(sol.h, 0.7, 0.05, K, np.empty_like(K))
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("op,n,s", [("burgers1d", 64, 3), ("burgers2d", 16, 2), ("vsf", 16, 3)])
+def test_stage_jacobian_matches_oracle(B, op, n, s):
+    nu = 0.02
+    p, length = make_problem(op, n, nu, s)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal(p.shape)
+    K = rng.standard_normal((s,) + p.shape)
+    V = rng.standard_normal((s,) + p.shape)
+    dt = 4e-3
+    A, _, _ = tab.gauss(s)
+    want = (orc.newton_matrix(p, u, K, dt, A) @ V.ravel()).reshape(V.shape)
+    with B.IrkSolver(u, op=op, n=n, stages=s, nu=nu, length=length) as sol:
+        sol.set_state(u)
+        got = B.irk_stage_jacobian_apply(sol.h, dt, K, V, np.empty_like(V))
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+# ---------------------------------------------------------------------------
+def run_parity(B, op, n, s, nu, dt, nsteps, seed=0, device_buffers=False, **cfg):
+    p, length = make_problem(op, n, nu, s)
+    u0 = initial(op, n, seed)
+    per_step, infos = [], []
+    u_ref = u0.copy()
+    with B.IrkSolver(u0 if op != "vsf" else u0.copy(), op=op, n=n, stages=s, nu=nu,
+                     length=length, **cfg) as sol:
+        # per step, restarting from the oracle's state
+        t = 0.0
+        for k in range(nsteps):
+            sol.set_state(u_ref)
+            st = sol.step(t, dt, 1)
+            infos.append(st.as_dict())
+            u_next, _, _ = oracle_step(p, s, u_ref, t, dt)
+            per_step.append(rel(sol.state(), u_next))
+            u_ref = u_next
+            t += dt
+        # whole run from u0
+        start = u0 if op != "vsf" else initial(op, n, seed)
+        if device_buffers:
+            d = torch.from_numpy(start.copy()).cuda()
+            sol.set_state(d)
+        else:
+            sol.set_state(start)
+        sol.step(0.0, dt, nsteps)
+        whole = rel(sol.state(), u_ref)
+    return per_step, whole, infos
+
+
+def test_config0_burgers1d_n256_gauss2_10_steps(B):
+    """1D viscous Burgers, N=256, nu=0.01, Gauss s=2, dt=1e-3, 10 steps."""
+    per_step, whole, infos = run_parity(B, "burgers1d", 256, 2, 0.01, 1e-3, 10, seed=0)
+    assert max(per_step) <= STEP_TOL, per_step
+    assert whole <= RUN_TOL, whole
+    assert all(i["final_rel_res"] <= 1e-10 for i in infos)
+    # s = 2 with Newton-like(3) is exact Newton: a few iterations per step
+    assert all(i["newton_its"] <= 4 for i in infos), infos
+
+
+@pytest.mark.parametrize("s", [1, 3, 4, 5])
+def test_burgers1d_all_stage_counts(B, s):
+    per_step, whole, _ = run_parity(B, "burgers1d", 128, s, 0.01, 2e-3, 3, seed=1)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole)
+
+
+@pytest.mark.parametrize("n,s", [(32, 2), (64, 2), (64, 3), (16, 5)])
+def test_burgers2d_parity(B, n, s):
+    per_step, whole, infos = run_parity(B, "burgers2d", n, s, 5e-3, 2e-3, 3, seed=1)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
+
+
+@pytest.mark.parametrize("n,s", [(32, 2), (32, 3), (16, 5)])
+def test_vsf_parity(B, n, s):
+    per_step, whole, infos = run_parity(B, "vsf", n, s, 1e-3, 5e-3, 2, seed=2)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_precision_preconditioner_same_result(B, prec):
+    """FP32 / BF16-stored V-cycles change Krylov counts, not the fixed point."""
+    per_step, whole, infos = run_parity(B, "burgers2d", 64, 3, 5e-3, 2e-3, 2, seed=3,
+                                        mg_precision=prec)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole)
+
+
+@pytest.mark.parametrize("kw", [dict(gamma_mode=1), dict(nonlinear_variant=2),
+                                dict(krylov_restart=3), dict(mg_levels=2)])
+def test_solver_variants_reach_same_fixed_point(B, kw):
+    per_step, whole, _ = run_parity(B, "burgers2d", 32, 3, 5e-3, 2e-3, 2, seed=4, **kw)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (kw, per_step, whole)
+
+
+def test_device_buffers_and_minimum_grid(B):
+    per_step, whole, _ = run_parity(B, "burgers2d", 8, 2, 5e-3, 2e-3, 2, seed=5, device_buffers=True)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 5])
+def test_linear_diffusion_pade_per_mode(B, s):
+    n, nu, dt = 64, 0.05, 0.004
+    u0 = np.random.default_rng(s).standard_normal((1, n))
+    with B.IrkSolver(u0, op="diffusion1d", n=n, stages=s, nu=nu) as sol:
+        sol.step(0.0, dt, 1)
+        u1 = sol.state()
+    coef = [math.factorial(2 * s - j) * math.factorial(s)
+            / (math.factorial(2 * s) * math.factorial(j) * math.factorial(s - j)) for j in range(s + 1)]
+    m = np.arange(n)
+    z = -dt * (4 * nu * n * n) * np.sin(np.pi * m / n) ** 2
+    R = np.polyval(coef[::-1], z) / np.polyval(coef[::-1], -z)
+    want = np.real(np.fft.ifft(R * np.fft.fft(u0[0])))
+    assert rel(u1[0], want) <= 1e-9
+
+
+# ---------------------------------------------------------------------------
+def test_full_size_burgers2d_512_one_step(B):
+    """2D Burgers 512^2, Gauss s=2, dt=2e-3 (the benchmark workload): the GPU
+    stages satisfy the oracle's stage equations to the Newton tolerance, the
+    update matches Eq. update, and u_{n+1} matches the oracle's GMRES variant."""
+    n, s, nu, dt = 512, 2, 5e-3, 2e-3
+    p = Problem("burgers2d", n, nu)
+    u0 = workloads.random_fourier_2d(n, seed=1)
+    with B.IrkSolver(u0, op="burgers2d", n=n, stages=s, nu=nu) as sol:
+        st = sol.step(0.0, dt, 1)
+        u1 = sol.state()
+        K = sol.stages()
+    A, b, c = tab.gauss(s)
+    F = orc.stage_residual(p, u0, K, 0.0, dt, A, c)
+    F0 = orc.stage_residual(p, u0, np.zeros_like(K), 0.0, dt, A, c)
+    assert np.linalg.norm(F) <= 2e-10 * np.linalg.norm(F0)
+    assert rel(u1, u0 + dt * np.tensordot(b, K, axes=(0, 0))) <= 1e-14
+    ref, _, _ = orc.step(p, s, u0, 0.0, dt, linear="gmres")
+    assert rel(u1, ref) <= STEP_TOL
+
+
+# ---------------------------------------------------------------------------
+def test_edge_cases(B):
+    n = 64
+    zero = np.zeros((1, n))
+    with B.IrkSolver(zero, op="burgers1d", n=n, stages=2, nu=0.01) as sol:
+        st = sol.step(0.0, 1e-3, 3)              # F(0) = 0: converged at k = 0
+        assert st.steps == 3 and st.newton_its == 0
+        assert np.all(sol.state() == 0)
+        st = sol.step(0.0, 1e-3, 0)              # nsteps = 0 is a no-op
+        assert st.steps == 0
+        with pytest.raises(B.IrkError):
+            sol.step(0.0, -1e-3, 1)
+        with pytest.raises(B.IrkError):
+            sol.step(0.0, float("nan"), 1)
+
+
+def test_failed_step_leaves_state_untouched(B):
+    n = 64
+    u0 = workloads.burgers1d_initial(n, seed=0)[None]
+    with B.IrkSolver(u0, op="burgers1d", n=n, stages=2, nu=0.01, newton_maxit=1) as sol:
+        before = sol.state().copy()
+        with pytest.raises(B.IrkError) as ei:
+            sol.step(0.0, 1e-2, 1)
+        assert ei.value.status == B.IRK_ERR_NEWTON_MAXIT
+        np.testing.assert_array_equal(sol.state(), before)
+    bad = u0.copy()
+    bad[0, 3] = np.nan
+    with B.IrkSolver(bad, op="burgers1d", n=n, stages=2, nu=0.01) as sol:
+        with pytest.raises(B.IrkError) as ei:
+            sol.step(0.0, 1e-3, 1)
+        assert ei.value.status == B.IRK_ERR_NEWTON_DIVERGED
+
+
+def test_checkpoint_resume_and_determinism_bit_equal(B):
+    n, s = 64, 3
+    u0 = workloads.random_fourier_2d(n, seed=7)
+    kw = dict(op="burgers2d", n=n, stages=s, nu=5e-3)
+    with B.IrkSolver(u0, **kw) as a:
+        a.step(0.0, 2e-3, 4)
+        full = a.state().copy()
+        a.set_state(u0)
+        a.step(0.0, 2e-3, 4)
+        again = a.state().copy()
+    with B.IrkSolver(u0, **kw) as b:
+        b.step(0.0, 2e-3, 2)
+        ck = b.state().copy()
+    with B.IrkSolver(ck, **kw) as c:
+        c.step(2 * 2e-3, 2e-3, 2)
+        resumed = c.state().copy()
+    np.testing.assert_array_equal(full, again)
+    np.testing.assert_array_equal(full, resumed)
