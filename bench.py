@@ -1,0 +1,408 @@
+"""Benchmark: Gauss-IRK steps/s on 2D viscous Burgers 512^2 (one GB300).
+
+A bench "step" is one IRK step at Newton relative residual 1e-10: the whole
+hot path (stage states, residual, Algorithm-1 block solves with FGMRES and
+V-cycles, updates) over the 512^2 (u, v) field, FP64 throughout (the plain
+FP64 GPU method).  Workload: nu = 5e-3, dt = 2e-3, seeded random-Fourier
+initial field (16 modes, |k| <= 8), Gauss s = 2 (headline) and s = 3.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  Timing: CUDA events on the solver's stream around
+each step, L2 flushed (a 512 MiB write) between steps outside the events;
+max over ranks; each rank runs an independent replica (weak scaling, no
+collective on the data path).  `e2e` times the same steps through the C ABI
+with host buffers: set_state from pinned host memory, the step, get_state
+back to host.  `--impl reference` times the FP64 CPU oracle on the same
+workload (a bounded number of steps on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 512
+NU = 5e-3
+DT = 2e-3
+SEED = 1
+WORKLOAD = "burgers2d_512_gauss2"
+METRIC = "IRK steps/s at 1e-10 Newton resid"
+UNIT = "steps/s"
+FP64_PEAK_TFLOPS_DERIVED = 152 * 2.070e9 * 4 / 1e12  # 2 DFMA/clk/SM at 2070 MHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--stages", type=int, default=2)
+    ap.add_argument("--mg-precision", type=int, default=0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the s=3 / FP32 / e2e / CPU legs")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://")
+    return rank, world
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_leg(stages: int) -> dict:
+    """The oracle, as it stands, on one IRK step of the same workload, run in
+    a fresh interpreter limited to one BLAS/OpenMP thread."""
+    code = (
+        "import time, json, sys; sys.path.insert(0, %r)\n"
+        "import workloads\n"
+        "from oracle import irk\n"
+        "from oracle.operators import Problem\n"
+        "p = Problem('burgers2d', %d, %r)\n"
+        "u0 = workloads.random_fourier_2d(%d, seed=%d)\n"
+        "t = time.perf_counter(); irk.step(p, %d, u0, 0.0, %r, linear='gmres')\n"
+        "print(json.dumps({'sec': time.perf_counter() - t}))\n"
+    ) % (ROOT, N, NU, N, SEED, stages, DT)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=600)
+    sec = json.loads(r.stdout.strip().splitlines()[-1])["sec"]
+    return {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 IRK step (Gauss s={stages}) of the 512^2 workload from u0: exact Newton, "
+                      "SciPy GMRES rtol 1e-13 on the assembled Jacobian, 1 thread"}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+    import workloads
+    from oracle import irk
+    from oracle.operators import Problem
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    p = Problem("burgers2d", N, NU)
+    u = workloads.random_fourier_2d(N, seed=SEED)
+    budget = 150.0  # seconds of timed oracle work at most
+    warm = min(args.warmup, 1)
+    t = 0.0
+    for _ in range(warm):
+        u, _, _ = irk.step(p, args.stages, u, t, DT, linear="gmres")
+        t += DT
+    times = []
+    t_start = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        u, _, _ = irk.step(p, args.stages, u, t, DT, linear="gmres")
+        times.append(time.perf_counter() - t0)
+        t += DT
+        if time.perf_counter() - t_start > budget:
+            break
+    sec = sum(times) / len(times)
+    val = 1.0 / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": len(times), "warmup": warm, "ms_per_step": 1e3 * sec, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.stages == 2 else f"burgers2d_512_gauss{args.stages}",
+                   "n": N, "nu": NU, "dt": DT, "stages": args.stages, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", "1")),
+                         "kind": "oracle",
+                         "sample": f"{len(times)} timed IRK steps (of {args.steps} requested, "
+                                   f"{budget:.0f} s budget) after {warm} warm-up, FP64 exact Newton "
+                                   "with SciPy GMRES on the host cores"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    import workloads
+    from paper_2101_01776_gb300 import build as pbuild
+    if not os.path.exists(pbuild.LIB):
+        pbuild.build()
+    from paper_2101_01776_gb300 import binding as B
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    u0 = workloads.random_fourier_2d(N, seed=SEED + rank)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make(stages, prec, profile):
+        cfg = B.irk_config_default(op="burgers2d", n=N, nu=NU, stages=stages,
+                                   mg_precision=prec, profile=profile)
+        h = B.irk_create(cfg, torch.from_numpy(u0).to(dev), stream)
+        return h
+
+    def timed_steps(h, nsteps, warm, t0=0.0):
+        t = t0
+        for _ in range(warm):
+            B.irk_step(h, t, DT, 1)
+            t += DT
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(nsteps)]
+        tot = {"newton_its": 0, "krylov_its": 0, "vcycles": 0, "prec_apps": 0, "launches": 0}
+        for k in range(nsteps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            st = B.irk_step(h, t, DT, 1)
+            ev[k][1].record(stream)
+            t += DT
+            tot["newton_its"] += st.newton_its
+            tot["krylov_its"] += st.krylov_its
+            tot["vcycles"] += st.vcycles
+            tot["prec_apps"] += st.prec_apps
+            tot["launches"] += st.kernel_launches
+        torch.cuda.synchronize(dev)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, tot, t
+
+    # ---- headline: plain FP64 GPU method -----------------------------------
+    h = make(args.stages, args.mg_precision, 0)
+    hbm_peak, peak_src = peaks()
+    clocks = ClockSampler(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t = 0.0
+    for _ in range(args.warmup):
+        B.irk_step(h, t, DT, 1)
+        t += DT
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ms, tot, t = timed_steps(h, args.steps, 0, t)
+    clk = clocks.stop()
+    B.irk_destroy(h)
+    # ---- per-kernel CUDA-event timing: an instrumented repeat of the timed
+    # steps (events around every launch slow the host's launch rate, so the
+    # headline above runs without them; kernel durations are unaffected)
+    h = make(args.stages, args.mg_precision, 1)
+    for _ in range(args.warmup):
+        B.irk_step(h, 0.0, DT, 1)
+    torch.cuda.synchronize(dev)
+    B.irk_reset_kernel_stats(h)
+    _ms_prof, _tot_prof, _ = timed_steps(h, args.steps, 0, args.warmup * DT)
+    kstats = B.irk_kernel_stats(h)
+    B.irk_destroy(h)
+    step_ms = sum(ms) / len(ms)
+    local_time = sum(ms)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([local_time], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        local_time = float(tt[0])
+        dist.barrier()
+    total_steps = args.steps * world
+    value = total_steps / (local_time / 1e3)
+
+    # ---- roofline of the dominant kernel class (CUDA-event time inside the timed region)
+    dom = max(kstats, key=lambda k: k["ms"])
+    ridge = FP64_PEAK_TFLOPS_DERIVED * 1e12 / (hbm_peak * 1e9)
+    intensity = dom["flops"] / max(dom["bytes"], 1.0)
+    traffic = read_traffic(dom["name"])
+    if intensity > ridge:
+        achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS_DERIVED,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS_DERIVED,
+                "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2070 MHz",
+                "traffic": traffic}
+    else:
+        achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": f"{peak_src} hbm_gbs",
+                "traffic": traffic}
+    roof.update({"kernel": dom["name"], "launches": dom["launches"],
+                 "timing": "CUDA events around each launch on the solver stream, "
+                           "instrumented repeat of the timed steps",
+                 "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1),
+                 "algorithmic_bytes_per_launch": dom["bytes"] / max(dom["launches"], 1),
+                 "algorithmic_flops_per_launch": dom["flops"] / max(dom["launches"], 1)})
+    kernel_table = sorted(
+        ({"name": k["name"], "launches": k["launches"], "ms": round(k["ms"], 3),
+          "share": round(k["ms"] / sum(x["ms"] for x in kstats), 4),
+          "GBps": round(k["bytes"] / max(k["ms"], 1e-9) / 1e6, 1),
+          "TFLOPs": round(k["flops"] / max(k["ms"], 1e-9) / 1e9, 4)} for k in kstats),
+        key=lambda r: -r["ms"])
+    step_bytes = sum(k["bytes"] for k in kstats) / args.steps
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.stages == 2 else f"burgers2d_512_gauss{args.stages}",
+                   "n": N, "nu": NU, "dt": DT, "stages": args.stages,
+                   "mg_precision": ["fp64", "fp32", "bf16"][args.mg_precision],
+                   "newton_rtol": 1e-10, "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "gpu_launches": tot["launches"],
+        "clocks": clk,
+        "solver": {"newton_its_per_step": tot["newton_its"] / args.steps,
+                   "krylov_its_per_step": tot["krylov_its"] / args.steps,
+                   "prec_apps_per_step": tot["prec_apps"] / args.steps,
+                   "vcycles_per_step": tot["vcycles"] / args.steps,
+                   "vcycles_per_s": tot["vcycles"] / (sum(ms) / 1e3),
+                   "algorithmic_GB_per_step": step_bytes / 1e9,
+                   "step_hbm_frac": step_bytes / (step_ms / 1e3) / (hbm_peak * 1e9)},
+        "kernels": kernel_table[:8],
+    }
+
+    if not args.no_extras and rank == 0:
+        # ---- e2e through the C ABI with host buffers -------------------------
+        h = make(args.stages, args.mg_precision, 0)
+        host_in = torch.from_numpy(u0.copy()).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        for _ in range(2):
+            B.irk_set_state(h, host_in)
+            B.irk_step(h, 0.0, DT, 1)
+            B.irk_get_state(h, host_out)
+        e2e_n = max(3, min(args.steps, 5))
+        t_e = 0.0
+        tt = 0.0
+        for _ in range(e2e_n):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            a = time.perf_counter()
+            B.irk_set_state(h, host_in)
+            B.irk_step(h, tt, DT, 1)
+            B.irk_get_state(h, host_out)
+            t_e += time.perf_counter() - a
+            host_in.copy_(host_out)
+            tt += DT
+        B.irk_destroy(h)
+        nbytes = u0.size * 8
+        line["e2e"] = {"value": e2e_n / t_e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": nbytes}
+        # ---- the other stage count and the FP32 V-cycle, same workload ------
+        extra = {}
+        for label, stages, prec in (("gauss3_fp64", 3, 0), ("gauss2_mg_fp32", 2, 1),
+                                    ("gauss3_mg_fp32", 3, 1)):
+            h = make(stages, prec, 0)
+            ms2, tot2, _ = timed_steps(h, 3, 2)
+            B.irk_destroy(h)
+            extra[label] = {"steps_per_s": 1e3 / (sum(ms2) / len(ms2)),
+                            "krylov_its_per_step": tot2["krylov_its"] / 3,
+                            "newton_its_per_step": tot2["newton_its"] / 3}
+        line["variants"] = extra
+        if world == 1:
+            try:
+                line["cpu_baseline"] = cpu_baseline_leg(args.stages)
+            except Exception as e:  # report, never hide
+                line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                        "sample": f"failed: {e!r}"[:200]}
+    elif "e2e" not in line:
+        line["e2e"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def read_traffic(kernel_class: str):
+    """DRAM bytes per launch of the kernel class from the committed ncu
+    summary, or None when absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    import hashlib
+    for line in open(path):
+        if line.startswith("#") or "=" not in line:
+            continue
+        kv = dict(x.split("=", 1) for x in line.split())
+        if kv.get("class") != kernel_class:
+            continue
+        src = os.path.join(ROOT, "paper_2101_01776_gb300", "csrc", kv.get("source", ""))
+        if not os.path.exists(src):
+            return None
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != kv.get("sha"):
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -104,6 +104,7 @@ typedef struct {
   int vcycles;          /* V-cycles applied */
   int max_newton_its;   /* worst step */
   double final_rel_res; /* ||F|| / ||F(0)|| at acceptance of the last step */
+  long long kernel_launches; /* this library's kernel launches in the call */
 } irk_stats;
 
 typedef struct {

@@ -10,7 +10,7 @@ equations M k_i = N(u_n + dt sum_j a_ij k_j, t_n + c_i dt) (Eq. stages) to
 a Newton relative residual far below 1e-10, using exact Newton on the fully
 coupled sN x sN system (Eq. k0) with a sparse direct solve (or, for grids
 where a direct factorisation does not fit, restarted GMRES on the same exact
-Jacobian to rtol 1e-13).  For the vorticity-streamfunction DAE (Sec. 5,
+Jacobian to rtol 1e-13).  For the vorticity-streamfunction DAE (Sec. 6,
 Eq. dae_stage) the constraint rows are included in the same Newton system.
 
 Modules

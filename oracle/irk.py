@@ -2,7 +2,7 @@
 
 Follows Sec. 1.1: u_{n+1} = u_n + dt sum_i b_i k_i (Eq. update) with
 0 = M k_i - N(u_n + dt sum_j a_ij k_j, t_n + c_i dt) (Eq. stages).  For the
-vorticity-streamfunction DAE (Sec. 5, Eq. dae_stage) the state is
+vorticity-streamfunction DAE (Sec. 6, Eq. dae_stage) the state is
 (omega, psi), M = diag(I, 0), the second row of N is the constraint G, and
 psi_{n+1} = psi_n + dt sum_i b_i l_i with l_i the psi-stage increments.
 

@@ -13,7 +13,7 @@ Operators (the problem M u' = N(u,t) of Sec. 1.1, Eq. problem):
                          -u Dx v - v Dy v + nu L v)                 (M = I)
                advective central form; Dx, Dy central differences and L the
                5-point Laplacian
-* vsf          state (omega, psi), M = diag(I, 0)  (Sec. 5, Eq. dae):
+* vsf          state (omega, psi), M = diag(I, 0)  (Sec. 6, Eq. dae):
                N_omega = J_A(psi, omega) + nu L omega
                G       = -L psi - omega        (algebraic row, the DAE's G)
                J_A is Arakawa's (1966) energy- and enstrophy-conserving

@@ -1,6 +1,6 @@
 """Vorticity-streamfunction helpers (oracle; test infrastructure).
 
-The constraint of the DAE (Sec. 5, Eq. dae) is G(omega, psi) = -L psi - omega = 0
+The constraint of the DAE (Sec. 6, Eq. dae) is G(omega, psi) = -L psi - omega = 0
 with L the periodic 5-point Laplacian.  On zero-mean fields it is inverted
 exactly with the FFT: the 5-point symbol of -L at wavenumber (kx, ky) is
 (4/h^2)(sin^2(pi kx/n) + sin^2(pi ky/n)); the (0,0) mode is set to zero.

@@ -51,7 +51,7 @@ class IrkStats(C.Structure):
     _fields_ = [
         ("steps", C.c_int), ("newton_its", C.c_int), ("krylov_its", C.c_int),
         ("prec_apps", C.c_int), ("vcycles", C.c_int), ("max_newton_its", C.c_int),
-        ("final_rel_res", C.c_double),
+        ("final_rel_res", C.c_double), ("kernel_launches", C.c_longlong),
     ]
 
     def as_dict(self):

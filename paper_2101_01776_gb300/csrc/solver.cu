@@ -151,12 +151,15 @@ void prof_maybe_flush(irk_handle* h) {
   if (h->cfg.profile && h->ev_used + 64 > (int)h->evpool.size()) prof_harvest(h);
 }
 
+// Wraps the launch(es) of one kernel class: counts them and, when profiling,
+// brackets them with CUDA events and records their algorithmic bytes/flops.
 struct ProfScope {
   irk_handle* h;
   int a, cls;
   double bytes, flops;
-  ProfScope(irk_handle* h_, int cls_, double bytes_, double flops_)
+  ProfScope(irk_handle* h_, int cls_, double bytes_, double flops_, int nlaunch = 1)
       : h(h_), a(-1), cls(cls_), bytes(bytes_), flops(flops_) {
+    h->stats.kernel_launches += nlaunch;
     prof_maybe_flush(h);
     a = prof_begin(h);
   }
@@ -408,7 +411,7 @@ void row_prec(irk_handle* h, double dt, int row, double sigma, const double* in,
     // omega: sigma - dt (J_A(psibar, .) + nu L); psi: (-L) z_psi = z_omega - r_psi / dt
     vcycle(h, row, MG_ADVECTIVE, 1, sigma, dt, dt * h->g.nu, 0, in, out);
     {
-      ProfScope ps(h, P_AXPBY, 24.0 * h->npts, 2.0 * h->npts);
+      ProfScope ps(h, P_AXPBY, 40.0 * h->npts, 3.0 * h->npts, 2);
       launch_axpby(h->tmp2, 1.0, out, 0.0, h->npts, h->st);
       launch_axpby(h->tmp2, -1.0 / dt, in + h->npts, 1.0, h->npts, h->st);
     }
@@ -667,7 +670,7 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
       launch_stage_update(h->L, s, h->tab.QR, h->yhat, h->K, h->st);
     }
     if (h->g.op == IRK_OP_VSF_2D) {
-      ProfScope ps(h, P_MEAN, 16.0 * h->npts * s, 2.0 * h->npts * s);
+      ProfScope ps(h, P_MEAN, 24.0 * h->npts * s, 2.0 * h->npts * s, 2);
       launch_remove_mean(h->npts, s, h->L, h->K + h->npts, h->partials, h->st);
     }
     h->stats.newton_its += 1;
