@@ -149,6 +149,34 @@ irk_status irk_stage_residual(irk_handle* h, double t_n, double dt, const double
 irk_status irk_stage_jacobian_apply(irk_handle* h, double dt, const double* K,
                                     const double* V, double* JV, int on_device);
 
+/* Stage residual without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- a host
+ * whose memory manager owns the device pool and forbids raw allocations, a
+ * latency-critical loop where cudaMalloc/cudaFree would synchronise the device,
+ * or an embedding with a fixed device-memory budget.
+ *
+ * Computes F_i = M k_i - N(u + dt sum_j a_ij k_j) for the autonomous operator
+ * `op` (no forcing) on a periodic n^dim grid of spacing length/n, and
+ * *fnorm = ||F||_2.  A is the s x s Butcher matrix (host, row-major; e.g. from
+ * irk_tableau).  u (ncomp*n^dim), K and F (s*ncomp*n^dim) and fnorm (one
+ * double) are caller-owned DEVICE pointers; the work is enqueued on
+ * cuda_stream (NULL = the legacy default stream) and the call returns without
+ * waiting for it.
+ *
+ * Scratch: a fixed 32 KiB file-scope device array (one partial sum per 256
+ * grid points) that every GPU loading the library keeps until exit.  Limit:
+ * n^dim <= 1,048,576 points (e.g. 1024^2); larger grids return IRK_ERR_NOMEM
+ * with a message on stderr and launch nothing.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it;
+ * make that first call before any stream capture.  Every call shares the
+ * array and leaves its partials there (each call rewrites every slot it
+ * reads, so nothing needs clearing); calls whose work overlaps on the GPU,
+ * e.g. on two streams, race on it.  Bad arguments return IRK_ERR_INVALID. */
+irk_status irk_stage_residual_noalloc(int op, int n, double length, double nu, int stages,
+                                      const double* A, double dt, const double* u,
+                                      const double* K, double* F, double* fnorm,
+                                      void* cuda_stream);
+
 /* Host-only: tableau of `family` with s stages and the standardized real Schur
  * form A0^{-1} = Q0 R0 Q0^T (Sec. 3.1).  A, Q0, R0 are s*s row-major; b, c
  * length s; block_sizes receives the diagonal block sizes (1 or 2) in order,

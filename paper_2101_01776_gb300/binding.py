@@ -92,6 +92,7 @@ def _load():
         "irk_last_error": (C.c_char_p, [vp]),
         "irk_status_string": (C.c_char_p, [i]),
         "irk_destroy": (None, [vp]),
+        "irk_stage_residual_noalloc": (i, [i, i, d, d, i, vp, d, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -105,7 +106,7 @@ EXPORTED = (
     "irk_config_default", "irk_create", "irk_step", "irk_get_state", "irk_set_state",
     "irk_get_stages", "irk_stage_residual", "irk_stage_jacobian_apply", "irk_tableau",
     "irk_kernel_stats", "irk_reset_kernel_stats", "irk_device_bytes", "irk_last_error",
-    "irk_status_string", "irk_destroy",
+    "irk_status_string", "irk_destroy", "irk_stage_residual_noalloc",
 )
 
 
@@ -192,6 +193,26 @@ def irk_stage_jacobian_apply(h, dt: float, K, V, JV):
         raise ValueError("K, V and JV must live in the same memory space")
     _check(LIB.irk_stage_jacobian_apply(h, dt, pk, pv, pj, dk), h)
     return JV
+
+
+def irk_stage_residual_noalloc(op, n: int, length: float, nu: float, stages: int, A, dt: float,
+                               u, K, F, fnorm, stream=None):
+    """Stage residual and ||F|| with no device allocation (all tensors on the
+    device; A a host float64 array).  Enqueued on `stream`; not synchronised."""
+    import numpy as np
+    if isinstance(op, str):
+        op = OP_NAMES[op]
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    ptrs = [_ptr(x) for x in (u, K, F, fnorm)]
+    if not all(dev for _, dev in ptrs):
+        raise ValueError("u, K, F and fnorm must be device tensors")
+    sp = None
+    if stream is not None:
+        sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    st = LIB.irk_stage_residual_noalloc(op, n, length, nu, stages, A.ctypes.data, dt,
+                                        *[p for p, _ in ptrs], sp)
+    if st != IRK_OK:
+        raise IrkError(st, "irk_stage_residual_noalloc rejected the call (see stderr)")
 
 
 def irk_tableau(s: int, family: int = IRK_GAUSS):
