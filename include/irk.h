@@ -93,6 +93,9 @@ typedef struct {
   int mg_coarse_sweeps; /* sweeps on the coarsest level; default 40 */
   double mg_omega;      /* Jacobi damping; 0 = default (0.8 in 2D, 2/3 in 1D) */
   int profile;          /* 1 = time each kernel class with CUDA events */
+  int use_graphs;       /* 1 (default) = replay each block preconditioner L_P
+                           as a CUDA graph captured once per dt; forced off
+                           while profile = 1 (per-launch events) */
 } irk_config;
 
 typedef struct {

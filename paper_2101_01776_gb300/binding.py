@@ -43,7 +43,7 @@ class IrkConfig(C.Structure):
         ("nonlinear_variant", C.c_int), ("gamma_mode", C.c_int),
         ("mg_precision", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
         ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double),
-        ("profile", C.c_int),
+        ("profile", C.c_int), ("use_graphs", C.c_int),
     ]
 
 

@@ -75,6 +75,14 @@ struct irk_handle {
   // FGMRES
   int m = 0;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *partials = nullptr, *dscal = nullptr;
+  // fixed staging of the preconditioner: V_j -> prec_in -> L_P -> prec_out -> Z_j
+  double *prec_in = nullptr, *prec_out = nullptr;
+  // one CUDA graph per diagonal block replaying L_P (valid for graph_dt)
+  cudaGraphExec_t gexec[IRK_MAXS] = {};
+  double graph_dt = 0.0;
+  bool graphs_failed = false;
+  int graph_vcycles[IRK_MAXS] = {};
+  long long graph_launches[IRK_MAXS] = {};
   double* hbuf = nullptr;  // pinned host
   int nparts = 0;
 
@@ -332,16 +340,40 @@ void mg_setup(irk_handle* h) {
   }
 }
 
+// Depth of the V-cycle for shift sigma (the V-cycle-depth autotuning rule).
+// The block operators sigma M - dt L are shift dominated: on level l the
+// Jacobi diagonal is D_l = sigma + 2 dim cdiff / h_l^2, and once sigma >= D_l/2
+// damped Jacobi alone reduces every error mode by at least (1 - omega/2) per
+// sweep, so coarsening further buys nothing.  The cycle stops at the first
+// such level (never above level 1: at least one coarse correction), or at the
+// bottom of the hierarchy for an unshifted operator (the Poisson block).
+int mg_depth(irk_handle* h, double sigma, double cdiff) {
+  if (h->cfg.mg_levels > 0) return std::min(h->cfg.mg_levels, h->nlev);
+  if (!(sigma > 0)) return h->nlev;
+  for (int l = 1; l < h->nlev; ++l) {
+    const double hl = h->lev[l].d.h;
+    const double D = sigma + 2.0 * h->dim * cdiff / (hl * hl);
+    if (sigma >= 0.5 * D) return l + 1;
+  }
+  return h->nlev;
+}
+
 // One V-cycle for A = sigma I + cadv adv(vel_k) - cdiff L on ncomp fields.
-// in/out: double, ncomp * npts_fine.
+// in/out: double, ncomp * npts_fine.  In FP64 storage the input is read in
+// place and the last fine-level sweep writes the output directly.
 void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double cadv, double cdiff,
             int project_mean, const double* in, double* out) {
-  const int nl = h->nlev, prec = h->prec, dim = h->dim;
+  const int nl = mg_depth(h, sigma, cdiff), prec = h->prec, dim = h->dim;
   const double om = h->mg_omega;
   const void* vrow[IRK_MAX_LEVELS];
   for (int l = 0; l < nl; ++l) vrow[l] = (row >= 0) ? h->vel[row][l] : nullptr;
   const long long n0 = (long long)ncomp * h->lev[0].d.npts;
-  {
+  const bool alias = (prec == IRK_MG_FP64);
+  const void* bl[IRK_MAX_LEVELS];
+  for (int l = 0; l < nl; ++l) bl[l] = h->lev[l].b;
+  if (alias) {
+    bl[0] = in;
+  } else {
     ProfScope ps(h, P_MG_CONVERT, n0 * (8.0 + h->esz), 0);
     launch_mg_convert_in(prec, in, h->lev[0].b, n0, h->st);
   }
@@ -357,14 +389,14 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
       const int first = (sw == 0);
       ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, l, first ? 2.0 * ncomp : 3.0 * ncomp + velf),
                    (double)ncomp * lv.d.npts * (first ? 1 : smooth_flops_pp));
-      launch_mg_smooth(prec, dim, kind, lv.d, ncomp, sigma, cadv, cdiff, om, vrow[l], lv.b,
+      launch_mg_smooth(prec, dim, kind, lv.d, ncomp, sigma, cadv, cdiff, om, vrow[l], bl[l],
                        cur[l], first ? cur[l] : alt[l], first, h->st);
       if (!first) std::swap(cur[l], alt[l]);
     }
     {
       ProfScope ps(h, P_MG_RESID, mg_level_bytes(h, l, 3.0 * ncomp + velf),
                    (double)ncomp * lv.d.npts * smooth_flops_pp);
-      launch_mg_residual(prec, dim, kind, lv.d, ncomp, sigma, cadv, cdiff, vrow[l], lv.b, cur[l],
+      launch_mg_residual(prec, dim, kind, lv.d, ncomp, sigma, cadv, cdiff, vrow[l], bl[l], cur[l],
                          lv.r, h->st);
     }
     {
@@ -374,13 +406,35 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     }
   }
   {
-    MGLevel& lc = h->lev[nl - 1];
-    ProfScope ps(h, P_MG_COARSE, mg_level_bytes(h, nl - 1, 2.0 * ncomp + velf),
-                 (double)ncomp * lc.d.npts * smooth_flops_pp * h->cfg.mg_coarse_sweeps);
-    launch_mg_coarse(prec, dim, kind, lc.d, ncomp, sigma, cadv, cdiff, om, h->cfg.mg_coarse_sweeps,
-                     project_mean, vrow[nl - 1], lc.b, lc.w, h->st);
-    cur[nl - 1] = lc.w;
+    const int c = nl - 1;
+    MGLevel& lc = h->lev[c];
+    if (lc.d.npts <= 256) {
+      ProfScope ps(h, P_MG_COARSE, mg_level_bytes(h, c, 2.0 * ncomp + velf),
+                   (double)ncomp * lc.d.npts * smooth_flops_pp * h->cfg.mg_coarse_sweeps);
+      launch_mg_coarse(prec, dim, kind, lc.d, ncomp, sigma, cadv, cdiff, om,
+                       h->cfg.mg_coarse_sweeps, project_mean, vrow[c], bl[c], lc.w, h->st);
+      cur[c] = lc.w;
+    } else {
+      // shift-dominated coarsest level: damped Jacobi to a 2e-2 reduction of
+      // its slowest mode (factor 1 - omega sigma / D), 2..12 sweeps
+      const double hc = lc.d.h;
+      const double D = sigma + 2.0 * dim * cdiff / (hc * hc);
+      const double rho = 1.0 - om * sigma / D;
+      int sweeps = (rho > 0 && rho < 1) ? (int)std::ceil(std::log(2e-2) / std::log(rho)) : 2;
+      sweeps = std::max(2, std::min(sweeps, 12));
+      cur[c] = lc.w;
+      alt[c] = lc.w2;
+      for (int sw = 0; sw < sweeps; ++sw) {
+        const int first = (sw == 0);
+        ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, c, first ? 2.0 * ncomp : 3.0 * ncomp + velf),
+                     (double)ncomp * lc.d.npts * (first ? 1 : smooth_flops_pp));
+        launch_mg_smooth(prec, dim, kind, lc.d, ncomp, sigma, cadv, cdiff, om, vrow[c], bl[c],
+                         cur[c], first ? cur[c] : alt[c], first, h->st);
+        if (!first) std::swap(cur[c], alt[c]);
+      }
+    }
   }
+  bool wrote_out = false;
   for (int l = nl - 2; l >= 0; --l) {
     MGLevel& lv = h->lev[l];
     {
@@ -389,14 +443,17 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
       launch_mg_prolong_add(prec, dim, lv.d, ncomp, cur[l + 1], cur[l], h->st);
     }
     for (int sw = 0; sw < h->cfg.mg_post; ++sw) {
+      const bool last_to_out = alias && l == 0 && sw == h->cfg.mg_post - 1;
+      void* dst = last_to_out ? (void*)out : alt[l];
       ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, l, 3.0 * ncomp + velf),
                    (double)ncomp * lv.d.npts * smooth_flops_pp);
-      launch_mg_smooth(prec, dim, kind, lv.d, ncomp, sigma, cadv, cdiff, om, vrow[l], lv.b,
-                       cur[l], alt[l], 0, h->st);
-      std::swap(cur[l], alt[l]);
+      launch_mg_smooth(prec, dim, kind, lv.d, ncomp, sigma, cadv, cdiff, om, vrow[l], bl[l],
+                       cur[l], dst, 0, h->st);
+      if (last_to_out) wrote_out = true;
+      else std::swap(cur[l], alt[l]);
     }
   }
-  {
+  if (!wrote_out) {
     ProfScope ps(h, P_MG_CONVERT, n0 * (8.0 + h->esz), 0);
     launch_mg_convert_out(prec, cur[0], out, n0, h->st);
   }
@@ -450,6 +507,54 @@ void block_prec(irk_handle* h, double dt, int blk, const double* v, double* z) {
 }
 
 // ---------------------------------------------------------------------------
+// L_P of block blk from prec_in to prec_out.  Its launch sequence is fixed
+// for a given dt (the V-cycle depth, shifts and buffers do not change), so it
+// is captured once into a CUDA graph per block and replayed; a capture that
+// the stream does not allow (e.g. the legacy default stream) falls back to
+// direct launches of the same kernels.
+void drop_graphs(irk_handle* h) {
+  for (int k = 0; k < IRK_MAXS; ++k)
+    if (h->gexec[k]) {
+      cudaGraphExecDestroy(h->gexec[k]);
+      h->gexec[k] = nullptr;
+    }
+}
+
+irk_status apply_prec(irk_handle* h, double dt, int blk) {
+  const bool want = h->cfg.use_graphs && !h->cfg.profile && !h->graphs_failed;
+  if (want && h->graph_dt != dt) {
+    drop_graphs(h);
+    h->graph_dt = dt;
+  }
+  if (want && !h->gexec[blk]) {
+    const irk_stats saved = h->stats;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      block_prec(h, dt, blk, h->prec_in, h->prec_out);
+      e = cudaStreamEndCapture(h->st, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec[blk], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    h->graph_vcycles[blk] = h->stats.vcycles - saved.vcycles;
+    h->graph_launches[blk] = h->stats.kernel_launches - saved.kernel_launches;
+    h->stats = saved;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h->gexec[blk] = nullptr;
+      h->graphs_failed = true;
+    }
+  }
+  if (want && h->gexec[blk]) {
+    CK(cudaGraphLaunch(h->gexec[blk], h->st));
+    h->stats.vcycles += h->graph_vcycles[blk];
+    h->stats.kernel_launches += h->graph_launches[blk];
+    return IRK_OK;
+  }
+  block_prec(h, dt, blk, h->prec_in, h->prec_out);
+  return IRK_OK;
+}
+
 // Flexible GMRES(m), right preconditioned, CGS2 (step a8).
 irk_status fgmres(irk_handle* h, double dt, int blk, const double* b, double* x, double rtol,
                   int* its_out, double* relres_out) {
@@ -478,7 +583,7 @@ irk_status fgmres(irk_handle* h, double dt, int blk, const double* b, double* x,
   while (true) {
     {
       ProfScope ps(h, P_SCALE, 16.0 * Lb, (double)Lb);
-      launch_scale_copy(r, 1.0 / rnorm, h->V, nullptr, Lb, h->st);
+      launch_scale_copy(r, 1.0 / rnorm, h->V, h->prec_in, Lb, h->st);
     }
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = rnorm;
@@ -487,8 +592,9 @@ irk_status fgmres(irk_handle* h, double dt, int blk, const double* b, double* x,
     for (int j = 0; j < m; ++j) {
       double* vj = h->V + (long long)j * ldv;
       double* zj = h->Z + (long long)j * ldv;
-      block_prec(h, dt, blk, vj, zj);
-      block_matvec_dt(h, dt, blk, zj, h->w, nullptr, nullptr);
+      (void)vj;
+      TRY(apply_prec(h, dt, blk));  // prec_in (= V_j) -> prec_out
+      block_matvec_dt(h, dt, blk, h->prec_out, h->w, h->prec_out, zj);  // w = D z_j; Z_j = z_j
       const int nv = j + 1;
       {
         ProfScope ps(h, P_GS_DOT, 8.0 * Lb * (nv + 1), 2.0 * Lb * nv);
@@ -545,7 +651,7 @@ irk_status fgmres(irk_handle* h, double dt, int blk, const double* b, double* x,
       if (res <= target || hn <= 1e-300 || total >= h->cfg.krylov_maxit) break;
       {
         ProfScope ps(h, P_SCALE, 16.0 * Lb, (double)Lb);
-        launch_scale_copy(h->w, 1.0 / hn, h->V + (long long)(j + 1) * ldv, nullptr, Lb, h->st);
+        launch_scale_copy(h->w, 1.0 / hn, h->V + (long long)(j + 1) * ldv, h->prec_in, Lb, h->st);
       }
     }
     // y = H^{-1} g on the leading (jlast+1) block, x += Z y
@@ -787,6 +893,8 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device) {
   add(8 * Lb * (h->m + 1));      // V
   add(8 * Lb * h->m);            // Z
   add(8 * Lb);                   // w
+  add(8 * Lb);                   // prec_in
+  add(8 * Lb);                   // prec_out
   h->nparts = std::max(blas_blocks(Lb) * 70, residual_blocks(g)) + 1024;
   add(8 * (size_t)h->nparts);    // partials
   add(8 * 512);                  // device scalars
@@ -817,6 +925,8 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device) {
   h->V = (double*)take(8 * Lb * (h->m + 1));
   h->Z = (double*)take(8 * Lb * h->m);
   h->w = (double*)take(8 * Lb);
+  h->prec_in = (double*)take(8 * Lb);
+  h->prec_out = (double*)take(8 * Lb);
   h->partials = (double*)take(8 * (size_t)h->nparts);
   h->dscal = (double*)take(8 * 512);
   for (int l = 0; l < h->nlev; ++l) {
@@ -917,6 +1027,7 @@ void irk_config_default(irk_config* c) {
   c->mg_coarse_sweeps = 40;
   c->mg_omega = 0.0;
   c->profile = 0;
+  c->use_graphs = 1;
 }
 
 const char* irk_status_string(irk_status st) {
@@ -1140,6 +1251,8 @@ void irk_destroy(irk_handle* h) {
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& ev : h->evpool) cudaEventDestroy(ev);
   if (h->hbuf) cudaFreeHost(h->hbuf);
+  for (int k = 0; k < IRK_MAXS; ++k)
+    if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
   if (h->arena) cudaFree(h->arena);
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
   delete h;

@@ -274,3 +274,18 @@ def test_checkpoint_resume_and_determinism_bit_equal(B):
         resumed = c.state().copy()
     np.testing.assert_array_equal(full, again)
     np.testing.assert_array_equal(full, resumed)
+
+
+def test_graph_replay_is_bit_identical_to_direct_launches(B):
+    """The CUDA-graph replay of L_P runs the same kernels in the same order."""
+    n, s = 64, 3
+    u0 = workloads.random_fourier_2d(n, seed=9)
+    stream = torch.cuda.Stream()
+    outs = []
+    for graphs in (0, 1):
+        with B.IrkSolver(torch.from_numpy(u0).cuda(), stream=stream, op="burgers2d", n=n,
+                         stages=s, nu=5e-3, use_graphs=graphs) as sol:
+            st = sol.step(0.0, 2e-3, 3)
+            outs.append((sol.state().copy(), st.krylov_its, st.vcycles))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1:] == outs[1][1:]
