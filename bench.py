@@ -118,19 +118,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline_leg(stages: int) -> dict:
+def cpu_baseline_leg(stages: int, save_path: str = "") -> dict:
     """The oracle, as it stands, on one IRK step of the same workload, run in
-    a fresh interpreter limited to one BLAS/OpenMP thread."""
+    a fresh interpreter limited to one BLAS/OpenMP thread.  The oracle's
+    u_{n+1} is saved to save_path (if given) for the precision report."""
     code = (
         "import time, json, sys; sys.path.insert(0, %r)\n"
+        "import numpy as np\n"
         "import workloads\n"
         "from oracle import irk\n"
         "from oracle.operators import Problem\n"
         "p = Problem('burgers2d', %d, %r)\n"
         "u0 = workloads.random_fourier_2d(%d, seed=%d)\n"
-        "t = time.perf_counter(); irk.step(p, %d, u0, 0.0, %r, linear='gmres')\n"
-        "print(json.dumps({'sec': time.perf_counter() - t}))\n"
-    ) % (ROOT, N, NU, N, SEED, stages, DT)
+        "t = time.perf_counter(); u1, K, info = irk.step(p, %d, u0, 0.0, %r, linear='gmres')\n"
+        "sec = time.perf_counter() - t\n"
+        "if %r: np.save(%r, u1)\n"
+        "print(json.dumps({'sec': sec}))\n"
+    ) % (ROOT, N, NU, N, SEED, stages, DT, bool(save_path), save_path)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                        timeout=600)
@@ -187,6 +191,7 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world):
+    global np
     import numpy as np
     import torch
     import workloads
@@ -361,18 +366,77 @@ def run_ours(args, rank, world):
             extra[label] = {"steps_per_s": 1e3 / (sum(ms2) / len(ms2)),
                             "krylov_its_per_step": tot2["krylov_its"] / 3,
                             "newton_its_per_step": tot2["newton_its"] / 3}
+        extra["vsf1024_gauss5"] = vsf_leg(B, torch, dev, stream, flush, timed_steps)
         line["variants"] = extra
+        # ---- precision report: one step from u0 per V-cycle storage precision
+        prec_u = {}
+        for prec, name in ((0, "fp64"), (1, "fp32"), (2, "bf16")):
+            h = make(args.stages, prec, 0)
+            st = B.irk_step(h, 0.0, DT, 1)
+            out = torch.empty(u0.shape, dtype=torch.float64, device=dev)
+            B.irk_get_state(h, out)
+            B.irk_destroy(h)
+            prec_u[name] = (out.cpu().numpy(), st)
         if world == 1:
+            import tempfile
+            tmp = os.path.join(tempfile.mkdtemp(), "oracle_u1.npy")
             try:
-                line["cpu_baseline"] = cpu_baseline_leg(args.stages)
+                line["cpu_baseline"] = cpu_baseline_leg(args.stages, tmp)
+                ref = np.load(tmp)
             except Exception as e:  # report, never hide
                 line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                         "sample": f"failed: {e!r}"[:200]}
+                ref = None
+            rep = {}
+            for name, (u1, st) in prec_u.items():
+                rep[name] = {"krylov_its": st.krylov_its, "newton_its": st.newton_its,
+                             "vcycles": st.vcycles, "final_rel_res": st.final_rel_res,
+                             "rel_l2_err_vs_oracle": (float(np.linalg.norm(u1 - ref) / np.linalg.norm(ref))
+                                                      if ref is not None else None)}
+            line["precision"] = {"workload": "one IRK step from u0 (512^2, Gauss s=%d)" % args.stages,
+                                 "per_precision": rep}
     elif "e2e" not in line:
         line["e2e"] = None
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def vsf_leg(B, torch, dev, stream, flush, timed_steps):
+    """Vorticity-streamfunction DAE, double shear layer 1024^2, Re=1000, Gauss
+    s=5, dt=5e-3, FP64 (and FP32 V-cycle): steps/s over 2 steps after 1."""
+    import math
+    import workloads
+    n, nu, dt = 1024, 1e-3, 5e-3
+    w0 = workloads.double_shear_layer_vorticity(n, seed=2)
+    u0 = np.zeros((2, n, n))
+    u0[0] = w0
+    out = {}
+    for prec in (0, 1):
+        cfg = B.irk_config_default(op="vsf", n=n, nu=nu, stages=5, length=2 * math.pi,
+                                   mg_precision=prec)
+        h = B.irk_create(cfg, torch.from_numpy(u0).to(dev), stream)
+        t, ms = 0.0, []
+        st = B.irk_step(h, t, dt, 1)
+        t += dt
+        kry = newt = 0
+        for _ in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = B.irk_step(h, t, dt, 1)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+            kry += st.krylov_its
+            newt += st.newton_its
+            t += dt
+        B.irk_destroy(h)
+        out["fp64" if prec == 0 else "mg_fp32"] = {
+            "steps_per_s": 1e3 / (sum(ms) / len(ms)), "krylov_its_per_step": kry / 2,
+            "newton_its_per_step": newt / 2}
+    return out
 
 
 def read_traffic(kernel_class: str):

@@ -60,29 +60,52 @@ __device__ __forceinline__ LvIdx lv_nbr(const MGLevelDesc& lv, int p) {
   return r;
 }
 
-// (A w)(p) for one component; w points at that component's field.
+// Stencil of A at one point in coefficient form, A w = D w_c + sum_k c_k w_k
+// over the neighbours k (E, W, N, S).  The four coefficients depend only on
+// the velocity, so they are formed once per point and shared by all
+// components; the Jacobi update then costs one FMA per neighbour.
+template <typename TC>
+struct Coef4 {
+  TC e, w, n, s;
+};
+
 template <typename TS, int DIM, int KIND>
-__device__ __forceinline__ typename Cmp<TS>::T apply_A(const LvIdx& q, const TS* __restrict__ w,
-                                                       const TS* __restrict__ vel, int npts,
-                                                       typename Cmp<TS>::T sigma,
-                                                       typename Cmp<TS>::T cadv,
-                                                       typename Cmp<TS>::T cdiff,
-                                                       typename Cmp<TS>::T inv2h,
-                                                       typename Cmp<TS>::T invh2) {
+__device__ __forceinline__ Coef4<typename Cmp<TS>::T> stencil_coef(
+    const LvIdx& q, const TS* __restrict__ vel, int npts, typename Cmp<TS>::T alpha,
+    typename Cmp<TS>::T beta) {
+  // alpha = cadv / (2h), beta = -cdiff / h^2 (off-diagonal diffusion weight)
   typedef typename Cmp<TS>::T TC;
-  const TC wc = ldv(w + q.c), we = ldv(w + q.e), ww = ldv(w + q.w);
-  TC lap, adv = 0;
-  if (DIM == 1) {
-    lap = (we + ww - TC(2) * wc) * invh2;
-  } else {
-    const TC wn = ldv(w + q.n), ws = ldv(w + q.s);
-    lap = (we + ww + wn + ws - TC(4) * wc) * invh2;
-    if (KIND == MG_ADVECTIVE)
-      adv = (ldv(vel + q.c) * (we - ww) + ldv(vel + npts + q.c) * (wn - ws)) * inv2h;
+  Coef4<TC> c;
+  c.e = c.w = c.n = c.s = beta;
+  if (KIND == MG_ADVECTIVE) {
+    const TC ax = ldv(vel + q.c);
+    c.e = fma(alpha, ax, beta);
+    c.w = fma(-alpha, ax, beta);
+    if (DIM == 2) {
+      const TC ay = ldv(vel + npts + q.c);
+      c.n = fma(alpha, ay, beta);
+      c.s = fma(-alpha, ay, beta);
+    }
+  } else if (KIND == MG_CONSERVATIVE_1D) {
+    c.e = fma(alpha, ldv(vel + q.e), beta);
+    c.w = fma(-alpha, ldv(vel + q.w), beta);
   }
-  if (DIM == 1 && KIND == MG_ADVECTIVE) adv = ldv(vel + q.c) * (we - ww) * inv2h;
-  if (KIND == MG_CONSERVATIVE_1D) adv = (ldv(vel + q.e) * we - ldv(vel + q.w) * ww) * inv2h;
-  return sigma * wc + cadv * adv - cdiff * lap;
+  return c;
+}
+
+// b - sum_k c_k w_k (the off-diagonal part of b - A w)
+template <typename TS, int DIM>
+__device__ __forceinline__ typename Cmp<TS>::T rhs_minus_offdiag(
+    const LvIdx& q, const TS* __restrict__ w, const Coef4<typename Cmp<TS>::T>& c,
+    typename Cmp<TS>::T b) {
+  typename Cmp<TS>::T t = b;
+  t = fma(-c.e, ldv(w + q.e), t);
+  t = fma(-c.w, ldv(w + q.w), t);
+  if (DIM == 2) {
+    t = fma(-c.n, ldv(w + q.n), t);
+    t = fma(-c.s, ldv(w + q.s), t);
+  }
+  return t;
 }
 
 template <typename TS, int DIM, int KIND>
@@ -93,23 +116,25 @@ __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, do
                                                    const TS* __restrict__ w_in,
                                                    TS* __restrict__ w_out, int first) {
   typedef typename Cmp<TS>::T TC;
-  const TC sigma = sigma_, cadv = cadv_, cdiff = cdiff_, omega = omega_;
-  const TC inv2h = TC(0.5 / lv.h), invh2 = TC(1.0 / (lv.h * lv.h));
-  const TC dinv = omega / (sigma + cdiff * TC(2 * DIM) * invh2);
+  const double invh2d = 1.0 / (lv.h * lv.h);
+  const double D = sigma_ + cdiff_ * (2 * DIM) * invh2d;
+  const TC alpha = TC(cadv_ * 0.5 / lv.h), beta = TC(-cdiff_ * invh2d);
+  const TC dinv = TC(omega_ / D), keep = TC(1.0 - omega_);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lv.npts; p += gridDim.x * blockDim.x) {
     const LvIdx q = lv_nbr<DIM>(lv, p);
+    if (first) {
+      for (int c = 0; c < ncomp; ++c) {
+        const long long off = (long long)c * lv.npts;
+        stv<TS, TC>(w_out + off + p, dinv * ldv(b + off + p));
+      }
+      continue;
+    }
+    const Coef4<TC> cf = stencil_coef<TS, DIM, KIND>(q, vel, lv.npts, alpha, beta);
     for (int c = 0; c < ncomp; ++c) {
       const long long off = (long long)c * lv.npts;
-      const TC bc = ldv(b + off + p);
-      TC out;
-      if (first) {
-        out = dinv * bc;
-      } else {
-        const TC aw = apply_A<TS, DIM, KIND>(q, w_in + off, vel, lv.npts, sigma, cadv, cdiff,
-                                             inv2h, invh2);
-        out = ldv(w_in + off + p) + dinv * (bc - aw);
-      }
-      stv<TS, TC>(w_out + off + p, out);
+      const TC t = rhs_minus_offdiag<TS, DIM>(q, w_in + off, cf, ldv(b + off + p));
+      // w + omega/D (b - D w - sum c w) = (1 - omega) w + omega/D (b - sum c w)
+      stv<TS, TC>(w_out + off + p, fma(dinv, t, keep * ldv(w_in + off + p)));
     }
   }
 }
@@ -121,15 +146,16 @@ __global__ void __launch_bounds__(256) k_mg_residual(MGLevelDesc lv, int ncomp, 
                                                      const TS* __restrict__ b,
                                                      const TS* __restrict__ w, TS* __restrict__ r) {
   typedef typename Cmp<TS>::T TC;
-  const TC sigma = sigma_, cadv = cadv_, cdiff = cdiff_;
-  const TC inv2h = TC(0.5 / lv.h), invh2 = TC(1.0 / (lv.h * lv.h));
+  const double invh2d = 1.0 / (lv.h * lv.h);
+  const TC D = TC(sigma_ + cdiff_ * (2 * DIM) * invh2d);
+  const TC alpha = TC(cadv_ * 0.5 / lv.h), beta = TC(-cdiff_ * invh2d);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lv.npts; p += gridDim.x * blockDim.x) {
     const LvIdx q = lv_nbr<DIM>(lv, p);
+    const Coef4<TC> cf = stencil_coef<TS, DIM, KIND>(q, vel, lv.npts, alpha, beta);
     for (int c = 0; c < ncomp; ++c) {
       const long long off = (long long)c * lv.npts;
-      const TC aw = apply_A<TS, DIM, KIND>(q, w + off, vel, lv.npts, sigma, cadv, cdiff, inv2h,
-                                           invh2);
-      stv<TS, TC>(r + off + p, ldv(b + off + p) - aw);
+      const TC t = rhs_minus_offdiag<TS, DIM>(q, w + off, cf, ldv(b + off + p));
+      stv<TS, TC>(r + off + p, fma(-D, ldv(w + off + p), t));
     }
   }
 }

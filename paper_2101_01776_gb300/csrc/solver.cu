@@ -324,22 +324,6 @@ double mg_level_bytes(irk_handle* h, int l, double fields) {
   return fields * h->lev[l].d.npts * (double)h->esz;
 }
 
-void mg_setup(irk_handle* h) {
-  // coefficient (velocity) hierarchy of every diagonal row from combo (k,k)
-  if (h->g.op == IRK_OP_DIFFUSION_1D) return;
-  for (int k = 0; k < h->s; ++k) {
-    {
-      ProfScope ps(h, P_MG_SETUP, 8.0 * h->L + mg_level_bytes(h, 0, h->dim), 0);
-      launch_velocity_from_combo(h->g, combo_ptr(h, k, k), h->vel[k][0], h->prec, h->st);
-    }
-    for (int l = 0; l + 1 < h->nlev; ++l) {
-      ProfScope ps(h, P_MG_SETUP, mg_level_bytes(h, l, h->dim) * 1.25, 0);
-      launch_mg_restrict(h->prec, h->dim, h->lev[l].d, h->dim, h->vel[k][l], h->vel[k][l + 1],
-                         h->st);
-    }
-  }
-}
-
 // Depth of the V-cycle for shift sigma (the V-cycle-depth autotuning rule).
 // The block operators sigma M - dt L are shift dominated: on level l the
 // Jacobi diagonal is D_l = sigma + 2 dim cdiff / h_l^2, and once sigma >= D_l/2
@@ -356,6 +340,32 @@ int mg_depth(irk_handle* h, double sigma, double cdiff) {
     if (sigma >= 0.5 * D) return l + 1;
   }
   return h->nlev;
+}
+
+// Shift of block row r in L_P: eta on the first row of a block, gamma (gamma*
+// or eta) on the second (Eq. Lprec, Eq. gamma*).
+double row_shift(irk_handle* h, int r) {
+  const int blk = h->blk_of[r];
+  if (r == h->tab.bstart[blk]) return h->tab.eta[blk];
+  return (h->cfg.gamma_mode == 1) ? h->tab.eta[blk] : h->tab.gamma_star[blk];
+}
+
+// Coefficient (velocity) hierarchy of every diagonal row from its combined
+// field (k,k), restricted down to the depth that row's V-cycle reaches.
+void mg_setup(irk_handle* h, double dt) {
+  if (h->g.op == IRK_OP_DIFFUSION_1D) return;
+  for (int k = 0; k < h->s; ++k) {
+    const int depth = mg_depth(h, row_shift(h, k), dt * h->g.nu);
+    {
+      ProfScope ps(h, P_MG_SETUP, 8.0 * h->L + mg_level_bytes(h, 0, h->dim), 0);
+      launch_velocity_from_combo(h->g, combo_ptr(h, k, k), h->vel[k][0], h->prec, h->st);
+    }
+    for (int l = 0; l + 1 < depth; ++l) {
+      ProfScope ps(h, P_MG_SETUP, mg_level_bytes(h, l, h->dim) * 1.25, 0);
+      launch_mg_restrict(h->prec, h->dim, h->lev[l].d, h->dim, h->vel[k][l], h->vel[k][l + 1],
+                         h->st);
+    }
+  }
 }
 
 // One V-cycle for A = sigma I + cadv adv(vel_k) - cdiff L on ncomp fields.
@@ -759,7 +769,7 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
     eta_lin = std::max(eta_lin, 0.2 * h->cfg.newton_rtol / rel);
     eta_lin = std::max(eta_lin, 1e-13);
     prev = fn;
-    mg_setup(h);
+    mg_setup(h, dt);
     for (int blk = h->tab.nblk - 1; blk >= 0; --blk) {
       const int a0 = h->tab.bstart[blk];
       const double* z = h->rhs + (long long)a0 * h->L;

@@ -289,3 +289,32 @@ def test_graph_replay_is_bit_identical_to_direct_launches(B):
             outs.append((sol.state().copy(), st.krylov_its, st.vcycles))
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
     assert outs[0][1:] == outs[1][1:]
+
+
+def test_vsf_medium_128_gauss5_parity(B):
+    """Vorticity-streamfunction DAE, 128^2, Gauss s=5 (order 10), dt=5e-3, Re=1000."""
+    per_step, whole, infos = run_parity(B, "vsf", 128, 5, 1e-3, 5e-3, 2, seed=2)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
+
+
+def test_full_size_vsf_1024_gauss5_one_step(B):
+    """Config [2] at full size (1024^2, s=5, dt=5e-3, Re=1000): the GPU stage
+    vectors satisfy the oracle's DAE stage equations (Eq. dae_stage) to the
+    Newton tolerance, the update matches Eq. update, the constraint -L psi =
+    omega holds after the step and the mean of omega is conserved."""
+    n, s, nu, dt = 1024, 5, 1e-3, 5e-3
+    p = Problem("vsf", n, nu, 2 * math.pi)
+    st0 = ovsf.initial_state(workloads.double_shear_layer_vorticity(n, seed=2), p.h)
+    with B.IrkSolver(st0.copy(), op="vsf", n=n, stages=s, nu=nu, length=2 * math.pi) as sol:
+        sol.set_state(st0)
+        info = sol.step(0.0, dt, 1)
+        u1 = sol.state()
+        K = sol.stages()
+    A, b, c = tab.gauss(s)
+    F = orc.stage_residual(p, st0, K, 0.0, dt, A, c)
+    F0 = orc.stage_residual(p, st0, np.zeros_like(K), 0.0, dt, A, c)
+    assert np.linalg.norm(F) <= 2e-10 * np.linalg.norm(F0), info.as_dict()
+    assert rel(u1, st0 + dt * np.tensordot(b, K, axes=(0, 0))) <= 1e-14
+    g = p.N(u1)[1]
+    assert np.abs(g).max() <= 1e-9 * np.abs(u1[0]).max()
+    assert abs(u1[0].mean()) <= 1e-12 * np.abs(u1[0]).max()
