@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--stages", type=int, default=2)
     ap.add_argument("--mg-precision", type=int, default=0)
     ap.add_argument("--no-extras", action="store_true", help="skip the s=3 / FP32 / e2e / CPU legs")
+    ap.add_argument("--serving-requests", type=int, default=128,
+                    help="requests of the 512-request serving mix to run (0 = skip)")
+    ap.add_argument("--serving-rate", type=float, default=200.0, help="Poisson arrival rate, req/s")
     return ap.parse_args()
 
 
@@ -368,6 +371,8 @@ def run_ours(args, rank, world):
                             "newton_its_per_step": tot2["newton_its"] / 3}
         extra["vsf1024_gauss5"] = vsf_leg(B, torch, dev, stream, flush, timed_steps)
         line["variants"] = extra
+        if args.serving_requests > 0:
+            line["serving"] = serving_leg(B, args.serving_requests, args.serving_rate)
         # ---- precision report: one step from u0 per V-cycle storage precision
         prec_u = {}
         for prec, name in ((0, "fp64"), (1, "fp32"), (2, "bf16")):
@@ -437,6 +442,48 @@ def vsf_leg(B, torch, dev, stream, flush, timed_steps):
             "steps_per_s": 1e3 / (sum(ms) / len(ms)), "krylov_its_per_step": kry / 2,
             "newton_its_per_step": newt / 2}
     return out
+
+
+def serving_leg(B, count, rate, slots=16, budget_gib=24):
+    """Config [4]: the first `count` requests of the seeded 512-request mix
+    (2D Burgers, grid from {64,128,256,512}^2, nu log-uniform in [1e-3,1e-1],
+    Gauss s in {2,3,4}, random-Fourier initial field seeded by request id,
+    20 steps at dt=1e-3), Poisson arrivals at `rate` req/s, served by the
+    continuous-batching runtime with `slots` slots and an HBM budget."""
+    import threading
+    import workloads
+    reqs = workloads.serving_requests(512, seed=4)[:count]
+    u0s = {}
+    for r in reqs:
+        u0s[r["id"]] = workloads.random_fourier_2d(r["n"], seed=r["seed"])
+    srv = B.irk_server_create(slots, budget_gib << 30)
+    ids = [None] * len(reqs)
+    rng = np.random.default_rng(5)
+    gaps = rng.exponential(1.0 / rate, size=len(reqs))
+
+    def producer():
+        for k, r in enumerate(reqs):
+            cfg = B.irk_config_default(op="burgers2d", n=r["n"], stages=r["s"], nu=r["nu"])
+            ids[k] = B.irk_server_submit(srv, cfg, u0s[r["id"]], 0.0, 1e-3, 20)
+            time.sleep(float(gaps[k]))
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    failed = 0
+    for k, r in enumerate(reqs):
+        try:
+            B.irk_server_wait(srv, ids[k], u0s[r["id"]].shape, 20)
+        except B.IrkError:
+            failed += 1
+    st = B.irk_server_stats_get(srv)
+    B.irk_server_destroy(srv)
+    return {"requests": count, "of_mix": 512, "arrival_rate_per_s": rate, "slots": slots,
+            "budget_GiB": budget_gib, "failed": failed, "steps": st["steps"],
+            "steps_per_s": st["steps_per_s"], "wall_s": st["wall_s"],
+            "p50_step_ms": st["p50_step_ms"], "p99_step_ms": st["p99_step_ms"],
+            "p50_request_ms": st["p50_request_ms"], "p99_request_ms": st["p99_request_ms"],
+            "p50_queue_ms": st["p50_queue_ms"], "p99_queue_ms": st["p99_queue_ms"],
+            "peak_active": st["peak_active"], "peak_GiB": st["peak_bytes"] / 2 ** 30}
 
 
 def read_traffic(kernel_class: str):

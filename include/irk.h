@@ -130,6 +130,17 @@ void irk_config_default(irk_config* cfg);
 irk_status irk_create(const irk_config* cfg, const double* u0, int u0_on_device,
                       void* cuda_stream, irk_handle** out);
 
+/* Device bytes the arena of a handle for cfg needs (host-only, no GPU);
+ * 0 if cfg is invalid. */
+size_t irk_config_device_bytes(const irk_config* cfg);
+
+/* As irk_create, but the handle carves its arena out of caller-owned device
+ * memory (256-byte aligned, at least irk_config_device_bytes(cfg) bytes) and
+ * never frees it.  Used by memory managers that own the device pool (the
+ * serving runtime below). */
+irk_status irk_create_in(const irk_config* cfg, const double* u0, int u0_on_device,
+                         void* cuda_stream, void* arena, size_t arena_bytes, irk_handle** out);
+
 /* Advance nsteps steps of size dt from time t_n (Algorithm 1 per step).
  * stats may be NULL. */
 irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats* stats);

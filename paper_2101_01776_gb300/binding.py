@@ -63,6 +63,21 @@ class IrkKernelStat(C.Structure):
                 ("bytes", C.c_double), ("flops", C.c_double)]
 
 
+class IrkServerStats(C.Structure):
+    _fields_ = [
+        ("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
+        ("steps", C.c_longlong), ("wall_s", C.c_double), ("steps_per_s", C.c_double),
+        ("p50_step_ms", C.c_double), ("p99_step_ms", C.c_double), ("max_step_ms", C.c_double),
+        ("p50_request_ms", C.c_double), ("p99_request_ms", C.c_double),
+        ("p50_queue_ms", C.c_double), ("p99_queue_ms", C.c_double),
+        ("peak_active", C.c_int), ("slots", C.c_int),
+        ("budget_bytes", C.c_size_t), ("peak_bytes", C.c_size_t),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class IrkError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{status_string(status)}: {msg}")
@@ -93,6 +108,13 @@ def _load():
         "irk_status_string": (C.c_char_p, [i]),
         "irk_destroy": (None, [vp]),
         "irk_stage_residual_noalloc": (i, [i, i, d, d, i, vp, d, vp, vp, vp, vp, vp]),
+        "irk_config_device_bytes": (sz, [P(IrkConfig)]),
+        "irk_create_in": (i, [P(IrkConfig), vp, i, vp, vp, sz, P(vp)]),
+        "irk_server_create": (i, [i, sz, P(vp)]),
+        "irk_server_submit": (i, [vp, P(IrkConfig), vp, d, d, i, P(C.c_longlong)]),
+        "irk_server_wait": (i, [vp, C.c_longlong, vp, P(IrkStats), vp]),
+        "irk_server_stats_get": (i, [vp, P(IrkServerStats)]),
+        "irk_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -107,6 +129,8 @@ EXPORTED = (
     "irk_get_stages", "irk_stage_residual", "irk_stage_jacobian_apply", "irk_tableau",
     "irk_kernel_stats", "irk_reset_kernel_stats", "irk_device_bytes", "irk_last_error",
     "irk_status_string", "irk_destroy", "irk_stage_residual_noalloc",
+    "irk_config_device_bytes", "irk_create_in", "irk_server_create", "irk_server_submit",
+    "irk_server_wait", "irk_server_stats_get", "irk_server_destroy",
 )
 
 
@@ -213,6 +237,57 @@ def irk_stage_residual_noalloc(op, n: int, length: float, nu: float, stages: int
                                         *[p for p, _ in ptrs], sp)
     if st != IRK_OK:
         raise IrkError(st, "irk_stage_residual_noalloc rejected the call (see stderr)")
+
+
+def irk_config_device_bytes(cfg: IrkConfig) -> int:
+    return int(LIB.irk_config_device_bytes(C.byref(cfg)))
+
+
+def irk_create_in(cfg: IrkConfig, u0, arena_ptr: int, arena_bytes: int, stream=None):
+    h = C.c_void_p()
+    p, dev = _ptr(u0)
+    sp = None
+    if stream is not None:
+        sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(LIB.irk_create_in(C.byref(cfg), p, dev, sp, C.c_void_p(arena_ptr), arena_bytes,
+                             C.byref(h)))
+    return h
+
+
+def irk_server_create(slots: int, budget_bytes: int = 0):
+    s = C.c_void_p()
+    _check(LIB.irk_server_create(slots, budget_bytes, C.byref(s)))
+    return s
+
+
+def irk_server_submit(s, cfg: IrkConfig, u0, t0: float, dt: float, nsteps: int) -> int:
+    import numpy as np
+    u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    rid = C.c_longlong()
+    _check(LIB.irk_server_submit(s, C.byref(cfg), u0.ctypes.data, t0, dt, nsteps, C.byref(rid)))
+    return rid.value
+
+
+def irk_server_wait(s, rid: int, shape, nsteps: int):
+    """(final state, IrkStats, per-step wall ms) of request rid (host arrays)."""
+    import numpy as np
+    out = np.empty(shape)
+    st = IrkStats()
+    ms = np.empty(max(nsteps, 1))
+    code = LIB.irk_server_wait(s, rid, out.ctypes.data, C.byref(st), ms.ctypes.data)
+    if code != IRK_OK:
+        raise IrkError(code, f"request {rid} failed")
+    return out, st, ms[:nsteps]
+
+
+def irk_server_stats_get(s) -> dict:
+    o = IrkServerStats()
+    _check(LIB.irk_server_stats_get(s, C.byref(o)))
+    return o.as_dict()
+
+
+def irk_server_destroy(s):
+    LIB.irk_server_destroy(s)
 
 
 def irk_tableau(s: int, family: int = IRK_GAUSS):

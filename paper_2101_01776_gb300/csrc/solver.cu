@@ -64,6 +64,9 @@ struct irk_handle {
 
   char* arena = nullptr;
   size_t arena_bytes = 0, arena_used = 0;
+  bool own_arena = true;
+  void* ext_arena = nullptr;  // caller-owned arena (irk_create_in)
+  size_t ext_bytes = 0;
 
   double *u = nullptr, *u_save = nullptr, *K = nullptr, *Y = nullptr, *rhs = nullptr,
          *yhat = nullptr, *combos = nullptr, *zbuf = nullptr, *tmp = nullptr, *tmp2 = nullptr;
@@ -824,7 +827,10 @@ irk_status validate(const irk_config* c, std::string& err) {
   return IRK_OK;
 }
 
-irk_status build(irk_handle* h, const double* u0, int u0_on_device) {
+// Plan the solver for h->cfg (tableau, grid, combined fields, MG levels,
+// arena size); unless plan_only, then place the arena (the caller's when
+// h->ext_arena is set, else one cudaMalloc), carve it and load u0.
+irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_only = false) {
   const irk_config& c = h->cfg;
   char ebuf[256] = {0};
   if (build_tableau(c.family, c.stages, &h->tab, ebuf, sizeof ebuf)) { h->err = ebuf; return IRK_ERR_INVALID; }
@@ -914,12 +920,23 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device) {
     for (int k = 0; k < s; ++k) add(f * h->dim);
   }
   h->arena_bytes = bytes + 4096;
-  cudaError_t e = cudaMalloc((void**)&h->arena, h->arena_bytes);
-  if (e != cudaSuccess) {
-    h->arena = nullptr;
-    h->err = std::string("device arena allocation failed: ") + cudaGetErrorString(e);
-    cudaGetLastError();
-    return IRK_ERR_NOMEM;
+  if (plan_only) return IRK_OK;
+  if (h->ext_arena) {
+    if (h->ext_bytes < h->arena_bytes) {
+      h->err = "caller-provided arena is smaller than irk_config_device_bytes()";
+      return IRK_ERR_NOMEM;
+    }
+    h->arena = (char*)h->ext_arena;
+    h->arena_bytes = h->ext_bytes;
+    h->own_arena = false;
+  } else {
+    cudaError_t e = cudaMalloc((void**)&h->arena, h->arena_bytes);
+    if (e != cudaSuccess) {
+      h->arena = nullptr;
+      h->err = std::string("device arena allocation failed: ") + cudaGetErrorString(e);
+      cudaGetLastError();
+      return IRK_ERR_NOMEM;
+    }
   }
   auto take = [&](size_t b) { return arena_take(h, b); };
   h->u = (double*)take(8 * h->L);
@@ -1075,8 +1092,9 @@ irk_status irk_tableau(int family, int s, double* A, double* b, double* c, doubl
   return IRK_OK;
 }
 
-irk_status irk_create(const irk_config* cfg, const double* u0, int u0_on_device, void* cuda_stream,
-                      irk_handle** out) {
+static irk_status create_impl(const irk_config* cfg, const double* u0, int u0_on_device,
+                              void* cuda_stream, void* arena, size_t arena_bytes,
+                              irk_handle** out) {
   if (!out) { g_create_error = "null output handle"; return IRK_ERR_INVALID; }
   *out = nullptr;
   std::string verr;
@@ -1092,6 +1110,8 @@ irk_status irk_create(const irk_config* cfg, const double* u0, int u0_on_device,
   irk_handle* h = new (std::nothrow) irk_handle();
   if (!h) { g_create_error = "host allocation failed"; return IRK_ERR_NOMEM; }
   h->cfg = *cfg;
+  h->ext_arena = arena;
+  h->ext_bytes = arena_bytes;
   memset(&h->stats, 0, sizeof(h->stats));
   cudaGetDevice(&h->device);
   if (cuda_stream) {
@@ -1112,6 +1132,30 @@ irk_status irk_create(const irk_config* cfg, const double* u0, int u0_on_device,
   }
   *out = h;
   return IRK_OK;
+}
+
+irk_status irk_create(const irk_config* cfg, const double* u0, int u0_on_device, void* cuda_stream,
+                      irk_handle** out) {
+  return create_impl(cfg, u0, u0_on_device, cuda_stream, nullptr, 0, out);
+}
+
+irk_status irk_create_in(const irk_config* cfg, const double* u0, int u0_on_device,
+                         void* cuda_stream, void* arena, size_t arena_bytes, irk_handle** out) {
+  if (!arena) { g_create_error = "null arena"; return IRK_ERR_INVALID; }
+  if ((reinterpret_cast<uintptr_t>(arena) & 255) != 0) {
+    g_create_error = "arena must be 256-byte aligned";
+    return IRK_ERR_INVALID;
+  }
+  return create_impl(cfg, u0, u0_on_device, cuda_stream, arena, arena_bytes, out);
+}
+
+size_t irk_config_device_bytes(const irk_config* cfg) {
+  std::string verr;
+  if (validate(cfg, verr) != IRK_OK) return 0;
+  irk_handle tmp;
+  tmp.cfg = *cfg;
+  if (build(&tmp, nullptr, 0, true) != IRK_OK) return 0;
+  return tmp.arena_bytes;
 }
 
 irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats* stats) {
@@ -1263,7 +1307,7 @@ void irk_destroy(irk_handle* h) {
   if (h->hbuf) cudaFreeHost(h->hbuf);
   for (int k = 0; k < IRK_MAXS; ++k)
     if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
-  if (h->arena) cudaFree(h->arena);
+  if (h->arena && h->own_arena) cudaFree(h->arena);
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
   delete h;
 }

@@ -24,9 +24,13 @@ def B():
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "irk.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = set(re.findall(r"\b(irk_[a-z_]+)\s*\(", text))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if not f.endswith(".h"):
+            continue
+        text = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+        names |= set(re.findall(r"\b(irk_[a-z_]+)\s*\(", text))
     return sorted(names)
 
 
@@ -73,6 +77,14 @@ def test_gauss2_schur_basis_is_identity(B):
     standardized form, so the block is exactly Newton (P-hat block diagonal)."""
     t = B.irk_tableau(2)
     np.testing.assert_array_equal(t["Q0"], np.eye(2))
+
+
+def test_device_bytes_is_host_only_and_grows_with_the_problem(B):
+    small = B.irk_config_default(op="burgers2d", n=64, stages=2)
+    big = B.irk_config_default(op="burgers2d", n=256, stages=4)
+    a, b = B.irk_config_device_bytes(small), B.irk_config_device_bytes(big)
+    assert 0 < a < b
+    assert B.irk_config_device_bytes(B.irk_config_default(stages=9)) == 0
 
 
 def test_invalid_configs_rejected_before_device(B):
