@@ -15,7 +15,7 @@ static constexpr int kChunk = 8;  // inner products accumulated per sweep
 
 int blas_blocks(long long L) {
   long long b = (L + IRK_BLAS_THREADS * 4 - 1) / (IRK_BLAS_THREADS * 4);
-  if (b > 152 * 4) b = 152 * 4;
+  if (b > 152 * 2) b = 152 * 2;
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -62,9 +62,90 @@ k_multi_dot(const double* __restrict__ V, long long ldv, int nv, const double* _
   }
 }
 
+// Exact-count variants for nv <= 16 (the common Krylov depths): every loop
+// unrolls to exactly nv FMAs, with no predicated-off slots in the FP64 pipe.
+template <int NV>
+__device__ __forceinline__ void block_sum_n(double (&v)[NV], double* sh, double* out) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k * 8 + wid] = v[k];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double r = 0.0;
+    for (int w = 0; w < nw; ++w) r += sh[threadIdx.x * 8 + w];
+    out[threadIdx.x] = r;
+  }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(IRK_BLAS_THREADS)
+k_multi_dot_n(const double* __restrict__ V, long long ldv, const double* __restrict__ w,
+              long long L, double* __restrict__ partials) {
+  __shared__ double sh[NV * 8];
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double wv = w[p];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = fma(V[k * ldv + p], wv, acc[k]);
+  }
+  block_sum_n<NV>(acc, sh, partials + (long long)blockIdx.x * NV);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(IRK_BLAS_THREADS)
+k_update_dot_n(const double* __restrict__ V, long long ldv, const double* __restrict__ h,
+               double* __restrict__ w, long long L, int with_dots, double* __restrict__ partials) {
+  __shared__ double sh[(NV + 1) * 8];
+  double hk[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) hk[k] = h[k];
+  double acc[NV + 1];
+#pragma unroll
+  for (int k = 0; k <= NV; ++k) acc[k] = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    double v[NV];
+    double x = w[p];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      v[k] = V[k * ldv + p];
+      x = fma(-hk[k], v[k], x);
+    }
+    w[p] = x;
+    if (with_dots) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) acc[k] = fma(v[k], x, acc[k]);
+    }
+    acc[NV] = fma(x, x, acc[NV]);
+  }
+  if (with_dots) {
+    block_sum_n<NV + 1>(acc, sh, partials + (long long)blockIdx.x * (NV + 1));
+  } else {
+    double nr[1] = {acc[NV]};
+    block_sum_n<1>(nr, sh, partials + (long long)blockIdx.x * (NV + 1) + NV);
+  }
+}
+
+#define IRK_NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
 void launch_multi_dot(const double* V, long long ldv, int nv, const double* w, long long L,
                       double* partials, cudaStream_t st) {
-  k_multi_dot<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V, ldv, nv, w, L, partials);
+  const int nb = blas_blocks(L);
+  switch (nv) {
+#define IRK_MD(N) case N: k_multi_dot_n<N><<<nb, IRK_BLAS_THREADS, 0, st>>>(V, ldv, w, L, partials); return;
+    IRK_NV_CASES(IRK_MD)
+#undef IRK_MD
+    default: k_multi_dot<<<nb, IRK_BLAS_THREADS, 0, st>>>(V, ldv, nv, w, L, partials);
+  }
 }
 
 // w <- w - sum_k h_k V_k; optionally partials of V_k . w_new (k < nv) and
@@ -112,8 +193,14 @@ k_update_dot(const double* __restrict__ V, long long ldv, int nv, const double* 
 
 void launch_update_dot(const double* V, long long ldv, int nv, const double* hdev, double* w,
                        long long L, int with_dots, double* partials, cudaStream_t st) {
-  k_update_dot<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V, ldv, nv, hdev, w, L, with_dots,
-                                                            partials);
+  const int nb = blas_blocks(L);
+  switch (nv) {
+#define IRK_UD(N) case N: k_update_dot_n<N><<<nb, IRK_BLAS_THREADS, 0, st>>>(V, ldv, hdev, w, L, with_dots, partials); return;
+    IRK_NV_CASES(IRK_UD)
+#undef IRK_UD
+    default:
+      k_update_dot<<<nb, IRK_BLAS_THREADS, 0, st>>>(V, ldv, nv, hdev, w, L, with_dots, partials);
+  }
 }
 
 // out[v] = sum_b partials[b * stride + v] in a fixed order, v < gridDim.x

@@ -108,18 +108,37 @@ __device__ __forceinline__ typename Cmp<TS>::T rhs_minus_offdiag(
   return t;
 }
 
+// Level constants of A, formed on the host (a uniform division per thread
+// costs more FP64 issue slots than the whole 5-point update).
+struct MGConst {
+  double alpha;  // cadv / (2h)
+  double beta;   // -cdiff / h^2
+  double D;      // sigma + 2 dim cdiff / h^2 (Jacobi diagonal)
+  double dinv;   // omega / D
+  double keep;   // 1 - omega
+};
+
+MGConst mg_const(const MGLevelDesc& lv, int dim, double sigma, double cadv, double cdiff,
+                 double omega) {
+  MGConst c;
+  const double invh2 = 1.0 / (lv.h * lv.h);
+  c.alpha = cadv * 0.5 / lv.h;
+  c.beta = -cdiff * invh2;
+  c.D = sigma + cdiff * (2 * dim) * invh2;
+  c.dinv = omega / c.D;
+  c.keep = 1.0 - omega;
+  return c;
+}
+
 template <typename TS, int DIM, int KIND>
-__global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, double sigma_,
-                                                   double cadv_, double cdiff_, double omega_,
+__global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, MGConst k,
                                                    const TS* __restrict__ vel,
                                                    const TS* __restrict__ b,
                                                    const TS* __restrict__ w_in,
                                                    TS* __restrict__ w_out, int first) {
   typedef typename Cmp<TS>::T TC;
-  const double invh2d = 1.0 / (lv.h * lv.h);
-  const double D = sigma_ + cdiff_ * (2 * DIM) * invh2d;
-  const TC alpha = TC(cadv_ * 0.5 / lv.h), beta = TC(-cdiff_ * invh2d);
-  const TC dinv = TC(omega_ / D), keep = TC(1.0 - omega_);
+  const TC alpha = TC(k.alpha), beta = TC(k.beta);
+  const TC dinv = TC(k.dinv), keep = TC(k.keep);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lv.npts; p += gridDim.x * blockDim.x) {
     const LvIdx q = lv_nbr<DIM>(lv, p);
     if (first) {
@@ -140,15 +159,13 @@ __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, do
 }
 
 template <typename TS, int DIM, int KIND>
-__global__ void __launch_bounds__(256) k_mg_residual(MGLevelDesc lv, int ncomp, double sigma_,
-                                                     double cadv_, double cdiff_,
+__global__ void __launch_bounds__(256) k_mg_residual(MGLevelDesc lv, int ncomp, MGConst k,
                                                      const TS* __restrict__ vel,
                                                      const TS* __restrict__ b,
                                                      const TS* __restrict__ w, TS* __restrict__ r) {
   typedef typename Cmp<TS>::T TC;
-  const double invh2d = 1.0 / (lv.h * lv.h);
-  const TC D = TC(sigma_ + cdiff_ * (2 * DIM) * invh2d);
-  const TC alpha = TC(cadv_ * 0.5 / lv.h), beta = TC(-cdiff_ * invh2d);
+  const TC D = TC(k.D);
+  const TC alpha = TC(k.alpha), beta = TC(k.beta);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lv.npts; p += gridDim.x * blockDim.x) {
     const LvIdx q = lv_nbr<DIM>(lv, p);
     const Coef4<TC> cf = stencil_coef<TS, DIM, KIND>(q, vel, lv.npts, alpha, beta);
@@ -306,7 +323,7 @@ __global__ void k_convert_out(const TS* __restrict__ src, double* __restrict__ d
 // ---------------------------------------------------------------------------
 static int grid_for(long long n) {
   long long b = (n + 255) / 256;
-  if (b > 152 * 8) b = 152 * 8;
+  if (b > 152 * 4) b = 152 * 4;
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -337,16 +354,17 @@ size_t mg_elem_size(int prec) {
 void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
                       double cadv, double cdiff, double omega, const void* vel, const void* b,
                       const void* w_in, void* w_out, int first, cudaStream_t st) {
+  const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, omega);
   IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_smooth<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
-      lv, ncomp, sigma, cadv, cdiff, omega, (const TS*)vel, (const TS*)b, (const TS*)w_in,
-      (TS*)w_out, first))));
+      lv, ncomp, k, (const TS*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first))));
 }
 
 void launch_mg_residual(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp,
                         double sigma, double cadv, double cdiff, const void* vel, const void* b,
                         const void* w, void* r, cudaStream_t st) {
+  const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, 1.0);
   IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_residual<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
-      lv, ncomp, sigma, cadv, cdiff, (const TS*)vel, (const TS*)b, (const TS*)w, (TS*)r))));
+      lv, ncomp, k, (const TS*)vel, (const TS*)b, (const TS*)w, (TS*)r))));
 }
 
 void launch_mg_restrict(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* rf,
