@@ -1,0 +1,333 @@
+// Device-resident flexible GMRES (step a8): the Arnoldi bookkeeping runs on
+// the GPU so that one restart cycle needs no host round trip.
+//
+// The iteration index j, the Hessenberg matrix, the Givens rotations and the
+// rotated right-hand side live in an FGState block in device memory.  The
+// basis kernels read j from there (so one captured kernel serves every j),
+// k_fg_arnoldi closes an iteration (Hessenberg column, rotations, residual
+// estimate) and ends the loop through the conditional handle of a CUDA-graph
+// WHILE node once the block has converged, lost its basis, or used m
+// iterations; the loop therefore runs at most m times.  The arithmetic is the
+// one of the host path (CGS2, Givens, back substitution), in FP64.
+#include "irk_internal.h"
+
+namespace irk {
+
+// ---------------------------------------------------------------------------
+// Inner products / updates with the basis size read from device memory.
+template <int NV>
+__device__ __forceinline__ void dev_block_sum(double (&v)[NV], double* sh, double* out) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k * 8 + wid] = v[k];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double r = 0.0;
+    for (int w = 0; w < nw; ++w) r += sh[threadIdx.x * 8 + w];
+    out[threadIdx.x] = r;
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void dev_multi_dot(const double* __restrict__ V, long long ldv,
+                                              const double* __restrict__ w, long long L,
+                                              double* __restrict__ partials, double* sh) {
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double wv = w[p];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = fma(V[k * ldv + p], wv, acc[k]);
+  }
+  dev_block_sum<NV>(acc, sh, partials + (long long)blockIdx.x * NV);
+}
+
+template <int NV>
+__device__ __forceinline__ void dev_update_dot(const double* __restrict__ V, long long ldv,
+                                               const double* __restrict__ h,
+                                               double* __restrict__ w, long long L,
+                                               int with_dots, double* __restrict__ partials,
+                                               double* sh) {
+  double hk[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) hk[k] = h[k];
+  double acc[NV + 1];
+#pragma unroll
+  for (int k = 0; k <= NV; ++k) acc[k] = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    double v[NV];
+    double x = w[p];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      v[k] = V[k * ldv + p];
+      x = fma(-hk[k], v[k], x);
+    }
+    w[p] = x;
+    if (with_dots) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) acc[k] = fma(v[k], x, acc[k]);
+    }
+    acc[NV] = fma(x, x, acc[NV]);
+  }
+  if (with_dots) {
+    dev_block_sum<NV + 1>(acc, sh, partials + (long long)blockIdx.x * (NV + 1));
+  } else {
+    double nr[1] = {acc[NV]};
+    dev_block_sum<1>(nr, sh, partials + (long long)blockIdx.x * (NV + 1) + NV);
+  }
+}
+
+// Generic (nv > 16) forms: chunks of 4 values
+__device__ void dev_multi_dot_any(const double* __restrict__ V, long long ldv, int nv,
+                                  const double* __restrict__ w, long long L,
+                                  double* __restrict__ partials, double* sh) {
+  for (int k0 = 0; k0 < nv; k0 += 4) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int kn = min(4, nv - k0);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+         p += (long long)gridDim.x * blockDim.x) {
+      const double wv = w[p];
+      for (int k = 0; k < kn; ++k) acc[k] = fma(V[(k0 + k) * ldv + p], wv, acc[k]);
+    }
+    double tmp[4];
+    dev_block_sum<4>(acc, sh, tmp);
+    if (threadIdx.x < kn) partials[(long long)blockIdx.x * nv + k0 + threadIdx.x] = tmp[threadIdx.x];
+  }
+}
+
+__device__ void dev_update_dot_any(const double* __restrict__ V, long long ldv, int nv,
+                                   const double* __restrict__ h, double* __restrict__ w,
+                                   long long L, int with_dots, double* __restrict__ partials,
+                                   double* sh) {
+  double nrm = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    double x = w[p];
+    for (int k = 0; k < nv; ++k) x = fma(-h[k], V[k * ldv + p], x);
+    w[p] = x;
+    nrm = fma(x, x, nrm);
+  }
+  const int nvals = nv + 1;
+  if (with_dots) {
+    for (int k0 = 0; k0 < nv; k0 += 4) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      const int kn = min(4, nv - k0);
+      for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+           p += (long long)gridDim.x * blockDim.x) {
+        const double x = w[p];
+        for (int k = 0; k < kn; ++k) acc[k] = fma(V[(k0 + k) * ldv + p], x, acc[k]);
+      }
+      double tmp[4];
+      dev_block_sum<4>(acc, sh, tmp);
+      if (threadIdx.x < kn) partials[(long long)blockIdx.x * nvals + k0 + threadIdx.x] = tmp[threadIdx.x];
+    }
+  }
+  double nr[1] = {nrm};
+  double tmp[1];
+  dev_block_sum<1>(nr, sh, tmp);
+  if (threadIdx.x == 0) partials[(long long)blockIdx.x * nvals + nv] = tmp[0];
+}
+
+#define IRK_DEV_NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
+__global__ void __launch_bounds__(IRK_BLAS_THREADS)
+k_fg_multi_dot(const double* __restrict__ V, long long ldv, const FGState* __restrict__ s,
+               const double* __restrict__ w, long long L, double* __restrict__ partials) {
+  __shared__ double sh[17 * 8];
+  const int nv = s->j + 1;
+  switch (nv) {
+#define IRK_C(N) case N: dev_multi_dot<N>(V, ldv, w, L, partials, sh); return;
+    IRK_DEV_NV_CASES(IRK_C)
+#undef IRK_C
+    default: dev_multi_dot_any(V, ldv, nv, w, L, partials, sh);
+  }
+}
+
+__global__ void __launch_bounds__(IRK_BLAS_THREADS)
+k_fg_update_dot(const double* __restrict__ V, long long ldv, const FGState* __restrict__ s,
+                const double* __restrict__ h, double* __restrict__ w, long long L, int with_dots,
+                double* __restrict__ partials) {
+  __shared__ double sh[17 * 8];
+  const int nv = s->j + 1;
+  switch (nv) {
+#define IRK_C(N) case N: dev_update_dot<N>(V, ldv, h, w, L, with_dots, partials, sh); return;
+    IRK_DEV_NV_CASES(IRK_C)
+#undef IRK_C
+    default: dev_update_dot_any(V, ldv, nv, h, w, L, with_dots, partials, sh);
+  }
+}
+
+// Sum the per-block partials in a fixed order, with nv = j + 1 from s:
+// mode 0 (multi_dot):       out[v] = sum_b partials[b*nv + v],         v < nv
+// mode 1 (update with dots): out[v] = sum_b partials[b*(nv+1) + v],    v < nv + 1
+// mode 2 (update, norm):    out[0] = sum_b partials[b*(nv+1) + nv]
+__global__ void k_fg_reduce(const double* __restrict__ partials, int nblk,
+                            const FGState* __restrict__ s, int mode, double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int nv = s->j + 1;
+  const int v = blockIdx.x;
+  const int count = mode == 0 ? nv : (mode == 1 ? nv + 1 : 1);
+  if (v >= count) return;
+  const int stride = mode == 0 ? nv : nv + 1;
+  const int off = mode == 2 ? nv : 0;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += partials[(long long)b * stride + v + off];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+    out[v] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Start of a cycle: beta = ||b|| (from its reduced square), g = beta e_1,
+// first basis scale 1/beta; an empty or non-finite right-hand side ends the
+// loop before it starts.
+__global__ void k_fg_init(FGState* s, const double* __restrict__ nrm2, const double* __restrict__ rtol,
+                          cudaGraphConditionalHandle cond) {
+  const double beta = sqrt(fmax(nrm2[0], 0.0));
+  s->j = 0;
+  s->k = 0;
+  s->its = 0;
+  s->beta = beta;
+  s->target = rtol[0] * beta;
+  s->res = beta;
+  for (int i = 0; i <= IRK_FG_MAXM; ++i) s->g[i] = 0.0;
+  s->g[0] = beta;
+  if (!(beta > 0.0) || !isfinite(beta)) {
+    s->status = isfinite(beta) ? 0 : 2;
+    s->inv_scale = 0.0;
+    cudaGraphSetConditional(cond, 0);
+  } else {
+    s->status = 0;
+    s->inv_scale = 1.0 / beta;
+  }
+}
+
+// v = w * s->inv_scale written to V_j (j from s) and to prec_in
+__global__ void k_fg_scale(const double* __restrict__ w, const FGState* __restrict__ s,
+                           double* __restrict__ V, long long ldv, double* __restrict__ prec_in,
+                           long long L) {
+  const double sc = s->inv_scale;
+  double* vj = V + (long long)s->j * ldv;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double x = w[p] * sc;
+    vj[p] = x;
+    prec_in[p] = x;
+  }
+}
+
+// Close iteration j: Hessenberg column from the two CGS passes, rotations,
+// residual estimate; stop or advance.
+__global__ void k_fg_arnoldi(FGState* s, const double* __restrict__ h1, const double* __restrict__ h2,
+                             const double* __restrict__ nrm2, int m, int maxit, double* its_total,
+                             cudaGraphConditionalHandle cond) {
+  const int j = s->j;
+  double* Hc = s->H + j * (IRK_FG_MAXM + 1);  // column j, rows 0..j+1
+  for (int i = 0; i <= j; ++i) Hc[i] = h1[i] + h2[i];
+  const double hn = sqrt(fmax(nrm2[0], 0.0));
+  for (int i = 0; i < j; ++i) {
+    const double t0 = s->cs[i] * Hc[i] + s->sn[i] * Hc[i + 1];
+    const double t1 = -s->sn[i] * Hc[i] + s->cs[i] * Hc[i + 1];
+    Hc[i] = t0;
+    Hc[i + 1] = t1;
+  }
+  const double hjj = Hc[j];
+  const double den = hypot(hjj, hn);
+  s->cs[j] = den > 0.0 ? hjj / den : 1.0;
+  s->sn[j] = den > 0.0 ? hn / den : 0.0;
+  Hc[j] = den;
+  Hc[j + 1] = 0.0;
+  s->g[j + 1] = -s->sn[j] * s->g[j];
+  s->g[j] = s->cs[j] * s->g[j];
+  const double res = fabs(s->g[j + 1]);
+  s->res = res;
+  s->its += 1;
+  its_total[0] += 1.0;
+  if (!isfinite(hn) || !isfinite(s->g[j + 1])) its_total[1] = 1.0;  // non-finite flag
+  const bool finite = isfinite(hn) && isfinite(res);
+  if (!finite) s->status = 2;
+  if (!finite || res <= s->target || hn <= 1e-300 || j + 1 >= m || s->its >= maxit) {
+    s->k = finite ? j + 1 : 0;
+    cudaGraphSetConditional(cond, 0);
+  } else {
+    s->j = j + 1;
+    s->inv_scale = 1.0 / hn;
+  }
+}
+
+// y = R^{-1} g on the leading k x k triangle
+__global__ void k_fg_solve(FGState* s) {
+  const int k = s->k;
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = s->g[i];
+    for (int q = i + 1; q < k; ++q) acc -= s->H[q * (IRK_FG_MAXM + 1) + i] * s->y[q];
+    s->y[i] = acc / s->H[i * (IRK_FG_MAXM + 1) + i];
+  }
+}
+
+// x += sum_{j<k} y_j Z_j
+__global__ void k_fg_lincomb(double* __restrict__ x, const double* __restrict__ Z, long long ldz,
+                             const FGState* __restrict__ s, long long L) {
+  __shared__ double ys[IRK_FG_MAXM];
+  const int k = s->k;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = s->y[j];
+  __syncthreads();
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    double acc = x[p];
+    for (int j = 0; j < k; ++j) acc = fma(ys[j], Z[j * ldz + p], acc);
+    x[p] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+void launch_fg_init(FGState* s, const double* nrm2, const double* rtol,
+                    cudaGraphConditionalHandle cond, cudaStream_t st) {
+  k_fg_init<<<1, 1, 0, st>>>(s, nrm2, rtol, cond);
+}
+void launch_fg_scale(const double* w, const FGState* s, double* V, long long ldv, double* prec_in,
+                     long long L, cudaStream_t st) {
+  k_fg_scale<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(w, s, V, ldv, prec_in, L);
+}
+void launch_fg_multi_dot(const double* V, long long ldv, const FGState* s, const double* w,
+                         long long L, double* partials, cudaStream_t st) {
+  k_fg_multi_dot<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V, ldv, s, w, L, partials);
+}
+void launch_fg_update_dot(const double* V, long long ldv, const FGState* s, const double* h,
+                          double* w, long long L, int with_dots, double* partials,
+                          cudaStream_t st) {
+  k_fg_update_dot<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V, ldv, s, h, w, L, with_dots,
+                                                               partials);
+}
+void launch_fg_reduce(const double* partials, int nblk, const FGState* s, int mode, int max_count,
+                      double* out, cudaStream_t st) {
+  k_fg_reduce<<<max_count, 256, 0, st>>>(partials, nblk, s, mode, out);
+}
+void launch_fg_arnoldi(FGState* s, const double* h1, const double* h2, const double* nrm2, int m,
+                       int maxit, double* its_total, cudaGraphConditionalHandle cond,
+                       cudaStream_t st) {
+  k_fg_arnoldi<<<1, 1, 0, st>>>(s, h1, h2, nrm2, m, maxit, its_total, cond);
+}
+void launch_fg_solve(FGState* s, cudaStream_t st) { k_fg_solve<<<1, 1, 0, st>>>(s); }
+void launch_fg_lincomb(double* x, const double* Z, long long ldz, const FGState* s, long long L,
+                       cudaStream_t st) {
+  k_fg_lincomb<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(x, Z, ldz, s, L);
+}
+
+}  // namespace irk

@@ -11,6 +11,7 @@
 #define IRK_MAX_TERMS 5
 #define IRK_MAX_LEVELS 16
 #define IRK_BLAS_THREADS 256
+#define IRK_FG_MAXM 64
 
 namespace irk {
 
@@ -88,6 +89,20 @@ struct StageOpArgs {
   double* copy_dst;      // optional: copy_src -> copy_dst (ncomp*npts*copy_rows)
   const double* copy_src;
   long long copy_len;
+  const int* copy_jdev;  // optional: copy_dst += (*copy_jdev) * copy_ldv (device index)
+  long long copy_ldv;
+};
+
+// Device-resident FGMRES(m) state of one block solve (Arnoldi/Givens data).
+struct FGState {
+  int j;          // current Arnoldi index
+  int k;          // columns of the final least-squares problem
+  int its;        // iterations of this cycle
+  int status;     // 0 ok, 2 non-finite
+  double beta, target, res, inv_scale;
+  double g[IRK_FG_MAXM + 1];
+  double cs[IRK_FG_MAXM], sn[IRK_FG_MAXM], y[IRK_FG_MAXM];
+  double H[IRK_FG_MAXM * (IRK_FG_MAXM + 1)];  // column-major, column j at j*(MAXM+1)
 };
 
 // ---------------------------------------------------------------------------
@@ -128,6 +143,25 @@ void launch_lincomb(double* x, const double* Z, long long ldz, int k, const doub
                     long long L, cudaStream_t st);
 void launch_norm2(const double* x, long long L, double* partials, cudaStream_t st);
 void launch_axpby(double* y, double a, const double* x, double b, long long L, cudaStream_t st);
+
+// Device-resident FGMRES (fgmres_dev.cu)
+void launch_fg_init(FGState* s, const double* nrm2, const double* rtol,
+                    cudaGraphConditionalHandle cond, cudaStream_t st);
+void launch_fg_scale(const double* w, const FGState* s, double* V, long long ldv, double* prec_in,
+                     long long L, cudaStream_t st);
+void launch_fg_multi_dot(const double* V, long long ldv, const FGState* s, const double* w,
+                         long long L, double* partials, cudaStream_t st);
+void launch_fg_update_dot(const double* V, long long ldv, const FGState* s, const double* h,
+                          double* w, long long L, int with_dots, double* partials,
+                          cudaStream_t st);
+void launch_fg_reduce(const double* partials, int nblk, const FGState* s, int mode, int max_count,
+                      double* out, cudaStream_t st);
+void launch_fg_arnoldi(FGState* s, const double* h1, const double* h2, const double* nrm2, int m,
+                       int maxit, double* its_total, cudaGraphConditionalHandle cond,
+                       cudaStream_t st);
+void launch_fg_solve(FGState* s, cudaStream_t st);
+void launch_fg_lincomb(double* x, const double* Z, long long ldz, const FGState* s, long long L,
+                       cudaStream_t st);
 
 // Multigrid (templated on the storage precision; prec = irk_mg_precision)
 void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,

@@ -210,6 +210,9 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MGLevelDesc fine, int ncomp
 }
 
 // Bilinear (linear in 1D) interpolation of the coarse correction, added to w.
+// One thread per coarse point updates the 2x2 (1D: 2) fine points it owns:
+// (2I,2J) += c00, (2I+1,2J) += (c00+c10)/2, (2I,2J+1) += (c00+c01)/2,
+// (2I+1,2J+1) += (c00+c10+c01+c11)/4.
 template <typename TS, int DIM>
 __global__ void __launch_bounds__(256) k_mg_prolong_add(MGLevelDesc fine, int ncomp,
                                                         const TS* __restrict__ wc,
@@ -217,26 +220,28 @@ __global__ void __launch_bounds__(256) k_mg_prolong_add(MGLevelDesc fine, int nc
   typedef typename Cmp<TS>::T TC;
   const int nc = fine.n >> 1, logc = fine.logn - 1, mc = nc - 1;
   const int ncpts = (DIM == 1) ? nc : nc * nc;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < fine.npts; p += gridDim.x * blockDim.x) {
+  const TC half = TC(0.5), quarter = TC(0.25);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < ncpts; p += gridDim.x * blockDim.x) {
     for (int c = 0; c < ncomp; ++c) {
       const TS* g = wc + (long long)c * ncpts;
-      TC e;
+      TS* f = wf + (long long)c * fine.npts;
       if (DIM == 1) {
-        const int I = p >> 1;
-        e = (p & 1) ? TC(0.5) * (ldv(g + I) + ldv(g + ((I + 1) & mc))) : ldv(g + I);
+        const TC c0 = ldv(g + p), c1 = ldv(g + ((p + 1) & mc));
+        stv<TS, TC>(f + 2 * p, ldv(f + 2 * p) + c0);
+        stv<TS, TC>(f + 2 * p + 1, ldv(f + 2 * p + 1) + half * (c0 + c1));
       } else {
-        const int i = p & (fine.n - 1), j = p >> fine.logn;
-        const int I = i >> 1, J = j >> 1, I1 = (I + 1) & mc, J1 = (J + 1) & mc;
-        const TC c00 = ldv(g + (J << logc) + I);
-        if (!(i & 1) && !(j & 1)) e = c00;
-        else if ((i & 1) && !(j & 1)) e = TC(0.5) * (c00 + ldv(g + (J << logc) + I1));
-        else if (!(i & 1) && (j & 1)) e = TC(0.5) * (c00 + ldv(g + (J1 << logc) + I));
-        else
-          e = TC(0.25) * (c00 + ldv(g + (J << logc) + I1) + ldv(g + (J1 << logc) + I) +
-                          ldv(g + (J1 << logc) + I1));
+        const int I = p & mc, J = p >> logc;
+        const int I1 = (I + 1) & mc, J1 = (J + 1) & mc;
+        const TC c00 = ldv(g + p), c10 = ldv(g + (J << logc) + I1);
+        const TC c01 = ldv(g + (J1 << logc) + I), c11 = ldv(g + (J1 << logc) + I1);
+        const int lf = fine.logn;
+        TS* r0 = f + ((2 * J) << lf) + 2 * I;
+        TS* r1 = r0 + fine.n;
+        stv<TS, TC>(r0, ldv(r0) + c00);
+        stv<TS, TC>(r0 + 1, ldv(r0 + 1) + half * (c00 + c10));
+        stv<TS, TC>(r1, ldv(r1) + half * (c00 + c01));
+        stv<TS, TC>(r1 + 1, ldv(r1 + 1) + quarter * ((c00 + c10) + (c01 + c11)));
       }
-      TS* dst = wf + (long long)c * fine.npts + p;
-      stv<TS, TC>(dst, ldv(dst) + e);
     }
   }
 }
@@ -380,11 +385,12 @@ void launch_mg_restrict(int prec, int dim, const MGLevelDesc& fine, int ncomp, c
 
 void launch_mg_prolong_add(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* wc,
                            void* wf, cudaStream_t st) {
+  const long long nc = dim == 1 ? fine.n / 2 : (long long)(fine.n / 2) * (fine.n / 2);
   IRK_DISPATCH_PREC(prec, {
     if (dim == 1)
-      k_mg_prolong_add<TS, 1><<<grid_for(fine.npts), 256, 0, st>>>(fine, ncomp, (const TS*)wc, (TS*)wf);
+      k_mg_prolong_add<TS, 1><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc, (TS*)wf);
     else
-      k_mg_prolong_add<TS, 2><<<grid_for(fine.npts), 256, 0, st>>>(fine, ncomp, (const TS*)wc, (TS*)wf);
+      k_mg_prolong_add<TS, 2><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc, (TS*)wf);
   });
 }
 

@@ -86,6 +86,16 @@ struct irk_handle {
   bool graphs_failed = false;
   int graph_vcycles[IRK_MAXS] = {};
   long long graph_launches[IRK_MAXS] = {};
+  // device-resident FGMRES: one graph per block = coupling + init + WHILE
+  // (L_P, matvec, CGS2, Arnoldi) + solution update
+  FGState* fgs = nullptr;  // one per block
+  cudaStream_t st_aux = nullptr;
+  cudaGraphExec_t fgexec[IRK_MAXS] = {};
+  double fg_dt = 0.0;
+  bool fg_failed = false;
+  long long fg_fixed_launches[IRK_MAXS] = {}, fg_body_launches[IRK_MAXS] = {};
+  int fg_body_vcycles[IRK_MAXS] = {};
+  double fg_seen_its[IRK_MAXS] = {};
   double* hbuf = nullptr;  // pinned host
   int nparts = 0;
 
@@ -741,9 +751,242 @@ irk_status eval_residual(irk_handle* h, double t_n, double dt, const double* K, 
     ProfScope ps(h, P_REDUCE, 8.0 * nb, nb);
     launch_reduce(h->partials, nb, 1, 1, h->dscal + 201, h->st);
   }
-  TRY(sync_read(h, h->dscal + 201, 1));
+  // the norm, plus (slots 320..) the device-FGMRES iteration counters
+  TRY(sync_read(h, h->dscal + 201, 140));
   *fnorm = std::sqrt(h->hbuf[0]);
   return IRK_OK;
+}
+
+// Device-FGMRES counters: dscal[320 + 2 blk] = iterations so far (all cycles),
+// dscal[321 + 2 blk] = non-finite flag.  hbuf holds dscal[201..340] after a
+// residual evaluation.
+irk_status collect_fg_counters(irk_handle* h) {
+  for (int blk = 0; blk < h->tab.nblk; ++blk) {
+    const double its = h->hbuf[320 - 201 + 2 * blk];
+    const double bad = h->hbuf[321 - 201 + 2 * blk];
+    const long long d = (long long)(its - h->fg_seen_its[blk]);
+    if (d > 0) {
+      h->stats.krylov_its += (int)d;
+      h->stats.prec_apps += (int)d * h->tab.bsize[blk];
+      h->stats.vcycles += (int)d * h->fg_body_vcycles[blk];
+      h->stats.kernel_launches += d * h->fg_body_launches[blk];
+    }
+    h->fg_seen_its[blk] = its;
+    if (bad != 0.0) {
+      h->err = "non-finite Krylov vector";
+      return IRK_ERR_KRYLOV_BREAKDOWN;
+    }
+  }
+  return IRK_OK;
+}
+
+void drop_fg_graphs(irk_handle* h) {
+  for (int k = 0; k < IRK_MAXS; ++k)
+    if (h->fgexec[k]) {
+      cudaGraphExecDestroy(h->fgexec[k]);
+      h->fgexec[k] = nullptr;
+    }
+}
+
+// One restart cycle of FGMRES on block blk as a single CUDA graph:
+//   prefix  z = rhs_blk - U dk_hat (Eq. D+U), x = 0, beta = ||z||, V_0 = z/beta
+//   WHILE   z_j = L_P v_j; w = D z_j (Z_j = z_j); CGS2; Arnoldi/Givens step
+//   suffix  y = R^{-1} g; x += Z y
+// The loop ends on the device (k_fg_arnoldi) after at most m iterations.
+irk_status build_fg_graph(irk_handle* h, double dt, int blk) {
+  const int a0 = h->tab.bstart[blk], bs = h->tab.bsize[blk];
+  const long long Lb = (long long)bs * h->L;
+  const long long ldv = Lb;
+  const int nb = blas_blocks(Lb);
+  FGState* fs = h->fgs + blk;
+  double* x = h->yhat + (long long)a0 * h->L;
+  const double* b = h->rhs + (long long)a0 * h->L;
+  const irk_stats saved = h->stats;
+  cudaGraph_t G = nullptr;
+  cudaGraphConditionalHandle cond;
+  CK(cudaGraphCreate(&G, 0));
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, G, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) { cudaGraphDestroy(G); cudaGetLastError(); return IRK_ERR_CUDA; }
+  e = cudaStreamBeginCaptureToGraph(h->st, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaGraphDestroy(G); cudaGetLastError(); return IRK_ERR_CUDA; }
+  // ---- prefix
+  if (blk < h->tab.nblk - 1) {
+    upper_coupling(h, dt, blk, h->zbuf);
+    b = h->zbuf;
+  }
+  cudaMemsetAsync(x, 0, sizeof(double) * Lb, h->st);
+  {
+    ProfScope ps(h, P_NORM, 8.0 * Lb, 2.0 * Lb);
+    launch_norm2(b, Lb, h->partials, h->st);
+  }
+  {
+    ProfScope ps(h, P_REDUCE, 8.0 * blas_blocks(Lb), blas_blocks(Lb));
+    launch_reduce(h->partials, blas_blocks(Lb), 1, 1, h->dscal + 310, h->st);
+  }
+  {
+    ProfScope ps(h, P_SCALE, 0, 0);
+    launch_fg_init(fs, h->dscal + 310, h->dscal + 300, cond, h->st);
+  }
+  {
+    ProfScope ps(h, P_SCALE, 16.0 * Lb, (double)Lb);
+    launch_fg_scale(b, fs, h->V, ldv, h->prec_in, Lb, h->st);
+  }
+  // ---- WHILE node after the prefix
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  e = cudaStreamGetCaptureInfo(h->st, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+  cudaGraphNode_t wnode = nullptr;
+  cudaGraph_t body = nullptr;
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&wnode, G, deps, nullptr, ndeps, &np);
+    if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
+  }
+  const long long prefix_launches = h->stats.kernel_launches - saved.kernel_launches;
+  long long body_launches = 0;
+  int body_vcycles = 0;
+  if (e == cudaSuccess) {
+    // capture the loop body on the auxiliary stream
+    e = cudaStreamBeginCaptureToGraph(h->st_aux, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaStream_t main = h->st;
+      h->st = h->st_aux;
+      const long long l0 = h->stats.kernel_launches;
+      const int v0 = h->stats.vcycles;
+      block_prec(h, dt, blk, h->prec_in, h->prec_out);
+      {
+        // w = D z_j with z_j = prec_out; Z_j = z_j (j read on the device)
+        const int s = h->s;
+        StageOpArgs a;
+        memset(&a, 0, sizeof(a));
+        a.nrow = bs;
+        a.dt = dt;
+        for (int rr = 0; rr < bs; ++rr) {
+          const int r = a0 + rr;
+          OpRow& row = a.row[rr];
+          row.y = h->w + (long long)rr * h->L;
+          row.sigma = 1;
+          for (int qq = 0; qq < bs; ++qq) {
+            const int q = a0 + qq;
+            OpTerm& t = row.t[row.nterm++];
+            t.x = h->prec_out + (long long)qq * h->L;
+            t.combo = keep_coupling(h, r, q) ? combo_ptr(h, r, q) : nullptr;
+            t.m = h->tab.R[r * s + q];
+            t.lin = (r == q) ? 1.0 : 0.0;
+          }
+        }
+        a.copy_dst = h->Z;
+        a.copy_src = h->prec_out;
+        a.copy_len = Lb;
+        a.copy_jdev = &fs->j;
+        a.copy_ldv = ldv;
+        run_stage_op(h, a);
+      }
+      double* dh1 = h->dscal;
+      double* dh2 = h->dscal + 64;
+      double* dnr = h->dscal + 130;
+      const int mcap = h->m + 2;
+      {
+        ProfScope ps(h, P_GS_DOT, 0, 0);
+        launch_fg_multi_dot(h->V, ldv, fs, h->w, Lb, h->partials, h->st);
+      }
+      {
+        ProfScope ps(h, P_REDUCE, 0, 0);
+        launch_fg_reduce(h->partials, nb, fs, 0, mcap, dh1, h->st);
+      }
+      {
+        ProfScope ps(h, P_GS_UPDATE, 0, 0);
+        launch_fg_update_dot(h->V, ldv, fs, dh1, h->w, Lb, 1, h->partials, h->st);
+      }
+      {
+        ProfScope ps(h, P_REDUCE, 0, 0);
+        launch_fg_reduce(h->partials, nb, fs, 1, mcap, dh2, h->st);
+      }
+      {
+        ProfScope ps(h, P_GS_UPDATE, 0, 0);
+        launch_fg_update_dot(h->V, ldv, fs, dh2, h->w, Lb, 0, h->partials, h->st);
+      }
+      {
+        ProfScope ps(h, P_REDUCE, 0, 0);
+        launch_fg_reduce(h->partials, nb, fs, 2, 1, dnr, h->st);
+      }
+      {
+        ProfScope ps(h, P_SCALE, 0, 0);
+        launch_fg_arnoldi(fs, dh1, dh2, dnr, h->m, h->cfg.krylov_maxit, h->dscal + 320 + 2 * blk,
+                          cond, h->st);
+      }
+      {
+        ProfScope ps(h, P_SCALE, 16.0 * Lb, (double)Lb);
+        launch_fg_scale(h->w, fs, h->V, ldv, h->prec_in, Lb, h->st);
+      }
+      body_launches = h->stats.kernel_launches - l0;
+      body_vcycles = h->stats.vcycles - v0;
+      h->st = main;
+      cudaGraph_t bout = nullptr;
+      e = cudaStreamEndCapture(h->st_aux, &bout);
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaStreamUpdateCaptureDependencies(h->st, &wnode, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies);
+  const long long l1 = h->stats.kernel_launches;
+  if (e == cudaSuccess) {
+    // ---- suffix
+    {
+      ProfScope ps(h, P_LINCOMB, 0, 0);
+      launch_fg_solve(fs, h->st);
+    }
+    {
+      ProfScope ps(h, P_LINCOMB, 0, 0);
+      launch_fg_lincomb(x, h->Z, ldv, fs, Lb, h->st);
+    }
+  }
+  cudaGraph_t out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(h->st, &out);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->fgexec[blk], G, 0);
+  cudaGraphDestroy(G);
+  h->fg_fixed_launches[blk] = prefix_launches + (h->stats.kernel_launches - l1);
+  h->fg_body_launches[blk] = body_launches;
+  h->fg_body_vcycles[blk] = body_vcycles;
+  h->stats = saved;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->fgexec[blk] = nullptr;
+    return IRK_ERR_CUDA;
+  }
+  return IRK_OK;
+}
+
+// All block solves of one Newton iteration through the device-resident graphs.
+// Returns false (and leaves no work queued) when graphs cannot be used.
+bool fg_device_solve(irk_handle* h, double dt, double eta) {
+  if (!h->cfg.use_graphs || h->cfg.profile || h->fg_failed || !h->st_aux) return false;
+  if (h->fg_dt != dt) {
+    drop_fg_graphs(h);
+    h->fg_dt = dt;
+  }
+  for (int blk = 0; blk < h->tab.nblk; ++blk)
+    if (!h->fgexec[blk] && build_fg_graph(h, dt, blk) != IRK_OK) {
+      drop_fg_graphs(h);
+      h->fg_failed = true;
+      return false;
+    }
+  h->hbuf[400] = eta;
+  if (cudaMemcpyAsync(h->dscal + 300, h->hbuf + 400, sizeof(double), cudaMemcpyHostToDevice,
+                      h->st) != cudaSuccess)
+    return false;
+  for (int blk = h->tab.nblk - 1; blk >= 0; --blk) {
+    cudaGraphLaunch(h->fgexec[blk], h->st);
+    h->stats.kernel_launches += h->fg_fixed_launches[blk];
+  }
+  return true;
 }
 
 irk_status newton_step(irk_handle* h, double t_n, double dt) {
@@ -753,6 +996,7 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
   int it = 0;
   for (;; ++it) {
     TRY(eval_residual(h, t_n, dt, h->K, h->rhs, nullptr, true, &fn));
+    if (it > 0) TRY(collect_fg_counters(h));
     if (!std::isfinite(fn)) { h->err = "non-finite stage residual"; return IRK_ERR_NEWTON_DIVERGED; }
     if (it == 0) f0 = fn;
     const double rel = (f0 > 0) ? fn / f0 : 0.0;
@@ -773,6 +1017,7 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
     eta_lin = std::max(eta_lin, 1e-13);
     prev = fn;
     mg_setup(h, dt);
+    if (!fg_device_solve(h, dt, eta_lin))
     for (int blk = h->tab.nblk - 1; blk >= 0; --blk) {
       const int a0 = h->tab.bstart[blk];
       const double* z = h->rhs + (long long)a0 * h->L;
@@ -911,6 +1156,7 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   add(8 * Lb);                   // w
   add(8 * Lb);                   // prec_in
   add(8 * Lb);                   // prec_out
+  add(sizeof(FGState) * h->tab.nblk);  // device FGMRES states
   h->nparts = std::max(blas_blocks(Lb) * 70, residual_blocks(g)) + 1024;
   add(8 * (size_t)h->nparts);    // partials
   add(8 * 512);                  // device scalars
@@ -954,6 +1200,7 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   h->w = (double*)take(8 * Lb);
   h->prec_in = (double*)take(8 * Lb);
   h->prec_out = (double*)take(8 * Lb);
+  h->fgs = (FGState*)take(sizeof(FGState) * h->tab.nblk);
   h->partials = (double*)take(8 * (size_t)h->nparts);
   h->dscal = (double*)take(8 * 512);
   for (int l = 0; l < h->nlev; ++l) {
@@ -1123,6 +1370,10 @@ static irk_status create_impl(const irk_config* cfg, const double* u0, int u0_on
       return IRK_ERR_CUDA;
     }
     h->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&h->st_aux, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    h->st_aux = nullptr;  // device-resident FGMRES unavailable; host loop is used
   }
   irk_status st = build(h, u0, u0_on_device);
   if (st != IRK_OK) {
@@ -1307,6 +1558,9 @@ void irk_destroy(irk_handle* h) {
   if (h->hbuf) cudaFreeHost(h->hbuf);
   for (int k = 0; k < IRK_MAXS; ++k)
     if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
+  for (int k = 0; k < IRK_MAXS; ++k)
+    if (h->fgexec[k]) cudaGraphExecDestroy(h->fgexec[k]);
+  if (h->st_aux) cudaStreamDestroy(h->st_aux);
   if (h->arena && h->own_arena) cudaFree(h->arena);
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
   delete h;

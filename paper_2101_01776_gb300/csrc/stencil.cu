@@ -269,6 +269,11 @@ template <int OP>
 __device__ __forceinline__ void term_apply(const GridDesc& g, const OpTerm& t, const Nbr& nb,
                                            double dt, double acc[2]) {
   const int npts = g.npts;
+  if (!t.combo && t.lin == 0.0) {  // mass term only: no neighbours needed
+    acc[0] = fma(t.m, __ldg(t.x + nb.c), acc[0]);
+    if (OP == IRK_OP_BURGERS_2D) acc[1] = fma(t.m, __ldg(t.x + npts + nb.c), acc[1]);
+    return;
+  }
   if (OP == IRK_OP_DIFFUSION_1D || OP == IRK_OP_BURGERS_1D) {
     const double* x = t.x;
     const double xc = __ldg(x + nb.c), xe = __ldg(x + nb.e), xw = __ldg(x + nb.w);
@@ -344,8 +349,11 @@ __global__ void __launch_bounds__(256) k_stage_op(GridDesc g, StageOpArgs a) {
         row.y[idx] = y;
       }
     }
-    if (a.copy_dst)
-      for (long long q = p; q < a.copy_len; q += g.npts) a.copy_dst[q] = a.copy_src[q];
+    if (a.copy_dst) {
+      double* dst = a.copy_dst;
+      if (a.copy_jdev) dst += (long long)(*a.copy_jdev) * a.copy_ldv;
+      for (long long q = p; q < a.copy_len; q += g.npts) dst[q] = a.copy_src[q];
+    }
   }
 }
 

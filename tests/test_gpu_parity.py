@@ -276,8 +276,10 @@ def test_checkpoint_resume_and_determinism_bit_equal(B):
     np.testing.assert_array_equal(full, resumed)
 
 
-def test_graph_replay_is_bit_identical_to_direct_launches(B):
-    """The CUDA-graph replay of L_P runs the same kernels in the same order."""
+def test_graph_path_matches_host_driven_path(B):
+    """The CUDA-graph path (L_P replay, FGMRES loop in a WHILE node with the
+    Arnoldi/Givens step on the device) reaches the same iterates as the
+    host-driven loop: same Krylov counts, states equal to rounding."""
     n, s = 64, 3
     u0 = workloads.random_fourier_2d(n, seed=9)
     stream = torch.cuda.Stream()
@@ -287,7 +289,7 @@ def test_graph_replay_is_bit_identical_to_direct_launches(B):
                          stages=s, nu=5e-3, use_graphs=graphs) as sol:
             st = sol.step(0.0, 2e-3, 3)
             outs.append((sol.state().copy(), st.krylov_its, st.vcycles))
-    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    assert rel(outs[1][0], outs[0][0]) <= 1e-12
     assert outs[0][1:] == outs[1][1:]
 
 
