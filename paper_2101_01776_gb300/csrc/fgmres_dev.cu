@@ -203,6 +203,10 @@ __global__ void k_fg_init(FGState* s, const double* __restrict__ nrm2, const dou
   s->j = 0;
   s->k = 0;
   s->its = 0;
+  s->stopped = 0;
+  s->guard = 0;
+  s->ctr1 = 0u;  // last-block counters start every cycle at zero
+  s->ctr2 = 0u;
   s->beta = beta;
   s->target = rtol[0] * beta;
   s->res = beta;
@@ -294,6 +298,239 @@ __global__ void k_fg_lincomb(double* __restrict__ x, const double* __restrict__ 
     for (int j = 0; j < k; ++j) acc = fma(ys[j], Z[j * ldz + p], acc);
     x[p] = acc;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Fused CGS2 (one Krylov iteration in three kernels).  Each kernel writes one
+// partial per block and value; the block that finishes last (atomic counter,
+// reset after use) sums the partials in a fixed order, so the results do not
+// depend on block scheduling.  The second projection's update is not stored:
+// ||w''||^2 = ||w'||^2 - ||h2||^2 (V orthonormal) gives the new Hessenberg
+// entry, and w'' = w' - V h2 is formed inside the normalisation kernel.
+
+// Sum `count` values (stride `stride`) of the partials of all blocks; called by
+// the whole last block; out[v] = sum_b partials[b*stride + v].
+__device__ void last_block_reduce(const double* partials, int nblk, int stride, int count,
+                                  double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int v = wid; v < count; v += nw) {
+    double acc = 0.0;
+    for (int b = lane; b < nblk; b += 32) acc += __ldcg(partials + (long long)b * stride + v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[v] = acc;
+  }
+}
+
+__device__ bool arrive_last(unsigned int* ctr) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ctr, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+template <int NV>
+__device__ __forceinline__ void gs1_body(const double* __restrict__ V, long long ldv,
+                                         const double* __restrict__ w, long long L,
+                                         double* __restrict__ partials, double* sh) {
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double wv = w[p];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = fma(V[k * ldv + p], wv, acc[k]);
+  }
+  dev_block_sum<NV>(acc, sh, partials + (long long)blockIdx.x * NV);
+}
+
+__global__ void __launch_bounds__(IRK_BLAS_THREADS)
+k_fg_gs1(const double* __restrict__ V, long long ldv, FGState* s, const double* __restrict__ w,
+         long long L, double* __restrict__ partials, double* __restrict__ h1) {
+  __shared__ double sh[17 * 8];
+  const int nv = s->j + 1;
+  switch (nv) {
+#define IRK_C(N) case N: gs1_body<N>(V, ldv, w, L, partials, sh); break;
+    IRK_DEV_NV_CASES(IRK_C)
+#undef IRK_C
+    default: dev_multi_dot_any(V, ldv, nv, w, L, partials, sh);
+  }
+  if (arrive_last(&s->ctr1)) {
+    last_block_reduce(partials, gridDim.x, nv, nv, h1);
+    if (threadIdx.x == 0) s->ctr1 = 0u;
+  }
+}
+
+// Arnoldi/Givens step of iteration j from h1, h2 (= h2[0..nv)) and ||w'||^2 = h2[nv].
+__device__ void arnoldi_step(FGState* s, const double* h1, const double* h2, int m, int maxit,
+                             double* its_total, cudaGraphConditionalHandle cond) {
+  const int j = s->j;
+  const int nv = j + 1;
+  double* Hc = s->H + j * (IRK_FG_MAXM + 1);
+  double h2sq = 0.0;
+  for (int i = 0; i <= j; ++i) {
+    Hc[i] = h1[i] + h2[i];
+    h2sq = fma(h2[i], h2[i], h2sq);
+  }
+  const double rem = h2[nv] - h2sq;
+  const double hn = rem > 0.0 ? sqrt(rem) : 0.0;
+  for (int i = 0; i < j; ++i) {
+    const double t0 = s->cs[i] * Hc[i] + s->sn[i] * Hc[i + 1];
+    const double t1 = -s->sn[i] * Hc[i] + s->cs[i] * Hc[i + 1];
+    Hc[i] = t0;
+    Hc[i + 1] = t1;
+  }
+  const double hjj = Hc[j];
+  const double den = hypot(hjj, hn);
+  s->cs[j] = den > 0.0 ? hjj / den : 1.0;
+  s->sn[j] = den > 0.0 ? hn / den : 0.0;
+  Hc[j] = den;
+  Hc[j + 1] = 0.0;
+  s->g[j + 1] = -s->sn[j] * s->g[j];
+  s->g[j] = s->cs[j] * s->g[j];
+  const double res = fabs(s->g[j + 1]);
+  s->res = res;
+  s->its += 1;
+  its_total[0] += 1.0;
+  const bool finite = isfinite(hn) && isfinite(res) && isfinite(h2[nv]);
+  if (!finite) {
+    s->status = 2;
+    its_total[1] = 1.0;
+  }
+  if (!finite || res <= s->target || hn <= 1e-300 || j + 1 >= m || s->its >= maxit) {
+    s->k = finite ? j + 1 : 0;
+    s->stopped = 1;
+    cudaGraphSetConditional(cond, 0);
+  } else {
+    s->j = j + 1;
+    s->inv_scale = 1.0 / hn;
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void gs2_body(const double* __restrict__ V, long long ldv,
+                                         const double* __restrict__ h1, double* __restrict__ w,
+                                         long long L, double* __restrict__ partials, double* sh) {
+  double hk[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) hk[k] = __ldcg(h1 + k);
+  double acc[NV + 1];
+#pragma unroll
+  for (int k = 0; k <= NV; ++k) acc[k] = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    double v[NV];
+    double x = w[p];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      v[k] = V[k * ldv + p];
+      x = fma(-hk[k], v[k], x);
+    }
+    w[p] = x;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = fma(v[k], x, acc[k]);
+    acc[NV] = fma(x, x, acc[NV]);
+  }
+  dev_block_sum<NV + 1>(acc, sh, partials + (long long)blockIdx.x * (NV + 1));
+}
+
+__global__ void __launch_bounds__(IRK_BLAS_THREADS)
+k_fg_gs2(const double* __restrict__ V, long long ldv, FGState* s, const double* __restrict__ h1,
+         double* __restrict__ w, long long L, double* __restrict__ partials, double* __restrict__ h2,
+         int m, int maxit, double* its_total, cudaGraphConditionalHandle cond) {
+  __shared__ double sh[17 * 8];
+  const int nv = s->j + 1;
+  switch (nv) {
+#define IRK_C(N) case N: gs2_body<N>(V, ldv, h1, w, L, partials, sh); break;
+    IRK_DEV_NV_CASES(IRK_C)
+#undef IRK_C
+    default: dev_update_dot_any(V, ldv, nv, h1, w, L, 1, partials, sh);
+  }
+  if (arrive_last(&s->ctr2)) {
+    last_block_reduce(partials, gridDim.x, nv + 1, nv + 1, h2);
+    __syncthreads();
+    __threadfence_block();
+    if (threadIdx.x == 0) {
+      s->ctr2 = 0u;
+      arnoldi_step(s, h1, h2, m, maxit, its_total, cond);
+    }
+  }
+}
+
+// V_{j+1} = (w' - V h2) * inv_scale, also written to prec_in (skipped once the
+// loop has stopped); nv = the new j (the basis size of the finished iteration).
+template <int NV>
+__device__ __forceinline__ void next_body(const double* __restrict__ V, long long ldv,
+                                          const double* __restrict__ h2, double sc,
+                                          const double* __restrict__ w, double* __restrict__ vn,
+                                          double* __restrict__ prec_in, long long L) {
+  double hk[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) hk[k] = h2[k];
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    double x = w[p];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) x = fma(-hk[k], V[k * ldv + p], x);
+    x *= sc;
+    vn[p] = x;
+    prec_in[p] = x;
+  }
+}
+
+__global__ void __launch_bounds__(IRK_BLAS_THREADS)
+k_fg_next(const double* __restrict__ V, long long ldv, FGState* s,
+          const double* __restrict__ h2, const double* __restrict__ w, double* Vout,
+          double* __restrict__ prec_in, long long L, int guard_limit,
+          cudaGraphConditionalHandle cond) {
+  // independent bound on the loop: whatever the Arnoldi step decided, the
+  // body runs at most guard_limit times per cycle
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !s->stopped) {
+    if (++s->guard >= guard_limit) {
+      s->status = 3;
+      s->stopped = 1;
+      cudaGraphSetConditional(cond, 0);
+    }
+  }
+  if (s->stopped) return;
+  const int nv = s->j;  // basis size before the new vector
+  const double sc = s->inv_scale;
+  double* vn = Vout + (long long)s->j * ldv;
+  switch (nv) {
+#define IRK_C(N) case N: next_body<N>(V, ldv, h2, sc, w, vn, prec_in, L); return;
+    IRK_DEV_NV_CASES(IRK_C)
+#undef IRK_C
+    default:
+      for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+           p += (long long)gridDim.x * blockDim.x) {
+        double x = w[p];
+        for (int k = 0; k < nv; ++k) x = fma(-h2[k], V[k * ldv + p], x);
+        x *= sc;
+        vn[p] = x;
+        prec_in[p] = x;
+      }
+  }
+}
+
+void launch_fg_gs1(const double* V, long long ldv, FGState* s, const double* w, long long L,
+                   double* partials, double* h1, cudaStream_t st) {
+  k_fg_gs1<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V, ldv, s, w, L, partials, h1);
+}
+void launch_fg_gs2(const double* V, long long ldv, FGState* s, const double* h1, double* w,
+                   long long L, double* partials, double* h2, int m, int maxit, double* its_total,
+                   cudaGraphConditionalHandle cond, cudaStream_t st) {
+  k_fg_gs2<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V, ldv, s, h1, w, L, partials, h2, m, maxit,
+                                                        its_total, cond);
+}
+void launch_fg_next(const double* V_, long long ldv, FGState* s, const double* h2,
+                    const double* w, double* V, double* prec_in, long long L, int guard_limit,
+                    cudaGraphConditionalHandle cond, cudaStream_t st) {
+  k_fg_next<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V_, ldv, s, h2, w, V, prec_in, L,
+                                                        guard_limit, cond);
 }
 
 // ---------------------------------------------------------------------------

@@ -99,6 +99,9 @@ struct FGState {
   int k;          // columns of the final least-squares problem
   int its;        // iterations of this cycle
   int status;     // 0 ok, 2 non-finite
+  int stopped;    // the loop has ended (set by the Arnoldi step)
+  int guard;      // body executions this cycle (independent loop bound)
+  unsigned int ctr1, ctr2;  // last-block counters of the fused CGS2 kernels
   double beta, target, res, inv_scale;
   double g[IRK_FG_MAXM + 1];
   double cs[IRK_FG_MAXM], sn[IRK_FG_MAXM], y[IRK_FG_MAXM];
@@ -160,6 +163,16 @@ void launch_fg_arnoldi(FGState* s, const double* h1, const double* h2, const dou
                        int maxit, double* its_total, cudaGraphConditionalHandle cond,
                        cudaStream_t st);
 void launch_fg_solve(FGState* s, cudaStream_t st);
+// fused CGS2 iteration: dots (+reduce), update+dots (+reduce, Arnoldi step),
+// next basis vector (second update fused with the normalisation)
+void launch_fg_gs1(const double* V, long long ldv, FGState* s, const double* w, long long L,
+                   double* partials, double* h1, cudaStream_t st);
+void launch_fg_gs2(const double* V, long long ldv, FGState* s, const double* h1, double* w,
+                   long long L, double* partials, double* h2, int m, int maxit, double* its_total,
+                   cudaGraphConditionalHandle cond, cudaStream_t st);
+void launch_fg_next(const double* V_, long long ldv, FGState* s, const double* h2,
+                    const double* w, double* V, double* prec_in, long long L, int guard_limit,
+                    cudaGraphConditionalHandle cond, cudaStream_t st);
 void launch_fg_lincomb(double* x, const double* Z, long long ldz, const FGState* s, long long L,
                        cudaStream_t st);
 

@@ -438,11 +438,13 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
                        h->cfg.mg_coarse_sweeps, project_mean, vrow[c], bl[c], lc.w, h->st);
       cur[c] = lc.w;
     } else {
-      // shift-dominated coarsest level: damped Jacobi to a 2e-2 reduction of
-      // its slowest mode (factor 1 - omega sigma / D), 2..12 sweeps
+      // shift-dominated coarsest level (sigma >= D/2): undamped Jacobi, whose
+      // iteration matrix has norm <= 1 - sigma/D <= 1/2 there, swept to a
+      // 2e-2 reduction, 2..12 sweeps
       const double hc = lc.d.h;
       const double D = sigma + 2.0 * dim * cdiff / (hc * hc);
-      const double rho = 1.0 - om * sigma / D;
+      const double omc = (sigma >= 0.5 * D) ? 1.0 : om;
+      const double rho = 1.0 - omc * sigma / D;
       int sweeps = (rho > 0 && rho < 1) ? (int)std::ceil(std::log(2e-2) / std::log(rho)) : 2;
       sweeps = std::max(2, std::min(sweeps, 12));
       cur[c] = lc.w;
@@ -451,7 +453,7 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
         const int first = (sw == 0);
         ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, c, first ? 2.0 * ncomp : 3.0 * ncomp + velf),
                      (double)ncomp * lc.d.npts * (first ? 1 : smooth_flops_pp));
-        launch_mg_smooth(prec, dim, kind, lc.d, ncomp, sigma, cadv, cdiff, om, vrow[c], bl[c],
+        launch_mg_smooth(prec, dim, kind, lc.d, ncomp, sigma, cadv, cdiff, omc, vrow[c], bl[c],
                          cur[c], first ? cur[c] : alt[c], first, h->st);
         if (!first) std::swap(cur[c], alt[c]);
       }
@@ -890,40 +892,18 @@ irk_status build_fg_graph(irk_handle* h, double dt, int blk) {
       }
       double* dh1 = h->dscal;
       double* dh2 = h->dscal + 64;
-      double* dnr = h->dscal + 130;
-      const int mcap = h->m + 2;
       {
         ProfScope ps(h, P_GS_DOT, 0, 0);
-        launch_fg_multi_dot(h->V, ldv, fs, h->w, Lb, h->partials, h->st);
-      }
-      {
-        ProfScope ps(h, P_REDUCE, 0, 0);
-        launch_fg_reduce(h->partials, nb, fs, 0, mcap, dh1, h->st);
+        launch_fg_gs1(h->V, ldv, fs, h->w, Lb, h->partials, dh1, h->st);
       }
       {
         ProfScope ps(h, P_GS_UPDATE, 0, 0);
-        launch_fg_update_dot(h->V, ldv, fs, dh1, h->w, Lb, 1, h->partials, h->st);
-      }
-      {
-        ProfScope ps(h, P_REDUCE, 0, 0);
-        launch_fg_reduce(h->partials, nb, fs, 1, mcap, dh2, h->st);
-      }
-      {
-        ProfScope ps(h, P_GS_UPDATE, 0, 0);
-        launch_fg_update_dot(h->V, ldv, fs, dh2, h->w, Lb, 0, h->partials, h->st);
-      }
-      {
-        ProfScope ps(h, P_REDUCE, 0, 0);
-        launch_fg_reduce(h->partials, nb, fs, 2, 1, dnr, h->st);
+        launch_fg_gs2(h->V, ldv, fs, dh1, h->w, Lb, h->partials, dh2, h->m, h->cfg.krylov_maxit,
+                      h->dscal + 320 + 2 * blk, cond, h->st);
       }
       {
         ProfScope ps(h, P_SCALE, 0, 0);
-        launch_fg_arnoldi(fs, dh1, dh2, dnr, h->m, h->cfg.krylov_maxit, h->dscal + 320 + 2 * blk,
-                          cond, h->st);
-      }
-      {
-        ProfScope ps(h, P_SCALE, 16.0 * Lb, (double)Lb);
-        launch_fg_scale(h->w, fs, h->V, ldv, h->prec_in, Lb, h->st);
+        launch_fg_next(h->V, ldv, fs, dh2, h->w, h->V, h->prec_in, Lb, h->m + 1, cond, h->st);
       }
       body_launches = h->stats.kernel_launches - l0;
       body_vcycles = h->stats.vcycles - v0;
