@@ -282,6 +282,38 @@ __device__ __forceinline__ void term_apply(const GridDesc& g, const OpTerm& t, c
       op = -(__ldg(t.combo + nb.e) * xe - __ldg(t.combo + nb.w) * xw) * g.inv2h;
     if (t.lin != 0.0) op = fma(t.lin * g.nu, (xe - 2.0 * xc + xw) * g.invh2, op);
     acc[0] += t.m * xc - dt * op;
+  } else if (OP == IRK_OP_BURGERS_2D && t.combo && t.lin != 0.0) {
+    // Diagonal term in coefficient form.  For component u:
+    //   m x_u - dt (-(x_u ub_x + ub Dx x_u + x_v ub_y + vb Dy x_u) + lin nu L x_u)
+    //   = (m + dt ub_x + 4 k) x_u + dt ub_y x_v + sum_K c_K x_u(K),
+    // with k = dt lin nu / h^2, c_E/W = +-dt ub/(2h) - k, c_N/S = +-dt vb/(2h) - k;
+    // the neighbour coefficients are shared by both components.
+    const double* bu = t.combo;
+    const double* bv = t.combo + npts;
+    const double ax = dt * g.inv2h * __ldg(bu + nb.c), ay = dt * g.inv2h * __ldg(bv + nb.c);
+    const double kd = dt * t.lin * g.nu * g.invh2;
+    const double ce = ax - kd, cw = -ax - kd, cn = ay - kd, cs = -ay - kd;
+    const double dth = dt * g.inv2h;
+    const double bux = dth * (__ldg(bu + nb.e) - __ldg(bu + nb.w));
+    const double buy = dth * (__ldg(bu + nb.n) - __ldg(bu + nb.s));
+    const double bvx = dth * (__ldg(bv + nb.e) - __ldg(bv + nb.w));
+    const double bvy = dth * (__ldg(bv + nb.n) - __ldg(bv + nb.s));
+    const double cc = t.m + 4.0 * kd;
+    const double* xu = t.x;
+    const double* xv = t.x + npts;
+    const double uc = __ldg(xu + nb.c), vc = __ldg(xv + nb.c);
+    double yu = fma(cc + bux, uc, buy * vc);
+    yu = fma(ce, __ldg(xu + nb.e), yu);
+    yu = fma(cw, __ldg(xu + nb.w), yu);
+    yu = fma(cn, __ldg(xu + nb.n), yu);
+    yu = fma(cs, __ldg(xu + nb.s), yu);
+    double yv = fma(cc + bvy, vc, bvx * uc);
+    yv = fma(ce, __ldg(xv + nb.e), yv);
+    yv = fma(cw, __ldg(xv + nb.w), yv);
+    yv = fma(cn, __ldg(xv + nb.n), yv);
+    yv = fma(cs, __ldg(xv + nb.s), yv);
+    acc[0] += yu;
+    acc[1] += yv;
   } else if (OP == IRK_OP_BURGERS_2D) {
     const double* xu = t.x;
     const double* xv = t.x + npts;
