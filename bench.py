@@ -72,6 +72,20 @@ def dist_setup(args):
     return rank, world
 
 
+def job_throughput(local_ms: float, steps_per_rank: int, world: int):
+    """Whole-job steps/s: the steps of all ranks over the slowest rank's time
+    (max over ranks, then a barrier).  Returns (steps/s, max time in ms)."""
+    t = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt[0])
+        dist.barrier()
+    return steps_per_rank * world / (t / 1e3), t
+
+
 # ---------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
@@ -271,15 +285,7 @@ def run_ours(args, rank, world):
     kstats = B.irk_kernel_stats(h)
     B.irk_destroy(h)
     step_ms = sum(ms) / len(ms)
-    local_time = sum(ms)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([local_time], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        local_time = float(tt[0])
-        dist.barrier()
-    total_steps = args.steps * world
-    value = total_steps / (local_time / 1e3)
+    value, local_time = job_throughput(sum(ms), args.steps, world)
 
     # ---- roofline of the dominant kernel class (CUDA-event time inside the timed region)
     dom = max(kstats, key=lambda k: k["ms"])

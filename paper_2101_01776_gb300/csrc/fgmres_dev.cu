@@ -3,12 +3,13 @@
 //
 // The iteration index j, the Hessenberg matrix, the Givens rotations and the
 // rotated right-hand side live in an FGState block in device memory.  The
-// basis kernels read j from there (so one captured kernel serves every j),
-// k_fg_arnoldi closes an iteration (Hessenberg column, rotations, residual
-// estimate) and ends the loop through the conditional handle of a CUDA-graph
-// WHILE node once the block has converged, lost its basis, or used m
-// iterations; the loop therefore runs at most m times.  The arithmetic is the
-// one of the host path (CGS2, Givens, back substitution), in FP64.
+// basis kernels read j from there (so one captured kernel serves every j).
+// The last block of k_fg_gs2 closes an iteration (Hessenberg column,
+// rotations, residual estimate) and ends the loop through the conditional
+// handle of a CUDA-graph WHILE node once the block has converged, lost its
+// basis, or used m iterations; k_fg_next also bounds the loop independently.
+// The arithmetic is the one of the host path (CGS2, Givens, back
+// substitution), in FP64.
 #include "irk_internal.h"
 
 namespace irk {
@@ -31,58 +32,6 @@ __device__ __forceinline__ void dev_block_sum(double (&v)[NV], double* sh, doubl
     double r = 0.0;
     for (int w = 0; w < nw; ++w) r += sh[threadIdx.x * 8 + w];
     out[threadIdx.x] = r;
-  }
-}
-
-template <int NV>
-__device__ __forceinline__ void dev_multi_dot(const double* __restrict__ V, long long ldv,
-                                              const double* __restrict__ w, long long L,
-                                              double* __restrict__ partials, double* sh) {
-  double acc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
-       p += (long long)gridDim.x * blockDim.x) {
-    const double wv = w[p];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = fma(V[k * ldv + p], wv, acc[k]);
-  }
-  dev_block_sum<NV>(acc, sh, partials + (long long)blockIdx.x * NV);
-}
-
-template <int NV>
-__device__ __forceinline__ void dev_update_dot(const double* __restrict__ V, long long ldv,
-                                               const double* __restrict__ h,
-                                               double* __restrict__ w, long long L,
-                                               int with_dots, double* __restrict__ partials,
-                                               double* sh) {
-  double hk[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) hk[k] = h[k];
-  double acc[NV + 1];
-#pragma unroll
-  for (int k = 0; k <= NV; ++k) acc[k] = 0.0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
-       p += (long long)gridDim.x * blockDim.x) {
-    double v[NV];
-    double x = w[p];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      v[k] = V[k * ldv + p];
-      x = fma(-hk[k], v[k], x);
-    }
-    w[p] = x;
-    if (with_dots) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k) acc[k] = fma(v[k], x, acc[k]);
-    }
-    acc[NV] = fma(x, x, acc[NV]);
-  }
-  if (with_dots) {
-    dev_block_sum<NV + 1>(acc, sh, partials + (long long)blockIdx.x * (NV + 1));
-  } else {
-    double nr[1] = {acc[NV]};
-    dev_block_sum<1>(nr, sh, partials + (long long)blockIdx.x * (NV + 1) + NV);
   }
 }
 
@@ -139,60 +88,6 @@ __device__ void dev_update_dot_any(const double* __restrict__ V, long long ldv, 
 
 #define IRK_DEV_NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
-__global__ void __launch_bounds__(IRK_BLAS_THREADS)
-k_fg_multi_dot(const double* __restrict__ V, long long ldv, const FGState* __restrict__ s,
-               const double* __restrict__ w, long long L, double* __restrict__ partials) {
-  __shared__ double sh[17 * 8];
-  const int nv = s->j + 1;
-  switch (nv) {
-#define IRK_C(N) case N: dev_multi_dot<N>(V, ldv, w, L, partials, sh); return;
-    IRK_DEV_NV_CASES(IRK_C)
-#undef IRK_C
-    default: dev_multi_dot_any(V, ldv, nv, w, L, partials, sh);
-  }
-}
-
-__global__ void __launch_bounds__(IRK_BLAS_THREADS)
-k_fg_update_dot(const double* __restrict__ V, long long ldv, const FGState* __restrict__ s,
-                const double* __restrict__ h, double* __restrict__ w, long long L, int with_dots,
-                double* __restrict__ partials) {
-  __shared__ double sh[17 * 8];
-  const int nv = s->j + 1;
-  switch (nv) {
-#define IRK_C(N) case N: dev_update_dot<N>(V, ldv, h, w, L, with_dots, partials, sh); return;
-    IRK_DEV_NV_CASES(IRK_C)
-#undef IRK_C
-    default: dev_update_dot_any(V, ldv, nv, h, w, L, with_dots, partials, sh);
-  }
-}
-
-// Sum the per-block partials in a fixed order, with nv = j + 1 from s:
-// mode 0 (multi_dot):       out[v] = sum_b partials[b*nv + v],         v < nv
-// mode 1 (update with dots): out[v] = sum_b partials[b*(nv+1) + v],    v < nv + 1
-// mode 2 (update, norm):    out[0] = sum_b partials[b*(nv+1) + nv]
-__global__ void k_fg_reduce(const double* __restrict__ partials, int nblk,
-                            const FGState* __restrict__ s, int mode, double* __restrict__ out) {
-  __shared__ double sh[32];
-  const int nv = s->j + 1;
-  const int v = blockIdx.x;
-  const int count = mode == 0 ? nv : (mode == 1 ? nv + 1 : 1);
-  if (v >= count) return;
-  const int stride = mode == 0 ? nv : nv + 1;
-  const int off = mode == 2 ? nv : 0;
-  double acc = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += partials[(long long)b * stride + v + off];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) sh[wid] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double r = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
-    out[v] = r;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Start of a cycle: beta = ||b|| (from its reduced square), g = beta e_1,
 // first basis scale 1/beta; an empty or non-finite right-hand side ends the
@@ -233,45 +128,6 @@ __global__ void k_fg_scale(const double* __restrict__ w, const FGState* __restri
     const double x = w[p] * sc;
     vj[p] = x;
     prec_in[p] = x;
-  }
-}
-
-// Close iteration j: Hessenberg column from the two CGS passes, rotations,
-// residual estimate; stop or advance.
-__global__ void k_fg_arnoldi(FGState* s, const double* __restrict__ h1, const double* __restrict__ h2,
-                             const double* __restrict__ nrm2, int m, int maxit, double* its_total,
-                             cudaGraphConditionalHandle cond) {
-  const int j = s->j;
-  double* Hc = s->H + j * (IRK_FG_MAXM + 1);  // column j, rows 0..j+1
-  for (int i = 0; i <= j; ++i) Hc[i] = h1[i] + h2[i];
-  const double hn = sqrt(fmax(nrm2[0], 0.0));
-  for (int i = 0; i < j; ++i) {
-    const double t0 = s->cs[i] * Hc[i] + s->sn[i] * Hc[i + 1];
-    const double t1 = -s->sn[i] * Hc[i] + s->cs[i] * Hc[i + 1];
-    Hc[i] = t0;
-    Hc[i + 1] = t1;
-  }
-  const double hjj = Hc[j];
-  const double den = hypot(hjj, hn);
-  s->cs[j] = den > 0.0 ? hjj / den : 1.0;
-  s->sn[j] = den > 0.0 ? hn / den : 0.0;
-  Hc[j] = den;
-  Hc[j + 1] = 0.0;
-  s->g[j + 1] = -s->sn[j] * s->g[j];
-  s->g[j] = s->cs[j] * s->g[j];
-  const double res = fabs(s->g[j + 1]);
-  s->res = res;
-  s->its += 1;
-  its_total[0] += 1.0;
-  if (!isfinite(hn) || !isfinite(s->g[j + 1])) its_total[1] = 1.0;  // non-finite flag
-  const bool finite = isfinite(hn) && isfinite(res);
-  if (!finite) s->status = 2;
-  if (!finite || res <= s->target || hn <= 1e-300 || j + 1 >= m || s->its >= maxit) {
-    s->k = finite ? j + 1 : 0;
-    cudaGraphSetConditional(cond, 0);
-  } else {
-    s->j = j + 1;
-    s->inv_scale = 1.0 / hn;
   }
 }
 
@@ -541,25 +397,6 @@ void launch_fg_init(FGState* s, const double* nrm2, const double* rtol,
 void launch_fg_scale(const double* w, const FGState* s, double* V, long long ldv, double* prec_in,
                      long long L, cudaStream_t st) {
   k_fg_scale<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(w, s, V, ldv, prec_in, L);
-}
-void launch_fg_multi_dot(const double* V, long long ldv, const FGState* s, const double* w,
-                         long long L, double* partials, cudaStream_t st) {
-  k_fg_multi_dot<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V, ldv, s, w, L, partials);
-}
-void launch_fg_update_dot(const double* V, long long ldv, const FGState* s, const double* h,
-                          double* w, long long L, int with_dots, double* partials,
-                          cudaStream_t st) {
-  k_fg_update_dot<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V, ldv, s, h, w, L, with_dots,
-                                                               partials);
-}
-void launch_fg_reduce(const double* partials, int nblk, const FGState* s, int mode, int max_count,
-                      double* out, cudaStream_t st) {
-  k_fg_reduce<<<max_count, 256, 0, st>>>(partials, nblk, s, mode, out);
-}
-void launch_fg_arnoldi(FGState* s, const double* h1, const double* h2, const double* nrm2, int m,
-                       int maxit, double* its_total, cudaGraphConditionalHandle cond,
-                       cudaStream_t st) {
-  k_fg_arnoldi<<<1, 1, 0, st>>>(s, h1, h2, nrm2, m, maxit, its_total, cond);
 }
 void launch_fg_solve(FGState* s, cudaStream_t st) { k_fg_solve<<<1, 1, 0, st>>>(s); }
 void launch_fg_lincomb(double* x, const double* Z, long long ldz, const FGState* s, long long L,

@@ -152,16 +152,6 @@ void launch_fg_init(FGState* s, const double* nrm2, const double* rtol,
                     cudaGraphConditionalHandle cond, cudaStream_t st);
 void launch_fg_scale(const double* w, const FGState* s, double* V, long long ldv, double* prec_in,
                      long long L, cudaStream_t st);
-void launch_fg_multi_dot(const double* V, long long ldv, const FGState* s, const double* w,
-                         long long L, double* partials, cudaStream_t st);
-void launch_fg_update_dot(const double* V, long long ldv, const FGState* s, const double* h,
-                          double* w, long long L, int with_dots, double* partials,
-                          cudaStream_t st);
-void launch_fg_reduce(const double* partials, int nblk, const FGState* s, int mode, int max_count,
-                      double* out, cudaStream_t st);
-void launch_fg_arnoldi(FGState* s, const double* h1, const double* h2, const double* nrm2, int m,
-                       int maxit, double* its_total, cudaGraphConditionalHandle cond,
-                       cudaStream_t st);
 void launch_fg_solve(FGState* s, cudaStream_t st);
 // fused CGS2 iteration: dots (+reduce), update+dots (+reduce, Arnoldi step),
 // next basis vector (second update fused with the normalisation)

@@ -792,9 +792,9 @@ void drop_fg_graphs(irk_handle* h) {
 
 // One restart cycle of FGMRES on block blk as a single CUDA graph:
 //   prefix  z = rhs_blk - U dk_hat (Eq. D+U), x = 0, beta = ||z||, V_0 = z/beta
-//   WHILE   z_j = L_P v_j; w = D z_j (Z_j = z_j); CGS2; Arnoldi/Givens step
+//   WHILE   z_j = L_P v_j; w = D z_j (Z_j = z_j); fused CGS2 + Arnoldi/Givens step
 //   suffix  y = R^{-1} g; x += Z y
-// The loop ends on the device (k_fg_arnoldi) after at most m iterations.
+// The loop ends on the device (Arnoldi step of k_fg_gs2) after at most m iterations.
 irk_status build_fg_graph(irk_handle* h, double dt, int blk) {
   const int a0 = h->tab.bstart[blk], bs = h->tab.bsize[blk];
   const long long Lb = (long long)bs * h->L;
