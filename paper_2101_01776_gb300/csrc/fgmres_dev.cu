@@ -94,7 +94,7 @@ __device__ void dev_update_dot_any(const double* __restrict__ V, long long ldv, 
 // loop before it starts.
 __global__ void k_fg_init(FGState* s, const double* __restrict__ nrm2, const double* __restrict__ rtol,
                           cudaGraphConditionalHandle cond) {
-  const double beta = sqrt(fmax(nrm2[0], 0.0));
+  const double beta = isfinite(nrm2[0]) ? sqrt(fmax(nrm2[0], 0.0)) : nrm2[0];
   s->j = 0;
   s->k = 0;
   s->its = 0;
@@ -114,6 +114,7 @@ __global__ void k_fg_init(FGState* s, const double* __restrict__ nrm2, const dou
   } else {
     s->status = 0;
     s->inv_scale = 1.0 / beta;
+    cudaGraphSetConditional(cond, 1);  // (re)open the loop for this cycle
   }
 }
 
@@ -387,6 +388,78 @@ void launch_fg_next(const double* V_, long long ldv, FGState* s, const double* h
                     cudaGraphConditionalHandle cond, cudaStream_t st) {
   k_fg_next<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V_, ldv, s, h2, w, V, prec_in, L,
                                                         guard_limit, cond);
+}
+
+// ---------------------------------------------------------------------------
+// Newton control on the device (whole-step graph).  State nw[]:
+//   0 ||F(0)||, 1 ||F||, 2 ||F||/||F(0)||, 3 previous ||F||, 4 updates done,
+//   5 status (0 ok, IRK_ERR_NEWTON_DIVERGED, IRK_ERR_NEWTON_MAXIT).
+// The tests and the forcing term are those of the host loop: stop on a
+// non-finite residual, at the tolerance, at the iteration limit, or on growth
+// by 1e3; otherwise eta = max(min(krylov_rtol, rel) [1e-3 rel if the last
+// update gained less than 2x], 0.2 newton_rtol / rel, 1e-13).
+__device__ double forcing_term(double rel, double fn, double prev, int it, double newton_rtol,
+                               double krylov_rtol) {
+  double eta = fmin(krylov_rtol, rel);
+  if (it > 0 && prev > 0.0 && fn > 0.5 * prev) eta = fmin(eta, 1e-3 * rel);
+  eta = fmax(eta, 0.2 * newton_rtol / rel);
+  return fmax(eta, 1e-13);
+}
+
+__global__ void k_newton_first(double* nw, const double* __restrict__ f2, double* rtol_slot,
+                               double newton_rtol, double krylov_rtol,
+                               cudaGraphConditionalHandle cond) {
+  // f2 is tested before any clamp: fmax(NaN, 0) would read as zero
+  const double f0 = isfinite(f2[0]) ? sqrt(fmax(f2[0], 0.0)) : f2[0];
+  nw[0] = f0;
+  nw[1] = f0;
+  nw[2] = f0 > 0.0 ? 1.0 : 0.0;
+  nw[3] = f0;
+  nw[4] = 0.0;
+  nw[5] = 0.0;
+  if (!isfinite(f0)) {
+    nw[5] = (double)IRK_ERR_NEWTON_DIVERGED;
+    cudaGraphSetConditional(cond, 0);
+  } else if (f0 == 0.0) {
+    cudaGraphSetConditional(cond, 0);  // k = 0 solves the stage equations
+  } else {
+    rtol_slot[0] = forcing_term(1.0, f0, f0, 0, newton_rtol, krylov_rtol);
+    cudaGraphSetConditional(cond, 1);
+  }
+}
+
+__global__ void k_newton_ctl(double* nw, const double* __restrict__ f2, double* rtol_slot,
+                             double newton_rtol, int maxit, double krylov_rtol,
+                             cudaGraphConditionalHandle cond) {
+  const double fn = isfinite(f2[0]) ? sqrt(fmax(f2[0], 0.0)) : f2[0];
+  const int it = (int)nw[4] + 1;
+  const double rel = fn / nw[0];
+  nw[1] = fn;
+  nw[2] = rel;
+  nw[4] = (double)it;
+  int stop = 1;
+  if (!isfinite(fn)) nw[5] = (double)IRK_ERR_NEWTON_DIVERGED;
+  else if (rel <= newton_rtol) nw[5] = 0.0;
+  else if (it >= maxit) nw[5] = (double)IRK_ERR_NEWTON_MAXIT;
+  else if (rel > 1e3) nw[5] = (double)IRK_ERR_NEWTON_DIVERGED;
+  else stop = 0;
+  if (stop) {
+    cudaGraphSetConditional(cond, 0);
+  } else {
+    rtol_slot[0] = forcing_term(rel, fn, nw[3], it, newton_rtol, krylov_rtol);
+    nw[3] = fn;
+  }
+}
+
+void launch_newton_first(double* nw, const double* f2, double* rtol_slot, double newton_rtol,
+                         double krylov_rtol, cudaGraphConditionalHandle cond, cudaStream_t st) {
+  k_newton_first<<<1, 1, 0, st>>>(nw, f2, rtol_slot, newton_rtol, krylov_rtol, cond);
+}
+
+void launch_newton_ctl(double* nw, const double* f2, double* rtol_slot, double newton_rtol,
+                       int maxit, double krylov_rtol, cudaGraphConditionalHandle cond,
+                       cudaStream_t st) {
+  k_newton_ctl<<<1, 1, 0, st>>>(nw, f2, rtol_slot, newton_rtol, maxit, krylov_rtol, cond);
 }
 
 // ---------------------------------------------------------------------------

@@ -96,6 +96,13 @@ struct irk_handle {
   long long fg_fixed_launches[IRK_MAXS] = {}, fg_body_launches[IRK_MAXS] = {};
   int fg_body_vcycles[IRK_MAXS] = {};
   double fg_seen_its[IRK_MAXS] = {};
+  // whole-step graph (Newton loop on the device)
+  cudaStream_t st_aux2 = nullptr;
+  cudaGraphExec_t stepexec = nullptr;
+  double step_dt = 0.0;
+  bool step_failed = false;
+  long long step_fixed_launches = 0, step_newton_launches = 0;
+  double* nws = nullptr;  // Newton state: dscal[400..]
   double* hbuf = nullptr;  // pinned host
   int nparts = 0;
 
@@ -722,8 +729,9 @@ void set_stage_args(irk_handle* h, StageStateArgs& a, double dt, const double* u
 }
 
 // stage states + residual + ||F|| (blocking read of the norm)
-irk_status eval_residual(irk_handle* h, double t_n, double dt, const double* K, double* rhs,
-                         double* Fraw, bool combos, double* fnorm) {
+// Stage states, residual and ||F||^2 (to dscal[201]); launches only.
+void launch_eval_residual(irk_handle* h, double t_n, double dt, const double* K, double* rhs,
+                          double* Fraw, bool combos) {
   StageStateArgs sa;
   set_stage_args(h, sa, dt, h->u, K, h->Y, combos ? h->combos : nullptr);
   {
@@ -753,6 +761,11 @@ irk_status eval_residual(irk_handle* h, double t_n, double dt, const double* K, 
     ProfScope ps(h, P_REDUCE, 8.0 * nb, nb);
     launch_reduce(h->partials, nb, 1, 1, h->dscal + 201, h->st);
   }
+}
+
+irk_status eval_residual(irk_handle* h, double t_n, double dt, const double* K, double* rhs,
+                         double* Fraw, bool combos, double* fnorm) {
+  launch_eval_residual(h, t_n, dt, K, rhs, Fraw, combos);
   // the norm, plus (slots 320..) the device-FGMRES iteration counters
   TRY(sync_read(h, h->dscal + 201, 140));
   *fnorm = std::sqrt(h->hbuf[0]);
@@ -790,54 +803,62 @@ void drop_fg_graphs(irk_handle* h) {
     }
 }
 
-// One restart cycle of FGMRES on block blk as a single CUDA graph:
+// One restart cycle of FGMRES on block blk, captured into the graph that
+// stream `outer` is capturing:
 //   prefix  z = rhs_blk - U dk_hat (Eq. D+U), x = 0, beta = ||z||, V_0 = z/beta
 //   WHILE   z_j = L_P v_j; w = D z_j (Z_j = z_j); fused CGS2 + Arnoldi/Givens step
 //   suffix  y = R^{-1} g; x += Z y
-// The loop ends on the device (Arnoldi step of k_fg_gs2) after at most m iterations.
-irk_status build_fg_graph(irk_handle* h, double dt, int blk) {
+// The loop body is captured on stream `inner`.  The loop ends on the device
+// (Arnoldi step of k_fg_gs2) after at most m iterations.
+struct CapCounts {
+  long long fixed = 0, body = 0;
+  int vcycles = 0;
+};
+
+cudaError_t capture_block_solve(irk_handle* h, double dt, int blk, cudaStream_t outer,
+                                cudaStream_t inner, CapCounts* cc) {
   const int a0 = h->tab.bstart[blk], bs = h->tab.bsize[blk];
   const long long Lb = (long long)bs * h->L;
   const long long ldv = Lb;
-  const int nb = blas_blocks(Lb);
   FGState* fs = h->fgs + blk;
   double* x = h->yhat + (long long)a0 * h->L;
   const double* b = h->rhs + (long long)a0 * h->L;
-  const irk_stats saved = h->stats;
+  cudaStream_t saved_st = h->st;
+  h->st = outer;
+  const long long l_start = h->stats.kernel_launches;
+  // the conditional handle lives in the graph being captured on `outer`
+  cudaStreamCaptureStatus cst;
   cudaGraph_t G = nullptr;
-  cudaGraphConditionalHandle cond;
-  CK(cudaGraphCreate(&G, 0));
-  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, G, 1, cudaGraphCondAssignDefault);
-  if (e != cudaSuccess) { cudaGraphDestroy(G); cudaGetLastError(); return IRK_ERR_CUDA; }
-  e = cudaStreamBeginCaptureToGraph(h->st, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) { cudaGraphDestroy(G); cudaGetLastError(); return IRK_ERR_CUDA; }
+  cudaError_t e = cudaStreamGetCaptureInfo(outer, &cst, nullptr, &G, nullptr, nullptr, nullptr);
+  cudaGraphConditionalHandle cond = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, G, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) { h->st = saved_st; return e; }
   // ---- prefix
   if (blk < h->tab.nblk - 1) {
     upper_coupling(h, dt, blk, h->zbuf);
     b = h->zbuf;
   }
-  cudaMemsetAsync(x, 0, sizeof(double) * Lb, h->st);
+  cudaMemsetAsync(x, 0, sizeof(double) * Lb, outer);
   {
     ProfScope ps(h, P_NORM, 8.0 * Lb, 2.0 * Lb);
-    launch_norm2(b, Lb, h->partials, h->st);
+    launch_norm2(b, Lb, h->partials, outer);
   }
   {
-    ProfScope ps(h, P_REDUCE, 8.0 * blas_blocks(Lb), blas_blocks(Lb));
-    launch_reduce(h->partials, blas_blocks(Lb), 1, 1, h->dscal + 310, h->st);
+    ProfScope ps(h, P_REDUCE, 0, 0);
+    launch_reduce(h->partials, blas_blocks(Lb), 1, 1, h->dscal + 310, outer);
   }
   {
     ProfScope ps(h, P_SCALE, 0, 0);
-    launch_fg_init(fs, h->dscal + 310, h->dscal + 300, cond, h->st);
+    launch_fg_init(fs, h->dscal + 310, h->dscal + 300, cond, outer);
   }
   {
     ProfScope ps(h, P_SCALE, 16.0 * Lb, (double)Lb);
-    launch_fg_scale(b, fs, h->V, ldv, h->prec_in, Lb, h->st);
+    launch_fg_scale(b, fs, h->V, ldv, h->prec_in, Lb, outer);
   }
   // ---- WHILE node after the prefix
-  cudaStreamCaptureStatus cst;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  e = cudaStreamGetCaptureInfo(h->st, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+  e = cudaStreamGetCaptureInfo(outer, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
   cudaGraphNode_t wnode = nullptr;
   cudaGraph_t body = nullptr;
   if (e == cudaSuccess) {
@@ -849,92 +870,102 @@ irk_status build_fg_graph(irk_handle* h, double dt, int blk) {
     e = cudaGraphAddNode(&wnode, G, deps, nullptr, ndeps, &np);
     if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
   }
-  const long long prefix_launches = h->stats.kernel_launches - saved.kernel_launches;
-  long long body_launches = 0;
-  int body_vcycles = 0;
-  if (e == cudaSuccess) {
-    // capture the loop body on the auxiliary stream
-    e = cudaStreamBeginCaptureToGraph(h->st_aux, body, nullptr, nullptr, 0,
+  cc->fixed += h->stats.kernel_launches - l_start;
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(inner, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      cudaStream_t main = h->st;
-      h->st = h->st_aux;
-      const long long l0 = h->stats.kernel_launches;
-      const int v0 = h->stats.vcycles;
-      block_prec(h, dt, blk, h->prec_in, h->prec_out);
-      {
-        // w = D z_j with z_j = prec_out; Z_j = z_j (j read on the device)
-        const int s = h->s;
-        StageOpArgs a;
-        memset(&a, 0, sizeof(a));
-        a.nrow = bs;
-        a.dt = dt;
-        for (int rr = 0; rr < bs; ++rr) {
-          const int r = a0 + rr;
-          OpRow& row = a.row[rr];
-          row.y = h->w + (long long)rr * h->L;
-          row.sigma = 1;
-          for (int qq = 0; qq < bs; ++qq) {
-            const int q = a0 + qq;
-            OpTerm& t = row.t[row.nterm++];
-            t.x = h->prec_out + (long long)qq * h->L;
-            t.combo = keep_coupling(h, r, q) ? combo_ptr(h, r, q) : nullptr;
-            t.m = h->tab.R[r * s + q];
-            t.lin = (r == q) ? 1.0 : 0.0;
-          }
+  if (e == cudaSuccess) {
+    h->st = inner;
+    const long long l0 = h->stats.kernel_launches;
+    const int v0 = h->stats.vcycles;
+    block_prec(h, dt, blk, h->prec_in, h->prec_out);
+    {
+      // w = D z_j with z_j = prec_out; Z_j = z_j (j read on the device)
+      const int s = h->s;
+      StageOpArgs a;
+      memset(&a, 0, sizeof(a));
+      a.nrow = bs;
+      a.dt = dt;
+      for (int rr = 0; rr < bs; ++rr) {
+        const int r = a0 + rr;
+        OpRow& row = a.row[rr];
+        row.y = h->w + (long long)rr * h->L;
+        row.sigma = 1;
+        for (int qq = 0; qq < bs; ++qq) {
+          const int q = a0 + qq;
+          OpTerm& t = row.t[row.nterm++];
+          t.x = h->prec_out + (long long)qq * h->L;
+          t.combo = keep_coupling(h, r, q) ? combo_ptr(h, r, q) : nullptr;
+          t.m = h->tab.R[r * s + q];
+          t.lin = (r == q) ? 1.0 : 0.0;
         }
-        a.copy_dst = h->Z;
-        a.copy_src = h->prec_out;
-        a.copy_len = Lb;
-        a.copy_jdev = &fs->j;
-        a.copy_ldv = ldv;
-        run_stage_op(h, a);
       }
-      double* dh1 = h->dscal;
-      double* dh2 = h->dscal + 64;
-      {
-        ProfScope ps(h, P_GS_DOT, 0, 0);
-        launch_fg_gs1(h->V, ldv, fs, h->w, Lb, h->partials, dh1, h->st);
-      }
-      {
-        ProfScope ps(h, P_GS_UPDATE, 0, 0);
-        launch_fg_gs2(h->V, ldv, fs, dh1, h->w, Lb, h->partials, dh2, h->m, h->cfg.krylov_maxit,
-                      h->dscal + 320 + 2 * blk, cond, h->st);
-      }
-      {
-        ProfScope ps(h, P_SCALE, 0, 0);
-        launch_fg_next(h->V, ldv, fs, dh2, h->w, h->V, h->prec_in, Lb, h->m + 1, cond, h->st);
-      }
-      body_launches = h->stats.kernel_launches - l0;
-      body_vcycles = h->stats.vcycles - v0;
-      h->st = main;
-      cudaGraph_t bout = nullptr;
-      e = cudaStreamEndCapture(h->st_aux, &bout);
+      a.copy_dst = h->Z;
+      a.copy_src = h->prec_out;
+      a.copy_len = Lb;
+      a.copy_jdev = &fs->j;
+      a.copy_ldv = ldv;
+      run_stage_op(h, a);
     }
+    double* dh1 = h->dscal;
+    double* dh2 = h->dscal + 64;
+    {
+      ProfScope ps(h, P_GS_DOT, 0, 0);
+      launch_fg_gs1(h->V, ldv, fs, h->w, Lb, h->partials, dh1, inner);
+    }
+    {
+      ProfScope ps(h, P_GS_UPDATE, 0, 0);
+      launch_fg_gs2(h->V, ldv, fs, dh1, h->w, Lb, h->partials, dh2, h->m, h->cfg.krylov_maxit,
+                    h->dscal + 320 + 2 * blk, cond, inner);
+    }
+    {
+      ProfScope ps(h, P_SCALE, 0, 0);
+      launch_fg_next(h->V, ldv, fs, dh2, h->w, h->V, h->prec_in, Lb, h->m + 1, cond, inner);
+    }
+    cc->body = h->stats.kernel_launches - l0;
+    cc->vcycles = h->stats.vcycles - v0;
+    h->st = outer;
+    cudaGraph_t bout = nullptr;
+    e = cudaStreamEndCapture(inner, &bout);
   }
   if (e == cudaSuccess)
-    e = cudaStreamUpdateCaptureDependencies(h->st, &wnode, nullptr, 1,
+    e = cudaStreamUpdateCaptureDependencies(outer, &wnode, nullptr, 1,
                                             cudaStreamSetCaptureDependencies);
-  const long long l1 = h->stats.kernel_launches;
   if (e == cudaSuccess) {
-    // ---- suffix
+    const long long l1 = h->stats.kernel_launches;
     {
       ProfScope ps(h, P_LINCOMB, 0, 0);
-      launch_fg_solve(fs, h->st);
+      launch_fg_solve(fs, outer);
     }
     {
       ProfScope ps(h, P_LINCOMB, 0, 0);
-      launch_fg_lincomb(x, h->Z, ldv, fs, Lb, h->st);
+      launch_fg_lincomb(x, h->Z, ldv, fs, Lb, outer);
     }
+    cc->fixed += h->stats.kernel_launches - l1;
   }
-  cudaGraph_t out = nullptr;
-  cudaError_t e2 = cudaStreamEndCapture(h->st, &out);
-  if (e == cudaSuccess) e = e2;
+  h->st = saved_st;
+  return e;
+}
+
+// Standalone graph of one block solve (used when the whole-step graph is not).
+irk_status build_fg_graph(irk_handle* h, double dt, int blk) {
+  const irk_stats saved = h->stats;
+  cudaGraph_t G = nullptr;
+  CK(cudaGraphCreate(&G, 0));
+  cudaError_t e = cudaStreamBeginCaptureToGraph(h->st, G, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal);
+  CapCounts cc;
+  if (e == cudaSuccess) {
+    e = capture_block_solve(h, dt, blk, h->st, h->st_aux, &cc);
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->st, &out);
+    if (e == cudaSuccess) e = e2;
+  }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&h->fgexec[blk], G, 0);
   cudaGraphDestroy(G);
-  h->fg_fixed_launches[blk] = prefix_launches + (h->stats.kernel_launches - l1);
-  h->fg_body_launches[blk] = body_launches;
-  h->fg_body_vcycles[blk] = body_vcycles;
+  h->fg_fixed_launches[blk] = cc.fixed;
+  h->fg_body_launches[blk] = cc.body;
+  h->fg_body_vcycles[blk] = cc.vcycles;
   h->stats = saved;
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -942,6 +973,175 @@ irk_status build_fg_graph(irk_handle* h, double dt, int blk) {
     return IRK_ERR_CUDA;
   }
   return IRK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Whole IRK step as one CUDA graph (Algorithm 1 with the Newton loop on the
+// device):
+//   k = 0; F, ||F(0)||; k_newton_first
+//   WHILE (Newton): MG setup; block solves (each with its own FGMRES WHILE);
+//                   k += (Q0 R0 (x) I) dk_hat; F; k_newton_ctl
+//   u_{n+1} = u_n + dt sum b_i k_i
+// k_newton_ctl applies the host loop's tests (tolerance, iteration limit,
+// growth, non-finite residual) and the same inexact-Newton forcing term; the
+// host reads one status block after the graph.  Not used with a time-
+// dependent source (its stage times would be baked into the graph).
+irk_status build_step_graph(irk_handle* h, double dt) {
+  if (h->stepexec) {
+    cudaGraphExecDestroy(h->stepexec);
+    h->stepexec = nullptr;
+  }
+  const irk_stats saved = h->stats;
+  const int s = h->s;
+  cudaGraph_t G = nullptr;
+  CK(cudaGraphCreate(&G, 0));
+  cudaGraphConditionalHandle ncond = 0;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&ncond, G, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(h->st, G, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  long long fixed = 0, newton_body = 0;
+  CapCounts blkcc[IRK_MAXS];
+  if (e == cudaSuccess) {
+    const long long l0 = h->stats.kernel_launches;
+    cudaMemsetAsync(h->K, 0, sizeof(double) * s * h->L, h->st);
+    launch_eval_residual(h, 0.0, dt, h->K, h->rhs, nullptr, true);
+    {
+      ProfScope ps(h, P_SCALE, 0, 0);
+      launch_newton_first(h->nws, h->dscal + 201, h->dscal + 300, h->cfg.newton_rtol,
+                          h->cfg.krylov_rtol, ncond, h->st);
+    }
+    fixed += h->stats.kernel_launches - l0;
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(h->st, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+    cudaGraphNode_t wnode = nullptr;
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) {
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = ncond;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      e = cudaGraphAddNode(&wnode, G, deps, nullptr, ndeps, &np);
+      if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(h->st_aux, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaStream_t main = h->st;
+      h->st = h->st_aux;
+      const long long l1 = h->stats.kernel_launches;
+      mg_setup(h, dt);
+      for (int blk = h->tab.nblk - 1; blk >= 0 && e == cudaSuccess; --blk)
+        e = capture_block_solve(h, dt, blk, h->st_aux, h->st_aux2, &blkcc[blk]);
+      if (e == cudaSuccess) {
+        {
+          ProfScope ps(h, P_UPDATE, 8.0 * h->L * 3 * s, 2.0 * h->L * s * s);
+          launch_stage_update(h->L, s, h->tab.QR, h->yhat, h->K, h->st);
+        }
+        if (h->g.op == IRK_OP_VSF_2D) {
+          ProfScope ps(h, P_MEAN, 24.0 * h->npts * s, 2.0 * h->npts * s, 2);
+          launch_remove_mean(h->npts, s, h->L, h->K + h->npts, h->partials, h->st);
+        }
+        launch_eval_residual(h, 0.0, dt, h->K, h->rhs, nullptr, true);
+        {
+          ProfScope ps(h, P_SCALE, 0, 0);
+          launch_newton_ctl(h->nws, h->dscal + 201, h->dscal + 300, h->cfg.newton_rtol,
+                            h->cfg.newton_maxit, h->cfg.krylov_rtol, ncond, h->st);
+        }
+      }
+      newton_body = h->stats.kernel_launches - l1;
+      h->st = main;
+      cudaGraph_t bout = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(h->st_aux, &bout);
+      if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(h->st, &wnode, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+      const long long l2 = h->stats.kernel_launches;
+      ProfScope ps(h, P_UPDATE, 8.0 * h->L * (2 + s), 2.0 * h->L * s);
+      launch_u_update(h->L, s, h->tab.b, dt, h->K, h->u, h->st);
+      fixed += h->stats.kernel_launches - l2;
+    }
+    cudaGraph_t out = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(h->st, &out);
+    if (e == cudaSuccess) e = e3;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->stepexec, G, 0);
+  cudaGraphDestroy(G);
+  h->stats = saved;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->stepexec = nullptr;
+    return IRK_ERR_CUDA;
+  }
+  // launches per Newton iteration outside the block loops, and per block
+  long long blocks_fixed = 0;
+  for (int blk = 0; blk < h->tab.nblk; ++blk) {
+    blocks_fixed += blkcc[blk].fixed;
+    h->fg_body_launches[blk] = blkcc[blk].body;
+    h->fg_body_vcycles[blk] = blkcc[blk].vcycles;
+  }
+  (void)blocks_fixed;
+  h->step_fixed_launches = fixed;
+  // launches of one Newton iteration without its Krylov-loop bodies (counted per iteration)
+  h->step_newton_launches = newton_body;
+  for (int blk = 0; blk < h->tab.nblk; ++blk) h->step_newton_launches -= blkcc[blk].body;
+  h->step_dt = dt;
+  return IRK_OK;
+}
+
+// One IRK step through the step graph.  Returns IRK_OK, a Newton/Krylov
+// status, or IRK_ERR_INVALID when the graph cannot be used (caller falls back).
+irk_status graph_step(irk_handle* h, double dt) {
+  if (!h->cfg.use_graphs || h->cfg.profile || h->cfg.forcing || h->step_failed || !h->st_aux ||
+      !h->st_aux2)
+    return IRK_ERR_INVALID;
+  if (!h->stepexec || h->step_dt != dt) {
+    if (build_step_graph(h, dt) != IRK_OK) {
+      h->step_failed = true;
+      return IRK_ERR_INVALID;
+    }
+  }
+  CK(cudaGraphLaunch(h->stepexec, h->st));
+  // Newton status (dscal[400..406]) and Krylov counters (dscal[320..330])
+  CK(cudaMemcpyAsync(h->hbuf, h->dscal + 300, sizeof(double) * 110, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const double* nw = h->hbuf + 100;  // dscal[400..]
+  const int its = (int)nw[4];
+  const int status = (int)nw[5];
+  h->stats.newton_its += its;
+  h->stats.max_newton_its = std::max(h->stats.max_newton_its, its);
+  h->stats.final_rel_res = nw[2];
+  h->stats.kernel_launches += h->step_fixed_launches + (long long)its * h->step_newton_launches;
+  for (int blk = 0; blk < h->tab.nblk; ++blk) {
+    const double kits = h->hbuf[20 + 2 * blk];  // dscal[320 + 2 blk]
+    const double bad = h->hbuf[21 + 2 * blk];
+    const long long d = (long long)(kits - h->fg_seen_its[blk]);
+    if (d > 0) {
+      h->stats.krylov_its += (int)d;
+      h->stats.prec_apps += (int)d * h->tab.bsize[blk];
+      h->stats.vcycles += (int)d * h->fg_body_vcycles[blk];
+      h->stats.kernel_launches += d * h->fg_body_launches[blk];
+    }
+    h->fg_seen_its[blk] = kits;
+    if (bad != 0.0) { h->err = "non-finite Krylov vector"; return IRK_ERR_KRYLOV_BREAKDOWN; }
+  }
+  if (status == 0) return IRK_OK;
+  char buf[160];
+  if (status == IRK_ERR_NEWTON_MAXIT) {
+    snprintf(buf, sizeof buf, "Newton did not reach rtol %.1e in %d iterations (rel %.3e)",
+             h->cfg.newton_rtol, its, nw[2]);
+  } else {
+    snprintf(buf, sizeof buf, "Newton diverged (rel %.3e after %d iterations)", nw[2], its);
+  }
+  h->err = buf;
+  return (irk_status)status;
 }
 
 // All block solves of one Newton iteration through the device-resident graphs.
@@ -1183,6 +1383,7 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   h->fgs = (FGState*)take(sizeof(FGState) * h->tab.nblk);
   h->partials = (double*)take(8 * (size_t)h->nparts);
   h->dscal = (double*)take(8 * 512);
+  h->nws = h->dscal + 400;
   for (int l = 0; l < h->nlev; ++l) {
     const size_t f = h->esz * (size_t)h->lev[l].d.npts;
     h->lev[l].w = take(f * h->C);
@@ -1355,6 +1556,10 @@ static irk_status create_impl(const irk_config* cfg, const double* u0, int u0_on
     cudaGetLastError();
     h->st_aux = nullptr;  // device-resident FGMRES unavailable; host loop is used
   }
+  if (cudaStreamCreateWithFlags(&h->st_aux2, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    h->st_aux2 = nullptr;  // whole-step graph unavailable
+  }
   irk_status st = build(h, u0, u0_on_device);
   if (st != IRK_OK) {
     g_create_error = h->err;
@@ -1402,7 +1607,8 @@ irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats*
     cudaError_t e = cudaMemcpyAsync(h->u_save, h->u, sizeof(double) * h->L,
                                     cudaMemcpyDeviceToDevice, h->st);
     if (e != cudaSuccess) { h->err = cudaGetErrorString(e); st = IRK_ERR_CUDA; break; }
-    st = newton_step(h, t, dt);
+    st = graph_step(h, dt);
+    if (st == IRK_ERR_INVALID) st = newton_step(h, t, dt);  // host-driven loop
     if (st != IRK_OK) {
       cudaMemcpyAsync(h->u, h->u_save, sizeof(double) * h->L, cudaMemcpyDeviceToDevice, h->st);
       cudaStreamSynchronize(h->st);
@@ -1540,7 +1746,9 @@ void irk_destroy(irk_handle* h) {
     if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
   for (int k = 0; k < IRK_MAXS; ++k)
     if (h->fgexec[k]) cudaGraphExecDestroy(h->fgexec[k]);
+  if (h->stepexec) cudaGraphExecDestroy(h->stepexec);
   if (h->st_aux) cudaStreamDestroy(h->st_aux);
+  if (h->st_aux2) cudaStreamDestroy(h->st_aux2);
   if (h->arena && h->own_arena) cudaFree(h->arena);
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
   delete h;
