@@ -93,9 +93,12 @@ typedef struct {
   int mg_coarse_sweeps; /* sweeps on the coarsest level; default 40 */
   double mg_omega;      /* Jacobi damping; 0 = default (0.8 in 2D, 2/3 in 1D) */
   int profile;          /* 1 = time each kernel class with CUDA events */
-  int use_graphs;       /* 1 (default) = replay each block preconditioner L_P
-                           as a CUDA graph captured once per dt; forced off
-                           while profile = 1 (per-launch events) */
+  int use_graphs;       /* 1 (default) = run each IRK step as one CUDA graph
+                           (Newton and FGMRES loops in conditional nodes),
+                           captured once per dt; forced off while profile = 1 */
+  int initial_guess;    /* Newton start: 1 (default) = the previous step's
+                           stages, 0 = zero.  The tolerance is relative to
+                           ||F(k=0)|| either way; irk_set_state resets it to 0 */
 } irk_config;
 
 typedef struct {
@@ -151,6 +154,11 @@ irk_status irk_set_state(irk_handle* h, const double* src, int src_on_device);
 
 /* Stage vectors k_1..k_s of the last accepted step (s*ncomp*n^dim values). */
 irk_status irk_get_stages(irk_handle* h, double* dst, int dst_on_device);
+
+/* Set the stage vectors used as the next step's Newton starting guess
+ * (with initial_guess = 1).  A checkpoint that must resume bit for bit saves
+ * the state and the stages and restores both, the stages after the state. */
+irk_status irk_set_stages(irk_handle* h, const double* src, int src_on_device);
 
 /* Stage residual F_i = M k_i - N(u + dt sum_j a_ij k_j, t_n + c_i dt)
  * (Eq. stages) of a caller-given stage block K about the current state.

@@ -43,7 +43,7 @@ class IrkConfig(C.Structure):
         ("nonlinear_variant", C.c_int), ("gamma_mode", C.c_int),
         ("mg_precision", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
         ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double),
-        ("profile", C.c_int), ("use_graphs", C.c_int),
+        ("profile", C.c_int), ("use_graphs", C.c_int), ("initial_guess", C.c_int),
     ]
 
 
@@ -98,6 +98,7 @@ def _load():
         "irk_get_state": (i, [vp, vp, i]),
         "irk_set_state": (i, [vp, vp, i]),
         "irk_get_stages": (i, [vp, vp, i]),
+        "irk_set_stages": (i, [vp, vp, i]),
         "irk_stage_residual": (i, [vp, d, d, vp, vp, i]),
         "irk_stage_jacobian_apply": (i, [vp, d, vp, vp, vp, i]),
         "irk_tableau": (i, [i, i, vp, vp, vp, vp, vp, vp, vp]),
@@ -126,7 +127,7 @@ def _load():
 LIB = _load()
 EXPORTED = (
     "irk_config_default", "irk_create", "irk_step", "irk_get_state", "irk_set_state",
-    "irk_get_stages", "irk_stage_residual", "irk_stage_jacobian_apply", "irk_tableau",
+    "irk_get_stages", "irk_set_stages", "irk_stage_residual", "irk_stage_jacobian_apply", "irk_tableau",
     "irk_kernel_stats", "irk_reset_kernel_stats", "irk_device_bytes", "irk_last_error",
     "irk_status_string", "irk_destroy", "irk_stage_residual_noalloc",
     "irk_config_device_bytes", "irk_create_in", "irk_server_create", "irk_server_submit",
@@ -200,6 +201,11 @@ def irk_get_stages(h, dst):
     p, dev = _ptr(dst)
     _check(LIB.irk_get_stages(h, p, dev), h)
     return dst
+
+
+def irk_set_stages(h, src):
+    p, dev = _ptr(src)
+    _check(LIB.irk_set_stages(h, p, dev), h)
 
 
 def irk_stage_residual(h, t_n: float, dt: float, K, F):
@@ -353,6 +359,9 @@ class IrkSolver:
 
     def set_state(self, src):
         irk_set_state(self.h, src)
+
+    def set_stages(self, src):
+        irk_set_stages(self.h, src)
 
     def stages(self, out=None):
         import numpy as np

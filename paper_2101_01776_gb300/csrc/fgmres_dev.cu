@@ -393,15 +393,21 @@ void launch_fg_next(const double* V_, long long ldv, FGState* s, const double* h
 // ---------------------------------------------------------------------------
 // Newton control on the device (whole-step graph).  State nw[]:
 //   0 ||F(0)||, 1 ||F||, 2 ||F||/||F(0)||, 3 previous ||F||, 4 updates done,
-//   5 status (0 ok, IRK_ERR_NEWTON_DIVERGED, IRK_ERR_NEWTON_MAXIT).
+//   5 status (0 ok, IRK_ERR_NEWTON_DIVERGED, IRK_ERR_NEWTON_MAXIT),
+//   6 relative residual of the previous Newton iterate.
 // The tests and the forcing term are those of the host loop: stop on a
 // non-finite residual, at the tolerance, at the iteration limit, or on growth
 // by 1e3; otherwise eta = max(min(krylov_rtol, rel) [1e-3 rel if the last
 // update gained less than 2x], 0.2 newton_rtol / rel, 1e-13).
-__device__ double forcing_term(double rel, double fn, double prev, int it, double newton_rtol,
-                               double krylov_rtol) {
+__device__ double forcing_term(double rel, double prev_rel, double fn, double prev, int it,
+                               double newton_rtol, double krylov_rtol) {
   double eta = fmin(krylov_rtol, rel);
   if (it > 0 && prev > 0.0 && fn > 0.5 * prev) eta = fmin(eta, 1e-3 * rel);
+  // finish: if the observed quadratic rate C = rel/prev_rel^2 (an over-estimate
+  // while the linear error dominates) predicts C rel^2 <= newton_rtol/4 for an
+  // exact step, solve just tightly enough to land at newton_rtol/2
+  if (it > 0 && prev_rel > 0.0 && (rel / (prev_rel * prev_rel)) * rel * rel <= 0.25 * newton_rtol)
+    eta = fmin(eta, 0.5 * newton_rtol / rel);
   eta = fmax(eta, 0.2 * newton_rtol / rel);
   return fmax(eta, 1e-13);
 }
@@ -423,32 +429,50 @@ __global__ void k_newton_first(double* nw, const double* __restrict__ f2, double
   } else if (f0 == 0.0) {
     cudaGraphSetConditional(cond, 0);  // k = 0 solves the stage equations
   } else {
-    rtol_slot[0] = forcing_term(1.0, f0, f0, 0, newton_rtol, krylov_rtol);
+    nw[6] = 1.0;
+    rtol_slot[0] = forcing_term(1.0, 0.0, f0, f0, 0, newton_rtol, krylov_rtol);
     cudaGraphSetConditional(cond, 1);
   }
 }
 
+// count = 1 after a Newton update; 0 for the check of a warm-start guess.
 __global__ void k_newton_ctl(double* nw, const double* __restrict__ f2, double* rtol_slot,
-                             double newton_rtol, int maxit, double krylov_rtol,
+                             double newton_rtol, int maxit, double krylov_rtol, int count,
                              cudaGraphConditionalHandle cond) {
+  if (nw[5] != 0.0) return;  // already failed (non-finite ||F(0)||)
   const double fn = isfinite(f2[0]) ? sqrt(fmax(f2[0], 0.0)) : f2[0];
-  const int it = (int)nw[4] + 1;
+  const int it = (int)nw[4] + count;
   const double rel = fn / nw[0];
   nw[1] = fn;
   nw[2] = rel;
   nw[4] = (double)it;
   int stop = 1;
   if (!isfinite(fn)) nw[5] = (double)IRK_ERR_NEWTON_DIVERGED;
-  else if (rel <= newton_rtol) nw[5] = 0.0;
+  else if (rel <= newton_rtol || nw[0] == 0.0) nw[5] = 0.0;
   else if (it >= maxit) nw[5] = (double)IRK_ERR_NEWTON_MAXIT;
   else if (rel > 1e3) nw[5] = (double)IRK_ERR_NEWTON_DIVERGED;
   else stop = 0;
   if (stop) {
     cudaGraphSetConditional(cond, 0);
   } else {
-    rtol_slot[0] = forcing_term(rel, fn, nw[3], it, newton_rtol, krylov_rtol);
+    rtol_slot[0] = forcing_term(rel, count ? nw[6] : 0.0, fn, nw[3], it, newton_rtol, krylov_rtol);
     nw[3] = fn;
+    nw[6] = rel;
   }
+}
+
+// k = 0 already solves the stage equations when ||F(0)|| = 0; a warm-start
+// guess is then replaced by zero stages.
+__global__ void k_zero_if_unforced(const double* __restrict__ nw, double* __restrict__ K,
+                                   long long len) {
+  if (nw[0] != 0.0) return;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < len;
+       p += (long long)gridDim.x * blockDim.x)
+    K[p] = 0.0;
+}
+
+void launch_zero_if_unforced(const double* nw, double* K, long long len, cudaStream_t st) {
+  k_zero_if_unforced<<<blas_blocks(len), IRK_BLAS_THREADS, 0, st>>>(nw, K, len);
 }
 
 void launch_newton_first(double* nw, const double* f2, double* rtol_slot, double newton_rtol,
@@ -457,9 +481,9 @@ void launch_newton_first(double* nw, const double* f2, double* rtol_slot, double
 }
 
 void launch_newton_ctl(double* nw, const double* f2, double* rtol_slot, double newton_rtol,
-                       int maxit, double krylov_rtol, cudaGraphConditionalHandle cond,
+                       int maxit, double krylov_rtol, cudaGraphConditionalHandle cond, int count,
                        cudaStream_t st) {
-  k_newton_ctl<<<1, 1, 0, st>>>(nw, f2, rtol_slot, newton_rtol, maxit, krylov_rtol, cond);
+  k_newton_ctl<<<1, 1, 0, st>>>(nw, f2, rtol_slot, newton_rtol, maxit, krylov_rtol, count, cond);
 }
 
 // ---------------------------------------------------------------------------

@@ -153,10 +153,11 @@ void launch_fg_init(FGState* s, const double* nrm2, const double* rtol,
 void launch_fg_scale(const double* w, const FGState* s, double* V, long long ldv, double* prec_in,
                      long long L, cudaStream_t st);
 void launch_fg_solve(FGState* s, cudaStream_t st);
+void launch_zero_if_unforced(const double* nw, double* K, long long len, cudaStream_t st);
 void launch_newton_first(double* nw, const double* f2, double* rtol_slot, double newton_rtol,
                          double krylov_rtol, cudaGraphConditionalHandle cond, cudaStream_t st);
 void launch_newton_ctl(double* nw, const double* f2, double* rtol_slot, double newton_rtol,
-                       int maxit, double krylov_rtol, cudaGraphConditionalHandle cond,
+                       int maxit, double krylov_rtol, cudaGraphConditionalHandle cond, int count,
                        cudaStream_t st);
 // fused CGS2 iteration: dots (+reduce), update+dots (+reduce, Arnoldi step),
 // next basis vector (second update fused with the normalisation)

@@ -1004,12 +1004,33 @@ irk_status build_step_graph(irk_handle* h, double dt) {
   CapCounts blkcc[IRK_MAXS];
   if (e == cudaSuccess) {
     const long long l0 = h->stats.kernel_launches;
-    cudaMemsetAsync(h->K, 0, sizeof(double) * s * h->L, h->st);
-    launch_eval_residual(h, 0.0, dt, h->K, h->rhs, nullptr, true);
-    {
-      ProfScope ps(h, P_SCALE, 0, 0);
-      launch_newton_first(h->nws, h->dscal + 201, h->dscal + 300, h->cfg.newton_rtol,
-                          h->cfg.krylov_rtol, ncond, h->st);
+    if (h->cfg.initial_guess == 1) {
+      // ||F(k=0)|| fixes the tolerance; Newton then starts from the previous stages
+      cudaMemsetAsync(h->yhat, 0, sizeof(double) * s * h->L, h->st);
+      launch_eval_residual(h, 0.0, dt, h->yhat, h->rhs, nullptr, false);
+      {
+        ProfScope ps(h, P_SCALE, 0, 0);
+        launch_newton_first(h->nws, h->dscal + 201, h->dscal + 300, h->cfg.newton_rtol,
+                            h->cfg.krylov_rtol, ncond, h->st);
+      }
+      {
+        ProfScope ps(h, P_SCALE, 0, 0);
+        launch_zero_if_unforced(h->nws, h->K, (long long)s * h->L, h->st);
+      }
+      launch_eval_residual(h, 0.0, dt, h->K, h->rhs, nullptr, true);
+      {
+        ProfScope ps(h, P_SCALE, 0, 0);
+        launch_newton_ctl(h->nws, h->dscal + 201, h->dscal + 300, h->cfg.newton_rtol,
+                          h->cfg.newton_maxit, h->cfg.krylov_rtol, ncond, 0, h->st);
+      }
+    } else {
+      cudaMemsetAsync(h->K, 0, sizeof(double) * s * h->L, h->st);
+      launch_eval_residual(h, 0.0, dt, h->K, h->rhs, nullptr, true);
+      {
+        ProfScope ps(h, P_SCALE, 0, 0);
+        launch_newton_first(h->nws, h->dscal + 201, h->dscal + 300, h->cfg.newton_rtol,
+                            h->cfg.krylov_rtol, ncond, h->st);
+      }
     }
     fixed += h->stats.kernel_launches - l0;
     cudaStreamCaptureStatus cst;
@@ -1050,7 +1071,7 @@ irk_status build_step_graph(irk_handle* h, double dt) {
         {
           ProfScope ps(h, P_SCALE, 0, 0);
           launch_newton_ctl(h->nws, h->dscal + 201, h->dscal + 300, h->cfg.newton_rtol,
-                            h->cfg.newton_maxit, h->cfg.krylov_rtol, ncond, h->st);
+                            h->cfg.newton_maxit, h->cfg.krylov_rtol, ncond, 1, h->st);
         }
       }
       newton_body = h->stats.kernel_launches - l1;
@@ -1171,14 +1192,21 @@ bool fg_device_solve(irk_handle* h, double dt, double eta) {
 
 irk_status newton_step(irk_handle* h, double t_n, double dt) {
   const int s = h->s;
-  CK(cudaMemsetAsync(h->K, 0, sizeof(double) * s * h->L, h->st));
-  double f0 = 0, fn = 0, prev = 0;
+  double f0 = 0, fn = 0, prev = 0, prev_rel = 0;
+  if (h->cfg.initial_guess == 1) {
+    // ||F(k=0)|| fixes the tolerance; Newton then starts from the previous stages
+    CK(cudaMemsetAsync(h->yhat, 0, sizeof(double) * s * h->L, h->st));
+    TRY(eval_residual(h, t_n, dt, h->yhat, h->rhs, nullptr, false, &f0));
+    if (f0 == 0.0) CK(cudaMemsetAsync(h->K, 0, sizeof(double) * s * h->L, h->st));
+  } else {
+    CK(cudaMemsetAsync(h->K, 0, sizeof(double) * s * h->L, h->st));
+  }
   int it = 0;
   for (;; ++it) {
     TRY(eval_residual(h, t_n, dt, h->K, h->rhs, nullptr, true, &fn));
     if (it > 0) TRY(collect_fg_counters(h));
-    if (!std::isfinite(fn)) { h->err = "non-finite stage residual"; return IRK_ERR_NEWTON_DIVERGED; }
-    if (it == 0) f0 = fn;
+    if (!std::isfinite(fn) || !std::isfinite(f0)) { h->err = "non-finite stage residual"; return IRK_ERR_NEWTON_DIVERGED; }
+    if (it == 0 && h->cfg.initial_guess != 1) f0 = fn;
     const double rel = (f0 > 0) ? fn / f0 : 0.0;
     h->stats.final_rel_res = rel;
     if (f0 == 0 || rel <= h->cfg.newton_rtol) break;
@@ -1190,12 +1218,17 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
       return IRK_ERR_NEWTON_MAXIT;
     }
     if (it > 0 && rel > 1e3) { h->err = "Newton residual grew by 1e3"; return IRK_ERR_NEWTON_DIVERGED; }
-    // inexact-Newton forcing term: tighten with the residual, never oversolve the last step
+    // inexact-Newton forcing term: tighten with the residual, finish in one
+    // step once the observed quadratic rate allows it, never oversolve
     double eta_lin = std::min(h->cfg.krylov_rtol, rel);
     if (it > 0 && prev > 0 && fn > 0.5 * prev) eta_lin = std::min(eta_lin, 1e-3 * rel);
+    if (it > 0 && prev_rel > 0 &&
+        (rel / (prev_rel * prev_rel)) * rel * rel <= 0.25 * h->cfg.newton_rtol)
+      eta_lin = std::min(eta_lin, 0.5 * h->cfg.newton_rtol / rel);
     eta_lin = std::max(eta_lin, 0.2 * h->cfg.newton_rtol / rel);
     eta_lin = std::max(eta_lin, 1e-13);
     prev = fn;
+    prev_rel = rel;
     mg_setup(h, dt);
     if (!fg_device_solve(h, dt, eta_lin))
     for (int blk = h->tab.nblk - 1; blk >= 0; --blk) {
@@ -1245,6 +1278,7 @@ irk_status validate(const irk_config* c, std::string& err) {
   if (!(c->krylov_rtol > 0) || c->krylov_restart < 1 || c->krylov_restart > 64 || c->krylov_maxit < 1) { err = "bad Krylov settings"; return IRK_ERR_INVALID; }
   if (c->nonlinear_variant != 2 && c->nonlinear_variant != 3) { err = "nonlinear_variant must be 2 or 3"; return IRK_ERR_INVALID; }
   if (c->gamma_mode != 0 && c->gamma_mode != 1) { err = "gamma_mode must be 0 or 1"; return IRK_ERR_INVALID; }
+  if (c->initial_guess != 0 && c->initial_guess != 1) { err = "initial_guess must be 0 or 1"; return IRK_ERR_INVALID; }
   if (c->mg_precision < 0 || c->mg_precision > 2) { err = "mg_precision must be 0..2"; return IRK_ERR_INVALID; }
   if (c->mg_pre < 1 || c->mg_post < 0 || c->mg_pre > 8 || c->mg_post > 8) { err = "mg sweeps out of range"; return IRK_ERR_INVALID; }
   if (c->mg_coarse_sweeps < 1 || c->mg_coarse_sweeps > 1000) { err = "mg_coarse_sweeps out of range"; return IRK_ERR_INVALID; }
@@ -1483,6 +1517,7 @@ void irk_config_default(irk_config* c) {
   c->mg_omega = 0.0;
   c->profile = 0;
   c->use_graphs = 1;
+  c->initial_guess = 1;
 }
 
 const char* irk_status_string(irk_status st) {
@@ -1611,6 +1646,7 @@ irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats*
     if (st == IRK_ERR_INVALID) st = newton_step(h, t, dt);  // host-driven loop
     if (st != IRK_OK) {
       cudaMemcpyAsync(h->u, h->u_save, sizeof(double) * h->L, cudaMemcpyDeviceToDevice, h->st);
+      cudaMemsetAsync(h->K, 0, sizeof(double) * h->L * h->s, h->st);  // discard the failed iterate
       cudaStreamSynchronize(h->st);
       break;
     }
@@ -1638,6 +1674,16 @@ irk_status irk_get_state(irk_handle* h, double* dst, int dst_on_device) {
 irk_status irk_set_state(irk_handle* h, const double* src, int src_on_device) {
   if (!h || !src) return IRK_ERR_INVALID;
   CK(cudaMemcpyAsync(h->u, src, sizeof(double) * h->L,
+                     src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  // a new state starts Newton from zero stages
+  CK(cudaMemsetAsync(h->K, 0, sizeof(double) * h->L * h->s, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
+
+irk_status irk_set_stages(irk_handle* h, const double* src, int src_on_device) {
+  if (!h || !src) return IRK_ERR_INVALID;
+  CK(cudaMemcpyAsync(h->K, src, sizeof(double) * h->L * h->s,
                      src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
   CK(cudaStreamSynchronize(h->st));
   return IRK_OK;

@@ -269,11 +269,22 @@ def test_checkpoint_resume_and_determinism_bit_equal(B):
     with B.IrkSolver(u0, **kw) as b:
         b.step(0.0, 2e-3, 2)
         ck = b.state().copy()
+        ck_stages = b.stages().copy()  # the warm-start guess of the next step
     with B.IrkSolver(ck, **kw) as c:
+        c.set_stages(ck_stages)
         c.step(2 * 2e-3, 2e-3, 2)
         resumed = c.state().copy()
     np.testing.assert_array_equal(full, again)
     np.testing.assert_array_equal(full, resumed)
+
+
+@pytest.mark.parametrize("guess", [0, 1])
+def test_initial_guess_reaches_the_same_fixed_point(B, guess):
+    """Newton from zero stages or from the previous step's stages: the same
+    stage equations, the same tolerance (relative to ||F(k=0)||)."""
+    per_step, whole, infos = run_parity(B, "burgers2d", 64, 2, 5e-3, 2e-3, 3, seed=6,
+                                        initial_guess=guess)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
 
 
 def test_graph_path_matches_host_driven_path(B):
