@@ -215,7 +215,7 @@ irk_status irk_reset_kernel_stats(irk_handle* h);
 size_t irk_device_bytes(const irk_handle* h);
 
 /* Human-readable text of the last failure on h (valid until the next call on
- * h), or of a failure in irk_create when h is NULL. */
+ * h), or, when h is NULL, of the calling thread's last failed irk_create. */
 const char* irk_last_error(const irk_handle* h);
 const char* irk_status_string(irk_status st);
 

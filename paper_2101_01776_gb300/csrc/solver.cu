@@ -123,7 +123,8 @@ struct irk_handle {
   irk_kernel_stat prof[P_NCLASS];
 };
 
-static std::string g_create_error;
+// creation errors have no handle to live in; one per thread (serving creates handles concurrently)
+static thread_local std::string g_create_error;
 
 namespace {
 
