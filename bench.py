@@ -226,9 +226,9 @@ def run_ours(args, rank, world):
     u0 = workloads.random_fourier_2d(N, seed=SEED + rank)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def make(stages, prec, profile):
+    def make(stages, prec, profile, variant=3):
         cfg = B.irk_config_default(op="burgers2d", n=N, nu=NU, stages=stages,
-                                   mg_precision=prec, profile=profile)
+                                   mg_precision=prec, profile=profile, nonlinear_variant=variant)
         h = B.irk_create(cfg, torch.from_numpy(u0).to(dev), stream)
         return h
 
@@ -367,9 +367,10 @@ def run_ours(args, rank, world):
                        "d2h_bytes_per_step": nbytes}
         # ---- the other stage count and the FP32 V-cycle, same workload ------
         extra = {}
-        for label, stages, prec in (("gauss3_fp64", 3, 0), ("gauss2_mg_fp32", 2, 1),
-                                    ("gauss3_mg_fp32", 3, 1)):
-            h = make(stages, prec, 0)
+        for label, stages, prec, var in (("gauss3_fp64", 3, 0, 3), ("gauss2_mg_fp32", 2, 1, 3),
+                                         ("gauss3_mg_fp32", 3, 1, 3),
+                                         ("gauss3_fp64_variant2", 3, 0, 2)):
+            h = make(stages, prec, 0, var)
             ms2, tot2, _ = timed_steps(h, 3, 2)
             B.irk_destroy(h)
             extra[label] = {"steps_per_s": 1e3 / (sum(ms2) / len(ms2)),
@@ -423,9 +424,13 @@ def vsf_leg(B, torch, dev, stream, flush, timed_steps):
     u0 = np.zeros((2, n, n))
     u0[0] = w0
     out = {}
-    for prec in (0, 1):
+    # default (Newton-like variant 3, FP64 / FP32 V-cycle) and the block-
+    # diagonal variant 2 (Sec. 3.2), which drops the small d_kl off-diagonal
+    # terms of the transformed Jacobian (same fixed point)
+    for label, prec, var in (("fp64", 0, 3), ("mg_fp32", 1, 3), ("fp64_variant2", 0, 2),
+                             ("mg_fp32_variant2", 1, 2)):
         cfg = B.irk_config_default(op="vsf", n=n, nu=nu, stages=5, length=2 * math.pi,
-                                   mg_precision=prec)
+                                   mg_precision=prec, nonlinear_variant=var)
         h = B.irk_create(cfg, torch.from_numpy(u0).to(dev), stream)
         t, ms = 0.0, []
         st = B.irk_step(h, t, dt, 1)
@@ -444,7 +449,7 @@ def vsf_leg(B, torch, dev, stream, flush, timed_steps):
             newt += st.newton_its
             t += dt
         B.irk_destroy(h)
-        out["fp64" if prec == 0 else "mg_fp32"] = {
+        out[label] = {
             "steps_per_s": 1e3 / (sum(ms) / len(ms)), "krylov_its_per_step": kry / 2,
             "newton_its_per_step": newt / 2}
     return out
