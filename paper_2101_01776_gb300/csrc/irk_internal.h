@@ -176,6 +176,10 @@ void launch_fg_lincomb(double* x, const double* Z, long long ldz, const FGState*
 void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
                       double cadv, double cdiff, double omega, const void* vel, const void* b,
                       const void* w_in, void* w_out, int first, cudaStream_t st);
+bool mg_smooth2_pays(int prec, int dim, const MGLevelDesc& lv, int first);
+void launch_mg_smooth2(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
+                       double cadv, double cdiff, double omega, const void* vel, const void* b,
+                       const void* w_in, void* w_out, int first, cudaStream_t st);
 void launch_mg_residual(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp,
                         double sigma, double cadv, double cdiff, const void* vel, const void* b,
                         const void* w, void* r, cudaStream_t st);

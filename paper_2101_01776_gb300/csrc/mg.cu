@@ -177,6 +177,98 @@ __global__ void __launch_bounds__(256) k_mg_residual(MGLevelDesc lv, int ncomp, 
   }
 }
 
+// Two damped-Jacobi sweeps in one launch (2D, temporal blocking): a 32 x 8
+// tile loads w_in on its halo-2 window into shared memory, computes the first
+// sweep on the halo-1 window (340 points, 11 warp passes against 8 for the
+// tile) and the second on the tile.  The intermediate sweep is rounded to the
+// storage type, so the result equals two single sweeps bit for bit.  Halves
+// the launches and the passes over w; used where a level is latency- or
+// memory-bound (coarse levels, FP32/BF16 storage), not on FP64 levels large
+// enough to be FP64-issue-bound, where the extra 19% of work would show.
+constexpr int kTX = 32, kTY = 8;
+
+template <typename TS>
+__device__ __forceinline__ typename Cmp<TS>::T round_to_storage(typename Cmp<TS>::T v) {
+  return (typename Cmp<TS>::T)(TS)v;
+}
+template <>
+__device__ __forceinline__ float round_to_storage<__nv_bfloat16>(float v) {
+  return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+template <typename TS, int KIND>
+__global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int ncomp, MGConst k,
+                                                        const TS* __restrict__ vel,
+                                                        const TS* __restrict__ b,
+                                                        const TS* __restrict__ w_in,
+                                                        TS* __restrict__ w_out, int first) {
+  typedef typename Cmp<TS>::T TC;
+  __shared__ TC s_in[kTY + 4][kTX + 4];
+  __shared__ TC s_w1[kTY + 2][kTX + 2];
+  const TC alpha = TC(k.alpha), beta = TC(k.beta), dinv = TC(k.dinv), keep = TC(k.keep);
+  const int n = lv.n, m = n - 1, ln = lv.logn;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  for (int c = 0; c < ncomp; ++c) {
+    const long long off = (long long)c * lv.npts;
+    if (!first) {
+      for (int q = tid; q < (kTY + 4) * (kTX + 4); q += kTX * kTY) {
+        const int ly = q / (kTX + 4), lx = q - ly * (kTX + 4);
+        const int gx = (x0 + lx - 2) & m, gy = (y0 + ly - 2) & m;
+        s_in[ly][lx] = ldv(w_in + off + (gy << ln) + gx);
+      }
+    }
+    __syncthreads();
+    // sweep 1 on the halo-1 window
+    for (int q = tid; q < (kTY + 2) * (kTX + 2); q += kTX * kTY) {
+      const int ly = q / (kTX + 2), lx = q - ly * (kTX + 2);
+      const int gx = (x0 + lx - 1) & m, gy = (y0 + ly - 1) & m;
+      const int gp = (gy << ln) + gx;
+      const TC bc = ldv(b + off + gp);
+      TC v;
+      if (first) {
+        v = dinv * bc;
+      } else {
+        TC ce = beta, cw = beta, cn = beta, cs = beta;
+        if (KIND == MG_ADVECTIVE) {
+          const TC ax = ldv(vel + gp), ay = ldv(vel + lv.npts + gp);
+          ce = fma(alpha, ax, beta); cw = fma(-alpha, ax, beta);
+          cn = fma(alpha, ay, beta); cs = fma(-alpha, ay, beta);
+        }
+        const int sy = ly + 1, sx = lx + 1;  // position in s_in
+        TC t = bc;
+        t = fma(-ce, s_in[sy][sx + 1], t);
+        t = fma(-cw, s_in[sy][sx - 1], t);
+        t = fma(-cn, s_in[sy + 1][sx], t);
+        t = fma(-cs, s_in[sy - 1][sx], t);
+        v = fma(dinv, t, keep * s_in[sy][sx]);
+      }
+      s_w1[ly][lx] = round_to_storage<TS>(v);
+    }
+    __syncthreads();
+    // sweep 2 on the tile
+    {
+      const int lx = threadIdx.x, ly = threadIdx.y;
+      const int gx = x0 + lx, gy = y0 + ly;
+      const int gp = (gy << ln) + gx;
+      TC ce = beta, cw = beta, cn = beta, cs = beta;
+      if (KIND == MG_ADVECTIVE) {
+        const TC ax = ldv(vel + gp), ay = ldv(vel + lv.npts + gp);
+        ce = fma(alpha, ax, beta); cw = fma(-alpha, ax, beta);
+        cn = fma(alpha, ay, beta); cs = fma(-alpha, ay, beta);
+      }
+      const int sy = ly + 1, sx = lx + 1;
+      TC t = ldv(b + off + gp);
+      t = fma(-ce, s_w1[sy][sx + 1], t);
+      t = fma(-cw, s_w1[sy][sx - 1], t);
+      t = fma(-cn, s_w1[sy + 1][sx], t);
+      t = fma(-cs, s_w1[sy - 1][sx], t);
+      stv<TS, TC>(w_out + off + gp, fma(dinv, t, keep * s_w1[sy][sx]));
+    }
+    __syncthreads();
+  }
+}
+
 // Full weighting: fine -> coarse (coarse n = fine n / 2), all components.
 template <typename TS, int DIM>
 __global__ void __launch_bounds__(256) k_mg_restrict(MGLevelDesc fine, int ncomp,
@@ -362,6 +454,32 @@ void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
   const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, omega);
   IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_smooth<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
       lv, ncomp, k, (const TS*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first))));
+}
+
+// Whether one k_mg_smooth2 launch should replace two k_mg_smooth launches.
+// Measured on GB300 with two components: FP32/BF16 storage gains at every
+// size up to 1024^2 (0.5-1.0x the time); FP64 gains up to 256^2 and for the
+// pair that starts from zero (its first sweep reads b only), but loses on
+// larger levels, where the sweep is FP64-issue-bound (1.16x at 512^2).
+bool mg_smooth2_pays(int prec, int dim, const MGLevelDesc& lv, int first) {
+  if (dim != 2 || lv.n < kTX) return false;  // n a power of two: tiles cover the grid
+  if (prec != IRK_MG_FP64) return true;
+  return lv.n <= 256 || first;
+}
+
+void launch_mg_smooth2(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
+                       double cadv, double cdiff, double omega, const void* vel, const void* b,
+                       const void* w_in, void* w_out, int first, cudaStream_t st) {
+  const MGConst k = mg_const(lv, 2, sigma, cadv, cdiff, omega);
+  const dim3 grid(lv.n / kTX, lv.n / kTY), block(kTX, kTY);
+  IRK_DISPATCH_PREC(prec, {
+    if (kind == MG_ADVECTIVE)
+      k_mg_smooth2<TS, MG_ADVECTIVE><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
+    else
+      k_mg_smooth2<TS, MG_DIFFUSION><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
+  });
 }
 
 void launch_mg_residual(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp,

@@ -32,12 +32,13 @@ namespace {
 enum ProfClass {
   P_STAGE = 0, P_RESID, P_STAGEOP, P_UPDATE, P_MG_SMOOTH, P_MG_RESID, P_MG_RESTRICT,
   P_MG_PROLONG, P_MG_COARSE, P_MG_CONVERT, P_MG_SETUP, P_GS_DOT, P_GS_UPDATE, P_REDUCE,
-  P_SCALE, P_LINCOMB, P_NORM, P_AXPBY, P_MEAN, P_NCLASS
+  P_SCALE, P_LINCOMB, P_NORM, P_AXPBY, P_MEAN, P_MG_SMOOTH2, P_NCLASS
 };
 const char* kProfNames[P_NCLASS] = {
   "stage_states", "residual", "stage_op", "stage_update", "mg_smooth", "mg_residual",
   "mg_restrict", "mg_prolong", "mg_coarse", "mg_convert", "mg_setup", "gs_multi_dot",
-  "gs_update_dot", "reduce", "scale_copy", "lincomb", "norm2", "axpby", "remove_mean"};
+  "gs_update_dot", "reduce", "scale_copy", "lincomb", "norm2", "axpby", "remove_mean",
+  "mg_smooth2"};
 
 struct PendingEvent {
   int cls;
@@ -389,6 +390,44 @@ void mg_setup(irk_handle* h, double dt) {
   }
 }
 
+// `sweeps` damped-Jacobi sweeps on level l (from w = 0 when from_zero); the
+// iterate ends in cur (cur/alt swap as the sweeps ping-pong), or in `last`
+// when given (the caller's output buffer).  Pairs of sweeps go to the
+// temporally blocked two-sweep kernel where it pays; it reads b on a halo, so
+// it never writes into b.
+void jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, double cadv,
+                   double cdiff, double om, const void* vel, const void* b, int sweeps,
+                   bool from_zero, void*& cur, void*& alt, void* last) {
+  const MGLevelDesc& d = h->lev[l].d;
+  const int prec = h->prec, dim = h->dim;
+  const int velf = (kind == MG_DIFFUSION) ? 0 : (kind == MG_CONSERVATIVE_1D ? 1 : dim);
+  const double fpp = 2.0 * (4 * dim + 6);  // flops per point and component of one sweep
+  const double pts = (double)ncomp * d.npts;
+  int sw = 0;
+  while (sw < sweeps) {
+    // a first sweep from zero reads no w, so it may write in place
+    const int first = from_zero && sw == 0;
+    void* dst = first ? cur : alt;
+    const bool ends_pair = (sw + 2 == sweeps);
+    if (sw + 1 < sweeps && mg_smooth2_pays(prec, dim, d, first) && !(ends_pair && last == b)) {
+      if (ends_pair && last) dst = last;
+      ProfScope ps(h, P_MG_SMOOTH2, mg_level_bytes(h, l, (first ? 2.0 : 3.0) * ncomp + velf),
+                   pts * (first ? 1 + fpp : 2 * fpp));
+      launch_mg_smooth2(prec, kind, d, ncomp, sigma, cadv, cdiff, om, vel, b, cur, dst, first,
+                        h->st);
+      sw += 2;
+    } else {
+      if (sw + 1 == sweeps && last) dst = last;
+      ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, l, first ? 2.0 * ncomp : 3.0 * ncomp + velf),
+                   pts * (first ? 1 : fpp));
+      launch_mg_smooth(prec, dim, kind, d, ncomp, sigma, cadv, cdiff, om, vel, b, cur, dst, first,
+                       h->st);
+      sw += 1;
+    }
+    if (dst == alt) std::swap(cur, alt);
+  }
+}
+
 // One V-cycle for A = sigma I + cadv adv(vel_k) - cdiff L on ncomp fields.
 // in/out: double, ncomp * npts_fine.  In FP64 storage the input is read in
 // place and the last fine-level sweep writes the output directly.
@@ -416,14 +455,8 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     MGLevel& lv = h->lev[l];
     cur[l] = lv.w;
     alt[l] = lv.w2;
-    for (int sw = 0; sw < h->cfg.mg_pre; ++sw) {
-      const int first = (sw == 0);
-      ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, l, first ? 2.0 * ncomp : 3.0 * ncomp + velf),
-                   (double)ncomp * lv.d.npts * (first ? 1 : smooth_flops_pp));
-      launch_mg_smooth(prec, dim, kind, lv.d, ncomp, sigma, cadv, cdiff, om, vrow[l], bl[l],
-                       cur[l], first ? cur[l] : alt[l], first, h->st);
-      if (!first) std::swap(cur[l], alt[l]);
-    }
+    jacobi_sweeps(h, l, kind, ncomp, sigma, cadv, cdiff, om, vrow[l], bl[l], h->cfg.mg_pre, true,
+                  cur[l], alt[l], nullptr);
     {
       ProfScope ps(h, P_MG_RESID, mg_level_bytes(h, l, 3.0 * ncomp + velf),
                    (double)ncomp * lv.d.npts * smooth_flops_pp);
@@ -457,14 +490,8 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
       sweeps = std::max(2, std::min(sweeps, 12));
       cur[c] = lc.w;
       alt[c] = lc.w2;
-      for (int sw = 0; sw < sweeps; ++sw) {
-        const int first = (sw == 0);
-        ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, c, first ? 2.0 * ncomp : 3.0 * ncomp + velf),
-                     (double)ncomp * lc.d.npts * (first ? 1 : smooth_flops_pp));
-        launch_mg_smooth(prec, dim, kind, lc.d, ncomp, sigma, cadv, cdiff, omc, vrow[c], bl[c],
-                         cur[c], first ? cur[c] : alt[c], first, h->st);
-        if (!first) std::swap(cur[c], alt[c]);
-      }
+      jacobi_sweeps(h, c, kind, ncomp, sigma, cadv, cdiff, omc, vrow[c], bl[c], sweeps, true,
+                    cur[c], alt[c], nullptr);
     }
   }
   bool wrote_out = false;
@@ -475,15 +502,11 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
                    (double)ncomp * lv.d.npts * 3);
       launch_mg_prolong_add(prec, dim, lv.d, ncomp, cur[l + 1], cur[l], h->st);
     }
-    for (int sw = 0; sw < h->cfg.mg_post; ++sw) {
-      const bool last_to_out = alias && l == 0 && sw == h->cfg.mg_post - 1;
-      void* dst = last_to_out ? (void*)out : alt[l];
-      ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, l, 3.0 * ncomp + velf),
-                   (double)ncomp * lv.d.npts * smooth_flops_pp);
-      launch_mg_smooth(prec, dim, kind, lv.d, ncomp, sigma, cadv, cdiff, om, vrow[l], bl[l],
-                       cur[l], dst, 0, h->st);
-      if (last_to_out) wrote_out = true;
-      else std::swap(cur[l], alt[l]);
+    if (h->cfg.mg_post > 0) {
+      const bool to_out = alias && l == 0;
+      jacobi_sweeps(h, l, kind, ncomp, sigma, cadv, cdiff, om, vrow[l], bl[l], h->cfg.mg_post,
+                    false, cur[l], alt[l], to_out ? (void*)out : nullptr);
+      if (to_out) wrote_out = true;
     }
   }
   if (!wrote_out) {
