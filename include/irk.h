@@ -58,7 +58,19 @@ typedef enum {
   IRK_ERR_NO_DEVICE = 8         /* no CUDA device is available */
 } irk_status;
 
-typedef enum { IRK_GAUSS = 0 } irk_family;
+/* Runge-Kutta families with A0 invertible and A0^{-1} positive stable (the
+ * standing assumption of Sec. 2; Table 1 covers all three). */
+typedef enum {
+  IRK_GAUSS = 0,        /* order 2s */
+  IRK_RADAU_IIA = 1,    /* order 2s-1, stiffly accurate */
+  IRK_LOBATTO_IIIC = 2  /* order 2s-2, s >= 2 */
+} irk_family;
+
+/* Basis of the A0^{-1} transform in Algorithm 1 (Sec. 3.1). */
+typedef enum {
+  IRK_BASIS_SCHUR = 0,  /* standardized real Schur form Q0 R0 Q0^T (default) */
+  IRK_BASIS_EIGEN = 1   /* real eigenvector basis T R T^{-1}, R block diagonal */
+} irk_basis;
 
 typedef enum {
   IRK_OP_DIFFUSION_1D = 0, /* N = nu D2 u                       (linear test)   */
@@ -72,7 +84,7 @@ typedef enum { IRK_MASS_IDENTITY = 0, IRK_MASS_DAE = 1 } irk_mass;
 typedef enum { IRK_MG_FP64 = 0, IRK_MG_FP32 = 1, IRK_MG_BF16 = 2 } irk_mg_precision;
 
 typedef struct {
-  int family;        /* irk_family; only IRK_GAUSS */
+  int family;        /* irk_family */
   int stages;        /* s, 1..5 */
   int op;            /* irk_op */
   int mass;          /* irk_mass; must be IRK_MASS_DAE exactly for IRK_OP_VSF_2D */
@@ -85,7 +97,17 @@ typedef struct {
   double krylov_rtol;   /* loosest FGMRES relative tolerance per block; default 1e-3 */
   int krylov_restart;   /* FGMRES(m) restart length m, 1..64; default 30 */
   int krylov_maxit;     /* total FGMRES iterations per block solve; default 200 */
-  int nonlinear_variant;/* Newton-like variant of Sec. 3.2: 2 or 3; default 3 */
+  int nonlinear_variant;/* nonlinear iteration (Sec. 3.2); default 3:
+                           0 simplified Newton: every diagonal block uses the
+                             Jacobian at the last stage state;
+                           1 block diagonal, each block lumped onto the stage
+                             of its largest d-vector entry;
+                           2 block diagonal (d_ii^T L-hat);
+                           3 block upper triangular within the pattern of R0
+                             (exact Newton for s = 2);
+                           4 exact Newton: an outer FGMRES on the true stage
+                             Jacobian, right-preconditioned by one
+                             Algorithm-1 sweep of variant 3 */
   int gamma_mode;       /* 0: gamma* = eta + beta^2/eta (Eq. gamma*), 1: gamma = eta */
   int mg_precision;     /* irk_mg_precision of the V-cycle preconditioner */
   int mg_levels;        /* 0 = coarsen down to the coarsest size below */
@@ -99,6 +121,7 @@ typedef struct {
   int initial_guess;    /* Newton start: 1 (default) = the previous step's
                            stages, 0 = zero.  The tolerance is relative to
                            ||F(k=0)|| either way; irk_set_state resets it to 0 */
+  int basis;            /* irk_basis; default IRK_BASIS_SCHUR */
 } irk_config;
 
 typedef struct {
@@ -111,6 +134,7 @@ typedef struct {
   int max_newton_its;   /* worst step */
   double final_rel_res; /* ||F|| / ||F(0)|| at acceptance of the last step */
   long long kernel_launches; /* this library's kernel launches in the call */
+  int outer_its;        /* variant 4: outer FGMRES iterations on the true Jacobian */
 } irk_stats;
 
 typedef struct {
@@ -205,6 +229,14 @@ irk_status irk_stage_residual_noalloc(int op, int n, double length, double nu, i
  * *nblocks their count.  Needs no GPU. */
 irk_status irk_tableau(int family, int s, double* A, double* b, double* c,
                        double* Q0, double* R0, int* block_sizes, int* nblocks);
+
+/* Host-only: the A0^{-1} transform of Algorithm 1 in either basis,
+ * A0^{-1} = T R T^{-1} (Sec. 3.1).  T, Tinv, R are s*s row-major (T = Q0,
+ * Tinv = Q0^T, R = R0 for IRK_BASIS_SCHUR); block_sizes and *nblocks as for
+ * irk_tableau.  Any output pointer may be NULL.  Unknown family or basis, or
+ * s out of range, returns IRK_ERR_INVALID.  Needs no GPU. */
+irk_status irk_transform(int family, int s, int basis, double* T, double* Tinv, double* R,
+                         int* block_sizes, int* nblocks);
 
 /* Per-kernel-class timing gathered while cfg.profile = 1 (CUDA events on the
  * handle's stream).  Writes up to max entries, *count = entries written. */

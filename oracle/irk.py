@@ -91,9 +91,10 @@ def _project_psi(prob: Problem, dK: np.ndarray) -> np.ndarray:
 
 def step(prob: Problem, s: int, u_n: np.ndarray, t_n: float, dt: float, *,
          linear: str = "direct", rtol: float = 1e-10, extra: int = 1,
-         maxit: int = 30, gmres_rtol: float = 1e-13):
-    """One Gauss-IRK step by exact Newton.  Returns (u_{n+1}, K, NewtonInfo)."""
-    A, b, c = tab.gauss(s)
+         maxit: int = 30, gmres_rtol: float = 1e-13, family: str = "gauss"):
+    """One IRK step (Gauss unless `family` says 'radau' or 'lobatto') by exact
+    Newton.  Returns (u_{n+1}, K, NewtonInfo)."""
+    A, b, c = tab.tableau(family, s)
     u_n = np.asarray(u_n, dtype=np.float64).reshape(prob.shape)
     K = np.zeros((s,) + prob.shape)
     info = NewtonInfo()

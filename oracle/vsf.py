@@ -48,10 +48,11 @@ def initial_state(omega0: np.ndarray, h: float) -> np.ndarray:
 
 def reduced_step(prob: Problem, s: int, state: np.ndarray, t_n: float, dt: float, *,
                  rtol: float = 1e-10, extra: int = 1, maxit: int = 30,
-                 gmres_rtol: float = 1e-13):
-    """One Gauss-IRK step of the psi-eliminated VSF system by exact Newton."""
+                 gmres_rtol: float = 1e-13, family: str = "gauss"):
+    """One IRK step (Gauss unless `family` is 'radau' or 'lobatto') of the
+    psi-eliminated VSF system by exact Newton."""
     assert prob.op == "vsf"
-    A, b, c = tab.gauss(s)
+    A, b, c = tab.tableau(family, s)
     h, nu = prob.h, prob.nu
     w_n = np.asarray(state[0], dtype=np.float64)
     n = prob.n

@@ -25,7 +25,9 @@ IRK_ERR_KRYLOV_BREAKDOWN = 6
 IRK_ERR_TIMEOUT = 7
 IRK_ERR_NO_DEVICE = 8
 
-IRK_GAUSS = 0
+IRK_GAUSS, IRK_RADAU_IIA, IRK_LOBATTO_IIIC = 0, 1, 2
+IRK_BASIS_SCHUR, IRK_BASIS_EIGEN = 0, 1
+FAMILY_NAMES = {"gauss": IRK_GAUSS, "radau": IRK_RADAU_IIA, "lobatto": IRK_LOBATTO_IIIC}
 IRK_OP_DIFFUSION_1D, IRK_OP_BURGERS_1D, IRK_OP_BURGERS_2D, IRK_OP_VSF_2D = 0, 1, 2, 3
 IRK_MASS_IDENTITY, IRK_MASS_DAE = 0, 1
 IRK_MG_FP64, IRK_MG_FP32, IRK_MG_BF16 = 0, 1, 2
@@ -44,6 +46,7 @@ class IrkConfig(C.Structure):
         ("mg_precision", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
         ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double),
         ("profile", C.c_int), ("use_graphs", C.c_int), ("initial_guess", C.c_int),
+        ("basis", C.c_int),
     ]
 
 
@@ -52,6 +55,7 @@ class IrkStats(C.Structure):
         ("steps", C.c_int), ("newton_its", C.c_int), ("krylov_its", C.c_int),
         ("prec_apps", C.c_int), ("vcycles", C.c_int), ("max_newton_its", C.c_int),
         ("final_rel_res", C.c_double), ("kernel_launches", C.c_longlong),
+        ("outer_its", C.c_int),
     ]
 
     def as_dict(self):
@@ -102,6 +106,7 @@ def _load():
         "irk_stage_residual": (i, [vp, d, d, vp, vp, i]),
         "irk_stage_jacobian_apply": (i, [vp, d, vp, vp, vp, i]),
         "irk_tableau": (i, [i, i, vp, vp, vp, vp, vp, vp, vp]),
+        "irk_transform": (i, [i, i, i, vp, vp, vp, vp, vp]),
         "irk_kernel_stats": (i, [vp, P(IrkKernelStat), i, P(i)]),
         "irk_reset_kernel_stats": (i, [vp]),
         "irk_device_bytes": (sz, [vp]),
@@ -131,7 +136,7 @@ EXPORTED = (
     "irk_kernel_stats", "irk_reset_kernel_stats", "irk_device_bytes", "irk_last_error",
     "irk_status_string", "irk_destroy", "irk_stage_residual_noalloc",
     "irk_config_device_bytes", "irk_create_in", "irk_server_create", "irk_server_submit",
-    "irk_server_wait", "irk_server_stats_get", "irk_server_destroy",
+    "irk_server_wait", "irk_server_stats_get", "irk_server_destroy", "irk_transform",
 )
 
 
@@ -145,6 +150,10 @@ def irk_config_default(**overrides) -> IrkConfig:
     for k, v in overrides.items():
         if k == "op" and isinstance(v, str):
             v = OP_NAMES[v]
+        if k == "family" and isinstance(v, str):
+            v = FAMILY_NAMES[v]
+        if not hasattr(cfg, k):
+            raise AttributeError(f"irk_config has no field {k!r}")
         setattr(cfg, k, v)
     if "op" in overrides and "mass" not in overrides:
         cfg.mass = IRK_MASS_DAE if cfg.op == IRK_OP_VSF_2D else IRK_MASS_IDENTITY
@@ -306,6 +315,17 @@ def irk_tableau(s: int, family: int = IRK_GAUSS):
     _check(LIB.irk_tableau(family, s, A.ctypes.data, b.ctypes.data, c.ctypes.data,
                            Q.ctypes.data, R.ctypes.data, bs.ctypes.data, C.byref(nb)))
     return {"A": A, "b": b, "c": c, "Q0": Q, "R0": R, "block_sizes": list(bs[:nb.value])}
+
+
+def irk_transform(s: int, family: int = IRK_GAUSS, basis: int = IRK_BASIS_SCHUR):
+    """Host-only A0^{-1} = T R T^{-1} in either basis: dict of numpy arrays."""
+    import numpy as np
+    T, Ti, R = (np.zeros((s, s)) for _ in range(3))
+    bs = np.zeros(s, dtype=np.int32)
+    nb = C.c_int()
+    _check(LIB.irk_transform(family, s, basis, T.ctypes.data, Ti.ctypes.data, R.ctypes.data,
+                             bs.ctypes.data, C.byref(nb)))
+    return {"T": T, "Tinv": Ti, "R": R, "block_sizes": list(bs[:nb.value])}
 
 
 def irk_kernel_stats(h):

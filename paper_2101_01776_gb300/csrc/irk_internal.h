@@ -9,22 +9,26 @@
 
 #define IRK_MAXS 5
 #define IRK_MAX_TERMS 5
+#define IRK_MAX_COMBOS (IRK_MAXS * IRK_MAXS)
 #define IRK_MAX_LEVELS 16
 #define IRK_BLAS_THREADS 256
 #define IRK_FG_MAXM 64
 
 namespace irk {
 
+// A0^{-1} = T R T^{-1}: T = Q0 (orthogonal, T^{-1} = Q0^T) and R = R0 in the
+// real Schur basis; T = real eigenvectors and R block diagonal otherwise.
 struct HostTableau {
   int s;
   double A[IRK_MAXS * IRK_MAXS], b[IRK_MAXS], c[IRK_MAXS];
-  double Ainv[IRK_MAXS * IRK_MAXS], Q[IRK_MAXS * IRK_MAXS], R[IRK_MAXS * IRK_MAXS];
-  double QR[IRK_MAXS * IRK_MAXS];  // Q0 R0: back-transform of Algorithm 1
+  double Ainv[IRK_MAXS * IRK_MAXS], T[IRK_MAXS * IRK_MAXS], Tinv[IRK_MAXS * IRK_MAXS];
+  double R[IRK_MAXS * IRK_MAXS];
+  double TR[IRK_MAXS * IRK_MAXS];  // T R: back-transform of Algorithm 1
   int nblk, bstart[IRK_MAXS], bsize[IRK_MAXS];
   double eta[IRK_MAXS], beta2[IRK_MAXS], gamma_star[IRK_MAXS];
 };
 
-int build_tableau(int family, int s, HostTableau* t, char* err, size_t errlen);
+int build_tableau(int family, int s, int basis, HostTableau* t, char* err, size_t errlen);
 
 // ---------------------------------------------------------------------------
 // Grid and operator description passed to every stencil kernel.
@@ -46,7 +50,7 @@ struct StageStateArgs {
   long long L;           // ncomp * npts
   double dt;
   double A[IRK_MAXS * IRK_MAXS];
-  double D[IRK_MAXS * (IRK_MAXS + 1) / 2 * IRK_MAXS];  // ncombo x s
+  double D[IRK_MAX_COMBOS * IRK_MAXS];  // ncombo x s
   const double* u;       // may be null (treated as 0)
   const double* K;       // s * L
   double* Y;             // s * L (may be null)

@@ -73,7 +73,7 @@ struct irk_handle {
          *yhat = nullptr, *combos = nullptr, *zbuf = nullptr, *tmp = nullptr, *tmp2 = nullptr;
   int ncombo = 0;
   int combo_of[IRK_MAXS][IRK_MAXS];
-  double Dq[IRK_MAXS * (IRK_MAXS + 1) / 2 * IRK_MAXS];
+  double Dq[IRK_MAX_COMBOS * IRK_MAXS];
   int blk_of[IRK_MAXS];
 
   // FGMRES
@@ -104,6 +104,11 @@ struct irk_handle {
   bool step_failed = false;
   long long step_fixed_launches = 0, step_newton_launches = 0;
   double* nws = nullptr;  // Newton state: dscal[400..]
+  // exact Newton (variant 4): outer FGMRES on the true stage Jacobian over
+  // all s stages; bases Vo ((mo+1) s L), Zo (mo s L), work wo, solution xo,
+  // right-hand side fo (= F), JVP scratch jw (= (A0 (x) I) v)
+  int mo = 0;
+  double *Vo = nullptr, *Zo = nullptr, *wo = nullptr, *xo = nullptr, *fo = nullptr, *jw = nullptr;
   double* hbuf = nullptr;  // pinned host
   int nparts = 0;
 
@@ -611,12 +616,16 @@ irk_status apply_prec(irk_handle* h, double dt, int blk) {
   return IRK_OK;
 }
 
-// Flexible GMRES(m), right preconditioned, CGS2 (step a8).
-irk_status fgmres(irk_handle* h, double dt, int blk, const double* b, double* x, double rtol,
-                  int* its_out, double* relres_out) {
-  const int bs = h->tab.bsize[blk];
-  const long long Lb = (long long)bs * h->L;
-  const int m = h->m;
+// Flexible GMRES(m), right preconditioned, classical Gram-Schmidt applied
+// twice (step a8), on vectors of length Lb with bases V ((m+1) Lb) and
+// Z (m Lb) and the work vector w.  step(j) leaves Z_j = P_j^{-1} V_j and
+// w = A Z_j (P_j may change with j); apply(x, y) computes y = A x for
+// restarts; counted() runs once per iteration.  V_j is also written to
+// `stage` when given (the fixed input buffer of a captured preconditioner).
+template <class Step, class Apply, class Counted>
+irk_status fgmres_core(irk_handle* h, long long Lb, int m, int maxit, double* V, double* Z,
+                       double* w, double* stage, const double* b, double* x, double rtol,
+                       int* its_out, double* relres_out, Step step, Apply apply, Counted counted) {
   const long long ldv = Lb;
   double beta;
   TRY(dev_norm(h, b, Lb, &beta));
@@ -639,22 +648,18 @@ irk_status fgmres(irk_handle* h, double dt, int blk, const double* b, double* x,
   while (true) {
     {
       ProfScope ps(h, P_SCALE, 16.0 * Lb, (double)Lb);
-      launch_scale_copy(r, 1.0 / rnorm, h->V, h->prec_in, Lb, h->st);
+      launch_scale_copy(r, 1.0 / rnorm, V, stage, Lb, h->st);
     }
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = rnorm;
     int jlast = -1;
     double res = rnorm;
     for (int j = 0; j < m; ++j) {
-      double* vj = h->V + (long long)j * ldv;
-      double* zj = h->Z + (long long)j * ldv;
-      (void)vj;
-      TRY(apply_prec(h, dt, blk));  // prec_in (= V_j) -> prec_out
-      block_matvec_dt(h, dt, blk, h->prec_out, h->w, h->prec_out, zj);  // w = D z_j; Z_j = z_j
+      TRY(step(j));  // Z_j = P^{-1} V_j, w = A Z_j
       const int nv = j + 1;
       {
         ProfScope ps(h, P_GS_DOT, 8.0 * Lb * (nv + 1), 2.0 * Lb * nv);
-        launch_multi_dot(h->V, ldv, nv, h->w, Lb, h->partials, h->st);
+        launch_multi_dot(V, ldv, nv, w, Lb, h->partials, h->st);
       }
       {
         ProfScope ps(h, P_REDUCE, 8.0 * nb * nv, (double)nb * nv);
@@ -662,7 +667,7 @@ irk_status fgmres(irk_handle* h, double dt, int blk, const double* b, double* x,
       }
       {
         ProfScope ps(h, P_GS_UPDATE, 8.0 * Lb * (nv + 2), 4.0 * Lb * nv + 2.0 * Lb);
-        launch_update_dot(h->V, ldv, nv, dh1, h->w, Lb, 1, h->partials, h->st);
+        launch_update_dot(V, ldv, nv, dh1, w, Lb, 1, h->partials, h->st);
       }
       {
         ProfScope ps(h, P_REDUCE, 8.0 * nb * (nv + 1), (double)nb * (nv + 1));
@@ -670,7 +675,7 @@ irk_status fgmres(irk_handle* h, double dt, int blk, const double* b, double* x,
       }
       {
         ProfScope ps(h, P_GS_UPDATE, 8.0 * Lb * (nv + 2), 2.0 * Lb * nv + 2.0 * Lb);
-        launch_update_dot(h->V, ldv, nv, dh2, h->w, Lb, 0, h->partials, h->st);
+        launch_update_dot(V, ldv, nv, dh2, w, Lb, 0, h->partials, h->st);
       }
       {
         ProfScope ps(h, P_REDUCE, 8.0 * nb, (double)nb);
@@ -702,12 +707,11 @@ irk_status fgmres(irk_handle* h, double dt, int blk, const double* b, double* x,
       res = std::fabs(gv[j + 1]);
       ++total;
       jlast = j;
-      h->stats.krylov_its += 1;
-      h->stats.prec_apps += bs;
-      if (res <= target || hn <= 1e-300 || total >= h->cfg.krylov_maxit) break;
+      counted();
+      if (res <= target || hn <= 1e-300 || total >= maxit) break;
       {
         ProfScope ps(h, P_SCALE, 16.0 * Lb, (double)Lb);
-        launch_scale_copy(h->w, 1.0 / hn, h->V + (long long)(j + 1) * ldv, h->prec_in, Lb, h->st);
+        launch_scale_copy(w, 1.0 / hn, V + (long long)(j + 1) * ldv, stage, Lb, h->st);
       }
     }
     // y = H^{-1} g on the leading (jlast+1) block, x += Z y
@@ -719,21 +723,41 @@ irk_status fgmres(irk_handle* h, double dt, int blk, const double* b, double* x,
     }
     {
       ProfScope ps(h, P_LINCOMB, 8.0 * Lb * (k + 2), 2.0 * Lb * k);
-      launch_lincomb(x, h->Z, ldv, k, y.data(), Lb, h->st);
+      launch_lincomb(x, Z, ldv, k, y.data(), Lb, h->st);
     }
     *its_out = total;
     if (res <= target) { *relres_out = res / beta; return IRK_OK; }
-    if (total >= h->cfg.krylov_maxit) { *relres_out = res / beta; return IRK_OK; }
-    // restart: r = b - D x
-    block_matvec_dt(h, dt, blk, x, h->w, nullptr, nullptr);
+    if (total >= maxit) { *relres_out = res / beta; return IRK_OK; }
+    // restart: r = b - A x
+    apply(x, w);
     {
       ProfScope ps(h, P_AXPBY, 24.0 * Lb, 2.0 * Lb);
-      launch_axpby(h->w, 1.0, b, -1.0, Lb, h->st);
+      launch_axpby(w, 1.0, b, -1.0, Lb, h->st);
     }
-    r = h->w;
+    r = w;
     TRY(dev_norm(h, r, Lb, &rnorm));
     if (!(rnorm > 0)) return IRK_OK;
   }
+}
+
+// FGMRES on diagonal block blk of Algorithm 1 (step a8), preconditioned by L_P.
+irk_status fgmres(irk_handle* h, double dt, int blk, const double* b, double* x, double rtol,
+                  int* its_out, double* relres_out) {
+  const int bs = h->tab.bsize[blk];
+  const long long Lb = (long long)bs * h->L;
+  auto step = [&](int j) -> irk_status {
+    TRY(apply_prec(h, dt, blk));  // prec_in (= V_j) -> prec_out
+    // w = D z_j, and Z_j = z_j
+    block_matvec_dt(h, dt, blk, h->prec_out, h->w, h->prec_out, h->Z + (long long)j * Lb);
+    return IRK_OK;
+  };
+  auto apply = [&](const double* xin, double* y) { block_matvec_dt(h, dt, blk, xin, y, nullptr, nullptr); };
+  auto counted = [&]() {
+    h->stats.krylov_its += 1;
+    h->stats.prec_apps += bs;
+  };
+  return fgmres_core(h, Lb, h->m, h->cfg.krylov_maxit, h->V, h->Z, h->w, h->prec_in, b, x, rtol,
+                     its_out, relres_out, step, apply, counted);
 }
 
 // ---------------------------------------------------------------------------
@@ -766,7 +790,9 @@ void launch_eval_residual(irk_handle* h, double t_n, double dt, const double* K,
   ResidualArgs ra;
   memset(&ra, 0, sizeof(ra));
   ra.s = h->s;
-  for (int i = 0; i < h->s * h->s; ++i) ra.Q[i] = h->tab.Q[i];
+  // the kernel forms rhs_k = -sum_i Q[i][k] F_i; Q = (T^{-1})^T gives -(T^{-1} (x) I) F
+  for (int i = 0; i < h->s; ++i)
+    for (int k = 0; k < h->s; ++k) ra.Q[i * h->s + k] = h->tab.Tinv[k * h->s + i];
   for (int i = 0; i < h->s; ++i) ra.tstage[i] = t_n + h->tab.c[i] * dt;
   ra.forcing = h->cfg.forcing;
   ra.Y = h->Y;
@@ -1085,7 +1111,7 @@ irk_status build_step_graph(irk_handle* h, double dt) {
       if (e == cudaSuccess) {
         {
           ProfScope ps(h, P_UPDATE, 8.0 * h->L * 3 * s, 2.0 * h->L * s * s);
-          launch_stage_update(h->L, s, h->tab.QR, h->yhat, h->K, h->st);
+          launch_stage_update(h->L, s, h->tab.TR, h->yhat, h->K, h->st);
         }
         if (h->g.op == IRK_OP_VSF_2D) {
           ProfScope ps(h, P_MEAN, 24.0 * h->npts * s, 2.0 * h->npts * s, 2);
@@ -1145,7 +1171,7 @@ irk_status build_step_graph(irk_handle* h, double dt) {
 // status, or IRK_ERR_INVALID when the graph cannot be used (caller falls back).
 irk_status graph_step(irk_handle* h, double dt) {
   if (!h->cfg.use_graphs || h->cfg.profile || h->cfg.forcing || h->step_failed || !h->st_aux ||
-      !h->st_aux2)
+      !h->st_aux2 || h->cfg.nonlinear_variant == 4)
     return IRK_ERR_INVALID;
   if (!h->stepexec || h->step_dt != dt) {
     if (build_step_graph(h, dt) != IRK_OK) {
@@ -1214,6 +1240,112 @@ bool fg_device_solve(irk_handle* h, double dt, double eta) {
   return true;
 }
 
+// Block backward substitution of Algorithm 1 on h->rhs into h->yhat: the
+// device-resident FGMRES graphs when available, else the host-driven loop.
+irk_status solve_blocks(irk_handle* h, double dt, double rtol, bool* on_device) {
+  *on_device = fg_device_solve(h, dt, rtol);
+  if (*on_device) return IRK_OK;
+  for (int blk = h->tab.nblk - 1; blk >= 0; --blk) {
+    const int a0 = h->tab.bstart[blk];
+    const double* z = h->rhs + (long long)a0 * h->L;
+    if (blk < h->tab.nblk - 1) {
+      upper_coupling(h, dt, blk, h->zbuf);
+      z = h->zbuf;
+    }
+    int its = 0;
+    double rr = 0;
+    TRY(fgmres(h, dt, blk, z, h->yhat + (long long)a0 * h->L, rtol, &its, &rr));
+  }
+  return IRK_OK;
+}
+
+// out = J v for the true stage Jacobian (Eq. keq4 before any approximation):
+// (J v)_i = M v_i - dt J(Y_i) sum_j a_ij v_j at the stage states in h->Y.
+void full_jvp(irk_handle* h, double dt, const double* v, double* out, double* wscratch) {
+  const int s = h->s;
+  StageStateArgs wa;
+  set_stage_args(h, wa, 1.0, nullptr, v, wscratch, nullptr);
+  {
+    ProfScope ps(h, P_STAGE, 8.0 * h->L * 2 * s, 2.0 * h->L * s * s);
+    launch_stage_states(h->g, wa, h->st);
+  }
+  for (int i = 0; i < s; i += 2) {
+    StageOpArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nrow = std::min(2, s - i);
+    a.dt = dt;
+    for (int rr = 0; rr < a.nrow; ++rr) {
+      const long long off = (long long)(i + rr) * h->L;
+      OpRow& row = a.row[rr];
+      row.y = out + off;
+      row.sigma = 1;
+      row.nterm = 2;
+      row.t[0].x = v + off;
+      row.t[0].combo = nullptr;
+      row.t[0].m = 1.0;
+      row.t[0].lin = 0.0;
+      row.t[1].x = wscratch + off;
+      row.t[1].combo = h->Y + off;
+      row.t[1].m = 0.0;
+      row.t[1].lin = 1.0;
+    }
+    run_stage_op(h, a);
+  }
+}
+
+// z = P^{-1} r for P the variant-3 approximation of the stage Jacobian:
+// P^{-1} = (T R (x) I) B^{-1} (T^{-1} (x) I), B the block upper triangular
+// matrix of Algorithm 1, applied by one block backward substitution with
+// inner FGMRES solves to relative tolerance rtol.
+irk_status alg1_sweep(irk_handle* h, double dt, const double* r, double* z, double rtol) {
+  const int s = h->s;
+  const long long Lo = (long long)s * h->L;
+  {
+    ProfScope ps(h, P_UPDATE, 8.0 * Lo * 2, 2.0 * h->L * s * s);
+    CK(cudaMemsetAsync(h->rhs, 0, sizeof(double) * Lo, h->st));
+    launch_stage_update(h->L, s, h->tab.Tinv, r, h->rhs, h->st);
+  }
+  bool on_device = false;
+  TRY(solve_blocks(h, dt, rtol, &on_device));
+  {
+    ProfScope ps(h, P_UPDATE, 8.0 * Lo * 2, 2.0 * h->L * s * s);
+    CK(cudaMemsetAsync(z, 0, sizeof(double) * Lo, h->st));
+    launch_stage_update(h->L, s, h->tab.TR, h->yhat, z, h->st);
+  }
+  if (h->g.op == IRK_OP_VSF_2D) {
+    // constant psi is in the null space of J; keep the iterates free of it
+    ProfScope ps(h, P_MEAN, 24.0 * h->npts * s, 2.0 * h->npts * s, 2);
+    launch_remove_mean(h->npts, s, h->L, z + h->npts, h->partials, h->st);
+  }
+  if (on_device) {
+    TRY(sync_read(h, h->dscal + 201, 140));
+    TRY(collect_fg_counters(h));
+  }
+  return IRK_OK;
+}
+
+// Exact Newton update (variant 4): solve J x = F (F in h->fo) by FGMRES over
+// all stages, right-preconditioned by one Algorithm-1 sweep, then K -= x.
+irk_status exact_newton_update(irk_handle* h, double dt, double rtol) {
+  const long long Lo = (long long)h->s * h->L;
+  const double rtol_in = h->cfg.krylov_rtol;
+  auto step = [&](int j) -> irk_status {
+    double* zj = h->Zo + (long long)j * Lo;
+    TRY(alg1_sweep(h, dt, h->Vo + (long long)j * Lo, zj, rtol_in));
+    full_jvp(h, dt, zj, h->wo, h->jw);
+    return IRK_OK;
+  };
+  auto apply = [&](const double* x, double* y) { full_jvp(h, dt, x, y, h->jw); };
+  auto counted = [&]() { h->stats.outer_its += 1; };
+  int its = 0;
+  double rr = 0;
+  TRY(fgmres_core(h, Lo, h->mo, h->cfg.krylov_maxit, h->Vo, h->Zo, h->wo, nullptr, h->fo, h->xo,
+                  rtol, &its, &rr, step, apply, counted));
+  ProfScope ps(h, P_AXPBY, 24.0 * Lo, 2.0 * Lo);
+  launch_axpby(h->K, -1.0, h->xo, 1.0, Lo, h->st);
+  return IRK_OK;
+}
+
 irk_status newton_step(irk_handle* h, double t_n, double dt) {
   const int s = h->s;
   double f0 = 0, fn = 0, prev = 0, prev_rel = 0;
@@ -1227,7 +1359,7 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
   }
   int it = 0;
   for (;; ++it) {
-    TRY(eval_residual(h, t_n, dt, h->K, h->rhs, nullptr, true, &fn));
+    TRY(eval_residual(h, t_n, dt, h->K, h->rhs, h->fo, true, &fn));
     if (it > 0) TRY(collect_fg_counters(h));
     if (!std::isfinite(fn) || !std::isfinite(f0)) { h->err = "non-finite stage residual"; return IRK_ERR_NEWTON_DIVERGED; }
     if (it == 0 && h->cfg.initial_guess != 1) f0 = fn;
@@ -1254,21 +1386,13 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
     prev = fn;
     prev_rel = rel;
     mg_setup(h, dt);
-    if (!fg_device_solve(h, dt, eta_lin))
-    for (int blk = h->tab.nblk - 1; blk >= 0; --blk) {
-      const int a0 = h->tab.bstart[blk];
-      const double* z = h->rhs + (long long)a0 * h->L;
-      if (blk < h->tab.nblk - 1) {
-        upper_coupling(h, dt, blk, h->zbuf);
-        z = h->zbuf;
-      }
-      int its = 0;
-      double rr = 0;
-      TRY(fgmres(h, dt, blk, z, h->yhat + (long long)a0 * h->L, eta_lin, &its, &rr));
-    }
-    {
+    if (h->cfg.nonlinear_variant == 4) {
+      TRY(exact_newton_update(h, dt, eta_lin));
+    } else {
+      bool on_device = false;
+      TRY(solve_blocks(h, dt, eta_lin, &on_device));
       ProfScope ps(h, P_UPDATE, 8.0 * h->L * 3 * s, 2.0 * h->L * s * s);
-      launch_stage_update(h->L, s, h->tab.QR, h->yhat, h->K, h->st);
+      launch_stage_update(h->L, s, h->tab.TR, h->yhat, h->K, h->st);
     }
     if (h->g.op == IRK_OP_VSF_2D) {
       ProfScope ps(h, P_MEAN, 24.0 * h->npts * s, 2.0 * h->npts * s, 2);
@@ -1287,7 +1411,9 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
 // ---------------------------------------------------------------------------
 irk_status validate(const irk_config* c, std::string& err) {
   if (!c) { err = "null config"; return IRK_ERR_INVALID; }
-  if (c->family != IRK_GAUSS) { err = "family must be IRK_GAUSS"; return IRK_ERR_INVALID; }
+  if (c->family < IRK_GAUSS || c->family > IRK_LOBATTO_IIIC) { err = "unknown family"; return IRK_ERR_INVALID; }
+  if (c->family == IRK_LOBATTO_IIIC && c->stages < 2) { err = "Lobatto IIIC needs stages >= 2"; return IRK_ERR_INVALID; }
+  if (c->basis != IRK_BASIS_SCHUR && c->basis != IRK_BASIS_EIGEN) { err = "basis must be 0 (Schur) or 1 (eigenvectors)"; return IRK_ERR_INVALID; }
   if (c->stages < 1 || c->stages > IRK_MAXS) { err = "stages must be in 1..5"; return IRK_ERR_INVALID; }
   if (c->op < IRK_OP_DIFFUSION_1D || c->op > IRK_OP_VSF_2D) { err = "unknown op"; return IRK_ERR_INVALID; }
   const int want_mass = (c->op == IRK_OP_VSF_2D) ? IRK_MASS_DAE : IRK_MASS_IDENTITY;
@@ -1300,7 +1426,7 @@ irk_status validate(const irk_config* c, std::string& err) {
   if (c->forcing == 1 && c->length != 1.0) { err = "forcing 1 needs length 1"; return IRK_ERR_INVALID; }
   if (!(c->newton_rtol > 0) || c->newton_maxit < 1) { err = "bad Newton tolerance"; return IRK_ERR_INVALID; }
   if (!(c->krylov_rtol > 0) || c->krylov_restart < 1 || c->krylov_restart > 64 || c->krylov_maxit < 1) { err = "bad Krylov settings"; return IRK_ERR_INVALID; }
-  if (c->nonlinear_variant != 2 && c->nonlinear_variant != 3) { err = "nonlinear_variant must be 2 or 3"; return IRK_ERR_INVALID; }
+  if (c->nonlinear_variant < 0 || c->nonlinear_variant > 4) { err = "nonlinear_variant must be 0..4"; return IRK_ERR_INVALID; }
   if (c->gamma_mode != 0 && c->gamma_mode != 1) { err = "gamma_mode must be 0 or 1"; return IRK_ERR_INVALID; }
   if (c->initial_guess != 0 && c->initial_guess != 1) { err = "initial_guess must be 0 or 1"; return IRK_ERR_INVALID; }
   if (c->mg_precision < 0 || c->mg_precision > 2) { err = "mg_precision must be 0..2"; return IRK_ERR_INVALID; }
@@ -1316,7 +1442,7 @@ irk_status validate(const irk_config* c, std::string& err) {
 irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_only = false) {
   const irk_config& c = h->cfg;
   char ebuf[256] = {0};
-  if (build_tableau(c.family, c.stages, &h->tab, ebuf, sizeof ebuf)) { h->err = ebuf; return IRK_ERR_INVALID; }
+  if (build_tableau(c.family, c.stages, c.basis, &h->tab, ebuf, sizeof ebuf)) { h->err = ebuf; return IRK_ERR_INVALID; }
   const int s = h->s = c.stages;
   h->dim = (c.op == IRK_OP_BURGERS_2D || c.op == IRK_OP_VSF_2D) ? 2 : 1;
   h->C = (h->dim == 2) ? 2 : 1;
@@ -1342,15 +1468,36 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   for (int i = 0; i < s; ++i)
     for (int j = 0; j < s; ++j) h->combo_of[i][j] = -1;
   h->ncombo = 0;
+  // Block (k,l) of the transformed Jacobian (T^{-1} (x) I) diag(J(Y_m)) (T (x) I)
+  // (Eq. Q0approx) is sum_m d_klm J(Y_m) with d_klm = (T^{-1})_km T_ml; each
+  // kept block gets one combined field sum_m d_klm Y_m (N is bilinear).
   for (int k = 0; k < s; ++k)
-    for (int l = k; l < s; ++l) {
-      if (!(k == l || (c.nonlinear_variant >= 3 && h->blk_of[k] <= h->blk_of[l]))) continue;
-      double dmax = 0;
-      for (int mm = 0; mm < s; ++mm) dmax = std::max(dmax, std::fabs(h->tab.Q[mm * s + k] * h->tab.Q[mm * s + l]));
+    for (int l = 0; l < s; ++l) {
+      const int v = std::min(c.nonlinear_variant, 3);  // variant 4 preconditions with 3
+      if (!(k == l || (v >= 3 && h->blk_of[k] <= h->blk_of[l]))) continue;
+      double d[IRK_MAXS], dmax = 0;
+      for (int mm = 0; mm < s; ++mm) {
+        d[mm] = h->tab.Tinv[k * s + mm] * h->tab.T[mm * s + l];
+        dmax = std::max(dmax, std::fabs(d[mm]));
+      }
       if (k != l && dmax < 1e-15) continue;
-      const int q = h->ncombo++;
-      for (int mm = 0; mm < s; ++mm) h->Dq[q * s + mm] = h->tab.Q[mm * s + k] * h->tab.Q[mm * s + l];
-      h->combo_of[k][l] = h->combo_of[l][k] = q;
+      if (v <= 1) {
+        // 0: one stage for all blocks (simplified Newton); 1: the stage of the
+        // largest |d_kk| entry (lumped).  Unit d-vectors keep sum_m d = 1.
+        int pick = s - 1;
+        if (v == 1)
+          for (int mm = 0; mm < s; ++mm)
+            if (std::fabs(d[mm]) > std::fabs(d[pick]) + 1e-15) pick = mm;
+        for (int mm = 0; mm < s; ++mm) d[mm] = (mm == pick) ? 1.0 : 0.0;
+      }
+      int q = -1;
+      for (int e = 0; e < h->ncombo && q < 0; ++e)
+        if (std::equal(d, d + s, h->Dq + e * s)) q = e;
+      if (q < 0) {
+        q = h->ncombo++;
+        std::copy(d, d + s, h->Dq + q * s);
+      }
+      h->combo_of[k][l] = q;
     }
   // multigrid levels
   h->prec = c.mg_precision;
@@ -1395,6 +1542,13 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   add(8 * Lb);                   // prec_in
   add(8 * Lb);                   // prec_out
   add(sizeof(FGState) * h->tab.nblk);  // device FGMRES states
+  const long long Lo = (long long)s * h->L;
+  h->mo = (c.nonlinear_variant == 4) ? h->m : 0;
+  if (h->mo) {
+    add(8 * Lo * (h->mo + 1));   // Vo
+    add(8 * Lo * h->mo);         // Zo
+    for (int k = 0; k < 4; ++k) add(8 * Lo);  // wo, xo, fo, jw
+  }
   h->nparts = std::max(blas_blocks(Lb) * 70, residual_blocks(g)) + 1024;
   add(8 * (size_t)h->nparts);    // partials
   add(8 * 512);                  // device scalars
@@ -1439,6 +1593,14 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   h->prec_in = (double*)take(8 * Lb);
   h->prec_out = (double*)take(8 * Lb);
   h->fgs = (FGState*)take(sizeof(FGState) * h->tab.nblk);
+  if (h->mo) {
+    h->Vo = (double*)take(8 * Lo * (h->mo + 1));
+    h->Zo = (double*)take(8 * Lo * h->mo);
+    h->wo = (double*)take(8 * Lo);
+    h->xo = (double*)take(8 * Lo);
+    h->fo = (double*)take(8 * Lo);
+    h->jw = (double*)take(8 * Lo);
+  }
   h->partials = (double*)take(8 * (size_t)h->nparts);
   h->dscal = (double*)take(8 * 512);
   h->nws = h->dscal + 400;
@@ -1563,15 +1725,31 @@ irk_status irk_tableau(int family, int s, double* A, double* b, double* c, doubl
                        int* block_sizes, int* nblocks) {
   HostTableau t;
   char ebuf[256];
-  if (build_tableau(family, s, &t, ebuf, sizeof ebuf)) return IRK_ERR_INVALID;
+  if (build_tableau(family, s, IRK_BASIS_SCHUR, &t, ebuf, sizeof ebuf)) return IRK_ERR_INVALID;
   for (int i = 0; i < s * s; ++i) {
     if (A) A[i] = t.A[i];
-    if (Q0) Q0[i] = t.Q[i];
+    if (Q0) Q0[i] = t.T[i];
     if (R0) R0[i] = t.R[i];
   }
   for (int i = 0; i < s; ++i) {
     if (b) b[i] = t.b[i];
     if (c) c[i] = t.c[i];
+  }
+  if (block_sizes)
+    for (int k = 0; k < t.nblk; ++k) block_sizes[k] = t.bsize[k];
+  if (nblocks) *nblocks = t.nblk;
+  return IRK_OK;
+}
+
+irk_status irk_transform(int family, int s, int basis, double* T, double* Tinv, double* R,
+                         int* block_sizes, int* nblocks) {
+  HostTableau t;
+  char ebuf[256];
+  if (build_tableau(family, s, basis, &t, ebuf, sizeof ebuf)) return IRK_ERR_INVALID;
+  for (int i = 0; i < s * s; ++i) {
+    if (T) T[i] = t.T[i];
+    if (Tinv) Tinv[i] = t.Tinv[i];
+    if (R) R[i] = t.R[i];
   }
   if (block_sizes)
     for (int k = 0; k < t.nblk; ++k) block_sizes[k] = t.bsize[k];
@@ -1752,28 +1930,7 @@ irk_status irk_stage_jacobian_apply(irk_handle* h, double dt, const double* K, c
   StageStateArgs sa;
   set_stage_args(h, sa, dt, h->u, Kd, h->Y, nullptr);
   launch_stage_states(h->g, sa, h->st);
-  StageStateArgs wa;
-  set_stage_args(h, wa, 1.0, nullptr, Vd, Wd, nullptr);
-  launch_stage_states(h->g, wa, h->st);
-  for (int i = 0; i < s; ++i) {
-    StageOpArgs a;
-    memset(&a, 0, sizeof(a));
-    a.nrow = 1;
-    a.dt = dt;
-    OpRow& row = a.row[0];
-    row.y = Out + (long long)i * h->L;
-    row.sigma = 1;
-    row.nterm = 2;
-    row.t[0].x = Vd + (long long)i * h->L;
-    row.t[0].combo = nullptr;
-    row.t[0].m = 1.0;
-    row.t[0].lin = 0.0;
-    row.t[1].x = Wd + (long long)i * h->L;
-    row.t[1].combo = h->Y + (long long)i * h->L;
-    row.t[1].m = 0.0;
-    row.t[1].lin = 1.0;
-    run_stage_op(h, a);
-  }
+  full_jvp(h, dt, Vd, Out, Wd);
   CK(cudaMemcpyAsync(JV, Out, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   prof_harvest(h);

@@ -1,9 +1,12 @@
 // Host-side tableau and A0^{-1} transform (step a1 of the hot path).
 //
-// Gauss collocation (Sec. 1.1, Eq. update/stages): the abscissae are the
-// Legendre roots mapped to [0,1]; A and b follow from the collocation
-// conditions sum_j a_ij c_j^{q} = c_i^{q+1}/(q+1) and sum_j b_j c_j^q = 1/(q+1),
-// q = 0..s-1, which fix the integrals of the Lagrange basis exactly.
+// Families (Sec. 1.1, Eq. update/stages; Table 1 lists all three):
+//   Gauss        abscissae = roots of P_s mapped to [0,1] (collocation, order 2s)
+//   Radau IIA    roots of P_s - P_{s-1}, right end point c_s = 1 (collocation, order 2s-1)
+//   Lobatto IIIC roots of P_s - P_{s-2}, both end points (order 2s-2, s >= 2)
+// b follows from sum_j b_j c_j^q = 1/(q+1), q = 0..s-1.  Collocation rows
+// satisfy sum_j a_ij c_j^q = c_i^{q+1}/(q+1), q = 0..s-1; Lobatto IIIC rows
+// instead take a_i1 = b_1 and the same conditions for q = 0..s-2.
 //
 // Real Schur form (Sec. 3.1): A0^{-1} = Q0 R0 Q0^T, Q0 orthogonal, R0 block
 // upper triangular with 1x1 blocks for real eigenvalues and standardized 2x2
@@ -12,7 +15,13 @@
 // polynomial; each real eigenvector (or the real span of a complex one) is
 // completed to an orthonormal basis that splits off its block, and each 2x2
 // block is finally rotated to equal diagonals by the smallest Givens angle.
-// gamma* = eta + beta^2/eta (Eq. gamma*).  Everything runs in long double.
+// gamma* = eta + beta^2/eta (Eq. gamma*).
+//
+// Eigenvector basis (basis = 1): A0^{-1} = T R T^{-1} with T the real and
+// imaginary parts of the eigenvectors and R block diagonal, [[eta, beta],
+// [-beta, eta]] per pair (the phi = beta case of the standardized block).
+// Algorithm 1 then needs T^{-1} in place of Q0^T and has no R0 coupling.
+// Everything runs in long double.
 #include "irk_internal.h"
 
 #include <algorithm>
@@ -147,6 +156,53 @@ static void poly_roots(const std::vector<ld>& p, std::vector<cld>& z) {
     }
 }
 
+// Legendre polynomial P_n in the monomial basis (coefficients of x^0..x^n),
+// from (q+1) P_{q+1} = (2q+1) x P_q - q P_{q-1}.
+static std::vector<ld> legendre_poly(int n) {
+  std::vector<ld> pm(1, 1), pc = {0, 1};
+  if (n == 0) return pm;
+  for (int q = 1; q < n; ++q) {
+    std::vector<ld> pn(q + 2, 0);
+    for (int i = 0; i <= q; ++i) pn[i + 1] += (ld)(2 * q + 1) * pc[i] / (q + 1);
+    for (int i = 0; i < (int)pm.size(); ++i) pn[i] -= (ld)q * pm[i] / (q + 1);
+    pm = pc;
+    pc = pn;
+  }
+  return pc;
+}
+
+// Abscissae in [0,1], increasing.
+static bool family_nodes(int family, int s, std::vector<ld>& c) {
+  c.assign(s, 0);
+  if (family == IRK_GAUSS) {
+    std::vector<ld> x(s);
+    legendre_roots(s, x.data());
+    for (int k = 0; k < s; ++k) c[k] = (1 + x[k]) / 2;
+    std::sort(c.begin(), c.end());
+    return true;
+  }
+  std::vector<ld> p = legendre_poly(s);
+  const std::vector<ld> q = legendre_poly(family == IRK_RADAU_IIA ? s - 1 : s - 2);
+  for (size_t i = 0; i < q.size(); ++i) p[i] -= q[i];
+  const ld lead = p[s];
+  for (auto& v : p) v /= lead;
+  std::vector<cld> z;
+  poly_roots(p, z);
+  for (int k = 0; k < s; ++k) {
+    ld x = z[k].real();
+    if (std::fabs(z[k].imag()) > 1e-12L) return false;
+    for (int it = 0; it < 5; ++it) {  // real Newton polish
+      const ld d = polyder(p, cld(x, 0)).real();
+      if (d != 0) x -= polyval(p, cld(x, 0)).real() / d;
+    }
+    if (std::fabs(x - 1) < 1e-15L) x = 1;   // the end points are exact roots
+    if (std::fabs(x + 1) < 1e-15L) x = -1;
+    c[k] = (1 + x) / 2;
+  }
+  std::sort(c.begin(), c.end());
+  return true;
+}
+
 // A null vector of the (nearly singular) m x m complex matrix B by Gaussian
 // elimination with complete pivoting.
 static void null_vector(int m, std::vector<cld> B, std::vector<cld>& x) {
@@ -256,15 +312,86 @@ static void apply_similarity(int s, int off, int m, const std::vector<ld>& H,
   Q = QT;
 }
 
-int build_tableau(int family, int s, HostTableau* t, char* err, size_t errlen) {
-  if (family != IRK_GAUSS) { snprintf(err, errlen, "only the Gauss family is built"); return 1; }
+struct EigGroup {
+  cld lam;   // eigenvalue of A0^{-1}; imag >= 0 represents a conjugate pair
+  int size;  // 1 (real) or 2 (pair)
+};
+
+// Real eigenvector basis: column(s) of T per group in order, R block diagonal.
+// A pair eta + i beta with eigenvector z = x + i y gives A0^{-1} [x y] =
+// [x y] [[eta, beta], [-beta, eta]]; z is rotated so that x is orthogonal to
+// y with |x| >= |y|, scaled to |z|^2 = 2 (unit norm for a real vector), and
+// signed so that the largest entry of x is positive.
+static bool eigen_basis(int s, const std::vector<ld>& Ainv, const std::vector<EigGroup>& groups,
+                        HostTableau* t, std::vector<ld>& T, std::vector<ld>& R, char* err,
+                        size_t errlen) {
+  T.assign(s * s, 0);
+  R.assign(s * s, 0);
+  int off = 0, nb = 0;
+  for (const EigGroup& g : groups) {
+    std::vector<cld> B(s * s);
+    for (int i = 0; i < s; ++i)
+      for (int j = 0; j < s; ++j) B[i * s + j] = Ainv[i * s + j];
+    for (int i = 0; i < s; ++i) B[i * s + i] -= g.lam;
+    std::vector<cld> z;
+    null_vector(s, B, z);
+    if (g.size == 1) {
+      int big = 0;
+      for (int i = 1; i < s; ++i)
+        if (std::abs(z[i]) > std::abs(z[big])) big = i;
+      const cld ph = std::conj(z[big]) / std::abs(z[big]);
+      ld nr = 0;
+      for (auto& v : z) { v *= ph; nr += v.real() * v.real(); }
+      nr = std::sqrt(nr);
+      for (int i = 0; i < s; ++i) T[i * s + off] = z[i].real() / nr;
+      R[off * s + off] = g.lam.real();
+    } else {
+      ld xx = 0, yy = 0, xy = 0;
+      for (auto& v : z) { xx += v.real() * v.real(); yy += v.imag() * v.imag(); xy += v.real() * v.imag(); }
+      const ld th = 0.5L * std::atan2(-2 * xy, xx - yy);
+      const cld rot = std::polar((ld)1, th);
+      ld nr = 0;
+      for (auto& v : z) { v *= rot; nr += std::norm(v); }
+      const ld scale = std::sqrt(2 / nr);
+      int big = 0;
+      for (int i = 1; i < s; ++i)
+        if (std::fabs(z[i].real()) > std::fabs(z[big].real())) big = i;
+      const ld sg = (z[big].real() < 0) ? -scale : scale;
+      for (int i = 0; i < s; ++i) {
+        T[i * s + off] = z[i].real() * sg;
+        T[i * s + off + 1] = z[i].imag() * sg;
+      }
+      const ld eta = g.lam.real(), beta = g.lam.imag();
+      R[off * s + off] = R[(off + 1) * s + off + 1] = eta;
+      R[off * s + off + 1] = beta;
+      R[(off + 1) * s + off] = -beta;
+    }
+    t->bstart[nb] = off;
+    t->bsize[nb] = g.size;
+    t->eta[nb] = (double)g.lam.real();
+    const ld beta2 = g.size == 2 ? g.lam.imag() * g.lam.imag() : 0;
+    t->beta2[nb] = (double)beta2;
+    t->gamma_star[nb] = (double)(g.lam.real() + beta2 / g.lam.real());
+    ++nb;
+    off += g.size;
+  }
+  t->nblk = nb;
+  if (off != s) { snprintf(err, errlen, "eigenvalue groups do not cover the stages"); return false; }
+  return true;
+}
+
+int build_tableau(int family, int s, int basis, HostTableau* t, char* err, size_t errlen) {
+  if (family != IRK_GAUSS && family != IRK_RADAU_IIA && family != IRK_LOBATTO_IIIC) {
+    snprintf(err, errlen, "unknown family %d", family);
+    return 1;
+  }
+  if (basis != 0 && basis != 1) { snprintf(err, errlen, "basis must be 0 (Schur) or 1 (eigenvectors)"); return 1; }
   if (s < 1 || s > IRK_MAXS) { snprintf(err, errlen, "stages must be 1..%d", IRK_MAXS); return 1; }
+  if (family == IRK_LOBATTO_IIIC && s < 2) { snprintf(err, errlen, "Lobatto IIIC needs s >= 2"); return 1; }
   memset(t, 0, sizeof(*t));
   t->s = s;
-  std::vector<ld> x(s), c(s);
-  legendre_roots(s, x.data());
-  for (int k = 0; k < s; ++k) c[k] = (1 + x[k]) / 2;
-  std::sort(c.begin(), c.end());
+  std::vector<ld> c;
+  if (!family_nodes(family, s, c)) { snprintf(err, errlen, "abscissae not real"); return 1; }
   std::vector<ld> V(s * s);
   for (int q = 0; q < s; ++q)
     for (int j = 0; j < s; ++j) V[q * s + j] = std::pow(c[j], (ld)q);
@@ -273,9 +400,18 @@ int build_tableau(int family, int s, HostTableau* t, char* err, size_t errlen) {
   if (!solve_ld(s, V, b)) { snprintf(err, errlen, "singular collocation system"); return 1; }
   std::vector<ld> A(s * s);
   for (int i = 0; i < s; ++i) {
-    std::vector<ld> r(s);
+    std::vector<ld> r(s), W = V;
     for (int q = 0; q < s; ++q) r[q] = std::pow(c[i], (ld)(q + 1)) / (q + 1);
-    if (!solve_ld(s, V, r)) { snprintf(err, errlen, "singular collocation system"); return 1; }
+    if (family == IRK_LOBATTO_IIIC) {
+      // a_i1 = b_1 replaces the condition of the highest power: rows [e_1; c^0..c^{s-2}]
+      for (int q = s - 1; q >= 1; --q) {
+        for (int j = 0; j < s; ++j) W[q * s + j] = V[(q - 1) * s + j];
+        r[q] = r[q - 1];
+      }
+      for (int j = 0; j < s; ++j) W[j] = (j == 0) ? 1 : 0;
+      r[0] = b[0];
+    }
+    if (!solve_ld(s, W, r)) { snprintf(err, errlen, "singular collocation system"); return 1; }
     for (int j = 0; j < s; ++j) A[i * s + j] = r[j];
   }
   std::vector<ld> Ainv;
@@ -287,8 +423,7 @@ int build_tableau(int family, int s, HostTableau* t, char* err, size_t errlen) {
   std::vector<cld> ev;
   poly_roots(p, ev);
   // groups: real eigenvalues and one representative (imag > 0) per pair
-  struct Grp { cld lam; int size; };
-  std::vector<Grp> groups;
+  std::vector<EigGroup> groups;
   std::vector<bool> used(s, false);
   for (int k = 0; k < s; ++k) {
     if (used[k]) continue;
@@ -306,118 +441,129 @@ int build_tableau(int family, int s, HostTableau* t, char* err, size_t errlen) {
     }
   }
   // deterministic order: increasing real part, then increasing |imag|
-  std::sort(groups.begin(), groups.end(), [](const Grp& a, const Grp& b) {
+  std::sort(groups.begin(), groups.end(), [](const EigGroup& a, const EigGroup& b) {
     if (a.lam.real() != b.lam.real()) return a.lam.real() < b.lam.real();
     return a.lam.imag() < b.lam.imag();
   });
   for (auto& g : groups)
     if (g.lam.real() <= 0) { snprintf(err, errlen, "Assumption 1 violated: eigenvalue of A0^{-1} with non-positive real part"); return 1; }
 
-  std::vector<ld> R = Ainv, Q(s * s, 0);
-  for (int k = 0; k < s; ++k) Q[k * s + k] = 1;
-  int off = 0;
-  for (size_t g = 0; g < groups.size(); ++g) {
-    int m = s - off, k = groups[g].size;
-    if (m == k) { off += k; break; }
-    std::vector<cld> B(m * m);
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) B[i * m + j] = R[(off + i) * s + off + j];
-    for (int i = 0; i < m; ++i) B[i * m + i] -= groups[g].lam;
-    std::vector<cld> xv;
-    null_vector(m, B, xv);
-    // fix the global phase: make the largest component real
-    int big = 0;
-    for (int i = 1; i < m; ++i)
-      if (std::abs(xv[i]) > std::abs(xv[big])) big = i;
-    cld ph = std::conj(xv[big]) / std::abs(xv[big]);
-    for (auto& v : xv) v *= ph;
-    std::vector<ld> U(m * k);
-    for (int i = 0; i < m; ++i) {
-      U[i * k + 0] = xv[i].real();
-      if (k == 2) U[i * k + 1] = xv[i].imag();
+  std::vector<ld> R, Q, Qinv;
+  if (basis == 1) {
+    if (!eigen_basis(s, Ainv, groups, t, Q, R, err, errlen)) return 1;
+    if (!invert_ld(s, Q, Qinv)) { snprintf(err, errlen, "eigenvector basis is singular"); return 1; }
+  } else {
+    R = Ainv;
+    Q.assign(s * s, 0);
+    for (int k = 0; k < s; ++k) Q[k * s + k] = 1;
+    int off = 0;
+    for (size_t g = 0; g < groups.size(); ++g) {
+      int m = s - off, k = groups[g].size;
+      if (m == k) { off += k; break; }
+      std::vector<cld> B(m * m);
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) B[i * m + j] = R[(off + i) * s + off + j];
+      for (int i = 0; i < m; ++i) B[i * m + i] -= groups[g].lam;
+      std::vector<cld> xv;
+      null_vector(m, B, xv);
+      // fix the global phase: make the largest component real
+      int big = 0;
+      for (int i = 1; i < m; ++i)
+        if (std::abs(xv[i]) > std::abs(xv[big])) big = i;
+      cld ph = std::conj(xv[big]) / std::abs(xv[big]);
+      for (auto& v : xv) v *= ph;
+      std::vector<ld> U(m * k);
+      for (int i = 0; i < m; ++i) {
+        U[i * k + 0] = xv[i].real();
+        if (k == 2) U[i * k + 1] = xv[i].imag();
+      }
+      std::vector<ld> H;
+      complete_basis(m, k, U, H);
+      apply_similarity(s, off, m, H, R, Q);
+      for (int i = off + k; i < s; ++i)
+        for (int j = off; j < off + k; ++j) R[i * s + j] = 0;
+      off += k;
     }
-    std::vector<ld> H;
-    complete_basis(m, k, U, H);
-    apply_similarity(s, off, m, H, R, Q);
-    for (int i = off + k; i < s; ++i)
-      for (int j = off; j < off + k; ++j) R[i * s + j] = 0;
-    off += k;
-  }
-  // block structure and standardization of the 2x2 blocks
-  int nb = 0;
-  for (int k = 0; k < s;) {
-    bool two = (k + 1 < s) && std::fabs(R[(k + 1) * s + k]) > 1e-12L * (1 + std::fabs(R[k * s + k]));
-    if (two) {
-      ld pp = R[k * s + k], qq = R[k * s + k + 1], rr = R[(k + 1) * s + k], tt = R[(k + 1) * s + k + 1];
-      ld theta;
-      if (std::fabs(qq + rr) > 1e-30L) theta = 0.5L * std::atan((pp - tt) / (qq + rr));
-      else theta = (std::fabs(pp - tt) > 0) ? 0.78539816339744830961566084581987572L : 0;
-      std::vector<ld> G = {std::cos(theta), std::sin(theta), -std::sin(theta), std::cos(theta)};
-      std::vector<ld> R2 = R, Q2 = Q;
-      apply_similarity(s, k, 2, G, R2, Q2);
-      if (std::fabs(R2[k * s + k] - R2[(k + 1) * s + k + 1]) > 1e-14L * (1 + std::fabs(pp))) {
-        G = {std::cos(-theta), std::sin(-theta), -std::sin(-theta), std::cos(-theta)};
-        R2 = R; Q2 = Q;
+    // block structure and standardization of the 2x2 blocks
+    int nb = 0;
+    for (int k = 0; k < s;) {
+      bool two = (k + 1 < s) && std::fabs(R[(k + 1) * s + k]) > 1e-12L * (1 + std::fabs(R[k * s + k]));
+      if (two) {
+        ld pp = R[k * s + k], qq = R[k * s + k + 1], rr = R[(k + 1) * s + k], tt = R[(k + 1) * s + k + 1];
+        ld theta;
+        if (std::fabs(qq + rr) > 1e-30L) theta = 0.5L * std::atan((pp - tt) / (qq + rr));
+        else theta = (std::fabs(pp - tt) > 0) ? 0.78539816339744830961566084581987572L : 0;
+        std::vector<ld> G = {std::cos(theta), std::sin(theta), -std::sin(theta), std::cos(theta)};
+        std::vector<ld> R2 = R, Q2 = Q;
         apply_similarity(s, k, 2, G, R2, Q2);
-      }
-      R = R2; Q = Q2;
-      ld d = 0.5L * (R[k * s + k] + R[(k + 1) * s + k + 1]);
-      R[k * s + k] = R[(k + 1) * s + k + 1] = d;
-      t->bstart[nb] = k; t->bsize[nb] = 2;
-      t->eta[nb] = (double)d;
-      ld beta2 = -R[k * s + k + 1] * R[(k + 1) * s + k];
-      if (beta2 <= 0) { snprintf(err, errlen, "2x2 Schur block without a complex pair"); return 1; }
-      t->beta2[nb] = (double)beta2;
-      t->gamma_star[nb] = (double)(d + beta2 / d);
-      ++nb;
-      k += 2;
-    } else {
-      t->bstart[nb] = k; t->bsize[nb] = 1;
-      t->eta[nb] = (double)R[k * s + k];
-      t->beta2[nb] = 0;
-      t->gamma_star[nb] = t->eta[nb];
-      ++nb;
-      k += 1;
-    }
-  }
-  t->nblk = nb;
-  for (int i = 0; i < s; ++i)
-    for (int j = 0; j < s; ++j)
-      if (i > j) {
-        // strictly below the block diagonal must vanish
-        int bi = -1, bj = -1;
-        for (int q = 0; q < nb; ++q) {
-          if (i >= t->bstart[q] && i < t->bstart[q] + t->bsize[q]) bi = q;
-          if (j >= t->bstart[q] && j < t->bstart[q] + t->bsize[q]) bj = q;
+        if (std::fabs(R2[k * s + k] - R2[(k + 1) * s + k + 1]) > 1e-14L * (1 + std::fabs(pp))) {
+          G = {std::cos(-theta), std::sin(-theta), -std::sin(-theta), std::cos(-theta)};
+          R2 = R; Q2 = Q;
+          apply_similarity(s, k, 2, G, R2, Q2);
         }
-        if (bi != bj) R[i * s + j] = 0;
+        R = R2; Q = Q2;
+        ld d = 0.5L * (R[k * s + k] + R[(k + 1) * s + k + 1]);
+        R[k * s + k] = R[(k + 1) * s + k + 1] = d;
+        t->bstart[nb] = k; t->bsize[nb] = 2;
+        t->eta[nb] = (double)d;
+        ld beta2 = -R[k * s + k + 1] * R[(k + 1) * s + k];
+        if (beta2 <= 0) { snprintf(err, errlen, "2x2 Schur block without a complex pair"); return 1; }
+        t->beta2[nb] = (double)beta2;
+        t->gamma_star[nb] = (double)(d + beta2 / d);
+        ++nb;
+        k += 2;
+      } else {
+        t->bstart[nb] = k; t->bsize[nb] = 1;
+        t->eta[nb] = (double)R[k * s + k];
+        t->beta2[nb] = 0;
+        t->gamma_star[nb] = t->eta[nb];
+        ++nb;
+        k += 1;
       }
-  // residual check: Q R Q^T == A0^{-1}
+    }
+    t->nblk = nb;
+    for (int i = 0; i < s; ++i)
+      for (int j = 0; j < s; ++j)
+        if (i > j) {
+          // strictly below the block diagonal must vanish
+          int bi = -1, bj = -1;
+          for (int q = 0; q < nb; ++q) {
+            if (i >= t->bstart[q] && i < t->bstart[q] + t->bsize[q]) bi = q;
+            if (j >= t->bstart[q] && j < t->bstart[q] + t->bsize[q]) bj = q;
+          }
+          if (bi != bj) R[i * s + j] = 0;
+        }
+    Qinv.assign(s * s, 0);
+    for (int i = 0; i < s; ++i)
+      for (int j = 0; j < s; ++j) Qinv[i * s + j] = Q[j * s + i];
+  }
+  // residual check: T R T^{-1} == A0^{-1}
   ld errmax = 0;
   for (int i = 0; i < s; ++i)
     for (int j = 0; j < s; ++j) {
       ld acc = 0;
       for (int a = 0; a < s; ++a)
-        for (int bb = 0; bb < s; ++bb) acc += Q[i * s + a] * R[a * s + bb] * Q[j * s + bb];
+        for (int bb = 0; bb < s; ++bb) acc += Q[i * s + a] * R[a * s + bb] * Qinv[bb * s + j];
       errmax = std::max(errmax, std::fabs(acc - Ainv[i * s + j]));
     }
-  if (errmax > 1e-12L) { snprintf(err, errlen, "real Schur reconstruction error %.3Le", errmax); return 1; }
+  if (errmax > 1e-12L) { snprintf(err, errlen, "A0^{-1} reconstruction error %.3Le", errmax); return 1; }
   for (int i = 0; i < s; ++i) {
     t->b[i] = (double)b[i];
     t->c[i] = (double)c[i];
     for (int j = 0; j < s; ++j) {
       t->A[i * s + j] = (double)A[i * s + j];
       t->Ainv[i * s + j] = (double)Ainv[i * s + j];
-      t->Q[i * s + j] = (double)Q[i * s + j];
+      t->T[i * s + j] = (double)Q[i * s + j];
+      t->Tinv[i * s + j] = (double)Qinv[i * s + j];
       t->R[i * s + j] = (double)R[i * s + j];
     }
   }
-  // T = Q0 R0, the back-transform of Algorithm 1
+  // T R, the back-transform of Algorithm 1 (Q0 R0 in the Schur basis)
   for (int i = 0; i < s; ++i)
     for (int j = 0; j < s; ++j) {
       ld acc = 0;
       for (int a = 0; a < s; ++a) acc += Q[i * s + a] * R[a * s + j];
-      t->QR[i * s + j] = (double)acc;
+      t->TR[i * s + j] = (double)acc;
     }
   return 0;
 }

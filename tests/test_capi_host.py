@@ -43,11 +43,15 @@ def test_library_exports_every_declared_symbol(B):
     assert set(names) == set(B.EXPORTED)
 
 
-@pytest.mark.parametrize("s", [1, 2, 3, 4, 5])
-def test_host_tableau_matches_oracle(B, s):
+FAMILIES = [("gauss", 0, s) for s in (1, 2, 3, 4, 5)] + [("radau", 1, s) for s in (1, 2, 3, 4, 5)] \
+    + [("lobatto", 2, s) for s in (2, 3, 4, 5)]
+
+
+@pytest.mark.parametrize("family,fid,s", FAMILIES)
+def test_host_tableau_matches_oracle(B, family, fid, s):
     from oracle import tableau as tab
-    t = B.irk_tableau(s)
-    A, b, c = tab.gauss(s)
+    t = B.irk_tableau(s, fid)
+    A, b, c = tab.tableau(family, s)
     np.testing.assert_allclose(t["A"], A, atol=1e-15)
     np.testing.assert_allclose(t["b"], b, atol=1e-15)
     np.testing.assert_allclose(t["c"], c, atol=1e-15)
@@ -72,6 +76,42 @@ def test_host_tableau_matches_oracle(B, s):
     assert sorted(ours) == sorted(theirs)
 
 
+@pytest.mark.parametrize("family,fid,s", FAMILIES)
+def test_host_eigen_basis_matches_oracle(B, family, fid, s):
+    """Eigenvector basis: T R T^{-1} = A0^{-1}, Tinv = T^{-1}, R block diagonal
+    with [[eta, beta], [-beta, eta]] blocks equal to the oracle's eigenvalues."""
+    from oracle import tableau as tab
+    A, _, _ = tab.tableau(family, s)
+    Ainv = np.linalg.inv(A)
+    e = B.irk_transform(s, fid, B.IRK_BASIS_EIGEN)
+    T, Ti, R = e["T"], e["Tinv"], e["R"]
+    np.testing.assert_allclose(T @ Ti, np.eye(s), atol=1e-13)
+    np.testing.assert_allclose(T @ R @ Ti, Ainv, atol=1e-11)
+    mask = np.zeros((s, s), bool)
+    k = 0
+    ours = []
+    for m in e["block_sizes"]:
+        mask[k:k + m, k:k + m] = True
+        if m == 2:
+            assert R[k, k] == R[k + 1, k + 1] and R[k, k + 1] == -R[k + 1, k] > 0
+        ours.append((round(R[k, k], 9), round(R[k, k + 1], 9) if m == 2 else 0.0))
+        k += m
+    assert np.all(R[~mask] == 0)
+    To, Ro, blocks = tab.real_eigen_basis(Ainv)
+    theirs = [(round(Ro[k, k], 9), round(Ro[k, k + 1], 9) if m == 2 else 0.0) for (k, m) in blocks]
+    assert ours == theirs  # same eigenvalue order: increasing real part
+    # the Schur transform from the same entry point is orthogonal
+    q = B.irk_transform(s, fid, B.IRK_BASIS_SCHUR)
+    np.testing.assert_allclose(q["Tinv"], q["T"].T, atol=0)
+    np.testing.assert_array_equal(q["T"], B.irk_tableau(s, fid)["Q0"])
+
+
+def test_transform_rejects_bad_arguments(B):
+    for args in [(2, 0, 2), (2, 3, 0), (0, 0, 0), (6, 0, 0), (1, 2, 0)]:
+        with pytest.raises(B.IrkError):
+            B.irk_transform(*args)
+
+
 def test_gauss2_schur_basis_is_identity(B):
     """Eq. Gauss4Radau3_example: A0^{-1} of 2-stage Gauss is already in
     standardized form, so the block is exactly Newton (P-hat block diagonal)."""
@@ -91,8 +131,9 @@ def test_invalid_configs_rejected_before_device(B):
     u0 = np.zeros(256)
     bad = [dict(stages=0), dict(stages=6), dict(n=100), dict(nu=0.0), dict(nu=-1.0),
            dict(op="vsf", mass=0), dict(op="burgers1d", mass=1), dict(family=3),
-           dict(krylov_restart=0), dict(krylov_restart=65), dict(nonlinear_variant=1),
-           dict(mg_precision=3), dict(forcing=1, op="burgers2d")]
+           dict(family=-1), dict(family=2, stages=1), dict(basis=2), dict(basis=-1),
+           dict(krylov_restart=0), dict(krylov_restart=65), dict(nonlinear_variant=5),
+           dict(nonlinear_variant=-1), dict(mg_precision=3), dict(forcing=1, op="burgers2d")]
     for kw in bad:
         cfg = B.irk_config_default(**kw)
         with pytest.raises(B.IrkError) as ei:

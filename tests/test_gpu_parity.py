@@ -52,11 +52,11 @@ def initial(op, n, seed):
     return ovsf.initial_state(w0, 2 * math.pi / n)
 
 
-def oracle_step(p, s, u, t, dt):
+def oracle_step(p, s, u, t, dt, family="gauss"):
     if p.op == "vsf":
-        return ovsf.reduced_step(p, s, u, t, dt)
+        return ovsf.reduced_step(p, s, u, t, dt, family=family)
     linear = "direct" if p.size * s <= 40000 else "gmres"
-    return orc.step(p, s, u, t, dt, linear=linear)
+    return orc.step(p, s, u, t, dt, linear=linear, family=family)
 
 
 # ---------------------------------------------------------------------------
@@ -112,6 +112,7 @@ def test_stage_jacobian_matches_oracle(B, op, n, s):
 def run_parity(B, op, n, s, nu, dt, nsteps, seed=0, device_buffers=False, **cfg):
     p, length = make_problem(op, n, nu, s)
     u0 = initial(op, n, seed)
+    family = cfg.get("family", "gauss")
     per_step, infos = [], []
     u_ref = u0.copy()
     with B.IrkSolver(u0 if op != "vsf" else u0.copy(), op=op, n=n, stages=s, nu=nu,
@@ -122,7 +123,7 @@ def run_parity(B, op, n, s, nu, dt, nsteps, seed=0, device_buffers=False, **cfg)
             sol.set_state(u_ref)
             st = sol.step(t, dt, 1)
             infos.append(st.as_dict())
-            u_next, _, _ = oracle_step(p, s, u_ref, t, dt)
+            u_next, _, _ = oracle_step(p, s, u_ref, t, dt, family)
             per_step.append(rel(sol.state(), u_next))
             u_ref = u_next
             t += dt
@@ -179,6 +180,77 @@ def test_mixed_precision_preconditioner_same_result(B, prec):
 def test_solver_variants_reach_same_fixed_point(B, kw):
     per_step, whole, _ = run_parity(B, "burgers2d", 32, 3, 5e-3, 2e-3, 2, seed=4, **kw)
     assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (kw, per_step, whole)
+
+
+@pytest.mark.parametrize("family,s", [("radau", 1), ("radau", 2), ("radau", 3), ("radau", 5),
+                                      ("lobatto", 2), ("lobatto", 3), ("lobatto", 4)])
+def test_radau_lobatto_burgers1d_parity(B, family, s):
+    """Radau IIA and Lobatto IIIC tableaux (Table 1) through the same solver."""
+    per_step, whole, infos = run_parity(B, "burgers1d", 128, s, 0.01, 2e-3, 3, seed=1,
+                                        family=family)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
+
+
+@pytest.mark.parametrize("op,n,family,s", [("burgers2d", 32, "radau", 3), ("burgers2d", 32, "lobatto", 2),
+                                           ("vsf", 32, "radau", 2), ("vsf", 16, "lobatto", 3)])
+def test_radau_lobatto_2d_parity(B, op, n, family, s):
+    nu, dt = (5e-3, 2e-3) if op == "burgers2d" else (1e-3, 5e-3)
+    per_step, whole, infos = run_parity(B, op, n, s, nu, dt, 2, seed=2, family=family)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
+
+
+@pytest.mark.parametrize("op,n,s,family", [("burgers1d", 128, 2, "gauss"), ("burgers1d", 128, 5, "gauss"),
+                                           ("burgers2d", 32, 3, "gauss"), ("burgers2d", 32, 4, "radau"),
+                                           ("vsf", 32, 3, "gauss")])
+def test_eigenvector_basis_reaches_same_fixed_point(B, op, n, s, family):
+    """The real eigenvector basis of A0^{-1} (non-orthogonal T) in place of the
+    Schur basis: the transform changes the iteration, not the solution."""
+    nu, dt = {"burgers1d": (0.01, 2e-3), "burgers2d": (5e-3, 2e-3), "vsf": (1e-3, 5e-3)}[op]
+    per_step, whole, infos = run_parity(B, op, n, s, nu, dt, 2, seed=6, basis=1, family=family)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 4])
+@pytest.mark.parametrize("op,n,s", [("burgers2d", 32, 3), ("burgers1d", 128, 4), ("vsf", 32, 3)])
+def test_nonlinear_variants_0_1_4(B, variant, op, n, s):
+    """Simplified Newton (0), lumped block diagonal (1) and exact Newton (4, outer
+    FGMRES on the true Jacobian) reach the same fixed point (Sec. 3.2)."""
+    nu, dt = {"burgers1d": (0.01, 2e-3), "burgers2d": (5e-3, 2e-3), "vsf": (1e-3, 5e-3)}[op]
+    per_step, whole, infos = run_parity(B, op, n, s, nu, dt, 2, seed=7, nonlinear_variant=variant)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
+    if variant == 4:
+        assert all(i["outer_its"] > 0 for i in infos), infos
+    else:
+        assert all(i["outer_its"] == 0 for i in infos), infos
+
+
+def test_exact_newton_converges_quadratically(B):
+    """Variant 4 is Newton on the true stage Jacobian: for s = 4 it needs no more
+    iterations than the block upper triangular variant 3, and at most 4 here."""
+    its = {}
+    for v in (3, 4):
+        _, _, infos = run_parity(B, "burgers2d", 32, 4, 5e-3, 4e-3, 2, seed=8, nonlinear_variant=v)
+        its[v] = [i["newton_its"] for i in infos]
+    assert all(a <= b for a, b in zip(its[4], its[3])), its
+    assert max(its[4]) <= 4, its
+
+
+@pytest.mark.parametrize("family,s,k", [("radau", 3, 2), ("lobatto", 3, 1), ("radau", 1, 0)])
+def test_linear_diffusion_pade_radau_lobatto(B, family, s, k):
+    """Per Fourier mode, one step multiplies by the (k, s) Pade approximant of
+    exp(dt lambda_m): k = s-1 for Radau IIA, s-2 for Lobatto IIIC."""
+    n, nu, dt = 64, 0.05, 0.004
+    u0 = np.random.default_rng(s + 10).standard_normal((1, n))
+    with B.IrkSolver(u0, op="diffusion1d", n=n, stages=s, nu=nu, family=family) as sol:
+        sol.step(0.0, dt, 1)
+        u1 = sol.state()
+    f = math.factorial
+    m = np.arange(n)
+    z = -dt * (4 * nu * n * n) * np.sin(np.pi * m / n) ** 2
+    P = sum(f(k + s - i) * f(k) / (f(k + s) * f(i) * f(k - i)) * z ** i for i in range(k + 1))
+    Q = sum(f(k + s - i) * f(s) / (f(k + s) * f(i) * f(s - i)) * (-z) ** i for i in range(s + 1))
+    want = np.real(np.fft.ifft(P / Q * np.fft.fft(u0[0])))
+    assert rel(u1[0], want) <= 1e-9
 
 
 def test_device_buffers_and_minimum_grid(B):

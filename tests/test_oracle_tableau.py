@@ -167,3 +167,138 @@ def test_snsd_remark_bound():
             S = rng.standard_normal((10, 10))
             L = -(S @ S.T) * rng.uniform(0.01, 100)
             assert _kappa_Pgamma(L, eta, beta, g) <= bound * (1 + 1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Radau IIA and Lobatto IIIC (the other rows of Table 1)
+
+def _order_conditions(A, b, c, p, q, r):
+    """B(p), C(q), D(r) simplifying conditions (Butcher)."""
+    for k in range(1, p + 1):
+        assert abs(b @ c ** (k - 1) - 1.0 / k) < 5e-14, ("B", k)
+    for k in range(1, q + 1):
+        np.testing.assert_allclose(A @ c ** (k - 1), c ** k / k, atol=5e-14, err_msg=f"C{k}")
+    for k in range(1, r + 1):
+        np.testing.assert_allclose(b * c ** (k - 1) @ A, b * (1 - c ** k) / k, atol=5e-14,
+                                   err_msg=f"D{k}")
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 5])
+def test_radau_iia_order_conditions(s):
+    """Radau IIA: B(2s-1), C(s), D(s-1); c_s = 1 and b = last row (stiffly accurate)."""
+    A, b, c = tab.radau_iia(s)
+    _order_conditions(A, b, c, 2 * s - 1, s, s - 1)
+    assert c[-1] == 1.0
+    np.testing.assert_allclose(A[-1], b, atol=1e-14)
+    # one order short of Gauss: B(2s) fails
+    assert abs(b @ c ** (2 * s - 1) - 1.0 / (2 * s)) > 1e-6
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 5])
+def test_lobatto_iiic_order_conditions(s):
+    """Lobatto IIIC: B(2s-2), C(s-1), D(s-1); a_i1 = b_1; c_1 = 0, c_s = 1."""
+    A, b, c = tab.lobatto_iiic(s)
+    _order_conditions(A, b, c, 2 * s - 2, s - 1, s - 1)
+    np.testing.assert_allclose(A[:, 0], b[0], atol=1e-15)
+    assert c[0] == 0.0 and c[-1] == 1.0
+    np.testing.assert_allclose(A[-1], b, atol=1e-14)
+
+
+def test_radau_lobatto_textbook_tableaux():
+    """Two- and three-stage tableaux as tabulated by Hairer and Wanner (vol. II, IV.5)."""
+    A, b, c = tab.radau_iia(2)
+    np.testing.assert_allclose(A, [[5 / 12, -1 / 12], [3 / 4, 1 / 4]], atol=1e-15)
+    np.testing.assert_allclose(b, [3 / 4, 1 / 4], atol=1e-15)
+    np.testing.assert_allclose(c, [1 / 3, 1.0], atol=1e-15)
+    r6 = math.sqrt(6.0)
+    A, b, c = tab.radau_iia(3)
+    np.testing.assert_allclose(c, [(4 - r6) / 10, (4 + r6) / 10, 1.0], atol=1e-15)
+    np.testing.assert_allclose(b, [(16 - r6) / 36, (16 + r6) / 36, 1 / 9], atol=1e-15)
+    np.testing.assert_allclose(A[0], [(88 - 7 * r6) / 360, (296 - 169 * r6) / 1800,
+                                      (-2 + 3 * r6) / 225], atol=1e-15)
+    A, b, c = tab.lobatto_iiic(2)
+    np.testing.assert_allclose(A, [[0.5, -0.5], [0.5, 0.5]], atol=1e-15)
+    A, b, c = tab.lobatto_iiic(3)
+    np.testing.assert_allclose(A, [[1 / 6, -1 / 3, 1 / 6], [1 / 6, 5 / 12, -1 / 12],
+                                   [1 / 6, 2 / 3, 1 / 6]], atol=1e-15)
+    np.testing.assert_allclose(b, [1 / 6, 2 / 3, 1 / 6], atol=1e-15)
+
+
+def _pade(k, j, z):
+    """(k, j) Pade approximant of exp(z) (Hairer-Wanner, Thm. IV.3.11)."""
+    P = sum(math.factorial(k + j - i) * math.factorial(k)
+            / (math.factorial(k + j) * math.factorial(i) * math.factorial(k - i)) * z ** i
+            for i in range(k + 1))
+    Q = sum(math.factorial(k + j - i) * math.factorial(j)
+            / (math.factorial(k + j) * math.factorial(i) * math.factorial(j - i)) * (-z) ** i
+            for i in range(j + 1))
+    return P / Q
+
+
+@pytest.mark.parametrize("family,s,k", [("gauss", s, s) for s in (1, 2, 3, 4, 5)]
+                         + [("radau", s, s - 1) for s in (1, 2, 3, 4, 5)]
+                         + [("lobatto", s, s - 2) for s in (2, 3, 4, 5)])
+def test_stability_function_is_pade(family, s, k):
+    """R(z) = 1 + z b^T (I - zA)^{-1} 1 equals the (k, s) Pade approximant:
+    k = s (Gauss), s-1 (Radau IIA), s-2 (Lobatto IIIC)."""
+    A, b, _ = tab.tableau(family, s)
+    for z in (-0.3, -2.0 + 1.5j, 0.7j, -40.0, 1.2 - 0.4j):
+        R = 1 + z * b @ np.linalg.solve(np.eye(s) - z * A, np.ones(s))
+        assert abs(R - _pade(k, s, z)) < 1e-12 * max(1.0, abs(R)), z
+
+
+@pytest.mark.parametrize("family,key", [("radau", "table1_radau_kappa_bounds"),
+                                        ("lobatto", "table1_lobatto_kappa_bounds")])
+@pytest.mark.parametrize("s", [2, 3, 4, 5])
+def test_table1_radau_lobatto(family, key, s):
+    """Table 1 rows for Radau IIA and Lobatto IIIC (Corollary 1 bounds).  Most
+    printed values are rounded up, two (Radau s=5: 2.6021 -> 2.60, Lobatto s=5:
+    1.1918 -> 1.19) to nearest, so each must be one of the two roundings."""
+    A, _, _ = tab.tableau(family, s)
+    Ainv = np.linalg.inv(A)
+    Q0, R0, blocks = tab.real_schur(Ainv)
+    np.testing.assert_allclose(Q0 @ R0 @ Q0.T, Ainv, atol=1e-11)
+    bounds = sorted(tab.kappa_bound(bc["eta"], bc["beta"]) for bc in tab.block_constants(R0, blocks))
+    printed = sorted(GOLDEN[key][str(s)])
+    assert len(bounds) == len(printed)
+    for got, want in zip(bounds, printed):
+        up = math.ceil(100 * got - 1e-9) / 100
+        near = round(100 * got) / 100
+        assert want in (up, near), (got, want)
+    # Assumption of Sec. 2: A0^{-1} positive stable
+    assert all(bc["eta"] > 0 for bc in tab.block_constants(R0, blocks))
+
+
+@pytest.mark.parametrize("family", ["gauss", "radau", "lobatto"])
+@pytest.mark.parametrize("s", [2, 3, 4, 5])
+def test_eigen_basis(family, s):
+    """A0^{-1} = T R T^{-1} with R = diag of [[eta, beta], [-beta, eta]] blocks whose
+    eta, beta are the Schur blocks' (the eigenvalues); d-vectors sum to delta_kl."""
+    A, _, _ = tab.tableau(family, s)
+    Ainv = np.linalg.inv(A)
+    T, R, blocks = tab.real_eigen_basis(Ainv)
+    np.testing.assert_allclose(T @ R @ np.linalg.inv(T), Ainv, atol=1e-11)
+    mask = np.zeros((s, s), bool)
+    for (k, m) in blocks:
+        mask[k:k + m, k:k + m] = True
+        if m == 2:
+            assert R[k, k] == R[k + 1, k + 1] and R[k, k + 1] == -R[k + 1, k] > 0
+    assert np.all(R[~mask] == 0)
+    _, R0, sblocks = tab.real_schur(Ainv)
+    se = sorted((round(b["eta"], 10), round(b["beta"], 10)) for b in tab.block_constants(R0, sblocks))
+    ee = sorted((round(R[k, k], 10), round(R[k, k + 1] if m == 2 else 0.0, 10)) for (k, m) in blocks)
+    assert se == ee
+    d = tab.d_vectors(T, np.linalg.inv(T))
+    np.testing.assert_allclose(d.sum(axis=-1), np.eye(s), atol=1e-12)
+
+
+def test_newton_like_1_lumping_on_radau3_example():
+    """Newton-like(1) on the Radau IIA(3) example (Sec. 3.2): block i keeps only the
+    stage of the largest |d_ii| entry, giving diag(L1, L2) there."""
+    A, _, _ = tab.radau_iia(2)
+    Q0, _, _ = tab.real_schur(np.linalg.inv(A))
+    d = tab.d_vectors(Q0)
+    picks = sorted(int(np.argmax(np.abs(d[i, i]))) for i in range(2))
+    assert picks == [0, 1]
+    np.testing.assert_allclose(sorted(np.max(np.abs(d[i, i])) for i in range(2)),
+                               [GOLDEN["radau_iia3_Phat"]["d11"][0]] * 2, atol=6e-4)
