@@ -226,9 +226,10 @@ def run_ours(args, rank, world):
     u0 = workloads.random_fourier_2d(N, seed=SEED + rank)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def make(stages, prec, profile, variant=3):
+    def make(stages, prec, profile, variant=3, **kw):
         cfg = B.irk_config_default(op="burgers2d", n=N, nu=NU, stages=stages,
-                                   mg_precision=prec, profile=profile, nonlinear_variant=variant)
+                                   mg_precision=prec, profile=profile, nonlinear_variant=variant,
+                                   **kw)
         h = B.irk_create(cfg, torch.from_numpy(u0).to(dev), stream)
         return h
 
@@ -240,7 +241,8 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize(dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(nsteps)]
-        tot = {"newton_its": 0, "krylov_its": 0, "vcycles": 0, "prec_apps": 0, "launches": 0}
+        tot = {"newton_its": 0, "krylov_its": 0, "vcycles": 0, "prec_apps": 0, "launches": 0,
+               "outer_its": 0}
         for k in range(nsteps):
             flush.zero_()
             ev[k][0].record(stream)
@@ -252,6 +254,7 @@ def run_ours(args, rank, world):
             tot["vcycles"] += st.vcycles
             tot["prec_apps"] += st.prec_apps
             tot["launches"] += st.kernel_launches
+            tot["outer_its"] += st.outer_its
         torch.cuda.synchronize(dev)
         ms = [a.elapsed_time(b) for a, b in ev]
         return ms, tot, t
@@ -378,6 +381,32 @@ def run_ours(args, rank, world):
                             "newton_its_per_step": tot2["newton_its"] / 3}
         extra["vsf1024_gauss5"] = vsf_leg(B, torch, dev, stream, flush, timed_steps)
         line["variants"] = extra
+        # ---- the nonlinear iterations of Sec. 3.2 side by side (same workload,
+        # Gauss s=3, FP64): simplified Newton (0), Newton-like (1)-(3), exact
+        # Newton (4); gamma = eta against gamma*; the eigenvector basis; and
+        # the Radau IIA / Lobatto IIIC rows of Table 1 at s=3
+        cmp_ = {}
+        for label, kw in (("variant0", dict(nonlinear_variant=0)),
+                          ("variant1", dict(nonlinear_variant=1)),
+                          ("variant2", dict(nonlinear_variant=2)),
+                          ("variant3", dict(nonlinear_variant=3)),
+                          ("variant4_exact_newton", dict(nonlinear_variant=4)),
+                          ("variant3_gamma_eta", dict(nonlinear_variant=3, gamma_mode=1)),
+                          ("variant3_eigen_basis", dict(nonlinear_variant=3, basis=1)),
+                          ("radau_iia3", dict(nonlinear_variant=3, family=1)),
+                          ("lobatto_iiic3", dict(nonlinear_variant=3, family=2))):
+            kw = dict(kw)
+            var = kw.pop("nonlinear_variant")
+            h = make(3, 0, 0, var, **kw)
+            ms2, tot2, _ = timed_steps(h, 3, 2)
+            B.irk_destroy(h)
+            cmp_[label] = {"steps_per_s": 1e3 / (sum(ms2) / len(ms2)),
+                           "newton_its_per_step": tot2["newton_its"] / 3,
+                           "krylov_its_per_step": tot2["krylov_its"] / 3,
+                           "outer_its_per_step": tot2["outer_its"] / 3,
+                           "vcycles_per_step": tot2["vcycles"] / 3}
+        line["solver_comparison"] = {"workload": "burgers2d 512^2, s=3, dt=2e-3, FP64 V-cycles",
+                                     "runs": cmp_}
         if args.serving_requests > 0:
             line["serving"] = serving_leg(B, args.serving_requests, args.serving_rate)
         # ---- precision report: one step from u0 per V-cycle storage precision
