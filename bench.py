@@ -539,10 +539,15 @@ def read_traffic(kernel_class: str):
         kv = dict(x.split("=", 1) for x in line.split())
         if kv.get("class") != kernel_class:
             continue
-        src = os.path.join(ROOT, "paper_2101_01776_gb300", "csrc", kv.get("source", ""))
-        if not os.path.exists(src):
+        # the kernel's source and the solver that sets its launch mix
+        srcs = [os.path.join(ROOT, "paper_2101_01776_gb300", "csrc", f)
+                for f in kv.get("source", "").split(",")]
+        if not srcs or not all(os.path.exists(f) for f in srcs):
             return None
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        hsh = hashlib.sha256()
+        for f in srcs:
+            hsh.update(open(f, "rb").read())
+        sha = hsh.hexdigest()[:16]
         if sha != kv.get("sha"):
             return None
         return float(kv["dram_bytes_per_launch"])

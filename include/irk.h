@@ -111,7 +111,8 @@ typedef struct {
   int gamma_mode;       /* 0: gamma* = eta + beta^2/eta (Eq. gamma*), 1: gamma = eta */
   int mg_precision;     /* irk_mg_precision of the V-cycle preconditioner */
   int mg_levels;        /* 0 = coarsen down to the coarsest size below */
-  int mg_pre, mg_post;  /* damped-Jacobi sweeps per level; default 2, 2 */
+  int mg_pre, mg_post;  /* damped-Jacobi sweeps per level (rows that are not
+                           shift-dominated, see mg_shifted_sweeps); default 2, 2 */
   int mg_coarse_sweeps; /* sweeps on the coarsest level; default 40 */
   double mg_omega;      /* Jacobi damping; 0 = default (0.8 in 2D, 2/3 in 1D) */
   int profile;          /* 1 = time each kernel class with CUDA events */
@@ -122,6 +123,13 @@ typedef struct {
                            stages, 0 = zero.  The tolerance is relative to
                            ||F(k=0)|| either way; irk_set_state resets it to 0 */
   int basis;            /* irk_basis; default IRK_BASIS_SCHUR */
+  int mg_shifted_sweeps;/* pre- and post-sweeps on shift-dominated rows of 2D
+                           grids (sigma >= 0.15 D on the finest level, D the
+                           Jacobi diagonal), where more smoothing does not
+                           lower the Krylov counts; default 1; 0 = mg_pre/mg_post */
+  double mg_coarse_reduction; /* error reduction the Jacobi sweeps target on a
+                           shift-dominated coarsest level (2..12 sweeps);
+                           default 2e-2; 0 = default */
 } irk_config;
 
 typedef struct {

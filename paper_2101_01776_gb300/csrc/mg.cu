@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
   const int n = lv.n, m = n - 1, ln = lv.logn;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
   const int tid = threadIdx.y * kTX + threadIdx.x;
-  for (int c = 0; c < ncomp; ++c) {
+  for (int c = blockIdx.z; c < ncomp; c += gridDim.z) {
     const long long off = (long long)c * lv.npts;
     if (!first) {
       for (int q = tid; q < (kTY + 4) * (kTX + 4); q += kTX * kTY) {
@@ -471,7 +471,11 @@ void launch_mg_smooth2(int prec, int kind, const MGLevelDesc& lv, int ncomp, dou
                        double cadv, double cdiff, double omega, const void* vel, const void* b,
                        const void* w_in, void* w_out, int first, cudaStream_t st) {
   const MGConst k = mg_const(lv, 2, sigma, cadv, cdiff, omega);
-  const dim3 grid(lv.n / kTX, lv.n / kTY), block(kTX, kTY);
+  // up to 256^2 one CTA per tile and component: twice the warps on a
+  // latency-bound level (the velocity coefficients are then formed per
+  // component); larger levels loop over the components in one CTA
+  const int zsplit = (lv.n <= 256) ? ncomp : 1;
+  const dim3 grid(lv.n / kTX, lv.n / kTY, zsplit), block(kTX, kTY);
   IRK_DISPATCH_PREC(prec, {
     if (kind == MG_ADVECTIVE)
       k_mg_smooth2<TS, MG_ADVECTIVE><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,

@@ -440,6 +440,17 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
             int project_mean, const double* in, double* out) {
   const int nl = mg_depth(h, sigma, cdiff), prec = h->prec, dim = h->dim;
   const double om = h->mg_omega;
+  // shift-dominated rows of 2D grids (sigma >= 0.15 D on the finest level)
+  // take mg_shifted_sweeps pre- and post-sweeps: measured on 2D Burgers and
+  // the VSF vorticity rows, their Krylov counts do not drop with more
+  // smoothing (on the 1D grids they do, so 1D keeps mg_pre/mg_post)
+  int pre = h->cfg.mg_pre, post = h->cfg.mg_post;
+  {
+    const double h0 = h->lev[0].d.h;
+    const double D0 = sigma + 2.0 * dim * cdiff / (h0 * h0);
+    if (dim == 2 && h->cfg.mg_shifted_sweeps > 0 && sigma >= 0.15 * D0)
+      pre = post = h->cfg.mg_shifted_sweeps;
+  }
   const void* vrow[IRK_MAX_LEVELS];
   for (int l = 0; l < nl; ++l) vrow[l] = (row >= 0) ? h->vel[row][l] : nullptr;
   const long long n0 = (long long)ncomp * h->lev[0].d.npts;
@@ -460,7 +471,7 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     MGLevel& lv = h->lev[l];
     cur[l] = lv.w;
     alt[l] = lv.w2;
-    jacobi_sweeps(h, l, kind, ncomp, sigma, cadv, cdiff, om, vrow[l], bl[l], h->cfg.mg_pre, true,
+    jacobi_sweeps(h, l, kind, ncomp, sigma, cadv, cdiff, om, vrow[l], bl[l], pre, true,
                   cur[l], alt[l], nullptr);
     {
       ProfScope ps(h, P_MG_RESID, mg_level_bytes(h, l, 3.0 * ncomp + velf),
@@ -486,12 +497,13 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     } else {
       // shift-dominated coarsest level (sigma >= D/2): undamped Jacobi, whose
       // iteration matrix has norm <= 1 - sigma/D <= 1/2 there, swept to a
-      // 2e-2 reduction, 2..12 sweeps
+      // the target reduction (mg_coarse_reduction, default 2e-2), 2..12 sweeps
       const double hc = lc.d.h;
       const double D = sigma + 2.0 * dim * cdiff / (hc * hc);
       const double omc = (sigma >= 0.5 * D) ? 1.0 : om;
       const double rho = 1.0 - omc * sigma / D;
-      int sweeps = (rho > 0 && rho < 1) ? (int)std::ceil(std::log(2e-2) / std::log(rho)) : 2;
+      const double red = h->cfg.mg_coarse_reduction > 0 ? h->cfg.mg_coarse_reduction : 2e-2;
+      int sweeps = (rho > 0 && rho < 1) ? (int)std::ceil(std::log(red) / std::log(rho)) : 2;
       sweeps = std::max(2, std::min(sweeps, 12));
       cur[c] = lc.w;
       alt[c] = lc.w2;
@@ -507,9 +519,9 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
                    (double)ncomp * lv.d.npts * 3);
       launch_mg_prolong_add(prec, dim, lv.d, ncomp, cur[l + 1], cur[l], h->st);
     }
-    if (h->cfg.mg_post > 0) {
+    if (post > 0) {
       const bool to_out = alias && l == 0;
-      jacobi_sweeps(h, l, kind, ncomp, sigma, cadv, cdiff, om, vrow[l], bl[l], h->cfg.mg_post,
+      jacobi_sweeps(h, l, kind, ncomp, sigma, cadv, cdiff, om, vrow[l], bl[l], post,
                     false, cur[l], alt[l], to_out ? (void*)out : nullptr);
       if (to_out) wrote_out = true;
     }
@@ -1432,6 +1444,8 @@ irk_status validate(const irk_config* c, std::string& err) {
   if (c->mg_precision < 0 || c->mg_precision > 2) { err = "mg_precision must be 0..2"; return IRK_ERR_INVALID; }
   if (c->mg_pre < 1 || c->mg_post < 0 || c->mg_pre > 8 || c->mg_post > 8) { err = "mg sweeps out of range"; return IRK_ERR_INVALID; }
   if (c->mg_coarse_sweeps < 1 || c->mg_coarse_sweeps > 1000) { err = "mg_coarse_sweeps out of range"; return IRK_ERR_INVALID; }
+  if (c->mg_shifted_sweeps < 0 || c->mg_shifted_sweeps > 8) { err = "mg_shifted_sweeps out of range"; return IRK_ERR_INVALID; }
+  if (!(c->mg_coarse_reduction >= 0 && c->mg_coarse_reduction < 1)) { err = "mg_coarse_reduction must be in [0, 1)"; return IRK_ERR_INVALID; }
   if (c->mg_levels < 0 || c->mg_levels > IRK_MAX_LEVELS) { err = "mg_levels out of range"; return IRK_ERR_INVALID; }
   return IRK_OK;
 }
@@ -1700,6 +1714,8 @@ void irk_config_default(irk_config* c) {
   c->mg_pre = 2;
   c->mg_post = 2;
   c->mg_coarse_sweeps = 40;
+  c->mg_shifted_sweeps = 1;
+  c->mg_coarse_reduction = 2e-2;
   c->mg_omega = 0.0;
   c->profile = 0;
   c->use_graphs = 1;

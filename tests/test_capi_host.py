@@ -133,7 +133,9 @@ def test_invalid_configs_rejected_before_device(B):
            dict(op="vsf", mass=0), dict(op="burgers1d", mass=1), dict(family=3),
            dict(family=-1), dict(family=2, stages=1), dict(basis=2), dict(basis=-1),
            dict(krylov_restart=0), dict(krylov_restart=65), dict(nonlinear_variant=5),
-           dict(nonlinear_variant=-1), dict(mg_precision=3), dict(forcing=1, op="burgers2d")]
+           dict(nonlinear_variant=-1), dict(mg_precision=3), dict(forcing=1, op="burgers2d"),
+           dict(mg_shifted_sweeps=-1), dict(mg_shifted_sweeps=9), dict(mg_coarse_reduction=1.0),
+           dict(mg_coarse_reduction=-0.1)]
     for kw in bad:
         cfg = B.irk_config_default(**kw)
         with pytest.raises(B.IrkError) as ei:
