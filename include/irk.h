@@ -130,6 +130,11 @@ typedef struct {
   double mg_coarse_reduction; /* error reduction the Jacobi sweeps target on a
                            shift-dominated coarsest level (2..12 sweeps);
                            default 2e-2; 0 = default */
+  int mg_coarse_chebyshev; /* 1: on a shift-dominated 2D coarsest level,
+                           Chebyshev-accelerated undamped Jacobi (fewer sweeps
+                           for the same reduction of the symmetric part);
+                           0 (default): plain Jacobi, which measured faster
+                           on the advective workloads */
 } irk_config;
 
 typedef struct {

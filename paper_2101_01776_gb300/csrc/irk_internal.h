@@ -76,6 +76,8 @@ struct ResidualArgs {
 struct OpTerm {
   const double* x;       // ncomp * npts
   const double* combo;   // ncomp * npts or null (no advective part)
+  const double* coef;    // Burgers-2D: 6 * npts coefficient fields of `combo` at this dt
+                         // (launch_combo_coef), or null: formed from combo per point
   double m;              // mass coefficient
   double lin;            // coefficient of the state-independent linear part
 };
@@ -119,7 +121,10 @@ struct MGLevelDesc {
   double h;
 };
 
-enum MGKind { MG_ADVECTIVE = 0, MG_CONSERVATIVE_1D = 1, MG_DIFFUSION = 2 };
+// MG_ADVECTIVE_PRE: MG_ADVECTIVE on a 2D grid with the four off-diagonal
+// coefficients precomputed per point (launch_mg_coef): the `vel` argument of
+// the MG kernels then holds 4 fields (E, W, N, S) instead of the velocity.
+enum MGKind { MG_ADVECTIVE = 0, MG_CONSERVATIVE_1D = 1, MG_DIFFUSION = 2, MG_ADVECTIVE_PRE = 3 };
 
 // ---------------------------------------------------------------------------
 // Launchers (defined in the .cu files).
@@ -127,6 +132,11 @@ void launch_stage_states(const GridDesc& g, const StageStateArgs& a, cudaStream_
 int residual_blocks(const GridDesc& g);
 void launch_residual(const GridDesc& g, const ResidualArgs& a, cudaStream_t st);
 void launch_stage_op(const GridDesc& g, const StageOpArgs& a, cudaStream_t st);
+// Burgers-2D coefficient fields of each combined field (ub, vb), formed once
+// per Newton iteration: dt ub/(2h), dt vb/(2h), dt Dx ub, dt Dy ub, dt Dx vb,
+// dt Dy vb (central differences); coef is ncombo * 6 * npts
+void launch_combo_coef(const GridDesc& g, const double* combos, int ncombo, double dt,
+                       double* coef, cudaStream_t st);
 void launch_stage_update(long long L, int s, const double* QR, const double* yhat, double* K,
                          cudaStream_t st);
 void launch_u_update(long long L, int s, const double* b, double dt, const double* K, double* u,
@@ -181,6 +191,18 @@ void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
                       double cadv, double cdiff, double omega, const void* vel, const void* b,
                       const void* w_in, void* w_out, int first, cudaStream_t st);
 bool mg_smooth2_pays(int prec, int dim, const MGLevelDesc& lv, int first);
+// The four off-diagonal coefficients of the 2D advective level operator,
+// coef = (beta + alpha a_x, beta - alpha a_x, beta + alpha a_y, beta - alpha a_y)
+// with alpha = cadv/(2h), beta = -cdiff/h^2, from the level velocity vel (2 fields)
+void launch_mg_coef(int prec, const MGLevelDesc& lv, double cadv, double cdiff, const void* vel,
+                    void* coef, cudaStream_t st);
+// Two Chebyshev-accelerated undamped Jacobi sweeps (2D, n >= 32): from x_prev
+// (x_{k-1}) and x_cur (x_k) to x_mid (x_{k+1}) and x_out (x_{k+2}) with the
+// three-term weights wa, wb; `first` starts from x_0 = 0
+void launch_mg_cheb2(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
+                     double cadv, double cdiff, const void* vel, const void* b, const void* x_prev,
+                     const void* x_cur, void* x_mid, void* x_out, double wa, double wb, int first,
+                     cudaStream_t st);
 void launch_mg_smooth2(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
                        double cadv, double cdiff, double omega, const void* vel, const void* b,
                        const void* w_in, void* w_out, int first, cudaStream_t st);
@@ -189,6 +211,15 @@ void launch_mg_residual(int prec, int dim, int kind, const MGLevelDesc& lv, int 
                         const void* w, void* r, cudaStream_t st);
 void launch_mg_restrict(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* rf,
                         void* bc, cudaStream_t st);
+// w_f = dinv b_f + P e_c: the prolongation onto a level whose only pre-sweep
+// started from zero and was folded into launch_mg_residual0
+void launch_mg_prolong_set(int prec, int dim, const MGLevelDesc& fine, int ncomp, double sigma,
+                           double cadv, double cdiff, double omega, const void* bf, const void* wc,
+                           void* wf, cudaStream_t st);
+// r = b - A (dinv b): the residual after one damped-Jacobi sweep from zero
+void launch_mg_residual0(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp,
+                         double sigma, double cadv, double cdiff, double omega, const void* vel,
+                         const void* b, void* r, cudaStream_t st);
 void launch_mg_prolong_add(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* wc,
                            void* wf, cudaStream_t st);
 void launch_mg_coarse(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,

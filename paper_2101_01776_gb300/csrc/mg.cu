@@ -89,8 +89,28 @@ __device__ __forceinline__ Coef4<typename Cmp<TS>::T> stencil_coef(
   } else if (KIND == MG_CONSERVATIVE_1D) {
     c.e = fma(alpha, ldv(vel + q.e), beta);
     c.w = fma(-alpha, ldv(vel + q.w), beta);
+  } else if (KIND == MG_ADVECTIVE_PRE) {  // 2D, coefficients precomputed
+    c.e = ldv(vel + q.c);
+    c.w = ldv(vel + npts + q.c);
+    c.n = ldv(vel + 2 * npts + q.c);
+    c.s = ldv(vel + 3 * npts + q.c);
   }
   return c;
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(256) k_mg_coef(MGLevelDesc lv, double alpha64, double beta64,
+                                                 const TS* __restrict__ vel, TS* __restrict__ coef) {
+  typedef typename Cmp<TS>::T TC;
+  const TC alpha = TC(alpha64), beta = TC(beta64);
+  const int npts = lv.npts;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += gridDim.x * blockDim.x) {
+    const TC ax = ldv(vel + p), ay = ldv(vel + npts + p);
+    stv<TS, TC>(coef + p, fma(alpha, ax, beta));
+    stv<TS, TC>(coef + npts + p, fma(-alpha, ax, beta));
+    stv<TS, TC>(coef + 2 * npts + p, fma(alpha, ay, beta));
+    stv<TS, TC>(coef + 3 * npts + p, fma(-alpha, ay, beta));
+  }
 }
 
 // b - sum_k c_k w_k (the off-diagonal part of b - A w)
@@ -177,6 +197,33 @@ __global__ void __launch_bounds__(256) k_mg_residual(MGLevelDesc lv, int ncomp, 
   }
 }
 
+// Residual after one damped-Jacobi sweep from w = 0, without storing that
+// sweep: w = dinv b, so r = b - A w = (1 - omega) b - dinv sum_k c_k b_k.
+// The prolongation then rebuilds w = dinv b + P e (k_mg_prolong<SET>).
+template <typename TS, int DIM, int KIND>
+__global__ void __launch_bounds__(256) k_mg_residual0(MGLevelDesc lv, int ncomp, MGConst k,
+                                                      const TS* __restrict__ vel,
+                                                      const TS* __restrict__ b, TS* __restrict__ r) {
+  typedef typename Cmp<TS>::T TC;
+  const TC alpha = TC(k.alpha), beta = TC(k.beta);
+  const TC dinv = TC(k.dinv), keep = TC(k.keep);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lv.npts; p += gridDim.x * blockDim.x) {
+    const LvIdx q = lv_nbr<DIM>(lv, p);
+    const Coef4<TC> cf = stencil_coef<TS, DIM, KIND>(q, vel, lv.npts, alpha, beta);
+#pragma unroll 1
+    for (int c = 0; c < ncomp; ++c) {
+      const TS* bb = b + (long long)c * lv.npts;
+      TC sum = cf.e * ldv(bb + q.e);
+      sum = fma(cf.w, ldv(bb + q.w), sum);
+      if (DIM == 2) {
+        sum = fma(cf.n, ldv(bb + q.n), sum);
+        sum = fma(cf.s, ldv(bb + q.s), sum);
+      }
+      stv<TS, TC>(r + (long long)c * lv.npts + p, fma(-dinv, sum, keep * ldv(bb + p)));
+    }
+  }
+}
+
 // Two damped-Jacobi sweeps in one launch (2D, temporal blocking): a 32 x 8
 // tile loads w_in on its halo-2 window into shared memory, computes the first
 // sweep on the halo-1 window (340 points, 11 warp passes against 8 for the
@@ -196,16 +243,24 @@ __device__ __forceinline__ float round_to_storage<__nv_bfloat16>(float v) {
   return __bfloat162float(__float2bfloat16_rn(v));
 }
 
-template <typename TS, int KIND>
+// CHEB: Chebyshev acceleration of undamped Jacobi (k.keep = 0): each sweep
+// becomes x_new = x_prev + omega (J(x) - x_prev), with x_prev the iterate
+// before x; the pair reads x_{k-1} (w_prev) and x_k (w_in) and writes x_{k+1}
+// (w_mid) and x_{k+2} (w_out).  `first`: x_0 = 0 (then w_in, w_prev unused).
+template <typename TS, int KIND, bool CHEB>
 __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int ncomp, MGConst k,
                                                         const TS* __restrict__ vel,
                                                         const TS* __restrict__ b,
                                                         const TS* __restrict__ w_in,
-                                                        TS* __restrict__ w_out, int first) {
+                                                        TS* __restrict__ w_out, int first,
+                                                        const TS* __restrict__ w_prev,
+                                                        TS* __restrict__ w_mid, double wa64,
+                                                        double wb64) {
   typedef typename Cmp<TS>::T TC;
   __shared__ TC s_in[kTY + 4][kTX + 4];
   __shared__ TC s_w1[kTY + 2][kTX + 2];
   const TC alpha = TC(k.alpha), beta = TC(k.beta), dinv = TC(k.dinv), keep = TC(k.keep);
+  const TC wa = TC(wa64), wb = TC(wb64);
   const int n = lv.n, m = n - 1, ln = lv.logn;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
   const int tid = threadIdx.y * kTX + threadIdx.x;
@@ -234,6 +289,9 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
           const TC ax = ldv(vel + gp), ay = ldv(vel + lv.npts + gp);
           ce = fma(alpha, ax, beta); cw = fma(-alpha, ax, beta);
           cn = fma(alpha, ay, beta); cs = fma(-alpha, ay, beta);
+        } else if (KIND == MG_ADVECTIVE_PRE) {
+          ce = ldv(vel + gp); cw = ldv(vel + lv.npts + gp);
+          cn = ldv(vel + 2 * lv.npts + gp); cs = ldv(vel + 3 * lv.npts + gp);
         }
         const int sy = ly + 1, sx = lx + 1;  // position in s_in
         TC t = bc;
@@ -242,8 +300,14 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
         t = fma(-cn, s_in[sy + 1][sx], t);
         t = fma(-cs, s_in[sy - 1][sx], t);
         v = fma(dinv, t, keep * s_in[sy][sx]);
+        if (CHEB) {
+          const TC xp = ldv(w_prev + off + gp);
+          v = fma(wa, v - xp, xp);
+        }
       }
-      s_w1[ly][lx] = round_to_storage<TS>(v);
+      v = round_to_storage<TS>(v);
+      s_w1[ly][lx] = v;
+      if (CHEB && lx >= 1 && lx <= kTX && ly >= 1 && ly <= kTY) stv<TS, TC>(w_mid + off + gp, v);
     }
     __syncthreads();
     // sweep 2 on the tile
@@ -256,6 +320,9 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
         const TC ax = ldv(vel + gp), ay = ldv(vel + lv.npts + gp);
         ce = fma(alpha, ax, beta); cw = fma(-alpha, ax, beta);
         cn = fma(alpha, ay, beta); cs = fma(-alpha, ay, beta);
+      } else if (KIND == MG_ADVECTIVE_PRE) {
+        ce = ldv(vel + gp); cw = ldv(vel + lv.npts + gp);
+        cn = ldv(vel + 2 * lv.npts + gp); cs = ldv(vel + 3 * lv.npts + gp);
       }
       const int sy = ly + 1, sx = lx + 1;
       TC t = ldv(b + off + gp);
@@ -263,7 +330,12 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
       t = fma(-cw, s_w1[sy][sx - 1], t);
       t = fma(-cn, s_w1[sy + 1][sx], t);
       t = fma(-cs, s_w1[sy - 1][sx], t);
-      stv<TS, TC>(w_out + off + gp, fma(dinv, t, keep * s_w1[sy][sx]));
+      TC v = fma(dinv, t, keep * s_w1[sy][sx]);
+      if (CHEB) {
+        const TC xp = first ? TC(0) : s_in[sy + 1][sx + 1];  // x_k at this point
+        v = fma(wb, v - xp, xp);
+      }
+      stv<TS, TC>(w_out + off + gp, v);
     }
     __syncthreads();
   }
@@ -278,6 +350,7 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MGLevelDesc fine, int ncomp
   const int nc = fine.n >> 1, logc = fine.logn - 1, m = fine.n - 1;
   const int ncpts = (DIM == 1) ? nc : nc * nc;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < ncpts; p += gridDim.x * blockDim.x) {
+#pragma unroll 1
     for (int c = 0; c < ncomp; ++c) {
       const TS* f = rf + (long long)c * fine.npts;
       TC v;
@@ -305,34 +378,38 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MGLevelDesc fine, int ncomp
 // One thread per coarse point updates the 2x2 (1D: 2) fine points it owns:
 // (2I,2J) += c00, (2I+1,2J) += (c00+c10)/2, (2I,2J+1) += (c00+c01)/2,
 // (2I+1,2J+1) += (c00+c10+c01+c11)/4.
-template <typename TS, int DIM>
+template <typename TS, int DIM, bool SET>
 __global__ void __launch_bounds__(256) k_mg_prolong_add(MGLevelDesc fine, int ncomp,
                                                         const TS* __restrict__ wc,
-                                                        TS* __restrict__ wf) {
+                                                        TS* __restrict__ wf,
+                                                        const TS* __restrict__ bf, double dinv64) {
+  // SET: w_f = dinv b_f + P e (the fine iterate was one sweep from zero and
+  // was never stored); otherwise w_f += P e
   typedef typename Cmp<TS>::T TC;
   const int nc = fine.n >> 1, logc = fine.logn - 1, mc = nc - 1;
   const int ncpts = (DIM == 1) ? nc : nc * nc;
-  const TC half = TC(0.5), quarter = TC(0.25);
+  const TC half = TC(0.5), quarter = TC(0.25), dinv = TC(dinv64);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < ncpts; p += gridDim.x * blockDim.x) {
     for (int c = 0; c < ncomp; ++c) {
       const TS* g = wc + (long long)c * ncpts;
       TS* f = wf + (long long)c * fine.npts;
+      const TS* fb = SET ? bf + (long long)c * fine.npts : nullptr;
+      auto base = [&](long long o) -> TC { return SET ? dinv * ldv(fb + o) : ldv(f + o); };
       if (DIM == 1) {
         const TC c0 = ldv(g + p), c1 = ldv(g + ((p + 1) & mc));
-        stv<TS, TC>(f + 2 * p, ldv(f + 2 * p) + c0);
-        stv<TS, TC>(f + 2 * p + 1, ldv(f + 2 * p + 1) + half * (c0 + c1));
+        stv<TS, TC>(f + 2 * p, base(2 * p) + c0);
+        stv<TS, TC>(f + 2 * p + 1, base(2 * p + 1) + half * (c0 + c1));
       } else {
         const int I = p & mc, J = p >> logc;
         const int I1 = (I + 1) & mc, J1 = (J + 1) & mc;
         const TC c00 = ldv(g + p), c10 = ldv(g + (J << logc) + I1);
         const TC c01 = ldv(g + (J1 << logc) + I), c11 = ldv(g + (J1 << logc) + I1);
         const int lf = fine.logn;
-        TS* r0 = f + ((2 * J) << lf) + 2 * I;
-        TS* r1 = r0 + fine.n;
-        stv<TS, TC>(r0, ldv(r0) + c00);
-        stv<TS, TC>(r0 + 1, ldv(r0 + 1) + half * (c00 + c10));
-        stv<TS, TC>(r1, ldv(r1) + half * (c00 + c01));
-        stv<TS, TC>(r1 + 1, ldv(r1 + 1) + quarter * ((c00 + c10) + (c01 + c11)));
+        const long long o0 = ((long long)(2 * J) << lf) + 2 * I, o1 = o0 + fine.n;
+        stv<TS, TC>(f + o0, base(o0) + c00);
+        stv<TS, TC>(f + o0 + 1, base(o0 + 1) + half * (c00 + c10));
+        stv<TS, TC>(f + o1, base(o1) + half * (c00 + c01));
+        stv<TS, TC>(f + o1 + 1, base(o1 + 1) + quarter * ((c00 + c10) + (c01 + c11)));
       }
     }
   }
@@ -444,6 +521,19 @@ size_t mg_elem_size(int prec) {
       else { constexpr int DIM = 1, KIND = MG_DIFFUSION; __VA_ARGS__; }                          \
     } else {                                                                              \
       if ((kind) == MG_ADVECTIVE) { constexpr int DIM = 2, KIND = MG_ADVECTIVE; __VA_ARGS__; }   \
+      else if ((kind) == MG_ADVECTIVE_PRE) { constexpr int DIM = 2, KIND = MG_ADVECTIVE_PRE; __VA_ARGS__; } \
+      else { constexpr int DIM = 2, KIND = MG_DIFFUSION; __VA_ARGS__; }                          \
+    }                                                                                     \
+  } while (0)
+
+#define IRK_DISPATCH_DK_VEL(dim, kind, ...)                                                  \
+  do {                                                                                    \
+    if ((dim) == 1) {                                                                     \
+      if ((kind) == MG_ADVECTIVE) { constexpr int DIM = 1, KIND = MG_ADVECTIVE; __VA_ARGS__; }   \
+      else if ((kind) == MG_CONSERVATIVE_1D) { constexpr int DIM = 1, KIND = MG_CONSERVATIVE_1D; __VA_ARGS__; } \
+      else { constexpr int DIM = 1, KIND = MG_DIFFUSION; __VA_ARGS__; }                          \
+    } else {                                                                              \
+      if ((kind) == MG_ADVECTIVE) { constexpr int DIM = 2, KIND = MG_ADVECTIVE; __VA_ARGS__; }   \
       else { constexpr int DIM = 2, KIND = MG_DIFFUSION; __VA_ARGS__; }                          \
     }                                                                                     \
   } while (0)
@@ -478,11 +568,34 @@ void launch_mg_smooth2(int prec, int kind, const MGLevelDesc& lv, int ncomp, dou
   const dim3 grid(lv.n / kTX, lv.n / kTY, zsplit), block(kTX, kTY);
   IRK_DISPATCH_PREC(prec, {
     if (kind == MG_ADVECTIVE)
-      k_mg_smooth2<TS, MG_ADVECTIVE><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
-          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
+      k_mg_smooth2<TS, MG_ADVECTIVE, false><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+          (const TS*)b, (const TS*)w_in, (TS*)w_out, first, nullptr, nullptr, 1.0, 1.0);
+    else if (kind == MG_ADVECTIVE_PRE)
+      k_mg_smooth2<TS, MG_ADVECTIVE_PRE, false><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+          (const TS*)b, (const TS*)w_in, (TS*)w_out, first, nullptr, nullptr, 1.0, 1.0);
     else
-      k_mg_smooth2<TS, MG_DIFFUSION><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
-          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
+      k_mg_smooth2<TS, MG_DIFFUSION, false><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+          (const TS*)b, (const TS*)w_in, (TS*)w_out, first, nullptr, nullptr, 1.0, 1.0);
+  });
+}
+
+void launch_mg_cheb2(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
+                     double cadv, double cdiff, const void* vel, const void* b, const void* x_prev,
+                     const void* x_cur, void* x_mid, void* x_out, double wa, double wb, int first,
+                     cudaStream_t st) {
+  const MGConst k = mg_const(lv, 2, sigma, cadv, cdiff, 1.0);  // undamped: keep = 0
+  const int zsplit = (lv.n <= 256) ? ncomp : 1;
+  const dim3 grid(lv.n / kTX, lv.n / kTY, zsplit), block(kTX, kTY);
+  IRK_DISPATCH_PREC(prec, {
+    if (kind == MG_ADVECTIVE)
+      k_mg_smooth2<TS, MG_ADVECTIVE, true><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+          (const TS*)b, (const TS*)x_cur, (TS*)x_out, first, (const TS*)x_prev, (TS*)x_mid, wa, wb);
+    else if (kind == MG_ADVECTIVE_PRE)
+      k_mg_smooth2<TS, MG_ADVECTIVE_PRE, true><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+          (const TS*)b, (const TS*)x_cur, (TS*)x_out, first, (const TS*)x_prev, (TS*)x_mid, wa, wb);
+    else
+      k_mg_smooth2<TS, MG_DIFFUSION, true><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+          (const TS*)b, (const TS*)x_cur, (TS*)x_out, first, (const TS*)x_prev, (TS*)x_mid, wa, wb);
   });
 }
 
@@ -510,10 +623,42 @@ void launch_mg_prolong_add(int prec, int dim, const MGLevelDesc& fine, int ncomp
   const long long nc = dim == 1 ? fine.n / 2 : (long long)(fine.n / 2) * (fine.n / 2);
   IRK_DISPATCH_PREC(prec, {
     if (dim == 1)
-      k_mg_prolong_add<TS, 1><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc, (TS*)wf);
+      k_mg_prolong_add<TS, 1, false><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc,
+                                                                   (TS*)wf, nullptr, 0.0);
     else
-      k_mg_prolong_add<TS, 2><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc, (TS*)wf);
+      k_mg_prolong_add<TS, 2, false><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc,
+                                                                   (TS*)wf, nullptr, 0.0);
   });
+}
+
+void launch_mg_prolong_set(int prec, int dim, const MGLevelDesc& fine, int ncomp, double sigma,
+                           double cadv, double cdiff, double omega, const void* bf, const void* wc,
+                           void* wf, cudaStream_t st) {
+  const MGConst k = mg_const(fine, dim, sigma, cadv, cdiff, omega);
+  const long long nc = dim == 1 ? fine.n / 2 : (long long)(fine.n / 2) * (fine.n / 2);
+  IRK_DISPATCH_PREC(prec, {
+    if (dim == 1)
+      k_mg_prolong_add<TS, 1, true><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc,
+                                                                  (TS*)wf, (const TS*)bf, k.dinv);
+    else
+      k_mg_prolong_add<TS, 2, true><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc,
+                                                                  (TS*)wf, (const TS*)bf, k.dinv);
+  });
+}
+
+void launch_mg_coef(int prec, const MGLevelDesc& lv, double cadv, double cdiff, const void* vel,
+                    void* coef, cudaStream_t st) {
+  const MGConst k = mg_const(lv, 2, 0.0, cadv, cdiff, 1.0);
+  IRK_DISPATCH_PREC(prec, (k_mg_coef<TS><<<grid_for(lv.npts), 256, 0, st>>>(
+      lv, k.alpha, k.beta, (const TS*)vel, (TS*)coef)));
+}
+
+void launch_mg_residual0(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp,
+                         double sigma, double cadv, double cdiff, double omega, const void* vel,
+                         const void* b, void* r, cudaStream_t st) {
+  const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, omega);
+  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_residual0<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
+      lv, ncomp, k, (const TS*)vel, (const TS*)b, (TS*)r))));
 }
 
 void launch_mg_coarse(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
@@ -522,7 +667,8 @@ void launch_mg_coarse(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
   IRK_DISPATCH_PREC(prec, {
     typedef typename Cmp<TS>::T TC;
     const size_t smem = sizeof(TC) * ((size_t)3 * ncomp * lv.npts + (size_t)dim * lv.npts);
-    IRK_DISPATCH_DK(dim, kind, (k_mg_coarse<TS, DIM, KIND><<<1, 256, smem, st>>>(
+    // the one-CTA kernel takes the velocity (MG_ADVECTIVE), never precomputed coefficients
+    IRK_DISPATCH_DK_VEL(dim, kind, (k_mg_coarse<TS, DIM, KIND><<<1, 256, smem, st>>>(
         lv, ncomp, sigma, cadv, cdiff, omega, sweeps, project_mean, (const TS*)vel,
         (const TS*)b, (TS*)w)));
   });

@@ -49,6 +49,7 @@ struct PendingEvent {
 struct MGLevel {
   MGLevelDesc d;
   void *w, *w2, *b, *r;
+  void *w3, *w4;  // Chebyshev iterates on levels that can be the coarsest (l >= 1)
 };
 
 }  // namespace
@@ -71,6 +72,7 @@ struct irk_handle {
 
   double *u = nullptr, *u_save = nullptr, *K = nullptr, *Y = nullptr, *rhs = nullptr,
          *yhat = nullptr, *combos = nullptr, *zbuf = nullptr, *tmp = nullptr, *tmp2 = nullptr;
+  double* coef = nullptr;  // Burgers-2D: 6 coefficient fields per combined field
   int ncombo = 0;
   int combo_of[IRK_MAXS][IRK_MAXS];
   double Dq[IRK_MAX_COMBOS * IRK_MAXS];
@@ -117,6 +119,11 @@ struct irk_handle {
   size_t esz = 8;
   MGLevel lev[IRK_MAX_LEVELS];
   void* vel[IRK_MAXS][IRK_MAX_LEVELS];
+  // FP64 2D advective rows: the four off-diagonal coefficients per level,
+  // formed once per Newton iteration from vel (valid for coef_cadv/cdiff)
+  bool use_pre = false;
+  void* coefh[IRK_MAXS][IRK_MAX_LEVELS] = {};
+  double coef_cadv = 0.0, coef_cdiff = 0.0;
   double mg_omega = 0.8;
 
   irk_stats stats;
@@ -263,11 +270,21 @@ const double* combo_ptr(irk_handle* h, int r, int q) {
   return idx < 0 ? nullptr : h->combos + (long long)idx * h->L;
 }
 
+bool keep_coupling(irk_handle* h, int r, int q);
+
+// The advective part of term (r, q): its combined field and, for Burgers-2D,
+// the coefficient fields formed from it once per Newton iteration.
+void set_combo(irk_handle* h, OpTerm& t, int r, int q) {
+  t.combo = keep_coupling(h, r, q) ? combo_ptr(h, r, q) : nullptr;
+  t.coef = (t.combo && h->coef) ? h->coef + (long long)h->combo_of[r][q] * 6 * h->npts : nullptr;
+}
+
 double stage_op_bytes(irk_handle* h, const StageOpArgs& a) {
   double words = 0;
   for (int r = 0; r < a.nrow; ++r) {
     words += h->L * (1 + (a.row[r].base ? 1 : 0));
-    for (int t = 0; t < a.row[r].nterm; ++t) words += h->L * (1 + (a.row[r].t[t].combo ? 1 : 0));
+    for (int t = 0; t < a.row[r].nterm; ++t)
+      words += h->L * (1 + (a.row[r].t[t].coef ? 3 : a.row[r].t[t].combo ? 1 : 0));
   }
   words += a.copy_len * 2.0;
   return words * 8.0;
@@ -276,9 +293,14 @@ double stage_op_bytes(irk_handle* h, const StageOpArgs& a) {
 double stage_op_flops(irk_handle* h, const StageOpArgs& a) {
   double f = 0;
   for (int r = 0; r < a.nrow; ++r)
-    for (int t = 0; t < a.row[r].nterm; ++t)
-      f += h->npts * (2.0 * h->C + (a.row[r].t[t].combo ? jadv_flops_per_point(h->g.op) : 0) +
-                      (a.row[r].t[t].lin != 0 ? jlin_flops_per_point(h->g.op) : 0));
+    for (int t = 0; t < a.row[r].nterm; ++t) {
+      const OpTerm& tm = a.row[r].t[t];
+      if (tm.coef)  // Burgers-2D coefficient form: 4 coefficients + 2 x (5 FMA, 1 add, 1 mul) + 2 adds
+        f += h->npts * 30.0;
+      else
+        f += h->npts * (2.0 * h->C + (tm.combo ? jadv_flops_per_point(h->g.op) : 0) +
+                        (tm.lin != 0 ? jlin_flops_per_point(h->g.op) : 0));
+    }
   return f;
 }
 
@@ -308,7 +330,7 @@ void block_matvec_dt(irk_handle* h, double dt, int blk, const double* x, double*
       const int q = a0 + qq;
       OpTerm& t = row.t[row.nterm++];
       t.x = x + (long long)qq * h->L;
-      t.combo = keep_coupling(h, r, q) ? combo_ptr(h, r, q) : nullptr;
+      set_combo(h, t, r, q);
       t.m = h->tab.R[r * s + q];
       t.lin = (r == q) ? 1.0 : 0.0;
     }
@@ -337,7 +359,7 @@ void upper_coupling(irk_handle* h, double dt, int blk, double* z) {
     for (int l = first_later; l < s; ++l) {
       OpTerm& t = row.t[row.nterm++];
       t.x = h->yhat + (long long)l * h->L;
-      t.combo = keep_coupling(h, r, l) ? combo_ptr(h, r, l) : nullptr;
+      set_combo(h, t, r, l);
       t.m = h->tab.R[r * s + l];
       t.lin = 0;
     }
@@ -392,7 +414,33 @@ void mg_setup(irk_handle* h, double dt) {
       launch_mg_restrict(h->prec, h->dim, h->lev[l].d, h->dim, h->vel[k][l], h->vel[k][l + 1],
                          h->st);
     }
+    if (h->use_pre)
+      for (int l = 0; l < depth; ++l) {
+        ProfScope ps(h, P_MG_SETUP, mg_level_bytes(h, l, 6.0), 4.0 * h->lev[l].d.npts);
+        launch_mg_coef(h->prec, h->lev[l].d, dt, dt * h->g.nu, h->vel[k][l], h->coefh[k][l],
+                       h->st);
+      }
   }
+  h->coef_cadv = dt;
+  h->coef_cdiff = dt * h->g.nu;
+}
+
+// FP64 operations (an FMA counts 2) per point of the MG kernels as built:
+// per component a sweep takes one FMA per neighbour, the diagonal FMA and
+// the (1 - omega) product; the residual one FMA per neighbour and the
+// diagonal FMA.  Coefficients formed on the fly cost one FMA per neighbour
+// and point (shared by the components); precomputed ones (MG_ADVECTIVE_PRE)
+// and the constant diffusion stencil cost nothing per sweep.
+double mg_coef_flops(int kind, int dim) {
+  if (kind == MG_ADVECTIVE) return 4.0 * dim;
+  if (kind == MG_CONSERVATIVE_1D) return 4.0;
+  return 0.0;
+}
+double mg_sweep_flops(int kind, int dim, int ncomp) {
+  return ncomp * (4.0 * dim + 3.0) + mg_coef_flops(kind, dim);
+}
+double mg_resid_flops(int kind, int dim, int ncomp) {
+  return ncomp * (4.0 * dim + 2.0) + mg_coef_flops(kind, dim);
 }
 
 // `sweeps` damped-Jacobi sweeps on level l (from w = 0 when from_zero); the
@@ -405,8 +453,10 @@ void jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, doub
                    bool from_zero, void*& cur, void*& alt, void* last) {
   const MGLevelDesc& d = h->lev[l].d;
   const int prec = h->prec, dim = h->dim;
-  const int velf = (kind == MG_DIFFUSION) ? 0 : (kind == MG_CONSERVATIVE_1D ? 1 : dim);
-  const double fpp = 2.0 * (4 * dim + 6);  // flops per point and component of one sweep
+  const int velf = (kind == MG_DIFFUSION) ? 0
+                   : (kind == MG_ADVECTIVE_PRE) ? 4 : (kind == MG_CONSERVATIVE_1D ? 1 : dim);
+  const double fsw = mg_sweep_flops(kind, dim, ncomp) * d.npts;  // one sweep
+  const double f0 = (double)ncomp * d.npts;                       // a sweep from zero
   const double pts = (double)ncomp * d.npts;
   int sw = 0;
   while (sw < sweeps) {
@@ -417,14 +467,14 @@ void jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, doub
     if (sw + 1 < sweeps && mg_smooth2_pays(prec, dim, d, first) && !(ends_pair && last == b)) {
       if (ends_pair && last) dst = last;
       ProfScope ps(h, P_MG_SMOOTH2, mg_level_bytes(h, l, (first ? 2.0 : 3.0) * ncomp + velf),
-                   pts * (first ? 1 + fpp : 2 * fpp));
+                   first ? f0 + fsw : 2.0 * fsw);
       launch_mg_smooth2(prec, kind, d, ncomp, sigma, cadv, cdiff, om, vel, b, cur, dst, first,
                         h->st);
       sw += 2;
     } else {
       if (sw + 1 == sweeps && last) dst = last;
       ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, l, first ? 2.0 * ncomp : 3.0 * ncomp + velf),
-                   pts * (first ? 1 : fpp));
+                   first ? f0 : fsw);
       launch_mg_smooth(prec, dim, kind, d, ncomp, sigma, cadv, cdiff, om, vel, b, cur, dst, first,
                        h->st);
       sw += 1;
@@ -444,15 +494,22 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
   // take mg_shifted_sweeps pre- and post-sweeps: measured on 2D Burgers and
   // the VSF vorticity rows, their Krylov counts do not drop with more
   // smoothing (on the 1D grids they do, so 1D keeps mg_pre/mg_post)
-  int pre = h->cfg.mg_pre, post = h->cfg.mg_post;
+  int npre = h->cfg.mg_pre, post = h->cfg.mg_post;
   {
     const double h0 = h->lev[0].d.h;
     const double D0 = sigma + 2.0 * dim * cdiff / (h0 * h0);
     if (dim == 2 && h->cfg.mg_shifted_sweeps > 0 && sigma >= 0.15 * D0)
-      pre = post = h->cfg.mg_shifted_sweeps;
+      npre = post = h->cfg.mg_shifted_sweeps;
   }
   const void* vrow[IRK_MAX_LEVELS];
   for (int l = 0; l < nl; ++l) vrow[l] = (row >= 0) ? h->vel[row][l] : nullptr;
+  // FP64 2D advective rows read the precomputed coefficients (kind kk, crow);
+  // the one-CTA coarsest solve keeps the velocity form (kind, vrow)
+  const bool pre = h->use_pre && kind == MG_ADVECTIVE && row >= 0 && cadv == h->coef_cadv &&
+                   cdiff == h->coef_cdiff;
+  const int kk = pre ? MG_ADVECTIVE_PRE : kind;
+  const void* crow[IRK_MAX_LEVELS];
+  for (int l = 0; l < nl; ++l) crow[l] = pre ? h->coefh[row][l] : vrow[l];
   const long long n0 = (long long)ncomp * h->lev[0].d.npts;
   const bool alias = (prec == IRK_MG_FP64);
   const void* bl[IRK_MAX_LEVELS];
@@ -465,18 +522,27 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
   }
   void* cur[IRK_MAX_LEVELS];
   void* alt[IRK_MAX_LEVELS];
-  const int velf = (kind == MG_DIFFUSION) ? 0 : (kind == MG_CONSERVATIVE_1D ? 1 : dim);
-  const double smooth_flops_pp = 2.0 * (4 * dim + 6);
+  const int velf = (kk == MG_DIFFUSION) ? 0
+                   : (kk == MG_ADVECTIVE_PRE) ? 4 : (kk == MG_CONSERVATIVE_1D ? 1 : dim);
+  const double fsweep = mg_sweep_flops(kk, dim, ncomp), fresid = mg_resid_flops(kk, dim, ncomp);
+  // a single pre-sweep starts from zero (w = dinv b): it is folded into the
+  // residual and rebuilt by the prolongation, one launch less per level
+  const bool fold_pre = (npre == 1);
   for (int l = 0; l + 1 < nl; ++l) {
     MGLevel& lv = h->lev[l];
     cur[l] = lv.w;
     alt[l] = lv.w2;
-    jacobi_sweeps(h, l, kind, ncomp, sigma, cadv, cdiff, om, vrow[l], bl[l], pre, true,
-                  cur[l], alt[l], nullptr);
-    {
+    if (fold_pre) {
+      ProfScope ps(h, P_MG_RESID, mg_level_bytes(h, l, 2.0 * ncomp + velf),
+                   (fresid + 2.0 * ncomp) * lv.d.npts);
+      launch_mg_residual0(prec, dim, kk, lv.d, ncomp, sigma, cadv, cdiff, om, crow[l], bl[l],
+                          lv.r, h->st);
+    } else {
+      jacobi_sweeps(h, l, kk, ncomp, sigma, cadv, cdiff, om, crow[l], bl[l], npre, true,
+                    cur[l], alt[l], nullptr);
       ProfScope ps(h, P_MG_RESID, mg_level_bytes(h, l, 3.0 * ncomp + velf),
-                   (double)ncomp * lv.d.npts * smooth_flops_pp);
-      launch_mg_residual(prec, dim, kind, lv.d, ncomp, sigma, cadv, cdiff, vrow[l], bl[l], cur[l],
+                   fresid * lv.d.npts);
+      launch_mg_residual(prec, dim, kk, lv.d, ncomp, sigma, cadv, cdiff, crow[l], bl[l], cur[l],
                          lv.r, h->st);
     }
     {
@@ -489,8 +555,8 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     const int c = nl - 1;
     MGLevel& lc = h->lev[c];
     if (lc.d.npts <= 256) {
-      ProfScope ps(h, P_MG_COARSE, mg_level_bytes(h, c, 2.0 * ncomp + velf),
-                   (double)ncomp * lc.d.npts * smooth_flops_pp * h->cfg.mg_coarse_sweeps);
+      ProfScope ps(h, P_MG_COARSE, mg_level_bytes(h, c, 2.0 * ncomp + (kind == MG_DIFFUSION ? 0 : dim)),
+                   mg_sweep_flops(kind, dim, ncomp) * lc.d.npts * h->cfg.mg_coarse_sweeps);
       launch_mg_coarse(prec, dim, kind, lc.d, ncomp, sigma, cadv, cdiff, om,
                        h->cfg.mg_coarse_sweeps, project_mean, vrow[c], bl[c], lc.w, h->st);
       cur[c] = lc.w;
@@ -507,8 +573,40 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
       sweeps = std::max(2, std::min(sweeps, 12));
       cur[c] = lc.w;
       alt[c] = lc.w2;
-      jacobi_sweeps(h, c, kind, ncomp, sigma, cadv, cdiff, omc, vrow[c], bl[c], sweeps, true,
-                    cur[c], alt[c], nullptr);
+      const double rhoj = 1.0 - sigma / D;  // undamped Jacobi on [sigma/D, 2 - sigma/D]
+      int msteps = 0;
+      if (h->cfg.mg_coarse_chebyshev && omc == 1.0 && dim == 2 && lc.d.n >= 32 && lc.w3 &&
+          rhoj > 0 && rhoj < 1) {
+        // Chebyshev acceleration: the error after m steps is at most
+        // 1/T_m(1/rho); the smallest even m in 2..12 reaching the target
+        const double ach = std::acosh(1.0 / rhoj);
+        for (int m = 2; m <= 12; m += 2)
+          if (1.0 / std::cosh(m * ach) <= red) { msteps = m; break; }
+        if (msteps == 0) msteps = 12;
+      }
+      if (msteps > 0 && msteps < sweeps) {
+        // three-term weights: w_1 = 1, w_2 = 1/(1 - rho^2/2), w_{k+1} = 1/(1 - rho^2 w_k/4)
+        double wk[13];
+        wk[1] = 1.0;
+        wk[2] = 1.0 / (1.0 - 0.5 * rhoj * rhoj);
+        for (int q = 3; q <= msteps; ++q) wk[q] = 1.0 / (1.0 - 0.25 * rhoj * rhoj * wk[q - 1]);
+        void* bufA[2] = {lc.w, lc.w2};
+        void* bufB[2] = {lc.w3, lc.w4};
+        void** in = bufB;   // (x_{k-1}, x_k) of the previous pair
+        void** outp = bufA;
+        for (int q = 0; q < msteps; q += 2) {
+          const int first = (q == 0);
+          ProfScope ps(h, P_MG_SMOOTH2, mg_level_bytes(h, c, (first ? 3.0 : 5.0) * ncomp + velf),
+                       (first ? ncomp + fsweep : 2.0 * fsweep + 6.0 * ncomp) * lc.d.npts);
+          launch_mg_cheb2(prec, kk, lc.d, ncomp, sigma, cadv, cdiff, crow[c], bl[c], in[0], in[1],
+                          outp[0], outp[1], wk[q + 1], wk[q + 2], first, h->st);
+          std::swap(in, outp);
+        }
+        cur[c] = in[1];  // x_m
+      } else {
+        jacobi_sweeps(h, c, kk, ncomp, sigma, cadv, cdiff, omc, crow[c], bl[c], sweeps, true,
+                      cur[c], alt[c], nullptr);
+      }
     }
   }
   bool wrote_out = false;
@@ -517,11 +615,15 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     {
       ProfScope ps(h, P_MG_PROLONG, mg_level_bytes(h, l, 2.0 * ncomp + (double)ncomp / (1 << dim)),
                    (double)ncomp * lv.d.npts * 3);
-      launch_mg_prolong_add(prec, dim, lv.d, ncomp, cur[l + 1], cur[l], h->st);
+      if (fold_pre)
+        launch_mg_prolong_set(prec, dim, lv.d, ncomp, sigma, cadv, cdiff, om, bl[l], cur[l + 1],
+                              cur[l], h->st);
+      else
+        launch_mg_prolong_add(prec, dim, lv.d, ncomp, cur[l + 1], cur[l], h->st);
     }
     if (post > 0) {
       const bool to_out = alias && l == 0;
-      jacobi_sweeps(h, l, kind, ncomp, sigma, cadv, cdiff, om, vrow[l], bl[l], post,
+      jacobi_sweeps(h, l, kk, ncomp, sigma, cadv, cdiff, om, crow[l], bl[l], post,
                     false, cur[l], alt[l], to_out ? (void*)out : nullptr);
       if (to_out) wrote_out = true;
     }
@@ -571,7 +673,7 @@ void block_prec(irk_handle* h, double dt, int blk, const double* v, double* z) {
   row.sigma = -1;
   row.nterm = 1;
   row.t[0].x = z;
-  row.t[0].combo = keep_coupling(h, b, a) ? combo_ptr(h, b, a) : nullptr;
+  set_combo(h, row.t[0], b, a);
   row.t[0].m = h->tab.R[b * s + a];
   row.t[0].lin = 0;
   run_stage_op(h, op);
@@ -799,6 +901,10 @@ void launch_eval_residual(irk_handle* h, double t_n, double dt, const double* K,
     ProfScope ps(h, P_STAGE, 8.0 * w, h->L * 2.0 * h->s * (h->s + (combos ? h->ncombo : 0)));
     launch_stage_states(h->g, sa, h->st);
   }
+  if (combos && h->coef) {
+    ProfScope ps(h, P_STAGE, 8.0 * h->npts * 8.0 * h->ncombo, 10.0 * h->npts * h->ncombo);
+    launch_combo_coef(h->g, h->combos, h->ncombo, dt, h->coef, h->st);
+  }
   ResidualArgs ra;
   memset(&ra, 0, sizeof(ra));
   ra.s = h->s;
@@ -957,7 +1063,7 @@ cudaError_t capture_block_solve(irk_handle* h, double dt, int blk, cudaStream_t 
           const int q = a0 + qq;
           OpTerm& t = row.t[row.nterm++];
           t.x = h->prec_out + (long long)qq * h->L;
-          t.combo = keep_coupling(h, r, q) ? combo_ptr(h, r, q) : nullptr;
+          set_combo(h, t, r, q);
           t.m = h->tab.R[r * s + q];
           t.lin = (r == q) ? 1.0 : 0.0;
         }
@@ -1446,6 +1552,7 @@ irk_status validate(const irk_config* c, std::string& err) {
   if (c->mg_coarse_sweeps < 1 || c->mg_coarse_sweeps > 1000) { err = "mg_coarse_sweeps out of range"; return IRK_ERR_INVALID; }
   if (c->mg_shifted_sweeps < 0 || c->mg_shifted_sweeps > 8) { err = "mg_shifted_sweeps out of range"; return IRK_ERR_INVALID; }
   if (!(c->mg_coarse_reduction >= 0 && c->mg_coarse_reduction < 1)) { err = "mg_coarse_reduction must be in [0, 1)"; return IRK_ERR_INVALID; }
+  if (c->mg_coarse_chebyshev != 0 && c->mg_coarse_chebyshev != 1) { err = "mg_coarse_chebyshev must be 0 or 1"; return IRK_ERR_INVALID; }
   if (c->mg_levels < 0 || c->mg_levels > IRK_MAX_LEVELS) { err = "mg_levels out of range"; return IRK_ERR_INVALID; }
   return IRK_OK;
 }
@@ -1547,6 +1654,8 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   add(8 * h->L * s);             // rhs
   add(8 * h->L * s);             // yhat
   add(8 * h->L * std::max(h->ncombo, 1));  // combos
+  const bool use_coef = (c.op == IRK_OP_BURGERS_2D && h->ncombo > 0);
+  if (use_coef) add(8 * (size_t)h->npts * 6 * h->ncombo);  // coefficient fields
   add(8 * Lb);                   // zbuf
   add(8 * h->L);                 // tmp
   add(8 * h->L);                 // tmp2
@@ -1566,10 +1675,14 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   h->nparts = std::max(blas_blocks(Lb) * 70, residual_blocks(g)) + 1024;
   add(8 * (size_t)h->nparts);    // partials
   add(8 * 512);                  // device scalars
+  h->use_pre = (h->prec == IRK_MG_FP64 && h->dim == 2);
   for (int l = 0; l < h->nlev; ++l) {
     const size_t f = h->esz * (size_t)h->lev[l].d.npts;
     add(f * h->C); add(f * h->C); add(f * h->C); add(f * h->C);
+    if (l >= 1) { add(f * h->C); add(f * h->C); }
     for (int k = 0; k < s; ++k) add(f * h->dim);
+    if (h->use_pre)
+      for (int k = 0; k < s; ++k) add(f * 4);
   }
   h->arena_bytes = bytes + 4096;
   if (plan_only) return IRK_OK;
@@ -1598,6 +1711,7 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   h->rhs = (double*)take(8 * h->L * s);
   h->yhat = (double*)take(8 * h->L * s);
   h->combos = (double*)take(8 * h->L * std::max(h->ncombo, 1));
+  h->coef = use_coef ? (double*)take(8 * (size_t)h->npts * 6 * h->ncombo) : nullptr;
   h->zbuf = (double*)take(8 * Lb);
   h->tmp = (double*)take(8 * h->L);
   h->tmp2 = (double*)take(8 * h->L);
@@ -1624,7 +1738,10 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
     h->lev[l].w2 = take(f * h->C);
     h->lev[l].b = take(f * h->C);
     h->lev[l].r = take(f * h->C);
+    h->lev[l].w3 = (l >= 1) ? take(f * h->C) : nullptr;
+    h->lev[l].w4 = (l >= 1) ? take(f * h->C) : nullptr;
     for (int k = 0; k < s; ++k) h->vel[k][l] = take(f * h->dim);
+    for (int k = 0; k < s; ++k) h->coefh[k][l] = h->use_pre ? take(f * 4) : nullptr;
   }
   for (int k = s; k < IRK_MAXS; ++k)
     for (int l = 0; l < IRK_MAX_LEVELS; ++l) h->vel[k][l] = nullptr;
@@ -1716,6 +1833,7 @@ void irk_config_default(irk_config* c) {
   c->mg_coarse_sweeps = 40;
   c->mg_shifted_sweeps = 1;
   c->mg_coarse_reduction = 2e-2;
+  c->mg_coarse_chebyshev = 0;
   c->mg_omega = 0.0;
   c->profile = 0;
   c->use_graphs = 1;
