@@ -130,11 +130,12 @@ typedef struct {
   double mg_coarse_reduction; /* error reduction the Jacobi sweeps target on a
                            shift-dominated coarsest level (2..12 sweeps);
                            default 2e-2; 0 = default */
-  int mg_coarse_chebyshev; /* 1: on a shift-dominated 2D coarsest level,
-                           Chebyshev-accelerated undamped Jacobi (fewer sweeps
-                           for the same reduction of the symmetric part);
-                           0 (default): plain Jacobi, which measured faster
-                           on the advective workloads */
+  int mg_coarse_smoother; /* sweeps on a shift-dominated 2D coarsest level
+                           (n >= 32) toward mg_coarse_reduction:
+                           0 (default) undamped Jacobi, in fused pairs;
+                           1 Chebyshev-accelerated Jacobi;
+                           2 red-black Gauss-Seidel, one sweep per launch,
+                             half the sweeps of Jacobi */
 } irk_config;
 
 typedef struct {

@@ -47,7 +47,7 @@ class IrkConfig(C.Structure):
         ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double),
         ("profile", C.c_int), ("use_graphs", C.c_int), ("initial_guess", C.c_int),
         ("basis", C.c_int), ("mg_shifted_sweeps", C.c_int), ("mg_coarse_reduction", C.c_double),
-        ("mg_coarse_chebyshev", C.c_int),
+        ("mg_coarse_smoother", C.c_int),
     ]
 
 

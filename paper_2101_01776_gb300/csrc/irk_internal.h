@@ -196,6 +196,11 @@ bool mg_smooth2_pays(int prec, int dim, const MGLevelDesc& lv, int first);
 // with alpha = cadv/(2h), beta = -cdiff/h^2, from the level velocity vel (2 fields)
 void launch_mg_coef(int prec, const MGLevelDesc& lv, double cadv, double cdiff, const void* vel,
                     void* coef, cudaStream_t st);
+// One undamped red-black Gauss-Seidel sweep (2D, n >= 32): w_in -> w_out
+// (w_in unused when first: w = 0)
+void launch_mg_rbgs(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
+                    double cadv, double cdiff, const void* vel, const void* b, const void* w_in,
+                    void* w_out, int first, cudaStream_t st);
 // Two Chebyshev-accelerated undamped Jacobi sweeps (2D, n >= 32): from x_prev
 // (x_{k-1}) and x_cur (x_k) to x_mid (x_{k+1}) and x_out (x_{k+2}) with the
 // three-term weights wa, wb; `first` starts from x_0 = 0

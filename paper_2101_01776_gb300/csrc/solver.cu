@@ -575,8 +575,15 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
       alt[c] = lc.w2;
       const double rhoj = 1.0 - sigma / D;  // undamped Jacobi on [sigma/D, 2 - sigma/D]
       int msteps = 0;
-      if (h->cfg.mg_coarse_chebyshev && omc == 1.0 && dim == 2 && lc.d.n >= 32 && lc.w3 &&
-          rhoj > 0 && rhoj < 1) {
+      const bool smem_ok = (omc == 1.0 && dim == 2 && lc.d.n >= 32 && rhoj > 0 && rhoj < 1);
+      int gs_sweeps = 0;
+      if (h->cfg.mg_coarse_smoother == 2 && smem_ok) {
+        // red-black Gauss-Seidel: rho_GS = rho_J^2 for the consistently
+        // ordered 5-point stencil
+        gs_sweeps = (int)std::ceil(std::log(red) / (2.0 * std::log(rhoj)));
+        gs_sweeps = std::max(1, std::min(gs_sweeps, 6));
+      }
+      if (h->cfg.mg_coarse_smoother == 1 && smem_ok && lc.w3) {
         // Chebyshev acceleration: the error after m steps is at most
         // 1/T_m(1/rho); the smallest even m in 2..12 reaching the target
         const double ach = std::acosh(1.0 / rhoj);
@@ -584,7 +591,19 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
           if (1.0 / std::cosh(m * ach) <= red) { msteps = m; break; }
         if (msteps == 0) msteps = 12;
       }
-      if (msteps > 0 && msteps < sweeps) {
+      if (gs_sweeps > 0) {
+        void* src = lc.w;
+        void* dst = lc.w2;
+        for (int q = 0; q < gs_sweeps; ++q) {
+          const int first = (q == 0);
+          ProfScope ps(h, P_MG_SMOOTH2, mg_level_bytes(h, c, (first ? 2.0 : 3.0) * ncomp + velf),
+                       (first ? 0.5 * ncomp + 0.5 * fsweep : fsweep) * lc.d.npts);
+          launch_mg_rbgs(prec, kk, lc.d, ncomp, sigma, cadv, cdiff, crow[c], bl[c], src, dst, first,
+                         h->st);
+          std::swap(src, dst);
+        }
+        cur[c] = src;
+      } else if (msteps > 0 && msteps < sweeps) {
         // three-term weights: w_1 = 1, w_2 = 1/(1 - rho^2/2), w_{k+1} = 1/(1 - rho^2 w_k/4)
         double wk[13];
         wk[1] = 1.0;
@@ -1552,7 +1571,7 @@ irk_status validate(const irk_config* c, std::string& err) {
   if (c->mg_coarse_sweeps < 1 || c->mg_coarse_sweeps > 1000) { err = "mg_coarse_sweeps out of range"; return IRK_ERR_INVALID; }
   if (c->mg_shifted_sweeps < 0 || c->mg_shifted_sweeps > 8) { err = "mg_shifted_sweeps out of range"; return IRK_ERR_INVALID; }
   if (!(c->mg_coarse_reduction >= 0 && c->mg_coarse_reduction < 1)) { err = "mg_coarse_reduction must be in [0, 1)"; return IRK_ERR_INVALID; }
-  if (c->mg_coarse_chebyshev != 0 && c->mg_coarse_chebyshev != 1) { err = "mg_coarse_chebyshev must be 0 or 1"; return IRK_ERR_INVALID; }
+  if (c->mg_coarse_smoother < 0 || c->mg_coarse_smoother > 2) { err = "mg_coarse_smoother must be 0..2"; return IRK_ERR_INVALID; }
   if (c->mg_levels < 0 || c->mg_levels > IRK_MAX_LEVELS) { err = "mg_levels out of range"; return IRK_ERR_INVALID; }
   return IRK_OK;
 }
@@ -1833,7 +1852,7 @@ void irk_config_default(irk_config* c) {
   c->mg_coarse_sweeps = 40;
   c->mg_shifted_sweeps = 1;
   c->mg_coarse_reduction = 2e-2;
-  c->mg_coarse_chebyshev = 0;
+  c->mg_coarse_smoother = 0;
   c->mg_omega = 0.0;
   c->profile = 0;
   c->use_graphs = 1;

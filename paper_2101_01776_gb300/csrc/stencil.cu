@@ -235,8 +235,59 @@ __global__ void __launch_bounds__(256) k_residual(GridDesc g, ResidualArgs a) {
   if (threadIdx.x == 0 && a.partials) a.partials[blockIdx.x] = tot;
 }
 
+// Burgers-2D residual with one thread per point and component: half the
+// per-thread state of k_residual (F for S stages of one component), twice the
+// threads, and the constants folded so that N costs 10 operations per
+// component:  N_c = nu/h^2 (sum of 4 neighbours - 4 f) - (u Dx + v Dy) f.
+// Work item q in [0, 2 npts): component q / npts, point q % npts.
+template <int S>
+__global__ void __launch_bounds__(256) k_residual_b2d(GridDesc g, ResidualArgs a) {
+  __shared__ double sh[32];
+  const int npts = g.npts;
+  const long long L = 2LL * npts;
+  const double nuh = g.nu * g.invh2, mi2h = -g.inv2h;
+  double sq = 0.0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 2 * npts; q += gridDim.x * blockDim.x) {
+    const int c = (q >= npts) ? 1 : 0;
+    const int p = q - c * npts;
+    const Nbr nb = neighbours(g, p);
+    double F[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      const double* Yi = a.Y + i * L;
+      const double* f = Yi + (long long)c * npts;
+      const double uc = __ldg(Yi + nb.c), vc = __ldg(Yi + npts + nb.c);
+      const double fc = c ? vc : uc;
+      const double fe = __ldg(f + nb.e), fw = __ldg(f + nb.w), fn = __ldg(f + nb.n), fs = __ldg(f + nb.s);
+      double adv = uc * (fe - fw);
+      adv = fma(vc, fn - fs, adv);
+      double lap = (fe + fw) + (fn + fs);
+      lap = fma(-4.0, fc, lap);
+      const double nv = fma(nuh, lap, mi2h * adv);
+      F[i] = __ldg(a.K + i * L + q) - nv;
+      sq = fma(F[i], F[i], sq);
+    }
+    if (a.Fraw) {
+#pragma unroll
+      for (int i = 0; i < S; ++i) a.Fraw[i * L + q] = F[i];
+    }
+    if (a.rhs) {
+#pragma unroll
+      for (int k = 0; k < S; ++k) {
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 0; i < S; ++i) acc = fma(-a.Q[i * S + k], F[i], acc);
+        a.rhs[k * L + q] = acc;
+      }
+    }
+  }
+  const double tot = block_sum(sq, sh);
+  if (threadIdx.x == 0 && a.partials) a.partials[blockIdx.x] = tot;
+}
+
 int residual_blocks(const GridDesc& g) {
-  int blocks = (g.npts + 255) / 256;
+  const long long items = (g.op == IRK_OP_BURGERS_2D) ? 2LL * g.npts : g.npts;
+  int blocks = (int)((items + 255) / 256);
   if (blocks > 152 * 4) blocks = 152 * 4;
   return blocks;
 }
@@ -244,6 +295,16 @@ int residual_blocks(const GridDesc& g) {
 template <int OP>
 static void launch_residual_op(const GridDesc& g, const ResidualArgs& a, cudaStream_t st) {
   const int blocks = residual_blocks(g);
+  if (OP == IRK_OP_BURGERS_2D && !a.forcing) {
+    switch (a.s) {
+      case 1: k_residual_b2d<1><<<blocks, 256, 0, st>>>(g, a); break;
+      case 2: k_residual_b2d<2><<<blocks, 256, 0, st>>>(g, a); break;
+      case 3: k_residual_b2d<3><<<blocks, 256, 0, st>>>(g, a); break;
+      case 4: k_residual_b2d<4><<<blocks, 256, 0, st>>>(g, a); break;
+      case 5: k_residual_b2d<5><<<blocks, 256, 0, st>>>(g, a); break;
+    }
+    return;
+  }
   switch (a.s) {
     case 1: k_residual<OP, 1><<<blocks, 256, 0, st>>>(g, a); break;
     case 2: k_residual<OP, 2><<<blocks, 256, 0, st>>>(g, a); break;

@@ -177,7 +177,8 @@ def test_mixed_precision_preconditioner_same_result(B, prec):
 
 @pytest.mark.parametrize("kw", [dict(gamma_mode=1), dict(nonlinear_variant=2),
                                 dict(krylov_restart=3), dict(mg_levels=2),
-                                dict(mg_coarse_chebyshev=1), dict(mg_shifted_sweeps=0)])
+                                dict(mg_coarse_smoother=2), dict(mg_coarse_smoother=1),
+                                dict(mg_shifted_sweeps=0)])
 def test_solver_variants_reach_same_fixed_point(B, kw):
     per_step, whole, _ = run_parity(B, "burgers2d", 32, 3, 5e-3, 2e-3, 2, seed=4, **kw)
     assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (kw, per_step, whole)
