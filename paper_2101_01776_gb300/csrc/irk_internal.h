@@ -76,8 +76,8 @@ struct ResidualArgs {
 struct OpTerm {
   const double* x;       // ncomp * npts
   const double* combo;   // ncomp * npts or null (no advective part)
-  const double* coef;    // Burgers-2D: 6 * npts coefficient fields of `combo` at this dt
-                         // (launch_combo_coef), or null: formed from combo per point
+  const double* coef;    // coefficient fields of `combo` at this dt (launch_combo_coef:
+                         // 6 * npts Burgers-2D, 16 * npts VSF), or null: formed per point
   double m;              // mass coefficient
   double lin;            // coefficient of the state-independent linear part
 };
@@ -135,8 +135,18 @@ void launch_stage_op(const GridDesc& g, const StageOpArgs& a, cudaStream_t st);
 // Burgers-2D coefficient fields of each combined field (ub, vb), formed once
 // per Newton iteration: dt ub/(2h), dt vb/(2h), dt Dx ub, dt Dy ub, dt Dx vb,
 // dt Dy vb (central differences); coef is ncombo * 6 * npts
-void launch_combo_coef(const GridDesc& g, const double* combos, int ncombo, double dt,
+// Combined fields that get coefficient fields: slot i of coef belongs to
+// combined field idx[i] (the fields of the diagonal blocks, read every Krylov
+// iteration; the upper-coupling fields are read once per Newton iteration)
+struct ComboList {
+  int n;
+  int idx[IRK_MAX_COMBOS];
+};
+void launch_combo_coef(const GridDesc& g, const double* combos, const ComboList& list, double dt,
                        double* coef, cudaStream_t st);
+// coefficient fields per combined field for `op` (6 Burgers-2D, 16 VSF: the
+// dt/(12h^2)-scaled Arakawa weights of psibar and wbar), 0 = none
+int combo_coef_fields(int op);
 void launch_stage_update(long long L, int s, const double* QR, const double* yhat, double* K,
                          cudaStream_t st);
 void launch_u_update(long long L, int s, const double* b, double dt, const double* K, double* u,
@@ -196,6 +206,11 @@ bool mg_smooth2_pays(int prec, int dim, const MGLevelDesc& lv, int first);
 // with alpha = cadv/(2h), beta = -cdiff/h^2, from the level velocity vel (2 fields)
 void launch_mg_coef(int prec, const MGLevelDesc& lv, double cadv, double cdiff, const void* vel,
                     void* coef, cudaStream_t st);
+// The bottom of a periodic 2D Poisson V-cycle (levels lv.n = 32 or 16 down to
+// 8) in one CTA; pinv is the 64 x 64 zero-mean pseudo-inverse of the 8^2
+// operator -L_h for cdiff = 1 (device memory, row-major)
+void launch_mg_bottom(int prec, const MGLevelDesc& lv, double cdiff, double omega, int pre,
+                      int post, const double* pinv, const void* b, void* w, cudaStream_t st);
 // One undamped red-black Gauss-Seidel sweep (2D, n >= 32): w_in -> w_out
 // (w_in unused when first: w = 0)
 void launch_mg_rbgs(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,

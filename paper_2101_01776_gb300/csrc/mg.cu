@@ -17,6 +17,8 @@
 // arithmetic (BF16-stored data, FP32 accumulation).
 #include <cuda_bf16.h>
 
+#include <cstring>
+
 #include "irk_internal.h"
 
 namespace irk {
@@ -421,6 +423,133 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_rbgs(MGLevelDesc lv, int ncomp
   }
 }
 
+// The bottom of a periodic 2D Poisson V-cycle in one CTA: levels n0 = 32 (or
+// 16) down to 8 held in shared memory.  Per level above 8: `pre` damped-Jacobi
+// sweeps from zero, residual, full weighting; on 8^2 the exact zero-mean
+// solve w = A^+ b with the 64 x 64 pseudo-inverse (pinv, row-major, for
+// cdiff = 1); back up: bilinear prolongation and `post` sweeps.  The same
+// stencils as the multi-launch kernels (A = -cdiff L_h), one point per
+// thread on 32^2.  Replaces about a dozen latency-bound launches and the
+// 40-sweep coarsest solve of the deep Poisson cycles.
+constexpr int kBotThreads = 1024;
+
+// Level constants of the bottom cycle, formed on the host (a division per
+// thread and sweep would cost more FP64 issue than the sweep itself).
+struct BottomConst {
+  int nl;                // levels n0, n0/2, ..., 8
+  int n[4], logn[4], off[4];
+  double c[4];           // cdiff / h_l^2
+  double dinv[4];        // omega / (4 c_l)
+  double keep;           // 1 - omega
+  double inv_cdiff;
+};
+
+template <typename TS>
+__global__ void __launch_bounds__(kBotThreads) k_mg_bottom(BottomConst K, int pre, int post,
+                                                          const double* __restrict__ pinv,
+                                                          const TS* __restrict__ b_in,
+                                                          TS* __restrict__ w_out) {
+  typedef typename Cmp<TS>::T TC;
+  extern __shared__ unsigned char smem_raw[];
+  TC* base = reinterpret_cast<TC*>(smem_raw);
+  const int tid = threadIdx.x, nl = K.nl;
+  auto W = [&](int l) { return base + K.off[l]; };
+  auto T = [&](int l) { return base + K.off[l] + K.n[l] * K.n[l]; };
+  auto Bv = [&](int l) { return base + K.off[l] + 2 * K.n[l] * K.n[l]; };
+  const int n0 = K.n[0];
+  for (int k = tid; k < n0 * n0; k += blockDim.x) Bv(0)[k] = ldv(b_in + k);
+  __syncthreads();
+  const TC keep = TC(K.keep);
+  // one damped-Jacobi sweep on level l: src -> dst (src == nullptr: from zero)
+  auto sweep = [&](int l, const TC* src, TC* dst) {
+    const int n = K.n[l], ln = K.logn[l], m = n - 1, np = n * n;
+    const TC c = TC(K.c[l]), dinv = TC(K.dinv[l]);
+    const TC* b = Bv(l);
+    for (int k = tid; k < np; k += blockDim.x) {
+      if (!src) { dst[k] = dinv * b[k]; continue; }
+      const int i = k & m, j = k >> ln;
+      const TC sn = src[(j << ln) + ((i + 1) & m)] + src[(j << ln) + ((i - 1) & m)] +
+                    src[(((j + 1) & m) << ln) + i] + src[(((j - 1) & m) << ln) + i];
+      dst[k] = fma(dinv, fma(c, sn, b[k]), keep * src[k]);
+    }
+    __syncthreads();
+  };
+  // `cnt` sweeps on level l ending in W(l); from zero when fromzero
+  auto smooth = [&](int l, int cnt, bool fromzero) {
+    TC* a = W(l);
+    TC* t = T(l);
+    const int np = K.n[l] * K.n[l];
+    if (fromzero && cnt == 0) {
+      for (int k = tid; k < np; k += blockDim.x) a[k] = TC(0);
+      __syncthreads();
+    }
+    for (int sw = 0; sw < cnt; ++sw) {
+      if (fromzero && sw == 0) { sweep(l, nullptr, a); continue; }
+      sweep(l, a, t);
+      for (int k = tid; k < np; k += blockDim.x) a[k] = t[k];
+      __syncthreads();
+    }
+  };
+  for (int l = 0; l + 1 < nl; ++l) {
+    smooth(l, pre, true);
+    // residual r = b - A w into T(l), then full weighting into B(l+1)
+    const int n = K.n[l], ln = K.logn[l], m = n - 1, np = n * n;
+    const TC c = TC(K.c[l]);
+    const TC* w = W(l);
+    const TC* b = Bv(l);
+    TC* r = T(l);
+    for (int k = tid; k < np; k += blockDim.x) {
+      const int i = k & m, j = k >> ln;
+      const TC sn = w[(j << ln) + ((i + 1) & m)] + w[(j << ln) + ((i - 1) & m)] +
+                    w[(((j + 1) & m) << ln) + i] + w[(((j - 1) & m) << ln) + i];
+      r[k] = fma(c, fma(TC(-4), w[k], sn), b[k]);
+    }
+    __syncthreads();
+    const int nc = n >> 1, lc = ln - 1;
+    TC* bc = Bv(l + 1);
+    for (int k = tid; k < nc * nc; k += blockDim.x) {
+      const int I = k & (nc - 1), J = k >> lc, i = 2 * I, j = 2 * J;
+      const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
+      const TC centre = r[(j << ln) + i];
+      const TC edges = r[(j << ln) + ip] + r[(j << ln) + im] + r[(jp << ln) + i] + r[(jm << ln) + i];
+      const TC corners = r[(jp << ln) + ip] + r[(jp << ln) + im] + r[(jm << ln) + ip] + r[(jm << ln) + im];
+      bc[k] = (TC(4) * centre + TC(2) * edges + corners) * TC(0.0625);
+    }
+    __syncthreads();
+  }
+  {
+    // exact zero-mean solve on 8^2: w = A^+ b (A^+ for cdiff = 1, scaled)
+    const int l = nl - 1;
+    const TC* b = Bv(l);
+    TC* w = W(l);
+    if (tid < 64) {
+      TC acc = 0;
+      for (int q = 0; q < 64; ++q) acc = fma(TC(__ldg(pinv + tid * 64 + q)), b[q], acc);
+      w[tid] = acc * TC(K.inv_cdiff);
+    }
+    __syncthreads();
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    const int n = K.n[l], nc = n >> 1, mc = nc - 1, lc = K.logn[l] - 1;
+    const TC* g = W(l + 1);
+    TC* f = W(l);
+    for (int k = tid; k < nc * nc; k += blockDim.x) {
+      const int I = k & mc, J = k >> lc;
+      const int I1 = (I + 1) & mc, J1 = (J + 1) & mc;
+      const TC c00 = g[(J << lc) + I], c10 = g[(J << lc) + I1];
+      const TC c01 = g[(J1 << lc) + I], c11 = g[(J1 << lc) + I1];
+      const int o0 = (2 * J) * n + 2 * I, o1 = o0 + n;
+      f[o0] += c00;
+      f[o0 + 1] += TC(0.5) * (c00 + c10);
+      f[o1] += TC(0.5) * (c00 + c01);
+      f[o1 + 1] += TC(0.25) * ((c00 + c10) + (c01 + c11));
+    }
+    __syncthreads();
+    smooth(l, post, false);
+  }
+  for (int k = tid; k < n0 * n0; k += blockDim.x) stv<TS, TC>(w_out + k, W(0)[k]);
+}
+
 // Full weighting: fine -> coarse (coarse n = fine n / 2), all components.
 template <typename TS, int DIM>
 __global__ void __launch_bounds__(256) k_mg_restrict(MGLevelDesc fine, int ncomp,
@@ -758,6 +887,30 @@ void launch_mg_residual0(int prec, int dim, int kind, const MGLevelDesc& lv, int
   const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, omega);
   IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_residual0<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
       lv, ncomp, k, (const TS*)vel, (const TS*)b, (TS*)r))));
+}
+
+void launch_mg_bottom(int prec, const MGLevelDesc& lv, double cdiff, double omega, int pre,
+                      int post, const double* pinv, const void* b, void* w, cudaStream_t st) {
+  BottomConst K;
+  memset(&K, 0, sizeof(K));
+  size_t words = 0;
+  for (int n = lv.n, l = 0; n >= 8 && l < 4; n >>= 1, ++l) {
+    K.n[l] = n;
+    K.logn[l] = lv.logn - l;
+    K.off[l] = (int)words;
+    const double hl = lv.h * (double)(lv.n / n);
+    K.c[l] = cdiff / (hl * hl);
+    K.dinv[l] = omega / (4.0 * K.c[l]);
+    words += 3 * (size_t)n * n;
+    K.nl = l + 1;
+  }
+  K.keep = 1.0 - omega;
+  K.inv_cdiff = 1.0 / cdiff;
+  IRK_DISPATCH_PREC(prec, {
+    typedef typename Cmp<TS>::T TC;
+    k_mg_bottom<TS><<<1, kBotThreads, sizeof(TC) * words, st>>>(K, pre, post, pinv,
+        (const TS*)b, (TS*)w);
+  });
 }
 
 void launch_mg_coarse(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,

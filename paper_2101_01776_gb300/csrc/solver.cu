@@ -72,7 +72,9 @@ struct irk_handle {
 
   double *u = nullptr, *u_save = nullptr, *K = nullptr, *Y = nullptr, *rhs = nullptr,
          *yhat = nullptr, *combos = nullptr, *zbuf = nullptr, *tmp = nullptr, *tmp2 = nullptr;
-  double* coef = nullptr;  // Burgers-2D: 6 coefficient fields per combined field
+  double* coef = nullptr;  // coefficient fields of the combined fields in coef_list
+  ComboList coef_list = {};
+  int coef_slot[IRK_MAX_COMBOS];  // slot in coef of a combined field, or -1
   int ncombo = 0;
   int combo_of[IRK_MAXS][IRK_MAXS];
   double Dq[IRK_MAX_COMBOS * IRK_MAXS];
@@ -122,6 +124,7 @@ struct irk_handle {
   // FP64 2D advective rows: the four off-diagonal coefficients per level,
   // formed once per Newton iteration from vel (valid for coef_cadv/cdiff)
   bool use_pre = false;
+  double* pinv = nullptr;  // 64 x 64 zero-mean pseudo-inverse of -L_h on 8^2 (2D, cdiff = 1)
   void* coefh[IRK_MAXS][IRK_MAX_LEVELS] = {};
   double coef_cadv = 0.0, coef_cdiff = 0.0;
   double mg_omega = 0.8;
@@ -276,7 +279,10 @@ bool keep_coupling(irk_handle* h, int r, int q);
 // the coefficient fields formed from it once per Newton iteration.
 void set_combo(irk_handle* h, OpTerm& t, int r, int q) {
   t.combo = keep_coupling(h, r, q) ? combo_ptr(h, r, q) : nullptr;
-  t.coef = (t.combo && h->coef) ? h->coef + (long long)h->combo_of[r][q] * 6 * h->npts : nullptr;
+  const int slot = t.combo ? h->coef_slot[h->combo_of[r][q]] : -1;
+  t.coef = (slot >= 0 && h->coef)
+               ? h->coef + (long long)slot * combo_coef_fields(h->g.op) * h->npts
+               : nullptr;
 }
 
 double stage_op_bytes(irk_handle* h, const StageOpArgs& a) {
@@ -284,7 +290,8 @@ double stage_op_bytes(irk_handle* h, const StageOpArgs& a) {
   for (int r = 0; r < a.nrow; ++r) {
     words += h->L * (1 + (a.row[r].base ? 1 : 0));
     for (int t = 0; t < a.row[r].nterm; ++t)
-      words += h->L * (1 + (a.row[r].t[t].coef ? 3 : a.row[r].t[t].combo ? 1 : 0));
+      words += h->L * (1 + (a.row[r].t[t].coef ? combo_coef_fields(h->g.op) / 2.0
+                            : a.row[r].t[t].combo ? 1 : 0));
   }
   words += a.copy_len * 2.0;
   return words * 8.0;
@@ -295,8 +302,9 @@ double stage_op_flops(irk_handle* h, const StageOpArgs& a) {
   for (int r = 0; r < a.nrow; ++r)
     for (int t = 0; t < a.row[r].nterm; ++t) {
       const OpTerm& tm = a.row[r].t[t];
-      if (tm.coef)  // Burgers-2D coefficient form: 4 coefficients + 2 x (5 FMA, 1 add, 1 mul) + 2 adds
-        f += h->npts * 30.0;
+      if (tm.coef)  // coefficient form: Burgers-2D 4 coefficients + 2 x (5 FMA, 1 add, 1 mul) + 2 adds;
+                    // VSF 16 FMAs (+ the two Laplacians of the linear part)
+        f += h->npts * (h->g.op == IRK_OP_VSF_2D ? 34.0 + (tm.lin != 0 ? 24.0 : 0.0) : 30.0);
       else
         f += h->npts * (2.0 * h->C + (tm.combo ? jadv_flops_per_point(h->g.op) : 0) +
                         (tm.lin != 0 ? jlin_flops_per_point(h->g.op) : 0));
@@ -528,7 +536,15 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
   // a single pre-sweep starts from zero (w = dinv b): it is folded into the
   // residual and rebuilt by the prolongation, one launch less per level
   const bool fold_pre = (npre == 1);
-  for (int l = 0; l + 1 < nl; ++l) {
+  // deep periodic Poisson cycles: the levels from 32^2 down run in one CTA
+  // with an exact zero-mean solve on 8^2
+  int lb = nl;
+  if (dim == 2 && kind == MG_DIFFUSION && sigma == 0.0 && ncomp == 1 && project_mean && h->pinv &&
+      h->lev[nl - 1].d.n == 8) {
+    lb = nl - 1;
+    while (lb > 0 && h->lev[lb - 1].d.n <= 32) --lb;
+  }
+  for (int l = 0; l + 1 < nl && l < lb; ++l) {
     MGLevel& lv = h->lev[l];
     cur[l] = lv.w;
     alt[l] = lv.w2;
@@ -551,7 +567,15 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
       launch_mg_restrict(prec, dim, lv.d, ncomp, lv.r, h->lev[l + 1].b, h->st);
     }
   }
-  {
+  if (lb < nl) {
+    MGLevel& lv = h->lev[lb];
+    double words = 0;
+    for (int l = lb; l < nl; ++l) words += 2.0 * h->lev[l].d.npts;
+    ProfScope ps(h, P_MG_COARSE, words * h->esz,
+                 (npre + post + 1) * 7.0 * lv.d.npts * 4.0 / 3.0 + 2.0 * 64 * 64);
+    launch_mg_bottom(prec, lv.d, cdiff, om, npre, post, h->pinv, bl[lb], lv.w, h->st);
+    cur[lb] = lv.w;
+  } else {
     const int c = nl - 1;
     MGLevel& lc = h->lev[c];
     if (lc.d.npts <= 256) {
@@ -629,7 +653,7 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     }
   }
   bool wrote_out = false;
-  for (int l = nl - 2; l >= 0; --l) {
+  for (int l = std::min(nl, lb) - 2 + (lb < nl ? 1 : 0); l >= 0; --l) {
     MGLevel& lv = h->lev[l];
     {
       ProfScope ps(h, P_MG_PROLONG, mg_level_bytes(h, l, 2.0 * ncomp + (double)ncomp / (1 << dim)),
@@ -921,8 +945,10 @@ void launch_eval_residual(irk_handle* h, double t_n, double dt, const double* K,
     launch_stage_states(h->g, sa, h->st);
   }
   if (combos && h->coef) {
-    ProfScope ps(h, P_STAGE, 8.0 * h->npts * 8.0 * h->ncombo, 10.0 * h->npts * h->ncombo);
-    launch_combo_coef(h->g, h->combos, h->ncombo, dt, h->coef, h->st);
+    const int ncf = combo_coef_fields(h->g.op);
+    ProfScope ps(h, P_STAGE, 8.0 * h->npts * (2.0 + ncf) * h->coef_list.n,
+                 (ncf == 16 ? 52.0 : 10.0) * h->npts * h->coef_list.n);
+    launch_combo_coef(h->g, h->combos, h->coef_list, dt, h->coef, h->st);
   }
   ResidualArgs ra;
   memset(&ra, 0, sizeof(ra));
@@ -1673,8 +1699,21 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   add(8 * h->L * s);             // rhs
   add(8 * h->L * s);             // yhat
   add(8 * h->L * std::max(h->ncombo, 1));  // combos
-  const bool use_coef = (c.op == IRK_OP_BURGERS_2D && h->ncombo > 0);
-  if (use_coef) add(8 * (size_t)h->npts * 6 * h->ncombo);  // coefficient fields
+  const int ncf = combo_coef_fields(c.op);
+  // coefficient fields for the combined fields of the diagonal blocks
+  h->coef_list.n = 0;
+  for (int q = 0; q < IRK_MAX_COMBOS; ++q) h->coef_slot[q] = -1;
+  if (ncf > 0)
+    for (int k = 0; k < s; ++k)
+      for (int l = 0; l < s; ++l) {
+        const int q = h->combo_of[k][l];
+        if (q >= 0 && h->blk_of[k] == h->blk_of[l] && h->coef_slot[q] < 0) {
+          h->coef_slot[q] = h->coef_list.n;
+          h->coef_list.idx[h->coef_list.n++] = q;
+        }
+      }
+  const bool use_coef = (h->coef_list.n > 0);
+  if (use_coef) add(8 * (size_t)h->npts * ncf * h->coef_list.n);  // coefficient fields
   add(8 * Lb);                   // zbuf
   add(8 * h->L);                 // tmp
   add(8 * h->L);                 // tmp2
@@ -1684,6 +1723,7 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   add(8 * Lb);                   // prec_in
   add(8 * Lb);                   // prec_out
   add(sizeof(FGState) * h->tab.nblk);  // device FGMRES states
+  if (h->dim == 2) add(8 * 64 * 64);  // bottom solve of the Poisson cycles
   const long long Lo = (long long)s * h->L;
   h->mo = (c.nonlinear_variant == 4) ? h->m : 0;
   if (h->mo) {
@@ -1730,7 +1770,7 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   h->rhs = (double*)take(8 * h->L * s);
   h->yhat = (double*)take(8 * h->L * s);
   h->combos = (double*)take(8 * h->L * std::max(h->ncombo, 1));
-  h->coef = use_coef ? (double*)take(8 * (size_t)h->npts * 6 * h->ncombo) : nullptr;
+  h->coef = use_coef ? (double*)take(8 * (size_t)h->npts * ncf * h->coef_list.n) : nullptr;
   h->zbuf = (double*)take(8 * Lb);
   h->tmp = (double*)take(8 * h->L);
   h->tmp2 = (double*)take(8 * h->L);
@@ -1740,6 +1780,7 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   h->prec_in = (double*)take(8 * Lb);
   h->prec_out = (double*)take(8 * Lb);
   h->fgs = (FGState*)take(sizeof(FGState) * h->tab.nblk);
+  h->pinv = (h->dim == 2) ? (double*)take(8 * 64 * 64) : nullptr;
   if (h->mo) {
     h->Vo = (double*)take(8 * Lo * (h->mo + 1));
     h->Zo = (double*)take(8 * Lo * h->mo);
@@ -1767,6 +1808,25 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   if (!h->dscal) { h->err = "arena layout overflow"; return IRK_ERR_NOMEM; }
   CK(cudaMemsetAsync(h->arena, 0, h->arena_used, h->st));
   CK(cudaMallocHost((void**)&h->hbuf, 4096));
+  if (h->pinv) {
+    // A^+ = sum over the nonzero Fourier modes k of v_k v_k^T / lambda_k, with
+    // lambda_k = (4 - 2 cos(2 pi kx/8) - 2 cos(2 pi ky/8)) / h^2 on the 8^2 level
+    std::vector<double> pv(64 * 64);
+    const long double h8 = (long double)c.length / 8, pi = 3.14159265358979323846264338327950288L;
+    for (int pp = 0; pp < 64; ++pp)
+      for (int qq = 0; qq < 64; ++qq) {
+        const int dx = (pp % 8) - (qq % 8), dy = (pp / 8) - (qq / 8);
+        long double acc = 0;
+        for (int ky = 0; ky < 8; ++ky)
+          for (int kx = 0; kx < 8; ++kx) {
+            if (kx == 0 && ky == 0) continue;
+            const long double lam = (4 - 2 * std::cos(2 * pi * kx / 8) - 2 * std::cos(2 * pi * ky / 8)) / (h8 * h8);
+            acc += std::cos(2 * pi * (kx * dx + ky * dy) / 8) / lam;
+          }
+        pv[pp * 64 + qq] = (double)(acc / 64);
+      }
+    CK(cudaMemcpy(h->pinv, pv.data(), sizeof(double) * 64 * 64, cudaMemcpyHostToDevice));
+  }
   if (c.profile) {
     h->evpool.resize(8192);
     for (auto& ev : h->evpool) CK(cudaEventCreate(&ev));

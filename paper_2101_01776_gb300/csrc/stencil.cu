@@ -427,6 +427,38 @@ __device__ __forceinline__ void term_apply(const GridDesc& g, const OpTerm& t, c
     }
     acc[0] += t.m * uc - dt * opu;
     acc[1] += t.m * vc - dt * opv;
+  } else if (t.coef) {  // VSF with the combined field's Arakawa weights precomputed
+    double xw9[3][3], xp9[3][3];
+    load9(t.x, nb, xw9);
+    load9(t.x + npts, nb, xp9);
+    const double* f = t.coef + nb.c;
+    const long long st = npts;
+    // -dt (J_A(psibar, xw) + J_A(xp, wbar)) in 16 FMAs, order E, W, N, S, NE, NW, SE, SW
+    double op = __ldg(f) * xw9[1][2];
+    op = fma(__ldg(f + st), xw9[1][0], op);
+    op = fma(__ldg(f + 2 * st), xw9[2][1], op);
+    op = fma(__ldg(f + 3 * st), xw9[0][1], op);
+    op = fma(__ldg(f + 4 * st), xw9[2][2], op);
+    op = fma(__ldg(f + 5 * st), xw9[2][0], op);
+    op = fma(__ldg(f + 6 * st), xw9[0][2], op);
+    op = fma(__ldg(f + 7 * st), xw9[0][0], op);
+    op = fma(__ldg(f + 8 * st), xp9[1][2], op);
+    op = fma(__ldg(f + 9 * st), xp9[1][0], op);
+    op = fma(__ldg(f + 10 * st), xp9[2][1], op);
+    op = fma(__ldg(f + 11 * st), xp9[0][1], op);
+    op = fma(__ldg(f + 12 * st), xp9[2][2], op);
+    op = fma(__ldg(f + 13 * st), xp9[2][0], op);
+    op = fma(__ldg(f + 14 * st), xp9[0][2], op);
+    op = fma(__ldg(f + 15 * st), xp9[0][0], op);
+    double opp = 0.0;
+    if (t.lin != 0.0) {
+      const double lw = (xw9[1][2] + xw9[1][0] + xw9[2][1] + xw9[0][1] - 4.0 * xw9[1][1]) * g.invh2;
+      const double lp = (xp9[1][2] + xp9[1][0] + xp9[2][1] + xp9[0][1] - 4.0 * xp9[1][1]) * g.invh2;
+      op = fma(-dt * t.lin * g.nu, lw, op);
+      opp = t.lin * (-xw9[1][1] - lp);
+    }
+    acc[0] += t.m * xw9[1][1] + op;
+    acc[1] += -dt * opp;
   } else {  // VSF: state (w, psi), M = diag(1, 0)
     double xw9[3][3], xp9[3][3];
     load9(t.x, nb, xw9);
@@ -475,14 +507,15 @@ __global__ void __launch_bounds__(256) k_stage_op(GridDesc g, StageOpArgs a) {
 }
 
 __global__ void __launch_bounds__(256) k_combo_coef(GridDesc g, const double* __restrict__ combos,
-                                                    int ncombo, double dt, double* __restrict__ coef) {
+                                                    ComboList list, double dt, double* __restrict__ coef) {
+  const int ncombo = list.n;
   const int npts = g.npts;
   const double dth = dt * g.inv2h;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += gridDim.x * blockDim.x) {
     const Nbr nb = neighbours(g, p);
 #pragma unroll 1
     for (int q = 0; q < ncombo; ++q) {
-      const double* bu = combos + (long long)q * 2 * npts;
+      const double* bu = combos + (long long)list.idx[q] * 2 * npts;
       const double* bv = bu + npts;
       double* f = coef + (long long)q * 6 * npts + p;
       f[0] = dth * __ldg(bu + nb.c);
@@ -495,11 +528,64 @@ __global__ void __launch_bounds__(256) k_combo_coef(GridDesc g, const double* __
   }
 }
 
-void launch_combo_coef(const GridDesc& g, const double* combos, int ncombo, double dt,
+// The Arakawa Jacobian J_A(a, b) is linear in b with an 8-point stencil whose
+// weights depend on a (no centre weight), and antisymmetric: J_A(x, b) =
+// -J_A(b, x).  Weights of b (times 12 h^2), in the order E, W, N, S, NE, NW,
+// SE, SW, from the three central forms of Arakawa's average.
+__device__ __forceinline__ void arakawa_weights(const double a[3][3], double wgt[8]) {
+  const double aE = a[1][2], aW = a[1][0], aN = a[2][1], aS = a[0][1];
+  const double aNE = a[2][2], aNW = a[2][0], aSE = a[0][2], aSW = a[0][0];
+  wgt[0] = -(aN - aS) - (aNE - aSE);  // E
+  wgt[1] = (aN - aS) + (aNW - aSW);   // W
+  wgt[2] = (aE - aW) + (aNE - aNW);   // N
+  wgt[3] = -(aE - aW) - (aSE - aSW);  // S
+  wgt[4] = aE - aN;                   // NE
+  wgt[5] = aN - aW;                   // NW
+  wgt[6] = aS - aE;                   // SE
+  wgt[7] = aW - aS;                   // SW
+}
+
+// VSF: 16 fields per combined field (wbar, psibar): P_k = -dt/(12h^2) times the
+// weights of J_A(psibar, .) (applied to x_omega) and Q_k = +dt/(12h^2) times
+// the weights of J_A(wbar, .) (applied to x_psi, by antisymmetry), so that
+// sum_k P_k xw_k + Q_k xp_k = -dt (J_A(psibar, xw) + J_A(xp, wbar)).
+// One work item per (combined field, half, point): half 0 forms P from psibar,
+// half 1 forms Q from wbar (write-bound: 64 bytes per item).
+__global__ void __launch_bounds__(256) k_combo_coef_vsf(GridDesc g, const double* __restrict__ combos,
+                                                        ComboList list, double dt, double* __restrict__ coef) {
+  const int npts = g.npts, ncombo = list.n;
+  const double sc = dt * g.inv12h2;
+  const long long items = 2LL * ncombo * npts;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(it % npts);
+    const long long qh = it / npts;  // 2 q + half
+    const int q = (int)(qh >> 1), half = (int)(qh & 1);
+    const Nbr nb = neighbours(g, p);
+    const double* src = combos + (long long)list.idx[q] * 2 * npts + (half ? 0 : npts);  // psibar | wbar
+    double a9[3][3], wgt[8];
+    load9(src, nb, a9);
+    arakawa_weights(a9, wgt);
+    const double scl = half ? sc : -sc;
+    double* f = coef + (long long)q * 16 * npts + (long long)half * 8 * npts + p;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[(long long)k * npts] = scl * wgt[k];
+  }
+}
+
+int combo_coef_fields(int op) {
+  return op == IRK_OP_BURGERS_2D ? 6 : (op == IRK_OP_VSF_2D ? 16 : 0);
+}
+
+void launch_combo_coef(const GridDesc& g, const double* combos, const ComboList& list, double dt,
                        double* coef, cudaStream_t st) {
+  if (list.n <= 0) return;
   int blocks = (g.npts + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_combo_coef<<<blocks, 256, 0, st>>>(g, combos, ncombo, dt, coef);
+  if (g.op == IRK_OP_VSF_2D)
+    k_combo_coef_vsf<<<152 * 8, 256, 0, st>>>(g, combos, list, dt, coef);
+  else
+    k_combo_coef<<<blocks, 256, 0, st>>>(g, combos, list, dt, coef);
 }
 
 void launch_stage_op(const GridDesc& g, const StageOpArgs& a, cudaStream_t st) {
