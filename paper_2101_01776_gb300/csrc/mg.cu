@@ -152,12 +152,17 @@ MGConst mg_const(const MGLevelDesc& lv, int dim, double sigma, double cadv, doub
   return c;
 }
 
+// epi_out (FP64 storage only): also write epi_out = epi_base + epi_coef w_out
+// pointwise (the mass-only coupling row of L_P, fused into the last sweep)
 template <typename TS, int DIM, int KIND>
 __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, MGConst k,
                                                    const TS* __restrict__ vel,
                                                    const TS* __restrict__ b,
                                                    const TS* __restrict__ w_in,
-                                                   TS* __restrict__ w_out, int first) {
+                                                   TS* __restrict__ w_out, int first,
+                                                   double* __restrict__ epi_out,
+                                                   const double* __restrict__ epi_base,
+                                                   double epi_coef) {
   typedef typename Cmp<TS>::T TC;
   const TC alpha = TC(k.alpha), beta = TC(k.beta);
   const TC dinv = TC(k.dinv), keep = TC(k.keep);
@@ -175,7 +180,9 @@ __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, MG
       const long long off = (long long)c * lv.npts;
       const TC t = rhs_minus_offdiag<TS, DIM>(q, w_in + off, cf, ldv(b + off + p));
       // w + omega/D (b - D w - sum c w) = (1 - omega) w + omega/D (b - sum c w)
-      stv<TS, TC>(w_out + off + p, fma(dinv, t, keep * ldv(w_in + off + p)));
+      const TC v = fma(dinv, t, keep * ldv(w_in + off + p));
+      stv<TS, TC>(w_out + off + p, v);
+      if (epi_out) epi_out[off + p] = fma(epi_coef, (double)v, epi_base[off + p]);
     }
   }
 }
@@ -749,10 +756,13 @@ size_t mg_elem_size(int prec) {
 
 void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
                       double cadv, double cdiff, double omega, const void* vel, const void* b,
-                      const void* w_in, void* w_out, int first, cudaStream_t st) {
+                      const void* w_in, void* w_out, int first, cudaStream_t st, double* epi_out,
+                      const double* epi_base, double epi_coef) {
   const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, omega);
+  if (prec != IRK_MG_FP64) epi_out = nullptr;  // the epilogue is defined on FP64 storage
   IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_smooth<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
-      lv, ncomp, k, (const TS*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first))));
+      lv, ncomp, k, (const TS*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, epi_out,
+      epi_base, epi_coef))));
 }
 
 // Whether one k_mg_smooth2 launch should replace two k_mg_smooth launches.

@@ -456,9 +456,19 @@ double mg_resid_flops(int kind, int dim, int ncomp) {
 // when given (the caller's output buffer).  Pairs of sweeps go to the
 // temporally blocked two-sweep kernel where it pays; it reads b on a halo, so
 // it never writes into b.
-void jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, double cadv,
+// A pointwise epilogue for the last sweep of a V-cycle in FP64 storage:
+// out = base + coef * w (the mass-only coupling row of L_P).
+struct MGEpilogue {
+  double* out;
+  const double* base;
+  double coef;
+};
+
+bool jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, double cadv,
                    double cdiff, double om, const void* vel, const void* b, int sweeps,
-                   bool from_zero, void*& cur, void*& alt, void* last) {
+                   bool from_zero, void*& cur, void*& alt, void* last,
+                   const MGEpilogue* epi = nullptr) {
+  bool epi_done = false;
   const MGLevelDesc& d = h->lev[l].d;
   const int prec = h->prec, dim = h->dim;
   const int velf = (kind == MG_DIFFUSION) ? 0
@@ -480,22 +490,30 @@ void jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, doub
                         h->st);
       sw += 2;
     } else {
-      if (sw + 1 == sweeps && last) dst = last;
-      ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, l, first ? 2.0 * ncomp : 3.0 * ncomp + velf),
-                   first ? f0 : fsw);
+      const bool final = (sw + 1 == sweeps);
+      if (final && last) dst = last;
+      const bool with_epi = final && last && epi && prec == IRK_MG_FP64 && !first;
+      ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, l, first ? 2.0 * ncomp : 3.0 * ncomp + velf) +
+                                       (with_epi ? 16.0 * ncomp * d.npts : 0.0),
+                   (first ? f0 : fsw) + (with_epi ? 2.0 * ncomp * d.npts : 0.0));
       launch_mg_smooth(prec, dim, kind, d, ncomp, sigma, cadv, cdiff, om, vel, b, cur, dst, first,
-                       h->st);
+                       h->st, with_epi ? epi->out : nullptr, with_epi ? epi->base : nullptr,
+                       with_epi ? epi->coef : 0.0);
+      epi_done = epi_done || with_epi;
       sw += 1;
     }
     if (dst == alt) std::swap(cur, alt);
   }
+  return epi_done;
 }
 
 // One V-cycle for A = sigma I + cadv adv(vel_k) - cdiff L on ncomp fields.
 // in/out: double, ncomp * npts_fine.  In FP64 storage the input is read in
 // place and the last fine-level sweep writes the output directly.
-void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double cadv, double cdiff,
-            int project_mean, const double* in, double* out) {
+// Returns whether `epi` (if given) was applied by the last fine-level sweep.
+bool vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double cadv, double cdiff,
+            int project_mean, const double* in, double* out, const MGEpilogue* epi = nullptr) {
+  bool epi_done = false;
   const int nl = mg_depth(h, sigma, cdiff), prec = h->prec, dim = h->dim;
   const double om = h->mg_omega;
   // shift-dominated rows of 2D grids (sigma >= 0.15 D on the finest level)
@@ -666,8 +684,10 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     }
     if (post > 0) {
       const bool to_out = alias && l == 0;
-      jacobi_sweeps(h, l, kk, ncomp, sigma, cadv, cdiff, om, crow[l], bl[l], post,
-                    false, cur[l], alt[l], to_out ? (void*)out : nullptr);
+      const bool e = jacobi_sweeps(h, l, kk, ncomp, sigma, cadv, cdiff, om, crow[l], bl[l], post,
+                                   false, cur[l], alt[l], to_out ? (void*)out : nullptr,
+                                   to_out ? epi : nullptr);
+      epi_done = epi_done || e;
       if (to_out) wrote_out = true;
     }
   }
@@ -676,10 +696,12 @@ void vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     launch_mg_convert_out(prec, cur[0], out, n0, h->st);
   }
   h->stats.vcycles += 1;
+  return epi_done;
 }
 
 // Inner inverse (sigma M - dt L_kk)^{-1} of one block row, approximated by MG.
-void row_prec(irk_handle* h, double dt, int row, double sigma, const double* in, double* out) {
+bool row_prec(irk_handle* h, double dt, int row, double sigma, const double* in, double* out,
+              const MGEpilogue* epi = nullptr) {
   const int op = h->g.op;
   if (op == IRK_OP_VSF_2D) {
     // Picard-type lower-triangular solve of the (omega, psi) row (Eq. vsf-system-1):
@@ -691,20 +713,37 @@ void row_prec(irk_handle* h, double dt, int row, double sigma, const double* in,
       launch_axpby(h->tmp2, -1.0 / dt, in + h->npts, 1.0, h->npts, h->st);
     }
     vcycle(h, -1, MG_DIFFUSION, 1, 0.0, 0.0, 1.0, 1, h->tmp2, out + h->npts);
-    return;
+    return false;
   }
   const int kind = (op == IRK_OP_BURGERS_1D) ? MG_CONSERVATIVE_1D
                    : (op == IRK_OP_BURGERS_2D) ? MG_ADVECTIVE : MG_DIFFUSION;
-  vcycle(h, row, kind, h->C, sigma, dt, dt * h->g.nu, 0, in, out);
+  return vcycle(h, row, kind, h->C, sigma, dt, dt * h->g.nu, 0, in, out, epi);
 }
 
 // z = L_P(v) for block blk (Eq. Lprec with the (2,1) block of Eq. diag_blocks)
 void block_prec(irk_handle* h, double dt, int blk, const double* v, double* z) {
   const int a = h->tab.bstart[blk], bs = h->tab.bsize[blk], s = h->s;
   const double eta = h->tab.eta[blk];
-  row_prec(h, dt, a, eta, v, z);
-  if (bs == 1) return;
+  if (bs == 1) {
+    row_prec(h, dt, a, eta, v, z);
+    return;
+  }
   const int b = a + 1;
+  const double gamma = (h->cfg.gamma_mode == 1) ? eta : h->tab.gamma_star[blk];
+  // a mass-only coupling row (no advective part for (b, a)) is pointwise:
+  // r_b' = v_b - R0_ba z_a is written by the last sweep of the first V-cycle
+  OpTerm probe;
+  memset(&probe, 0, sizeof(probe));
+  set_combo(h, probe, b, a);
+  if (!probe.combo) {
+    const MGEpilogue epi = {h->tmp, v + h->L, -h->tab.R[b * s + a]};
+    if (row_prec(h, dt, a, eta, v, z, &epi)) {
+      row_prec(h, dt, b, gamma, h->tmp, z + h->L);
+      return;
+    }
+  } else {
+    row_prec(h, dt, a, eta, v, z);
+  }
   StageOpArgs op;
   memset(&op, 0, sizeof(op));
   op.nrow = 1;
@@ -720,7 +759,6 @@ void block_prec(irk_handle* h, double dt, int blk, const double* v, double* z) {
   row.t[0].m = h->tab.R[b * s + a];
   row.t[0].lin = 0;
   run_stage_op(h, op);
-  const double gamma = (h->cfg.gamma_mode == 1) ? eta : h->tab.gamma_star[blk];
   row_prec(h, dt, b, gamma, h->tmp, z + h->L);
 }
 
