@@ -407,6 +407,22 @@ def run_ours(args, rank, world):
                            "vcycles_per_step": tot2["vcycles"] / 3}
         line["solver_comparison"] = {"workload": "burgers2d 512^2, s=3, dt=2e-3, FP64 V-cycles",
                                      "runs": cmp_}
+        # ---- the empirical autotuner on the headline workload (2 timed steps
+        # per candidate), then the same timed steps as the headline
+        h = make(args.stages, args.mg_precision, 0)
+        for _ in range(2):
+            B.irk_step(h, 0.0, DT, 1)
+        t_tune = time.perf_counter()
+        chosen = B.irk_autotune(h, 2 * DT, DT, 2)
+        t_tune = time.perf_counter() - t_tune
+        ms3, tot3, _ = timed_steps(h, args.steps, args.warmup, 2 * DT)
+        B.irk_destroy(h)
+        line["autotuned"] = {
+            "steps_per_s": 1e3 / (sum(ms3) / len(ms3)), "tuning_s": t_tune,
+            "krylov_its_per_step": tot3["krylov_its"] / args.steps,
+            "chosen": {"mg_shifted_sweeps": chosen.mg_shifted_sweeps,
+                       "mg_coarse_smoother": chosen.mg_coarse_smoother,
+                       "mg_coarse_reduction": chosen.mg_coarse_reduction}}
         if args.serving_requests > 0:
             line["serving"] = serving_leg(B, args.serving_requests, args.serving_rate)
         # ---- precision report: one step from u0 per V-cycle storage precision

@@ -252,6 +252,24 @@ irk_status irk_tableau(int family, int s, double* A, double* b, double* c,
 irk_status irk_transform(int family, int s, int basis, double* T, double* Tinv, double* R,
                          int* block_sizes, int* nblocks);
 
+/* The handle's current settings (after irk_autotune, the chosen ones). */
+irk_status irk_get_config(const irk_handle* h, irk_config* out);
+
+/* Empirical tuning of the V-cycle preconditioner on the handle's own
+ * workload.  From the current state and stages, each candidate setting is
+ * timed over `steps` IRK steps of size dt (after one untimed step that
+ * captures its graphs), by CUDA events on the handle's stream; candidates
+ * come by coordinate descent over mg_shifted_sweeps {1, 2},
+ * mg_coarse_smoother {0, 2} and mg_coarse_reduction {2e-2, 5e-3}, starting
+ * from the current settings, and the fastest is kept.  A candidate whose
+ * step fails is skipped.  State and stages are restored afterwards, and the
+ * statistics of the trial steps are discarded.  Allocates a backup of the
+ * state and stages (cudaMalloc) for the duration of the call.  The choice
+ * depends on measured times and can differ between runs; every candidate
+ * reaches the same Newton tolerance.  *chosen (may be NULL) receives the
+ * kept settings.  1 <= steps <= 100. */
+irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_config* chosen);
+
 /* Per-kernel-class timing gathered while cfg.profile = 1 (CUDA events on the
  * handle's stream).  Writes up to max entries, *count = entries written. */
 irk_status irk_kernel_stats(irk_handle* h, irk_kernel_stat* out, int max, int* count);

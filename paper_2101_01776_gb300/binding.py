@@ -108,6 +108,8 @@ def _load():
         "irk_stage_jacobian_apply": (i, [vp, d, vp, vp, vp, i]),
         "irk_tableau": (i, [i, i, vp, vp, vp, vp, vp, vp, vp]),
         "irk_transform": (i, [i, i, i, vp, vp, vp, vp, vp]),
+        "irk_get_config": (i, [vp, P(IrkConfig)]),
+        "irk_autotune": (i, [vp, d, d, i, P(IrkConfig)]),
         "irk_kernel_stats": (i, [vp, P(IrkKernelStat), i, P(i)]),
         "irk_reset_kernel_stats": (i, [vp]),
         "irk_device_bytes": (sz, [vp]),
@@ -138,6 +140,7 @@ EXPORTED = (
     "irk_status_string", "irk_destroy", "irk_stage_residual_noalloc",
     "irk_config_device_bytes", "irk_create_in", "irk_server_create", "irk_server_submit",
     "irk_server_wait", "irk_server_stats_get", "irk_server_destroy", "irk_transform",
+    "irk_get_config", "irk_autotune",
 )
 
 
@@ -327,6 +330,18 @@ def irk_transform(s: int, family: int = IRK_GAUSS, basis: int = IRK_BASIS_SCHUR)
     _check(LIB.irk_transform(family, s, basis, T.ctypes.data, Ti.ctypes.data, R.ctypes.data,
                              bs.ctypes.data, C.byref(nb)))
     return {"T": T, "Tinv": Ti, "R": R, "block_sizes": list(bs[:nb.value])}
+
+
+def irk_get_config(h) -> IrkConfig:
+    cfg = IrkConfig()
+    _check(LIB.irk_get_config(h, C.byref(cfg)), h)
+    return cfg
+
+
+def irk_autotune(h, t_n: float, dt: float, steps: int = 2) -> IrkConfig:
+    cfg = IrkConfig()
+    _check(LIB.irk_autotune(h, t_n, dt, steps, C.byref(cfg)), h)
+    return cfg
 
 
 def irk_kernel_stats(h):

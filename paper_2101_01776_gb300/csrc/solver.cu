@@ -2188,6 +2188,109 @@ irk_status irk_stage_jacobian_apply(irk_handle* h, double dt, const double* K, c
   return IRK_OK;
 }
 
+// Drop every captured graph (L_P, block solves, whole step): the next step
+// captures again with the handle's current settings.
+static void invalidate_graphs(irk_handle* h) {
+  drop_graphs(h);
+  h->graph_dt = 0.0;
+  drop_fg_graphs(h);
+  h->fg_dt = 0.0;
+  for (int k = 0; k < IRK_MAXS; ++k) h->fg_seen_its[k] = 0.0;
+  if (h->stepexec) {
+    cudaGraphExecDestroy(h->stepexec);
+    h->stepexec = nullptr;
+  }
+  h->step_dt = 0.0;
+}
+
+irk_status irk_get_config(const irk_handle* h, irk_config* out) {
+  if (!h || !out) return IRK_ERR_INVALID;
+  *out = h->cfg;
+  return IRK_OK;
+}
+
+irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_config* chosen) {
+  if (!h || !(dt > 0) || !std::isfinite(dt) || steps < 1 || steps > 100 || !std::isfinite(t_n)) {
+    if (h) h->err = "autotune: dt must be positive, 1 <= steps <= 100";
+    return IRK_ERR_INVALID;
+  }
+  const size_t ub = sizeof(double) * h->L, kb = sizeof(double) * h->L * h->s;
+  double *u0 = nullptr, *k0 = nullptr;
+  cudaError_t e = cudaMalloc((void**)&u0, ub);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&k0, kb);
+  if (e != cudaSuccess) {
+    cudaFree(u0);
+    cudaGetLastError();
+    h->err = "autotune: no device memory for the state backup";
+    return IRK_ERR_NOMEM;
+  }
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  irk_status st = IRK_OK;
+  const irk_stats saved_stats = h->stats;
+  auto restore = [&]() -> irk_status {
+    CK(cudaMemcpyAsync(h->u, u0, ub, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->K, k0, kb, cudaMemcpyDeviceToDevice, h->st));
+    return IRK_OK;
+  };
+  // ms per step of the current settings from the saved state (one untimed
+  // step first: it captures the graphs), or +inf when a step fails
+  auto measure = [&](double* ms) -> irk_status {
+    invalidate_graphs(h);
+    TRY(restore());
+    *ms = INFINITY;
+    if (irk_step(h, t_n, dt, 1, nullptr) != IRK_OK) return IRK_OK;
+    TRY(restore());
+    CK(cudaEventRecord(ev0, h->st));
+    const irk_status r = irk_step(h, t_n, dt, steps, nullptr);
+    CK(cudaEventRecord(ev1, h->st));
+    CK(cudaEventSynchronize(ev1));
+    if (r != IRK_OK) return IRK_OK;
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, ev0, ev1));
+    *ms = t / steps;
+    return IRK_OK;
+  };
+  do {
+    e = cudaMemcpyAsync(u0, h->u, ub, cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(k0, h->K, kb, cudaMemcpyDeviceToDevice, h->st);
+    if (e != cudaSuccess) { h->err = cudaGetErrorString(e); st = IRK_ERR_CUDA; break; }
+    double best = 0;
+    st = measure(&best);
+    if (st != IRK_OK) break;
+    // coordinate descent over the multigrid knobs of the V-cycle preconditioner
+    struct Knob { int which; double vals[2]; };
+    const Knob knobs[3] = {{0, {1, 2}}, {1, {0, 2}}, {2, {2e-2, 5e-3}}};
+    for (const Knob& kn : knobs) {
+      for (double v : kn.vals) {
+        irk_config trial = h->cfg;
+        if (kn.which == 0) { if (trial.mg_shifted_sweeps == (int)v) continue; trial.mg_shifted_sweeps = (int)v; }
+        if (kn.which == 1) { if (trial.mg_coarse_smoother == (int)v) continue; trial.mg_coarse_smoother = (int)v; }
+        if (kn.which == 2) { if (trial.mg_coarse_reduction == v) continue; trial.mg_coarse_reduction = v; }
+        const irk_config keep = h->cfg;
+        h->cfg = trial;
+        double ms = 0;
+        st = measure(&ms);
+        if (st != IRK_OK) break;
+        if (ms < best) best = ms;
+        else h->cfg = keep;
+      }
+      if (st != IRK_OK) break;
+    }
+  } while (0);
+  invalidate_graphs(h);
+  if (st == IRK_OK) st = restore();
+  cudaStreamSynchronize(h->st);
+  h->stats = saved_stats;
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  cudaFree(u0);
+  cudaFree(k0);
+  if (chosen) *chosen = h->cfg;
+  return st;
+}
+
 irk_status irk_kernel_stats(irk_handle* h, irk_kernel_stat* out, int max, int* count) {
   if (!h || !out || !count) return IRK_ERR_INVALID;
   prof_harvest(h);

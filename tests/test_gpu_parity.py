@@ -405,3 +405,27 @@ def test_full_size_vsf_1024_gauss5_one_step(B):
     g = p.N(u1)[1]
     assert np.abs(g).max() <= 1e-9 * np.abs(u1[0]).max()
     assert abs(u1[0].mean()) <= 1e-12 * np.abs(u1[0]).max()
+
+
+def test_autotune_restores_state_and_keeps_parity(B):
+    """irk_autotune times candidate V-cycle settings from the current state,
+    restores state and stages, and keeps one of the candidates; stepping with
+    the chosen settings still reaches the oracle's fixed point."""
+    n, s, nu, dt = 64, 2, 5e-3, 2e-3
+    p, length = make_problem("burgers2d", n, nu, s)
+    u0 = initial("burgers2d", n, 9)
+    with B.IrkSolver(u0, op="burgers2d", n=n, stages=s, nu=nu, length=length) as sol:
+        sol.step(0.0, dt, 1)
+        u1 = sol.state()
+        k1 = sol.stages()
+        chosen = B.irk_autotune(sol.h, dt, dt, 1)
+        np.testing.assert_array_equal(sol.state(), u1)
+        np.testing.assert_array_equal(sol.stages(), k1)
+        got = B.irk_get_config(sol.h)
+        assert got.mg_shifted_sweeps == chosen.mg_shifted_sweeps in (1, 2)
+        assert got.mg_coarse_smoother == chosen.mg_coarse_smoother in (0, 2)
+        assert got.mg_coarse_reduction in (2e-2, 5e-3)
+        sol.step(dt, dt, 1)
+        u2 = sol.state()
+    want, _, _ = oracle_step(p, s, u1, dt, dt)
+    assert rel(u2, want) <= STEP_TOL
