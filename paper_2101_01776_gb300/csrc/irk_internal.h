@@ -80,6 +80,7 @@ struct OpTerm {
                          // 6 * npts Burgers-2D, 16 * npts VSF), or null: formed per point
   double m;              // mass coefficient
   double lin;            // coefficient of the state-independent linear part
+  double kd, cc;         // set by launch_stage_op: dt lin nu / h^2 and m + 4 kd
 };
 struct OpRow {
   double* y;

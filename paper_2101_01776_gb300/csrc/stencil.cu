@@ -349,9 +349,8 @@ __device__ __forceinline__ void term_apply(const GridDesc& g, const OpTerm& t, c
     const double* f = t.coef + nb.c;
     const double AX = __ldg(f), AY = __ldg(f + npts), DU = __ldg(f + 2 * npts);
     const double XUV = __ldg(f + 3 * npts), XVU = __ldg(f + 4 * npts), DV = __ldg(f + 5 * npts);
-    const double kd = dt * t.lin * g.nu * g.invh2;
+    const double kd = t.kd, cc = t.cc;  // uniform, formed on the host
     const double ce = AX - kd, cw = -AX - kd, cn = AY - kd, cs = -AY - kd;
-    const double cc = t.m + 4.0 * kd;
     const double* xu = t.x;
     const double* xv = t.x + npts;
     const double uc = __ldg(xu + nb.c), vc = __ldg(xv + nb.c);
@@ -588,7 +587,14 @@ void launch_combo_coef(const GridDesc& g, const double* combos, const ComboList&
     k_combo_coef<<<blocks, 256, 0, st>>>(g, combos, list, dt, coef);
 }
 
-void launch_stage_op(const GridDesc& g, const StageOpArgs& a, cudaStream_t st) {
+void launch_stage_op(const GridDesc& g, const StageOpArgs& a_in, cudaStream_t st) {
+  StageOpArgs a = a_in;
+  for (int r = 0; r < a.nrow; ++r)
+    for (int t = 0; t < a.row[r].nterm; ++t) {
+      OpTerm& tm = a.row[r].t[t];
+      tm.kd = a.dt * tm.lin * g.nu * g.invh2;
+      tm.cc = tm.m + 4.0 * tm.kd;
+    }
   int blocks = (g.npts + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   switch (g.op) {
