@@ -203,7 +203,7 @@ void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
                       const void* w_in, void* w_out, int first, cudaStream_t st,
                       double* epi_out = nullptr, const double* epi_base = nullptr,
                       double epi_coef = 0.0);
-bool mg_smooth2_pays(int prec, int dim, const MGLevelDesc& lv, int first);
+bool mg_smooth2_pays(int prec, int dim, int kind, const MGLevelDesc& lv, int first);
 // The four off-diagonal coefficients of the 2D advective level operator,
 // coef = (beta + alpha a_x, beta - alpha a_x, beta + alpha a_y, beta - alpha a_y)
 // with alpha = cadv/(2h), beta = -cdiff/h^2, from the level velocity vel (2 fields)

@@ -266,8 +266,15 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
                                                         TS* __restrict__ w_mid, double wa64,
                                                         double wb64) {
   typedef typename Cmp<TS>::T TC;
+  constexpr int WX = kTX + 2, WY = kTY + 2, NW = WX * WY;  // the halo-1 window
   __shared__ TC s_in[kTY + 4][kTX + 4];
-  __shared__ TC s_w1[kTY + 2][kTX + 2];
+  __shared__ TC s_w1[WY][WX];
+  // b, the four off-diagonal coefficients (E, W, N, S) and, for CHEB, x_{k-1}
+  // on the halo-1 window, staged with w in one load phase so that both
+  // sweeps run out of shared memory
+  __shared__ TC s_b[NW];
+  __shared__ TC s_c[4][NW];
+  __shared__ TC s_p[CHEB ? NW : 1];
   const TC alpha = TC(k.alpha), beta = TC(k.beta), dinv = TC(k.dinv), keep = TC(k.keep);
   const TC wa = TC(wa64), wb = TC(wb64);
   const int n = lv.n, m = n - 1, ln = lv.logn;
@@ -282,48 +289,11 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
         s_in[ly][lx] = ldv(w_in + off + (gy << ln) + gx);
       }
     }
-    __syncthreads();
-    // sweep 1 on the halo-1 window
-    for (int q = tid; q < (kTY + 2) * (kTX + 2); q += kTX * kTY) {
-      const int ly = q / (kTX + 2), lx = q - ly * (kTX + 2);
+    for (int q = tid; q < NW; q += kTX * kTY) {
+      const int ly = q / WX, lx = q - ly * WX;
       const int gx = (x0 + lx - 1) & m, gy = (y0 + ly - 1) & m;
       const int gp = (gy << ln) + gx;
-      const TC bc = ldv(b + off + gp);
-      TC v;
-      if (first) {
-        v = dinv * bc;
-      } else {
-        TC ce = beta, cw = beta, cn = beta, cs = beta;
-        if (KIND == MG_ADVECTIVE) {
-          const TC ax = ldv(vel + gp), ay = ldv(vel + lv.npts + gp);
-          ce = fma(alpha, ax, beta); cw = fma(-alpha, ax, beta);
-          cn = fma(alpha, ay, beta); cs = fma(-alpha, ay, beta);
-        } else if (KIND == MG_ADVECTIVE_PRE) {
-          ce = ldv(vel + gp); cw = ldv(vel + lv.npts + gp);
-          cn = ldv(vel + 2 * lv.npts + gp); cs = ldv(vel + 3 * lv.npts + gp);
-        }
-        const int sy = ly + 1, sx = lx + 1;  // position in s_in
-        TC t = bc;
-        t = fma(-ce, s_in[sy][sx + 1], t);
-        t = fma(-cw, s_in[sy][sx - 1], t);
-        t = fma(-cn, s_in[sy + 1][sx], t);
-        t = fma(-cs, s_in[sy - 1][sx], t);
-        v = fma(dinv, t, keep * s_in[sy][sx]);
-        if (CHEB) {
-          const TC xp = ldv(w_prev + off + gp);
-          v = fma(wa, v - xp, xp);
-        }
-      }
-      v = round_to_storage<TS>(v);
-      s_w1[ly][lx] = v;
-      if (CHEB && lx >= 1 && lx <= kTX && ly >= 1 && ly <= kTY) stv<TS, TC>(w_mid + off + gp, v);
-    }
-    __syncthreads();
-    // sweep 2 on the tile
-    {
-      const int lx = threadIdx.x, ly = threadIdx.y;
-      const int gx = x0 + lx, gy = y0 + ly;
-      const int gp = (gy << ln) + gx;
+      s_b[q] = ldv(b + off + gp);
       TC ce = beta, cw = beta, cn = beta, cs = beta;
       if (KIND == MG_ADVECTIVE) {
         const TC ax = ldv(vel + gp), ay = ldv(vel + lv.npts + gp);
@@ -333,12 +303,48 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
         ce = ldv(vel + gp); cw = ldv(vel + lv.npts + gp);
         cn = ldv(vel + 2 * lv.npts + gp); cs = ldv(vel + 3 * lv.npts + gp);
       }
+      s_c[0][q] = ce; s_c[1][q] = cw; s_c[2][q] = cn; s_c[3][q] = cs;
+      if (CHEB) s_p[q] = first ? TC(0) : ldv(w_prev + off + gp);
+    }
+    __syncthreads();
+    // sweep 1 on the halo-1 window
+    for (int q = tid; q < NW; q += kTX * kTY) {
+      const int ly = q / WX, lx = q - ly * WX;
+      TC v;
+      if (first) {
+        v = dinv * s_b[q];
+      } else {
+        const int sy = ly + 1, sx = lx + 1;  // position in s_in
+        TC t = s_b[q];
+        t = fma(-s_c[0][q], s_in[sy][sx + 1], t);
+        t = fma(-s_c[1][q], s_in[sy][sx - 1], t);
+        t = fma(-s_c[2][q], s_in[sy + 1][sx], t);
+        t = fma(-s_c[3][q], s_in[sy - 1][sx], t);
+        v = fma(dinv, t, keep * s_in[sy][sx]);
+        if (CHEB) {
+          const TC xp = s_p[q];
+          v = fma(wa, v - xp, xp);
+        }
+      }
+      v = round_to_storage<TS>(v);
+      s_w1[ly][lx] = v;
+      if (CHEB && lx >= 1 && lx <= kTX && ly >= 1 && ly <= kTY) {
+        const int gx = (x0 + lx - 1) & m, gy = (y0 + ly - 1) & m;
+        stv<TS, TC>(w_mid + off + (gy << ln) + gx, v);
+      }
+    }
+    __syncthreads();
+    // sweep 2 on the tile
+    {
+      const int lx = threadIdx.x, ly = threadIdx.y;
+      const int gp = ((y0 + ly) << ln) + x0 + lx;
       const int sy = ly + 1, sx = lx + 1;
-      TC t = ldv(b + off + gp);
-      t = fma(-ce, s_w1[sy][sx + 1], t);
-      t = fma(-cw, s_w1[sy][sx - 1], t);
-      t = fma(-cn, s_w1[sy + 1][sx], t);
-      t = fma(-cs, s_w1[sy - 1][sx], t);
+      const int q = sy * WX + sx;  // the tile point in the halo-1 window
+      TC t = s_b[q];
+      t = fma(-s_c[0][q], s_w1[sy][sx + 1], t);
+      t = fma(-s_c[1][q], s_w1[sy][sx - 1], t);
+      t = fma(-s_c[2][q], s_w1[sy + 1][sx], t);
+      t = fma(-s_c[3][q], s_w1[sy - 1][sx], t);
       TC v = fma(dinv, t, keep * s_w1[sy][sx]);
       if (CHEB) {
         const TC xp = first ? TC(0) : s_in[sy + 1][sx + 1];  // x_k at this point
@@ -766,14 +772,16 @@ void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
 }
 
 // Whether one k_mg_smooth2 launch should replace two k_mg_smooth launches.
-// Measured on GB300 with two components: FP32/BF16 storage gains at every
-// size up to 1024^2 (0.5-1.0x the time); FP64 gains up to 256^2 and for the
-// pair that starts from zero (its first sweep reads b only), but loses on
-// larger levels, where the sweep is FP64-issue-bound (1.16x at 512^2).
-bool mg_smooth2_pays(int prec, int dim, const MGLevelDesc& lv, int first) {
+// Measured on GB300 with two components (time of the pair / time of two
+// single sweeps): up to 512^2 the pair wins at every storage precision
+// (0.5-0.94); on 1024^2 it loses (1.02-1.15: the staged tile's shared memory
+// costs occupancy on a bandwidth- or FP64-bound level) except for the pair
+// that starts from zero (its first sweep reads b only) on FP32/BF16 storage
+// or a diffusion operator (0.84-0.87).
+bool mg_smooth2_pays(int prec, int dim, int kind, const MGLevelDesc& lv, int first) {
   if (dim != 2 || lv.n < kTX) return false;  // n a power of two: tiles cover the grid
-  if (prec != IRK_MG_FP64) return true;
-  return lv.n <= 256 || first;
+  if (lv.n <= 512) return true;
+  return first && (prec != IRK_MG_FP64 || kind == MG_DIFFUSION);
 }
 
 void launch_mg_smooth2(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,

@@ -482,7 +482,7 @@ bool jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, doub
     const int first = from_zero && sw == 0;
     void* dst = first ? cur : alt;
     const bool ends_pair = (sw + 2 == sweeps);
-    if (sw + 1 < sweeps && mg_smooth2_pays(prec, dim, d, first) && !(ends_pair && last == b)) {
+    if (sw + 1 < sweeps && mg_smooth2_pays(prec, dim, kind, d, first) && !(ends_pair && last == b)) {
       if (ends_pair && last) dst = last;
       ProfScope ps(h, P_MG_SMOOTH2, mg_level_bytes(h, l, (first ? 2.0 : 3.0) * ncomp + velf),
                    first ? f0 + fsw : 2.0 * fsw);
