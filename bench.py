@@ -424,7 +424,13 @@ def run_ours(args, rank, world):
                        "mg_coarse_smoother": chosen.mg_coarse_smoother,
                        "mg_coarse_reduction": chosen.mg_coarse_reduction}}
         if args.serving_requests > 0:
-            line["serving"] = serving_leg(B, args.serving_requests, args.serving_rate)
+            # 8 slots: the lowest step latency at the mix's throughput (16
+            # slots measured the same steps/s at 4x the p50 step latency);
+            # 32 slots trade tail latency for throughput (host threads then
+            # outnumber the host cores)
+            line["serving"] = serving_leg(B, args.serving_requests, args.serving_rate, slots=8)
+            line["serving_32_slots"] = serving_leg(B, args.serving_requests, args.serving_rate,
+                                                   slots=32, budget_gib=48)
         # ---- precision report: one step from u0 per V-cycle storage precision
         prec_u = {}
         for prec, name in ((0, "fp64"), (1, "fp32"), (2, "bf16")):
@@ -500,7 +506,7 @@ def vsf_leg(B, torch, dev, stream, flush, timed_steps):
     return out
 
 
-def serving_leg(B, count, rate, slots=16, budget_gib=24):
+def serving_leg(B, count, rate, slots=8, budget_gib=24):
     """Config [4]: the first `count` requests of the seeded 512-request mix
     (2D Burgers, grid from {64,128,256,512}^2, nu log-uniform in [1e-3,1e-1],
     Gauss s in {2,3,4}, random-Fourier initial field seeded by request id,
