@@ -190,6 +190,13 @@ irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats*
 irk_status irk_get_state(irk_handle* h, double* dst, int dst_on_device);
 irk_status irk_set_state(irk_handle* h, const double* src, int src_on_device);
 
+/* irk_set_state for a caller that streams one trajectory through host
+ * memory: replaces the state but keeps the stages of the last accepted step
+ * as the next Newton guess (initial_guess = 1).  The tolerance stays relative
+ * to ||F(k=0)||, so the fixed point does not depend on the guess; for an
+ * unrelated state use irk_set_state, which starts from zero stages. */
+irk_status irk_set_state_keep_stages(irk_handle* h, const double* src, int src_on_device);
+
 /* Stage vectors k_1..k_s of the last accepted step (s*ncomp*n^dim values). */
 irk_status irk_get_stages(irk_handle* h, double* dst, int dst_on_device);
 

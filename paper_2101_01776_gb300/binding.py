@@ -102,6 +102,7 @@ def _load():
         "irk_step": (i, [vp, d, d, i, P(IrkStats)]),
         "irk_get_state": (i, [vp, vp, i]),
         "irk_set_state": (i, [vp, vp, i]),
+        "irk_set_state_keep_stages": (i, [vp, vp, i]),
         "irk_get_stages": (i, [vp, vp, i]),
         "irk_set_stages": (i, [vp, vp, i]),
         "irk_stage_residual": (i, [vp, d, d, vp, vp, i]),
@@ -140,7 +141,7 @@ EXPORTED = (
     "irk_status_string", "irk_destroy", "irk_stage_residual_noalloc",
     "irk_config_device_bytes", "irk_create_in", "irk_server_create", "irk_server_submit",
     "irk_server_wait", "irk_server_stats_get", "irk_server_destroy", "irk_transform",
-    "irk_get_config", "irk_autotune",
+    "irk_get_config", "irk_autotune", "irk_set_state_keep_stages",
 )
 
 
@@ -208,6 +209,11 @@ def irk_get_state(h, dst):
 def irk_set_state(h, src):
     p, dev = _ptr(src)
     _check(LIB.irk_set_state(h, p, dev), h)
+
+
+def irk_set_state_keep_stages(h, src):
+    p, dev = _ptr(src)
+    _check(LIB.irk_set_state_keep_stages(h, p, dev), h)
 
 
 def irk_get_stages(h, dst):

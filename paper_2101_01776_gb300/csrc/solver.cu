@@ -2134,6 +2134,14 @@ irk_status irk_set_state(irk_handle* h, const double* src, int src_on_device) {
   return IRK_OK;
 }
 
+irk_status irk_set_state_keep_stages(irk_handle* h, const double* src, int src_on_device) {
+  if (!h || !src) return IRK_ERR_INVALID;
+  CK(cudaMemcpyAsync(h->u, src, sizeof(double) * h->L,
+                     src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
+
 irk_status irk_set_stages(irk_handle* h, const double* src, int src_on_device) {
   if (!h || !src) return IRK_ERR_INVALID;
   CK(cudaMemcpyAsync(h->K, src, sizeof(double) * h->L * h->s,

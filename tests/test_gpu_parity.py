@@ -429,3 +429,27 @@ def test_autotune_restores_state_and_keeps_parity(B):
         u2 = sol.state()
     want, _, _ = oracle_step(p, s, u1, dt, dt)
     assert rel(u2, want) <= STEP_TOL
+
+
+def test_set_state_keep_stages_keeps_the_guess(B):
+    """irk_set_state_keep_stages replaces the state and keeps the stages as the
+    Newton guess; irk_set_state zeroes them; both reach the oracle's u_{n+1}."""
+    n, s, nu, dt = 32, 2, 5e-3, 2e-3
+    p, length = make_problem("burgers2d", n, nu, s)
+    u0 = initial("burgers2d", n, 10)
+    with B.IrkSolver(u0, op="burgers2d", n=n, stages=s, nu=nu, length=length) as sol:
+        sol.step(0.0, dt, 1)
+        u1 = sol.state()
+        k1 = sol.stages()
+        assert np.abs(k1).max() > 0
+        B.irk_set_state_keep_stages(sol.h, u1)
+        np.testing.assert_array_equal(sol.stages(), k1)
+        warm = sol.step(dt, dt, 1)
+        u2w = sol.state()
+        sol.set_state(u1)
+        assert np.abs(sol.stages()).max() == 0
+        cold = sol.step(dt, dt, 1)
+        u2c = sol.state()
+    want, _, _ = oracle_step(p, s, u1, dt, dt)
+    assert rel(u2w, want) <= STEP_TOL and rel(u2c, want) <= STEP_TOL
+    assert warm.newton_its <= cold.newton_its
