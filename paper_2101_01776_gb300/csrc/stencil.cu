@@ -285,8 +285,60 @@ __global__ void __launch_bounds__(256) k_residual_b2d(GridDesc g, ResidualArgs a
   if (threadIdx.x == 0 && a.partials) a.partials[blockIdx.x] = tot;
 }
 
+// VSF residual with one thread per point and component (as k_residual_b2d):
+// the vorticity item forms J_A(psi, w) + nu L w (M = 1), the streamfunction
+// item the constraint row -L psi - w (M = 0).
+template <int S>
+__global__ void __launch_bounds__(256) k_residual_vsf(GridDesc g, ResidualArgs a) {
+  __shared__ double sh[32];
+  const int npts = g.npts;
+  const long long L = 2LL * npts;
+  double sq = 0.0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 2 * npts; q += gridDim.x * blockDim.x) {
+    const int c = (q >= npts) ? 1 : 0;
+    const int p = q - c * npts;
+    const Nbr nb = neighbours(g, p);
+    double F[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      const double* Yw = a.Y + i * L;
+      const double* Yp = Yw + npts;
+      double nv;
+      if (c == 0) {
+        double w9[3][3], p9[3][3];
+        load9(Yw, nb, w9);
+        load9(Yp, nb, p9);
+        const double lw = (w9[1][2] + w9[1][0] + w9[2][1] + w9[0][1] - 4.0 * w9[1][1]) * g.invh2;
+        nv = arakawa12(p9, w9) * g.inv12h2 + g.nu * lw;
+        F[i] = __ldg(a.K + i * L + q) - nv;
+      } else {
+        const double lp = (__ldg(Yp + nb.e) + __ldg(Yp + nb.w) + __ldg(Yp + nb.n) +
+                           __ldg(Yp + nb.s) - 4.0 * __ldg(Yp + nb.c)) * g.invh2;
+        nv = -lp - __ldg(Yw + nb.c);
+        F[i] = -nv;
+      }
+      sq = fma(F[i], F[i], sq);
+    }
+    if (a.Fraw) {
+#pragma unroll
+      for (int i = 0; i < S; ++i) a.Fraw[i * L + q] = F[i];
+    }
+    if (a.rhs) {
+#pragma unroll
+      for (int k = 0; k < S; ++k) {
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 0; i < S; ++i) acc = fma(-a.Q[i * S + k], F[i], acc);
+        a.rhs[k * L + q] = acc;
+      }
+    }
+  }
+  const double tot = block_sum(sq, sh);
+  if (threadIdx.x == 0 && a.partials) a.partials[blockIdx.x] = tot;
+}
+
 int residual_blocks(const GridDesc& g) {
-  const long long items = (g.op == IRK_OP_BURGERS_2D) ? 2LL * g.npts : g.npts;
+  const long long items = (g.op == IRK_OP_BURGERS_2D || g.op == IRK_OP_VSF_2D) ? 2LL * g.npts : g.npts;
   int blocks = (int)((items + 255) / 256);
   if (blocks > 152 * 4) blocks = 152 * 4;
   return blocks;
@@ -302,6 +354,16 @@ static void launch_residual_op(const GridDesc& g, const ResidualArgs& a, cudaStr
       case 3: k_residual_b2d<3><<<blocks, 256, 0, st>>>(g, a); break;
       case 4: k_residual_b2d<4><<<blocks, 256, 0, st>>>(g, a); break;
       case 5: k_residual_b2d<5><<<blocks, 256, 0, st>>>(g, a); break;
+    }
+    return;
+  }
+  if (OP == IRK_OP_VSF_2D && !a.forcing) {
+    switch (a.s) {
+      case 1: k_residual_vsf<1><<<blocks, 256, 0, st>>>(g, a); break;
+      case 2: k_residual_vsf<2><<<blocks, 256, 0, st>>>(g, a); break;
+      case 3: k_residual_vsf<3><<<blocks, 256, 0, st>>>(g, a); break;
+      case 4: k_residual_vsf<4><<<blocks, 256, 0, st>>>(g, a); break;
+      case 5: k_residual_vsf<5><<<blocks, 256, 0, st>>>(g, a); break;
     }
     return;
   }
