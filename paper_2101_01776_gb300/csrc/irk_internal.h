@@ -202,7 +202,7 @@ void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
                       double cadv, double cdiff, double omega, const void* vel, const void* b,
                       const void* w_in, void* w_out, int first, cudaStream_t st,
                       double* epi_out = nullptr, const double* epi_base = nullptr,
-                      double epi_coef = 0.0);
+                      double epi_coef = 0.0, double epi_bcoef = 1.0);
 bool mg_smooth2_pays(int prec, int dim, int kind, const MGLevelDesc& lv, int first);
 // The four off-diagonal coefficients of the 2D advective level operator,
 // coef = (beta + alpha a_x, beta - alpha a_x, beta + alpha a_y, beta - alpha a_y)

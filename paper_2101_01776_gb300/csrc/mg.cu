@@ -152,7 +152,8 @@ MGConst mg_const(const MGLevelDesc& lv, int dim, double sigma, double cadv, doub
   return c;
 }
 
-// epi_out (FP64 storage only): also write epi_out = epi_base + epi_coef w_out
+// epi_out (FP64 storage only): also write epi_out = epi_bcoef epi_base +
+// epi_coef w_out pointwise (an L_P coupling row fused into the last sweep)
 // pointwise (the mass-only coupling row of L_P, fused into the last sweep)
 template <typename TS, int DIM, int KIND>
 __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, MGConst k,
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, MG
                                                    TS* __restrict__ w_out, int first,
                                                    double* __restrict__ epi_out,
                                                    const double* __restrict__ epi_base,
-                                                   double epi_coef) {
+                                                   double epi_coef, double epi_bcoef) {
   typedef typename Cmp<TS>::T TC;
   const TC alpha = TC(k.alpha), beta = TC(k.beta);
   const TC dinv = TC(k.dinv), keep = TC(k.keep);
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, MG
       // w + omega/D (b - D w - sum c w) = (1 - omega) w + omega/D (b - sum c w)
       const TC v = fma(dinv, t, keep * ldv(w_in + off + p));
       stv<TS, TC>(w_out + off + p, v);
-      if (epi_out) epi_out[off + p] = fma(epi_coef, (double)v, epi_base[off + p]);
+      if (epi_out) epi_out[off + p] = fma(epi_coef, (double)v, epi_bcoef * epi_base[off + p]);
     }
   }
 }
@@ -763,12 +764,12 @@ size_t mg_elem_size(int prec) {
 void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
                       double cadv, double cdiff, double omega, const void* vel, const void* b,
                       const void* w_in, void* w_out, int first, cudaStream_t st, double* epi_out,
-                      const double* epi_base, double epi_coef) {
+                      const double* epi_base, double epi_coef, double epi_bcoef) {
   const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, omega);
   if (prec != IRK_MG_FP64) epi_out = nullptr;  // the epilogue is defined on FP64 storage
   IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_smooth<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
       lv, ncomp, k, (const TS*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, epi_out,
-      epi_base, epi_coef))));
+      epi_base, epi_coef, epi_bcoef))));
 }
 
 // Whether one k_mg_smooth2 launch should replace two k_mg_smooth launches.

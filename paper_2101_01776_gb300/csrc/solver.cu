@@ -457,11 +457,12 @@ double mg_resid_flops(int kind, int dim, int ncomp) {
 // temporally blocked two-sweep kernel where it pays; it reads b on a halo, so
 // it never writes into b.
 // A pointwise epilogue for the last sweep of a V-cycle in FP64 storage:
-// out = base + coef * w (the mass-only coupling row of L_P).
+// out = bcoef * base + coef * w (a pointwise coupling row of L_P).
 struct MGEpilogue {
   double* out;
   const double* base;
-  double coef;
+  double coef;         // out = bcoef * base + coef * w
+  double bcoef = 1.0;
 };
 
 bool jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, double cadv,
@@ -498,7 +499,7 @@ bool jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, doub
                    (first ? f0 : fsw) + (with_epi ? 2.0 * ncomp * d.npts : 0.0));
       launch_mg_smooth(prec, dim, kind, d, ncomp, sigma, cadv, cdiff, om, vel, b, cur, dst, first,
                        h->st, with_epi ? epi->out : nullptr, with_epi ? epi->base : nullptr,
-                       with_epi ? epi->coef : 0.0);
+                       with_epi ? epi->coef : 0.0, with_epi ? epi->bcoef : 1.0);
       epi_done = epi_done || with_epi;
       sw += 1;
     }
@@ -706,8 +707,10 @@ bool row_prec(irk_handle* h, double dt, int row, double sigma, const double* in,
   if (op == IRK_OP_VSF_2D) {
     // Picard-type lower-triangular solve of the (omega, psi) row (Eq. vsf-system-1):
     // omega: sigma - dt (J_A(psibar, .) + nu L); psi: (-L) z_psi = z_omega - r_psi / dt
-    vcycle(h, row, MG_ADVECTIVE, 1, sigma, dt, dt * h->g.nu, 0, in, out);
-    {
+    // the psi right-hand side z_omega - r_psi / dt is pointwise: written by
+    // the last sweep of the omega V-cycle when it can be, else two axpby
+    const MGEpilogue ep = {h->tmp2, in + h->npts, 1.0, -1.0 / dt};
+    if (!vcycle(h, row, MG_ADVECTIVE, 1, sigma, dt, dt * h->g.nu, 0, in, out, &ep)) {
       ProfScope ps(h, P_AXPBY, 40.0 * h->npts, 3.0 * h->npts, 2);
       launch_axpby(h->tmp2, 1.0, out, 0.0, h->npts, h->st);
       launch_axpby(h->tmp2, -1.0 / dt, in + h->npts, 1.0, h->npts, h->st);
@@ -736,7 +739,7 @@ void block_prec(irk_handle* h, double dt, int blk, const double* v, double* z) {
   memset(&probe, 0, sizeof(probe));
   set_combo(h, probe, b, a);
   if (!probe.combo) {
-    const MGEpilogue epi = {h->tmp, v + h->L, -h->tab.R[b * s + a]};
+    const MGEpilogue epi = {h->tmp, v + h->L, -h->tab.R[b * s + a], 1.0};
     if (row_prec(h, dt, a, eta, v, z, &epi)) {
       row_prec(h, dt, b, gamma, h->tmp, z + h->L);
       return;
