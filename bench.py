@@ -12,8 +12,8 @@ One JSON line on rank 0.  Timing: CUDA events on the solver's stream around
 each step, L2 flushed (a 512 MiB write) between steps outside the events;
 max over ranks; each rank runs an independent replica (weak scaling, no
 collective on the data path).  `e2e` times the same steps through the C ABI
-with host buffers: set_state from pinned host memory, the step, get_state
-back to host.  `--impl reference` times the FP64 CPU oracle on the same
+with host buffers, as a caller streaming one trajectory: the state in from
+pinned host memory (set_state_keep_stages), the step, get_state back to host.  `--impl reference` times the FP64 CPU oracle on the same
 workload (a bounded number of steps on the host cores).
 """
 from __future__ import annotations
