@@ -204,6 +204,7 @@ void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
                       double* epi_out = nullptr, const double* epi_base = nullptr,
                       double epi_coef = 0.0, double epi_bcoef = 1.0);
 bool mg_smooth2_pays(int prec, int dim, int kind, const MGLevelDesc& lv, int first);
+bool mg_smooth3_pays(int prec, int dim, const MGLevelDesc& lv);
 // The four off-diagonal coefficients of the 2D advective level operator,
 // coef = (beta + alpha a_x, beta - alpha a_x, beta + alpha a_y, beta - alpha a_y)
 // with alpha = cadv/(2h), beta = -cdiff/h^2, from the level velocity vel (2 fields)
@@ -214,6 +215,11 @@ void launch_mg_coef(int prec, const MGLevelDesc& lv, double cadv, double cdiff, 
 // operator -L_h for cdiff = 1 (device memory, row-major)
 void launch_mg_bottom(int prec, const MGLevelDesc& lv, double cdiff, double omega, int pre,
                       int post, const double* pinv, const void* b, void* w, cudaStream_t st);
+// Three damped-Jacobi sweeps in one launch (2D, n >= 32), bit-equal to three
+// single sweeps: w_in -> w_out (w_in unused when first: w = 0)
+void launch_mg_smooth3(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
+                       double cadv, double cdiff, double omega, const void* vel, const void* b,
+                       const void* w_in, void* w_out, int first, cudaStream_t st);
 // One undamped red-black Gauss-Seidel sweep (2D, n >= 32): w_in -> w_out
 // (w_in unused when first: w = 0)
 void launch_mg_rbgs(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,

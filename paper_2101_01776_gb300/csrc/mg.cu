@@ -357,6 +357,101 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
   }
 }
 
+// Three damped-Jacobi sweeps in one launch, for latency-bound levels: the
+// tile loads w on its halo-3 window and b and the coefficients on its halo-2
+// window, then sweeps the halo-2 window, the halo-1 window and the tile out
+// of shared memory (1028 point updates for 768 useful ones).  Intermediate
+// sweeps are rounded to the storage type: three single sweeps bit for bit.
+template <typename TS, int KIND>
+__global__ void __launch_bounds__(kTX * kTY) k_mg_smooth3(MGLevelDesc lv, int ncomp, MGConst k,
+                                                        const TS* __restrict__ vel,
+                                                        const TS* __restrict__ b,
+                                                        const TS* __restrict__ w_in,
+                                                        TS* __restrict__ w_out, int first) {
+  typedef typename Cmp<TS>::T TC;
+  constexpr int X3 = kTX + 6, Y3 = kTY + 6;  // halo-3 window
+  constexpr int X2 = kTX + 4, Y2 = kTY + 4;  // halo-2 window (b, coefficients)
+  __shared__ TC s_w0[Y3][X3];
+  __shared__ TC s_w1[Y2][X2];
+  __shared__ TC s_b[Y2 * X2];
+  __shared__ TC s_c[4][Y2 * X2];
+  const TC alpha = TC(k.alpha), beta = TC(k.beta), dinv = TC(k.dinv), keep = TC(k.keep);
+  const int n = lv.n, m = n - 1, ln = lv.logn;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+  constexpr int NT = kTX * kTY;
+  for (int c = blockIdx.z; c < ncomp; c += gridDim.z) {
+    const long long off = (long long)c * lv.npts;
+    if (!first)
+      for (int q = tid; q < Y3 * X3; q += NT) {
+        const int ly = q / X3, lx = q - ly * X3;
+        const int gx = (x0 + lx - 3) & m, gy = (y0 + ly - 3) & m;
+        s_w0[ly][lx] = ldv(w_in + off + (gy << ln) + gx);
+      }
+    for (int q = tid; q < Y2 * X2; q += NT) {
+      const int ly = q / X2, lx = q - ly * X2;
+      const int gx = (x0 + lx - 2) & m, gy = (y0 + ly - 2) & m;
+      const int gp = (gy << ln) + gx;
+      s_b[q] = ldv(b + off + gp);
+      TC ce = beta, cw = beta, cn = beta, cs = beta;
+      if (KIND == MG_ADVECTIVE) {
+        const TC ax = ldv(vel + gp), ay = ldv(vel + lv.npts + gp);
+        ce = fma(alpha, ax, beta); cw = fma(-alpha, ax, beta);
+        cn = fma(alpha, ay, beta); cs = fma(-alpha, ay, beta);
+      } else if (KIND == MG_ADVECTIVE_PRE) {
+        ce = ldv(vel + gp); cw = ldv(vel + lv.npts + gp);
+        cn = ldv(vel + 2 * lv.npts + gp); cs = ldv(vel + 3 * lv.npts + gp);
+      }
+      s_c[0][q] = ce; s_c[1][q] = cw; s_c[2][q] = cn; s_c[3][q] = cs;
+    }
+    __syncthreads();
+    // sweep 1 on the halo-2 window: s_w0 (halo 3) -> s_w1 (halo 2)
+    for (int q = tid; q < Y2 * X2; q += NT) {
+      const int ly = q / X2, lx = q - ly * X2;
+      TC v;
+      if (first) {
+        v = dinv * s_b[q];
+      } else {
+        const int sy = ly + 1, sx = lx + 1;
+        TC t = s_b[q];
+        t = fma(-s_c[0][q], s_w0[sy][sx + 1], t);
+        t = fma(-s_c[1][q], s_w0[sy][sx - 1], t);
+        t = fma(-s_c[2][q], s_w0[sy + 1][sx], t);
+        t = fma(-s_c[3][q], s_w0[sy - 1][sx], t);
+        v = fma(dinv, t, keep * s_w0[sy][sx]);
+      }
+      s_w1[ly][lx] = round_to_storage<TS>(v);
+    }
+    __syncthreads();
+    // sweep 2 on the halo-1 window: s_w1 -> s_w0 (reused, halo-1 positions)
+    for (int q = tid; q < (kTY + 2) * (kTX + 2); q += NT) {
+      const int ly = q / (kTX + 2), lx = q - ly * (kTX + 2);
+      const int sy = ly + 1, sx = lx + 1;  // in the halo-2 window
+      const int cq = sy * X2 + sx;
+      TC t = s_b[cq];
+      t = fma(-s_c[0][cq], s_w1[sy][sx + 1], t);
+      t = fma(-s_c[1][cq], s_w1[sy][sx - 1], t);
+      t = fma(-s_c[2][cq], s_w1[sy + 1][sx], t);
+      t = fma(-s_c[3][cq], s_w1[sy - 1][sx], t);
+      s_w0[ly][lx] = round_to_storage<TS>(fma(dinv, t, keep * s_w1[sy][sx]));
+    }
+    __syncthreads();
+    // sweep 3 on the tile: s_w0 (halo-1 window at [0..kTY+1][0..kTX+1]) -> global
+    {
+      const int lx = threadIdx.x, ly = threadIdx.y;
+      const int sy = ly + 1, sx = lx + 1;  // in the halo-1 window
+      const int cq = (ly + 2) * X2 + (lx + 2);
+      TC t = s_b[cq];
+      t = fma(-s_c[0][cq], s_w0[sy][sx + 1], t);
+      t = fma(-s_c[1][cq], s_w0[sy][sx - 1], t);
+      t = fma(-s_c[2][cq], s_w0[sy + 1][sx], t);
+      t = fma(-s_c[3][cq], s_w0[sy - 1][sx], t);
+      stv<TS, TC>(w_out + off + ((y0 + ly) << ln) + x0 + lx, fma(dinv, t, keep * s_w0[sy][sx]));
+    }
+    __syncthreads();
+  }
+}
+
 // One red-black Gauss-Seidel sweep (2D, undamped) per launch: red points
 // ((x + y) even) are updated from their black neighbours, then black points
 // from the new red ones.  A 32 x 8 tile loads w on its halo-2 window, updates
@@ -779,6 +874,14 @@ void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
 // costs occupancy on a bandwidth- or FP64-bound level) except for the pair
 // that starts from zero (its first sweep reads b only) on FP32/BF16 storage
 // or a diffusion operator (0.84-0.87).
+// Whether one k_mg_smooth3 launch should replace a pair and a single sweep
+// (measured on GB300, two components: 0.5-0.93 up to 512^2 at every storage
+// precision and on 1024^2 for FP32/BF16; 1.05-1.12 for FP64 on 1024^2).
+bool mg_smooth3_pays(int prec, int dim, const MGLevelDesc& lv) {
+  if (dim != 2 || lv.n < kTX) return false;
+  return lv.n <= 512 || prec != IRK_MG_FP64;
+}
+
 bool mg_smooth2_pays(int prec, int dim, int kind, const MGLevelDesc& lv, int first) {
   if (dim != 2 || lv.n < kTX) return false;  // n a power of two: tiles cover the grid
   if (lv.n <= 512) return true;
@@ -822,6 +925,25 @@ void launch_mg_rbgs(int prec, int kind, const MGLevelDesc& lv, int ncomp, double
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
     else
       k_mg_rbgs<TS, MG_DIFFUSION><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
+  });
+}
+
+void launch_mg_smooth3(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
+                       double cadv, double cdiff, double omega, const void* vel, const void* b,
+                       const void* w_in, void* w_out, int first, cudaStream_t st) {
+  const MGConst k = mg_const(lv, 2, sigma, cadv, cdiff, omega);
+  const int zsplit = (lv.n <= 256) ? ncomp : 1;
+  const dim3 grid(lv.n / kTX, lv.n / kTY, zsplit), block(kTX, kTY);
+  IRK_DISPATCH_PREC(prec, {
+    if (kind == MG_ADVECTIVE)
+      k_mg_smooth3<TS, MG_ADVECTIVE><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
+    else if (kind == MG_ADVECTIVE_PRE)
+      k_mg_smooth3<TS, MG_ADVECTIVE_PRE><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
+    else
+      k_mg_smooth3<TS, MG_DIFFUSION><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
   });
 }

@@ -38,7 +38,7 @@ const char* kProfNames[P_NCLASS] = {
   "stage_states", "residual", "stage_op", "stage_update", "mg_smooth", "mg_residual",
   "mg_restrict", "mg_prolong", "mg_coarse", "mg_convert", "mg_setup", "gs_multi_dot",
   "gs_update_dot", "reduce", "scale_copy", "lincomb", "norm2", "axpby", "remove_mean",
-  "mg_smooth2"};
+  "mg_smooth_tile"};
 
 struct PendingEvent {
   int cls;
@@ -483,7 +483,16 @@ bool jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, doub
     const int first = from_zero && sw == 0;
     void* dst = first ? cur : alt;
     const bool ends_pair = (sw + 2 == sweeps);
-    if (sw + 1 < sweeps && mg_smooth2_pays(prec, dim, kind, d, first) && !(ends_pair && last == b)) {
+    const int rem = sweeps - sw;
+    // three sweeps per launch for 3, 5, 6, 7, ... remaining (4 go as two pairs)
+    if (rem >= 3 && rem != 4 && mg_smooth3_pays(prec, dim, d) && !(rem == 3 && last == b)) {
+      if (rem == 3 && last) dst = last;
+      ProfScope ps(h, P_MG_SMOOTH2, mg_level_bytes(h, l, (first ? 2.0 : 3.0) * ncomp + velf),
+                   first ? f0 + 2.0 * fsw : 3.0 * fsw);
+      launch_mg_smooth3(prec, kind, d, ncomp, sigma, cadv, cdiff, om, vel, b, cur, dst, first,
+                        h->st);
+      sw += 3;
+    } else if (sw + 1 < sweeps && mg_smooth2_pays(prec, dim, kind, d, first) && !(ends_pair && last == b)) {
       if (ends_pair && last) dst = last;
       ProfScope ps(h, P_MG_SMOOTH2, mg_level_bytes(h, l, (first ? 2.0 : 3.0) * ncomp + velf),
                    first ? f0 + fsw : 2.0 * fsw);
