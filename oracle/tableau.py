@@ -7,6 +7,8 @@ Radau IIA is collocation on the right Radau nodes (zeros of P_s - P_{s-1}).
 Lobatto IIIC (Table 1) uses the Lobatto nodes (zeros of P_s - P_{s-2}),
 b = the Lobatto weights, a_i1 = b_1 and the conditions
 sum_j a_ij c_j^{q-1} = c_i^q / q for q = 1..s-1.
+SDIRK (the diagonally implicit methods the paper compares against, Sec. 5):
+lower triangular A with one diagonal value gamma, stiffly accurate.
 
 Real Schur form (Sec. 3.1): A0^{-1} = Q0 R0 Q0^T with Q0 orthogonal and R0
 block upper triangular, 1x1 blocks for real eigenvalues and standardized
@@ -90,9 +92,41 @@ def lobatto_iiic(s: int):
     return A, b, c
 
 
+def sdirk(s: int):
+    """Return (A, b, c) of the L-stable, stiffly accurate SDIRK method with s
+    stages used as the diagonally implicit comparison (Sec. 1.2, Sec. 5):
+    s = 1 backward Euler (order 1); s = 2 gamma = 1 - sqrt(2)/2 (order 2);
+    s = 3 Alexander's method, gamma the root in (1/6, 1/2) of
+    x^3 - 3x^2 + 3x/2 - 1/6 (order 3); s = 5 the order-4 method of
+    Hairer and Wanner (Sec. IV.6), gamma = 1/4, rational coefficients.
+    """
+    if s == 1:
+        return np.array([[1.0]]), np.array([1.0]), np.array([1.0])
+    if s == 2:
+        g = 1.0 - np.sqrt(2.0) / 2.0
+        A = np.array([[g, 0.0], [1.0 - g, g]])
+    elif s == 3:
+        r = np.roots([1.0, -3.0, 1.5, -1.0 / 6.0])
+        g = float(np.real(r[(np.abs(r.imag) < 1e-12) & (r.real > 1 / 6) & (r.real < 0.5)][0]))
+        t2 = 0.5 * (1.0 + g)
+        b1 = -(6.0 * g * g - 16.0 * g + 1.0) / 4.0
+        b2 = (6.0 * g * g - 20.0 * g + 5.0) / 4.0
+        A = np.array([[g, 0.0, 0.0], [t2 - g, g, 0.0], [b1, b2, g]])
+    elif s == 5:
+        A = np.array([[1 / 4, 0, 0, 0, 0],
+                      [1 / 2, 1 / 4, 0, 0, 0],
+                      [17 / 50, -1 / 25, 1 / 4, 0, 0],
+                      [371 / 1360, -137 / 2720, 15 / 544, 1 / 4, 0],
+                      [25 / 24, -49 / 48, 125 / 16, -85 / 12, 1 / 4]])
+    else:
+        raise ValueError("SDIRK stage count must be 1, 2, 3 or 5")
+    return A, A[-1].copy(), A.sum(axis=1)
+
+
 def tableau(family: str, s: int):
-    """(A, b, c) by family name: 'gauss', 'radau' or 'lobatto'."""
-    return {"gauss": gauss, "radau": radau_iia, "lobatto": lobatto_iiic}[family](s)
+    """(A, b, c) by family name: 'gauss', 'radau', 'lobatto' or 'sdirk'."""
+    return {"gauss": gauss, "radau": radau_iia, "lobatto": lobatto_iiic,
+            "sdirk": sdirk}[family](s)
 
 
 def real_eigen_basis(Ainv: np.ndarray):

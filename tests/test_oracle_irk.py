@@ -142,6 +142,38 @@ def test_observed_order_is_2s_on_manufactured_solution(s):
     assert np.all(np.abs(rates - 2 * s) < 0.35), rates
 
 
+@pytest.mark.parametrize("s", [1, 2, 3, 5])
+def test_sdirk_linear_diffusion_matches_stability_function(s):
+    """SDIRK on u_t = nu L u multiplies mode m by R(z) = 1 + z b^T (I - z A)^{-1} 1
+    (the stability function's definition), z = dt lambda_m; for backward
+    Euler that is 1/(1 - z)."""
+    n, nu, dt = 32, 0.05, 0.01
+    p = Problem("diffusion1d", n, nu)
+    u0 = np.random.default_rng(10 + s).standard_normal((1, n))
+    u1, _, _ = irk.step(p, s, u0, 0.0, dt, family="sdirk")
+    A, b, _ = tab.sdirk(s)
+    m = np.arange(n)
+    z = -dt * (4 * nu / p.h ** 2) * np.sin(np.pi * m / n) ** 2
+    R = np.array([1.0 + zz * (b @ np.linalg.solve(np.eye(s) - zz * A, np.ones(s))) for zz in z])
+    if s == 1:
+        np.testing.assert_allclose(R, 1.0 / (1.0 - z), rtol=1e-14)
+    np.testing.assert_allclose(np.fft.fft(u1[0]), R * np.fft.fft(u0[0]),
+                               atol=1e-12 * np.abs(np.fft.fft(u0[0])).max())
+
+
+@pytest.mark.parametrize("s,order", [(1, 1), (2, 2), (3, 3), (5, 4)])
+def test_sdirk_observed_order_on_manufactured_solution(s, order):
+    """Same manufactured solution as above: SDIRK's error falls at its
+    classical order (1, 2, 3, 4) once dt is in the asymptotic range."""
+    p = Problem("burgers1d", 32, 0.02, forcing=1)
+    errs = []
+    for nst in (16, 32, 64):
+        u, _ = irk.integrate(p, s, p.exact_manufactured(0.0), 0.0, 1.0 / nst, nst, family="sdirk")
+        errs.append(np.abs(u - p.exact_manufactured(1.0)).max())
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(rates - order) < 0.3), rates
+
+
 def test_newton_quadratic_convergence_config0():
     p = Problem("burgers1d", 256, 0.01)
     u0 = workloads.burgers1d_initial(256, seed=0)[None]

@@ -302,3 +302,82 @@ def test_newton_like_1_lumping_on_radau3_example():
     assert picks == [0, 1]
     np.testing.assert_allclose(sorted(np.max(np.abs(d[i, i])) for i in range(2)),
                                [GOLDEN["radau_iia3_Phat"]["d11"][0]] * 2, atol=6e-4)
+
+
+def _tree_conditions(A, b, c):
+    """Elementary weights minus 1/gamma(t) for the 17 rooted trees of order
+    <= 5 (Butcher's order conditions, Hairer-Norsett-Wanner Sec. II.2),
+    grouped by order."""
+    Ac = A @ c
+    out = {1: [b.sum() - 1.0],
+           2: [b @ c - 1 / 2],
+           3: [b @ c ** 2 - 1 / 3, b @ Ac - 1 / 6],
+           4: [b @ c ** 3 - 1 / 4, b @ (c * Ac) - 1 / 8, b @ (A @ c ** 2) - 1 / 12,
+               b @ (A @ Ac) - 1 / 24],
+           5: [b @ c ** 4 - 1 / 5, b @ (c ** 2 * Ac) - 1 / 10, b @ (c * (A @ c ** 2)) - 1 / 15,
+               b @ (c * (A @ Ac)) - 1 / 30, b @ (Ac * Ac) - 1 / 20, b @ (A @ c ** 3) - 1 / 20,
+               b @ (A @ (c * Ac)) - 1 / 40, b @ (A @ (A @ c ** 2)) - 1 / 60,
+               b @ (A @ (A @ Ac)) - 1 / 120]}
+    return out
+
+
+@pytest.mark.parametrize("s,order", [(1, 1), (2, 2), (3, 3), (5, 4)])
+def test_sdirk_order_exactly(s, order):
+    """Every tree condition up to the claimed order holds; one of the next
+    order fails (so a dropped or mistyped coefficient cannot hide)."""
+    A, b, c = tab.sdirk(s)
+    np.testing.assert_allclose(A.sum(axis=1), c, atol=1e-15)
+    conds = _tree_conditions(A, b, c)
+    for p in range(1, order + 1):
+        assert max(abs(x) for x in conds[p]) < 1e-13, (p, conds[p])
+    assert max(abs(x) for x in conds[order + 1]) > 1e-4
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 5])
+def test_sdirk_structure_and_l_stability(s):
+    """Lower triangular with one diagonal value, stiffly accurate (b = last
+    row), R(inf) = 1 - b^T A^{-1} 1 = 0, |R(iy)| <= 1 (A-stability: the only
+    pole 1/gamma lies in the right half-plane)."""
+    A, b, c = tab.sdirk(s)
+    g = A[0, 0]
+    assert np.allclose(np.triu(A, 1), 0.0)
+    np.testing.assert_allclose(np.diag(A), g, atol=0)
+    np.testing.assert_allclose(b, A[-1], atol=0)
+    assert abs(c[-1] - 1.0) < 1e-15
+    e = np.ones(s)
+    assert abs(1.0 - b @ np.linalg.solve(A, e)) < 1e-13
+    for y in np.concatenate([np.logspace(-3, 6, 200), [1e9]]):
+        R = 1.0 + 1j * y * (b @ np.linalg.solve(np.eye(s) - 1j * y * A, e))
+        assert abs(R) <= 1.0 + 1e-13
+
+
+def test_sdirk_closed_forms():
+    """gamma of the 2-stage method solves gamma^2 - 2 gamma + 1/2 = 0 (order 2
+    with b = last row); Alexander's gamma is the root near 0.4358665215 of
+    its cubic; the order-4 method has the nodes 1/4, 3/4, 11/20, 1/2, 1."""
+    A2, _, _ = tab.sdirk(2)
+    g2 = A2[0, 0]
+    assert abs(g2 * g2 - 2 * g2 + 0.5) < 1e-15
+    A3, _, _ = tab.sdirk(3)
+    assert abs(A3[0, 0] - 0.4358665215) < 1e-10
+    A5, b5, c5 = tab.sdirk(5)
+    np.testing.assert_allclose(c5, [1 / 4, 3 / 4, 11 / 20, 1 / 2, 1.0], atol=1e-15)
+
+
+def test_sdirk_reversal_schur_form():
+    """A0^{-1} of an SDIRK tableau is lower triangular: with the reversal
+    permutation J (orthogonal), J A0^{-1} J is upper triangular with every
+    diagonal entry 1/gamma, i.e. a real Schur form with 1x1 blocks only, and
+    all off-diagonal d-vectors (J_km J_ml, k != l) vanish."""
+    for s in (2, 3, 5):
+        A, _, _ = tab.sdirk(s)
+        Ainv = np.linalg.inv(A)
+        J = np.eye(s)[::-1]
+        R = J @ Ainv @ J
+        assert np.allclose(np.tril(R, -1), 0.0, atol=1e-13)
+        np.testing.assert_allclose(np.diag(R), 1.0 / A[0, 0], rtol=1e-13)
+        d = tab.d_vectors(J)
+        for k in range(s):
+            for l in range(s):
+                if k != l:
+                    assert np.all(d[k, l] == 0.0)
