@@ -419,6 +419,25 @@ def run_ours(args, rank, world):
                            "vcycles_per_step": tot2["vcycles"] / 3}
         line["solver_comparison"] = {"workload": "burgers2d 512^2, s=3, dt=2e-3, FP64 V-cycles",
                                      "runs": cmp_}
+        # ---- fully implicit against SDIRK of equal order (the comparison of
+        # Sec. 7: preconditioner applications per step), same workload and dt;
+        # SDIRK solves its stages one after another
+        dirk = {}
+        for label, fam, ns in (("gauss1_order2", 0, 1), ("sdirk2_order2", 3, 2),
+                               ("radau_iia2_order3", 1, 2), ("sdirk3_order3", 3, 3),
+                               ("gauss2_order4", 0, 2), ("sdirk5_order4", 3, 5),
+                               ("gauss3_order6", 0, 3)):
+            h = make(ns, 0, 0, 3, family=fam)
+            ms2, tot2, _ = timed_steps(h, 3, 2)
+            B.irk_destroy(h)
+            dirk[label] = {"steps_per_s": 1e3 / (sum(ms2) / len(ms2)),
+                           "newton_its_per_step": tot2["newton_its"] / 3,
+                           "krylov_its_per_step": tot2["krylov_its"] / 3,
+                           "prec_apps_per_step": tot2["prec_apps"] / 3,
+                           "vcycles_per_step": tot2["vcycles"] / 3}
+        line["gauss_vs_sdirk"] = {"workload": "burgers2d 512^2, dt=2e-3, FP64 V-cycles, "
+                                              "3 steps after 2", "runs": dirk}
+        line["vsf_dae_solvers"] = vsf_dae_leg(B, torch, dev, stream, flush)
         # ---- the empirical autotuner on the headline workload (2 timed steps
         # per candidate), then the same timed steps as the headline
         h = make(args.stages, args.mg_precision, 0)
@@ -475,6 +494,52 @@ def run_ours(args, rank, world):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def vsf_dae_leg(B, torch, dev, stream, flush):
+    """The two DAE solvers of Sec. 7.2 on the double shear layer, 256^2,
+    Re=1000, dt=5e-3, FP64, 2 steps after 1: Eq. vsf-system-1 (dae_solver 0:
+    FGMRES on each (omega, psi) block, one omega and one psi V-cycle per
+    preconditioner application) and the block forward solve of Eq.
+    vsf-system-2 (dae_solver 1); Gauss s=1..5 and SDIRK of orders 1-4.
+    Reports omega and psi V-cycles per step (the paper's AIR and AMG
+    iteration counts of Table dsl-iters)."""
+    import math
+    import workloads
+    n, nu, dt = 256, 1e-3, 5e-3
+    u0 = np.zeros((2, n, n))
+    u0[0] = workloads.double_shear_layer_vorticity(n, seed=2)
+    runs = {}
+    for fam, name, stages in ((0, "gauss", (1, 2, 3, 4, 5)), (3, "sdirk", (1, 2, 3, 5))):
+        for ns in stages:
+            for ds in (0, 1):
+                cfg = B.irk_config_default(op="vsf", n=n, nu=nu, stages=ns, family=fam,
+                                           length=2 * math.pi, dae_solver=ds)
+                h = B.irk_create(cfg, torch.from_numpy(u0).to(dev), stream)
+                t = 0.0
+                B.irk_step(h, t, dt, 1)
+                t += dt
+                ms, agg = [], {"newton_its": 0, "prec_apps": 0, "vcycles": 0, "poisson_vcycles": 0}
+                for _ in range(2):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    st = B.irk_step(h, t, dt, 1)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    ms.append(e0.elapsed_time(e1))
+                    for k in agg:
+                        agg[k] += getattr(st, k)
+                    t += dt
+                B.irk_destroy(h)
+                runs[f"{name}{ns}_system{ds + 1}"] = {
+                    "steps_per_s": 1e3 / (sum(ms) / len(ms)),
+                    "newton_its_per_step": agg["newton_its"] / 2,
+                    "prec_apps_per_step": agg["prec_apps"] / 2,
+                    "omega_vcycles_per_step": (agg["vcycles"] - agg["poisson_vcycles"]) / 2,
+                    "psi_vcycles_per_step": agg["poisson_vcycles"] / 2}
+    return {"workload": "vsf 256^2 double shear layer, Re=1000, dt=5e-3, FP64", "runs": runs}
 
 
 def vsf_leg(B, torch, dev, stream, flush, timed_steps):

@@ -59,11 +59,17 @@ typedef enum {
 } irk_status;
 
 /* Runge-Kutta families with A0 invertible and A0^{-1} positive stable (the
- * standing assumption of Sec. 2; Table 1 covers all three). */
+ * standing assumption of Sec. 2; Table 1 covers the first three).  SDIRK is
+ * the diagonally implicit comparison of Sec. 7 (Tables ev-solvers,
+ * naca-iters, dsl-iters; DIRK background in Sec. 2.1): lower
+ * triangular A0 with one diagonal value gamma, stiffly accurate, L-stable. */
 typedef enum {
   IRK_GAUSS = 0,        /* order 2s */
   IRK_RADAU_IIA = 1,    /* order 2s-1, stiffly accurate */
-  IRK_LOBATTO_IIIC = 2  /* order 2s-2, s >= 2 */
+  IRK_LOBATTO_IIIC = 2, /* order 2s-2, s >= 2 */
+  IRK_SDIRK = 3         /* s = 1, 2, 3, 5: order 1, 2, 3, 4 (backward Euler;
+                           gamma = 1 - sqrt(1/2); Alexander's 3-stage method;
+                           the 5-stage order-4 method of Hairer and Wanner) */
 } irk_family;
 
 /* Basis of the A0^{-1} transform in Algorithm 1 (Sec. 3.1). */
@@ -136,6 +142,21 @@ typedef struct {
                            1 Chebyshev-accelerated Jacobi;
                            2 red-black Gauss-Seidel, one sweep per launch,
                              half the sweeps of Jacobi */
+  int dirk_sequential;  /* IRK_SDIRK only: 1 (default) = solve the stages one
+                           after another, each a nonlinear solve of
+                           M k_i = N(u_n + dt sum_{j<i} a_ij k_j + dt gamma k_i)
+                           with its own Newton loop (the usual DIRK solve);
+                           0 = Algorithm 1 over the coupled stage system (the
+                           transformed Jacobian is exactly block upper
+                           triangular, so variant 3 is exact Newton there) */
+  int dae_solver;       /* IRK_OP_VSF_2D only (Sec. 7.2): 0 (default) = FGMRES
+                           on each (omega, psi) block of Eq. vsf-system-1 with
+                           one omega V-cycle and one psi V-cycle per
+                           preconditioner application; 1 = block forward
+                           solve of the reordered Picard system Eq.
+                           vsf-system-2: FGMRES on the omega block to
+                           krylov_rtol, then one MG-preconditioned FGMRES
+                           Poisson solve per stream function row */
 } irk_config;
 
 typedef struct {
@@ -149,6 +170,8 @@ typedef struct {
   double final_rel_res; /* ||F|| / ||F(0)|| at acceptance of the last step */
   long long kernel_launches; /* this library's kernel launches in the call */
   int outer_its;        /* variant 4: outer FGMRES iterations on the true Jacobian */
+  int poisson_vcycles;  /* VSF: V-cycles on the stream function Poisson block
+                           (included in vcycles) */
 } irk_stats;
 
 typedef struct {

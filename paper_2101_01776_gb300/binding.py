@@ -25,9 +25,10 @@ IRK_ERR_KRYLOV_BREAKDOWN = 6
 IRK_ERR_TIMEOUT = 7
 IRK_ERR_NO_DEVICE = 8
 
-IRK_GAUSS, IRK_RADAU_IIA, IRK_LOBATTO_IIIC = 0, 1, 2
+IRK_GAUSS, IRK_RADAU_IIA, IRK_LOBATTO_IIIC, IRK_SDIRK = 0, 1, 2, 3
 IRK_BASIS_SCHUR, IRK_BASIS_EIGEN = 0, 1
-FAMILY_NAMES = {"gauss": IRK_GAUSS, "radau": IRK_RADAU_IIA, "lobatto": IRK_LOBATTO_IIIC}
+FAMILY_NAMES = {"gauss": IRK_GAUSS, "radau": IRK_RADAU_IIA, "lobatto": IRK_LOBATTO_IIIC,
+                "sdirk": IRK_SDIRK}
 IRK_OP_DIFFUSION_1D, IRK_OP_BURGERS_1D, IRK_OP_BURGERS_2D, IRK_OP_VSF_2D = 0, 1, 2, 3
 IRK_MASS_IDENTITY, IRK_MASS_DAE = 0, 1
 IRK_MG_FP64, IRK_MG_FP32, IRK_MG_BF16 = 0, 1, 2
@@ -47,7 +48,7 @@ class IrkConfig(C.Structure):
         ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double),
         ("profile", C.c_int), ("use_graphs", C.c_int), ("initial_guess", C.c_int),
         ("basis", C.c_int), ("mg_shifted_sweeps", C.c_int), ("mg_coarse_reduction", C.c_double),
-        ("mg_coarse_smoother", C.c_int),
+        ("mg_coarse_smoother", C.c_int), ("dirk_sequential", C.c_int), ("dae_solver", C.c_int),
     ]
 
 
@@ -56,7 +57,7 @@ class IrkStats(C.Structure):
         ("steps", C.c_int), ("newton_its", C.c_int), ("krylov_its", C.c_int),
         ("prec_apps", C.c_int), ("vcycles", C.c_int), ("max_newton_its", C.c_int),
         ("final_rel_res", C.c_double), ("kernel_launches", C.c_longlong),
-        ("outer_its", C.c_int),
+        ("outer_its", C.c_int), ("poisson_vcycles", C.c_int),
     ]
 
     def as_dict(self):

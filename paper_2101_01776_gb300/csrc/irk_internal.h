@@ -29,6 +29,9 @@ struct HostTableau {
 };
 
 int build_tableau(int family, int s, int basis, HostTableau* t, char* err, size_t errlen);
+// The single-stage tableau A = [gamma], b = [1], c = [0] (one SDIRK stage
+// solved on its own); nonzero for gamma <= 0.
+int build_tableau_single(double gamma, HostTableau* t);
 
 // ---------------------------------------------------------------------------
 // Grid and operator description passed to every stencil kernel.
@@ -98,6 +101,7 @@ struct StageOpArgs {
   long long copy_len;
   const int* copy_jdev;  // optional: copy_dst += (*copy_jdev) * copy_ldv (device index)
   long long copy_ldv;
+  int vsf_omega_only;    // VSF: rows and terms hold omega alone (Picard omega block)
 };
 
 // Device-resident FGMRES(m) state of one block solve (Arnoldi/Givens data).
@@ -133,6 +137,7 @@ void launch_stage_states(const GridDesc& g, const StageStateArgs& a, cudaStream_
 int residual_blocks(const GridDesc& g);
 void launch_residual(const GridDesc& g, const ResidualArgs& a, cudaStream_t st);
 void launch_stage_op(const GridDesc& g, const StageOpArgs& a, cudaStream_t st);
+void launch_neg_laplacian(const GridDesc& g, const double* x, double* y, cudaStream_t st);
 // Burgers-2D coefficient fields of each combined field (ub, vb), formed once
 // per Newton iteration: dt ub/(2h), dt vb/(2h), dt Dx ub, dt Dy ub, dt Dx vb,
 // dt Dy vb (central differences); coef is ncombo * 6 * npts

@@ -32,13 +32,13 @@ namespace {
 enum ProfClass {
   P_STAGE = 0, P_RESID, P_STAGEOP, P_UPDATE, P_MG_SMOOTH, P_MG_RESID, P_MG_RESTRICT,
   P_MG_PROLONG, P_MG_COARSE, P_MG_CONVERT, P_MG_SETUP, P_GS_DOT, P_GS_UPDATE, P_REDUCE,
-  P_SCALE, P_LINCOMB, P_NORM, P_AXPBY, P_MEAN, P_MG_SMOOTH2, P_NCLASS
+  P_SCALE, P_LINCOMB, P_NORM, P_AXPBY, P_MEAN, P_MG_SMOOTH2, P_POISSON, P_NCLASS
 };
 const char* kProfNames[P_NCLASS] = {
   "stage_states", "residual", "stage_op", "stage_update", "mg_smooth", "mg_residual",
   "mg_restrict", "mg_prolong", "mg_coarse", "mg_convert", "mg_setup", "gs_multi_dot",
   "gs_update_dot", "reduce", "scale_copy", "lincomb", "norm2", "axpby", "remove_mean",
-  "mg_smooth_tile"};
+  "mg_smooth_tile", "poisson_op"};
 
 struct PendingEvent {
   int cls;
@@ -89,7 +89,7 @@ struct irk_handle {
   cudaGraphExec_t gexec[IRK_MAXS] = {};
   double graph_dt = 0.0;
   bool graphs_failed = false;
-  int graph_vcycles[IRK_MAXS] = {};
+  int graph_vcycles[IRK_MAXS] = {}, graph_pvcycles[IRK_MAXS] = {};
   long long graph_launches[IRK_MAXS] = {};
   // device-resident FGMRES: one graph per block = coupling + init + WHILE
   // (L_P, matvec, CGS2, Arnoldi) + solution update
@@ -99,7 +99,7 @@ struct irk_handle {
   double fg_dt = 0.0;
   bool fg_failed = false;
   long long fg_fixed_launches[IRK_MAXS] = {}, fg_body_launches[IRK_MAXS] = {};
-  int fg_body_vcycles[IRK_MAXS] = {};
+  int fg_body_vcycles[IRK_MAXS] = {}, fg_body_pvcycles[IRK_MAXS] = {};
   double fg_seen_its[IRK_MAXS] = {};
   // whole-step graph (Newton loop on the device)
   cudaStream_t st_aux2 = nullptr;
@@ -137,6 +137,14 @@ struct irk_handle {
   int ev_used = 0;
   std::vector<PendingEvent> pending;
   irk_kernel_stat prof[P_NCLASS];
+
+  // SDIRK solved stage by stage: a single-stage solver (A = [gamma]) whose
+  // arena lies in this handle's arena solves each stage equation in turn;
+  // inner_gamma > 0 marks such a single-stage solver
+  irk_handle* inner = nullptr;
+  void* inner_arena = nullptr;
+  size_t inner_bytes = 0;
+  double inner_gamma = 0.0;
 };
 
 // creation errors have no handle to live in; one per thread (serving creates handles concurrently)
@@ -706,6 +714,7 @@ bool vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     launch_mg_convert_out(prec, cur[0], out, n0, h->st);
   }
   h->stats.vcycles += 1;
+  if (row < 0 && kind == MG_DIFFUSION) h->stats.poisson_vcycles += 1;
   return epi_done;
 }
 
@@ -805,6 +814,7 @@ irk_status apply_prec(irk_handle* h, double dt, int blk) {
     if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec[blk], graph, 0);
     if (graph) cudaGraphDestroy(graph);
     h->graph_vcycles[blk] = h->stats.vcycles - saved.vcycles;
+    h->graph_pvcycles[blk] = h->stats.poisson_vcycles - saved.poisson_vcycles;
     h->graph_launches[blk] = h->stats.kernel_launches - saved.kernel_launches;
     h->stats = saved;
     if (e != cudaSuccess) {
@@ -816,6 +826,7 @@ irk_status apply_prec(irk_handle* h, double dt, int blk) {
   if (want && h->gexec[blk]) {
     CK(cudaGraphLaunch(h->gexec[blk], h->st));
     h->stats.vcycles += h->graph_vcycles[blk];
+    h->stats.poisson_vcycles += h->graph_pvcycles[blk];
     h->stats.kernel_launches += h->graph_launches[blk];
     return IRK_OK;
   }
@@ -1047,6 +1058,7 @@ irk_status collect_fg_counters(irk_handle* h) {
       h->stats.krylov_its += (int)d;
       h->stats.prec_apps += (int)d * h->tab.bsize[blk];
       h->stats.vcycles += (int)d * h->fg_body_vcycles[blk];
+      h->stats.poisson_vcycles += (int)d * h->fg_body_pvcycles[blk];
       h->stats.kernel_launches += d * h->fg_body_launches[blk];
     }
     h->fg_seen_its[blk] = its;
@@ -1075,7 +1087,7 @@ void drop_fg_graphs(irk_handle* h) {
 // (Arnoldi step of k_fg_gs2) after at most m iterations.
 struct CapCounts {
   long long fixed = 0, body = 0;
-  int vcycles = 0;
+  int vcycles = 0, pvcycles = 0;
 };
 
 cudaError_t capture_block_solve(irk_handle* h, double dt, int blk, cudaStream_t outer,
@@ -1140,7 +1152,7 @@ cudaError_t capture_block_solve(irk_handle* h, double dt, int blk, cudaStream_t 
   if (e == cudaSuccess) {
     h->st = inner;
     const long long l0 = h->stats.kernel_launches;
-    const int v0 = h->stats.vcycles;
+    const int v0 = h->stats.vcycles, pv0 = h->stats.poisson_vcycles;
     block_prec(h, dt, blk, h->prec_in, h->prec_out);
     {
       // w = D z_j with z_j = prec_out; Z_j = z_j (j read on the device)
@@ -1187,6 +1199,7 @@ cudaError_t capture_block_solve(irk_handle* h, double dt, int blk, cudaStream_t 
     }
     cc->body = h->stats.kernel_launches - l0;
     cc->vcycles = h->stats.vcycles - v0;
+    cc->pvcycles = h->stats.poisson_vcycles - pv0;
     h->st = outer;
     cudaGraph_t bout = nullptr;
     e = cudaStreamEndCapture(inner, &bout);
@@ -1229,6 +1242,7 @@ irk_status build_fg_graph(irk_handle* h, double dt, int blk) {
   h->fg_fixed_launches[blk] = cc.fixed;
   h->fg_body_launches[blk] = cc.body;
   h->fg_body_vcycles[blk] = cc.vcycles;
+  h->fg_body_pvcycles[blk] = cc.pvcycles;
   h->stats = saved;
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1370,6 +1384,7 @@ irk_status build_step_graph(irk_handle* h, double dt) {
     blocks_fixed += blkcc[blk].fixed;
     h->fg_body_launches[blk] = blkcc[blk].body;
     h->fg_body_vcycles[blk] = blkcc[blk].vcycles;
+    h->fg_body_pvcycles[blk] = blkcc[blk].pvcycles;
   }
   (void)blocks_fixed;
   h->step_fixed_launches = fixed;
@@ -1384,7 +1399,7 @@ irk_status build_step_graph(irk_handle* h, double dt) {
 // status, or IRK_ERR_INVALID when the graph cannot be used (caller falls back).
 irk_status graph_step(irk_handle* h, double dt) {
   if (!h->cfg.use_graphs || h->cfg.profile || h->cfg.forcing || h->step_failed || !h->st_aux ||
-      !h->st_aux2 || h->cfg.nonlinear_variant == 4)
+      !h->st_aux2 || h->cfg.nonlinear_variant == 4 || h->cfg.dae_solver == 1)
     return IRK_ERR_INVALID;
   if (!h->stepexec || h->step_dt != dt) {
     if (build_step_graph(h, dt) != IRK_OK) {
@@ -1411,6 +1426,7 @@ irk_status graph_step(irk_handle* h, double dt) {
       h->stats.krylov_its += (int)d;
       h->stats.prec_apps += (int)d * h->tab.bsize[blk];
       h->stats.vcycles += (int)d * h->fg_body_vcycles[blk];
+      h->stats.poisson_vcycles += (int)d * h->fg_body_pvcycles[blk];
       h->stats.kernel_launches += d * h->fg_body_launches[blk];
     }
     h->fg_seen_its[blk] = kits;
@@ -1455,7 +1471,181 @@ bool fg_device_solve(irk_handle* h, double dt, double eta) {
 
 // Block backward substitution of Algorithm 1 on h->rhs into h->yhat: the
 // device-resident FGMRES graphs when available, else the host-driven loop.
+// ---------------------------------------------------------------------------
+// Block forward solve of Eq. vsf-system-2 (VSF, dae_solver = 1).  With the
+// Picard linearization the advection acts on omega with the lagged stream
+// function only, so once one Schur block's unknowns are ordered (omega rows,
+// psi rows) its system is block lower triangular: the omega rows alone are
+// the eta/gamma* block system of Sec. 4 (solved by FGMRES with the omega
+// part of L_P to rtol), and each psi row is then the Poisson problem
+// dt (x_omega + L x_psi) = z_psi, i.e. (-L) x_psi = x_omega - z_psi / dt,
+// solved by FGMRES with the Poisson V-cycle to rtol.  Omega vectors of a
+// block are stored row after row, npts values each.
+
+// y = D x on the omega rows of block blk (Picard: no J_A(x_psi, wbar) term)
+void omega_block_matvec(irk_handle* h, double dt, int blk, const double* x, double* y,
+                        const double* copy_src, double* copy_dst) {
+  const int a0 = h->tab.bstart[blk], bs = h->tab.bsize[blk], s = h->s;
+  StageOpArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nrow = bs;
+  a.dt = dt;
+  a.vsf_omega_only = 1;
+  for (int rr = 0; rr < bs; ++rr) {
+    const int r = a0 + rr;
+    OpRow& row = a.row[rr];
+    row.y = y + (long long)rr * h->npts;
+    row.sigma = 1;
+    for (int qq = 0; qq < bs; ++qq) {
+      const int q = a0 + qq;
+      OpTerm& t = row.t[row.nterm++];
+      t.x = x + (long long)qq * h->npts;
+      set_combo(h, t, r, q);
+      t.m = h->tab.R[r * s + q];
+      t.lin = (r == q) ? 1.0 : 0.0;
+    }
+  }
+  a.copy_dst = copy_dst;
+  a.copy_src = copy_src;
+  a.copy_len = copy_dst ? (long long)bs * h->npts : 0;
+  run_stage_op(h, a);
+}
+
+// omega rows of z_blk = rhs_blk - sum_{l beyond blk} U_{r,l} yhat_l (the psi
+// rows of U vanish: M = diag(I, 0) and no linear term off the diagonal)
+void omega_upper_coupling(irk_handle* h, double dt, int blk, double* z) {
+  const int a0 = h->tab.bstart[blk], bs = h->tab.bsize[blk], s = h->s;
+  StageOpArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nrow = bs;
+  a.dt = dt;
+  a.vsf_omega_only = 1;
+  for (int rr = 0; rr < bs; ++rr) {
+    const int r = a0 + rr;
+    OpRow& row = a.row[rr];
+    row.y = z + (long long)rr * h->npts;
+    row.base = h->rhs + (long long)r * h->L;
+    row.alpha = 1;
+    row.sigma = -1;
+    for (int l = a0 + bs; l < s; ++l) {
+      OpTerm& t = row.t[row.nterm++];
+      t.x = h->yhat + (long long)l * h->L;
+      set_combo(h, t, r, l);
+      t.m = h->tab.R[r * s + l];
+      t.lin = 0;
+    }
+  }
+  run_stage_op(h, a);
+}
+
+// z = the omega part of L_P (Eq. Lprec) for block blk
+void omega_block_prec(irk_handle* h, double dt, int blk, const double* v, double* z) {
+  const int a = h->tab.bstart[blk], bs = h->tab.bsize[blk], s = h->s;
+  const double eta = h->tab.eta[blk];
+  const double cdiff = dt * h->g.nu;
+  vcycle(h, a, MG_ADVECTIVE, 1, eta, dt, cdiff, 0, v, z);
+  if (bs == 1) return;
+  const int b = a + 1;
+  const double gamma = (h->cfg.gamma_mode == 1) ? eta : h->tab.gamma_star[blk];
+  // r_b' = v_b - (coupling row (b, a)) z_a
+  StageOpArgs op;
+  memset(&op, 0, sizeof(op));
+  op.nrow = 1;
+  op.dt = dt;
+  op.vsf_omega_only = 1;
+  OpRow& row = op.row[0];
+  row.y = h->tmp;
+  row.base = v + h->npts;
+  row.alpha = 1;
+  row.sigma = -1;
+  row.nterm = 1;
+  row.t[0].x = z;
+  set_combo(h, row.t[0], b, a);
+  row.t[0].m = h->tab.R[b * s + a];
+  row.t[0].lin = 0;
+  run_stage_op(h, op);
+  vcycle(h, b, MG_ADVECTIVE, 1, gamma, dt, cdiff, 0, h->tmp, z + h->npts);
+}
+
+// x = (-L)^+ b by FGMRES with the Poisson V-cycle (b's mean removed first)
+irk_status poisson_fgmres(irk_handle* h, double* b, double* x, double rtol) {
+  const long long n = h->npts;
+  {
+    ProfScope ps(h, P_MEAN, 24.0 * n, 2.0 * n, 2);
+    launch_remove_mean(h->npts, 1, n, b, h->partials, h->st);
+  }
+  auto step = [&](int j) -> irk_status {
+    vcycle(h, -1, MG_DIFFUSION, 1, 0.0, 0.0, 1.0, 1, h->prec_in, h->prec_out);
+    {
+      ProfScope ps(h, P_POISSON, 16.0 * n, 6.0 * n);
+      launch_neg_laplacian(h->g, h->prec_out, h->w, h->st);
+    }
+    CK(cudaMemcpyAsync(h->Z + (long long)j * n, h->prec_out, sizeof(double) * n,
+                       cudaMemcpyDeviceToDevice, h->st));
+    return IRK_OK;
+  };
+  auto apply = [&](const double* xin, double* y) {
+    ProfScope ps(h, P_POISSON, 16.0 * n, 6.0 * n);
+    launch_neg_laplacian(h->g, xin, y, h->st);
+  };
+  auto counted = [&]() {};
+  int its = 0;
+  double rr = 0;
+  return fgmres_core(h, n, h->m, h->cfg.krylov_maxit, h->V, h->Z, h->w, h->prec_in, b, x, rtol,
+                     &its, &rr, step, apply, counted);
+}
+
+irk_status vsf_forward_solve(irk_handle* h, double dt, double rtol) {
+  const long long n = h->npts;
+  for (int blk = h->tab.nblk - 1; blk >= 0; --blk) {
+    const int a0 = h->tab.bstart[blk], bs = h->tab.bsize[blk];
+    // omega right-hand side and solution, row after row, in zbuf
+    double* zw = h->zbuf;
+    double* xw = h->zbuf + (long long)bs * n;
+    if (blk < h->tab.nblk - 1) {
+      omega_upper_coupling(h, dt, blk, zw);
+    } else {
+      for (int rr = 0; rr < bs; ++rr)
+        CK(cudaMemcpyAsync(zw + rr * n, h->rhs + (long long)(a0 + rr) * h->L, sizeof(double) * n,
+                           cudaMemcpyDeviceToDevice, h->st));
+    }
+    const long long Lb = (long long)bs * n;
+    auto step = [&](int j) -> irk_status {
+      omega_block_prec(h, dt, blk, h->prec_in, h->prec_out);
+      omega_block_matvec(h, dt, blk, h->prec_out, h->w, h->prec_out, h->Z + (long long)j * Lb);
+      return IRK_OK;
+    };
+    auto apply = [&](const double* xin, double* y) {
+      omega_block_matvec(h, dt, blk, xin, y, nullptr, nullptr);
+    };
+    auto counted = [&]() {
+      h->stats.krylov_its += 1;
+      h->stats.prec_apps += bs;
+    };
+    int its = 0;
+    double rr = 0;
+    TRY(fgmres_core(h, Lb, h->m, h->cfg.krylov_maxit, h->V, h->Z, h->w, h->prec_in, zw, xw, rtol,
+                    &its, &rr, step, apply, counted));
+    for (int q = 0; q < bs; ++q) {
+      double* yrow = h->yhat + (long long)(a0 + q) * h->L;
+      CK(cudaMemcpyAsync(yrow, xw + q * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+      // Poisson right-hand side x_omega - z_psi / dt
+      {
+        ProfScope ps(h, P_AXPBY, 40.0 * n, 3.0 * n, 2);
+        launch_axpby(h->tmp2, 1.0, xw + q * n, 0.0, n, h->st);
+        launch_axpby(h->tmp2, -1.0 / dt, h->rhs + (long long)(a0 + q) * h->L + n, 1.0, n, h->st);
+      }
+      TRY(poisson_fgmres(h, h->tmp2, yrow + n, rtol));
+    }
+  }
+  return IRK_OK;
+}
+
 irk_status solve_blocks(irk_handle* h, double dt, double rtol, bool* on_device) {
+  if (h->cfg.dae_solver == 1) {
+    *on_device = false;
+    return vsf_forward_solve(h, dt, rtol);
+  }
   *on_device = fg_device_solve(h, dt, rtol);
   if (*on_device) return IRK_OK;
   for (int blk = h->tab.nblk - 1; blk >= 0; --blk) {
@@ -1621,10 +1811,58 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
   return IRK_OK;
 }
 
+// One SDIRK step stage by stage: stage i is the single-stage problem
+// M k_i = N(u_n + dt sum_{j<i} a_ij k_j + dt gamma k_i, t_n + c_i dt), solved
+// by the stage solver (its own Newton loop, Algorithm 1 with one 1x1 block of
+// shift 1/gamma) from the base state written into its u; then
+// u_{n+1} = u_n + dt sum_i b_i k_i (Eq. update).
+irk_status sdirk_sequential_step(irk_handle* h, double t_n, double dt) {
+  irk_handle* in = h->inner;
+  const int s = h->s;
+  const size_t vb = sizeof(double) * h->L;
+  for (int i = 0; i < s; ++i) {
+    CK(cudaMemcpyAsync(in->u, h->u, vb, cudaMemcpyDeviceToDevice, h->st));
+    if (i > 0) {
+      ProfScope ps(h, P_UPDATE, 8.0 * h->L * (2 + i), 2.0 * h->L * i);
+      launch_u_update(h->L, i, h->tab.A + i * s, dt, h->K, in->u, h->st);
+    }
+    // Newton guess: this stage at the previous step (zero after a reset)
+    if (h->cfg.initial_guess == 1)
+      CK(cudaMemcpyAsync(in->K, h->K + (long long)i * h->L, vb, cudaMemcpyDeviceToDevice, h->st));
+    memset(&in->stats, 0, sizeof(in->stats));
+    irk_status st = graph_step(in, dt);
+    if (st == IRK_ERR_INVALID) st = newton_step(in, t_n + h->tab.c[i] * dt, dt);
+    h->stats.newton_its += in->stats.newton_its;
+    h->stats.max_newton_its = std::max(h->stats.max_newton_its, in->stats.max_newton_its);
+    h->stats.krylov_its += in->stats.krylov_its;
+    h->stats.prec_apps += in->stats.prec_apps;
+    h->stats.vcycles += in->stats.vcycles;
+    h->stats.poisson_vcycles += in->stats.poisson_vcycles;
+    h->stats.outer_its += in->stats.outer_its;
+    h->stats.kernel_launches += in->stats.kernel_launches;
+    h->stats.final_rel_res = std::max(i == 0 ? 0.0 : h->stats.final_rel_res, in->stats.final_rel_res);
+    if (st != IRK_OK) {
+      h->err = "SDIRK stage " + std::to_string(i) + ": " + in->err;
+      cudaMemsetAsync(in->K, 0, vb, h->st);
+      return st;
+    }
+    CK(cudaMemcpyAsync(h->K + (long long)i * h->L, in->K, vb, cudaMemcpyDeviceToDevice, h->st));
+  }
+  ProfScope ps(h, P_UPDATE, 8.0 * h->L * (2 + s), 2.0 * h->L * s);
+  launch_u_update(h->L, s, h->tab.b, dt, h->K, h->u, h->st);
+  return IRK_OK;
+}
+
 // ---------------------------------------------------------------------------
 irk_status validate(const irk_config* c, std::string& err) {
   if (!c) { err = "null config"; return IRK_ERR_INVALID; }
-  if (c->family < IRK_GAUSS || c->family > IRK_LOBATTO_IIIC) { err = "unknown family"; return IRK_ERR_INVALID; }
+  if (c->family < IRK_GAUSS || c->family > IRK_SDIRK) { err = "unknown family"; return IRK_ERR_INVALID; }
+  if (c->family == IRK_SDIRK && !(c->stages == 1 || c->stages == 2 || c->stages == 3 || c->stages == 5)) { err = "SDIRK stages must be 1, 2, 3 or 5"; return IRK_ERR_INVALID; }
+  if (c->family == IRK_SDIRK && c->stages > 1 && c->basis != IRK_BASIS_SCHUR) { err = "SDIRK has no eigenvector basis (one repeated eigenvalue): use the Schur basis"; return IRK_ERR_INVALID; }
+  if (c->dirk_sequential != 0 && c->dirk_sequential != 1) { err = "dirk_sequential must be 0 or 1"; return IRK_ERR_INVALID; }
+  if (c->dae_solver != 0 && c->dae_solver != 1) { err = "dae_solver must be 0 or 1"; return IRK_ERR_INVALID; }
+  if (c->dae_solver == 1 && c->op != IRK_OP_VSF_2D) { err = "dae_solver 1 is defined for the VSF operator"; return IRK_ERR_INVALID; }
+  if (c->dae_solver == 1 && c->nonlinear_variant == 4) { err = "dae_solver 1 solves the Picard system: nonlinear_variant 0..3"; return IRK_ERR_INVALID; }
   if (c->family == IRK_LOBATTO_IIIC && c->stages < 2) { err = "Lobatto IIIC needs stages >= 2"; return IRK_ERR_INVALID; }
   if (c->basis != IRK_BASIS_SCHUR && c->basis != IRK_BASIS_EIGEN) { err = "basis must be 0 (Schur) or 1 (eigenvectors)"; return IRK_ERR_INVALID; }
   if (c->stages < 1 || c->stages > IRK_MAXS) { err = "stages must be in 1..5"; return IRK_ERR_INVALID; }
@@ -1652,13 +1890,30 @@ irk_status validate(const irk_config* c, std::string& err) {
   return IRK_OK;
 }
 
+// Configuration of the single-stage solver of a stage-by-stage SDIRK handle:
+// the same operator, grid and solver settings with one stage (its tableau,
+// A = [gamma], replaces the family's).
+irk_config stage_solver_config(const irk_config& c) {
+  irk_config ic = c;
+  ic.family = IRK_SDIRK;
+  ic.stages = 1;
+  ic.basis = IRK_BASIS_SCHUR;
+  ic.dirk_sequential = 0;
+  return ic;
+}
+
 // Plan the solver for h->cfg (tableau, grid, combined fields, MG levels,
 // arena size); unless plan_only, then place the arena (the caller's when
 // h->ext_arena is set, else one cudaMalloc), carve it and load u0.
 irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_only = false) {
   const irk_config& c = h->cfg;
   char ebuf[256] = {0};
-  if (build_tableau(c.family, c.stages, c.basis, &h->tab, ebuf, sizeof ebuf)) { h->err = ebuf; return IRK_ERR_INVALID; }
+  if (h->inner_gamma > 0) {
+    if (build_tableau_single(h->inner_gamma, &h->tab)) { h->err = "single-stage gamma must be positive"; return IRK_ERR_INVALID; }
+  } else if (build_tableau(c.family, c.stages, c.basis, &h->tab, ebuf, sizeof ebuf)) {
+    h->err = ebuf;
+    return IRK_ERR_INVALID;
+  }
   const int s = h->s = c.stages;
   h->dim = (c.op == IRK_OP_BURGERS_2D || c.op == IRK_OP_VSF_2D) ? 2 : 1;
   h->C = (h->dim == 2) ? 2 : 1;
@@ -1794,6 +2049,16 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
       for (int k = 0; k < s; ++k) add(f * 4);
   }
   h->arena_bytes = bytes + 4096;
+  // stage-by-stage SDIRK: the single-stage solver's arena follows this one's
+  h->inner_bytes = 0;
+  if (c.family == IRK_SDIRK && c.dirk_sequential == 1 && s > 1 && h->inner_gamma == 0) {
+    irk_handle plan;
+    plan.cfg = stage_solver_config(c);
+    plan.inner_gamma = h->tab.A[0];
+    TRY(build(&plan, nullptr, 0, true));
+    h->inner_bytes = plan.arena_bytes;
+    h->arena_bytes += h->inner_bytes + 256;
+  }
   if (plan_only) return IRK_OK;
   if (h->ext_arena) {
     if (h->ext_bytes < h->arena_bytes) {
@@ -1855,7 +2120,8 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   }
   for (int k = s; k < IRK_MAXS; ++k)
     for (int l = 0; l < IRK_MAX_LEVELS; ++l) h->vel[k][l] = nullptr;
-  if (!h->dscal) { h->err = "arena layout overflow"; return IRK_ERR_NOMEM; }
+  h->inner_arena = h->inner_bytes ? take(h->inner_bytes) : nullptr;
+  if (!h->dscal || (h->inner_bytes && !h->inner_arena)) { h->err = "arena layout overflow"; return IRK_ERR_NOMEM; }
   CK(cudaMemsetAsync(h->arena, 0, h->arena_used, h->st));
   CK(cudaMallocHost((void**)&h->hbuf, 4096));
   if (h->pinv) {
@@ -1926,6 +2192,7 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
     }
     h->prec = save_prec;
     h->stats.vcycles = 0;
+    h->stats.poisson_vcycles = 0;
   }
   CK(cudaStreamSynchronize(h->st));
   return IRK_OK;
@@ -1967,6 +2234,8 @@ void irk_config_default(irk_config* c) {
   c->profile = 0;
   c->use_graphs = 1;
   c->initial_guess = 1;
+  c->dirk_sequential = 1;
+  c->dae_solver = 0;
 }
 
 const char* irk_status_string(irk_status st) {
@@ -2022,7 +2291,7 @@ irk_status irk_transform(int family, int s, int basis, double* T, double* Tinv, 
 
 static irk_status create_impl(const irk_config* cfg, const double* u0, int u0_on_device,
                               void* cuda_stream, void* arena, size_t arena_bytes,
-                              irk_handle** out) {
+                              irk_handle** out, double inner_gamma = 0.0) {
   if (!out) { g_create_error = "null output handle"; return IRK_ERR_INVALID; }
   *out = nullptr;
   std::string verr;
@@ -2040,6 +2309,7 @@ static irk_status create_impl(const irk_config* cfg, const double* u0, int u0_on
   h->cfg = *cfg;
   h->ext_arena = arena;
   h->ext_bytes = arena_bytes;
+  h->inner_gamma = inner_gamma;
   memset(&h->stats, 0, sizeof(h->stats));
   cudaGetDevice(&h->device);
   if (cuda_stream) {
@@ -2065,6 +2335,17 @@ static irk_status create_impl(const irk_config* cfg, const double* u0, int u0_on
     g_create_error = h->err;
     irk_destroy(h);
     return st;
+  }
+  if (h->inner_arena) {
+    // the stage solver shares the stream and lives in this handle's arena
+    const irk_config ic = stage_solver_config(h->cfg);
+    st = create_impl(&ic, h->u, 1, (void*)h->st, h->inner_arena, h->inner_bytes, &h->inner,
+                     h->tab.A[0]);
+    if (st != IRK_OK) {
+      g_create_error = "stage solver: " + g_create_error;
+      irk_destroy(h);
+      return st;
+    }
   }
   *out = h;
   return IRK_OK;
@@ -2107,8 +2388,12 @@ irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats*
     cudaError_t e = cudaMemcpyAsync(h->u_save, h->u, sizeof(double) * h->L,
                                     cudaMemcpyDeviceToDevice, h->st);
     if (e != cudaSuccess) { h->err = cudaGetErrorString(e); st = IRK_ERR_CUDA; break; }
-    st = graph_step(h, dt);
-    if (st == IRK_ERR_INVALID) st = newton_step(h, t, dt);  // host-driven loop
+    if (h->inner) {
+      st = sdirk_sequential_step(h, t, dt);
+    } else {
+      st = graph_step(h, dt);
+      if (st == IRK_ERR_INVALID) st = newton_step(h, t, dt);  // host-driven loop
+    }
     if (st != IRK_OK) {
       cudaMemcpyAsync(h->u, h->u_save, sizeof(double) * h->L, cudaMemcpyDeviceToDevice, h->st);
       cudaMemsetAsync(h->K, 0, sizeof(double) * h->L * h->s, h->st);  // discard the failed iterate
@@ -2124,6 +2409,7 @@ irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats*
     if (e != cudaSuccess) { h->err = cudaGetErrorString(e); st = IRK_ERR_CUDA; }
   }
   prof_harvest(h);
+  if (h->inner) prof_harvest(h->inner);
   if (stats) *stats = h->stats;
   return st;
 }
@@ -2258,6 +2544,13 @@ irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_con
   // step first: it captures the graphs), or +inf when a step fails
   auto measure = [&](double* ms) -> irk_status {
     invalidate_graphs(h);
+    if (h->inner) {
+      // the stage solver of a stage-by-stage SDIRK handle runs the V-cycles
+      h->inner->cfg.mg_shifted_sweeps = h->cfg.mg_shifted_sweeps;
+      h->inner->cfg.mg_coarse_smoother = h->cfg.mg_coarse_smoother;
+      h->inner->cfg.mg_coarse_reduction = h->cfg.mg_coarse_reduction;
+      invalidate_graphs(h->inner);
+    }
     TRY(restore());
     *ms = INFINITY;
     if (irk_step(h, t_n, dt, 1, nullptr) != IRK_OK) return IRK_OK;
@@ -2314,9 +2607,19 @@ irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_con
 irk_status irk_kernel_stats(irk_handle* h, irk_kernel_stat* out, int max, int* count) {
   if (!h || !out || !count) return IRK_ERR_INVALID;
   prof_harvest(h);
+  if (h->inner) prof_harvest(h->inner);
   int n = 0;
-  for (int k = 0; k < P_NCLASS && n < max; ++k)
-    if (h->prof[k].launches > 0) out[n++] = h->prof[k];
+  for (int k = 0; k < P_NCLASS && n < max; ++k) {
+    irk_kernel_stat ks = h->prof[k];
+    if (h->inner) {  // the stage solver's launches of the same class
+      const irk_kernel_stat& q = h->inner->prof[k];
+      ks.launches += q.launches;
+      ks.ms += q.ms;
+      ks.bytes += q.bytes;
+      ks.flops += q.flops;
+    }
+    if (ks.launches > 0) out[n++] = ks;
+  }
   *count = n;
   return IRK_OK;
 }
@@ -2328,6 +2631,7 @@ irk_status irk_reset_kernel_stats(irk_handle* h) {
     h->prof[k].launches = 0;
     h->prof[k].ms = h->prof[k].bytes = h->prof[k].flops = 0;
   }
+  if (h->inner) irk_reset_kernel_stats(h->inner);
   return IRK_OK;
 }
 
@@ -2340,6 +2644,7 @@ const char* irk_last_error(const irk_handle* h) {
 
 void irk_destroy(irk_handle* h) {
   if (!h) return;
+  if (h->inner) irk_destroy(h->inner);
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& ev : h->evpool) cudaEventDestroy(ev);
   if (h->hbuf) cudaFreeHost(h->hbuf);

@@ -388,7 +388,10 @@ void launch_residual(const GridDesc& g, const ResidualArgs& a, cudaStream_t st) 
 // ---------------------------------------------------------------------------
 // One term of the row operator at point p, accumulated into acc[c]:
 //   m M x - dt (Jadv(Ybar) x + lin Jlin x)
-template <int OP>
+// WONLY (VSF only): x, y and base hold the vorticity alone (the stream
+// function parts are absent): the J_A(x_psi, wbar) coupling and the psi row
+// are dropped, which is the omega block of the Picard system Eq. vsf-system-2.
+template <int OP, bool WONLY = false>
 __device__ __forceinline__ void term_apply(const GridDesc& g, const OpTerm& t, const Nbr& nb,
                                            double dt, double acc[2]) {
   const int npts = g.npts;
@@ -491,7 +494,7 @@ __device__ __forceinline__ void term_apply(const GridDesc& g, const OpTerm& t, c
   } else if (t.coef) {  // VSF with the combined field's Arakawa weights precomputed
     double xw9[3][3], xp9[3][3];
     load9(t.x, nb, xw9);
-    load9(t.x + npts, nb, xp9);
+    if (!WONLY) load9(t.x + npts, nb, xp9);
     const double* f = t.coef + nb.c;
     const long long st = npts;
     // -dt (J_A(psibar, xw) + J_A(xp, wbar)) in 16 FMAs, order E, W, N, S, NE, NW, SE, SW
@@ -503,54 +506,64 @@ __device__ __forceinline__ void term_apply(const GridDesc& g, const OpTerm& t, c
     op = fma(__ldg(f + 5 * st), xw9[2][0], op);
     op = fma(__ldg(f + 6 * st), xw9[0][2], op);
     op = fma(__ldg(f + 7 * st), xw9[0][0], op);
-    op = fma(__ldg(f + 8 * st), xp9[1][2], op);
-    op = fma(__ldg(f + 9 * st), xp9[1][0], op);
-    op = fma(__ldg(f + 10 * st), xp9[2][1], op);
-    op = fma(__ldg(f + 11 * st), xp9[0][1], op);
-    op = fma(__ldg(f + 12 * st), xp9[2][2], op);
-    op = fma(__ldg(f + 13 * st), xp9[2][0], op);
-    op = fma(__ldg(f + 14 * st), xp9[0][2], op);
-    op = fma(__ldg(f + 15 * st), xp9[0][0], op);
+    if (!WONLY) {
+      op = fma(__ldg(f + 8 * st), xp9[1][2], op);
+      op = fma(__ldg(f + 9 * st), xp9[1][0], op);
+      op = fma(__ldg(f + 10 * st), xp9[2][1], op);
+      op = fma(__ldg(f + 11 * st), xp9[0][1], op);
+      op = fma(__ldg(f + 12 * st), xp9[2][2], op);
+      op = fma(__ldg(f + 13 * st), xp9[2][0], op);
+      op = fma(__ldg(f + 14 * st), xp9[0][2], op);
+      op = fma(__ldg(f + 15 * st), xp9[0][0], op);
+    }
     double opp = 0.0;
     if (t.lin != 0.0) {
       const double lw = (xw9[1][2] + xw9[1][0] + xw9[2][1] + xw9[0][1] - 4.0 * xw9[1][1]) * g.invh2;
-      const double lp = (xp9[1][2] + xp9[1][0] + xp9[2][1] + xp9[0][1] - 4.0 * xp9[1][1]) * g.invh2;
       op = fma(-dt * t.lin * g.nu, lw, op);
-      opp = t.lin * (-xw9[1][1] - lp);
+      if (!WONLY) {
+        const double lp = (xp9[1][2] + xp9[1][0] + xp9[2][1] + xp9[0][1] - 4.0 * xp9[1][1]) * g.invh2;
+        opp = t.lin * (-xw9[1][1] - lp);
+      }
     }
     acc[0] += t.m * xw9[1][1] + op;
-    acc[1] += -dt * opp;
+    if (!WONLY) acc[1] += -dt * opp;
   } else {  // VSF: state (w, psi), M = diag(1, 0)
     double xw9[3][3], xp9[3][3];
     load9(t.x, nb, xw9);
-    load9(t.x + npts, nb, xp9);
+    if (!WONLY) load9(t.x + npts, nb, xp9);
     double opw = 0.0, opp = 0.0;
     if (t.combo) {
       double bw9[3][3], bp9[3][3];
-      load9(t.combo, nb, bw9);
       load9(t.combo + npts, nb, bp9);
-      opw = (arakawa12(bp9, xw9) + arakawa12(xp9, bw9)) * g.inv12h2;
+      if (WONLY) {
+        opw = arakawa12(bp9, xw9) * g.inv12h2;
+      } else {
+        load9(t.combo, nb, bw9);
+        opw = (arakawa12(bp9, xw9) + arakawa12(xp9, bw9)) * g.inv12h2;
+      }
     }
     if (t.lin != 0.0) {
       const double lw = (xw9[1][2] + xw9[1][0] + xw9[2][1] + xw9[0][1] - 4.0 * xw9[1][1]) * g.invh2;
-      const double lp = (xp9[1][2] + xp9[1][0] + xp9[2][1] + xp9[0][1] - 4.0 * xp9[1][1]) * g.invh2;
       opw = fma(t.lin * g.nu, lw, opw);
-      opp = t.lin * (-xw9[1][1] - lp);
+      if (!WONLY) {
+        const double lp = (xp9[1][2] + xp9[1][0] + xp9[2][1] + xp9[0][1] - 4.0 * xp9[1][1]) * g.invh2;
+        opp = t.lin * (-xw9[1][1] - lp);
+      }
     }
     acc[0] += t.m * xw9[1][1] - dt * opw;
-    acc[1] += -dt * opp;
+    if (!WONLY) acc[1] += -dt * opp;
   }
 }
 
-template <int OP>
+template <int OP, bool WONLY = false>
 __global__ void __launch_bounds__(256) k_stage_op(GridDesc g, StageOpArgs a) {
-  constexpr int C = (OP == IRK_OP_BURGERS_2D || OP == IRK_OP_VSF_2D) ? 2 : 1;
+  constexpr int C = WONLY ? 1 : (OP == IRK_OP_BURGERS_2D || OP == IRK_OP_VSF_2D) ? 2 : 1;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npts; p += gridDim.x * blockDim.x) {
     const Nbr nb = neighbours(g, p);
     for (int r = 0; r < a.nrow; ++r) {
       const OpRow& row = a.row[r];
       double acc[2] = {0.0, 0.0};
-      for (int k = 0; k < row.nterm; ++k) term_apply<OP>(g, row.t[k], nb, a.dt, acc);
+      for (int k = 0; k < row.nterm; ++k) term_apply<OP, WONLY>(g, row.t[k], nb, a.dt, acc);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         const long long idx = (long long)c * g.npts + p;
@@ -663,8 +676,28 @@ void launch_stage_op(const GridDesc& g, const StageOpArgs& a_in, cudaStream_t st
     case IRK_OP_DIFFUSION_1D: k_stage_op<IRK_OP_DIFFUSION_1D><<<blocks, 256, 0, st>>>(g, a); break;
     case IRK_OP_BURGERS_1D: k_stage_op<IRK_OP_BURGERS_1D><<<blocks, 256, 0, st>>>(g, a); break;
     case IRK_OP_BURGERS_2D: k_stage_op<IRK_OP_BURGERS_2D><<<blocks, 256, 0, st>>>(g, a); break;
-    case IRK_OP_VSF_2D: k_stage_op<IRK_OP_VSF_2D><<<blocks, 256, 0, st>>>(g, a); break;
+    case IRK_OP_VSF_2D:
+      if (a.vsf_omega_only) k_stage_op<IRK_OP_VSF_2D, true><<<blocks, 256, 0, st>>>(g, a);
+      else k_stage_op<IRK_OP_VSF_2D><<<blocks, 256, 0, st>>>(g, a);
+      break;
   }
+}
+
+// y = -L_h x (5-point, periodic, 2D): the stream function rows of Eq.
+// vsf-system-2 divided by -dt, for the Poisson FGMRES of the forward solve.
+__global__ void __launch_bounds__(256) k_neg_laplacian_2d(GridDesc g, const double* __restrict__ x,
+                                                          double* __restrict__ y) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npts; p += gridDim.x * blockDim.x) {
+    const Nbr nb = neighbours(g, p);
+    y[p] = (4.0 * __ldg(x + nb.c) - __ldg(x + nb.e) - __ldg(x + nb.w) - __ldg(x + nb.n) -
+            __ldg(x + nb.s)) * g.invh2;
+  }
+}
+
+void launch_neg_laplacian(const GridDesc& g, const double* x, double* y, cudaStream_t st) {
+  int blocks = (g.npts + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_neg_laplacian_2d<<<blocks, 256, 0, st>>>(g, x, y);
 }
 
 // ---------------------------------------------------------------------------

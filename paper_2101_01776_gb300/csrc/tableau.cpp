@@ -21,6 +21,16 @@
 // imaginary parts of the eigenvectors and R block diagonal, [[eta, beta],
 // [-beta, eta]] per pair (the phi = beta case of the standardized block).
 // Algorithm 1 then needs T^{-1} in place of Q0^T and has no R0 coupling.
+//
+// SDIRK (the diagonally implicit methods of the comparisons in Sec. 7):
+// lower triangular A with one diagonal value gamma, stiffly accurate (b =
+// last row), L-stable: s = 1 backward Euler, s = 2 gamma = 1 - sqrt(1/2),
+// s = 3 Alexander's method (c_2 = (1 + gamma)/2, b from B(3), gamma from the
+// remaining order-3 condition), s = 5 the order-4 method of Hairer and
+// Wanner (gamma = 1/4).  A0^{-1} is lower triangular with the one eigenvalue
+// 1/gamma (not diagonalizable for s > 1), so its real Schur form is exact:
+// Q0 = the reversal permutation J, R0 = J A0^{-1} J upper triangular, every
+// block 1x1 with eta = 1/gamma, and every off-diagonal d-vector is zero.
 // Everything runs in long double.
 #include "irk_internal.h"
 
@@ -380,8 +390,158 @@ static bool eigen_basis(int s, const std::vector<ld>& Ainv, const std::vector<Ei
   return true;
 }
 
+// A of the SDIRK method with s stages (row-major); false for other s.
+static bool sdirk_matrix(int s, std::vector<ld>& A) {
+  A.assign(s * s, 0);
+  if (s == 1) {
+    A[0] = 1;
+    return true;
+  }
+  if (s == 2) {
+    // stiffly accurate: b = (1 - g, g), c = (g, 1); order 2 needs b.c = 1/2,
+    // i.e. g^2 - 2g + 1/2 = 0, and the root below 1 is L-stable
+    const ld g = 1 - std::sqrt((ld)0.5);
+    A[0] = g;
+    A[2] = 1 - g;
+    A[3] = g;
+    return true;
+  }
+  if (s == 3) {
+    // c = (g, (1 + g)/2, 1); b solves sum_j b_j c_j^q = 1/(q+1), q = 0..2;
+    // g is the root in (0.3, 0.5) of b^T A c = 1/6 (bisection)
+    auto fill = [&](ld g, std::vector<ld>& M) -> bool {
+      const ld c2 = (1 + g) / 2;
+      std::vector<ld> V = {1, 1, 1, g, c2, 1, g * g, c2 * c2, 1};
+      std::vector<ld> b = {1, (ld)0.5, (ld)1 / 3};
+      if (!solve_ld(3, V, b)) return false;
+      M.assign(9, 0);
+      M[0] = g;
+      M[3] = c2 - g;
+      M[4] = g;
+      M[6] = b[0];
+      M[7] = b[1];
+      M[8] = g;
+      return true;
+    };
+    auto cond = [&](ld g) -> ld {
+      std::vector<ld> M;
+      if (!fill(g, M)) return 0;
+      const ld c[3] = {g, (1 + g) / 2, 1};
+      ld acc = 0;
+      for (int i = 0; i < 3; ++i) {
+        ld ac = 0;
+        for (int j = 0; j < 3; ++j) ac += M[i * 3 + j] * c[j];
+        acc += M[6 + i] * ac;
+      }
+      return acc - (ld)1 / 6;
+    };
+    ld lo = (ld)0.3, hi = (ld)0.5;
+    const bool neg_lo = cond(lo) < 0;
+    for (int it = 0; it < 200; ++it) {
+      const ld mid = (lo + hi) / 2;
+      if ((cond(mid) < 0) == neg_lo) lo = mid; else hi = mid;
+    }
+    return fill((lo + hi) / 2, A);
+  }
+  if (s == 5) {
+    static const ld tab[5][5] = {
+        {(ld)1 / 4, 0, 0, 0, 0},
+        {(ld)1 / 2, (ld)1 / 4, 0, 0, 0},
+        {(ld)17 / 50, (ld)-1 / 25, (ld)1 / 4, 0, 0},
+        {(ld)371 / 1360, (ld)-137 / 2720, (ld)15 / 544, (ld)1 / 4, 0},
+        {(ld)25 / 24, (ld)-49 / 48, (ld)125 / 16, (ld)-85 / 12, (ld)1 / 4}};
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) A[i * 5 + j] = tab[i][j];
+    return true;
+  }
+  return false;
+}
+
+// Store A, b, c, A0^{-1}, T, T^{-1}, R and T R; false (with err) when the
+// factorization does not reproduce A0^{-1}.
+static bool store_tableau(int s, const std::vector<ld>& A, const std::vector<ld>& b,
+                          const std::vector<ld>& c, const std::vector<ld>& Ainv,
+                          const std::vector<ld>& Q, const std::vector<ld>& R,
+                          const std::vector<ld>& Qinv, HostTableau* t, char* err, size_t errlen) {
+  ld errmax = 0;
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) {
+      ld acc = 0;
+      for (int a = 0; a < s; ++a)
+        for (int bb = 0; bb < s; ++bb) acc += Q[i * s + a] * R[a * s + bb] * Qinv[bb * s + j];
+      errmax = std::max(errmax, std::fabs(acc - Ainv[i * s + j]));
+    }
+  if (errmax > 1e-12L) { snprintf(err, errlen, "A0^{-1} reconstruction error %.3Le", errmax); return false; }
+  for (int i = 0; i < s; ++i) {
+    t->b[i] = (double)b[i];
+    t->c[i] = (double)c[i];
+    for (int j = 0; j < s; ++j) {
+      t->A[i * s + j] = (double)A[i * s + j];
+      t->Ainv[i * s + j] = (double)Ainv[i * s + j];
+      t->T[i * s + j] = (double)Q[i * s + j];
+      t->Tinv[i * s + j] = (double)Qinv[i * s + j];
+      t->R[i * s + j] = (double)R[i * s + j];
+    }
+  }
+  // T R, the back-transform of Algorithm 1 (Q0 R0 in the Schur basis)
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) {
+      ld acc = 0;
+      for (int a = 0; a < s; ++a) acc += Q[i * s + a] * R[a * s + j];
+      t->TR[i * s + j] = (double)acc;
+    }
+  return true;
+}
+
+static int build_sdirk(int s, int basis, HostTableau* t, char* err, size_t errlen) {
+  std::vector<ld> A;
+  if (!sdirk_matrix(s, A)) { snprintf(err, errlen, "SDIRK stages must be 1, 2, 3 or 5"); return 1; }
+  if (basis == 1 && s > 1) {
+    snprintf(err, errlen, "SDIRK's A0^{-1} has one repeated eigenvalue and no eigenvector basis; use the Schur basis");
+    return 1;
+  }
+  std::vector<ld> b(s), c(s, 0), Ainv;
+  for (int i = 0; i < s; ++i) {
+    b[i] = A[(s - 1) * s + i];
+    for (int j = 0; j < s; ++j) c[i] += A[i * s + j];
+  }
+  if (!invert_ld(s, A, Ainv)) { snprintf(err, errlen, "A0 is singular"); return 1; }
+  std::vector<ld> Q(s * s, 0), R(s * s, 0);
+  for (int i = 0; i < s; ++i) Q[i * s + (s - 1 - i)] = 1;
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) R[i * s + j] = (i <= j) ? Ainv[(s - 1 - i) * s + (s - 1 - j)] : 0;
+  t->nblk = s;
+  for (int k = 0; k < s; ++k) {
+    t->bstart[k] = k;
+    t->bsize[k] = 1;
+    t->eta[k] = (double)R[k * s + k];
+    t->beta2[k] = 0;
+    t->gamma_star[k] = t->eta[k];
+  }
+  return store_tableau(s, A, b, c, Ainv, Q, R, Q, t, err, errlen) ? 0 : 1;
+}
+
+int build_tableau_single(double gamma, HostTableau* t) {
+  if (!(gamma > 0)) return 1;
+  memset(t, 0, sizeof(*t));
+  t->s = 1;
+  t->A[0] = gamma;
+  t->b[0] = 1;
+  t->c[0] = 0;
+  t->Ainv[0] = 1 / (ld)gamma;
+  t->T[0] = t->Tinv[0] = 1;
+  t->R[0] = t->TR[0] = t->Ainv[0];
+  t->nblk = 1;
+  t->bstart[0] = 0;
+  t->bsize[0] = 1;
+  t->eta[0] = t->gamma_star[0] = t->R[0];
+  t->beta2[0] = 0;
+  return 0;
+}
+
 int build_tableau(int family, int s, int basis, HostTableau* t, char* err, size_t errlen) {
-  if (family != IRK_GAUSS && family != IRK_RADAU_IIA && family != IRK_LOBATTO_IIIC) {
+  if (family != IRK_GAUSS && family != IRK_RADAU_IIA && family != IRK_LOBATTO_IIIC &&
+      family != IRK_SDIRK) {
     snprintf(err, errlen, "unknown family %d", family);
     return 1;
   }
@@ -390,6 +550,7 @@ int build_tableau(int family, int s, int basis, HostTableau* t, char* err, size_
   if (family == IRK_LOBATTO_IIIC && s < 2) { snprintf(err, errlen, "Lobatto IIIC needs s >= 2"); return 1; }
   memset(t, 0, sizeof(*t));
   t->s = s;
+  if (family == IRK_SDIRK) return build_sdirk(s, basis, t, err, errlen);
   std::vector<ld> c;
   if (!family_nodes(family, s, c)) { snprintf(err, errlen, "abscissae not real"); return 1; }
   std::vector<ld> V(s * s);
@@ -537,35 +698,8 @@ int build_tableau(int family, int s, int basis, HostTableau* t, char* err, size_
     for (int i = 0; i < s; ++i)
       for (int j = 0; j < s; ++j) Qinv[i * s + j] = Q[j * s + i];
   }
-  // residual check: T R T^{-1} == A0^{-1}
-  ld errmax = 0;
-  for (int i = 0; i < s; ++i)
-    for (int j = 0; j < s; ++j) {
-      ld acc = 0;
-      for (int a = 0; a < s; ++a)
-        for (int bb = 0; bb < s; ++bb) acc += Q[i * s + a] * R[a * s + bb] * Qinv[bb * s + j];
-      errmax = std::max(errmax, std::fabs(acc - Ainv[i * s + j]));
-    }
-  if (errmax > 1e-12L) { snprintf(err, errlen, "A0^{-1} reconstruction error %.3Le", errmax); return 1; }
-  for (int i = 0; i < s; ++i) {
-    t->b[i] = (double)b[i];
-    t->c[i] = (double)c[i];
-    for (int j = 0; j < s; ++j) {
-      t->A[i * s + j] = (double)A[i * s + j];
-      t->Ainv[i * s + j] = (double)Ainv[i * s + j];
-      t->T[i * s + j] = (double)Q[i * s + j];
-      t->Tinv[i * s + j] = (double)Qinv[i * s + j];
-      t->R[i * s + j] = (double)R[i * s + j];
-    }
-  }
-  // T R, the back-transform of Algorithm 1 (Q0 R0 in the Schur basis)
-  for (int i = 0; i < s; ++i)
-    for (int j = 0; j < s; ++j) {
-      ld acc = 0;
-      for (int a = 0; a < s; ++a) acc += Q[i * s + a] * R[a * s + j];
-      t->TR[i * s + j] = (double)acc;
-    }
-  return 0;
+  // residual check T R T^{-1} == A0^{-1}, then store
+  return store_tableau(s, A, b, c, Ainv, Q, R, Qinv, t, err, errlen) ? 0 : 1;
 }
 
 }  // namespace irk

@@ -107,7 +107,9 @@ def test_host_eigen_basis_matches_oracle(B, family, fid, s):
 
 
 def test_transform_rejects_bad_arguments(B):
-    for args in [(2, 0, 2), (2, 3, 0), (0, 0, 0), (6, 0, 0), (1, 2, 0)]:
+    # (s, family, basis): bad basis, unknown family, s out of range, Lobatto s=1,
+    # SDIRK without its 4-stage method, SDIRK in an eigenvector basis
+    for args in [(2, 0, 2), (2, 4, 0), (0, 0, 0), (6, 0, 0), (1, 2, 0), (4, 3, 0), (2, 3, 1)]:
         with pytest.raises(B.IrkError):
             B.irk_transform(*args)
 
@@ -130,7 +132,9 @@ def test_device_bytes_is_host_only_and_grows_with_the_problem(B):
 def test_invalid_configs_rejected_before_device(B):
     u0 = np.zeros(256)
     bad = [dict(stages=0), dict(stages=6), dict(n=100), dict(nu=0.0), dict(nu=-1.0),
-           dict(op="vsf", mass=0), dict(op="burgers1d", mass=1), dict(family=3),
+           dict(op="vsf", mass=0), dict(op="burgers1d", mass=1), dict(family=4),
+           dict(family=3, stages=4), dict(family=3, stages=2, basis=1), dict(dirk_sequential=2),
+           dict(dae_solver=2), dict(dae_solver=1), dict(dae_solver=-1),
            dict(family=-1), dict(family=2, stages=1), dict(basis=2), dict(basis=-1),
            dict(krylov_restart=0), dict(krylov_restart=65), dict(nonlinear_variant=5),
            dict(nonlinear_variant=-1), dict(mg_precision=3), dict(forcing=1, op="burgers2d"),
@@ -151,3 +155,35 @@ def test_no_device_reported_cleanly(B):
     with pytest.raises(B.IrkError) as ei:
         B.irk_create(cfg, np.zeros(256))
     assert ei.value.status == B.IRK_ERR_NO_DEVICE
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 5])
+def test_sdirk_tableau_and_exact_schur_form(B, s):
+    """The library's SDIRK tableau (derived from the order conditions) equals
+    the oracle's closed forms; its transform is the reversal permutation with
+    R0 = J A0^{-1} J upper triangular, every block 1x1 with eta = 1/gamma."""
+    from oracle import tableau as tab
+    t = B.irk_tableau(s, B.IRK_SDIRK)
+    A, b, c = tab.sdirk(s)
+    # the oracle's 3-stage gamma is a double-precision polynomial root (a few
+    # ulps); the library bisects the order-3 condition in long double
+    np.testing.assert_allclose(t["A"], A, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(t["b"], b, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(t["c"], c, rtol=0, atol=1e-14)
+    J = np.eye(s)[::-1]
+    np.testing.assert_array_equal(t["Q0"], J)
+    np.testing.assert_allclose(t["R0"], J @ np.linalg.inv(A) @ J, rtol=1e-14, atol=1e-13)
+    assert list(t["block_sizes"]) == [1] * s
+    q = B.irk_transform(s, B.IRK_SDIRK, B.IRK_BASIS_SCHUR)
+    np.testing.assert_array_equal(q["Tinv"], J)
+
+
+def test_sdirk_stage_by_stage_arena_holds_the_stage_solver(B):
+    """A stage-by-stage SDIRK handle carves a single-stage solver out of its
+    own arena; the coupled form needs no such second solver."""
+    seq = B.irk_config_default(op="burgers2d", n=64, family="sdirk", stages=3)
+    coupled = B.irk_config_default(op="burgers2d", n=64, family="sdirk", stages=3, dirk_sequential=0)
+    one = B.irk_config_default(op="burgers2d", n=64, family="sdirk", stages=1)
+    a, b, c = (B.irk_config_device_bytes(x) for x in (seq, coupled, one))
+    assert 0 < c < b < a
+    assert a >= b + c - 4096

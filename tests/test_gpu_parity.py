@@ -255,6 +255,93 @@ def test_linear_diffusion_pade_radau_lobatto(B, family, s, k):
     assert rel(u1[0], want) <= 1e-9
 
 
+@pytest.mark.parametrize("seq", [1, 0])
+@pytest.mark.parametrize("op,n,s", [("burgers1d", 128, 1), ("burgers1d", 128, 2), ("burgers1d", 128, 3),
+                                    ("burgers1d", 128, 5), ("burgers2d", 32, 3), ("burgers2d", 16, 5),
+                                    ("vsf", 32, 2), ("vsf", 16, 3)])
+def test_sdirk_parity(B, op, n, s, seq):
+    """SDIRK, the diagonally implicit comparison of Sec. 7, stage by stage
+    (seq = 1: every stage its own Newton loop on the single-stage solver) and
+    coupled (seq = 0: Algorithm 1 over the stage system, whose transformed
+    Jacobian is exactly block upper triangular): both reach the oracle's
+    solution of the full stage equations."""
+    nu, dt = {"burgers1d": (0.01, 2e-3), "burgers2d": (5e-3, 2e-3), "vsf": (1e-3, 5e-3)}[op]
+    per_step, whole, infos = run_parity(B, op, n, s, nu, dt, 2, seed=9, family="sdirk",
+                                        dirk_sequential=seq)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
+    # 1x1 blocks only: one preconditioner application per Krylov iteration
+    assert all(i["prec_apps"] == i["krylov_its"] > 0 for i in infos), infos
+    if seq:
+        # every stage runs at least one Newton iteration of its own
+        assert all(i["newton_its"] >= s for i in infos), infos
+    if op == "vsf":
+        # one stream function V-cycle per preconditioner application
+        assert all(i["poisson_vcycles"] == i["prec_apps"] for i in infos), infos
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 5])
+def test_sdirk_linear_diffusion_stability_function(B, s):
+    """Per Fourier mode one SDIRK step multiplies by R(z) = 1 + z b^T (I - z A)^{-1} 1,
+    z = dt lambda_m (the tableau's stability function)."""
+    n, nu, dt = 64, 0.05, 0.004
+    u0 = np.random.default_rng(s + 20).standard_normal((1, n))
+    with B.IrkSolver(u0, op="diffusion1d", n=n, stages=s, nu=nu, family="sdirk") as sol:
+        sol.step(0.0, dt, 1)
+        u1 = sol.state()
+    A, b, _ = tab.sdirk(s)
+    m = np.arange(n)
+    z = -dt * (4 * nu * n * n) * np.sin(np.pi * m / n) ** 2
+    R = np.array([1.0 + zz * (b @ np.linalg.solve(np.eye(s) - zz * A, np.ones(s))) for zz in z])
+    want = np.real(np.fft.ifft(R * np.fft.fft(u0[0])))
+    assert rel(u1[0], want) <= 1e-9
+
+
+def test_sdirk_stage_by_stage_profile_and_kernel_stats(B):
+    """Profiled stage-by-stage SDIRK: the stage solver's kernel classes are
+    reported through the outer handle."""
+    u0 = initial("burgers2d", 32, 3)
+    with B.IrkSolver(u0, op="burgers2d", n=32, stages=3, nu=5e-3, family="sdirk", profile=1) as sol:
+        st = sol.step(0.0, 2e-3, 2).as_dict()
+        ks = {k["name"]: k for k in B.irk_kernel_stats(sol.h)}
+    assert st["steps"] == 2 and st["newton_its"] >= 6, st
+    for name in ("residual", "stage_op", "mg_smooth"):
+        assert name in ks and ks[name]["launches"] > 0 and ks[name]["ms"] > 0, ks.keys()
+
+
+@pytest.mark.parametrize("n,s,family", [(32, 2, "gauss"), (32, 3, "gauss"), (16, 5, "gauss"),
+                                         (32, 1, "gauss"), (16, 3, "sdirk"), (32, 2, "radau")])
+def test_vsf_block_triangular_forward_solve_parity(B, n, s, family):
+    """Eq. vsf-system-2 (dae_solver = 1): the block forward solve of the
+    reordered Picard system (FGMRES on the omega block with the omega part of
+    L_P, then one MG-preconditioned Poisson FGMRES per stream function row)
+    reaches the oracle's fixed point; the stream function V-cycles are
+    counted apart from the omega V-cycles."""
+    per_step, whole, infos = run_parity(B, "vsf", n, s, 1e-3, 5e-3, 2, seed=2, dae_solver=1,
+                                        family=family)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
+    for i in infos:
+        omega = i["vcycles"] - i["poisson_vcycles"]
+        assert i["poisson_vcycles"] > 0 and omega == i["prec_apps"] > 0, i
+
+
+def test_vsf_forward_solve_counts_against_eq_vsf_system_1(B):
+    """Both DAE solvers on the same step: Eq. vsf-system-1 applies one omega
+    and one psi V-cycle per preconditioner application; the forward solve
+    spends its psi V-cycles in the Poisson solves instead (the paper's
+    comparison of the two, Table dsl-iters, reports both counts)."""
+    n, s = 32, 3
+    u0 = initial("vsf", n, 5)
+    out = {}
+    for ds in (0, 1):
+        with B.IrkSolver(u0.copy(), op="vsf", n=n, stages=s, nu=1e-3, length=2 * math.pi,
+                         dae_solver=ds) as sol:
+            out[ds] = (sol.step(0.0, 5e-3, 2).as_dict(), sol.state())
+    assert rel(out[1][1], out[0][1]) <= 2 * STEP_TOL
+    a, b = out[0][0], out[1][0]
+    assert a["poisson_vcycles"] == a["prec_apps"], a
+    assert b["poisson_vcycles"] > 0 and b["vcycles"] - b["poisson_vcycles"] == b["prec_apps"], b
+
+
 def test_device_buffers_and_minimum_grid(B):
     per_step, whole, _ = run_parity(B, "burgers2d", 8, 2, 5e-3, 2e-3, 2, seed=5, device_buffers=True)
     assert max(per_step) <= STEP_TOL and whole <= RUN_TOL
