@@ -7,7 +7,7 @@ Radau IIA is collocation on the right Radau nodes (zeros of P_s - P_{s-1}).
 Lobatto IIIC (Table 1) uses the Lobatto nodes (zeros of P_s - P_{s-2}),
 b = the Lobatto weights, a_i1 = b_1 and the conditions
 sum_j a_ij c_j^{q-1} = c_i^q / q for q = 1..s-1.
-SDIRK (the diagonally implicit methods the paper compares against, Sec. 5):
+SDIRK (the diagonally implicit methods the paper compares against, Sec. 7):
 lower triangular A with one diagonal value gamma, stiffly accurate.
 
 Real Schur form (Sec. 3.1): A0^{-1} = Q0 R0 Q0^T with Q0 orthogonal and R0
@@ -94,7 +94,7 @@ def lobatto_iiic(s: int):
 
 def sdirk(s: int):
     """Return (A, b, c) of the L-stable, stiffly accurate SDIRK method with s
-    stages used as the diagonally implicit comparison (Sec. 1.2, Sec. 5):
+    stages used as the diagonally implicit comparison (Sec. 2.1, Sec. 7):
     s = 1 backward Euler (order 1); s = 2 gamma = 1 - sqrt(2)/2 (order 2);
     s = 3 Alexander's method, gamma the root in (1/6, 1/2) of
     x^3 - 3x^2 + 3x/2 - 1/6 (order 3); s = 5 the order-4 method of
