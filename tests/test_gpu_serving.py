@@ -125,3 +125,40 @@ def test_requests_arriving_while_others_run(B):
     p = Problem("burgers2d", q["n"], q["nu"])
     ref, _ = orc.integrate(p, q["s"], q["u0"], 0.0, dt, nsteps)
     assert rel(served[k], ref) <= 1e-8
+
+
+def test_served_families_and_dae_solver_equal_alone(B):
+    """Requests of every tableau family and the VSF forward solve through the
+    server: a stage-by-stage SDIRK handle carves its single-stage solver out of
+    the arena the server hands it, and each result equals its solo run."""
+    import math
+    dt, nsteps = 1e-3, 2
+    specs = [dict(op="burgers2d", n=64, stages=3, nu=1e-2, family="sdirk"),
+             dict(op="burgers2d", n=64, stages=5, nu=1e-2, family="sdirk", dirk_sequential=0),
+             dict(op="burgers2d", n=32, stages=3, nu=1e-2, family="radau"),
+             dict(op="burgers2d", n=32, stages=3, nu=1e-2, family="lobatto"),
+             dict(op="vsf", n=32, stages=2, nu=1e-3, length=2 * math.pi, dae_solver=1),
+             dict(op="vsf", n=32, stages=2, nu=1e-3, length=2 * math.pi, family="sdirk")]
+    u0s = []
+    for k, sp in enumerate(specs):
+        if sp["op"] == "vsf":
+            u = np.zeros((2, sp["n"], sp["n"]))
+            u[0] = workloads.double_shear_layer_vorticity(sp["n"], seed=k)
+        else:
+            u = workloads.random_fourier_2d(sp["n"], seed=200 + k)
+        u0s.append(u)
+    srv = B.irk_server_create(3, 2 << 30)
+    try:
+        ids = [B.irk_server_submit(srv, B.irk_config_default(**sp), u, 0.0, dt, nsteps)
+               for sp, u in zip(specs, u0s)]
+        served = [B.irk_server_wait(srv, i, u.shape, nsteps) for i, u in zip(ids, u0s)]
+        st = B.irk_server_stats_get(srv)
+    finally:
+        B.irk_server_destroy(srv)
+    assert st["completed"] == len(specs) and st["failed"] == 0
+    for sp, u0, (u, stats, _) in zip(specs, u0s, served):
+        with B.IrkSolver(u0, **sp) as sol:
+            sol.step(0.0, dt, nsteps)
+            ref = sol.state()
+        assert stats.steps == nsteps
+        assert rel(u, ref) <= MIX_TOL, sp
