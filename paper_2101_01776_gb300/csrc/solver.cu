@@ -2157,12 +2157,16 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   if (c.op == IRK_OP_VSF_2D) {
     // consistent psi: -L psi = omega (zero mean) by MG-preconditioned FGMRES-free
     // defect correction with the Poisson V-cycle, to a relative residual of 1e-14
+    // or, on fine grids, the rounding floor of -L_h psi in FP64 (about
+    // 4e-16 / h^2 relative): the loop stops once a V-cycle no longer halves a
+    // defect that is already below 1e-9
     launch_remove_mean(h->npts, 1, h->npts, h->u, h->partials, h->st);
     double* psi = h->u + h->npts;
     CK(cudaMemsetAsync(psi, 0, sizeof(double) * h->npts, h->st));
     double bnorm = 0;
     TRY(dev_norm(h, h->u, h->npts, &bnorm));
     const int save_prec = h->prec;
+    double prev_dn = 0;
     for (int it = 0; it < 200 && bnorm > 0; ++it) {
       // defect d = omega - (-L psi) in tmp; via the row operator with x = (0, psi)
       StageOpArgs a;
@@ -2185,6 +2189,8 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
       double dn = 0;
       TRY(dev_norm(h, h->w + h->npts, h->npts, &dn));
       if (dn <= 1e-14 * bnorm) break;
+      if (it > 0 && dn > 0.5 * prev_dn && dn <= 1e-9 * bnorm) break;
+      prev_dn = dn;
       h->prec = IRK_MG_FP64;
       vcycle(h, -1, MG_DIFFUSION, 1, 0.0, 0.0, 1.0, 1, h->w + h->npts, h->tmp);
       h->prec = save_prec;
