@@ -207,7 +207,8 @@ void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
                       double cadv, double cdiff, double omega, const void* vel, const void* b,
                       const void* w_in, void* w_out, int first, cudaStream_t st,
                       double* epi_out = nullptr, const double* epi_base = nullptr,
-                      double epi_coef = 0.0, double epi_bcoef = 1.0);
+                      double epi_coef = 0.0, double epi_bcoef = 1.0,
+                      const double* b64 = nullptr, double* out64 = nullptr);
 bool mg_smooth2_pays(int prec, int dim, int kind, const MGLevelDesc& lv, int first);
 bool mg_smooth3_pays(int prec, int dim, const MGLevelDesc& lv);
 // The four off-diagonal coefficients of the 2D advective level operator,
@@ -247,13 +248,15 @@ void launch_mg_restrict(int prec, int dim, const MGLevelDesc& fine, int ncomp, c
                         void* bc, cudaStream_t st);
 // w_f = dinv b_f + P e_c: the prolongation onto a level whose only pre-sweep
 // started from zero and was folded into launch_mg_residual0
+// b64 / out64 (FP32 and BF16 storage, finest level): b read from the FP64
+// input, the result written to the FP64 output (no conversion launches)
 void launch_mg_prolong_set(int prec, int dim, const MGLevelDesc& fine, int ncomp, double sigma,
                            double cadv, double cdiff, double omega, const void* bf, const void* wc,
-                           void* wf, cudaStream_t st);
+                           void* wf, cudaStream_t st, const double* b64 = nullptr);
 // r = b - A (dinv b): the residual after one damped-Jacobi sweep from zero
 void launch_mg_residual0(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp,
                          double sigma, double cadv, double cdiff, double omega, const void* vel,
-                         const void* b, void* r, cudaStream_t st);
+                         const void* b, void* r, cudaStream_t st, const double* b64 = nullptr);
 void launch_mg_prolong_add(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* wc,
                            void* wf, cudaStream_t st);
 void launch_mg_coarse(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,

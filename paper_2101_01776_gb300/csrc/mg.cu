@@ -20,6 +20,7 @@
 #include <cstring>
 
 #include "irk_internal.h"
+#include <type_traits>
 
 namespace irk {
 
@@ -152,10 +153,31 @@ MGConst mg_const(const MGLevelDesc& lv, int dim, double sigma, double cadv, doub
   return c;
 }
 
-// epi_out (FP64 storage only): also write epi_out = epi_bcoef epi_base +
-// epi_coef w_out pointwise (an L_P coupling row fused into the last sweep)
-// pointwise (the mass-only coupling row of L_P, fused into the last sweep)
-template <typename TS, int DIM, int KIND>
+template <typename TS>
+__device__ __forceinline__ typename Cmp<TS>::T round_to_storage(typename Cmp<TS>::T v) {
+  return (typename Cmp<TS>::T)(TS)v;
+}
+template <>
+__device__ __forceinline__ float round_to_storage<__nv_bfloat16>(float v) {
+  return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+// Fine-level right-hand side of a reduced-precision V-cycle read straight
+// from the FP64 input (b64), rounded to the storage type as a stored copy
+// would be; FP64 storage reads its input in place and never takes b64.
+template <typename TS>
+__device__ __forceinline__ typename Cmp<TS>::T ld_rhs(const TS* b, const double* b64, long long i) {
+  typedef typename Cmp<TS>::T TC;
+  if (!std::is_same<TS, double>::value && b64) return round_to_storage<TS>((TC)b64[i]);
+  return ldv(b + i);
+}
+
+// epi_out: also write epi_out = epi_bcoef epi_base + epi_coef w pointwise
+// (the mass-only coupling row of L_P, fused into the last sweep).
+// WIDE (reduced-precision storage, finest level): read b from the FP64 input
+// b64 and write the result to the FP64 output out64 instead of w_out, both
+// rounded as the stored copies would be.
+template <typename TS, int DIM, int KIND, bool WIDE = false>
 __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, MGConst k,
                                                    const TS* __restrict__ vel,
                                                    const TS* __restrict__ b,
@@ -163,27 +185,36 @@ __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, MG
                                                    TS* __restrict__ w_out, int first,
                                                    double* __restrict__ epi_out,
                                                    const double* __restrict__ epi_base,
-                                                   double epi_coef, double epi_bcoef) {
+                                                   double epi_coef, double epi_bcoef,
+                                                   const double* __restrict__ b64,
+                                                   double* __restrict__ out64) {
   typedef typename Cmp<TS>::T TC;
   const TC alpha = TC(k.alpha), beta = TC(k.beta);
   const TC dinv = TC(k.dinv), keep = TC(k.keep);
+  auto rhs = [&](long long i) -> TC {
+    return WIDE ? round_to_storage<TS>((TC)b64[i]) : ldv(b + i);
+  };
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lv.npts; p += gridDim.x * blockDim.x) {
     const LvIdx q = lv_nbr<DIM>(lv, p);
     if (first) {
       for (int c = 0; c < ncomp; ++c) {
         const long long off = (long long)c * lv.npts;
-        stv<TS, TC>(w_out + off + p, dinv * ldv(b + off + p));
+        const TC v = dinv * rhs(off + p);
+        if (WIDE) out64[off + p] = (double)round_to_storage<TS>(v);
+        else stv<TS, TC>(w_out + off + p, v);
       }
       continue;
     }
     const Coef4<TC> cf = stencil_coef<TS, DIM, KIND>(q, vel, lv.npts, alpha, beta);
     for (int c = 0; c < ncomp; ++c) {
       const long long off = (long long)c * lv.npts;
-      const TC t = rhs_minus_offdiag<TS, DIM>(q, w_in + off, cf, ldv(b + off + p));
+      const TC t = rhs_minus_offdiag<TS, DIM>(q, w_in + off, cf, rhs(off + p));
       // w + omega/D (b - D w - sum c w) = (1 - omega) w + omega/D (b - sum c w)
       const TC v = fma(dinv, t, keep * ldv(w_in + off + p));
-      stv<TS, TC>(w_out + off + p, v);
-      if (epi_out) epi_out[off + p] = fma(epi_coef, (double)v, epi_bcoef * epi_base[off + p]);
+      const double vo = (double)round_to_storage<TS>(v);
+      if (WIDE) out64[off + p] = vo;
+      else stv<TS, TC>(w_out + off + p, v);
+      if (epi_out) epi_out[off + p] = fma(epi_coef, vo, epi_bcoef * epi_base[off + p]);
     }
   }
 }
@@ -213,7 +244,8 @@ __global__ void __launch_bounds__(256) k_mg_residual(MGLevelDesc lv, int ncomp, 
 template <typename TS, int DIM, int KIND>
 __global__ void __launch_bounds__(256) k_mg_residual0(MGLevelDesc lv, int ncomp, MGConst k,
                                                       const TS* __restrict__ vel,
-                                                      const TS* __restrict__ b, TS* __restrict__ r) {
+                                                      const TS* __restrict__ b, TS* __restrict__ r,
+                                                      const double* __restrict__ b64) {
   typedef typename Cmp<TS>::T TC;
   const TC alpha = TC(k.alpha), beta = TC(k.beta);
   const TC dinv = TC(k.dinv), keep = TC(k.keep);
@@ -222,14 +254,16 @@ __global__ void __launch_bounds__(256) k_mg_residual0(MGLevelDesc lv, int ncomp,
     const Coef4<TC> cf = stencil_coef<TS, DIM, KIND>(q, vel, lv.npts, alpha, beta);
 #pragma unroll 1
     for (int c = 0; c < ncomp; ++c) {
-      const TS* bb = b + (long long)c * lv.npts;
-      TC sum = cf.e * ldv(bb + q.e);
-      sum = fma(cf.w, ldv(bb + q.w), sum);
+      const long long off = (long long)c * lv.npts;
+      const TS* bb = b + off;
+      const double* bb64 = b64 ? b64 + off : nullptr;
+      TC sum = cf.e * ld_rhs(bb, bb64, q.e);
+      sum = fma(cf.w, ld_rhs(bb, bb64, q.w), sum);
       if (DIM == 2) {
-        sum = fma(cf.n, ldv(bb + q.n), sum);
-        sum = fma(cf.s, ldv(bb + q.s), sum);
+        sum = fma(cf.n, ld_rhs(bb, bb64, q.n), sum);
+        sum = fma(cf.s, ld_rhs(bb, bb64, q.s), sum);
       }
-      stv<TS, TC>(r + (long long)c * lv.npts + p, fma(-dinv, sum, keep * ldv(bb + p)));
+      stv<TS, TC>(r + off + p, fma(-dinv, sum, keep * ld_rhs(bb, bb64, p)));
     }
   }
 }
@@ -244,14 +278,6 @@ __global__ void __launch_bounds__(256) k_mg_residual0(MGLevelDesc lv, int ncomp,
 // enough to be FP64-issue-bound, where the extra 19% of work would show.
 constexpr int kTX = 32, kTY = 8;
 
-template <typename TS>
-__device__ __forceinline__ typename Cmp<TS>::T round_to_storage(typename Cmp<TS>::T v) {
-  return (typename Cmp<TS>::T)(TS)v;
-}
-template <>
-__device__ __forceinline__ float round_to_storage<__nv_bfloat16>(float v) {
-  return __bfloat162float(__float2bfloat16_rn(v));
-}
 
 // CHEB: Chebyshev acceleration of undamped Jacobi (k.keep = 0): each sweep
 // becomes x_new = x_prev + omega (J(x) - x_prev), with x_prev the iterate
@@ -700,7 +726,8 @@ template <typename TS, int DIM, bool SET>
 __global__ void __launch_bounds__(256) k_mg_prolong_add(MGLevelDesc fine, int ncomp,
                                                         const TS* __restrict__ wc,
                                                         TS* __restrict__ wf,
-                                                        const TS* __restrict__ bf, double dinv64) {
+                                                        const TS* __restrict__ bf, double dinv64,
+                                                        const double* __restrict__ b64) {
   // SET: w_f = dinv b_f + P e (the fine iterate was one sweep from zero and
   // was never stored); otherwise w_f += P e
   typedef typename Cmp<TS>::T TC;
@@ -712,7 +739,8 @@ __global__ void __launch_bounds__(256) k_mg_prolong_add(MGLevelDesc fine, int nc
       const TS* g = wc + (long long)c * ncpts;
       TS* f = wf + (long long)c * fine.npts;
       const TS* fb = SET ? bf + (long long)c * fine.npts : nullptr;
-      auto base = [&](long long o) -> TC { return SET ? dinv * ldv(fb + o) : ldv(f + o); };
+      const double* fb64 = (SET && b64) ? b64 + (long long)c * fine.npts : nullptr;
+      auto base = [&](long long o) -> TC { return SET ? dinv * ld_rhs(fb, fb64, o) : ldv(f + o); };
       if (DIM == 1) {
         const TC c0 = ldv(g + p), c1 = ldv(g + ((p + 1) & mc));
         stv<TS, TC>(f + 2 * p, base(2 * p) + c0);
@@ -863,12 +891,22 @@ size_t mg_elem_size(int prec) {
 void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
                       double cadv, double cdiff, double omega, const void* vel, const void* b,
                       const void* w_in, void* w_out, int first, cudaStream_t st, double* epi_out,
-                      const double* epi_base, double epi_coef, double epi_bcoef) {
+                      const double* epi_base, double epi_coef, double epi_bcoef,
+                      const double* b64, double* out64) {
   const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, omega);
-  if (prec != IRK_MG_FP64) epi_out = nullptr;  // the epilogue is defined on FP64 storage
-  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_smooth<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
-      lv, ncomp, k, (const TS*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, epi_out,
-      epi_base, epi_coef, epi_bcoef))));
+  // FP64 storage reads and writes in place; the wide form needs both pointers
+  const bool wide = (prec != IRK_MG_FP64) && b64 && out64;
+  if (prec != IRK_MG_FP64 && !wide) epi_out = nullptr;  // the epilogue reads the FP64 result
+  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, {
+    if (wide)
+      k_mg_smooth<TS, DIM, KIND, true><<<grid_for(lv.npts), 256, 0, st>>>(
+          lv, ncomp, k, (const TS*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, epi_out,
+          epi_base, epi_coef, epi_bcoef, b64, out64);
+    else
+      k_mg_smooth<TS, DIM, KIND, false><<<grid_for(lv.npts), 256, 0, st>>>(
+          lv, ncomp, k, (const TS*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, epi_out,
+          epi_base, epi_coef, epi_bcoef, nullptr, nullptr);
+  }));
 }
 
 // Whether one k_mg_smooth2 launch should replace two k_mg_smooth launches.
@@ -997,25 +1035,26 @@ void launch_mg_prolong_add(int prec, int dim, const MGLevelDesc& fine, int ncomp
   IRK_DISPATCH_PREC(prec, {
     if (dim == 1)
       k_mg_prolong_add<TS, 1, false><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc,
-                                                                   (TS*)wf, nullptr, 0.0);
+                                                                   (TS*)wf, nullptr, 0.0, nullptr);
     else
       k_mg_prolong_add<TS, 2, false><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc,
-                                                                   (TS*)wf, nullptr, 0.0);
+                                                                   (TS*)wf, nullptr, 0.0, nullptr);
   });
 }
 
 void launch_mg_prolong_set(int prec, int dim, const MGLevelDesc& fine, int ncomp, double sigma,
                            double cadv, double cdiff, double omega, const void* bf, const void* wc,
-                           void* wf, cudaStream_t st) {
+                           void* wf, cudaStream_t st, const double* b64) {
   const MGConst k = mg_const(fine, dim, sigma, cadv, cdiff, omega);
+  if (prec == IRK_MG_FP64) b64 = nullptr;
   const long long nc = dim == 1 ? fine.n / 2 : (long long)(fine.n / 2) * (fine.n / 2);
   IRK_DISPATCH_PREC(prec, {
     if (dim == 1)
       k_mg_prolong_add<TS, 1, true><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc,
-                                                                  (TS*)wf, (const TS*)bf, k.dinv);
+                                                                  (TS*)wf, (const TS*)bf, k.dinv, b64);
     else
       k_mg_prolong_add<TS, 2, true><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc,
-                                                                  (TS*)wf, (const TS*)bf, k.dinv);
+                                                                  (TS*)wf, (const TS*)bf, k.dinv, b64);
   });
 }
 
@@ -1028,10 +1067,11 @@ void launch_mg_coef(int prec, const MGLevelDesc& lv, double cadv, double cdiff, 
 
 void launch_mg_residual0(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp,
                          double sigma, double cadv, double cdiff, double omega, const void* vel,
-                         const void* b, void* r, cudaStream_t st) {
+                         const void* b, void* r, cudaStream_t st, const double* b64) {
   const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, omega);
+  if (prec == IRK_MG_FP64) b64 = nullptr;
   IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_residual0<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
-      lv, ncomp, k, (const TS*)vel, (const TS*)b, (TS*)r))));
+      lv, ncomp, k, (const TS*)vel, (const TS*)b, (TS*)r, b64))));
 }
 
 void launch_mg_bottom(int prec, const MGLevelDesc& lv, double cdiff, double omega, int pre,

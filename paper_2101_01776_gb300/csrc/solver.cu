@@ -473,10 +473,14 @@ struct MGEpilogue {
   double bcoef = 1.0;
 };
 
+// b64 / out64: a reduced-precision finest level reading its right-hand side
+// from the FP64 input and writing its last sweep to the FP64 output (single
+// sweeps only: the callers pass them with one sweep)
 bool jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, double cadv,
                    double cdiff, double om, const void* vel, const void* b, int sweeps,
                    bool from_zero, void*& cur, void*& alt, void* last,
-                   const MGEpilogue* epi = nullptr) {
+                   const MGEpilogue* epi = nullptr, const double* b64 = nullptr,
+                   double* out64 = nullptr) {
   bool epi_done = false;
   const MGLevelDesc& d = h->lev[l].d;
   const int prec = h->prec, dim = h->dim;
@@ -510,13 +514,18 @@ bool jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, doub
     } else {
       const bool final = (sw + 1 == sweeps);
       if (final && last) dst = last;
-      const bool with_epi = final && last && epi && prec == IRK_MG_FP64 && !first;
+      const bool wide = final && out64 && prec != IRK_MG_FP64;
+      const bool with_epi = final && epi && !first && ((last && prec == IRK_MG_FP64) || wide);
+      // b and the result in FP64 instead of the storage type
+      const double wide_bytes = (b64 ? (8.0 - h->esz) * ncomp * d.npts : 0.0) +
+                                (wide ? (8.0 - h->esz) * ncomp * d.npts : 0.0);
       ProfScope ps(h, P_MG_SMOOTH, mg_level_bytes(h, l, first ? 2.0 * ncomp : 3.0 * ncomp + velf) +
-                                       (with_epi ? 16.0 * ncomp * d.npts : 0.0),
+                                       wide_bytes + (with_epi ? 16.0 * ncomp * d.npts : 0.0),
                    (first ? f0 : fsw) + (with_epi ? 2.0 * ncomp * d.npts : 0.0));
       launch_mg_smooth(prec, dim, kind, d, ncomp, sigma, cadv, cdiff, om, vel, b, cur, dst, first,
                        h->st, with_epi ? epi->out : nullptr, with_epi ? epi->base : nullptr,
-                       with_epi ? epi->coef : 0.0, with_epi ? epi->bcoef : 1.0);
+                       with_epi ? epi->coef : 0.0, with_epi ? epi->bcoef : 1.0, b64,
+                       wide ? out64 : nullptr);
       epi_done = epi_done || with_epi;
       sw += 1;
     }
@@ -556,16 +565,6 @@ bool vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
   for (int l = 0; l < nl; ++l) crow[l] = pre ? h->coefh[row][l] : vrow[l];
   const long long n0 = (long long)ncomp * h->lev[0].d.npts;
   const bool alias = (prec == IRK_MG_FP64);
-  const void* bl[IRK_MAX_LEVELS];
-  for (int l = 0; l < nl; ++l) bl[l] = h->lev[l].b;
-  if (alias) {
-    bl[0] = in;
-  } else {
-    ProfScope ps(h, P_MG_CONVERT, n0 * (8.0 + h->esz), 0);
-    launch_mg_convert_in(prec, in, h->lev[0].b, n0, h->st);
-  }
-  void* cur[IRK_MAX_LEVELS];
-  void* alt[IRK_MAX_LEVELS];
   const int velf = (kk == MG_DIFFUSION) ? 0
                    : (kk == MG_ADVECTIVE_PRE) ? 4 : (kk == MG_CONSERVATIVE_1D ? 1 : dim);
   const double fsweep = mg_sweep_flops(kk, dim, ncomp), fresid = mg_resid_flops(kk, dim, ncomp);
@@ -580,15 +579,31 @@ bool vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     lb = nl - 1;
     while (lb > 0 && h->lev[lb - 1].d.n <= 32) --lb;
   }
+  // reduced-precision storage with the folded pre-sweep and one post-sweep:
+  // the finest level's three kernels read b from the FP64 input and the last
+  // sweep writes the FP64 output, so no conversion launches are needed
+  const bool wide_io = !alias && fold_pre && post == 1 && nl >= 2 && lb >= 1;
+  const double* b64 = wide_io ? in : nullptr;
+  const void* bl[IRK_MAX_LEVELS];
+  for (int l = 0; l < nl; ++l) bl[l] = h->lev[l].b;
+  if (alias) {
+    bl[0] = in;
+  } else if (!wide_io) {
+    ProfScope ps(h, P_MG_CONVERT, n0 * (8.0 + h->esz), 0);
+    launch_mg_convert_in(prec, in, h->lev[0].b, n0, h->st);
+  }
+  void* cur[IRK_MAX_LEVELS];
+  void* alt[IRK_MAX_LEVELS];
   for (int l = 0; l + 1 < nl && l < lb; ++l) {
     MGLevel& lv = h->lev[l];
     cur[l] = lv.w;
     alt[l] = lv.w2;
     if (fold_pre) {
-      ProfScope ps(h, P_MG_RESID, mg_level_bytes(h, l, 2.0 * ncomp + velf),
+      const double wb = (l == 0 && b64) ? (8.0 - h->esz) * ncomp * lv.d.npts : 0.0;
+      ProfScope ps(h, P_MG_RESID, mg_level_bytes(h, l, 2.0 * ncomp + velf) + wb,
                    (fresid + 2.0 * ncomp) * lv.d.npts);
       launch_mg_residual0(prec, dim, kk, lv.d, ncomp, sigma, cadv, cdiff, om, crow[l], bl[l],
-                          lv.r, h->st);
+                          lv.r, h->st, l == 0 ? b64 : nullptr);
     } else {
       jacobi_sweeps(h, l, kk, ncomp, sigma, cadv, cdiff, om, crow[l], bl[l], npre, true,
                     cur[l], alt[l], nullptr);
@@ -692,19 +707,21 @@ bool vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
   for (int l = std::min(nl, lb) - 2 + (lb < nl ? 1 : 0); l >= 0; --l) {
     MGLevel& lv = h->lev[l];
     {
-      ProfScope ps(h, P_MG_PROLONG, mg_level_bytes(h, l, 2.0 * ncomp + (double)ncomp / (1 << dim)),
+      const double wb = (l == 0 && b64) ? (8.0 - h->esz) * ncomp * lv.d.npts : 0.0;
+      ProfScope ps(h, P_MG_PROLONG, mg_level_bytes(h, l, 2.0 * ncomp + (double)ncomp / (1 << dim)) + wb,
                    (double)ncomp * lv.d.npts * 3);
       if (fold_pre)
         launch_mg_prolong_set(prec, dim, lv.d, ncomp, sigma, cadv, cdiff, om, bl[l], cur[l + 1],
-                              cur[l], h->st);
+                              cur[l], h->st, l == 0 ? b64 : nullptr);
       else
         launch_mg_prolong_add(prec, dim, lv.d, ncomp, cur[l + 1], cur[l], h->st);
     }
     if (post > 0) {
-      const bool to_out = alias && l == 0;
+      const bool to_out = (alias || wide_io) && l == 0;
       const bool e = jacobi_sweeps(h, l, kk, ncomp, sigma, cadv, cdiff, om, crow[l], bl[l], post,
-                                   false, cur[l], alt[l], to_out ? (void*)out : nullptr,
-                                   to_out ? epi : nullptr);
+                                   false, cur[l], alt[l], (to_out && alias) ? (void*)out : nullptr,
+                                   to_out ? epi : nullptr, l == 0 ? b64 : nullptr,
+                                   (to_out && wide_io) ? out : nullptr);
       epi_done = epi_done || e;
       if (to_out) wrote_out = true;
     }

@@ -175,6 +175,24 @@ def test_mixed_precision_preconditioner_same_result(B, prec):
     assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole)
 
 
+@pytest.mark.parametrize("op,n,s,prec", [("burgers2d", 64, 2, 1), ("burgers2d", 32, 2, 2),
+                                         ("vsf", 64, 2, 1), ("vsf", 32, 3, 2), ("burgers1d", 128, 2, 1)])
+def test_mixed_precision_fine_level_reads_fp64(B, op, n, s, prec):
+    """Reduced-precision V-cycles whose finest level reads the FP64 input and
+    writes the FP64 output directly (and, for 2-stage Gauss and the VSF
+    rows, the L_P coupling right-hand side with it) reach the oracle's fixed
+    point; the V-cycle then launches no conversion kernels."""
+    nu, dt = {"burgers1d": (0.01, 2e-3), "burgers2d": (5e-3, 2e-3), "vsf": (1e-3, 5e-3)}[op]
+    per_step, whole, infos = run_parity(B, op, n, s, nu, dt, 2, seed=12, mg_precision=prec)
+    assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
+    if op == "burgers2d":
+        u0 = initial(op, n, 12)
+        with B.IrkSolver(u0, op=op, n=n, stages=s, nu=nu, mg_precision=prec, profile=1) as sol:
+            sol.step(0.0, dt, 1)
+            names = {k["name"] for k in B.irk_kernel_stats(sol.h)}
+        assert "mg_convert" not in names, names
+
+
 @pytest.mark.parametrize("kw", [dict(gamma_mode=1), dict(nonlinear_variant=2),
                                 dict(krylov_restart=3), dict(mg_levels=2),
                                 dict(mg_coarse_smoother=2), dict(mg_coarse_smoother=1),
