@@ -125,9 +125,18 @@ typedef struct {
   int use_graphs;       /* 1 (default) = run each IRK step as one CUDA graph
                            (Newton and FGMRES loops in conditional nodes),
                            captured once per dt; forced off while profile = 1 */
-  int initial_guess;    /* Newton start: 1 (default) = the previous step's
-                           stages, 0 = zero.  The tolerance is relative to
-                           ||F(k=0)|| either way; irk_set_state resets it to 0 */
+  int initial_guess;    /* Newton start (the tolerance is relative to
+                           ||F(k=0)|| in every case):
+                           2 (default) = the previous step's stages
+                             extrapolated along the collocation polynomial
+                             (Gauss, Radau IIA: k_j = sum_i k_i l_i(1 + c_j
+                             dt/dt_prev), l_i the Lagrange basis on the
+                             abscissae); other families use them as they are;
+                           1 = the previous step's stages;
+                           0 = zero.
+                           irk_set_state resets the stages to zero;
+                           irk_set_stages marks the given stages as from a
+                           step of the next step's dt */
   int basis;            /* irk_basis; default IRK_BASIS_SCHUR */
   int mg_shifted_sweeps;/* pre- and post-sweeps on shift-dominated rows of 2D
                            grids (sigma >= 0.15 D on the finest level, D the
@@ -215,7 +224,7 @@ irk_status irk_set_state(irk_handle* h, const double* src, int src_on_device);
 
 /* irk_set_state for a caller that streams one trajectory through host
  * memory: replaces the state but keeps the stages of the last accepted step
- * as the next Newton guess (initial_guess = 1).  The tolerance stays relative
+ * as the basis of the next Newton guess (initial_guess 1 or 2).  The tolerance stays relative
  * to ||F(k=0)||, so the fixed point does not depend on the guess; for an
  * unrelated state use irk_set_state, which starts from zero stages. */
 irk_status irk_set_state_keep_stages(irk_handle* h, const double* src, int src_on_device);
@@ -223,9 +232,10 @@ irk_status irk_set_state_keep_stages(irk_handle* h, const double* src, int src_o
 /* Stage vectors k_1..k_s of the last accepted step (s*ncomp*n^dim values). */
 irk_status irk_get_stages(irk_handle* h, double* dst, int dst_on_device);
 
-/* Set the stage vectors used as the next step's Newton starting guess
- * (with initial_guess = 1).  A checkpoint that must resume bit for bit saves
- * the state and the stages and restores both, the stages after the state. */
+/* Set the stage vectors the next step's Newton starting guess is formed from
+ * (initial_guess 1 or 2; for 2 they count as stages of a step of the next
+ * step's dt).  A checkpoint that must resume bit for bit saves the state and
+ * the stages and restores both, the stages after the state. */
 irk_status irk_set_stages(irk_handle* h, const double* src, int src_on_device);
 
 /* Stage residual F_i = M k_i - N(u + dt sum_j a_ij k_j, t_n + c_i dt)

@@ -26,6 +26,7 @@ struct HostTableau {
   double TR[IRK_MAXS * IRK_MAXS];  // T R: back-transform of Algorithm 1
   int nblk, bstart[IRK_MAXS], bsize[IRK_MAXS];
   double eta[IRK_MAXS], beta2[IRK_MAXS], gamma_star[IRK_MAXS];
+  int collocation;  // Gauss, Radau IIA: k_i = u'(t_n + c_i dt) of the collocation polynomial
 };
 
 int build_tableau(int family, int s, int basis, HostTableau* t, char* err, size_t errlen);
@@ -153,6 +154,8 @@ void launch_combo_coef(const GridDesc& g, const double* combos, const ComboList&
 // coefficient fields per combined field for `op` (6 Burgers-2D, 16 VSF: the
 // dt/(12h^2)-scaled Arakawa weights of psibar and wbar), 0 = none
 int combo_coef_fields(int op);
+// K_j <- sum_i E_ji K_i per point, E (s x s, row-major) read from device memory
+void launch_stage_extrapolate(long long L, int s, const double* E, double* K, cudaStream_t st);
 void launch_stage_update(long long L, int s, const double* QR, const double* yhat, double* K,
                          cudaStream_t st);
 void launch_u_update(long long L, int s, const double* b, double dt, const double* K, double* u,

@@ -141,6 +141,12 @@ struct irk_handle {
   // SDIRK solved stage by stage: a single-stage solver (A = [gamma]) whose
   // arena lies in this handle's arena solves each stage equation in turn;
   // inner_gamma > 0 marks such a single-stage solver
+  // Newton starting value (initial_guess = 2): dt of the last accepted step
+  // (0: none, -1: stages set by the caller, taken as from a step of the same
+  // dt) and the ratio for which the extrapolation matrix sits in dscal[450..]
+  double last_dt = 0.0;
+  double E_ratio = -2.0;
+
   irk_handle* inner = nullptr;
   void* inner_arena = nullptr;
   size_t inner_bytes = 0;
@@ -1280,6 +1286,42 @@ irk_status build_fg_graph(irk_handle* h, double dt, int blk) {
 // growth, non-finite residual) and the same inexact-Newton forcing term; the
 // host reads one status block after the graph.  Not used with a time-
 // dependent source (its stage times would be baked into the graph).
+// Newton starting value of a collocation method (initial_guess = 2): the
+// previous step's stages are the derivative of its collocation polynomial at
+// t_{n-1} + c_i h_old, so k_j = sum_i k_i l_i(1 + c_j h/h_old) (l_i the
+// Lagrange basis on the abscissae) extrapolates it to this step's nodes.
+constexpr int kExtrapSlot = 450;  // dscal[450 .. 450 + s*s)
+
+bool use_extrapolation(const irk_handle* h) {
+  return h->cfg.initial_guess == 2 && h->tab.collocation && h->s > 1;
+}
+
+// Upload E for this step's ratio h/h_old (identity when there is no previous
+// step); the captured graphs read it from device memory.
+irk_status prepare_guess(irk_handle* h, double dt) {
+  if (!use_extrapolation(h)) return IRK_OK;
+  const double r = h->last_dt > 0 ? dt / h->last_dt : (h->last_dt < 0 ? 1.0 : 0.0);
+  if (r == h->E_ratio) return IRK_OK;
+  const int s = h->s;
+  double* E = h->hbuf + 256;  // pinned; the previous upload has completed (steps synchronize)
+  for (int j = 0; j < s; ++j)
+    for (int i = 0; i < s; ++i) {
+      if (r == 0.0) {
+        E[j * s + i] = (i == j) ? 1.0 : 0.0;
+        continue;
+      }
+      const long double th = 1.0L + (long double)h->tab.c[j] * r;
+      long double l = 1.0L;
+      for (int m = 0; m < s; ++m)
+        if (m != i) l *= (th - h->tab.c[m]) / ((long double)h->tab.c[i] - h->tab.c[m]);
+      E[j * s + i] = (double)l;
+    }
+  CK(cudaMemcpyAsync(h->dscal + kExtrapSlot, E, sizeof(double) * s * s, cudaMemcpyHostToDevice,
+                     h->st));
+  h->E_ratio = r;
+  return IRK_OK;
+}
+
 irk_status build_step_graph(irk_handle* h, double dt) {
   if (h->stepexec) {
     cudaGraphExecDestroy(h->stepexec);
@@ -1298,14 +1340,19 @@ irk_status build_step_graph(irk_handle* h, double dt) {
   CapCounts blkcc[IRK_MAXS];
   if (e == cudaSuccess) {
     const long long l0 = h->stats.kernel_launches;
-    if (h->cfg.initial_guess == 1) {
-      // ||F(k=0)|| fixes the tolerance; Newton then starts from the previous stages
+    if (h->cfg.initial_guess >= 1) {
+      // ||F(k=0)|| fixes the tolerance; Newton then starts from the previous
+      // stages, extrapolated along the collocation polynomial (guess 2)
       cudaMemsetAsync(h->yhat, 0, sizeof(double) * s * h->L, h->st);
       launch_eval_residual(h, 0.0, dt, h->yhat, h->rhs, nullptr, false);
       {
         ProfScope ps(h, P_SCALE, 0, 0);
         launch_newton_first(h->nws, h->dscal + 201, h->dscal + 300, h->cfg.newton_rtol,
                             h->cfg.krylov_rtol, ncond, h->st);
+      }
+      if (use_extrapolation(h)) {
+        ProfScope ps(h, P_UPDATE, 16.0 * h->L * s, 2.0 * h->L * s * s);
+        launch_stage_extrapolate(h->L, s, h->dscal + kExtrapSlot, h->K, h->st);
       }
       {
         ProfScope ps(h, P_SCALE, 0, 0);
@@ -1769,10 +1816,15 @@ irk_status exact_newton_update(irk_handle* h, double dt, double rtol) {
 irk_status newton_step(irk_handle* h, double t_n, double dt) {
   const int s = h->s;
   double f0 = 0, fn = 0, prev = 0, prev_rel = 0;
-  if (h->cfg.initial_guess == 1) {
-    // ||F(k=0)|| fixes the tolerance; Newton then starts from the previous stages
+  if (h->cfg.initial_guess >= 1) {
+    // ||F(k=0)|| fixes the tolerance; Newton then starts from the previous
+    // stages, extrapolated along the collocation polynomial (guess 2)
     CK(cudaMemsetAsync(h->yhat, 0, sizeof(double) * s * h->L, h->st));
     TRY(eval_residual(h, t_n, dt, h->yhat, h->rhs, nullptr, false, &f0));
+    if (use_extrapolation(h)) {
+      ProfScope ps(h, P_UPDATE, 16.0 * h->L * s, 2.0 * h->L * s * s);
+      launch_stage_extrapolate(h->L, s, h->dscal + kExtrapSlot, h->K, h->st);
+    }
     if (f0 == 0.0) CK(cudaMemsetAsync(h->K, 0, sizeof(double) * s * h->L, h->st));
   } else {
     CK(cudaMemsetAsync(h->K, 0, sizeof(double) * s * h->L, h->st));
@@ -1782,7 +1834,7 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
     TRY(eval_residual(h, t_n, dt, h->K, h->rhs, h->fo, true, &fn));
     if (it > 0) TRY(collect_fg_counters(h));
     if (!std::isfinite(fn) || !std::isfinite(f0)) { h->err = "non-finite stage residual"; return IRK_ERR_NEWTON_DIVERGED; }
-    if (it == 0 && h->cfg.initial_guess != 1) f0 = fn;
+    if (it == 0 && h->cfg.initial_guess == 0) f0 = fn;
     const double rel = (f0 > 0) ? fn / f0 : 0.0;
     h->stats.final_rel_res = rel;
     if (f0 == 0 || rel <= h->cfg.newton_rtol) break;
@@ -1844,7 +1896,7 @@ irk_status sdirk_sequential_step(irk_handle* h, double t_n, double dt) {
       launch_u_update(h->L, i, h->tab.A + i * s, dt, h->K, in->u, h->st);
     }
     // Newton guess: this stage at the previous step (zero after a reset)
-    if (h->cfg.initial_guess == 1)
+    if (h->cfg.initial_guess >= 1)
       CK(cudaMemcpyAsync(in->K, h->K + (long long)i * h->L, vb, cudaMemcpyDeviceToDevice, h->st));
     memset(&in->stats, 0, sizeof(in->stats));
     irk_status st = graph_step(in, dt);
@@ -1896,7 +1948,7 @@ irk_status validate(const irk_config* c, std::string& err) {
   if (!(c->krylov_rtol > 0) || c->krylov_restart < 1 || c->krylov_restart > 64 || c->krylov_maxit < 1) { err = "bad Krylov settings"; return IRK_ERR_INVALID; }
   if (c->nonlinear_variant < 0 || c->nonlinear_variant > 4) { err = "nonlinear_variant must be 0..4"; return IRK_ERR_INVALID; }
   if (c->gamma_mode != 0 && c->gamma_mode != 1) { err = "gamma_mode must be 0 or 1"; return IRK_ERR_INVALID; }
-  if (c->initial_guess != 0 && c->initial_guess != 1) { err = "initial_guess must be 0 or 1"; return IRK_ERR_INVALID; }
+  if (c->initial_guess < 0 || c->initial_guess > 2) { err = "initial_guess must be 0, 1 or 2"; return IRK_ERR_INVALID; }
   if (c->mg_precision < 0 || c->mg_precision > 2) { err = "mg_precision must be 0..2"; return IRK_ERR_INVALID; }
   if (c->mg_pre < 1 || c->mg_post < 0 || c->mg_pre > 8 || c->mg_post > 8) { err = "mg sweeps out of range"; return IRK_ERR_INVALID; }
   if (c->mg_coarse_sweeps < 1 || c->mg_coarse_sweeps > 1000) { err = "mg_coarse_sweeps out of range"; return IRK_ERR_INVALID; }
@@ -2256,7 +2308,7 @@ void irk_config_default(irk_config* c) {
   c->mg_omega = 0.0;
   c->profile = 0;
   c->use_graphs = 1;
-  c->initial_guess = 1;
+  c->initial_guess = 2;
   c->dirk_sequential = 1;
   c->dae_solver = 0;
 }
@@ -2414,15 +2466,20 @@ irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats*
     if (h->inner) {
       st = sdirk_sequential_step(h, t, dt);
     } else {
-      st = graph_step(h, dt);
-      if (st == IRK_ERR_INVALID) st = newton_step(h, t, dt);  // host-driven loop
+      st = prepare_guess(h, dt);
+      if (st == IRK_OK) {
+        st = graph_step(h, dt);
+        if (st == IRK_ERR_INVALID) st = newton_step(h, t, dt);  // host-driven loop
+      }
     }
     if (st != IRK_OK) {
       cudaMemcpyAsync(h->u, h->u_save, sizeof(double) * h->L, cudaMemcpyDeviceToDevice, h->st);
       cudaMemsetAsync(h->K, 0, sizeof(double) * h->L * h->s, h->st);  // discard the failed iterate
       cudaStreamSynchronize(h->st);
+      h->last_dt = 0.0;
       break;
     }
+    h->last_dt = dt;
     h->stats.steps += 1;
     t += dt;
   }
@@ -2451,6 +2508,7 @@ irk_status irk_set_state(irk_handle* h, const double* src, int src_on_device) {
                      src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
   // a new state starts Newton from zero stages
   CK(cudaMemsetAsync(h->K, 0, sizeof(double) * h->L * h->s, h->st));
+  h->last_dt = 0.0;
   CK(cudaStreamSynchronize(h->st));
   return IRK_OK;
 }
@@ -2467,6 +2525,7 @@ irk_status irk_set_stages(irk_handle* h, const double* src, int src_on_device) {
   if (!h || !src) return IRK_ERR_INVALID;
   CK(cudaMemcpyAsync(h->K, src, sizeof(double) * h->L * h->s,
                      src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  h->last_dt = -1.0;  // the caller's stages: taken as from a step of the next step's dt
   CK(cudaStreamSynchronize(h->st));
   return IRK_OK;
 }

@@ -723,6 +723,41 @@ __global__ void __launch_bounds__(256) k_stage_update(long long L, SmallMat T, c
   }
 }
 
+// Newton starting value from the previous step's stages (in place; E read
+// from device memory, so one captured graph follows the host's choice of E)
+template <int S>
+__global__ void __launch_bounds__(256) k_stage_extrapolate(long long L, const double* __restrict__ E,
+                                                           double* __restrict__ K) {
+  __shared__ double e[S * S];
+  for (int i = threadIdx.x; i < S * S; i += blockDim.x) e[i] = E[i];
+  __syncthreads();
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
+       p += (long long)gridDim.x * blockDim.x) {
+    double k[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) k[i] = K[i * L + p];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      double acc = 0.0;
+#pragma unroll
+      for (int i = 0; i < S; ++i) acc = fma(e[j * S + i], k[i], acc);
+      K[j * L + p] = acc;
+    }
+  }
+}
+
+void launch_stage_extrapolate(long long L, int s, const double* E, double* K, cudaStream_t st) {
+  int blocks = (int)((L + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  switch (s) {
+    case 1: k_stage_extrapolate<1><<<blocks, 256, 0, st>>>(L, E, K); break;
+    case 2: k_stage_extrapolate<2><<<blocks, 256, 0, st>>>(L, E, K); break;
+    case 3: k_stage_extrapolate<3><<<blocks, 256, 0, st>>>(L, E, K); break;
+    case 4: k_stage_extrapolate<4><<<blocks, 256, 0, st>>>(L, E, K); break;
+    case 5: k_stage_extrapolate<5><<<blocks, 256, 0, st>>>(L, E, K); break;
+  }
+}
+
 void launch_stage_update(long long L, int s, const double* QR, const double* yhat, double* K,
                          cudaStream_t st) {
   SmallMat T;

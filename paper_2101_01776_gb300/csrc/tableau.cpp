@@ -698,6 +698,7 @@ int build_tableau(int family, int s, int basis, HostTableau* t, char* err, size_
     for (int i = 0; i < s; ++i)
       for (int j = 0; j < s; ++j) Qinv[i * s + j] = Q[j * s + i];
   }
+  t->collocation = (family == IRK_GAUSS || family == IRK_RADAU_IIA);
   // residual check T R T^{-1} == A0^{-1}, then store
   return store_tableau(s, A, b, c, Ainv, Q, R, Qinv, t, err, errlen) ? 0 : 1;
 }

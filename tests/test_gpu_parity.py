@@ -457,13 +457,40 @@ def test_checkpoint_resume_and_determinism_bit_equal(B):
     np.testing.assert_array_equal(full, resumed)
 
 
-@pytest.mark.parametrize("guess", [0, 1])
+@pytest.mark.parametrize("guess", [0, 1, 2])
 def test_initial_guess_reaches_the_same_fixed_point(B, guess):
-    """Newton from zero stages or from the previous step's stages: the same
-    stage equations, the same tolerance (relative to ||F(k=0)||)."""
+    """Newton from zero stages, from the previous step's stages or from their
+    extrapolation along the collocation polynomial: the same stage equations,
+    the same tolerance (relative to ||F(k=0)||)."""
     per_step, whole, infos = run_parity(B, "burgers2d", 64, 2, 5e-3, 2e-3, 3, seed=6,
                                         initial_guess=guess)
     assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
+
+
+@pytest.mark.parametrize("op,n,s,family", [("burgers2d", 64, 3, "gauss"), ("vsf", 64, 5, "gauss"),
+                                           ("burgers2d", 64, 3, "radau"), ("burgers1d", 256, 4, "gauss")])
+def test_extrapolated_guess_saves_iterations(B, op, n, s, family):
+    """Over a smooth trajectory the extrapolated starting value (guess 2) needs
+    no more Krylov iterations than the previous stages (guess 1), and the two
+    runs agree to the Newton tolerance; a step after a change of dt and a
+    reset state still converge."""
+    nu, dt, length = {"burgers1d": (0.01, 2e-3, 1.0), "burgers2d": (5e-3, 2e-3, 1.0),
+                      "vsf": (1e-3, 5e-3, 2 * math.pi)}[op]
+    u0 = initial(op, n, 8)
+    kry, out = {}, {}
+    for guess in (1, 2):
+        with B.IrkSolver(u0.copy(), op=op, n=n, stages=s, nu=nu, length=length, family=family,
+                         initial_guess=guess) as sol:
+            sol.step(0.0, dt, 2)
+            st = sol.step(2 * dt, dt, 4).as_dict()
+            kry[guess] = st["krylov_its"]
+            out[guess] = sol.state().copy()
+            st2 = sol.step(6 * dt, 0.5 * dt, 2).as_dict()  # dt change: ratio 1/2
+            sol.set_state(out[guess])
+            st3 = sol.step(6 * dt, dt, 1).as_dict()  # reset: zero stages
+            assert st2["steps"] == 2 and st3["steps"] == 1
+    assert kry[2] <= kry[1], kry
+    assert rel(out[2], out[1]) <= 1e-9, rel(out[2], out[1])
 
 
 def test_graph_path_matches_host_driven_path(B):
