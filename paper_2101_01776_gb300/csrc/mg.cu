@@ -20,6 +20,7 @@
 #include <cstring>
 
 #include "irk_internal.h"
+#include <cstdlib>
 #include <type_traits>
 
 namespace irk {
@@ -383,29 +384,30 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
   }
 }
 
-// Three damped-Jacobi sweeps in one launch, for latency-bound levels: the
+// Three damped-Jacobi sweeps in one launch, for latency-bound levels: a 32 x TY
 // tile loads w on its halo-3 window and b and the coefficients on its halo-2
 // window, then sweeps the halo-2 window, the halo-1 window and the tile out
-// of shared memory (1028 point updates for 768 useful ones).  Intermediate
-// sweeps are rounded to the storage type: three single sweeps bit for bit.
-template <typename TS, int KIND>
-__global__ void __launch_bounds__(kTX * kTY) k_mg_smooth3(MGLevelDesc lv, int ncomp, MGConst k,
+// of shared memory (TY = 8: 1028 point updates for 768 useful ones; TY = 16:
+// 1844 for 1536).  Intermediate sweeps are rounded to the storage type: three
+// single sweeps bit for bit.
+template <typename TS, int KIND, int TY>
+__global__ void __launch_bounds__(kTX * TY) k_mg_smooth3(MGLevelDesc lv, int ncomp, MGConst k,
                                                         const TS* __restrict__ vel,
                                                         const TS* __restrict__ b,
                                                         const TS* __restrict__ w_in,
                                                         TS* __restrict__ w_out, int first) {
   typedef typename Cmp<TS>::T TC;
-  constexpr int X3 = kTX + 6, Y3 = kTY + 6;  // halo-3 window
-  constexpr int X2 = kTX + 4, Y2 = kTY + 4;  // halo-2 window (b, coefficients)
+  constexpr int X3 = kTX + 6, Y3 = TY + 6;  // halo-3 window
+  constexpr int X2 = kTX + 4, Y2 = TY + 4;  // halo-2 window (b, coefficients)
   __shared__ TC s_w0[Y3][X3];
   __shared__ TC s_w1[Y2][X2];
   __shared__ TC s_b[Y2 * X2];
   __shared__ TC s_c[4][Y2 * X2];
   const TC alpha = TC(k.alpha), beta = TC(k.beta), dinv = TC(k.dinv), keep = TC(k.keep);
   const int n = lv.n, m = n - 1, ln = lv.logn;
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
   const int tid = threadIdx.y * kTX + threadIdx.x;
-  constexpr int NT = kTX * kTY;
+  constexpr int NT = kTX * TY;
   for (int c = blockIdx.z; c < ncomp; c += gridDim.z) {
     const long long off = (long long)c * lv.npts;
     if (!first)
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth3(MGLevelDesc lv, int nc
     }
     __syncthreads();
     // sweep 2 on the halo-1 window: s_w1 -> s_w0 (reused, halo-1 positions)
-    for (int q = tid; q < (kTY + 2) * (kTX + 2); q += NT) {
+    for (int q = tid; q < (TY + 2) * (kTX + 2); q += NT) {
       const int ly = q / (kTX + 2), lx = q - ly * (kTX + 2);
       const int sy = ly + 1, sx = lx + 1;  // in the halo-2 window
       const int cq = sy * X2 + sx;
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth3(MGLevelDesc lv, int nc
       s_w0[ly][lx] = round_to_storage<TS>(fma(dinv, t, keep * s_w1[sy][sx]));
     }
     __syncthreads();
-    // sweep 3 on the tile: s_w0 (halo-1 window at [0..kTY+1][0..kTX+1]) -> global
+    // sweep 3 on the tile: s_w0 (halo-1 window at [0..TY+1][0..kTX+1]) -> global
     {
       const int lx = threadIdx.x, ly = threadIdx.y;
       const int sy = ly + 1, sx = lx + 1;  // in the halo-1 window
@@ -976,18 +978,29 @@ void launch_mg_smooth3(int prec, int kind, const MGLevelDesc& lv, int ncomp, dou
                        const void* w_in, void* w_out, int first, cudaStream_t st) {
   const MGConst k = mg_const(lv, 2, sigma, cadv, cdiff, omega);
   const int zsplit = (lv.n <= 256) ? ncomp : 1;
-  const dim3 grid(lv.n / kTX, lv.n / kTY, zsplit), block(kTX, kTY);
+  // FP64: 32 x 16 tiles, whose sweeps update 1.20x the tile's points against
+  // 1.34x for 32 x 8 (the class got 4-6% faster on the 256^2 level); FP32 and
+  // BF16 keep 32 x 8, where twice the CTAs measured slightly ahead
+  const bool tall = (prec == IRK_MG_FP64);
+  const int ty = tall ? 16 : kTY;
+  const dim3 grid(lv.n / kTX, lv.n / ty, zsplit), block(kTX, ty);
+#define IRK_S3(TY_)                                                                               \
+  do {                                                                                            \
+    if (kind == MG_ADVECTIVE)                                                                     \
+      k_mg_smooth3<TS, MG_ADVECTIVE, TY_><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,   \
+          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                                      \
+    else if (kind == MG_ADVECTIVE_PRE)                                                            \
+      k_mg_smooth3<TS, MG_ADVECTIVE_PRE, TY_><<<grid, block, 0, st>>>(lv, ncomp, k,               \
+          (const TS*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                      \
+    else                                                                                          \
+      k_mg_smooth3<TS, MG_DIFFUSION, TY_><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,   \
+          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                                      \
+  } while (0)
   IRK_DISPATCH_PREC(prec, {
-    if (kind == MG_ADVECTIVE)
-      k_mg_smooth3<TS, MG_ADVECTIVE><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
-          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
-    else if (kind == MG_ADVECTIVE_PRE)
-      k_mg_smooth3<TS, MG_ADVECTIVE_PRE><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
-          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
-    else
-      k_mg_smooth3<TS, MG_DIFFUSION><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
-          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
+    if (tall) IRK_S3(16);
+    else IRK_S3(kTY);
   });
+#undef IRK_S3
 }
 
 void launch_mg_cheb2(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
