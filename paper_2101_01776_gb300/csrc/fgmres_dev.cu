@@ -449,6 +449,7 @@ __global__ void k_newton_ctl(double* nw, const double* __restrict__ f2, double* 
   int stop = 1;
   if (!isfinite(fn)) nw[5] = (double)IRK_ERR_NEWTON_DIVERGED;
   else if (rel <= newton_rtol || nw[0] == 0.0) nw[5] = 0.0;
+  else if (count == 0 && rel > 1.0) nw[5] = (double)kGuessRejected;  // warm start worse than zero
   else if (it >= maxit) nw[5] = (double)IRK_ERR_NEWTON_MAXIT;
   else if (rel > 1e3) nw[5] = (double)IRK_ERR_NEWTON_DIVERGED;
   else stop = 0;

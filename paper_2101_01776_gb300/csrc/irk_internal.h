@@ -30,6 +30,9 @@ struct HostTableau {
 };
 
 int build_tableau(int family, int s, int basis, HostTableau* t, char* err, size_t errlen);
+// Internal Newton status of the device loop: the warm-start guess has a
+// larger residual than zero stages; the step restarts from zero.
+constexpr int kGuessRejected = 100;
 // The single-stage tableau A = [gamma], b = [1], c = [0] (one SDIRK stage
 // solved on its own); nonzero for gamma <= 0.
 int build_tableau_single(double gamma, HostTableau* t);

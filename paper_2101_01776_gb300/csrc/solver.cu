@@ -1476,6 +1476,17 @@ irk_status graph_step(irk_handle* h, double dt) {
   CK(cudaMemcpyAsync(h->hbuf, h->dscal + 300, sizeof(double) * 110, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   const double* nw = h->hbuf + 100;  // dscal[400..]
+  if ((int)nw[5] == kGuessRejected) {
+    // the warm start was worse than zero stages: run the step again from
+    // zero, from the saved state (the graph's final update has run)
+    h->stats.kernel_launches += h->step_fixed_launches;
+    CK(cudaMemcpyAsync(h->u, h->u_save, sizeof(double) * h->L, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemsetAsync(h->K, 0, sizeof(double) * h->s * h->L, h->st));
+    CK(cudaGraphLaunch(h->stepexec, h->st));
+    CK(cudaMemcpyAsync(h->hbuf, h->dscal + 300, sizeof(double) * 110, cudaMemcpyDeviceToHost,
+                       h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
   const int its = (int)nw[4];
   const int status = (int)nw[5];
   h->stats.newton_its += its;
@@ -1832,6 +1843,11 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
   int it = 0;
   for (;; ++it) {
     TRY(eval_residual(h, t_n, dt, h->K, h->rhs, h->fo, true, &fn));
+    if (it == 0 && h->cfg.initial_guess >= 1 && f0 > 0 && fn > f0) {
+      // the warm start is worse than zero stages: start from zero instead
+      CK(cudaMemsetAsync(h->K, 0, sizeof(double) * s * h->L, h->st));
+      TRY(eval_residual(h, t_n, dt, h->K, h->rhs, h->fo, true, &fn));
+    }
     if (it > 0) TRY(collect_fg_counters(h));
     if (!std::isfinite(fn) || !std::isfinite(f0)) { h->err = "non-finite stage residual"; return IRK_ERR_NEWTON_DIVERGED; }
     if (it == 0 && h->cfg.initial_guess == 0) f0 = fn;
@@ -1895,6 +1911,8 @@ irk_status sdirk_sequential_step(irk_handle* h, double t_n, double dt) {
       ProfScope ps(h, P_UPDATE, 8.0 * h->L * (2 + i), 2.0 * h->L * i);
       launch_u_update(h->L, i, h->tab.A + i * s, dt, h->K, in->u, h->st);
     }
+    // the stage solver restores its base from u_save if it restarts from zero
+    CK(cudaMemcpyAsync(in->u_save, in->u, vb, cudaMemcpyDeviceToDevice, h->st));
     // Newton guess: this stage at the previous step (zero after a reset)
     if (h->cfg.initial_guess >= 1)
       CK(cudaMemcpyAsync(in->K, h->K + (long long)i * h->L, vb, cudaMemcpyDeviceToDevice, h->st));

@@ -467,6 +467,26 @@ def test_initial_guess_reaches_the_same_fixed_point(B, guess):
     assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
 
 
+@pytest.mark.parametrize("graphs,family,s", [(1, "gauss", 2), (0, "gauss", 3), (1, "sdirk", 2),
+                                              (1, "radau", 3)])
+def test_bad_warm_start_restarts_from_zero(B, graphs, family, s):
+    """A warm start whose residual exceeds that of zero stages (here: stages
+    set to large noise) is rejected and the step restarts from zero, from the
+    saved state: it still reaches the oracle's solution (graph path, host
+    path, and the stage solver of stage-by-stage SDIRK)."""
+    op, n, nu, dt = "burgers2d", 32, 5e-3, 2e-3
+    p, _ = make_problem(op, n, nu, s)
+    u0 = initial(op, n, 13)
+    with B.IrkSolver(u0, op=op, n=n, stages=s, nu=nu, family=family, use_graphs=graphs) as sol:
+        bad = 1e3 * np.random.default_rng(0).standard_normal((s,) + u0.shape)
+        sol.set_stages(np.ascontiguousarray(bad))
+        st = sol.step(0.0, dt, 1).as_dict()
+        got = sol.state()
+    want, _, _ = oracle_step(p, s, u0, 0.0, dt, family)
+    assert rel(got, want) <= STEP_TOL, (rel(got, want), st)
+    assert st["final_rel_res"] <= 1e-10, st
+
+
 @pytest.mark.parametrize("op,n,s,family", [("burgers2d", 64, 3, "gauss"), ("vsf", 64, 5, "gauss"),
                                            ("burgers2d", 64, 3, "radau"), ("burgers1d", 256, 4, "gauss")])
 def test_extrapolated_guess_saves_iterations(B, op, n, s, family):
