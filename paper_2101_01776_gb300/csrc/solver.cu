@@ -2242,8 +2242,8 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
   CK(cudaMemcpyAsync(h->u, u0, sizeof(double) * (c.op == IRK_OP_VSF_2D ? h->npts : h->L),
                      u0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
   if (c.op == IRK_OP_VSF_2D) {
-    // consistent psi: -L psi = omega (zero mean) by MG-preconditioned FGMRES-free
-    // defect correction with the Poisson V-cycle, to a relative residual of 1e-14
+    // consistent psi: -L psi = omega (zero mean) by defect correction with the
+    // Poisson V-cycle, to a relative residual of 1e-14
     // or, on fine grids, the rounding floor of -L_h psi in FP64 (about
     // 4e-16 / h^2 relative): the loop stops once a V-cycle no longer halves a
     // defect that is already below 1e-9
@@ -2255,31 +2255,19 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
     const int save_prec = h->prec;
     double prev_dn = 0;
     for (int it = 0; it < 200 && bnorm > 0; ++it) {
-      // defect d = omega - (-L psi) in tmp; via the row operator with x = (0, psi)
-      StageOpArgs a;
-      memset(&a, 0, sizeof(a));
-      a.nrow = 1;
-      a.dt = 1.0;
-      // Jlin of VSF on x = (0, psi): psi row = -(0) - L psi; row scaled by -dt -> L psi ... use tmp2 as zeros
-      CK(cudaMemsetAsync(h->zbuf, 0, sizeof(double) * h->npts, h->st));
-      CK(cudaMemcpyAsync(h->zbuf + h->npts, psi, sizeof(double) * h->npts, cudaMemcpyDeviceToDevice, h->st));
-      a.row[0].y = h->w;
-      a.row[0].sigma = 1;
-      a.row[0].nterm = 1;
-      a.row[0].t[0].x = h->zbuf;
-      a.row[0].t[0].combo = nullptr;
-      a.row[0].t[0].m = 0;
-      a.row[0].t[0].lin = 1;
-      run_stage_op(h, a);  // w_psi = -dt * (-L psi) = L psi
-      // defect = omega + L psi  (since -L psi should equal omega)
-      launch_axpby(h->w + h->npts, 1.0, h->u, 1.0, h->npts, h->st);
+      // defect d = omega - (-L_h psi) in w
+      {
+        ProfScope ps(h, P_POISSON, 16.0 * h->npts, 6.0 * h->npts);
+        launch_neg_laplacian(h->g, psi, h->w, h->st);
+      }
+      launch_axpby(h->w, 1.0, h->u, -1.0, h->npts, h->st);
       double dn = 0;
-      TRY(dev_norm(h, h->w + h->npts, h->npts, &dn));
+      TRY(dev_norm(h, h->w, h->npts, &dn));
       if (dn <= 1e-14 * bnorm) break;
       if (it > 0 && dn > 0.5 * prev_dn && dn <= 1e-9 * bnorm) break;
       prev_dn = dn;
       h->prec = IRK_MG_FP64;
-      vcycle(h, -1, MG_DIFFUSION, 1, 0.0, 0.0, 1.0, 1, h->w + h->npts, h->tmp);
+      vcycle(h, -1, MG_DIFFUSION, 1, 0.0, 0.0, 1.0, 1, h->w, h->tmp);
       h->prec = save_prec;
       launch_axpby(psi, 1.0, h->tmp, 1.0, h->npts, h->st);
     }
