@@ -412,11 +412,12 @@ __device__ double forcing_term(double rel, double prev_rel, double fn, double pr
   return fmax(eta, 1e-13);
 }
 
-__global__ void k_newton_first(double* nw, const double* __restrict__ f2, double* rtol_slot,
-                               double newton_rtol, double krylov_rtol,
+__global__ void k_newton_first(double* nw, const double* __restrict__ f2, double f2_scale,
+                               double* rtol_slot, double newton_rtol, double krylov_rtol,
                                cudaGraphConditionalHandle cond) {
-  // f2 is tested before any clamp: fmax(NaN, 0) would read as zero
-  const double f0 = isfinite(f2[0]) ? sqrt(fmax(f2[0], 0.0)) : f2[0];
+  // f2 is tested before any clamp: fmax(NaN, 0) would read as zero; f2_scale
+  // = s when f2 holds one of s equal stage residuals
+  const double f0 = isfinite(f2[0]) ? sqrt(fmax(f2_scale * f2[0], 0.0)) : f2[0];
   nw[0] = f0;
   nw[1] = f0;
   nw[2] = f0 > 0.0 ? 1.0 : 0.0;
@@ -449,7 +450,7 @@ __global__ void k_newton_ctl(double* nw, const double* __restrict__ f2, double* 
   int stop = 1;
   if (!isfinite(fn)) nw[5] = (double)IRK_ERR_NEWTON_DIVERGED;
   else if (rel <= newton_rtol || nw[0] == 0.0) nw[5] = 0.0;
-  else if (count == 0 && rel > 1.0) nw[5] = (double)kGuessRejected;  // warm start worse than zero
+  else if (count == 0 && rel > kGuessLimit) nw[5] = (double)kGuessRejected;  // worse than zero
   else if (it >= maxit) nw[5] = (double)IRK_ERR_NEWTON_MAXIT;
   else if (rel > 1e3) nw[5] = (double)IRK_ERR_NEWTON_DIVERGED;
   else stop = 0;
@@ -476,9 +477,10 @@ void launch_zero_if_unforced(const double* nw, double* K, long long len, cudaStr
   k_zero_if_unforced<<<blas_blocks(len), IRK_BLAS_THREADS, 0, st>>>(nw, K, len);
 }
 
-void launch_newton_first(double* nw, const double* f2, double* rtol_slot, double newton_rtol,
-                         double krylov_rtol, cudaGraphConditionalHandle cond, cudaStream_t st) {
-  k_newton_first<<<1, 1, 0, st>>>(nw, f2, rtol_slot, newton_rtol, krylov_rtol, cond);
+void launch_newton_first(double* nw, const double* f2, double f2_scale, double* rtol_slot,
+                         double newton_rtol, double krylov_rtol, cudaGraphConditionalHandle cond,
+                         cudaStream_t st) {
+  k_newton_first<<<1, 1, 0, st>>>(nw, f2, f2_scale, rtol_slot, newton_rtol, krylov_rtol, cond);
 }
 
 void launch_newton_ctl(double* nw, const double* f2, double* rtol_slot, double newton_rtol,

@@ -33,6 +33,9 @@ int build_tableau(int family, int s, int basis, HostTableau* t, char* err, size_
 // Internal Newton status of the device loop: the warm-start guess has a
 // larger residual than zero stages; the step restarts from zero.
 constexpr int kGuessRejected = 100;
+// a warm start counts as worse than zero stages above this ||F(guess)|| / ||F(0)||
+// (margin over 1: the two norms are summed in different orders)
+constexpr double kGuessLimit = 1.001;
 // The single-stage tableau A = [gamma], b = [1], c = [0] (one SDIRK stage
 // solved on its own); nonzero for gamma <= 0.
 int build_tableau_single(double gamma, HostTableau* t);
@@ -190,8 +193,9 @@ void launch_fg_scale(const double* w, const FGState* s, double* V, long long ldv
                      long long L, cudaStream_t st);
 void launch_fg_solve(FGState* s, cudaStream_t st);
 void launch_zero_if_unforced(const double* nw, double* K, long long len, cudaStream_t st);
-void launch_newton_first(double* nw, const double* f2, double* rtol_slot, double newton_rtol,
-                         double krylov_rtol, cudaGraphConditionalHandle cond, cudaStream_t st);
+void launch_newton_first(double* nw, const double* f2, double f2_scale, double* rtol_slot,
+                         double newton_rtol, double krylov_rtol, cudaGraphConditionalHandle cond,
+                         cudaStream_t st);
 void launch_newton_ctl(double* nw, const double* f2, double* rtol_slot, double newton_rtol,
                        int maxit, double krylov_rtol, cudaGraphConditionalHandle cond, int count,
                        cudaStream_t st);

@@ -1060,6 +1060,39 @@ void launch_eval_residual(irk_handle* h, double t_n, double dt, const double* K,
   }
 }
 
+// ||F(k = 0)||^2 into dscal[201], the reference of the Newton tolerance.  With
+// k = 0 every stage reads Y_i = u_n, so for an autonomous N the s stage
+// residuals are all -N(u_n) (and -G(u_n) on the DAE constraint rows): one stage
+// is evaluated and f0_scale(h) = s multiplies its square norm.  A time-
+// dependent source takes the full evaluation (scale 1).
+double f0_scale(const irk_handle* h) { return h->cfg.forcing ? 1.0 : (double)h->s; }
+
+void launch_f0_norm(irk_handle* h, double t_n, double dt) {
+  if (h->cfg.forcing) {
+    cudaMemsetAsync(h->yhat, 0, sizeof(double) * h->s * h->L, h->st);
+    launch_eval_residual(h, t_n, dt, h->yhat, h->rhs, nullptr, false);
+    return;
+  }
+  cudaMemsetAsync(h->yhat, 0, sizeof(double) * h->L, h->st);
+  ResidualArgs ra;
+  memset(&ra, 0, sizeof(ra));
+  ra.s = 1;
+  ra.Q[0] = 1.0;
+  ra.tstage[0] = t_n;
+  ra.Y = h->u;
+  ra.K = h->yhat;
+  ra.partials = h->partials;
+  const int nb = residual_blocks(h->g);
+  {
+    ProfScope ps(h, P_RESID, 16.0 * h->L, h->npts * (n_flops_per_point(h->g.op) + 4.0 * h->C));
+    launch_residual(h->g, ra, h->st);
+  }
+  {
+    ProfScope ps(h, P_REDUCE, 8.0 * nb, nb);
+    launch_reduce(h->partials, nb, 1, 1, h->dscal + 201, h->st);
+  }
+}
+
 irk_status eval_residual(irk_handle* h, double t_n, double dt, const double* K, double* rhs,
                          double* Fraw, bool combos, double* fnorm) {
   launch_eval_residual(h, t_n, dt, K, rhs, Fraw, combos);
@@ -1343,12 +1376,11 @@ irk_status build_step_graph(irk_handle* h, double dt) {
     if (h->cfg.initial_guess >= 1) {
       // ||F(k=0)|| fixes the tolerance; Newton then starts from the previous
       // stages, extrapolated along the collocation polynomial (guess 2)
-      cudaMemsetAsync(h->yhat, 0, sizeof(double) * s * h->L, h->st);
-      launch_eval_residual(h, 0.0, dt, h->yhat, h->rhs, nullptr, false);
+      launch_f0_norm(h, 0.0, dt);
       {
         ProfScope ps(h, P_SCALE, 0, 0);
-        launch_newton_first(h->nws, h->dscal + 201, h->dscal + 300, h->cfg.newton_rtol,
-                            h->cfg.krylov_rtol, ncond, h->st);
+        launch_newton_first(h->nws, h->dscal + 201, f0_scale(h), h->dscal + 300,
+                            h->cfg.newton_rtol, h->cfg.krylov_rtol, ncond, h->st);
       }
       if (use_extrapolation(h)) {
         ProfScope ps(h, P_UPDATE, 16.0 * h->L * s, 2.0 * h->L * s * s);
@@ -1369,7 +1401,7 @@ irk_status build_step_graph(irk_handle* h, double dt) {
       launch_eval_residual(h, 0.0, dt, h->K, h->rhs, nullptr, true);
       {
         ProfScope ps(h, P_SCALE, 0, 0);
-        launch_newton_first(h->nws, h->dscal + 201, h->dscal + 300, h->cfg.newton_rtol,
+        launch_newton_first(h->nws, h->dscal + 201, 1.0, h->dscal + 300, h->cfg.newton_rtol,
                             h->cfg.krylov_rtol, ncond, h->st);
       }
     }
@@ -1488,7 +1520,8 @@ irk_status graph_step(irk_handle* h, double dt) {
     CK(cudaStreamSynchronize(h->st));
   }
   const int its = (int)nw[4];
-  const int status = (int)nw[5];
+  // zero stages cannot be rejected again (ratio 1); if they were, report divergence
+  const int status = ((int)nw[5] == kGuessRejected) ? (int)IRK_ERR_NEWTON_DIVERGED : (int)nw[5];
   h->stats.newton_its += its;
   h->stats.max_newton_its = std::max(h->stats.max_newton_its, its);
   h->stats.final_rel_res = nw[2];
@@ -1830,8 +1863,9 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
   if (h->cfg.initial_guess >= 1) {
     // ||F(k=0)|| fixes the tolerance; Newton then starts from the previous
     // stages, extrapolated along the collocation polynomial (guess 2)
-    CK(cudaMemsetAsync(h->yhat, 0, sizeof(double) * s * h->L, h->st));
-    TRY(eval_residual(h, t_n, dt, h->yhat, h->rhs, nullptr, false, &f0));
+    launch_f0_norm(h, t_n, dt);
+    TRY(sync_read(h, h->dscal + 201, 1));
+    f0 = std::sqrt(f0_scale(h) * h->hbuf[0]);
     if (use_extrapolation(h)) {
       ProfScope ps(h, P_UPDATE, 16.0 * h->L * s, 2.0 * h->L * s * s);
       launch_stage_extrapolate(h->L, s, h->dscal + kExtrapSlot, h->K, h->st);
@@ -1843,7 +1877,7 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
   int it = 0;
   for (;; ++it) {
     TRY(eval_residual(h, t_n, dt, h->K, h->rhs, h->fo, true, &fn));
-    if (it == 0 && h->cfg.initial_guess >= 1 && f0 > 0 && fn > f0) {
+    if (it == 0 && h->cfg.initial_guess >= 1 && f0 > 0 && fn > kGuessLimit * f0) {
       // the warm start is worse than zero stages: start from zero instead
       CK(cudaMemsetAsync(h->K, 0, sizeof(double) * s * h->L, h->st));
       TRY(eval_residual(h, t_n, dt, h->K, h->rhs, h->fo, true, &fn));
