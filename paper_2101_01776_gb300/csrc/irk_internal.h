@@ -224,6 +224,10 @@ bool mg_smooth3_pays(int prec, int dim, const MGLevelDesc& lv);
 // The four off-diagonal coefficients of the 2D advective level operator,
 // coef = (beta + alpha a_x, beta - alpha a_x, beta + alpha a_y, beta - alpha a_y)
 // with alpha = cadv/(2h), beta = -cdiff/h^2, from the level velocity vel (2 fields)
+// Velocity and coefficients of the two finest 2D levels in one launch (FP64)
+void launch_mg_setup2(const MGLevelDesc& fine, const MGLevelDesc& coarse, double cadv, double cdiff,
+                      const double* combo, void* vel0, void* coef0, void* vel1, void* coef1,
+                      cudaStream_t st);
 void launch_mg_coef(int prec, const MGLevelDesc& lv, double cadv, double cdiff, const void* vel,
                     void* coef, cudaStream_t st);
 // The bottom of a periodic 2D Poisson V-cycle (levels lv.n = 32 or 16 down to

@@ -1071,6 +1071,61 @@ void launch_mg_prolong_set(int prec, int dim, const MGLevelDesc& fine, int ncomp
   });
 }
 
+// Velocity and stencil coefficients of the two finest levels in one pass
+// (FP64 storage, 2D, velocity = the combined field itself): each coarse point
+// writes, for the 2 x 2 fine points it owns, the velocity and the four
+// coefficients beta +- alpha a (the values k_velocity and k_mg_coef store),
+// and for itself the full-weighted velocity (k_mg_restrict's operation order)
+// and its coefficients.  One launch instead of four per row.
+__global__ void __launch_bounds__(256) k_mg_setup2(MGLevelDesc fine, const double* __restrict__ combo,
+                                                   double* __restrict__ vel0,
+                                                   double* __restrict__ coef0,
+                                                   double* __restrict__ vel1,
+                                                   double* __restrict__ coef1, double a0, double b0,
+                                                   double a1, double b1) {
+  const int nc = fine.n >> 1, logc = fine.logn - 1, m = fine.n - 1, lf = fine.logn;
+  const int ncpts = nc * nc, npts = fine.npts;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < ncpts; p += gridDim.x * blockDim.x) {
+    const int I = p & (nc - 1), J = p >> logc;
+    const int i = 2 * I, j = 2 * J;
+    const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m;
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      const double* f = combo + (long long)c * npts;
+      double* v0 = vel0 + (long long)c * npts;
+      double* cp0 = coef0 + (long long)(2 * c) * npts;  // (e, w) for x, (n, s) for y
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int o = ((j + (q >> 1)) << lf) + i + (q & 1);
+        const double a = __ldg(f + o);
+        v0[o] = a;
+        cp0[o] = fma(a0, a, b0);
+        cp0[npts + o] = fma(-a0, a, b0);
+      }
+      const double centre = __ldg(f + (j << lf) + i);
+      const double edges = __ldg(f + (j << lf) + ip) + __ldg(f + (j << lf) + im) +
+                           __ldg(f + (jp << lf) + i) + __ldg(f + (jm << lf) + i);
+      const double corners = __ldg(f + (jp << lf) + ip) + __ldg(f + (jp << lf) + im) +
+                             __ldg(f + (jm << lf) + ip) + __ldg(f + (jm << lf) + im);
+      const double v = (4.0 * centre + 2.0 * edges + corners) * 0.0625;
+      vel1[(long long)c * ncpts + p] = v;
+      coef1[(long long)(2 * c) * ncpts + p] = fma(a1, v, b1);
+      coef1[(long long)(2 * c + 1) * ncpts + p] = fma(-a1, v, b1);
+    }
+  }
+}
+
+void launch_mg_setup2(const MGLevelDesc& fine, const MGLevelDesc& coarse, double cadv, double cdiff,
+                      const double* combo, void* vel0, void* coef0, void* vel1, void* coef1,
+                      cudaStream_t st) {
+  const MGConst k0 = mg_const(fine, 2, 0.0, cadv, cdiff, 1.0);
+  const MGConst k1 = mg_const(coarse, 2, 0.0, cadv, cdiff, 1.0);
+  const long long nc = (long long)(fine.n / 2) * (fine.n / 2);
+  k_mg_setup2<<<grid_for(nc), 256, 0, st>>>(fine, combo, (double*)vel0, (double*)coef0,
+                                            (double*)vel1, (double*)coef1, k0.alpha, k0.beta,
+                                            k1.alpha, k1.beta);
+}
+
 void launch_mg_coef(int prec, const MGLevelDesc& lv, double cadv, double cdiff, const void* vel,
                     void* coef, cudaStream_t st) {
   const MGConst k = mg_const(lv, 2, 0.0, cadv, cdiff, 1.0);

@@ -427,17 +427,25 @@ void mg_setup(irk_handle* h, double dt) {
   if (h->g.op == IRK_OP_DIFFUSION_1D) return;
   for (int k = 0; k < h->s; ++k) {
     const int depth = mg_depth(h, row_shift(h, k), dt * h->g.nu);
-    {
+    // FP64 Burgers-2D rows: the two finest levels' velocity and coefficients
+    // in one launch (the same values as the separate kernels below)
+    const bool fused = h->g.op == IRK_OP_BURGERS_2D && h->use_pre && depth >= 2;
+    if (fused) {
+      const double n0 = h->lev[0].d.npts;
+      ProfScope ps(h, P_MG_SETUP, 8.0 * (2.0 + 6.0 + 6.0 / 4.0) * n0, 4.0 * n0 * 1.25 + 5.0 * n0);
+      launch_mg_setup2(h->lev[0].d, h->lev[1].d, dt, dt * h->g.nu, combo_ptr(h, k, k),
+                       h->vel[k][0], h->coefh[k][0], h->vel[k][1], h->coefh[k][1], h->st);
+    } else {
       ProfScope ps(h, P_MG_SETUP, 8.0 * h->L + mg_level_bytes(h, 0, h->dim), 0);
       launch_velocity_from_combo(h->g, combo_ptr(h, k, k), h->vel[k][0], h->prec, h->st);
     }
-    for (int l = 0; l + 1 < depth; ++l) {
+    for (int l = fused ? 1 : 0; l + 1 < depth; ++l) {
       ProfScope ps(h, P_MG_SETUP, mg_level_bytes(h, l, h->dim) * 1.25, 0);
       launch_mg_restrict(h->prec, h->dim, h->lev[l].d, h->dim, h->vel[k][l], h->vel[k][l + 1],
                          h->st);
     }
     if (h->use_pre)
-      for (int l = 0; l < depth; ++l) {
+      for (int l = fused ? 2 : 0; l < depth; ++l) {
         ProfScope ps(h, P_MG_SETUP, mg_level_bytes(h, l, 6.0), 4.0 * h->lev[l].d.npts);
         launch_mg_coef(h->prec, h->lev[l].d, dt, dt * h->g.nu, h->vel[k][l], h->coefh[k][l],
                        h->st);
