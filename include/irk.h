@@ -103,12 +103,13 @@ typedef struct {
   double krylov_rtol;   /* loosest FGMRES relative tolerance per block; default 1e-3 */
   int krylov_restart;   /* FGMRES(m) restart length m, 1..64; default 30 */
   int krylov_maxit;     /* total FGMRES iterations per block solve; default 200 */
-  int nonlinear_variant;/* nonlinear iteration (Sec. 3.2); default 3:
+  int nonlinear_variant;/* nonlinear iteration (Sec. 3.2); default 2:
                            0 simplified Newton: every diagonal block uses the
                              Jacobian at the last stage state;
                            1 block diagonal, each block lumped onto the stage
                              of its largest d-vector entry;
-                           2 block diagonal (d_ii^T L-hat);
+                           2 block diagonal (d_ii^T L-hat); the same as 3 for
+                             2-stage Gauss (Q0 = I) and SDIRK (no coupling);
                            3 block upper triangular within the pattern of R0
                              (exact Newton for s = 2);
                            4 exact Newton: an outer FGMRES on the true stage
