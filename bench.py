@@ -472,7 +472,8 @@ def run_ours(args, rank, world):
             "krylov_its_per_step": tot3["krylov_its"] / args.steps,
             "chosen": {"mg_shifted_sweeps": chosen.mg_shifted_sweeps,
                        "mg_coarse_smoother": chosen.mg_coarse_smoother,
-                       "mg_coarse_reduction": chosen.mg_coarse_reduction}}
+                       "mg_coarse_reduction": chosen.mg_coarse_reduction,
+                       "mg_tile_rows": chosen.mg_tile_rows, "mg_levels": chosen.mg_levels}}
         if args.serving_requests > 0:
             # 8 slots: the lowest step latency at the mix's throughput (16
             # slots measured the same steps/s at 4x the p50 step latency);

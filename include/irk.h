@@ -167,6 +167,9 @@ typedef struct {
                            vsf-system-2: FGMRES on the omega block to
                            krylov_rtol, then one MG-preconditioned FGMRES
                            Poisson solve per stream function row */
+  int mg_tile_rows;     /* rows of the 32-wide tiles of the three-sweep V-cycle
+                           kernel: 0 (default) = 16 with FP64 storage, 8
+                           otherwise; 8 or 16 to fix it (an autotuner knob) */
 } irk_config;
 
 typedef struct {

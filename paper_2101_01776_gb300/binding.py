@@ -49,6 +49,7 @@ class IrkConfig(C.Structure):
         ("profile", C.c_int), ("use_graphs", C.c_int), ("initial_guess", C.c_int),
         ("basis", C.c_int), ("mg_shifted_sweeps", C.c_int), ("mg_coarse_reduction", C.c_double),
         ("mg_coarse_smoother", C.c_int), ("dirk_sequential", C.c_int), ("dae_solver", C.c_int),
+        ("mg_tile_rows", C.c_int),
     ]
 
 

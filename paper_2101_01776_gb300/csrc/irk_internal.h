@@ -239,7 +239,8 @@ void launch_mg_bottom(int prec, const MGLevelDesc& lv, double cdiff, double omeg
 // single sweeps: w_in -> w_out (w_in unused when first: w = 0)
 void launch_mg_smooth3(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
                        double cadv, double cdiff, double omega, const void* vel, const void* b,
-                       const void* w_in, void* w_out, int first, cudaStream_t st);
+                       const void* w_in, void* w_out, int first, cudaStream_t st,
+                       int tile_rows = 0);
 // One undamped red-black Gauss-Seidel sweep (2D, n >= 32): w_in -> w_out
 // (w_in unused when first: w = 0)
 void launch_mg_rbgs(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,

@@ -975,13 +975,13 @@ void launch_mg_rbgs(int prec, int kind, const MGLevelDesc& lv, int ncomp, double
 
 void launch_mg_smooth3(int prec, int kind, const MGLevelDesc& lv, int ncomp, double sigma,
                        double cadv, double cdiff, double omega, const void* vel, const void* b,
-                       const void* w_in, void* w_out, int first, cudaStream_t st) {
+                       const void* w_in, void* w_out, int first, cudaStream_t st, int tile_rows) {
   const MGConst k = mg_const(lv, 2, sigma, cadv, cdiff, omega);
   const int zsplit = (lv.n <= 256) ? ncomp : 1;
   // FP64: 32 x 16 tiles, whose sweeps update 1.20x the tile's points against
   // 1.34x for 32 x 8 (the class got 4-6% faster on the 256^2 level); FP32 and
   // BF16 keep 32 x 8, where twice the CTAs measured slightly ahead
-  const bool tall = (prec == IRK_MG_FP64);
+  const bool tall = tile_rows == 16 || (tile_rows == 0 && prec == IRK_MG_FP64);
   const int ty = tall ? 16 : kTY;
   const dim3 grid(lv.n / kTX, lv.n / ty, zsplit), block(kTX, ty);
 #define IRK_S3(TY_)                                                                               \

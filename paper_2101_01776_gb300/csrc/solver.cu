@@ -516,7 +516,7 @@ bool jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, doub
       ProfScope ps(h, P_MG_SMOOTH2, mg_level_bytes(h, l, (first ? 2.0 : 3.0) * ncomp + velf),
                    first ? f0 + 2.0 * fsw : 3.0 * fsw);
       launch_mg_smooth3(prec, kind, d, ncomp, sigma, cadv, cdiff, om, vel, b, cur, dst, first,
-                        h->st);
+                        h->st, h->cfg.mg_tile_rows);
       sw += 3;
     } else if (sw + 1 < sweeps && mg_smooth2_pays(prec, dim, kind, d, first) && !(ends_pair && last == b)) {
       if (ends_pair && last) dst = last;
@@ -2015,6 +2015,7 @@ irk_status validate(const irk_config* c, std::string& err) {
   if (c->mg_shifted_sweeps < 0 || c->mg_shifted_sweeps > 8) { err = "mg_shifted_sweeps out of range"; return IRK_ERR_INVALID; }
   if (!(c->mg_coarse_reduction >= 0 && c->mg_coarse_reduction < 1)) { err = "mg_coarse_reduction must be in [0, 1)"; return IRK_ERR_INVALID; }
   if (c->mg_coarse_smoother < 0 || c->mg_coarse_smoother > 2) { err = "mg_coarse_smoother must be 0..2"; return IRK_ERR_INVALID; }
+  if (c->mg_tile_rows != 0 && c->mg_tile_rows != 8 && c->mg_tile_rows != 16) { err = "mg_tile_rows must be 0, 8 or 16"; return IRK_ERR_INVALID; }
   if (c->mg_levels < 0 || c->mg_levels > IRK_MAX_LEVELS) { err = "mg_levels out of range"; return IRK_ERR_INVALID; }
   return IRK_OK;
 }
@@ -2682,6 +2683,8 @@ irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_con
       h->inner->cfg.mg_shifted_sweeps = h->cfg.mg_shifted_sweeps;
       h->inner->cfg.mg_coarse_smoother = h->cfg.mg_coarse_smoother;
       h->inner->cfg.mg_coarse_reduction = h->cfg.mg_coarse_reduction;
+      h->inner->cfg.mg_tile_rows = h->cfg.mg_tile_rows;
+      h->inner->cfg.mg_levels = h->cfg.mg_levels;
       invalidate_graphs(h->inner);
     }
     TRY(restore());
@@ -2705,15 +2708,28 @@ irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_con
     double best = 0;
     st = measure(&best);
     if (st != IRK_OK) break;
-    // coordinate descent over the multigrid knobs of the V-cycle preconditioner
+    // coordinate descent over the multigrid knobs of the V-cycle preconditioner:
+    // sweeps on shift-dominated rows, the coarsest-level smoother and its
+    // target, the tile height of the three-sweep kernel, and the V-cycle
+    // depth (the automatic depth of the first row against one level deeper)
     struct Knob { int which; double vals[2]; };
-    const Knob knobs[3] = {{0, {1, 2}}, {1, {0, 2}}, {2, {2e-2, 5e-3}}};
+    const int d0 = mg_depth(h, row_shift(h, 0), dt * h->g.nu);
+    const double deeper = (h->cfg.mg_levels == 0 && d0 + 1 <= h->nlev) ? d0 + 1 : 0;
+    const int auto_rows = (h->prec == IRK_MG_FP64) ? 16 : 8;
+    const Knob knobs[5] = {{0, {1, 2}}, {1, {0, 2}}, {2, {2e-2, 5e-3}}, {3, {8, 16}},
+                           {4, {0, deeper}}};
     for (const Knob& kn : knobs) {
       for (double v : kn.vals) {
         irk_config trial = h->cfg;
         if (kn.which == 0) { if (trial.mg_shifted_sweeps == (int)v) continue; trial.mg_shifted_sweeps = (int)v; }
         if (kn.which == 1) { if (trial.mg_coarse_smoother == (int)v) continue; trial.mg_coarse_smoother = (int)v; }
         if (kn.which == 2) { if (trial.mg_coarse_reduction == v) continue; trial.mg_coarse_reduction = v; }
+        if (kn.which == 3) {
+          const int now = trial.mg_tile_rows ? trial.mg_tile_rows : auto_rows;
+          if (now == (int)v) continue;
+          trial.mg_tile_rows = (int)v;
+        }
+        if (kn.which == 4) { if (trial.mg_levels == (int)v) continue; trial.mg_levels = (int)v; }
         const irk_config keep = h->cfg;
         h->cfg = trial;
         double ms = 0;

@@ -135,7 +135,7 @@ def test_invalid_configs_rejected_before_device(B):
            dict(op="vsf", mass=0), dict(op="burgers1d", mass=1), dict(family=4),
            dict(family=3, stages=4), dict(family=3, stages=2, basis=1), dict(dirk_sequential=2),
            dict(dae_solver=2), dict(dae_solver=1), dict(dae_solver=-1),
-           dict(initial_guess=3), dict(initial_guess=-1),
+           dict(initial_guess=3), dict(initial_guess=-1), dict(mg_tile_rows=7), dict(mg_tile_rows=-8),
            dict(family=-1), dict(family=2, stages=1), dict(basis=2), dict(basis=-1),
            dict(krylov_restart=0), dict(krylov_restart=65), dict(nonlinear_variant=5),
            dict(nonlinear_variant=-1), dict(mg_precision=3), dict(forcing=1, op="burgers2d"),

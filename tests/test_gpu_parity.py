@@ -196,7 +196,8 @@ def test_mixed_precision_fine_level_reads_fp64(B, op, n, s, prec):
 @pytest.mark.parametrize("kw", [dict(gamma_mode=1), dict(nonlinear_variant=2),
                                 dict(krylov_restart=3), dict(mg_levels=2),
                                 dict(mg_coarse_smoother=2), dict(mg_coarse_smoother=1),
-                                dict(mg_shifted_sweeps=0)])
+                                dict(mg_shifted_sweeps=0), dict(mg_tile_rows=8),
+                                dict(mg_tile_rows=16, mg_precision=1), dict(nonlinear_variant=3)])
 def test_solver_variants_reach_same_fixed_point(B, kw):
     per_step, whole, _ = run_parity(B, "burgers2d", 32, 3, 5e-3, 2e-3, 2, seed=4, **kw)
     assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (kw, per_step, whole)
@@ -577,6 +578,8 @@ def test_autotune_restores_state_and_keeps_parity(B):
         assert got.mg_shifted_sweeps == chosen.mg_shifted_sweeps in (1, 2)
         assert got.mg_coarse_smoother == chosen.mg_coarse_smoother in (0, 2)
         assert got.mg_coarse_reduction in (2e-2, 5e-3)
+        assert got.mg_tile_rows == chosen.mg_tile_rows in (0, 8, 16)
+        assert got.mg_levels == chosen.mg_levels and got.mg_levels >= 0
         sol.step(dt, dt, 1)
         u2 = sol.state()
     want, _, _ = oracle_step(p, s, u1, dt, dt)
