@@ -274,11 +274,11 @@ def test_linear_diffusion_pade_radau_lobatto(B, family, s, k):
     assert rel(u1[0], want) <= 1e-9
 
 
-@pytest.mark.parametrize("seq", [1, 0])
+@pytest.mark.parametrize("seq,guess", [(1, 2), (0, 2), (1, 0)])
 @pytest.mark.parametrize("op,n,s", [("burgers1d", 128, 1), ("burgers1d", 128, 2), ("burgers1d", 128, 3),
                                     ("burgers1d", 128, 5), ("burgers2d", 32, 3), ("burgers2d", 16, 5),
                                     ("vsf", 32, 2), ("vsf", 16, 3)])
-def test_sdirk_parity(B, op, n, s, seq):
+def test_sdirk_parity(B, op, n, s, seq, guess):
     """SDIRK, the diagonally implicit comparison of Sec. 7, stage by stage
     (seq = 1: every stage its own Newton loop on the single-stage solver) and
     coupled (seq = 0: Algorithm 1 over the stage system, whose transformed
@@ -286,7 +286,7 @@ def test_sdirk_parity(B, op, n, s, seq):
     solution of the full stage equations."""
     nu, dt = {"burgers1d": (0.01, 2e-3), "burgers2d": (5e-3, 2e-3), "vsf": (1e-3, 5e-3)}[op]
     per_step, whole, infos = run_parity(B, op, n, s, nu, dt, 2, seed=9, family="sdirk",
-                                        dirk_sequential=seq)
+                                        dirk_sequential=seq, initial_guess=guess)
     assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
     # 1x1 blocks only: one preconditioner application per Krylov iteration
     assert all(i["prec_apps"] == i["krylov_its"] > 0 for i in infos), infos
@@ -327,16 +327,17 @@ def test_sdirk_stage_by_stage_profile_and_kernel_stats(B):
         assert name in ks and ks[name]["launches"] > 0 and ks[name]["ms"] > 0, ks.keys()
 
 
-@pytest.mark.parametrize("n,s,family", [(32, 2, "gauss"), (32, 3, "gauss"), (16, 5, "gauss"),
-                                         (32, 1, "gauss"), (16, 3, "sdirk"), (32, 2, "radau")])
-def test_vsf_block_triangular_forward_solve_parity(B, n, s, family):
+@pytest.mark.parametrize("n,s,family,prec", [(32, 2, "gauss", 0), (32, 3, "gauss", 0), (16, 5, "gauss", 0),
+                                              (32, 1, "gauss", 0), (16, 3, "sdirk", 0), (32, 2, "radau", 0),
+                                              (32, 3, "gauss", 1), (32, 2, "gauss", 2)])
+def test_vsf_block_triangular_forward_solve_parity(B, n, s, family, prec):
     """Eq. vsf-system-2 (dae_solver = 1): the block forward solve of the
     reordered Picard system (FGMRES on the omega block with the omega part of
     L_P, then one MG-preconditioned Poisson FGMRES per stream function row)
     reaches the oracle's fixed point; the stream function V-cycles are
     counted apart from the omega V-cycles."""
     per_step, whole, infos = run_parity(B, "vsf", n, s, 1e-3, 5e-3, 2, seed=2, dae_solver=1,
-                                        family=family)
+                                        family=family, mg_precision=prec)
     assert max(per_step) <= STEP_TOL and whole <= RUN_TOL, (per_step, whole, infos)
     for i in infos:
         omega = i["vcycles"] - i["poisson_vcycles"]
