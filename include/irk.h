@@ -304,8 +304,9 @@ irk_status irk_get_config(const irk_handle* h, irk_config* out);
  * timed over `steps` IRK steps of size dt (after one untimed step that
  * captures its graphs), by CUDA events on the handle's stream; candidates
  * come by coordinate descent over mg_shifted_sweeps {1, 2},
- * mg_coarse_smoother {0, 2} and mg_coarse_reduction {2e-2, 5e-3}, starting
- * from the current settings, and the fastest is kept.  A candidate whose
+ * mg_coarse_smoother {0, 2}, mg_coarse_reduction {2e-2, 5e-3}, mg_tile_rows
+ * {8, 16} and mg_levels {0 (automatic), automatic depth + 1}, starting from
+ * the current settings, and the fastest is kept.  A candidate whose
  * step fails is skipped.  State and stages are restored afterwards, and the
  * statistics of the trial steps are discarded.  Allocates a backup of the
  * state and stages (cudaMalloc) for the duration of the call.  The choice
@@ -329,6 +330,21 @@ const char* irk_status_string(irk_status st);
 
 /* Release the handle and its device memory.  NULL-safe. */
 void irk_destroy(irk_handle* h);
+
+/* Bounds-checked debug build only (the library compiled with -DIRK_BOUNDS).
+ * There, the device index checks of the kernels (grid neighbours, multigrid
+ * tiles and transfers, Krylov basis columns) do not access memory out of
+ * range.  Each out-of-range index counts a hit in a per-source-file device
+ * record and is replaced by 0.  irk_step collects the records after every
+ * step and fails the step (IRK_ERR_CUDA, the first hit in irk_last_error) if
+ * any hit was recorded.  This call returns the hits recorded since the last
+ * collection and clears them.  It writes the first hit's file, line, index and
+ * extent to msg (msg_len bytes including the terminator; msg may be NULL).
+ * selftest != 0 first runs a one-thread kernel that checks index 1 against
+ * extent 1; the check records one hit and redirects the store to index 0.
+ * Returns -1 in the normal build (needs no GPU there), -2 if a CUDA call
+ * fails.  Not thread-safe: the records are global to the process. */
+long long irk_debug_bounds(int selftest, char* msg, size_t msg_len);
 
 #ifdef __cplusplus
 }

@@ -13,7 +13,9 @@ import os
 
 from . import build as _build
 
-_LIB_PATH = _build.LIB
+# IRK_LIBRARY selects another build of the same library (the bounds-checked
+# one, _lib/libirk_bounds.so); the default is the optimised build.
+_LIB_PATH = os.environ.get("IRK_LIBRARY") or _build.LIB
 
 IRK_OK = 0
 IRK_ERR_INVALID = 1
@@ -127,6 +129,7 @@ def _load():
         "irk_server_wait": (i, [vp, C.c_longlong, vp, P(IrkStats), vp]),
         "irk_server_stats_get": (i, [vp, P(IrkServerStats)]),
         "irk_server_destroy": (None, [vp]),
+        "irk_debug_bounds": (C.c_longlong, [i, C.c_char_p, sz]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -143,7 +146,7 @@ EXPORTED = (
     "irk_status_string", "irk_destroy", "irk_stage_residual_noalloc",
     "irk_config_device_bytes", "irk_create_in", "irk_server_create", "irk_server_submit",
     "irk_server_wait", "irk_server_stats_get", "irk_server_destroy", "irk_transform",
-    "irk_get_config", "irk_autotune", "irk_set_state_keep_stages",
+    "irk_get_config", "irk_autotune", "irk_set_state_keep_stages", "irk_debug_bounds",
 )
 
 
@@ -350,6 +353,14 @@ def irk_autotune(h, t_n: float, dt: float, steps: int = 2) -> IrkConfig:
     cfg = IrkConfig()
     _check(LIB.irk_autotune(h, t_n, dt, steps, C.byref(cfg)), h)
     return cfg
+
+
+def irk_debug_bounds(selftest: bool = False):
+    """(hits, message) of the bounds-checked build's device records since the
+    last call; hits is -1 in the normal build and -2 after a CUDA error."""
+    buf = C.create_string_buffer(256)
+    hits = LIB.irk_debug_bounds(int(selftest), buf, len(buf))
+    return hits, buf.value.decode(errors="replace")
 
 
 def irk_kernel_stats(h):

@@ -289,4 +289,16 @@ void launch_axpby(double* y, double a, const double* x, double b, long long L, c
   k_axpby<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(y, a, x, b, L);
 }
 
+#ifdef IRK_BOUNDS
+static __device__ double g_selftest_slot[1];
+
+__global__ void k_bounds_selftest(long long index, long long extent) {
+  g_selftest_slot[IRK_IDX(index, extent)] = 1.0;
+}
+
+void launch_bounds_selftest(cudaStream_t st) { k_bounds_selftest<<<1, 1, 0, st>>>(1, 1); }
+#endif
+
 }  // namespace irk
+
+IRK_BOUNDS_TU(blas)

@@ -123,6 +123,7 @@ __global__ void k_fg_scale(const double* __restrict__ w, const FGState* __restri
                            double* __restrict__ V, long long ldv, double* __restrict__ prec_in,
                            long long L) {
   const double sc = s->inv_scale;
+  IRK_CHECK(s->j, IRK_FG_MAXM + 1);
   double* vj = V + (long long)s->j * ldv;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
        p += (long long)gridDim.x * blockDim.x) {
@@ -135,6 +136,7 @@ __global__ void k_fg_scale(const double* __restrict__ w, const FGState* __restri
 // y = R^{-1} g on the leading k x k triangle
 __global__ void k_fg_solve(FGState* s) {
   const int k = s->k;
+  IRK_CHECK(k, IRK_FG_MAXM + 1);
   for (int i = k - 1; i >= 0; --i) {
     double acc = s->g[i];
     for (int q = i + 1; q < k; ++q) acc -= s->H[q * (IRK_FG_MAXM + 1) + i] * s->y[q];
@@ -147,6 +149,7 @@ __global__ void k_fg_lincomb(double* __restrict__ x, const double* __restrict__ 
                              const FGState* __restrict__ s, long long L) {
   __shared__ double ys[IRK_FG_MAXM];
   const int k = s->k;
+  IRK_CHECK(k, IRK_FG_MAXM + 1);
   for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = s->y[j];
   __syncthreads();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
@@ -210,6 +213,7 @@ k_fg_gs1(const double* __restrict__ V, long long ldv, FGState* s, const double* 
          long long L, double* __restrict__ partials, double* __restrict__ h1) {
   __shared__ double sh[17 * 8];
   const int nv = s->j + 1;
+  IRK_CHECK(s->j, IRK_FG_MAXM);
   switch (nv) {
 #define IRK_C(N) case N: gs1_body<N>(V, ldv, w, L, partials, sh); break;
     IRK_DEV_NV_CASES(IRK_C)
@@ -227,6 +231,8 @@ __device__ void arnoldi_step(FGState* s, const double* h1, const double* h2, int
                              double* its_total, cudaGraphConditionalHandle cond) {
   const int j = s->j;
   const int nv = j + 1;
+  IRK_CHECK(j, m);
+  IRK_CHECK(m - 1, IRK_FG_MAXM);
   double* Hc = s->H + j * (IRK_FG_MAXM + 1);
   double h2sq = 0.0;
   for (int i = 0; i <= j; ++i) {
@@ -301,6 +307,7 @@ k_fg_gs2(const double* __restrict__ V, long long ldv, FGState* s, const double* 
          int m, int maxit, double* its_total, cudaGraphConditionalHandle cond) {
   __shared__ double sh[17 * 8];
   const int nv = s->j + 1;
+  IRK_CHECK(s->j, IRK_FG_MAXM);
   switch (nv) {
 #define IRK_C(N) case N: gs2_body<N>(V, ldv, h1, w, L, partials, sh); break;
     IRK_DEV_NV_CASES(IRK_C)
@@ -356,6 +363,7 @@ k_fg_next(const double* __restrict__ V, long long ldv, FGState* s,
   if (s->stopped) return;
   const int nv = s->j;  // basis size before the new vector
   const double sc = s->inv_scale;
+  IRK_CHECK(s->j, IRK_FG_MAXM + 1);
   double* vn = Vout + (long long)s->j * ldv;
   switch (nv) {
 #define IRK_C(N) case N: next_body<N>(V, ldv, h2, sc, w, vn, prec_in, L); return;
@@ -505,3 +513,5 @@ void launch_fg_lincomb(double* x, const double* Z, long long ldz, const FGState*
 }
 
 }  // namespace irk
+
+IRK_BOUNDS_TU(fgmres)

@@ -2,10 +2,14 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/irk.h"
+#include "bounds.h"
 
 #define IRK_MAXS 5
 #define IRK_MAX_TERMS 5
@@ -15,6 +19,44 @@
 #define IRK_FG_MAXM 64
 
 namespace irk {
+
+#ifdef IRK_BOUNDS
+// per-translation-unit records of the bounds-checked build (bounds.h)
+int bounds_take_stencil(BoundsRecord* out);
+int bounds_take_mg(BoundsRecord* out);
+int bounds_take_blas(BoundsRecord* out);
+int bounds_take_fgmres(BoundsRecord* out);
+int bounds_take_noalloc(BoundsRecord* out);
+// one thread checks index 1 against extent 1 (one hit in blas.cu's record)
+// and stores through the checked index, which the check turns into 0
+void launch_bounds_selftest(cudaStream_t st);
+// Hits of every translation unit's record since the last collection (the
+// records are cleared), the first hit described in *msg; -1 when a CUDA call
+// fails.
+long long bounds_collect(std::string* msg);
+#endif
+
+// Host-side trace ranges in the NVTX domain "irk": API calls, steps, Newton
+// iterations, block solves, V-cycles.  With no tool attached (no
+// NVTX_INJECTION64_PATH) a push/pop is one indirect call to a no-op.  Inside a
+// captured CUDA graph the ranges mark the capture, not the replay.
+inline nvtxDomainHandle_t trace_domain() {
+  static nvtxDomainHandle_t d = nvtxDomainCreateA("irk");
+  return d;
+}
+struct TraceRange {
+  explicit TraceRange(const char* name) {
+    nvtxEventAttributes_t a = {};
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = name;
+    nvtxDomainRangePushEx(trace_domain(), &a);
+  }
+  ~TraceRange() { nvtxDomainRangePop(trace_domain()); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // A0^{-1} = T R T^{-1}: T = Q0 (orthogonal, T^{-1} = Q0^T) and R = R0 in the
 // real Schur basis; T = real eigenvectors and R block diagonal otherwise.

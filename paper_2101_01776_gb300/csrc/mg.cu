@@ -50,18 +50,24 @@ __device__ __forceinline__ LvIdx lv_nbr(const MGLevelDesc& lv, int p) {
   LvIdx r;
   r.c = p;
   const int m = lv.n - 1;
+  IRK_CHECK(p, lv.npts);
   if (DIM == 1) {
-    r.e = (p + 1) & m;
-    r.w = (p - 1) & m;
+    r.e = IRK_IDX((p + 1) & m, lv.npts);
+    r.w = IRK_IDX((p - 1) & m, lv.npts);
     r.n = r.s = p;
   } else {
     const int i = p & m, j = p >> lv.logn;
-    r.e = (j << lv.logn) + ((i + 1) & m);
-    r.w = (j << lv.logn) + ((i - 1) & m);
-    r.n = (((j + 1) & m) << lv.logn) + i;
-    r.s = (((j - 1) & m) << lv.logn) + i;
+    r.e = IRK_IDX((j << lv.logn) + ((i + 1) & m), lv.npts);
+    r.w = IRK_IDX((j << lv.logn) + ((i - 1) & m), lv.npts);
+    r.n = IRK_IDX((((j + 1) & m) << lv.logn) + i, lv.npts);
+    r.s = IRK_IDX((((j - 1) & m) << lv.logn) + i, lv.npts);
   }
   return r;
+}
+
+// Grid point (gx, gy) of a level with n = 2^ln points per side (2D tile kernels)
+__device__ __forceinline__ int tile_pt(int gx, int gy, int ln, int n) {
+  return ((int)IRK_IDX(gy, n) << ln) + (int)IRK_IDX(gx, n);
 }
 
 // Stencil of A at one point in coefficient form, A w = D w_c + sum_k c_k w_k
@@ -314,13 +320,13 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
       for (int q = tid; q < (kTY + 4) * (kTX + 4); q += kTX * kTY) {
         const int ly = q / (kTX + 4), lx = q - ly * (kTX + 4);
         const int gx = (x0 + lx - 2) & m, gy = (y0 + ly - 2) & m;
-        s_in[ly][lx] = ldv(w_in + off + (gy << ln) + gx);
+        s_in[ly][lx] = ldv(w_in + off + tile_pt(gx, gy, ln, n));
       }
     }
     for (int q = tid; q < NW; q += kTX * kTY) {
       const int ly = q / WX, lx = q - ly * WX;
       const int gx = (x0 + lx - 1) & m, gy = (y0 + ly - 1) & m;
-      const int gp = (gy << ln) + gx;
+      const int gp = tile_pt(gx, gy, ln, n);
       s_b[q] = ldv(b + off + gp);
       TC ce = beta, cw = beta, cn = beta, cs = beta;
       if (KIND == MG_ADVECTIVE) {
@@ -358,14 +364,14 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
       s_w1[ly][lx] = v;
       if (CHEB && lx >= 1 && lx <= kTX && ly >= 1 && ly <= kTY) {
         const int gx = (x0 + lx - 1) & m, gy = (y0 + ly - 1) & m;
-        stv<TS, TC>(w_mid + off + (gy << ln) + gx, v);
+        stv<TS, TC>(w_mid + off + tile_pt(gx, gy, ln, n), v);
       }
     }
     __syncthreads();
     // sweep 2 on the tile
     {
       const int lx = threadIdx.x, ly = threadIdx.y;
-      const int gp = ((y0 + ly) << ln) + x0 + lx;
+      const int gp = tile_pt(x0 + lx, y0 + ly, ln, n);
       const int sy = ly + 1, sx = lx + 1;
       const int q = sy * WX + sx;  // the tile point in the halo-1 window
       TC t = s_b[q];
@@ -414,12 +420,12 @@ __global__ void __launch_bounds__(kTX * TY) k_mg_smooth3(MGLevelDesc lv, int nco
       for (int q = tid; q < Y3 * X3; q += NT) {
         const int ly = q / X3, lx = q - ly * X3;
         const int gx = (x0 + lx - 3) & m, gy = (y0 + ly - 3) & m;
-        s_w0[ly][lx] = ldv(w_in + off + (gy << ln) + gx);
+        s_w0[ly][lx] = ldv(w_in + off + tile_pt(gx, gy, ln, n));
       }
     for (int q = tid; q < Y2 * X2; q += NT) {
       const int ly = q / X2, lx = q - ly * X2;
       const int gx = (x0 + lx - 2) & m, gy = (y0 + ly - 2) & m;
-      const int gp = (gy << ln) + gx;
+      const int gp = tile_pt(gx, gy, ln, n);
       s_b[q] = ldv(b + off + gp);
       TC ce = beta, cw = beta, cn = beta, cs = beta;
       if (KIND == MG_ADVECTIVE) {
@@ -474,7 +480,7 @@ __global__ void __launch_bounds__(kTX * TY) k_mg_smooth3(MGLevelDesc lv, int nco
       t = fma(-s_c[1][cq], s_w0[sy][sx - 1], t);
       t = fma(-s_c[2][cq], s_w0[sy + 1][sx], t);
       t = fma(-s_c[3][cq], s_w0[sy - 1][sx], t);
-      stv<TS, TC>(w_out + off + ((y0 + ly) << ln) + x0 + lx, fma(dinv, t, keep * s_w0[sy][sx]));
+      stv<TS, TC>(w_out + off + tile_pt(x0 + lx, y0 + ly, ln, n), fma(dinv, t, keep * s_w0[sy][sx]));
     }
     __syncthreads();
   }
@@ -515,7 +521,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_rbgs(MGLevelDesc lv, int ncomp
     for (int q = tid; q < (kTY + 4) * (kTX + 4); q += kTX * kTY) {
       const int ly = q / (kTX + 4), lx = q - ly * (kTX + 4);
       const int gx = (x0 + lx - 2) & m, gy = (y0 + ly - 2) & m;
-      s_w[ly][lx] = first ? TC(0) : ldv(w_in + off + (gy << ln) + gx);
+      s_w[ly][lx] = first ? TC(0) : ldv(w_in + off + tile_pt(gx, gy, ln, n));
     }
     __syncthreads();
     // red points of the halo-1 window: window row r (0..kTY+1), 17 per row;
@@ -525,7 +531,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_rbgs(MGLevelDesc lv, int ncomp
       const int cx = 2 * j + (r & 1);  // window column with cx + r even
       const int sy = r + 1, sx = cx + 1;  // position in s_w
       const int gx = (x0 + cx - 1) & m, gy = (y0 + r - 1) & m;
-      const int gp = (gy << ln) + gx;
+      const int gp = tile_pt(gx, gy, ln, n);
       TC ce, cw, cn, cs;
       coefs(gp, ce, cw, cn, cs);
       TC t = ldv(b + off + gp);
@@ -541,7 +547,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_rbgs(MGLevelDesc lv, int ncomp
       const int r = tid / (kTX / 2), j = tid - r * (kTX / 2);
       const int cx = 2 * j + ((r + 1) & 1);  // tile column with cx + r odd
       const int sy = r + 2, sx = cx + 2;
-      const int gp = ((y0 + r) << ln) + x0 + cx;
+      const int gp = tile_pt(x0 + cx, y0 + r, ln, n);
       TC ce, cw, cn, cs;
       coefs(gp, ce, cw, cn, cs);
       TC t = ldv(b + off + gp);
@@ -554,7 +560,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_rbgs(MGLevelDesc lv, int ncomp
     __syncthreads();
     {
       const int lx = threadIdx.x, ly = threadIdx.y;
-      stv<TS, TC>(w_out + off + ((y0 + ly) << ln) + x0 + lx, s_w[ly + 2][lx + 2]);
+      stv<TS, TC>(w_out + off + tile_pt(x0 + lx, y0 + ly, ln, n), s_w[ly + 2][lx + 2]);
     }
     __syncthreads();
   }
@@ -745,6 +751,7 @@ __global__ void __launch_bounds__(256) k_mg_prolong_add(MGLevelDesc fine, int nc
       auto base = [&](long long o) -> TC { return SET ? dinv * ld_rhs(fb, fb64, o) : ldv(f + o); };
       if (DIM == 1) {
         const TC c0 = ldv(g + p), c1 = ldv(g + ((p + 1) & mc));
+        IRK_CHECK(2 * p + 1, fine.npts);
         stv<TS, TC>(f + 2 * p, base(2 * p) + c0);
         stv<TS, TC>(f + 2 * p + 1, base(2 * p + 1) + half * (c0 + c1));
       } else {
@@ -754,6 +761,7 @@ __global__ void __launch_bounds__(256) k_mg_prolong_add(MGLevelDesc fine, int nc
         const TC c01 = ldv(g + (J1 << logc) + I), c11 = ldv(g + (J1 << logc) + I1);
         const int lf = fine.logn;
         const long long o0 = ((long long)(2 * J) << lf) + 2 * I, o1 = o0 + fine.n;
+        IRK_CHECK(o1 + 1, fine.npts);
         stv<TS, TC>(f + o0, base(o0) + c00);
         stv<TS, TC>(f + o0 + 1, base(o0 + 1) + half * (c00 + c10));
         stv<TS, TC>(f + o1, base(o1) + half * (c00 + c01));
@@ -1096,7 +1104,7 @@ __global__ void __launch_bounds__(256) k_mg_setup2(MGLevelDesc fine, const doubl
       double* cp0 = coef0 + (long long)(2 * c) * npts;  // (e, w) for x, (n, s) for y
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int o = ((j + (q >> 1)) << lf) + i + (q & 1);
+        const int o = IRK_IDX(((j + (q >> 1)) << lf) + i + (q & 1), npts);
         const double a = __ldg(f + o);
         v0[o] = a;
         cp0[o] = fma(a0, a, b0);
@@ -1189,3 +1197,5 @@ void launch_mg_convert_out(int prec, const void* src, double* dst, long long len
 }
 
 }  // namespace irk
+
+IRK_BOUNDS_TU(mg)

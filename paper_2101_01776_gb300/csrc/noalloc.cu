@@ -56,7 +56,7 @@ __device__ __forceinline__ void y9(const NoallocArgs& a, int S, long long L, int
                                    int y, double v[3][3]) {
   for (int dy = -1; dy <= 1; ++dy)
     for (int dx = -1; dx <= 1; ++dx) {
-      const int q = (wrap_idx(y + dy, a.n) << a.logn) + wrap_idx(x + dx, a.n);
+      const int q = IRK_IDX((wrap_idx(y + dy, a.n) << a.logn) + wrap_idx(x + dx, a.n), a.npts);
       v[dy + 1][dx + 1] = y_at(a, S, L, i, c, q);
     }
 }
@@ -224,5 +224,19 @@ extern "C" irk_status irk_stage_residual_noalloc(int op, int n, double length, d
     fprintf(stderr, "irk_stage_residual_noalloc: launch failed: %s\n", cudaGetErrorString(e));
     return IRK_ERR_CUDA;
   }
+#ifdef IRK_BOUNDS
+  {
+    // the debug build waits for the kernels and fails the call on any hit
+    std::string msg;
+    const long long hits = cudaStreamSynchronize(st) == cudaSuccess ? bounds_collect(&msg) : -1;
+    if (hits != 0) {
+      fprintf(stderr, "irk_stage_residual_noalloc: bounds check: %s\n",
+              hits < 0 ? "records could not be read" : msg.c_str());
+      return IRK_ERR_CUDA;
+    }
+  }
+#endif
   return IRK_OK;
 }
+
+IRK_BOUNDS_TU(noalloc)

@@ -154,6 +154,7 @@ void worker_loop(irk_server* s, int slot) {
       ++s->active;
       s->peak_active = std::max(s->peak_active, s->active);
     }
+    irk::TraceRange tr("serve_request");  // admission to release, on this worker's thread
     irk_handle* h = nullptr;
     irk_status stt = irk_create_in(&r->cfg, r->u.data(), 0, st, s->base + r->off, r->bytes, &h);
     memset(&r->stats, 0, sizeof(r->stats));

@@ -554,6 +554,7 @@ bool jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, doub
 // Returns whether `epi` (if given) was applied by the last fine-level sweep.
 bool vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double cadv, double cdiff,
             int project_mean, const double* in, double* out, const MGEpilogue* epi = nullptr) {
+  TraceRange tr("vcycle");
   bool epi_done = false;
   const int nl = mg_depth(h, sigma, cdiff), prec = h->prec, dim = h->dim;
   const double om = h->mg_omega;
@@ -1505,6 +1506,7 @@ irk_status graph_step(irk_handle* h, double dt) {
   if (!h->cfg.use_graphs || h->cfg.profile || h->cfg.forcing || h->step_failed || !h->st_aux ||
       !h->st_aux2 || h->cfg.nonlinear_variant == 4 || h->cfg.dae_solver == 1)
     return IRK_ERR_INVALID;
+  TraceRange tr("step_graph");
   if (!h->stepexec || h->step_dt != dt) {
     if (build_step_graph(h, dt) != IRK_OK) {
       h->step_failed = true;
@@ -1712,6 +1714,7 @@ irk_status poisson_fgmres(irk_handle* h, double* b, double* x, double rtol) {
 }
 
 irk_status vsf_forward_solve(irk_handle* h, double dt, double rtol) {
+  TraceRange tr("vsf_forward_solve");
   const long long n = h->npts;
   for (int blk = h->tab.nblk - 1; blk >= 0; --blk) {
     const int a0 = h->tab.bstart[blk], bs = h->tab.bsize[blk];
@@ -1758,6 +1761,7 @@ irk_status vsf_forward_solve(irk_handle* h, double dt, double rtol) {
 }
 
 irk_status solve_blocks(irk_handle* h, double dt, double rtol, bool* on_device) {
+  TraceRange tr("block_solves");
   if (h->cfg.dae_solver == 1) {
     *on_device = false;
     return vsf_forward_solve(h, dt, rtol);
@@ -1846,6 +1850,7 @@ irk_status alg1_sweep(irk_handle* h, double dt, const double* r, double* z, doub
 // Exact Newton update (variant 4): solve J x = F (F in h->fo) by FGMRES over
 // all stages, right-preconditioned by one Algorithm-1 sweep, then K -= x.
 irk_status exact_newton_update(irk_handle* h, double dt, double rtol) {
+  TraceRange tr("exact_newton_update");
   const long long Lo = (long long)h->s * h->L;
   const double rtol_in = h->cfg.krylov_rtol;
   auto step = [&](int j) -> irk_status {
@@ -1866,6 +1871,7 @@ irk_status exact_newton_update(irk_handle* h, double dt, double rtol) {
 }
 
 irk_status newton_step(irk_handle* h, double t_n, double dt) {
+  TraceRange tr("newton");
   const int s = h->s;
   double f0 = 0, fn = 0, prev = 0, prev_rel = 0;
   if (h->cfg.initial_guess >= 1) {
@@ -1884,6 +1890,7 @@ irk_status newton_step(irk_handle* h, double t_n, double dt) {
   }
   int it = 0;
   for (;; ++it) {
+    TraceRange tri("newton_iteration");
     TRY(eval_residual(h, t_n, dt, h->K, h->rhs, h->fo, true, &fn));
     if (it == 0 && h->cfg.initial_guess >= 1 && f0 > 0 && fn > kGuessLimit * f0) {
       // the warm start is worse than zero stages: start from zero instead
@@ -1948,6 +1955,7 @@ irk_status sdirk_sequential_step(irk_handle* h, double t_n, double dt) {
   const int s = h->s;
   const size_t vb = sizeof(double) * h->L;
   for (int i = 0; i < s; ++i) {
+    TraceRange tr("sdirk_stage");
     CK(cudaMemcpyAsync(in->u, h->u, vb, cudaMemcpyDeviceToDevice, h->st));
     if (i > 0) {
       ProfScope ps(h, P_UPDATE, 8.0 * h->L * (2 + i), 2.0 * h->L * i);
@@ -2326,6 +2334,38 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
 
 // ===========================================================================
 // C ABI
+#ifdef IRK_BOUNDS
+long long irk::bounds_collect(std::string* msg) {
+  struct Tu { const char* file; int (*take)(BoundsRecord*); };
+  const Tu tus[] = {{"stencil.cu", bounds_take_stencil}, {"mg.cu", bounds_take_mg},
+                    {"blas.cu", bounds_take_blas}, {"fgmres_dev.cu", bounds_take_fgmres},
+                    {"noalloc.cu", bounds_take_noalloc}};
+  long long total = 0;
+  for (const Tu& tu : tus) {
+    BoundsRecord r;
+    if (tu.take(&r) != 0) return -1;
+    if (r.hits != 0u && total == 0 && msg) {
+      char buf[200];
+      snprintf(buf, sizeof buf, "index %lld outside [0, %lld) at %s:%d (%u hits)", r.index,
+               r.extent, tu.file, r.line, r.hits);
+      *msg = buf;
+    }
+    total += r.hits;
+  }
+  return total;
+}
+
+// After a step: any recorded hit fails it (the caller restores the state).
+static irk_status bounds_status(irk_handle* h) {
+  CK(cudaStreamSynchronize(h->st));
+  std::string m;
+  const long long hits = bounds_collect(&m);
+  if (hits == 0) return IRK_OK;
+  h->err = hits < 0 ? std::string("bounds records could not be read") : "bounds check: " + m;
+  return IRK_ERR_CUDA;
+}
+#endif
+
 extern "C" {
 
 void irk_config_default(irk_config* c) {
@@ -2419,6 +2459,7 @@ irk_status irk_transform(int family, int s, int basis, double* T, double* Tinv, 
 static irk_status create_impl(const irk_config* cfg, const double* u0, int u0_on_device,
                               void* cuda_stream, void* arena, size_t arena_bytes,
                               irk_handle** out, double inner_gamma = 0.0) {
+  TraceRange tr("irk_create");
   if (!out) { g_create_error = "null output handle"; return IRK_ERR_INVALID; }
   *out = nullptr;
   std::string verr;
@@ -2508,10 +2549,12 @@ irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats*
     h->err = "dt must be positive and finite, nsteps >= 0";
     return IRK_ERR_INVALID;
   }
+  TraceRange tr("irk_step");
   memset(&h->stats, 0, sizeof(h->stats));
   irk_status st = IRK_OK;
   double t = t_n;
   for (int k = 0; k < nsteps; ++k) {
+    TraceRange trs("step");
     cudaError_t e = cudaMemcpyAsync(h->u_save, h->u, sizeof(double) * h->L,
                                     cudaMemcpyDeviceToDevice, h->st);
     if (e != cudaSuccess) { h->err = cudaGetErrorString(e); st = IRK_ERR_CUDA; break; }
@@ -2524,6 +2567,9 @@ irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats*
         if (st == IRK_ERR_INVALID) st = newton_step(h, t, dt);  // host-driven loop
       }
     }
+#ifdef IRK_BOUNDS
+    if (st == IRK_OK) st = bounds_status(h);
+#endif
     if (st != IRK_OK) {
       cudaMemcpyAsync(h->u, h->u_save, sizeof(double) * h->L, cudaMemcpyDeviceToDevice, h->st);
       cudaMemsetAsync(h->K, 0, sizeof(double) * h->L * h->s, h->st);  // discard the failed iterate
@@ -2593,6 +2639,7 @@ irk_status irk_get_stages(irk_handle* h, double* dst, int dst_on_device) {
 irk_status irk_stage_residual(irk_handle* h, double t_n, double dt, const double* K, double* F,
                               int on_device) {
   if (!h || !K || !F) return IRK_ERR_INVALID;
+  TraceRange tr("irk_stage_residual");
   const size_t bytes = sizeof(double) * h->L * h->s;
   // stage the input in yhat (free between steps) and the output in rhs
   CK(cudaMemcpyAsync(h->yhat, K, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
@@ -2601,12 +2648,16 @@ irk_status irk_stage_residual(irk_handle* h, double t_n, double dt, const double
   CK(cudaMemcpyAsync(F, h->rhs, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   prof_harvest(h);
+#ifdef IRK_BOUNDS
+  TRY(bounds_status(h));
+#endif
   return IRK_OK;
 }
 
 irk_status irk_stage_jacobian_apply(irk_handle* h, double dt, const double* K, const double* V,
                                     double* JV, int on_device) {
   if (!h || !K || !V || !JV) return IRK_ERR_INVALID;
+  TraceRange tr("irk_stage_jacobian_apply");
   const int s = h->s;
   const size_t bytes = sizeof(double) * h->L * s;
   const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -2625,6 +2676,9 @@ irk_status irk_stage_jacobian_apply(irk_handle* h, double dt, const double* K, c
   CK(cudaMemcpyAsync(JV, Out, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   prof_harvest(h);
+#ifdef IRK_BOUNDS
+  TRY(bounds_status(h));
+#endif
   return IRK_OK;
 }
 
@@ -2654,6 +2708,7 @@ irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_con
     if (h) h->err = "autotune: dt must be positive, 1 <= steps <= 100";
     return IRK_ERR_INVALID;
   }
+  TraceRange tr("irk_autotune");
   const size_t ub = sizeof(double) * h->L, kb = sizeof(double) * h->L * h->s;
   double *u0 = nullptr, *k0 = nullptr;
   cudaError_t e = cudaMalloc((void**)&u0, ub);
@@ -2807,6 +2862,33 @@ void irk_destroy(irk_handle* h) {
   if (h->arena && h->own_arena) cudaFree(h->arena);
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
   delete h;
+}
+
+long long irk_debug_bounds(int selftest, char* msg, size_t msg_len) {
+  std::string m;
+  long long hits = -1;
+#ifdef IRK_BOUNDS
+  if (selftest) {
+    launch_bounds_selftest(0);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      cudaGetLastError();
+      m = "self-test launch failed";
+      hits = -2;
+    }
+  }
+  if (hits != -2) {
+    hits = bounds_collect(&m);
+    if (hits < 0) {
+      hits = -2;
+      m = "bounds records could not be read";
+    }
+  }
+#else
+  (void)selftest;
+  m = "not a bounds-checked build";
+#endif
+  if (msg && msg_len > 0) snprintf(msg, msg_len, "%s", m.c_str());
+  return hits;
 }
 
 }  // extern "C"

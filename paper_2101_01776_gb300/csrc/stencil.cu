@@ -84,14 +84,16 @@ struct Nbr {
 __device__ __forceinline__ Nbr neighbours(const GridDesc& g, int p) {
   Nbr r;
   r.c = p;
+  IRK_CHECK(p, g.npts);
   if (g.dim == 1) {
-    r.e = wrapn(p + 1, g.n);
-    r.w = wrapn(p - 1, g.n);
+    r.e = IRK_IDX(wrapn(p + 1, g.n), g.npts);
+    r.w = IRK_IDX(wrapn(p - 1, g.n), g.npts);
     r.n = r.s = r.ne = r.nw = r.se = r.sw = p;
   } else {
     const int i = p & (g.n - 1), j = p >> g.logn;
-    const int ip = wrapn(i + 1, g.n), im = wrapn(i - 1, g.n);
-    const int jp = wrapn(j + 1, g.n), jm = wrapn(j - 1, g.n);
+    const int ip = IRK_IDX(wrapn(i + 1, g.n), g.n), im = IRK_IDX(wrapn(i - 1, g.n), g.n);
+    const int jp = IRK_IDX(wrapn(j + 1, g.n), g.n), jm = IRK_IDX(wrapn(j - 1, g.n), g.n);
+    IRK_CHECK(j, g.n);
     r.e = (j << g.logn) + ip;
     r.w = (j << g.logn) + im;
     r.n = (jp << g.logn) + i;
@@ -886,3 +888,5 @@ void launch_remove_mean(long long npts, int nfields, long long stride, double* x
 }
 
 }  // namespace irk
+
+IRK_BOUNDS_TU(stencil)
