@@ -170,6 +170,11 @@ typedef struct {
   int mg_tile_rows;     /* rows of the 32-wide tiles of the three-sweep V-cycle
                            kernel: 0 (default) = 16 with FP64 storage, 8
                            otherwise; 8 or 16 to fix it (an autotuner knob) */
+  int mg_fuse_transfer; /* 1 (default): on 2D levels of n >= 32 whose single
+                           pre-sweep is folded into the residual, one kernel
+                           forms the residual and restricts it; 0: two
+                           kernels and a stored residual.  Same result bit
+                           for bit */
 } irk_config;
 
 typedef struct {

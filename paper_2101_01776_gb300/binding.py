@@ -52,6 +52,7 @@ class IrkConfig(C.Structure):
         ("basis", C.c_int), ("mg_shifted_sweeps", C.c_int), ("mg_coarse_reduction", C.c_double),
         ("mg_coarse_smoother", C.c_int), ("dirk_sequential", C.c_int), ("dae_solver", C.c_int),
         ("mg_tile_rows", C.c_int),
+        ("mg_fuse_transfer", C.c_int),
     ]
 
 

@@ -314,6 +314,12 @@ void launch_mg_prolong_set(int prec, int dim, const MGLevelDesc& fine, int ncomp
 void launch_mg_residual0(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp,
                          double sigma, double cadv, double cdiff, double omega, const void* vel,
                          const void* b, void* r, cudaStream_t st, const double* b64 = nullptr);
+// launch_mg_residual0 and launch_mg_restrict in one launch (2D, fine n >= 32,
+// ncomp <= 2): the coarse right-hand side bc, bit for bit, without storing r
+void launch_mg_resid0_restrict(int prec, int kind, const MGLevelDesc& fine, int ncomp,
+                               double sigma, double cadv, double cdiff, double omega,
+                               const void* vel, const void* b, void* bc, cudaStream_t st,
+                               const double* b64 = nullptr);
 void launch_mg_prolong_add(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* wc,
                            void* wf, cudaStream_t st);
 void launch_mg_coarse(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp, double sigma,

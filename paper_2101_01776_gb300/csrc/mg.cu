@@ -726,6 +726,70 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MGLevelDesc fine, int ncomp
   }
 }
 
+// The folded pre-sweep's residual (k_mg_residual0) and its full-weighting
+// restriction (k_mg_restrict) in one launch, 2D.  A CTA owns a 16 x 8 tile of
+// coarse points.  It stages b on the fine window that the 3 x 3 weights and
+// the 5-point stencil reach (35 x 19 points per component), forms r on the
+// 33 x 17 window that the weights read (1.10x the owned 32 x 16 points),
+// rounded to the storage type as a stored r would be, and writes the coarse
+// right-hand side.  The operations and their order are those of the two
+// kernels, so the result is bit-identical, and r never goes to memory.
+constexpr int kRCX = 16, kRCY = 8;
+
+template <typename TS, int KIND>
+__global__ void __launch_bounds__(256) k_mg_resid0_restrict(MGLevelDesc fine, int ncomp, MGConst k,
+                                                            const TS* __restrict__ vel,
+                                                            const TS* __restrict__ b,
+                                                            const double* __restrict__ b64,
+                                                            TS* __restrict__ bc) {
+  typedef typename Cmp<TS>::T TC;
+  constexpr int BX = 2 * kRCX + 3, BY = 2 * kRCY + 3;  // b window: r window + stencil halo
+  constexpr int RX = 2 * kRCX + 1, RY = 2 * kRCY + 1;  // r window: owned points + weight halo
+  __shared__ TC s_b[2][BY][BX];
+  __shared__ TC s_r[2][RY][RX];
+  const TC alpha = TC(k.alpha), beta = TC(k.beta), dinv = TC(k.dinv), keep = TC(k.keep);
+  const int n = fine.n, m = n - 1, ln = fine.logn, npts = fine.npts;
+  const int nc = n >> 1, logc = ln - 1;
+  const int I0 = blockIdx.x * kRCX, J0 = blockIdx.y * kRCY;
+  const int fx0 = 2 * I0, fy0 = 2 * J0;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int q = tid; q < ncomp * BY * BX; q += nt) {
+    const int c = q / (BY * BX), rem = q - c * (BY * BX);
+    const int ly = rem / BX, lx = rem - ly * BX;
+    const int gp = tile_pt((fx0 - 2 + lx) & m, (fy0 - 2 + ly) & m, ln, n);
+    const long long off = (long long)c * npts;
+    s_b[IRK_IDX(c, 2)][ly][lx] = ld_rhs(b + off, b64 ? b64 + off : nullptr, gp);
+  }
+  __syncthreads();
+  for (int q = tid; q < RY * RX; q += nt) {
+    const int ry = q / RX, rx = q - ry * RX;
+    LvIdx pt;
+    pt.c = tile_pt((fx0 - 1 + rx) & m, (fy0 - 1 + ry) & m, ln, n);
+    pt.e = pt.w = pt.n = pt.s = pt.c;  // the 2D kinds read their coefficients at the point
+    const Coef4<TC> cf = stencil_coef<TS, 2, KIND>(pt, vel, npts, alpha, beta);
+    const int sy = ry + 1, sx = rx + 1;  // the point in the b window
+    for (int c = 0; c < ncomp; ++c) {
+      TC sum = cf.e * s_b[c][sy][sx + 1];
+      sum = fma(cf.w, s_b[c][sy][sx - 1], sum);
+      sum = fma(cf.n, s_b[c][sy + 1][sx], sum);
+      sum = fma(cf.s, s_b[c][sy - 1][sx], sum);
+      s_r[c][ry][rx] = round_to_storage<TS>(fma(-dinv, sum, keep * s_b[c][sy][sx]));
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < ncomp * kRCY * kRCX; q += nt) {
+    const int c = q / (kRCY * kRCX), rem = q - c * (kRCY * kRCX);
+    const int cy = rem / kRCX, cx = rem - cy * kRCX;
+    const int y = 2 * cy + 1, x = 2 * cx + 1;  // fine point (2I, 2J) in the r window
+    const TC centre = s_r[c][y][x];
+    const TC edges = s_r[c][y][x + 1] + s_r[c][y][x - 1] + s_r[c][y + 1][x] + s_r[c][y - 1][x];
+    const TC corners = s_r[c][y + 1][x + 1] + s_r[c][y + 1][x - 1] + s_r[c][y - 1][x + 1] +
+                       s_r[c][y - 1][x - 1];
+    const TC v = (TC(4) * centre + TC(2) * edges + corners) * TC(0.0625);
+    stv<TS, TC>(bc + (long long)c * nc * nc + tile_pt(I0 + cx, J0 + cy, logc, nc), v);
+  }
+}
+
 // Bilinear (linear in 1D) interpolation of the coarse correction, added to w.
 // One thread per coarse point updates the 2x2 (1D: 2) fine points it owns:
 // (2I,2J) += c00, (2I+1,2J) += (c00+c10)/2, (2I,2J+1) += (c00+c01)/2,
@@ -1148,6 +1212,26 @@ void launch_mg_residual0(int prec, int dim, int kind, const MGLevelDesc& lv, int
   if (prec == IRK_MG_FP64) b64 = nullptr;
   IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_residual0<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
       lv, ncomp, k, (const TS*)vel, (const TS*)b, (TS*)r, b64))));
+}
+
+void launch_mg_resid0_restrict(int prec, int kind, const MGLevelDesc& fine, int ncomp,
+                               double sigma, double cadv, double cdiff, double omega,
+                               const void* vel, const void* b, void* bc, cudaStream_t st,
+                               const double* b64) {
+  const MGConst k = mg_const(fine, 2, sigma, cadv, cdiff, omega);
+  if (prec == IRK_MG_FP64) b64 = nullptr;
+  const dim3 grid((fine.n / 2) / kRCX, (fine.n / 2) / kRCY);
+  IRK_DISPATCH_PREC(prec, {
+    if (kind == MG_ADVECTIVE)
+      k_mg_resid0_restrict<TS, MG_ADVECTIVE><<<grid, 256, 0, st>>>(fine, ncomp, k, (const TS*)vel,
+                                                                  (const TS*)b, b64, (TS*)bc);
+    else if (kind == MG_ADVECTIVE_PRE)
+      k_mg_resid0_restrict<TS, MG_ADVECTIVE_PRE><<<grid, 256, 0, st>>>(
+          fine, ncomp, k, (const TS*)vel, (const TS*)b, b64, (TS*)bc);
+    else
+      k_mg_resid0_restrict<TS, MG_DIFFUSION><<<grid, 256, 0, st>>>(fine, ncomp, k, (const TS*)vel,
+                                                                  (const TS*)b, b64, (TS*)bc);
+  });
 }
 
 void launch_mg_bottom(int prec, const MGLevelDesc& lv, double cdiff, double omega, int pre,

@@ -613,6 +613,15 @@ bool vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     MGLevel& lv = h->lev[l];
     cur[l] = lv.w;
     alt[l] = lv.w2;
+    if (fold_pre && dim == 2 && lv.d.n >= 32 && ncomp <= 2 && h->cfg.mg_fuse_transfer) {
+      // residual and restriction in one launch: r stays on chip
+      const double wb = (l == 0 && b64) ? (8.0 - h->esz) * ncomp * lv.d.npts : 0.0;
+      ProfScope ps(h, P_MG_RESID, mg_level_bytes(h, l, ncomp * 1.25 + velf) + wb,
+                   (fresid + 2.0 * ncomp) * lv.d.npts + 12.0 * ncomp * lv.d.npts / 4);
+      launch_mg_resid0_restrict(prec, kk, lv.d, ncomp, sigma, cadv, cdiff, om, crow[l], bl[l],
+                                h->lev[l + 1].b, h->st, l == 0 ? b64 : nullptr);
+      continue;
+    }
     if (fold_pre) {
       const double wb = (l == 0 && b64) ? (8.0 - h->esz) * ncomp * lv.d.npts : 0.0;
       ProfScope ps(h, P_MG_RESID, mg_level_bytes(h, l, 2.0 * ncomp + velf) + wb,
@@ -2024,6 +2033,7 @@ irk_status validate(const irk_config* c, std::string& err) {
   if (!(c->mg_coarse_reduction >= 0 && c->mg_coarse_reduction < 1)) { err = "mg_coarse_reduction must be in [0, 1)"; return IRK_ERR_INVALID; }
   if (c->mg_coarse_smoother < 0 || c->mg_coarse_smoother > 2) { err = "mg_coarse_smoother must be 0..2"; return IRK_ERR_INVALID; }
   if (c->mg_tile_rows != 0 && c->mg_tile_rows != 8 && c->mg_tile_rows != 16) { err = "mg_tile_rows must be 0, 8 or 16"; return IRK_ERR_INVALID; }
+  if (c->mg_fuse_transfer != 0 && c->mg_fuse_transfer != 1) { err = "mg_fuse_transfer must be 0 or 1"; return IRK_ERR_INVALID; }
   if (c->mg_levels < 0 || c->mg_levels > IRK_MAX_LEVELS) { err = "mg_levels out of range"; return IRK_ERR_INVALID; }
   return IRK_OK;
 }
@@ -2403,6 +2413,7 @@ void irk_config_default(irk_config* c) {
   c->initial_guess = 2;
   c->dirk_sequential = 1;
   c->dae_solver = 0;
+  c->mg_fuse_transfer = 1;
 }
 
 const char* irk_status_string(irk_status st) {

@@ -532,6 +532,29 @@ def test_graph_path_matches_host_driven_path(B):
     assert outs[0][1:] == outs[1][1:]
 
 
+@pytest.mark.parametrize("op,n,s,prec,graphs", [("burgers2d", 64, 2, 0, 1), ("burgers2d", 64, 3, 1, 1),
+                                               ("burgers2d", 128, 2, 2, 1), ("burgers2d", 64, 2, 0, 0),
+                                               ("vsf", 64, 3, 0, 1), ("vsf", 64, 2, 1, 0)])
+def test_fused_residual_restriction_is_bit_identical(B, op, n, s, prec, graphs):
+    """The V-cycle's folded-pre-sweep residual and its restriction in one
+    kernel (mg_fuse_transfer = 1) against the two separate kernels: the same
+    operations in the same order, so the states are equal bit for bit and the
+    Newton, Krylov and V-cycle counts agree (FP64, FP32 and BF16 storage;
+    Burgers' precomputed and per-point coefficients; the VSF vorticity rows;
+    graph and host-driven loops)."""
+    nu = 5e-3 if op == "burgers2d" else 1e-3
+    _, length = make_problem(op, n, nu, s)
+    u0 = initial(op, n, seed=6)
+    outs = []
+    for fuse in (0, 1):
+        with B.IrkSolver(u0.copy(), op=op, n=n, stages=s, nu=nu, length=length, mg_precision=prec,
+                         use_graphs=graphs, mg_fuse_transfer=fuse) as sol:
+            st = sol.step(0.0, 2e-3 if op == "burgers2d" else 5e-3, 3)
+            outs.append((sol.state().copy(), st.newton_its, st.krylov_its, st.vcycles))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1:] == outs[1][1:] and outs[1][3] > 0
+
+
 def test_vsf_medium_128_gauss5_parity(B):
     """Vorticity-streamfunction DAE, 128^2, Gauss s=5 (order 10), dt=5e-3, Re=1000."""
     per_step, whole, infos = run_parity(B, "vsf", 128, 5, 1e-3, 5e-3, 2, seed=2)
