@@ -401,10 +401,14 @@ def run_ours(args, rank, world):
                        "d2h_bytes_per_step": nbytes}
         # ---- the other stage count and the FP32 V-cycle, same workload ------
         extra = {}
-        for label, stages, prec, var in (("gauss3_fp64", 3, 0, None), ("gauss2_mg_fp32", 2, 1, None),
-                                         ("gauss3_mg_fp32", 3, 1, None),
-                                         ("gauss3_fp64_variant3", 3, 0, 3)):
-            h = make(stages, prec, 0, var)
+        # (the *_transfer runs: the residual-restriction fusion against the
+        # automatic choice, fused with FP32 storage, two kernels with FP64)
+        for label, stages, prec, var, kw in (
+                ("gauss3_fp64", 3, 0, None, {}), ("gauss2_mg_fp32", 2, 1, None, {}),
+                ("gauss3_mg_fp32", 3, 1, None, {}), ("gauss3_fp64_variant3", 3, 0, 3, {}),
+                ("gauss2_fp64_fused_transfer", 2, 0, None, dict(mg_fuse_transfer=1)),
+                ("gauss2_mg_fp32_separate_transfer", 2, 1, None, dict(mg_fuse_transfer=2))):
+            h = make(stages, prec, 0, var, **kw)
             ms2, tot2, _ = timed_steps(h, 3, 2)
             B.irk_destroy(h)
             extra[label] = {"steps_per_s": 1e3 / (sum(ms2) / len(ms2)),
@@ -473,7 +477,8 @@ def run_ours(args, rank, world):
             "chosen": {"mg_shifted_sweeps": chosen.mg_shifted_sweeps,
                        "mg_coarse_smoother": chosen.mg_coarse_smoother,
                        "mg_coarse_reduction": chosen.mg_coarse_reduction,
-                       "mg_tile_rows": chosen.mg_tile_rows, "mg_levels": chosen.mg_levels}}
+                       "mg_tile_rows": chosen.mg_tile_rows, "mg_levels": chosen.mg_levels,
+                       "mg_fuse_transfer": chosen.mg_fuse_transfer}}
         if args.serving_requests > 0:
             # 8 slots: the lowest step latency at the mix's throughput (16
             # slots measured the same steps/s at 4x the p50 step latency);

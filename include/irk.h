@@ -170,11 +170,14 @@ typedef struct {
   int mg_tile_rows;     /* rows of the 32-wide tiles of the three-sweep V-cycle
                            kernel: 0 (default) = 16 with FP64 storage, 8
                            otherwise; 8 or 16 to fix it (an autotuner knob) */
-  int mg_fuse_transfer; /* 1 (default): on 2D levels of n >= 32 whose single
-                           pre-sweep is folded into the residual, one kernel
-                           forms the residual and restricts it; 0: two
-                           kernels and a stored residual.  Same result bit
-                           for bit */
+  int mg_fuse_transfer; /* 2D levels of n >= 32 whose single pre-sweep is
+                           folded into the residual: 1 = one kernel forms
+                           the residual and restricts it; 2 = two kernels
+                           and a stored residual; 0 (default) = 1 with
+                           FP32/BF16 storage, 2 with FP64 (measured faster
+                           there: the fused kernel's FP64 stencil work is
+                           not hidden).  Same result bit for bit; an
+                           autotuner knob */
 } irk_config;
 
 typedef struct {
@@ -310,8 +313,9 @@ irk_status irk_get_config(const irk_handle* h, irk_config* out);
  * captures its graphs), by CUDA events on the handle's stream; candidates
  * come by coordinate descent over mg_shifted_sweeps {1, 2},
  * mg_coarse_smoother {0, 2}, mg_coarse_reduction {2e-2, 5e-3}, mg_tile_rows
- * {8, 16} and mg_levels {0 (automatic), automatic depth + 1}, starting from
- * the current settings, and the fastest is kept.  A candidate whose
+ * {8, 16}, mg_levels {0 (automatic), automatic depth + 1} and
+ * mg_fuse_transfer {1, 2}, starting from the current settings, and the
+ * fastest is kept.  A candidate whose
  * step fails is skipped.  State and stages are restored afterwards, and the
  * statistics of the trial steps are discarded.  Allocates a backup of the
  * state and stages (cudaMalloc) for the duration of the call.  The choice

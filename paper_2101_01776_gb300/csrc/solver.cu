@@ -613,7 +613,9 @@ bool vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
     MGLevel& lv = h->lev[l];
     cur[l] = lv.w;
     alt[l] = lv.w2;
-    if (fold_pre && dim == 2 && lv.d.n >= 32 && ncomp <= 2 && h->cfg.mg_fuse_transfer) {
+    const int fuse_mode = h->cfg.mg_fuse_transfer ? h->cfg.mg_fuse_transfer
+                                                  : (prec == IRK_MG_FP64 ? 2 : 1);
+    if (fold_pre && dim == 2 && lv.d.n >= 32 && ncomp <= 2 && fuse_mode == 1) {
       // residual and restriction in one launch: r stays on chip
       const double wb = (l == 0 && b64) ? (8.0 - h->esz) * ncomp * lv.d.npts : 0.0;
       ProfScope ps(h, P_MG_RESID, mg_level_bytes(h, l, ncomp * 1.25 + velf) + wb,
@@ -2033,7 +2035,7 @@ irk_status validate(const irk_config* c, std::string& err) {
   if (!(c->mg_coarse_reduction >= 0 && c->mg_coarse_reduction < 1)) { err = "mg_coarse_reduction must be in [0, 1)"; return IRK_ERR_INVALID; }
   if (c->mg_coarse_smoother < 0 || c->mg_coarse_smoother > 2) { err = "mg_coarse_smoother must be 0..2"; return IRK_ERR_INVALID; }
   if (c->mg_tile_rows != 0 && c->mg_tile_rows != 8 && c->mg_tile_rows != 16) { err = "mg_tile_rows must be 0, 8 or 16"; return IRK_ERR_INVALID; }
-  if (c->mg_fuse_transfer != 0 && c->mg_fuse_transfer != 1) { err = "mg_fuse_transfer must be 0 or 1"; return IRK_ERR_INVALID; }
+  if (c->mg_fuse_transfer < 0 || c->mg_fuse_transfer > 2) { err = "mg_fuse_transfer must be 0, 1 or 2"; return IRK_ERR_INVALID; }
   if (c->mg_levels < 0 || c->mg_levels > IRK_MAX_LEVELS) { err = "mg_levels out of range"; return IRK_ERR_INVALID; }
   return IRK_OK;
 }
@@ -2413,7 +2415,7 @@ void irk_config_default(irk_config* c) {
   c->initial_guess = 2;
   c->dirk_sequential = 1;
   c->dae_solver = 0;
-  c->mg_fuse_transfer = 1;
+  c->mg_fuse_transfer = 0;
 }
 
 const char* irk_status_string(irk_status st) {
@@ -2751,6 +2753,7 @@ irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_con
       h->inner->cfg.mg_coarse_reduction = h->cfg.mg_coarse_reduction;
       h->inner->cfg.mg_tile_rows = h->cfg.mg_tile_rows;
       h->inner->cfg.mg_levels = h->cfg.mg_levels;
+      h->inner->cfg.mg_fuse_transfer = h->cfg.mg_fuse_transfer;
       invalidate_graphs(h->inner);
     }
     TRY(restore());
@@ -2777,13 +2780,15 @@ irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_con
     // coordinate descent over the multigrid knobs of the V-cycle preconditioner:
     // sweeps on shift-dominated rows, the coarsest-level smoother and its
     // target, the tile height of the three-sweep kernel, and the V-cycle
-    // depth (the automatic depth of the first row against one level deeper)
+    // depth (the automatic depth of the first row against one level deeper),
+    // and the fused residual-restriction kernel against the two kernels
     struct Knob { int which; double vals[2]; };
     const int d0 = mg_depth(h, row_shift(h, 0), dt * h->g.nu);
     const double deeper = (h->cfg.mg_levels == 0 && d0 + 1 <= h->nlev) ? d0 + 1 : 0;
     const int auto_rows = (h->prec == IRK_MG_FP64) ? 16 : 8;
-    const Knob knobs[5] = {{0, {1, 2}}, {1, {0, 2}}, {2, {2e-2, 5e-3}}, {3, {8, 16}},
-                           {4, {0, deeper}}};
+    const int auto_fuse = (h->prec == IRK_MG_FP64) ? 2 : 1;
+    const Knob knobs[6] = {{0, {1, 2}}, {1, {0, 2}}, {2, {2e-2, 5e-3}}, {3, {8, 16}},
+                           {4, {0, deeper}}, {5, {1, 2}}};
     for (const Knob& kn : knobs) {
       for (double v : kn.vals) {
         irk_config trial = h->cfg;
@@ -2796,6 +2801,11 @@ irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_con
           trial.mg_tile_rows = (int)v;
         }
         if (kn.which == 4) { if (trial.mg_levels == (int)v) continue; trial.mg_levels = (int)v; }
+        if (kn.which == 5) {
+          const int now = trial.mg_fuse_transfer ? trial.mg_fuse_transfer : auto_fuse;
+          if (now == (int)v) continue;
+          trial.mg_fuse_transfer = (int)v;
+        }
         const irk_config keep = h->cfg;
         h->cfg = trial;
         double ms = 0;

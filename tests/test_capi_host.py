@@ -141,7 +141,7 @@ def test_invalid_configs_rejected_before_device(B):
            dict(nonlinear_variant=-1), dict(mg_precision=3), dict(forcing=1, op="burgers2d"),
            dict(mg_shifted_sweeps=-1), dict(mg_shifted_sweeps=9), dict(mg_coarse_reduction=1.0),
            dict(mg_coarse_reduction=-0.1), dict(mg_coarse_smoother=3), dict(mg_coarse_smoother=-1),
-           dict(mg_fuse_transfer=2), dict(mg_fuse_transfer=-1)]
+           dict(mg_fuse_transfer=3), dict(mg_fuse_transfer=-1)]
     for kw in bad:
         cfg = B.irk_config_default(**kw)
         with pytest.raises(B.IrkError) as ei:

@@ -537,7 +537,7 @@ def test_graph_path_matches_host_driven_path(B):
                                                ("vsf", 64, 3, 0, 1), ("vsf", 64, 2, 1, 0)])
 def test_fused_residual_restriction_is_bit_identical(B, op, n, s, prec, graphs):
     """The V-cycle's folded-pre-sweep residual and its restriction in one
-    kernel (mg_fuse_transfer = 1) against the two separate kernels: the same
+    kernel (mg_fuse_transfer = 1) against the two separate kernels (2): the same
     operations in the same order, so the states are equal bit for bit and the
     Newton, Krylov and V-cycle counts agree (FP64, FP32 and BF16 storage;
     Burgers' precomputed and per-point coefficients; the VSF vorticity rows;
@@ -546,7 +546,7 @@ def test_fused_residual_restriction_is_bit_identical(B, op, n, s, prec, graphs):
     _, length = make_problem(op, n, nu, s)
     u0 = initial(op, n, seed=6)
     outs = []
-    for fuse in (0, 1):
+    for fuse in (2, 1):
         with B.IrkSolver(u0.copy(), op=op, n=n, stages=s, nu=nu, length=length, mg_precision=prec,
                          use_graphs=graphs, mg_fuse_transfer=fuse) as sol:
             st = sol.step(0.0, 2e-3 if op == "burgers2d" else 5e-3, 3)
@@ -604,6 +604,7 @@ def test_autotune_restores_state_and_keeps_parity(B):
         assert got.mg_coarse_reduction in (2e-2, 5e-3)
         assert got.mg_tile_rows == chosen.mg_tile_rows in (0, 8, 16)
         assert got.mg_levels == chosen.mg_levels and got.mg_levels >= 0
+        assert got.mg_fuse_transfer == chosen.mg_fuse_transfer in (0, 1, 2)
         sol.step(dt, dt, 1)
         u2 = sol.state()
     want, _, _ = oracle_step(p, s, u1, dt, dt)
