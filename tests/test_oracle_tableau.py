@@ -169,6 +169,124 @@ def test_snsd_remark_bound():
             assert _kappa_Pgamma(L, eta, beta, g) <= bound * (1 + 1e-10)
 
 
+def _kappa_P(L1, L2, eta, beta, gamma):
+    """Condition number of the right-preconditioned Schur complement
+    [eta I - L2 + beta^2 (eta I - L1)^{-1}] (gamma I - L2)^{-1} (Eq. P_gamma)."""
+    I = np.eye(L1.shape[0])
+    P = (eta * I - L2 + beta ** 2 * np.linalg.inv(eta * I - L1)) @ np.linalg.inv(gamma * I - L2)
+    sv = np.linalg.svd(P, compute_uv=False)
+    return sv[0] / sv[-1]
+
+
+def _rotation_blocks(rng, n, a_range, b_sign):
+    """Block-diagonal real normal matrix with 2x2 blocks [[a, b], [-b, a]]:
+    eigenvalues a +- i b, a <= 0 drawn from a_range, b of sign b_sign."""
+    D = np.zeros((n, n))
+    for i in range(0, n, 2):
+        a = rng.uniform(*a_range)
+        b = b_sign * rng.uniform(0, 20)
+        D[i:i + 2, i:i + 2] = [[a, b], [-b, a]]
+    return D
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 5])
+def test_theorem2_bound_for_distinct_operators(s):
+    """Theorem (conditioning of the preconditioned operator, L1 != L2): with
+    W(L1), W(L2) <= 0 and <L1 w, L2 w> >= 0 for all w, kappa(P_gamma*) <=
+    2 + beta^2/eta^2 for every 2x2 block of Gauss(s).  Operator pairs: a
+    non-normal L1 with L2 a positive multiple of it, and commuting normal
+    pairs (shared orthogonal basis, eigenvalues a_k +- i b_k with a_k <= 0 and
+    b1_k b2_k >= 0).  Both satisfy the assumptions, which the test also checks
+    numerically."""
+    A, _, _ = tab.gauss(s)
+    Q0, R0, blocks = tab.real_schur(np.linalg.inv(A))
+    rng = np.random.default_rng(100 + s)
+    n = 10
+    for (k, m), bc in zip(blocks, tab.block_constants(R0, blocks)):
+        if m == 1:
+            continue
+        eta, beta, g = bc["eta"], bc["beta"], bc["gamma_star"]
+        bound = 2.0 + beta ** 2 / eta ** 2
+        pairs = []
+        for _ in range(15):
+            S = rng.standard_normal((n, n))
+            Kq = rng.standard_normal((n, n))
+            L1 = -(S @ S.T) * rng.uniform(0, 3) + (Kq - Kq.T) * rng.uniform(0, 5)
+            pairs.append((L1, rng.uniform(0.1, 5.0) * L1))
+            Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+            sign = rng.choice([-1.0, 1.0])
+            D1 = _rotation_blocks(rng, n, (-30, 0), sign)
+            D2 = _rotation_blocks(rng, n, (-30, 0), sign)
+            pairs.append((Q @ D1 @ Q.T, Q @ D2 @ Q.T))
+        for L1, L2 in pairs:
+            for L in (L1, L2):  # W(L) <= 0
+                assert np.linalg.eigvalsh(0.5 * (L + L.T)).max() <= 1e-9
+            M = L1.T @ L2  # <L1 w, L2 w> >= 0
+            assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() >= -1e-9
+            kap = _kappa_P(L1, L2, eta, beta, g)
+            assert kap <= bound * (1 + 1e-10), (s, kap, bound)
+
+
+def _gmres_relres(M, rhs, maxit):
+    """Relative residuals of unrestarted GMRES from x = 0 on a small dense
+    system (Arnoldi with modified Gram-Schmidt, least squares per iteration)."""
+    n = rhs.size
+    b0 = np.linalg.norm(rhs)
+    V = np.zeros((n, maxit + 1))
+    H = np.zeros((maxit + 1, maxit))
+    V[:, 0] = rhs / b0
+    out = []
+    for j in range(maxit):
+        w = M @ V[:, j]
+        for i in range(j + 1):
+            H[i, j] = V[:, i] @ w
+            w = w - H[i, j] * V[:, i]
+        H[j + 1, j] = np.linalg.norm(w)
+        e1 = np.zeros(j + 2)
+        e1[0] = b0
+        y = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)[0]
+        out.append(np.linalg.norm(H[:j + 2, :j + 1] @ y - e1) / b0)
+        if H[j + 1, j] <= 1e-14 * b0:
+            break
+        V[:, j + 1] = w / H[j + 1, j]
+    return out
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 5])
+def test_block_preconditioner_with_exact_schur_complement_two_iterations(s):
+    """Sec. 4, Eqs. block0, Lprec, Schur: the block lower-triangular L_P with
+    the exact Schur complement S makes GMRES on the right-preconditioned 2x2
+    block system converge in two iterations.  The block system is assembled
+    from the entries of R0; L_P and S from the oracle's (eta, beta, phi), so a
+    wrong block constant leaves the iteration unconverged at two (checked
+    with the sign of the coupling entry flipped)."""
+    A, _, _ = tab.gauss(s)
+    Q0, R0, blocks = tab.real_schur(np.linalg.inv(A))
+    rng = np.random.default_rng(200 + s)
+    n = 12
+    I, Z = np.eye(n), np.zeros((n, n))
+    for (k, m), bc in zip(blocks, tab.block_constants(R0, blocks)):
+        if m == 1:
+            continue
+        eta, beta, phi = bc["eta"], bc["beta"], bc["phi"]
+        S1, S2 = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+        K1, K2 = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+        L1 = -(S1 @ S1.T) + (K1 - K1.T)
+        L2 = -(S2 @ S2.T) + (K2 - K2.T)
+        blk = np.block([[R0[k, k] * I - L1, R0[k, k + 1] * I],
+                        [R0[k + 1, k] * I, R0[k + 1, k + 1] * I - L2]])
+        rhs = rng.standard_normal(2 * n)
+        for coupling, converged in ((-beta ** 2 / phi, True), (beta ** 2 / phi, False)):
+            schur = eta * I - L2 + beta ** 2 * np.linalg.inv(eta * I - L1)
+            LP = np.linalg.inv(np.block([[eta * I - L1, Z], [coupling * I, schur]]))
+            res = _gmres_relres(blk @ LP, rhs, 4)
+            assert res[0] > 1e-6
+            if converged:
+                assert len(res) >= 2 and res[1] <= 1e-10, (s, res)
+            else:
+                assert res[1] > 1e-6, (s, res)
+
+
 # ---------------------------------------------------------------------------
 # Radau IIA and Lobatto IIIC (the other rows of Table 1)
 
