@@ -30,64 +30,17 @@
 
 #include "../../include/irk_serve.h"
 #include "irk_internal.h"
+#include "pool.h"
 
 namespace {
+
+using irk::PoolAllocator;
 
 using clk = std::chrono::steady_clock;
 
 double ms_between(clk::time_point a, clk::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
 }
-
-// First-fit allocator over one device buffer (offsets, 256-byte granules).
-class PoolAllocator {
- public:
-  void init(size_t bytes) {
-    size_ = bytes & ~(size_t)255;
-    free_.clear();
-    free_[0] = size_;
-    used_ = peak_ = 0;
-  }
-  bool alloc(size_t bytes, size_t* off) {
-    bytes = (bytes + 255) & ~(size_t)255;
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= bytes) {
-        *off = it->first;
-        const size_t rest = it->second - bytes;
-        const size_t start = it->first + bytes;
-        free_.erase(it);
-        if (rest) free_[start] = rest;
-        used_ += bytes;
-        peak_ = std::max(peak_, used_);
-        return true;
-      }
-    }
-    return false;
-  }
-  void release(size_t off, size_t bytes) {
-    bytes = (bytes + 255) & ~(size_t)255;
-    used_ -= bytes;
-    auto it = free_.emplace(off, bytes).first;
-    auto next = std::next(it);
-    if (next != free_.end() && it->first + it->second == next->first) {
-      it->second += next->second;
-      free_.erase(next);
-    }
-    if (it != free_.begin()) {
-      auto prev = std::prev(it);
-      if (prev->first + prev->second == it->first) {
-        prev->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-  size_t size() const { return size_; }
-  size_t peak() const { return peak_; }
-
- private:
-  std::map<size_t, size_t> free_;
-  size_t size_ = 0, used_ = 0, peak_ = 0;
-};
 
 struct Request {
   long long id = 0;
