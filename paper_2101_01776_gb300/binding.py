@@ -183,6 +183,43 @@ def _ptr(x):
     return C.c_void_p(x.ctypes.data), 0
 
 
+def _nbytes(x) -> int:
+    return x.numel() * x.element_size() if hasattr(x, "data_ptr") else x.nbytes
+
+
+def _state_len(cfg) -> int:
+    """Values of one state vector: ncomp * n^dim (the 2D operators carry two fields)."""
+    two_d = cfg.op in (IRK_OP_BURGERS_2D, IRK_OP_VSF_2D)
+    return (2 if two_d else 1) * cfg.n ** (2 if two_d else 1)
+
+
+def _need(x, count: int, what: str):
+    """The library copies `count` float64 values through the pointer: refuse a
+    smaller buffer here instead of letting the copy run past its end."""
+    if _nbytes(x) < 8 * count:
+        raise ValueError(f"{what} holds {_nbytes(x) // 8} float64 values; {count} are needed")
+
+
+def _need_state(cfg, u0):
+    # only for a valid config (device bytes > 0); irk_create reports the others
+    if LIB.irk_config_device_bytes(C.byref(cfg)) > 0:
+        _need(u0, _state_len(cfg), "u0")
+
+
+# handle address -> (state values, stages); op, n and stages are fixed at
+# irk_create, and irk_destroy drops the entry
+_HANDLE_SIZES = {}
+
+
+def _handle_len(h, stages: bool) -> int:
+    key = getattr(h, "value", h)
+    if key not in _HANDLE_SIZES:
+        cfg = irk_get_config(h)
+        _HANDLE_SIZES[key] = (_state_len(cfg), cfg.stages)
+    n, s = _HANDLE_SIZES[key]
+    return n * (s if stages else 1)
+
+
 def _check(st: int, handle=None):
     if st != IRK_OK:
         msg = LIB.irk_last_error(handle).decode(errors="replace")
@@ -193,6 +230,7 @@ def irk_create(cfg: IrkConfig, u0, stream=None):
     """Return an opaque handle (c_void_p).  stream: torch.cuda.Stream, raw handle or None."""
     h = C.c_void_p()
     p, dev = _ptr(u0)
+    _need_state(cfg, u0)
     sp = None
     if stream is not None:
         sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -208,28 +246,33 @@ def irk_step(h, t_n: float, dt: float, nsteps: int = 1) -> IrkStats:
 
 def irk_get_state(h, dst):
     p, dev = _ptr(dst)
+    _need(dst, _handle_len(h, False), "dst")
     _check(LIB.irk_get_state(h, p, dev), h)
     return dst
 
 
 def irk_set_state(h, src):
     p, dev = _ptr(src)
+    _need(src, _handle_len(h, False), "src")
     _check(LIB.irk_set_state(h, p, dev), h)
 
 
 def irk_set_state_keep_stages(h, src):
     p, dev = _ptr(src)
+    _need(src, _handle_len(h, False), "src")
     _check(LIB.irk_set_state_keep_stages(h, p, dev), h)
 
 
 def irk_get_stages(h, dst):
     p, dev = _ptr(dst)
+    _need(dst, _handle_len(h, True), "dst")
     _check(LIB.irk_get_stages(h, p, dev), h)
     return dst
 
 
 def irk_set_stages(h, src):
     p, dev = _ptr(src)
+    _need(src, _handle_len(h, True), "src")
     _check(LIB.irk_set_stages(h, p, dev), h)
 
 
@@ -238,6 +281,9 @@ def irk_stage_residual(h, t_n: float, dt: float, K, F):
     pf, df = _ptr(F)
     if dk != df:
         raise ValueError("K and F must live in the same memory space")
+    n = _handle_len(h, True)
+    _need(K, n, "K")
+    _need(F, n, "F")
     _check(LIB.irk_stage_residual(h, t_n, dt, pk, pf, dk), h)
     return F
 
@@ -246,6 +292,9 @@ def irk_stage_jacobian_apply(h, dt: float, K, V, JV):
     (pk, dk), (pv, dv), (pj, dj) = _ptr(K), _ptr(V), _ptr(JV)
     if not (dk == dv == dj):
         raise ValueError("K, V and JV must live in the same memory space")
+    n = _handle_len(h, True)
+    for x, what in ((K, "K"), (V, "V"), (JV, "JV")):
+        _need(x, n, what)
     _check(LIB.irk_stage_jacobian_apply(h, dt, pk, pv, pj, dk), h)
     return JV
 
@@ -277,6 +326,7 @@ def irk_config_device_bytes(cfg: IrkConfig) -> int:
 def irk_create_in(cfg: IrkConfig, u0, arena_ptr: int, arena_bytes: int, stream=None):
     h = C.c_void_p()
     p, dev = _ptr(u0)
+    _need_state(cfg, u0)
     sp = None
     if stream is not None:
         sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -291,11 +341,18 @@ def irk_server_create(slots: int, budget_bytes: int = 0):
     return s
 
 
+# (server address, request id) -> (state values, steps) of each submitted
+# request, so that irk_server_wait hands the library buffers of the right size
+_SUBMITTED = {}
+
+
 def irk_server_submit(s, cfg: IrkConfig, u0, t0: float, dt: float, nsteps: int) -> int:
     import numpy as np
     u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    _need_state(cfg, u0)
     rid = C.c_longlong()
     _check(LIB.irk_server_submit(s, C.byref(cfg), u0.ctypes.data, t0, dt, nsteps, C.byref(rid)))
+    _SUBMITTED[(getattr(s, "value", s), rid.value)] = (_state_len(cfg), nsteps)
     return rid.value
 
 
@@ -303,6 +360,10 @@ def irk_server_wait(s, rid: int, shape, nsteps: int):
     """(final state, IrkStats, per-step wall ms) of request rid (host arrays)."""
     import numpy as np
     out = np.empty(shape)
+    known = _SUBMITTED.pop((getattr(s, "value", s), rid), None)
+    if known is not None:
+        _need(out, known[0], "shape")
+        nsteps = known[1]
     st = IrkStats()
     ms = np.empty(max(nsteps, 1))
     code = LIB.irk_server_wait(s, rid, out.ctypes.data, C.byref(st), ms.ctypes.data)
@@ -385,6 +446,7 @@ def irk_last_error(h=None) -> str:
 
 
 def irk_destroy(h):
+    _HANDLE_SIZES.pop(getattr(h, "value", h), None)
     LIB.irk_destroy(h)
 
 

@@ -189,3 +189,21 @@ def test_sdirk_stage_by_stage_arena_holds_the_stage_solver(B):
     a, b, c = (B.irk_config_device_bytes(x) for x in (seq, coupled, one))
     assert 0 < c < b < a
     assert a >= b + c - 4096
+
+
+def test_binding_refuses_short_buffers(B):
+    """The library copies ncomp * n^dim values through the state pointer; the
+    binding refuses a smaller buffer before calling it (a valid config only:
+    invalid configs still reach the library's own checks)."""
+    for kw, short in ((dict(op="burgers2d", n=64), np.zeros((2, 64, 63))),
+                      (dict(op="vsf", n=32), np.zeros((1, 32, 32))),
+                      (dict(op="burgers1d", n=256), np.zeros(255))):
+        cfg = B.irk_config_default(**kw)
+        with pytest.raises(ValueError, match="float64 values"):
+            B.irk_create(cfg, short)
+    # a right-sized state passes the binding (and fails on the missing device here)
+    import torch
+    if not torch.cuda.is_available():
+        cfg = B.irk_config_default(op="burgers2d", n=64)
+        with pytest.raises(B.IrkError):
+            B.irk_create(cfg, np.zeros((2, 64, 64)))
