@@ -310,6 +310,19 @@ def irk_stage_residual_noalloc(op, n: int, length: float, nu: float, stages: int
     ptrs = [_ptr(x) for x in (u, K, F, fnorm)]
     if not all(dev for _, dev in ptrs):
         raise ValueError("u, K, F and fnorm must be device tensors")
+    two_d = op in (IRK_OP_BURGERS_2D, IRK_OP_VSF_2D)
+    npts = n ** (2 if two_d else 1) if isinstance(n, int) and n > 0 else 0
+    # sizes matter only for calls the library would run: a known op, 1..5
+    # stages, n a power of two >= 8 and at most 2^20 points (its scratch
+    # limit); it rejects the others before touching any buffer
+    if op in (IRK_OP_DIFFUSION_1D, IRK_OP_BURGERS_1D, IRK_OP_BURGERS_2D, IRK_OP_VSF_2D) and \
+            1 <= stages <= 5 and npts and n >= 8 and not (n & (n - 1)) and npts <= 1 << 20:
+        L = (2 if two_d else 1) * npts
+        _need(A, stages * stages, "A")
+        _need(u, L, "u")
+        _need(K, stages * L, "K")
+        _need(F, stages * L, "F")
+        _need(fnorm, 1, "fnorm")
     sp = None
     if stream is not None:
         sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
