@@ -207,3 +207,54 @@ def test_binding_refuses_short_buffers(B):
         cfg = B.irk_config_default(op="burgers2d", n=64)
         with pytest.raises(B.IrkError):
             B.irk_create(cfg, np.zeros((2, 64, 64)))
+
+
+def _c_struct_fields(header, typedef_name):
+    """(name, C type) of each member of `typedef struct { ... } typedef_name;`
+    in the header, in declaration order (comments removed; `a, b;` split)."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", header)).read(), flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + typedef_name + r"\s*;", text)
+    assert m, typedef_name
+    out = []
+    for decl in m.group(1).split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        mm = re.match(r"((?:unsigned |long |const )*(?:long|int|double|char|size_t|float))\s+(.*)", decl)
+        assert mm, decl
+        ctype = mm.group(1)
+        for name in mm.group(2).split(","):
+            name = name.strip()
+            arr = re.match(r"(\w+)\[(\d+)\]", name)
+            out.append((arr.group(1), f"{ctype}[{arr.group(2)}]") if arr else (name, ctype))
+    return out
+
+
+@pytest.mark.parametrize("header,typedef,cls", [("irk.h", "irk_config", "IrkConfig"),
+                                                ("irk.h", "irk_stats", "IrkStats"),
+                                                ("irk.h", "irk_kernel_stat", "IrkKernelStat"),
+                                                ("irk_serve.h", "irk_server_stats", "IrkServerStats")])
+def test_binding_structs_mirror_the_headers(B, header, typedef, cls):
+    """Every ctypes structure of the binding lists the header's members in the
+    same order with the same C types, so the library and the binding agree on
+    the layout (a mismatch would shift every later field)."""
+    import ctypes
+    want = _c_struct_fields(header, typedef)
+    ctypes_of = {"int": ctypes.c_int, "double": ctypes.c_double, "long long": ctypes.c_longlong,
+                 "size_t": ctypes.c_size_t, "float": ctypes.c_float}
+    got = getattr(B, cls)._fields_
+    assert [n for n, _ in got] == [n for n, _ in want], typedef
+    for (name, ct), (_, t) in zip(want, got):
+        if ct.startswith("char["):
+            assert t._type_ is ctypes.c_char and t._length_ == int(ct[5:-1]), name
+        else:
+            assert t is ctypes_of[ct], (name, ct, t)
+
+
+def test_config_defaults_are_the_documented_ones(B):
+    """irk_config_default against the defaults the header documents for the
+    solver's switches."""
+    c = B.irk_config_default()
+    assert (c.initial_guess, c.nonlinear_variant, c.dirk_sequential, c.dae_solver) == (2, 2, 1, 0)
+    assert (c.mg_tile_rows, c.mg_fuse_transfer, c.mg_levels) == (0, 0, 0)
+    assert c.use_graphs == 1 and c.newton_rtol == 1e-10
