@@ -280,10 +280,16 @@ irk_status irk_stage_jacobian_apply(irk_handle* h, double dt, const double* K,
  * n^dim <= 1,048,576 points (e.g. 1024^2); larger grids return IRK_ERR_NOMEM
  * with a message on stderr and launch nothing.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) and caches it;
- * make that first call before any stream capture.  Every call shares the
- * array and leaves its partials there (each call rewrites every slot it
- * reads, so nothing needs clearing); calls whose work overlaps on the GPU,
- * e.g. on two streams, race on it.  Bad arguments return IRK_ERR_INVALID. */
+ * make that first call before any stream capture.  The cache lives as long
+ * as the process: after cudaDeviceReset on that device the cached address is
+ * stale, so do not call this entry again in such a process.  Every call
+ * shares the array and leaves its partials there (each call rewrites every
+ * slot it reads, so nothing needs clearing); calls whose work overlaps on
+ * the GPU, e.g. on two streams, race on it.  u, K, F and fnorm must be
+ * device (or managed) memory of the current device, checked with
+ * cudaPointerGetAttributes before anything is launched; a buffer on another
+ * device or in host memory, and any other bad argument, returns
+ * IRK_ERR_INVALID. */
 irk_status irk_stage_residual_noalloc(int op, int n, double length, double nu, int stages,
                                       const double* A, double dt, const double* u,
                                       const double* K, double* F, double* fnorm,

@@ -310,6 +310,9 @@ def irk_stage_residual_noalloc(op, n: int, length: float, nu: float, stages: int
     ptrs = [_ptr(x) for x in (u, K, F, fnorm)]
     if not all(dev for _, dev in ptrs):
         raise ValueError("u, K, F and fnorm must be device tensors")
+    devices = {x.device for x in (u, K, F, fnorm)}
+    if len(devices) != 1:
+        raise ValueError("u, K, F and fnorm must live on one device")
     two_d = op in (IRK_OP_BURGERS_2D, IRK_OP_VSF_2D)
     npts = n ** (2 if two_d else 1) if isinstance(n, int) and n > 0 else 0
     # sizes matter only for calls the library would run: a known op, 1..5
@@ -326,8 +329,10 @@ def irk_stage_residual_noalloc(op, n: int, length: float, nu: float, stages: int
     sp = None
     if stream is not None:
         sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
-    st = LIB.irk_stage_residual_noalloc(op, n, length, nu, stages, A.ctypes.data, dt,
-                                        *[p for p, _ in ptrs], sp)
+    import torch
+    with torch.cuda.device(u.device):  # the library runs on the current device
+        st = LIB.irk_stage_residual_noalloc(op, n, length, nu, stages, A.ctypes.data, dt,
+                                            *[p for p, _ in ptrs], sp)
     if st != IRK_OK:
         raise IrkError(st, "irk_stage_residual_noalloc rejected the call (see stderr)")
 

@@ -179,6 +179,26 @@ extern "C" irk_status irk_stage_residual_noalloc(int op, int n, double length, d
     cudaGetLastError();
     return IRK_ERR_NO_DEVICE;
   }
+  // The kernels run on the current device and read and write the four
+  // buffers directly: each must be device (or managed) memory of that device.
+  // A buffer of another GPU would be reached without peer access, and host
+  // memory not at all; both are argument errors, found before any launch.
+  {
+    const void* bufs[4] = {u, K, F, fnorm};
+    const char* names[4] = {"u", "K", "F", "fnorm"};
+    for (int b = 0; b < 4; ++b) {
+      cudaPointerAttributes attr;
+      if (cudaPointerGetAttributes(&attr, bufs[b]) != cudaSuccess ||
+          (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) ||
+          (attr.type == cudaMemoryTypeDevice && attr.device != dev)) {
+        cudaGetLastError();
+        fprintf(stderr,
+                "irk_stage_residual_noalloc: %s is not device memory of the current device %d\n",
+                names[b], dev);
+        return IRK_ERR_INVALID;
+      }
+    }
+  }
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_partials_mutex);
