@@ -55,9 +55,10 @@ def parse():
                     help="timed workload; the extras and the reference arm run on burgers2d_512 only")
     ap.add_argument("--mg-precision", type=int, default=0)
     ap.add_argument("--no-extras", action="store_true", help="skip the s=3 / FP32 / e2e / CPU legs")
-    ap.add_argument("--serving-requests", type=int, default=128,
+    ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the 512-request serving mix to run (0 = skip)")
-    ap.add_argument("--serving-rate", type=float, default=200.0, help="Poisson arrival rate, req/s")
+    ap.add_argument("--serving-rates", default="25,50,200",
+                    help="Poisson arrival rates to sweep, req/s (comma-separated)")
     return ap.parse_args()
 
 
@@ -283,6 +284,8 @@ def run_ours(args, rank, world):
         ms = [a.elapsed_time(b) for a, b in ev]
         return ms, tot, t
 
+    # ---- ALU ceilings of this GPU, measured (FMA chains on every SM) -------
+    alu_peaks = {"fp64": B.irk_measure_alu_peak(0, stream), "fp32": B.irk_measure_alu_peak(1, stream)}
     # ---- headline: plain FP64 GPU method -----------------------------------
     h = make(args.stages, args.mg_precision, 0)
     hbm_peak, peak_src = peaks()
@@ -321,14 +324,16 @@ def run_ours(args, rank, world):
         # (the velocity and conversion classes read FP64 fields)
         fp32 = (args.mg_precision > 0 and k["name"].startswith("mg_")
                 and k["name"] not in ("mg_setup", "mg_convert"))
-        alu_peak = FP32_PEAK_TFLOPS_DERIVED if fp32 else FP64_PEAK_TFLOPS_DERIVED
+        alu_peak = alu_peaks["fp32" if fp32 else "fp64"]
         intensity = k["flops"] / max(k["bytes"], 1.0)
         if intensity > alu_peak * 1e12 / (hbm_peak * 1e9):
             achieved = k["flops"] / (k["ms"] / 1e3) / 1e12
             r = {"bound": "alu", "achieved": achieved, "peak": alu_peak,
                  "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                 "peak_source": ("derived FP32: 152 SMs x 128 FFMA/clk x 2070 MHz" if fp32
-                                 else "derived FP64: 152 SMs x 2 DFMA/clk x 2070 MHz")}
+                 "peak_source": ("measured on this GPU by irk_measure_alu_peak (%s FMA chains, "
+                                 "8 x 256 threads per SM, best of 5); derived %.3f"
+                                 % ("FP32" if fp32 else "FP64",
+                                    FP32_PEAK_TFLOPS_DERIVED if fp32 else FP64_PEAK_TFLOPS_DERIVED))}
         else:
             achieved = k["bytes"] / (k["ms"] / 1e3) / 1e9
             r = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -364,6 +369,7 @@ def run_ours(args, rank, world):
         "roofline_next": roof_next,
         "gpu_launches": tot["launches"],
         "clocks": clk,
+        "alu_peaks_measured_tflops": alu_peaks,
         "solver": {"newton_its_per_step": tot["newton_its"] / args.steps,
                    "krylov_its_per_step": tot["krylov_its"] / args.steps,
                    "prec_apps_per_step": tot["prec_apps"] / args.steps,
@@ -486,12 +492,16 @@ def run_ours(args, rank, world):
                        "mg_tile_rows": chosen.mg_tile_rows, "mg_levels": chosen.mg_levels,
                        "mg_fuse_transfer": chosen.mg_fuse_transfer}}
         if args.serving_requests > 0:
-            # 8 slots: the lowest step latency at the mix's throughput (16
-            # slots measured the same steps/s at 4x the p50 step latency);
-            # 32 slots trade tail latency for throughput (host threads then
-            # outnumber the host cores)
-            line["serving"] = serving_leg(B, args.serving_requests, args.serving_rate, slots=8)
-            line["serving_32_slots"] = serving_leg(B, args.serving_requests, args.serving_rate,
+            # the mix at several Poisson arrival rates, from below the
+            # service rate to saturation; 8 slots (the lowest step latency at
+            # the mix's throughput; 16 measured the same steps/s at 4x the p50
+            # step latency); 32 slots at the highest rate trade tail latency
+            # for throughput (host threads then outnumber the host cores)
+            rates = [float(r) for r in args.serving_rates.split(",") if r]
+            line["serving"] = {
+                "requests": args.serving_requests, "of_mix": 512, "slots": 8,
+                "per_rate": [serving_leg(B, args.serving_requests, r, slots=8) for r in rates]}
+            line["serving_32_slots"] = serving_leg(B, args.serving_requests, rates[-1],
                                                    slots=32, budget_gib=48)
         # ---- precision report: one step from u0 per V-cycle storage precision
         prec_u = {}
@@ -518,13 +528,31 @@ def run_ours(args, rank, world):
                              "vcycles": st.vcycles, "final_rel_res": st.final_rel_res,
                              "rel_l2_err_vs_oracle": (float(np.linalg.norm(u1 - ref) / np.linalg.norm(ref))
                                                       if ref is not None else None)}
-            line["precision"] = {"workload": "one IRK step from u0 (512^2, Gauss s=%d)" % args.stages,
-                                 "per_precision": rep}
+            line["precision"] = {"burgers2d_512": {"workload": "one IRK step from u0 (512^2, Gauss s=%d)"
+                                                               % args.stages, "per_precision": rep},
+                                 "vsf_1024": vsf_precision_leg(B, torch, dev, stream)}
     elif "e2e" not in line:
         line["e2e"] = None
     if rank == 0:
+        # the side results go last, the most read last of all, rounded to
+        # four significant digits (the tail of the line is what logs keep)
+        for k in ("kernels", "roofline_next", "variants", "solver_comparison", "gauss_vs_sdirk",
+                  "vsf_dae_solvers", "autotuned", "serving_32_slots", "serving",
+                  "batched_serving", "precision"):
+            if k in line:
+                line[k] = _round(line.pop(k))
         print(json.dumps(line), flush=True)
     return 0
+
+
+def _round(x):
+    if isinstance(x, float):
+        return float(f"{x:.4g}")
+    if isinstance(x, dict):
+        return {k: _round(v) for k, v in x.items()}
+    if isinstance(x, list):
+        return [_round(v) for v in x]
+    return x
 
 
 def vsf_dae_leg(B, torch, dev, stream, flush):
@@ -586,8 +614,8 @@ def vsf_leg(B, torch, dev, stream, flush, timed_steps):
     # the default block-diagonal variant 2 (FP64 / FP32 V-cycle) and the block
     # upper triangular variant 3 (Sec. 3.2), which keeps the small d_kl
     # off-diagonal terms of the transformed Jacobian (same fixed point)
-    for label, prec, var in (("fp64", 0, 2), ("mg_fp32", 1, 2), ("fp64_variant3", 0, 3),
-                             ("mg_fp32_variant3", 1, 3)):
+    for label, prec, var in (("fp64", 0, 2), ("mg_fp32", 1, 2), ("mg_bf16", 2, 2),
+                             ("fp64_variant3", 0, 3), ("mg_fp32_variant3", 1, 3)):
         cfg = B.irk_config_default(op="vsf", n=n, nu=nu, stages=5, length=2 * math.pi,
                                    mg_precision=prec, nonlinear_variant=var)
         h = B.irk_create(cfg, torch.from_numpy(u0).to(dev), stream)
@@ -612,6 +640,37 @@ def vsf_leg(B, torch, dev, stream, flush, timed_steps):
             "steps_per_s": 1e3 / (sum(ms) / len(ms)), "krylov_its_per_step": kry / 2,
             "newton_its_per_step": newt / 2}
     return out
+
+
+def vsf_precision_leg(B, torch, dev, stream):
+    """Config [3] on the DAE: one IRK step from the double shear layer 1024^2
+    (Re=1000, Gauss s=5, dt=5e-3) per V-cycle precision (FP64; FP32; BF16
+    storage with FP32 arithmetic), FP64 everywhere else.  Error of omega
+    against the oracle's first step, read from the stored trajectory that
+    tests/golden/make_trajectories.py writes with the oracle."""
+    import math
+    import workloads
+    path = os.path.join(ROOT, "tests", "golden", "traj_vsf_1024_gauss5.npz")
+    ref = np.load(path)["u_step1"] if os.path.exists(path) else None
+    n, nu, dt = 1024, 1e-3, 5e-3
+    u0 = np.zeros((2, n, n))
+    u0[0] = workloads.double_shear_layer_vorticity(n, seed=2)
+    rep = {}
+    for prec, name in ((0, "fp64"), (1, "fp32"), (2, "bf16")):
+        cfg = B.irk_config_default(op="vsf", n=n, nu=nu, stages=5, length=2 * math.pi,
+                                   mg_precision=prec)
+        h = B.irk_create(cfg, torch.from_numpy(u0).to(dev), stream)
+        st = B.irk_step(h, 0.0, dt, 1)
+        out = torch.empty((2, n, n), dtype=torch.float64, device=dev)
+        B.irk_get_state(h, out)
+        B.irk_destroy(h)
+        w1 = out[0].cpu().numpy()
+        rep[name] = {"krylov_its": st.krylov_its, "newton_its": st.newton_its,
+                     "vcycles": st.vcycles, "final_rel_res": st.final_rel_res,
+                     "rel_l2_err_omega_vs_oracle": (float(np.linalg.norm(w1 - ref) / np.linalg.norm(ref))
+                                                    if ref is not None else None)}
+    return {"workload": "one IRK step from the double shear layer (1024^2, Gauss s=5, dt=5e-3)",
+            "per_precision": rep}
 
 
 def serving_leg(B, count, rate, slots=8, budget_gib=24):

@@ -335,6 +335,16 @@ irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_con
 irk_status irk_kernel_stats(irk_handle* h, irk_kernel_stat* out, int max, int* count);
 irk_status irk_reset_kernel_stats(irk_handle* h);
 
+/* Measurement utility; the paper has no counterpart.  Measures the fused
+ * multiply-add throughput of the current device in TFLOP/s (one FMA = two
+ * operations), the roofline ceiling of kernels bound by floating-point
+ * arithmetic: precision 0 = FP64, 1 = FP32.  Runs independent FMA chains on
+ * 8 blocks of 256 threads per SM on cuda_stream (NULL = legacy default
+ * stream), timed by CUDA events, best of five runs of about 20 ms after one
+ * calibration run; allocates and frees one small output buffer.  Blocks until
+ * done.  Other precision values or a NULL tflops return IRK_ERR_INVALID. */
+irk_status irk_measure_alu_peak(int precision, void* cuda_stream, double* tflops);
+
 /* Device bytes held by the handle's arena. */
 size_t irk_device_bytes(const irk_handle* h);
 

@@ -123,6 +123,7 @@ def _load():
         "irk_status_string": (C.c_char_p, [i]),
         "irk_destroy": (None, [vp]),
         "irk_stage_residual_noalloc": (i, [i, i, d, d, i, vp, d, vp, vp, vp, vp, vp]),
+        "irk_measure_alu_peak": (i, [i, vp, P(d)]),
         "irk_config_device_bytes": (sz, [P(IrkConfig)]),
         "irk_create_in": (i, [P(IrkConfig), vp, i, vp, vp, sz, P(vp)]),
         "irk_server_create": (i, [i, sz, P(vp)]),
@@ -148,6 +149,7 @@ EXPORTED = (
     "irk_config_device_bytes", "irk_create_in", "irk_server_create", "irk_server_submit",
     "irk_server_wait", "irk_server_stats_get", "irk_server_destroy", "irk_transform",
     "irk_get_config", "irk_autotune", "irk_set_state_keep_stages", "irk_debug_bounds",
+    "irk_measure_alu_peak",
 )
 
 
@@ -335,6 +337,16 @@ def irk_stage_residual_noalloc(op, n: int, length: float, nu: float, stages: int
                                             *[p for p, _ in ptrs], sp)
     if st != IRK_OK:
         raise IrkError(st, "irk_stage_residual_noalloc rejected the call (see stderr)")
+
+
+def irk_measure_alu_peak(precision: int = 0, stream=None) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (0 = FP64, 1 = FP32)."""
+    sp = None
+    if stream is not None:
+        sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    out = C.c_double()
+    _check(LIB.irk_measure_alu_peak(precision, sp, C.byref(out)))
+    return out.value
 
 
 def irk_config_device_bytes(cfg: IrkConfig) -> int:

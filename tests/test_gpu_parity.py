@@ -633,3 +633,15 @@ def test_set_state_keep_stages_keeps_the_guess(B):
     want, _, _ = oracle_step(p, s, u1, dt, dt)
     assert rel(u2w, want) <= STEP_TOL and rel(u2c, want) <= STEP_TOL
     assert warm.newton_its <= cold.newton_its
+
+
+def test_measured_alu_peaks_are_plausible(B):
+    """irk_measure_alu_peak: FP64 FMA throughput within the derived ceiling
+    (152 SMs x 2 DFMA/clk at up to 2070 MHz) and FP32 far above it."""
+    fp64 = B.irk_measure_alu_peak(0)
+    fp32 = B.irk_measure_alu_peak(1)
+    derived64 = 152 * 2 * 2 * 2.070e9 / 1e12
+    assert 0.3 * derived64 <= fp64 <= 1.05 * derived64, fp64
+    assert fp32 >= 20 * fp64, (fp32, fp64)
+    with pytest.raises(B.IrkError):
+        B.irk_measure_alu_peak(2)
