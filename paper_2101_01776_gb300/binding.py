@@ -132,6 +132,16 @@ def _load():
         "irk_server_stats_get": (i, [vp, P(IrkServerStats)]),
         "irk_server_destroy": (None, [vp]),
         "irk_debug_bounds": (C.c_longlong, [i, C.c_char_p, sz]),
+        "irk_batch_create": (i, [i, vp, P(vp)]),
+        "irk_batch_instance_bytes": (sz, [P(IrkConfig)]),
+        "irk_batch_add": (i, [vp, P(IrkConfig), vp, i, d, vp, sz, P(i)]),
+        "irk_batch_step": (i, [vp, vp, vp]),
+        "irk_batch_get_state": (i, [vp, i, vp, i]),
+        "irk_batch_get_stages": (i, [vp, i, vp, i]),
+        "irk_batch_remove": (i, [vp, i]),
+        "irk_batch_count": (i, [vp]),
+        "irk_batch_last_error": (C.c_char_p, [vp]),
+        "irk_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -149,7 +159,9 @@ EXPORTED = (
     "irk_config_device_bytes", "irk_create_in", "irk_server_create", "irk_server_submit",
     "irk_server_wait", "irk_server_stats_get", "irk_server_destroy", "irk_transform",
     "irk_get_config", "irk_autotune", "irk_set_state_keep_stages", "irk_debug_bounds",
-    "irk_measure_alu_peak",
+    "irk_measure_alu_peak", "irk_batch_create", "irk_batch_instance_bytes", "irk_batch_add",
+    "irk_batch_step", "irk_batch_get_state", "irk_batch_get_stages", "irk_batch_remove",
+    "irk_batch_count", "irk_batch_last_error", "irk_batch_destroy",
 )
 
 
@@ -521,6 +533,91 @@ class IrkSolver:
         if self.h is not None:
             irk_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class IrkBatch:
+    """Owning wrapper around an irk_batch (include/irk_batch.h): many 2D
+    Burgers problems of different sizes stepped together (marshalling only)."""
+
+    def __init__(self, capacity: int, stream=None):
+        self.capacity = capacity
+        self.b = C.c_void_p()
+        sp = None
+        if stream is not None:
+            sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        st = LIB.irk_batch_create(capacity, sp, C.byref(self.b))
+        if st != IRK_OK:
+            raise IrkError(st, "irk_batch_create failed")
+        self.shapes = {}
+
+    def _check(self, st):
+        if st != IRK_OK:
+            raise IrkError(st, LIB.irk_batch_last_error(self.b).decode(errors="replace"))
+
+    @staticmethod
+    def instance_bytes(cfg: IrkConfig) -> int:
+        return LIB.irk_batch_instance_bytes(C.byref(cfg))
+
+    def add(self, u0, dt: float, arena_ptr: int = 0, arena_bytes: int = 0, **cfg) -> int:
+        c = irk_config_default(**cfg)
+        p, dev = _ptr(u0)
+        _need(u0, 2 * c.n * c.n, "u0")
+        slot = C.c_int(-1)
+        self._check(LIB.irk_batch_add(self.b, C.byref(c), p, dev, dt,
+                                      C.c_void_p(arena_ptr) if arena_ptr else None, arena_bytes,
+                                      C.byref(slot)))
+        self.shapes[slot.value] = ((2, c.n, c.n), c.stages)
+        return slot.value
+
+    def step(self):
+        """One step of every resident instance; returns {slot: (status, stats dict)}."""
+        stats = (IrkStats * self.capacity)()
+        status = (C.c_int * self.capacity)()
+        self._check(LIB.irk_batch_step(self.b, stats, status))
+        return {k: (status[k], stats[k].as_dict()) for k in self.shapes}
+
+    def state(self, slot: int, out=None):
+        import numpy as np
+        if out is None:
+            out = np.empty(self.shapes[slot][0])
+        p, dev = _ptr(out)
+        _need(out, int(np.prod(self.shapes[slot][0])), "out")
+        self._check(LIB.irk_batch_get_state(self.b, slot, p, dev))
+        return out
+
+    def stages(self, slot: int, out=None):
+        import numpy as np
+        shape, s = self.shapes[slot]
+        if out is None:
+            out = np.empty((s,) + shape)
+        p, dev = _ptr(out)
+        _need(out, s * int(np.prod(shape)), "out")
+        self._check(LIB.irk_batch_get_stages(self.b, slot, p, dev))
+        return out
+
+    def remove(self, slot: int):
+        self._check(LIB.irk_batch_remove(self.b, slot))
+        self.shapes.pop(slot, None)
+
+    def count(self) -> int:
+        return LIB.irk_batch_count(self.b)
+
+    def close(self):
+        if self.b:
+            LIB.irk_batch_destroy(self.b)
+            self.b = C.c_void_p()
 
     def __del__(self):
         try:

@@ -258,3 +258,29 @@ def test_config_defaults_are_the_documented_ones(B):
     assert (c.initial_guess, c.nonlinear_variant, c.dirk_sequential, c.dae_solver) == (2, 2, 1, 0)
     assert (c.mg_tile_rows, c.mg_fuse_transfer, c.mg_levels) == (0, 0, 0)
     assert c.use_graphs == 1 and c.newton_rtol == 1e-10
+
+
+def test_batch_instance_bytes_accepts_only_the_batched_configurations(B):
+    """irk_batch_instance_bytes (host-only) sizes an instance's arena for the
+    batched 2D Burgers path and returns 0 for what it does not serve."""
+    ok = B.irk_config_default(op="burgers2d", n=64, stages=3, nu=1e-2)
+    small = B.IrkBatch.instance_bytes(ok)
+    assert small > 0
+    bigger = B.IrkBatch.instance_bytes(B.irk_config_default(op="burgers2d", n=128, stages=3, nu=1e-2))
+    assert bigger > 3 * small
+    more_stages = B.IrkBatch.instance_bytes(B.irk_config_default(op="burgers2d", n=64, stages=4, nu=1e-2))
+    assert more_stages > small
+    for kw in (dict(op="burgers1d", n=64), dict(op="vsf", n=64), dict(op="burgers2d", n=16),
+               dict(op="burgers2d", n=64, mg_precision=1), dict(op="burgers2d", n=64, nonlinear_variant=3),
+               dict(op="burgers2d", n=64, family="lobatto", stages=3),
+               dict(op="burgers2d", n=64, krylov_restart=40), dict(op="burgers2d", n=96)):
+        assert B.IrkBatch.instance_bytes(B.irk_config_default(**kw)) == 0, kw
+
+
+def test_batch_create_without_a_device(B):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    with pytest.raises(B.IrkError) as ei:
+        B.IrkBatch(4)
+    assert ei.value.status == B.IRK_ERR_NO_DEVICE
