@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the s=3 / FP32 / e2e / CPU legs")
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the 512-request serving mix to run (0 = skip)")
-    ap.add_argument("--serving-rates", default="25,50,200",
+    ap.add_argument("--serving-rates", default="50,100,400",
                     help="Poisson arrival rates to sweep, req/s (comma-separated)")
     return ap.parse_args()
 
@@ -503,6 +503,21 @@ def run_ours(args, rank, world):
                 "per_rate": [serving_leg(B, args.serving_requests, r, slots=8) for r in rates]}
             line["serving_32_slots"] = serving_leg(B, args.serving_requests, rates[-1],
                                                    slots=32, budget_gib=48)
+            # the batched form: every resident request in one graph launch
+            # per step (include/irk_batch.h), same mix and rates
+            line["batched_serving"] = {
+                "requests": args.serving_requests, "of_mix": 512, "capacity": 32,
+                "per_rate": [serving_leg(B, args.serving_requests, r, slots=32, budget_gib=48,
+                                         batched=True) for r in rates]}
+            # the 64^2/128^2 part of the mix at the highest rate, both forms
+            small = [r for r in workloads.serving_requests(512, seed=4)[:args.serving_requests]
+                     if r["n"] <= 128]
+            line["serving_small_grids"] = {
+                "requests": len(small), "grids": [64, 128], "arrival_rate_per_s": rates[-1],
+                "streams_8_slots": serving_leg(B, 0, rates[-1], slots=8, reqs=small),
+                "streams_32_slots": serving_leg(B, 0, rates[-1], slots=32, budget_gib=48, reqs=small),
+                "batched_32": serving_leg(B, 0, rates[-1], slots=32, budget_gib=48, batched=True,
+                                          reqs=small)}
         # ---- precision report: one step from u0 per V-cycle storage precision
         prec_u = {}
         for prec, name in ((0, "fp64"), (1, "fp32"), (2, "bf16")):
@@ -538,7 +553,7 @@ def run_ours(args, rank, world):
         # four significant digits (the tail of the line is what logs keep)
         for k in ("kernels", "roofline_next", "variants", "solver_comparison", "gauss_vs_sdirk",
                   "vsf_dae_solvers", "autotuned", "serving_32_slots", "serving",
-                  "batched_serving", "precision"):
+                  "serving_small_grids", "batched_serving", "precision"):
             if k in line:
                 line[k] = _round(line.pop(k))
         print(json.dumps(line), flush=True)
@@ -673,19 +688,24 @@ def vsf_precision_leg(B, torch, dev, stream):
             "per_precision": rep}
 
 
-def serving_leg(B, count, rate, slots=8, budget_gib=24):
+def serving_leg(B, count, rate, slots=8, budget_gib=24, batched=False, reqs=None):
     """Config [4]: the first `count` requests of the seeded 512-request mix
     (2D Burgers, grid from {64,128,256,512}^2, nu log-uniform in [1e-3,1e-1],
     Gauss s in {2,3,4}, random-Fourier initial field seeded by request id,
-    20 steps at dt=1e-3), Poisson arrivals at `rate` req/s, served by the
-    continuous-batching runtime with `slots` slots and an HBM budget."""
+    20 steps at dt=1e-3), or the given `reqs`, Poisson arrivals at `rate`
+    req/s, served by the continuous-batching runtime with `slots` slots (one
+    stream and host thread each) or, batched, by the batched server with
+    `slots` resident requests stepped together, within an HBM budget."""
     import threading
     import workloads
-    reqs = workloads.serving_requests(512, seed=4)[:count]
+    if reqs is None:
+        reqs = workloads.serving_requests(512, seed=4)[:count]
+    count = len(reqs)
     u0s = {}
     for r in reqs:
         u0s[r["id"]] = workloads.random_fourier_2d(r["n"], seed=r["seed"])
-    srv = B.irk_server_create(slots, budget_gib << 30)
+    srv = (B.irk_server_create_batched(slots, budget_gib << 30) if batched
+           else B.irk_server_create(slots, budget_gib << 30))
     ids = [None] * len(reqs)
     rng = np.random.default_rng(5)
     gaps = rng.exponential(1.0 / rate, size=len(reqs))
@@ -707,6 +727,7 @@ def serving_leg(B, count, rate, slots=8, budget_gib=24):
     st = B.irk_server_stats_get(srv)
     B.irk_server_destroy(srv)
     return {"requests": count, "of_mix": 512, "arrival_rate_per_s": rate, "slots": slots,
+            "form": "batched" if batched else "streams",
             "budget_GiB": budget_gib, "failed": failed, "steps": st["steps"],
             "steps_per_s": st["steps_per_s"], "wall_s": st["wall_s"],
             "p50_step_ms": st["p50_step_ms"], "p99_step_ms": st["p99_step_ms"],

@@ -49,6 +49,17 @@ typedef struct {
  * (bytes; 0 = half of the currently free device memory), reserved at once. */
 irk_status irk_server_create(int slots, size_t budget_bytes, irk_server** out);
 
+/* The batched form of the server (include/irk_batch.h): up to `capacity`
+ * (1..64) resident requests are advanced together, one CUDA graph launch per
+ * step covering all of them, by a single driver thread; a request is admitted
+ * when a slot is free and its arena (irk_batch_instance_bytes) fits in the
+ * free part of the budget, and leaves the batch when its steps are done.
+ * Every request's step latency is the wall time of the batched step it took
+ * part in.  Requests the batched path does not serve (see irk_batch.h) are
+ * rejected at submission with IRK_ERR_INVALID.  Results are bit for bit those
+ * of the same request alone in a batch. */
+irk_status irk_server_create_batched(int capacity, size_t budget_bytes, irk_server** out);
+
 /* Queue one problem: cfg as for irk_create (not profiled), initial state u0
  * (host, ncomp*n^dim values; copied), start time t0, step dt, nsteps steps.
  * Returns its id.  IRK_ERR_NOMEM if its arena exceeds the whole budget. */

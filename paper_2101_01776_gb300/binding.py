@@ -127,6 +127,7 @@ def _load():
         "irk_config_device_bytes": (sz, [P(IrkConfig)]),
         "irk_create_in": (i, [P(IrkConfig), vp, i, vp, vp, sz, P(vp)]),
         "irk_server_create": (i, [i, sz, P(vp)]),
+        "irk_server_create_batched": (i, [i, sz, P(vp)]),
         "irk_server_submit": (i, [vp, P(IrkConfig), vp, d, d, i, P(C.c_longlong)]),
         "irk_server_wait": (i, [vp, C.c_longlong, vp, P(IrkStats), vp]),
         "irk_server_stats_get": (i, [vp, P(IrkServerStats)]),
@@ -161,7 +162,7 @@ EXPORTED = (
     "irk_get_config", "irk_autotune", "irk_set_state_keep_stages", "irk_debug_bounds",
     "irk_measure_alu_peak", "irk_batch_create", "irk_batch_instance_bytes", "irk_batch_add",
     "irk_batch_step", "irk_batch_get_state", "irk_batch_get_stages", "irk_batch_remove",
-    "irk_batch_count", "irk_batch_last_error", "irk_batch_destroy",
+    "irk_batch_count", "irk_batch_last_error", "irk_batch_destroy", "irk_server_create_batched",
 )
 
 
@@ -380,6 +381,12 @@ def irk_create_in(cfg: IrkConfig, u0, arena_ptr: int, arena_bytes: int, stream=N
 def irk_server_create(slots: int, budget_bytes: int = 0):
     s = C.c_void_p()
     _check(LIB.irk_server_create(slots, budget_bytes, C.byref(s)))
+    return s
+
+
+def irk_server_create_batched(capacity: int, budget_bytes: int = 0):
+    s = C.c_void_p()
+    _check(LIB.irk_server_create_batched(capacity, budget_bytes, C.byref(s)))
     return s
 
 

@@ -1114,24 +1114,43 @@ Layout layout(const irk_config* c, double length_check, InstHost* ih, char* base
       R.coef[l] = take(4 * nl);
     }
   }
+  // The block solves of one instance run one after another (back
+  // substitution), so they share one set of Krylov and multigrid work
+  // buffers, sized for the largest block; each keeps its own FGMRES state.
+  int bsmax = 1;
+  for (int k = 0; k < tab.nblk; ++k) bsmax = std::max(bsmax, tab.bsize[k]);
+  const long long Lmax = bsmax * L;
+  double* V = take((m + 1) * Lmax);
+  double* Z = take(m * Lmax);
+  double* w = take(Lmax);
+  double* pin = take(Lmax);
+  double* pout = take(Lmax);
+  double* tmpb = take(L);
+  double *mb[kMaxLev], *mw[kMaxLev], *mw2[kMaxLev], *mr[kMaxLev];
+  for (int l = 0; l < nlev; ++l) {
+    const long long nl = (long long)(n >> l) * (n >> l);
+    mb[l] = l == 0 ? nullptr : take(2 * nl);
+    mw[l] = take(2 * nl);
+    mw2[l] = take(2 * nl);
+    mr[l] = take(2 * nl);
+  }
   for (int k = 0; k < tab.nblk; ++k) {
     SysHost& S = H.sys[k];
     S.a = tab.bstart[k];
     S.bs = tab.bsize[k];
     S.Lb = S.bs * L;
-    S.V = take((m + 1) * S.Lb);
-    S.Z = take(m * S.Lb);
-    S.w = take(S.Lb);
-    S.pin = take(S.Lb);
-    S.pout = take(S.Lb);
-    S.tmpb = take(L);
+    S.V = V;
+    S.Z = Z;
+    S.w = w;
+    S.pin = pin;
+    S.pout = pout;
+    S.tmpb = tmpb;
     S.fs = (FGState*)take((sizeof(FGState) + 7) / 8);
     for (int l = 0; l < nlev; ++l) {
-      const long long nl = (long long)(n >> l) * (n >> l);
-      S.mb[l] = l == 0 ? nullptr : take(2 * nl);
-      S.mw[l] = take(2 * nl);
-      S.mw2[l] = take(2 * nl);
-      S.mr[l] = take(2 * nl);
+      S.mb[l] = mb[l];
+      S.mw[l] = mw[l];
+      S.mw2[l] = mw2[l];
+      S.mr[l] = mr[l];
     }
   }
   lo.bytes = off;

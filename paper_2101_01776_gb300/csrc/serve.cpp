@@ -28,6 +28,7 @@
 #include <thread>
 #include <vector>
 
+#include "../../include/irk_batch.h"
 #include "../../include/irk_serve.h"
 #include "irk_internal.h"
 #include "pool.h"
@@ -77,9 +78,37 @@ struct irk_server {
   clk::time_point first_submit, last_done;
   std::vector<double> step_ms, req_ms, queue_ms;
   int device = 0;
+  // batched form: one driver thread steps every resident request together
+  bool batched = false;
+  irk_batch* batch = nullptr;
+  cudaStream_t bstream = nullptr;
 };
 
 namespace {
+
+// Completion bookkeeping of one request (caller holds no lock).
+void finish_request(irk_server* s, const std::shared_ptr<Request>& r, irk_status stt) {
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->pool.release(r->off, r->bytes);
+    --s->active;
+    r->status = stt;
+    r->t_done = clk::now();
+    r->done = true;
+    s->last_done = r->t_done;
+    if (stt == IRK_OK) {
+      ++s->completed;
+      s->steps += (long long)r->step_ms.size();
+      s->step_ms.insert(s->step_ms.end(), r->step_ms.begin(), r->step_ms.end());
+      s->req_ms.push_back(ms_between(r->t_submit, r->t_done));
+      s->queue_ms.push_back(ms_between(r->t_submit, r->t_admit));
+    } else {
+      ++s->failed;
+    }
+  }
+  s->cv_work.notify_all();
+  s->cv_done.notify_all();
+}
 
 void worker_loop(irk_server* s, int slot) {
   cudaSetDevice(s->device);
@@ -135,26 +164,98 @@ void worker_loop(irk_server* s, int slot) {
     } else {
       r->err = irk_last_error(nullptr);
     }
+    finish_request(s, r, stt);
+  }
+}
+
+// Batched form: admit waiting requests into free batch slots as their arenas
+// fit the budget, advance all residents by one step in one graph launch
+// (irk_batch_step), retire the finished ones; repeat.  The wall time of a
+// batched step is every resident's step latency.
+void batch_loop(irk_server* s) {
+  cudaSetDevice(s->device);
+  struct Res {
+    std::shared_ptr<Request> r;
+    int slot;
+  };
+  std::vector<Res> res;
+  std::vector<irk_stats> st(s->slots);
+  std::vector<irk_status> sts(s->slots);
+  for (;;) {
+    std::vector<std::shared_ptr<Request>> admitted;
     {
-      std::lock_guard<std::mutex> lk(s->mu);
-      s->pool.release(r->off, r->bytes);
-      --s->active;
-      r->status = stt;
-      r->t_done = clk::now();
-      r->done = true;
-      s->last_done = r->t_done;
-      if (stt == IRK_OK) {
-        ++s->completed;
-        s->steps += (long long)r->step_ms.size();
-        s->step_ms.insert(s->step_ms.end(), r->step_ms.begin(), r->step_ms.end());
-        s->req_ms.push_back(ms_between(r->t_submit, r->t_done));
-        s->queue_ms.push_back(ms_between(r->t_submit, r->t_admit));
-      } else {
-        ++s->failed;
+      std::unique_lock<std::mutex> lk(s->mu);
+      for (;;) {
+        if (s->stop) {
+          lk.unlock();
+          for (auto& x : res) irk_batch_remove(s->batch, x.slot);
+          return;
+        }
+        for (auto it = s->pending.begin();
+             it != s->pending.end() && (int)(res.size() + admitted.size()) < s->slots;) {
+          size_t off;
+          if (s->pool.alloc((*it)->bytes, &off)) {
+            (*it)->off = off;
+            (*it)->t_admit = clk::now();
+            admitted.push_back(*it);
+            it = s->pending.erase(it);
+            ++s->active;
+          } else {
+            ++it;
+          }
+        }
+        s->peak_active = std::max(s->peak_active, s->active);
+        if (!res.empty() || !admitted.empty()) break;
+        s->cv_work.wait(lk);
       }
     }
-    s->cv_work.notify_all();
-    s->cv_done.notify_all();
+    for (auto& r : admitted) {
+      memset(&r->stats, 0, sizeof(r->stats));
+      if (r->nsteps == 0) {
+        finish_request(s, r, IRK_OK);
+        continue;
+      }
+      int slot = -1;
+      const irk_status a = irk_batch_add(s->batch, &r->cfg, r->u.data(), 0, r->dt,
+                                         s->base + r->off, r->bytes, &slot);
+      if (a != IRK_OK) {
+        r->err = irk_batch_last_error(s->batch);
+        finish_request(s, r, a);
+        continue;
+      }
+      r->step_ms.reserve(r->nsteps);
+      res.push_back({r, slot});
+    }
+    if (res.empty()) continue;
+    const auto t0 = clk::now();
+    const irk_status e = irk_batch_step(s->batch, st.data(), sts.data());
+    const double ms = ms_between(t0, clk::now());
+    std::vector<Res> keep;
+    for (auto& x : res) {
+      Request& q = *x.r;
+      irk_status stt = e;
+      if (stt == IRK_OK) {
+        const irk_stats& one = st[x.slot];
+        q.step_ms.push_back(ms);
+        q.stats.steps += one.steps;
+        q.stats.newton_its += one.newton_its;
+        q.stats.krylov_its += one.krylov_its;
+        q.stats.prec_apps += one.prec_apps;
+        q.stats.vcycles += one.vcycles;
+        q.stats.max_newton_its = std::max(q.stats.max_newton_its, one.max_newton_its);
+        q.stats.final_rel_res = one.final_rel_res;
+        stt = sts[x.slot];
+      }
+      if (stt == IRK_OK && (int)q.step_ms.size() < q.nsteps) {
+        keep.push_back(x);
+        continue;
+      }
+      if (stt == IRK_OK) stt = irk_batch_get_state(s->batch, x.slot, q.u.data(), 0);
+      if (stt != IRK_OK && q.err.empty()) q.err = irk_batch_last_error(s->batch);
+      irk_batch_remove(s->batch, x.slot);
+      finish_request(s, x.r, stt);
+    }
+    res.swap(keep);
   }
 }
 
@@ -208,10 +309,51 @@ irk_status irk_server_create(int slots, size_t budget_bytes, irk_server** out) {
   return IRK_OK;
 }
 
+irk_status irk_server_create_batched(int capacity, size_t budget_bytes, irk_server** out) {
+  if (!out || capacity < 1 || capacity > 64) return IRK_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return IRK_ERR_NO_DEVICE;
+  }
+  irk_server* s = new (std::nothrow) irk_server();
+  if (!s) return IRK_ERR_NOMEM;
+  cudaGetDevice(&s->device);
+  if (budget_bytes == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { delete s; return IRK_ERR_CUDA; }
+    budget_bytes = fr / 2;
+  }
+  if (cudaMalloc((void**)&s->base, budget_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return IRK_ERR_NOMEM;
+  }
+  s->pool.init(budget_bytes);
+  s->slots = capacity;
+  s->batched = true;
+  irk_status st = IRK_OK;
+  if (cudaStreamCreateWithFlags(&s->bstream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    st = IRK_ERR_CUDA;
+  }
+  if (st == IRK_OK) st = irk_batch_create(capacity, s->bstream, &s->batch);
+  if (st != IRK_OK) {
+    if (s->bstream) cudaStreamDestroy(s->bstream);
+    cudaFree(s->base);
+    delete s;
+    return st;
+  }
+  s->workers.emplace_back(batch_loop, s);
+  *out = s;
+  return IRK_OK;
+}
+
 irk_status irk_server_submit(irk_server* s, const irk_config* cfg, const double* u0, double t0,
                              double dt, int nsteps, long long* id) {
   if (!s || !cfg || !u0 || !id || nsteps < 0 || !(dt > 0)) return IRK_ERR_INVALID;
-  const size_t bytes = irk_config_device_bytes(cfg);
+  const size_t bytes = s->batched ? irk_batch_instance_bytes(cfg) : irk_config_device_bytes(cfg);
   if (bytes == 0) return IRK_ERR_INVALID;
   if (bytes > s->pool.size()) return IRK_ERR_NOMEM;  // could never be admitted
   auto r = std::make_shared<Request>();
@@ -290,6 +432,8 @@ void irk_server_destroy(irk_server* s) {
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
   for (auto st : s->streams) cudaStreamDestroy(st);
+  if (s->batch) irk_batch_destroy(s->batch);
+  if (s->bstream) cudaStreamDestroy(s->bstream);
   if (s->base) cudaFree(s->base);
   delete s;
 }

@@ -162,3 +162,51 @@ def test_served_families_and_dae_solver_equal_alone(B):
             ref = sol.state()
         assert stats.steps == nsteps
         assert rel(u, ref) <= MIX_TOL, sp
+
+
+def served_batched(B, reqs, dt, nsteps, capacity, gaps=None):
+    srv = B.irk_server_create_batched(capacity, 2 << 30)
+    try:
+        ids = []
+        for k, q in enumerate(reqs):
+            cfg = B.irk_config_default(op="burgers2d", n=q["n"], stages=q["s"], nu=q["nu"])
+            ids.append(B.irk_server_submit(srv, cfg, q["u0"], 0.0, dt, nsteps))
+            if gaps is not None:
+                time.sleep(float(gaps[k]))
+        out = [B.irk_server_wait(srv, i, q["u0"].shape, nsteps) for i, q in zip(ids, reqs)]
+        st = B.irk_server_stats_get(srv)
+    finally:
+        B.irk_server_destroy(srv)
+    return out, st
+
+
+def test_batched_server_mix_equals_alone_and_oracle(B):
+    """The batched server (one graph launch per step for all residents):
+    requests arriving while others run give bit for bit the result they give
+    alone in the batched server, and a served request matches the oracle."""
+    dt, nsteps = 1e-3, 4
+    reqs = request_mix(9, seed=5)
+    gaps = np.random.default_rng(1).exponential(0.005, size=len(reqs))
+    served, st = served_batched(B, reqs, dt, nsteps, capacity=4, gaps=gaps)
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["steps"] == len(reqs) * nsteps and 1 <= st["peak_active"] <= 4
+    assert st["p50_step_ms"] <= st["p99_step_ms"] <= st["max_step_ms"]
+    for q, (u, stats, ms) in zip(reqs, served):
+        assert stats.steps == nsteps and len(ms) == nsteps
+        (u1, _, _), = served_batched(B, [q], dt, nsteps, capacity=1)[0]
+        assert np.array_equal(u, u1)
+    k = min(range(len(reqs)), key=lambda i: reqs[i]["n"] * reqs[i]["s"])
+    q = reqs[k]
+    ref, _ = orc.integrate(Problem("burgers2d", q["n"], q["nu"]), q["s"], q["u0"], 0.0, dt, nsteps)
+    assert rel(served[k][0], ref) <= 1e-8
+
+
+def test_batched_server_rejects_what_the_batch_does_not_serve(B):
+    srv = B.irk_server_create_batched(2, 1 << 30)
+    try:
+        cfg = B.irk_config_default(op="burgers1d", n=64, stages=2, nu=1e-2)
+        with pytest.raises(B.IrkError) as ei:
+            B.irk_server_submit(srv, cfg, np.zeros((1, 64)), 0.0, 1e-3, 2)
+        assert ei.value.status == B.IRK_ERR_INVALID
+    finally:
+        B.irk_server_destroy(srv)
