@@ -505,10 +505,13 @@ def run_ours(args, rank, world):
                                                    slots=32, budget_gib=48)
             # the batched form: every resident request in one graph launch
             # per step (include/irk_batch.h), same mix and rates
+            # (n >= 512 on 8 stream workers beside the batch: those grids fill
+            # the GPU alone and would hold the batch to their step time)
             line["batched_serving"] = {
                 "requests": args.serving_requests, "of_mix": 512, "capacity": 32,
+                "stream_slots_for_512": 8,
                 "per_rate": [serving_leg(B, args.serving_requests, r, slots=32, budget_gib=48,
-                                         batched=True) for r in rates]}
+                                         batched=True, streams_for_large=8) for r in rates]}
             # the 64^2/128^2 part of the mix at the highest rate, both forms
             small = [r for r in workloads.serving_requests(512, seed=4)[:args.serving_requests]
                      if r["n"] <= 128]
@@ -688,14 +691,17 @@ def vsf_precision_leg(B, torch, dev, stream):
             "per_precision": rep}
 
 
-def serving_leg(B, count, rate, slots=8, budget_gib=24, batched=False, reqs=None):
+def serving_leg(B, count, rate, slots=8, budget_gib=24, batched=False, reqs=None,
+                streams_for_large=0):
     """Config [4]: the first `count` requests of the seeded 512-request mix
     (2D Burgers, grid from {64,128,256,512}^2, nu log-uniform in [1e-3,1e-1],
     Gauss s in {2,3,4}, random-Fourier initial field seeded by request id,
     20 steps at dt=1e-3), or the given `reqs`, Poisson arrivals at `rate`
     req/s, served by the continuous-batching runtime with `slots` slots (one
     stream and host thread each) or, batched, by the batched server with
-    `slots` resident requests stepped together, within an HBM budget."""
+    `slots` resident requests stepped together (and, with streams_for_large,
+    the 512^2 requests on that many stream workers beside the batch), within
+    an HBM budget."""
     import threading
     import workloads
     if reqs is None:
@@ -704,7 +710,8 @@ def serving_leg(B, count, rate, slots=8, budget_gib=24, batched=False, reqs=None
     u0s = {}
     for r in reqs:
         u0s[r["id"]] = workloads.random_fourier_2d(r["n"], seed=r["seed"])
-    srv = (B.irk_server_create_batched(slots, budget_gib << 30) if batched
+    srv = (B.irk_server_create_batched(slots, budget_gib << 30, stream_slots=streams_for_large,
+                                       stream_min_n=512 if streams_for_large else 0) if batched
            else B.irk_server_create(slots, budget_gib << 30))
     ids = [None] * len(reqs)
     rng = np.random.default_rng(5)
@@ -727,7 +734,8 @@ def serving_leg(B, count, rate, slots=8, budget_gib=24, batched=False, reqs=None
     st = B.irk_server_stats_get(srv)
     B.irk_server_destroy(srv)
     return {"requests": count, "of_mix": 512, "arrival_rate_per_s": rate, "slots": slots,
-            "form": "batched" if batched else "streams",
+            "form": ("batched + %d streams for 512^2" % streams_for_large if streams_for_large
+                     else "batched") if batched else "streams",
             "budget_GiB": budget_gib, "failed": failed, "steps": st["steps"],
             "steps_per_s": st["steps_per_s"], "wall_s": st["wall_s"],
             "p50_step_ms": st["p50_step_ms"], "p99_step_ms": st["p99_step_ms"],

@@ -55,10 +55,15 @@ irk_status irk_server_create(int slots, size_t budget_bytes, irk_server** out);
  * when a slot is free and its arena (irk_batch_instance_bytes) fits in the
  * free part of the budget, and leaves the batch when its steps are done.
  * Every request's step latency is the wall time of the batched step it took
- * part in.  Requests the batched path does not serve (see irk_batch.h) are
- * rejected at submission with IRK_ERR_INVALID.  Results are bit for bit those
- * of the same request alone in a batch. */
-irk_status irk_server_create_batched(int capacity, size_t budget_bytes, irk_server** out);
+ * part in.  With stream_slots > 0, requests of grid size n >= stream_min_n
+ * are instead served as in irk_server_create by stream_slots worker threads,
+ * each with its own stream, next to the batch (large grids fill the GPU on
+ * their own and would hold every small request of the batch to their step
+ * time).  Requests the batched path does not serve (see irk_batch.h) are
+ * rejected at submission with IRK_ERR_INVALID.  A batched request's result is
+ * bit for bit that of the same request alone in a batch. */
+irk_status irk_server_create_batched(int capacity, int stream_slots, int stream_min_n,
+                                    size_t budget_bytes, irk_server** out);
 
 /* Queue one problem: cfg as for irk_create (not profiled), initial state u0
  * (host, ncomp*n^dim values; copied), start time t0, step dt, nsteps steps.

@@ -127,7 +127,7 @@ def _load():
         "irk_config_device_bytes": (sz, [P(IrkConfig)]),
         "irk_create_in": (i, [P(IrkConfig), vp, i, vp, vp, sz, P(vp)]),
         "irk_server_create": (i, [i, sz, P(vp)]),
-        "irk_server_create_batched": (i, [i, sz, P(vp)]),
+        "irk_server_create_batched": (i, [i, i, i, sz, P(vp)]),
         "irk_server_submit": (i, [vp, P(IrkConfig), vp, d, d, i, P(C.c_longlong)]),
         "irk_server_wait": (i, [vp, C.c_longlong, vp, P(IrkStats), vp]),
         "irk_server_stats_get": (i, [vp, P(IrkServerStats)]),
@@ -384,9 +384,11 @@ def irk_server_create(slots: int, budget_bytes: int = 0):
     return s
 
 
-def irk_server_create_batched(capacity: int, budget_bytes: int = 0):
+def irk_server_create_batched(capacity: int, budget_bytes: int = 0, stream_slots: int = 0,
+                              stream_min_n: int = 0):
     s = C.c_void_p()
-    _check(LIB.irk_server_create_batched(capacity, budget_bytes, C.byref(s)))
+    _check(LIB.irk_server_create_batched(capacity, stream_slots, stream_min_n, budget_bytes,
+                                         C.byref(s)))
     return s
 
 

@@ -50,6 +50,7 @@ struct Request {
   double t0 = 0, dt = 0;
   int nsteps = 0;
   size_t bytes = 0, off = 0;
+  bool in_batch = false;  // served by the batched driver (else by a stream worker)
   irk_status status = IRK_OK;
   irk_stats stats;
   std::string err;
@@ -80,6 +81,8 @@ struct irk_server {
   int device = 0;
   // batched form: one driver thread steps every resident request together
   bool batched = false;
+  int batch_capacity = 0;
+  int stream_min_n = 0;  // batched form: grids of n >= this go to the stream workers
   irk_batch* batch = nullptr;
   cudaStream_t bstream = nullptr;
 };
@@ -122,6 +125,7 @@ void worker_loop(irk_server* s, int slot) {
         // oldest pending request whose arena fits in the free budget
         for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
           size_t off;
+          if ((*it)->in_batch) continue;
           if (s->pool.alloc((*it)->bytes, &off)) {
             r = *it;
             r->off = off;
@@ -179,8 +183,8 @@ void batch_loop(irk_server* s) {
     int slot;
   };
   std::vector<Res> res;
-  std::vector<irk_stats> st(s->slots);
-  std::vector<irk_status> sts(s->slots);
+  std::vector<irk_stats> st(s->batch_capacity);
+  std::vector<irk_status> sts(s->batch_capacity);
   for (;;) {
     std::vector<std::shared_ptr<Request>> admitted;
     {
@@ -192,8 +196,12 @@ void batch_loop(irk_server* s) {
           return;
         }
         for (auto it = s->pending.begin();
-             it != s->pending.end() && (int)(res.size() + admitted.size()) < s->slots;) {
+             it != s->pending.end() && (int)(res.size() + admitted.size()) < s->batch_capacity;) {
           size_t off;
+          if (!(*it)->in_batch) {
+            ++it;
+            continue;
+          }
           if (s->pool.alloc((*it)->bytes, &off)) {
             (*it)->off = off;
             (*it)->t_admit = clk::now();
@@ -309,8 +317,11 @@ irk_status irk_server_create(int slots, size_t budget_bytes, irk_server** out) {
   return IRK_OK;
 }
 
-irk_status irk_server_create_batched(int capacity, size_t budget_bytes, irk_server** out) {
-  if (!out || capacity < 1 || capacity > 64) return IRK_ERR_INVALID;
+irk_status irk_server_create_batched(int capacity, int stream_slots, int stream_min_n,
+                                    size_t budget_bytes, irk_server** out) {
+  if (!out || capacity < 1 || capacity > 64 || stream_slots < 0 || stream_slots > 256 ||
+      (stream_slots > 0 && stream_min_n < 1))
+    return IRK_ERR_INVALID;
   *out = nullptr;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -331,21 +342,32 @@ irk_status irk_server_create_batched(int capacity, size_t budget_bytes, irk_serv
     return IRK_ERR_NOMEM;
   }
   s->pool.init(budget_bytes);
-  s->slots = capacity;
+  s->slots = capacity + stream_slots;
   s->batched = true;
+  s->batch_capacity = capacity;
+  s->stream_min_n = stream_slots > 0 ? stream_min_n : 0;
   irk_status st = IRK_OK;
   if (cudaStreamCreateWithFlags(&s->bstream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     st = IRK_ERR_CUDA;
   }
+  s->streams.resize(stream_slots);
+  for (int k = 0; k < stream_slots && st == IRK_OK; ++k)
+    if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      s->streams.resize(k);
+      st = IRK_ERR_CUDA;
+    }
   if (st == IRK_OK) st = irk_batch_create(capacity, s->bstream, &s->batch);
   if (st != IRK_OK) {
+    for (auto q : s->streams) cudaStreamDestroy(q);
     if (s->bstream) cudaStreamDestroy(s->bstream);
     cudaFree(s->base);
     delete s;
     return st;
   }
   s->workers.emplace_back(batch_loop, s);
+  for (int k = 0; k < stream_slots; ++k) s->workers.emplace_back(worker_loop, s, k);
   *out = s;
   return IRK_OK;
 }
@@ -353,7 +375,10 @@ irk_status irk_server_create_batched(int capacity, size_t budget_bytes, irk_serv
 irk_status irk_server_submit(irk_server* s, const irk_config* cfg, const double* u0, double t0,
                              double dt, int nsteps, long long* id) {
   if (!s || !cfg || !u0 || !id || nsteps < 0 || !(dt > 0)) return IRK_ERR_INVALID;
-  const size_t bytes = s->batched ? irk_batch_instance_bytes(cfg) : irk_config_device_bytes(cfg);
+  // the batched form serves a request in the batch unless its grid goes to
+  // the stream workers (n >= stream_min_n when there are any)
+  const bool in_batch = s->batched && !(s->stream_min_n > 0 && cfg->n >= s->stream_min_n);
+  const size_t bytes = in_batch ? irk_batch_instance_bytes(cfg) : irk_config_device_bytes(cfg);
   if (bytes == 0) return IRK_ERR_INVALID;
   if (bytes > s->pool.size()) return IRK_ERR_NOMEM;  // could never be admitted
   auto r = std::make_shared<Request>();
@@ -365,6 +390,7 @@ irk_status irk_server_submit(irk_server* s, const irk_config* cfg, const double*
   r->dt = dt;
   r->nsteps = nsteps;
   r->bytes = bytes;
+  r->in_batch = in_batch;
   r->t_submit = clk::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);

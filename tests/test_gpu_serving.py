@@ -210,3 +210,28 @@ def test_batched_server_rejects_what_the_batch_does_not_serve(B):
         assert ei.value.status == B.IRK_ERR_INVALID
     finally:
         B.irk_server_destroy(srv)
+
+
+def test_hybrid_server_batches_small_grids_and_streams_large_ones(B):
+    """The batched server with stream workers for n >= 128: the 32^2/64^2
+    requests run in the batch (bit for bit their result alone in a batch),
+    the 128^2 ones on their own streams (their single-instance result)."""
+    dt, nsteps = 1e-3, 3
+    reqs = request_mix(8, seed=9)
+    assert any(q["n"] >= 128 for q in reqs) and any(q["n"] < 128 for q in reqs)
+    srv = B.irk_server_create_batched(4, 2 << 30, stream_slots=2, stream_min_n=128)
+    try:
+        ids = [B.irk_server_submit(srv, B.irk_config_default(op="burgers2d", n=q["n"], stages=q["s"],
+                                                             nu=q["nu"]), q["u0"], 0.0, dt, nsteps)
+               for q in reqs]
+        served = [B.irk_server_wait(srv, i, q["u0"].shape, nsteps)[0] for i, q in zip(ids, reqs)]
+        st = B.irk_server_stats_get(srv)
+    finally:
+        B.irk_server_destroy(srv)
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    for q, u in zip(reqs, served):
+        if q["n"] >= 128:
+            assert rel(u, alone(B, q, dt, nsteps)) <= MIX_TOL
+        else:
+            (u1, _, _), = served_batched(B, [q], dt, nsteps, capacity=1)[0]
+            assert np.array_equal(u, u1)
