@@ -87,6 +87,12 @@ typedef enum {
 
 typedef enum { IRK_MASS_IDENTITY = 0, IRK_MASS_DAE = 1 } irk_mass;
 
+/* Storage and arithmetic of the V-cycle preconditioner (Newton residual,
+ * stage updates, FGMRES and its Gram-Schmidt stay FP64 in every case):
+ * FP64 everything FP64; FP32 vectors and operator data in FP32 with FP32
+ * arithmetic; BF16 the operator data (the velocity of every level) stored in
+ * BF16, vectors (iterates, right-hand sides, residuals) in FP32, FP32
+ * arithmetic. */
 typedef enum { IRK_MG_FP64 = 0, IRK_MG_FP32 = 1, IRK_MG_BF16 = 2 } irk_mg_precision;
 
 typedef struct {

@@ -328,6 +328,11 @@ void launch_mg_coarse(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
 void launch_mg_convert_in(int prec, const double* src, void* dst, long long len, cudaStream_t st);
 void launch_mg_convert_out(int prec, const void* src, double* dst, long long len,
                            cudaStream_t st);
+// bytes per value of the V-cycle's vectors and of its velocity fields
 size_t mg_elem_size(int prec);
+size_t mg_vel_size(int prec);
+// full weighting of a velocity hierarchy (stored as the precision's velocity type)
+void launch_mg_restrict_vel(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* vf,
+                            void* vc, cudaStream_t st);
 
 }  // namespace irk

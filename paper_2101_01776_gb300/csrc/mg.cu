@@ -79,9 +79,9 @@ struct Coef4 {
   TC e, w, n, s;
 };
 
-template <typename TS, int DIM, int KIND>
+template <typename TS, int DIM, int KIND, typename TV = TS>
 __device__ __forceinline__ Coef4<typename Cmp<TS>::T> stencil_coef(
-    const LvIdx& q, const TS* __restrict__ vel, int npts, typename Cmp<TS>::T alpha,
+    const LvIdx& q, const TV* __restrict__ vel, int npts, typename Cmp<TS>::T alpha,
     typename Cmp<TS>::T beta) {
   // alpha = cadv / (2h), beta = -cdiff / h^2 (off-diagonal diffusion weight)
   typedef typename Cmp<TS>::T TC;
@@ -184,9 +184,9 @@ __device__ __forceinline__ typename Cmp<TS>::T ld_rhs(const TS* b, const double*
 // WIDE (reduced-precision storage, finest level): read b from the FP64 input
 // b64 and write the result to the FP64 output out64 instead of w_out, both
 // rounded as the stored copies would be.
-template <typename TS, int DIM, int KIND, bool WIDE = false>
+template <typename TS, int DIM, int KIND, bool WIDE = false, typename TV = TS>
 __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, MGConst k,
-                                                   const TS* __restrict__ vel,
+                                                   const TV* __restrict__ vel,
                                                    const TS* __restrict__ b,
                                                    const TS* __restrict__ w_in,
                                                    TS* __restrict__ w_out, int first,
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, MG
       }
       continue;
     }
-    const Coef4<TC> cf = stencil_coef<TS, DIM, KIND>(q, vel, lv.npts, alpha, beta);
+    const Coef4<TC> cf = stencil_coef<TS, DIM, KIND, TV>(q, vel, lv.npts, alpha, beta);
     for (int c = 0; c < ncomp; ++c) {
       const long long off = (long long)c * lv.npts;
       const TC t = rhs_minus_offdiag<TS, DIM>(q, w_in + off, cf, rhs(off + p));
@@ -226,9 +226,9 @@ __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, MG
   }
 }
 
-template <typename TS, int DIM, int KIND>
+template <typename TS, int DIM, int KIND, typename TV = TS>
 __global__ void __launch_bounds__(256) k_mg_residual(MGLevelDesc lv, int ncomp, MGConst k,
-                                                     const TS* __restrict__ vel,
+                                                     const TV* __restrict__ vel,
                                                      const TS* __restrict__ b,
                                                      const TS* __restrict__ w, TS* __restrict__ r) {
   typedef typename Cmp<TS>::T TC;
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(256) k_mg_residual(MGLevelDesc lv, int ncomp, 
   const TC alpha = TC(k.alpha), beta = TC(k.beta);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lv.npts; p += gridDim.x * blockDim.x) {
     const LvIdx q = lv_nbr<DIM>(lv, p);
-    const Coef4<TC> cf = stencil_coef<TS, DIM, KIND>(q, vel, lv.npts, alpha, beta);
+    const Coef4<TC> cf = stencil_coef<TS, DIM, KIND, TV>(q, vel, lv.npts, alpha, beta);
     for (int c = 0; c < ncomp; ++c) {
       const long long off = (long long)c * lv.npts;
       const TC t = rhs_minus_offdiag<TS, DIM>(q, w + off, cf, ldv(b + off + p));
@@ -248,9 +248,9 @@ __global__ void __launch_bounds__(256) k_mg_residual(MGLevelDesc lv, int ncomp, 
 // Residual after one damped-Jacobi sweep from w = 0, without storing that
 // sweep: w = dinv b, so r = b - A w = (1 - omega) b - dinv sum_k c_k b_k.
 // The prolongation then rebuilds w = dinv b + P e (k_mg_prolong<SET>).
-template <typename TS, int DIM, int KIND>
+template <typename TS, int DIM, int KIND, typename TV = TS>
 __global__ void __launch_bounds__(256) k_mg_residual0(MGLevelDesc lv, int ncomp, MGConst k,
-                                                      const TS* __restrict__ vel,
+                                                      const TV* __restrict__ vel,
                                                       const TS* __restrict__ b, TS* __restrict__ r,
                                                       const double* __restrict__ b64) {
   typedef typename Cmp<TS>::T TC;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(256) k_mg_residual0(MGLevelDesc lv, int ncomp,
   const TC dinv = TC(k.dinv), keep = TC(k.keep);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lv.npts; p += gridDim.x * blockDim.x) {
     const LvIdx q = lv_nbr<DIM>(lv, p);
-    const Coef4<TC> cf = stencil_coef<TS, DIM, KIND>(q, vel, lv.npts, alpha, beta);
+    const Coef4<TC> cf = stencil_coef<TS, DIM, KIND, TV>(q, vel, lv.npts, alpha, beta);
 #pragma unroll 1
     for (int c = 0; c < ncomp; ++c) {
       const long long off = (long long)c * lv.npts;
@@ -290,9 +290,9 @@ constexpr int kTX = 32, kTY = 8;
 // becomes x_new = x_prev + omega (J(x) - x_prev), with x_prev the iterate
 // before x; the pair reads x_{k-1} (w_prev) and x_k (w_in) and writes x_{k+1}
 // (w_mid) and x_{k+2} (w_out).  `first`: x_0 = 0 (then w_in, w_prev unused).
-template <typename TS, int KIND, bool CHEB>
+template <typename TS, int KIND, bool CHEB, typename TV = TS>
 __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int ncomp, MGConst k,
-                                                        const TS* __restrict__ vel,
+                                                        const TV* __restrict__ vel,
                                                         const TS* __restrict__ b,
                                                         const TS* __restrict__ w_in,
                                                         TS* __restrict__ w_out, int first,
@@ -396,9 +396,9 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
 // of shared memory (TY = 8: 1028 point updates for 768 useful ones; TY = 16:
 // 1844 for 1536).  Intermediate sweeps are rounded to the storage type: three
 // single sweeps bit for bit.
-template <typename TS, int KIND, int TY>
+template <typename TS, int KIND, int TY, typename TV = TS>
 __global__ void __launch_bounds__(kTX * TY) k_mg_smooth3(MGLevelDesc lv, int ncomp, MGConst k,
-                                                        const TS* __restrict__ vel,
+                                                        const TV* __restrict__ vel,
                                                         const TS* __restrict__ b,
                                                         const TS* __restrict__ w_in,
                                                         TS* __restrict__ w_out, int first) {
@@ -493,9 +493,9 @@ __global__ void __launch_bounds__(kTX * TY) k_mg_smooth3(MGLevelDesc lv, int nco
 // points of the tile (128 of 256), so a sweep costs one update per point plus
 // 16% on the halo.  For a consistently ordered 5-point operator one GS sweep
 // reduces the error like two Jacobi sweeps (rho_GS = rho_J^2).  first: w = 0.
-template <typename TS, int KIND>
+template <typename TS, int KIND, typename TV = TS>
 __global__ void __launch_bounds__(kTX * kTY) k_mg_rbgs(MGLevelDesc lv, int ncomp, MGConst k,
-                                                     const TS* __restrict__ vel,
+                                                     const TV* __restrict__ vel,
                                                      const TS* __restrict__ b,
                                                      const TS* __restrict__ w_in,
                                                      TS* __restrict__ w_out, int first) {
@@ -736,9 +736,9 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MGLevelDesc fine, int ncomp
 // kernels, so the result is bit-identical, and r never goes to memory.
 constexpr int kRCX = 16, kRCY = 8;
 
-template <typename TS, int KIND>
+template <typename TS, int KIND, typename TV = TS>
 __global__ void __launch_bounds__(256) k_mg_resid0_restrict(MGLevelDesc fine, int ncomp, MGConst k,
-                                                            const TS* __restrict__ vel,
+                                                            const TV* __restrict__ vel,
                                                             const TS* __restrict__ b,
                                                             const double* __restrict__ b64,
                                                             TS* __restrict__ bc) {
@@ -766,7 +766,7 @@ __global__ void __launch_bounds__(256) k_mg_resid0_restrict(MGLevelDesc fine, in
     LvIdx pt;
     pt.c = tile_pt((fx0 - 1 + rx) & m, (fy0 - 1 + ry) & m, ln, n);
     pt.e = pt.w = pt.n = pt.s = pt.c;  // the 2D kinds read their coefficients at the point
-    const Coef4<TC> cf = stencil_coef<TS, 2, KIND>(pt, vel, npts, alpha, beta);
+    const Coef4<TC> cf = stencil_coef<TS, 2, KIND, TV>(pt, vel, npts, alpha, beta);
     const int sy = ry + 1, sx = rx + 1;  // the point in the b window
     for (int c = 0; c < ncomp; ++c) {
       TC sum = cf.e * s_b[c][sy][sx + 1];
@@ -837,10 +837,10 @@ __global__ void __launch_bounds__(256) k_mg_prolong_add(MGLevelDesc fine, int nc
 
 // Coarsest level in one CTA: w = 0, `sweeps` damped-Jacobi sweeps from shared
 // memory.  project_mean removes the constant null mode of a pure Laplacian.
-template <typename TS, int DIM, int KIND>
+template <typename TS, int DIM, int KIND, typename TV = TS>
 __global__ void k_mg_coarse(MGLevelDesc lv, int ncomp, double sigma_, double cadv_, double cdiff_,
                             double omega_, int sweeps, int project_mean,
-                            const TS* __restrict__ vel, const TS* __restrict__ b,
+                            const TV* __restrict__ vel, const TS* __restrict__ b,
                             TS* __restrict__ w) {
   typedef typename Cmp<TS>::T TC;
   extern __shared__ unsigned char smem_raw[];
@@ -926,15 +926,16 @@ static int grid_for(long long n) {
   return (int)b;
 }
 
-size_t mg_elem_size(int prec) {
-  return prec == IRK_MG_FP64 ? sizeof(double) : (prec == IRK_MG_FP32 ? sizeof(float) : 2);
-}
+size_t mg_elem_size(int prec) { return prec == IRK_MG_FP64 ? sizeof(double) : sizeof(float); }
 
-#define IRK_DISPATCH_PREC(prec, ...)                                    \
-  do {                                                                  \
-    if ((prec) == IRK_MG_FP64) { typedef double TS; __VA_ARGS__; }      \
-    else if ((prec) == IRK_MG_FP32) { typedef float TS; __VA_ARGS__; }  \
-    else { typedef __nv_bfloat16 TS; __VA_ARGS__; }                     \
+// TS: storage of the V-cycle's vectors (iterates, right-hand sides,
+// residuals); TV: storage of its operator data (the level velocities).
+// IRK_MG_BF16 keeps the vectors in FP32 and stores the velocities in BF16.
+#define IRK_DISPATCH_PREC(prec, ...)                                                        \
+  do {                                                                                      \
+    if ((prec) == IRK_MG_FP64) { typedef double TS; typedef double TV; __VA_ARGS__; }       \
+    else if ((prec) == IRK_MG_FP32) { typedef float TS; typedef float TV; __VA_ARGS__; }    \
+    else { typedef float TS; typedef __nv_bfloat16 TV; __VA_ARGS__; }                       \
   } while (0)
 
 #define IRK_DISPATCH_DK(dim, kind, ...)                                                  \
@@ -973,12 +974,12 @@ void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
   if (prec != IRK_MG_FP64 && !wide) epi_out = nullptr;  // the epilogue reads the FP64 result
   IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, {
     if (wide)
-      k_mg_smooth<TS, DIM, KIND, true><<<grid_for(lv.npts), 256, 0, st>>>(
-          lv, ncomp, k, (const TS*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, epi_out,
+      k_mg_smooth<TS, DIM, KIND, true, TV><<<grid_for(lv.npts), 256, 0, st>>>(
+          lv, ncomp, k, (const TV*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, epi_out,
           epi_base, epi_coef, epi_bcoef, b64, out64);
     else
-      k_mg_smooth<TS, DIM, KIND, false><<<grid_for(lv.npts), 256, 0, st>>>(
-          lv, ncomp, k, (const TS*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, epi_out,
+      k_mg_smooth<TS, DIM, KIND, false, TV><<<grid_for(lv.npts), 256, 0, st>>>(
+          lv, ncomp, k, (const TV*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, epi_out,
           epi_base, epi_coef, epi_bcoef, nullptr, nullptr);
   }));
 }
@@ -1015,13 +1016,13 @@ void launch_mg_smooth2(int prec, int kind, const MGLevelDesc& lv, int ncomp, dou
   const dim3 grid(lv.n / kTX, lv.n / kTY, zsplit), block(kTX, kTY);
   IRK_DISPATCH_PREC(prec, {
     if (kind == MG_ADVECTIVE)
-      k_mg_smooth2<TS, MG_ADVECTIVE, false><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+      k_mg_smooth2<TS, MG_ADVECTIVE, false, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first, nullptr, nullptr, 1.0, 1.0);
     else if (kind == MG_ADVECTIVE_PRE)
-      k_mg_smooth2<TS, MG_ADVECTIVE_PRE, false><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+      k_mg_smooth2<TS, MG_ADVECTIVE_PRE, false, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first, nullptr, nullptr, 1.0, 1.0);
     else
-      k_mg_smooth2<TS, MG_DIFFUSION, false><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+      k_mg_smooth2<TS, MG_DIFFUSION, false, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first, nullptr, nullptr, 1.0, 1.0);
   });
 }
@@ -1034,13 +1035,13 @@ void launch_mg_rbgs(int prec, int kind, const MGLevelDesc& lv, int ncomp, double
   const dim3 grid(lv.n / kTX, lv.n / kTY, zsplit), block(kTX, kTY);
   IRK_DISPATCH_PREC(prec, {
     if (kind == MG_ADVECTIVE)
-      k_mg_rbgs<TS, MG_ADVECTIVE><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+      k_mg_rbgs<TS, MG_ADVECTIVE, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
     else if (kind == MG_ADVECTIVE_PRE)
-      k_mg_rbgs<TS, MG_ADVECTIVE_PRE><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+      k_mg_rbgs<TS, MG_ADVECTIVE_PRE, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
     else
-      k_mg_rbgs<TS, MG_DIFFUSION><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+      k_mg_rbgs<TS, MG_DIFFUSION, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
   });
 }
@@ -1059,13 +1060,13 @@ void launch_mg_smooth3(int prec, int kind, const MGLevelDesc& lv, int ncomp, dou
 #define IRK_S3(TY_)                                                                               \
   do {                                                                                            \
     if (kind == MG_ADVECTIVE)                                                                     \
-      k_mg_smooth3<TS, MG_ADVECTIVE, TY_><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,   \
+      k_mg_smooth3<TS, MG_ADVECTIVE, TY_, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,   \
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                                      \
     else if (kind == MG_ADVECTIVE_PRE)                                                            \
-      k_mg_smooth3<TS, MG_ADVECTIVE_PRE, TY_><<<grid, block, 0, st>>>(lv, ncomp, k,               \
-          (const TS*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                      \
+      k_mg_smooth3<TS, MG_ADVECTIVE_PRE, TY_, TV><<<grid, block, 0, st>>>(lv, ncomp, k,               \
+          (const TV*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                      \
     else                                                                                          \
-      k_mg_smooth3<TS, MG_DIFFUSION, TY_><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,   \
+      k_mg_smooth3<TS, MG_DIFFUSION, TY_, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,   \
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                                      \
   } while (0)
   IRK_DISPATCH_PREC(prec, {
@@ -1084,13 +1085,13 @@ void launch_mg_cheb2(int prec, int kind, const MGLevelDesc& lv, int ncomp, doubl
   const dim3 grid(lv.n / kTX, lv.n / kTY, zsplit), block(kTX, kTY);
   IRK_DISPATCH_PREC(prec, {
     if (kind == MG_ADVECTIVE)
-      k_mg_smooth2<TS, MG_ADVECTIVE, true><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+      k_mg_smooth2<TS, MG_ADVECTIVE, true, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)x_cur, (TS*)x_out, first, (const TS*)x_prev, (TS*)x_mid, wa, wb);
     else if (kind == MG_ADVECTIVE_PRE)
-      k_mg_smooth2<TS, MG_ADVECTIVE_PRE, true><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+      k_mg_smooth2<TS, MG_ADVECTIVE_PRE, true, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)x_cur, (TS*)x_out, first, (const TS*)x_prev, (TS*)x_mid, wa, wb);
     else
-      k_mg_smooth2<TS, MG_DIFFUSION, true><<<grid, block, 0, st>>>(lv, ncomp, k, (const TS*)vel,
+      k_mg_smooth2<TS, MG_DIFFUSION, true, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)x_cur, (TS*)x_out, first, (const TS*)x_prev, (TS*)x_mid, wa, wb);
   });
 }
@@ -1099,8 +1100,8 @@ void launch_mg_residual(int prec, int dim, int kind, const MGLevelDesc& lv, int 
                         double sigma, double cadv, double cdiff, const void* vel, const void* b,
                         const void* w, void* r, cudaStream_t st) {
   const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, 1.0);
-  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_residual<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
-      lv, ncomp, k, (const TS*)vel, (const TS*)b, (const TS*)w, (TS*)r))));
+  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_residual<TS, DIM, KIND, TV><<<grid_for(lv.npts), 256, 0, st>>>(
+      lv, ncomp, k, (const TV*)vel, (const TS*)b, (const TS*)w, (TS*)r))));
 }
 
 void launch_mg_restrict(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* rf,
@@ -1112,6 +1113,21 @@ void launch_mg_restrict(int prec, int dim, const MGLevelDesc& fine, int ncomp, c
     else
       k_mg_restrict<TS, 2><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)rf, (TS*)bc);
   });
+}
+
+void launch_mg_restrict_vel(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* vf,
+                            void* vc, cudaStream_t st) {
+  const long long nc = dim == 1 ? fine.n / 2 : (long long)(fine.n / 2) * (fine.n / 2);
+  IRK_DISPATCH_PREC(prec, {
+    if (dim == 1)
+      k_mg_restrict<TV, 1><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TV*)vf, (TV*)vc);
+    else
+      k_mg_restrict<TV, 2><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TV*)vf, (TV*)vc);
+  });
+}
+
+size_t mg_vel_size(int prec) {
+  return prec == IRK_MG_FP64 ? sizeof(double) : (prec == IRK_MG_FP32 ? sizeof(float) : 2);
 }
 
 void launch_mg_prolong_add(int prec, int dim, const MGLevelDesc& fine, int ncomp, const void* wc,
@@ -1201,8 +1217,10 @@ void launch_mg_setup2(const MGLevelDesc& fine, const MGLevelDesc& coarse, double
 void launch_mg_coef(int prec, const MGLevelDesc& lv, double cadv, double cdiff, const void* vel,
                     void* coef, cudaStream_t st) {
   const MGConst k = mg_const(lv, 2, 0.0, cadv, cdiff, 1.0);
-  IRK_DISPATCH_PREC(prec, (k_mg_coef<TS><<<grid_for(lv.npts), 256, 0, st>>>(
-      lv, k.alpha, k.beta, (const TS*)vel, (TS*)coef)));
+  // the precomputed-coefficient form serves FP64 storage only
+  if (prec != IRK_MG_FP64) return;
+  k_mg_coef<double><<<grid_for(lv.npts), 256, 0, st>>>(lv, k.alpha, k.beta, (const double*)vel,
+                                                      (double*)coef);
 }
 
 void launch_mg_residual0(int prec, int dim, int kind, const MGLevelDesc& lv, int ncomp,
@@ -1210,8 +1228,8 @@ void launch_mg_residual0(int prec, int dim, int kind, const MGLevelDesc& lv, int
                          const void* b, void* r, cudaStream_t st, const double* b64) {
   const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, omega);
   if (prec == IRK_MG_FP64) b64 = nullptr;
-  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_residual0<TS, DIM, KIND><<<grid_for(lv.npts), 256, 0, st>>>(
-      lv, ncomp, k, (const TS*)vel, (const TS*)b, (TS*)r, b64))));
+  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_residual0<TS, DIM, KIND, TV><<<grid_for(lv.npts), 256, 0, st>>>(
+      lv, ncomp, k, (const TV*)vel, (const TS*)b, (TS*)r, b64))));
 }
 
 void launch_mg_resid0_restrict(int prec, int kind, const MGLevelDesc& fine, int ncomp,
@@ -1223,13 +1241,13 @@ void launch_mg_resid0_restrict(int prec, int kind, const MGLevelDesc& fine, int 
   const dim3 grid((fine.n / 2) / kRCX, (fine.n / 2) / kRCY);
   IRK_DISPATCH_PREC(prec, {
     if (kind == MG_ADVECTIVE)
-      k_mg_resid0_restrict<TS, MG_ADVECTIVE><<<grid, 256, 0, st>>>(fine, ncomp, k, (const TS*)vel,
+      k_mg_resid0_restrict<TS, MG_ADVECTIVE, TV><<<grid, 256, 0, st>>>(fine, ncomp, k, (const TV*)vel,
                                                                   (const TS*)b, b64, (TS*)bc);
     else if (kind == MG_ADVECTIVE_PRE)
-      k_mg_resid0_restrict<TS, MG_ADVECTIVE_PRE><<<grid, 256, 0, st>>>(
-          fine, ncomp, k, (const TS*)vel, (const TS*)b, b64, (TS*)bc);
+      k_mg_resid0_restrict<TS, MG_ADVECTIVE_PRE, TV><<<grid, 256, 0, st>>>(
+          fine, ncomp, k, (const TV*)vel, (const TS*)b, b64, (TS*)bc);
     else
-      k_mg_resid0_restrict<TS, MG_DIFFUSION><<<grid, 256, 0, st>>>(fine, ncomp, k, (const TS*)vel,
+      k_mg_resid0_restrict<TS, MG_DIFFUSION, TV><<<grid, 256, 0, st>>>(fine, ncomp, k, (const TV*)vel,
                                                                   (const TS*)b, b64, (TS*)bc);
   });
 }
@@ -1265,8 +1283,8 @@ void launch_mg_coarse(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
     typedef typename Cmp<TS>::T TC;
     const size_t smem = sizeof(TC) * ((size_t)3 * ncomp * lv.npts + (size_t)dim * lv.npts);
     // the one-CTA kernel takes the velocity (MG_ADVECTIVE), never precomputed coefficients
-    IRK_DISPATCH_DK_VEL(dim, kind, (k_mg_coarse<TS, DIM, KIND><<<1, 256, smem, st>>>(
-        lv, ncomp, sigma, cadv, cdiff, omega, sweeps, project_mean, (const TS*)vel,
+    IRK_DISPATCH_DK_VEL(dim, kind, (k_mg_coarse<TS, DIM, KIND, TV><<<1, 256, smem, st>>>(
+        lv, ncomp, sigma, cadv, cdiff, omega, sweeps, project_mean, (const TV*)vel,
         (const TS*)b, (TS*)w)));
   });
 }

@@ -440,9 +440,10 @@ void mg_setup(irk_handle* h, double dt) {
       launch_velocity_from_combo(h->g, combo_ptr(h, k, k), h->vel[k][0], h->prec, h->st);
     }
     for (int l = fused ? 1 : 0; l + 1 < depth; ++l) {
-      ProfScope ps(h, P_MG_SETUP, mg_level_bytes(h, l, h->dim) * 1.25, 0);
-      launch_mg_restrict(h->prec, h->dim, h->lev[l].d, h->dim, h->vel[k][l], h->vel[k][l + 1],
-                         h->st);
+      ProfScope ps(h, P_MG_SETUP,
+                   mg_level_bytes(h, l, h->dim) * 1.25 * mg_vel_size(h->prec) / h->esz, 0);
+      launch_mg_restrict_vel(h->prec, h->dim, h->lev[l].d, h->dim, h->vel[k][l], h->vel[k][l + 1],
+                             h->st);
     }
     if (h->use_pre)
       for (int l = fused ? 2 : 0; l < depth; ++l) {
@@ -498,8 +499,10 @@ bool jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, doub
   bool epi_done = false;
   const MGLevelDesc& d = h->lev[l].d;
   const int prec = h->prec, dim = h->dim;
-  const int velf = (kind == MG_DIFFUSION) ? 0
-                   : (kind == MG_ADVECTIVE_PRE) ? 4 : (kind == MG_CONSERVATIVE_1D ? 1 : dim);
+  // velocity fields, in units of the vectors' value size (BF16 velocities: half)
+  const double velf = ((kind == MG_DIFFUSION) ? 0
+                       : (kind == MG_ADVECTIVE_PRE) ? 4 : (kind == MG_CONSERVATIVE_1D ? 1 : dim)) *
+                      (kind == MG_ADVECTIVE_PRE ? 1.0 : (double)mg_vel_size(prec) / h->esz);
   const double fsw = mg_sweep_flops(kind, dim, ncomp) * d.npts;  // one sweep
   const double f0 = (double)ncomp * d.npts;                       // a sweep from zero
   const double pts = (double)ncomp * d.npts;
@@ -580,8 +583,9 @@ bool vcycle(irk_handle* h, int row, int kind, int ncomp, double sigma, double ca
   for (int l = 0; l < nl; ++l) crow[l] = pre ? h->coefh[row][l] : vrow[l];
   const long long n0 = (long long)ncomp * h->lev[0].d.npts;
   const bool alias = (prec == IRK_MG_FP64);
-  const int velf = (kk == MG_DIFFUSION) ? 0
-                   : (kk == MG_ADVECTIVE_PRE) ? 4 : (kk == MG_CONSERVATIVE_1D ? 1 : dim);
+  const double velf = ((kk == MG_DIFFUSION) ? 0
+                       : (kk == MG_ADVECTIVE_PRE) ? 4 : (kk == MG_CONSERVATIVE_1D ? 1 : dim)) *
+                      (kk == MG_ADVECTIVE_PRE ? 1.0 : (double)mg_vel_size(prec) / h->esz);
   const double fsweep = mg_sweep_flops(kk, dim, ncomp), fresid = mg_resid_flops(kk, dim, ncomp);
   // a single pre-sweep starts from zero (w = dinv b): it is folded into the
   // residual and rebuilt by the prolongation, one launch less per level
@@ -2194,7 +2198,8 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
     const size_t f = h->esz * (size_t)h->lev[l].d.npts;
     add(f * h->C); add(f * h->C); add(f * h->C); add(f * h->C);
     if (l >= 1) { add(f * h->C); add(f * h->C); }
-    for (int k = 0; k < s; ++k) add(f * h->dim);
+    const size_t fv = mg_vel_size(h->prec) * (size_t)h->lev[l].d.npts;
+    for (int k = 0; k < s; ++k) add(fv * h->dim);
     if (h->use_pre)
       for (int k = 0; k < s; ++k) add(f * 4);
   }
@@ -2265,7 +2270,8 @@ irk_status build(irk_handle* h, const double* u0, int u0_on_device, bool plan_on
     h->lev[l].r = take(f * h->C);
     h->lev[l].w3 = (l >= 1) ? take(f * h->C) : nullptr;
     h->lev[l].w4 = (l >= 1) ? take(f * h->C) : nullptr;
-    for (int k = 0; k < s; ++k) h->vel[k][l] = take(f * h->dim);
+    const size_t fv = mg_vel_size(h->prec) * (size_t)h->lev[l].d.npts;
+    for (int k = 0; k < s; ++k) h->vel[k][l] = take(fv * h->dim);
     for (int k = 0; k < s; ++k) h->coefh[k][l] = h->use_pre ? take(f * 4) : nullptr;
   }
   for (int k = s; k < IRK_MAXS; ++k)
