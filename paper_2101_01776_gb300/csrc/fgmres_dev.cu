@@ -9,7 +9,9 @@
 // handle of a CUDA-graph WHILE node once the block has converged, lost its
 // basis, or used m iterations; k_fg_next also bounds the loop independently.
 // The arithmetic is the one of the host path (CGS2, Givens, back
-// substitution), in FP64.
+// substitution), in FP64.  Outside a graph (the solver's per-kernel timing
+// mode launches these kernels one by one) the handle is zero and the loop
+// state lives only in the FGState block.
 #include "irk_internal.h"
 
 namespace irk {
@@ -110,11 +112,11 @@ __global__ void k_fg_init(FGState* s, const double* __restrict__ nrm2, const dou
   if (!(beta > 0.0) || !isfinite(beta)) {
     s->status = isfinite(beta) ? 0 : 2;
     s->inv_scale = 0.0;
-    cudaGraphSetConditional(cond, 0);
+    if (cond) cudaGraphSetConditional(cond, 0);
   } else {
     s->status = 0;
     s->inv_scale = 1.0 / beta;
-    cudaGraphSetConditional(cond, 1);  // (re)open the loop for this cycle
+    if (cond) cudaGraphSetConditional(cond, 1);  // (re)open the loop for this cycle
   }
 }
 
@@ -267,7 +269,7 @@ __device__ void arnoldi_step(FGState* s, const double* h1, const double* h2, int
   if (!finite || res <= s->target || hn <= 1e-300 || j + 1 >= m || s->its >= maxit) {
     s->k = finite ? j + 1 : 0;
     s->stopped = 1;
-    cudaGraphSetConditional(cond, 0);
+    if (cond) cudaGraphSetConditional(cond, 0);
   } else {
     s->j = j + 1;
     s->inv_scale = 1.0 / hn;
@@ -357,7 +359,7 @@ k_fg_next(const double* __restrict__ V, long long ldv, FGState* s,
     if (++s->guard >= guard_limit) {
       s->status = 3;
       s->stopped = 1;
-      cudaGraphSetConditional(cond, 0);
+      if (cond) cudaGraphSetConditional(cond, 0);
     }
   }
   if (s->stopped) return;
@@ -434,13 +436,13 @@ __global__ void k_newton_first(double* nw, const double* __restrict__ f2, double
   nw[5] = 0.0;
   if (!isfinite(f0)) {
     nw[5] = (double)IRK_ERR_NEWTON_DIVERGED;
-    cudaGraphSetConditional(cond, 0);
+    if (cond) cudaGraphSetConditional(cond, 0);
   } else if (f0 == 0.0) {
-    cudaGraphSetConditional(cond, 0);  // k = 0 solves the stage equations
+    if (cond) cudaGraphSetConditional(cond, 0);  // k = 0 solves the stage equations
   } else {
     nw[6] = 1.0;
     rtol_slot[0] = forcing_term(1.0, 0.0, f0, f0, 0, newton_rtol, krylov_rtol);
-    cudaGraphSetConditional(cond, 1);
+    if (cond) cudaGraphSetConditional(cond, 1);
   }
 }
 
@@ -463,7 +465,7 @@ __global__ void k_newton_ctl(double* nw, const double* __restrict__ f2, double* 
   else if (rel > 1e3) nw[5] = (double)IRK_ERR_NEWTON_DIVERGED;
   else stop = 0;
   if (stop) {
-    cudaGraphSetConditional(cond, 0);
+    if (cond) cudaGraphSetConditional(cond, 0);
   } else {
     rtol_slot[0] = forcing_term(rel, count ? nw[6] : 0.0, fn, nw[3], it, newton_rtol, krylov_rtol);
     nw[3] = fn;

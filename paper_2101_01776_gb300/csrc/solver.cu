@@ -32,13 +32,14 @@ namespace {
 enum ProfClass {
   P_STAGE = 0, P_RESID, P_STAGEOP, P_UPDATE, P_MG_SMOOTH, P_MG_RESID, P_MG_RESTRICT,
   P_MG_PROLONG, P_MG_COARSE, P_MG_CONVERT, P_MG_SETUP, P_GS_DOT, P_GS_UPDATE, P_REDUCE,
-  P_SCALE, P_LINCOMB, P_NORM, P_AXPBY, P_MEAN, P_MG_SMOOTH2, P_POISSON, P_NCLASS
+  P_SCALE, P_LINCOMB, P_NORM, P_AXPBY, P_MEAN, P_MG_SMOOTH2, P_POISSON, P_FG_GS1, P_FG_GS2,
+  P_FG_NEXT, P_FG_CTL, P_NCLASS
 };
 const char* kProfNames[P_NCLASS] = {
   "stage_states", "residual", "stage_op", "stage_update", "mg_smooth", "mg_residual",
   "mg_restrict", "mg_prolong", "mg_coarse", "mg_convert", "mg_setup", "gs_multi_dot",
   "gs_update_dot", "reduce", "scale_copy", "lincomb", "norm2", "axpby", "remove_mean",
-  "mg_smooth_tile", "poisson_op"};
+  "mg_smooth_tile", "poisson_op", "fg_gs1", "fg_gs2", "fg_next", "fg_control"};
 
 struct PendingEvent {
   int cls;
@@ -1265,16 +1266,16 @@ cudaError_t capture_block_solve(irk_handle* h, double dt, int blk, cudaStream_t 
     double* dh1 = h->dscal;
     double* dh2 = h->dscal + 64;
     {
-      ProfScope ps(h, P_GS_DOT, 0, 0);
+      ProfScope ps(h, P_FG_GS1, 0, 0);
       launch_fg_gs1(h->V, ldv, fs, h->w, Lb, h->partials, dh1, inner);
     }
     {
-      ProfScope ps(h, P_GS_UPDATE, 0, 0);
+      ProfScope ps(h, P_FG_GS2, 0, 0);
       launch_fg_gs2(h->V, ldv, fs, dh1, h->w, Lb, h->partials, dh2, h->m, h->cfg.krylov_maxit,
                     h->dscal + 320 + 2 * blk, cond, inner);
     }
     {
-      ProfScope ps(h, P_SCALE, 0, 0);
+      ProfScope ps(h, P_FG_NEXT, 0, 0);
       launch_fg_next(h->V, ldv, fs, dh2, h->w, h->V, h->prec_in, Lb, h->m + 1, cond, inner);
     }
     cc->body = h->stats.kernel_launches - l0;
@@ -1301,6 +1302,101 @@ cudaError_t capture_block_solve(irk_handle* h, double dt, int blk, cudaStream_t 
   }
   h->st = saved_st;
   return e;
+}
+
+// The block solve of the captured path launched kernel by kernel (per-kernel
+// timing, cfg.profile = 1): the same prefix, body and suffix kernels as
+// capture_block_solve, with a zero conditional handle; the host reads the
+// FGState's loop flag after each body.  j = body index, so the algorithmic
+// bytes and flops of the CGS2 kernels are known here.
+irk_status direct_block_solve(irk_handle* h, double dt, int blk) {
+  const int a0 = h->tab.bstart[blk], bs = h->tab.bsize[blk], s = h->s;
+  const long long Lb = (long long)bs * h->L, ldv = Lb;
+  FGState* fs = h->fgs + blk;
+  double* x = h->yhat + (long long)a0 * h->L;
+  const double* b = h->rhs + (long long)a0 * h->L;
+  if (blk < h->tab.nblk - 1) {
+    upper_coupling(h, dt, blk, h->zbuf);
+    b = h->zbuf;
+  }
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * Lb, h->st));
+  {
+    ProfScope ps(h, P_NORM, 8.0 * Lb, 2.0 * Lb);
+    launch_norm2(b, Lb, h->partials, h->st);
+  }
+  {
+    ProfScope ps(h, P_REDUCE, 8.0 * blas_blocks(Lb), blas_blocks(Lb));
+    launch_reduce(h->partials, blas_blocks(Lb), 1, 1, h->dscal + 310, h->st);
+  }
+  {
+    ProfScope ps(h, P_FG_CTL, 0, 0);
+    launch_fg_init(fs, h->dscal + 310, h->dscal + 300, 0, h->st);
+  }
+  {
+    ProfScope ps(h, P_SCALE, 16.0 * Lb, (double)Lb);
+    launch_fg_scale(b, fs, h->V, ldv, h->prec_in, Lb, h->st);
+  }
+  for (int j = 0; j <= h->m; ++j) {
+    int stopped = 1;
+    CK(cudaMemcpyAsync(&stopped, &fs->stopped, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    prof_harvest(h);
+    if (stopped) break;
+    block_prec(h, dt, blk, h->prec_in, h->prec_out);
+    StageOpArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nrow = bs;
+    a.dt = dt;
+    for (int rr = 0; rr < bs; ++rr) {
+      const int r = a0 + rr;
+      OpRow& row = a.row[rr];
+      row.y = h->w + (long long)rr * h->L;
+      row.sigma = 1;
+      for (int qq = 0; qq < bs; ++qq) {
+        const int q = a0 + qq;
+        OpTerm& t = row.t[row.nterm++];
+        t.x = h->prec_out + (long long)qq * h->L;
+        set_combo(h, t, r, q);
+        t.m = h->tab.R[r * s + q];
+        t.lin = (r == q) ? 1.0 : 0.0;
+      }
+    }
+    a.copy_dst = h->Z;
+    a.copy_src = h->prec_out;
+    a.copy_len = Lb;
+    a.copy_jdev = &fs->j;
+    a.copy_ldv = ldv;
+    run_stage_op(h, a);
+    const double nv = j + 1;
+    double* dh1 = h->dscal;
+    double* dh2 = h->dscal + 64;
+    {
+      // V_0..V_j and w in; one FMA per value and basis vector
+      ProfScope ps(h, P_FG_GS1, 8.0 * Lb * (nv + 1), 2.0 * Lb * nv);
+      launch_fg_gs1(h->V, ldv, fs, h->w, Lb, h->partials, dh1, h->st);
+    }
+    {
+      // w -= V h1 (nv FMAs), then V^T w and ||w||^2 (nv + 1 FMAs): w in and out
+      ProfScope ps(h, P_FG_GS2, 8.0 * Lb * (nv + 2), 2.0 * Lb * (2.0 * nv + 1.0));
+      launch_fg_gs2(h->V, ldv, fs, dh1, h->w, Lb, h->partials, dh2, h->m, h->cfg.krylov_maxit,
+                    h->dscal + 320 + 2 * blk, 0, h->st);
+    }
+    {
+      // V_{j+1} = (w - V h2) / h: V and w in, V_{j+1} and the preconditioner input out
+      ProfScope ps(h, P_FG_NEXT, 8.0 * Lb * (nv + 3), 2.0 * Lb * nv + Lb);
+      launch_fg_next(h->V, ldv, fs, dh2, h->w, h->V, h->prec_in, Lb, h->m + 1, 0, h->st);
+    }
+  }
+  {
+    ProfScope ps(h, P_FG_CTL, 0, 0);
+    launch_fg_solve(fs, h->st);
+  }
+  {
+    // k basis vectors of Z and x in, x out (k <= m; the count is on the device)
+    ProfScope ps(h, P_LINCOMB, 0, 0);
+    launch_fg_lincomb(x, h->Z, ldv, fs, Lb, h->st);
+  }
+  return IRK_OK;
 }
 
 // Standalone graph of one block solve (used when the whole-step graph is not).
@@ -1783,6 +1879,15 @@ irk_status solve_blocks(irk_handle* h, double dt, double rtol, bool* on_device) 
   }
   *on_device = fg_device_solve(h, dt, rtol);
   if (*on_device) return IRK_OK;
+  if (h->cfg.profile && h->cfg.use_graphs && !h->fg_failed) {
+    // per-kernel timing of the path the graphs run: their kernels, one launch each
+    h->hbuf[400] = rtol;
+    CK(cudaMemcpyAsync(h->dscal + 300, h->hbuf + 400, sizeof(double), cudaMemcpyHostToDevice,
+                       h->st));
+    for (int blk = h->tab.nblk - 1; blk >= 0; --blk) TRY(direct_block_solve(h, dt, blk));
+    *on_device = true;
+    return IRK_OK;
+  }
   for (int blk = h->tab.nblk - 1; blk >= 0; --blk) {
     const int a0 = h->tab.bstart[blk];
     const double* z = h->rhs + (long long)a0 * h->L;

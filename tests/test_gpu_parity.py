@@ -645,3 +645,26 @@ def test_measured_alu_peaks_are_plausible(B):
     assert fp32 >= 20 * fp64, (fp32, fp64)
     with pytest.raises(B.IrkError):
         B.irk_measure_alu_peak(2)
+
+
+@pytest.mark.parametrize("s", [2, 3])
+def test_profiled_path_runs_the_graph_kernels(B, s):
+    """With per-kernel timing on (profile = 1) the block solves launch the
+    kernels of the captured graph path one by one: the same iterates and
+    Krylov counts as the graphs, and the timing classes of that path
+    (fg_gs1, fg_gs2, fg_next) instead of the host-driven loop's."""
+    n = 64
+    u0 = workloads.random_fourier_2d(n, seed=14)
+    outs = []
+    for prof in (0, 1):
+        with B.IrkSolver(u0, op="burgers2d", n=n, stages=s, nu=5e-3, profile=prof) as sol:
+            st = sol.step(0.0, 2e-3, 3)
+            outs.append((sol.state().copy(), st.krylov_its, st.newton_its))
+            if prof:
+                names = {k["name"]: k for k in B.irk_kernel_stats(sol.h)}
+    assert rel(outs[1][0], outs[0][0]) <= 1e-12
+    assert outs[0][1:] == outs[1][1:]
+    for c in ("fg_gs1", "fg_gs2", "fg_next", "mg_smooth_tile", "stage_op"):
+        assert names[c]["launches"] > 0 and names[c]["ms"] > 0, c
+    assert names["fg_gs1"]["launches"] == names["fg_gs2"]["launches"] == outs[1][1]
+    assert "gs_multi_dot" not in names or names["gs_multi_dot"]["launches"] == 0
