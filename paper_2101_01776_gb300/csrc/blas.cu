@@ -45,6 +45,7 @@ __device__ __forceinline__ void block_sum_chunk(double (&v)[kChunk], double* sh,
 __global__ void __launch_bounds__(IRK_BLAS_THREADS)
 k_multi_dot(const double* __restrict__ V, long long ldv, int nv, const double* __restrict__ w,
             long long L, double* __restrict__ partials) {
+  pdl_entry();
   __shared__ double sh[kChunk * 32];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (int k0 = 0; k0 < nv; k0 += kChunk) {
@@ -87,6 +88,7 @@ template <int NV>
 __global__ void __launch_bounds__(IRK_BLAS_THREADS)
 k_multi_dot_n(const double* __restrict__ V, long long ldv, const double* __restrict__ w,
               long long L, double* __restrict__ partials) {
+  pdl_entry();
   __shared__ double sh[NV * 8];
   double acc[NV];
 #pragma unroll
@@ -104,6 +106,7 @@ template <int NV>
 __global__ void __launch_bounds__(IRK_BLAS_THREADS)
 k_update_dot_n(const double* __restrict__ V, long long ldv, const double* __restrict__ h,
                double* __restrict__ w, long long L, int with_dots, double* __restrict__ partials) {
+  pdl_entry();
   __shared__ double sh[(NV + 1) * 8];
   double hk[NV];
 #pragma unroll
@@ -141,10 +144,10 @@ void launch_multi_dot(const double* V, long long ldv, int nv, const double* w, l
                       double* partials, cudaStream_t st) {
   const int nb = blas_blocks(L);
   switch (nv) {
-#define IRK_MD(N) case N: k_multi_dot_n<N><<<nb, IRK_BLAS_THREADS, 0, st>>>(V, ldv, w, L, partials); return;
+#define IRK_MD(N) case N: launch_pdl(k_multi_dot_n<N>, nb, IRK_BLAS_THREADS, 0, st, V, ldv, w, L, partials); return;
     IRK_NV_CASES(IRK_MD)
 #undef IRK_MD
-    default: k_multi_dot<<<nb, IRK_BLAS_THREADS, 0, st>>>(V, ldv, nv, w, L, partials);
+    default: launch_pdl(k_multi_dot, nb, IRK_BLAS_THREADS, 0, st, V, ldv, nv, w, L, partials);
   }
 }
 
@@ -153,6 +156,7 @@ void launch_multi_dot(const double* V, long long ldv, int nv, const double* w, l
 __global__ void __launch_bounds__(IRK_BLAS_THREADS)
 k_update_dot(const double* __restrict__ V, long long ldv, int nv, const double* __restrict__ h,
              double* __restrict__ w, long long L, int with_dots, double* __restrict__ partials) {
+  pdl_entry();
   __shared__ double sh[kChunk * 32];
   __shared__ double hs[128];
   for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = h[k];
@@ -195,17 +199,18 @@ void launch_update_dot(const double* V, long long ldv, int nv, const double* hde
                        long long L, int with_dots, double* partials, cudaStream_t st) {
   const int nb = blas_blocks(L);
   switch (nv) {
-#define IRK_UD(N) case N: k_update_dot_n<N><<<nb, IRK_BLAS_THREADS, 0, st>>>(V, ldv, hdev, w, L, with_dots, partials); return;
+#define IRK_UD(N) case N: launch_pdl(k_update_dot_n<N>, nb, IRK_BLAS_THREADS, 0, st, V, ldv, hdev, w, L, with_dots, partials); return;
     IRK_NV_CASES(IRK_UD)
 #undef IRK_UD
     default:
-      k_update_dot<<<nb, IRK_BLAS_THREADS, 0, st>>>(V, ldv, nv, hdev, w, L, with_dots, partials);
+      launch_pdl(k_update_dot, nb, IRK_BLAS_THREADS, 0, st, V, ldv, nv, hdev, w, L, with_dots, partials);
   }
 }
 
 // out[v] = sum_b partials[b * stride + v] in a fixed order, v < gridDim.x
 __global__ void k_reduce(const double* __restrict__ partials, int nblk, int stride,
                          double* __restrict__ out) {
+  pdl_entry();
   __shared__ double sh[32];
   const int v = blockIdx.x;
   double acc = 0.0;
@@ -224,11 +229,12 @@ __global__ void k_reduce(const double* __restrict__ partials, int nblk, int stri
 
 void launch_reduce(const double* partials, int nblk, int stride, int nvals, double* out,
                    cudaStream_t st) {
-  k_reduce<<<nvals, 256, 0, st>>>(partials, nblk, stride, out);
+  launch_pdl(k_reduce, nvals, 256, 0, st, partials, nblk, stride, out);
 }
 
 __global__ void k_scale_copy(const double* __restrict__ w, double s, double* __restrict__ v,
                              double* __restrict__ v2, long long L) {
+  pdl_entry();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
        p += (long long)gridDim.x * blockDim.x) {
     const double x = w[p] * s;
@@ -239,7 +245,7 @@ __global__ void k_scale_copy(const double* __restrict__ w, double s, double* __r
 
 void launch_scale_copy(const double* w, double scale, double* v, double* v2, long long L,
                        cudaStream_t st) {
-  k_scale_copy<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(w, scale, v, v2, L);
+  launch_pdl(k_scale_copy, blas_blocks(L), IRK_BLAS_THREADS, 0, st, w, scale, v, v2, L);
 }
 
 struct Coef64 {
@@ -248,6 +254,7 @@ struct Coef64 {
 
 __global__ void k_lincomb(double* __restrict__ x, const double* __restrict__ Z, long long ldz, int k,
                           Coef64 c, long long L) {
+  pdl_entry();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
        p += (long long)gridDim.x * blockDim.x) {
     double acc = x[p];
@@ -260,10 +267,11 @@ void launch_lincomb(double* x, const double* Z, long long ldz, int k, const doub
                     long long L, cudaStream_t st) {
   Coef64 c;
   for (int j = 0; j < k && j < 64; ++j) c.y[j] = y[j];
-  k_lincomb<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(x, Z, ldz, k, c, L);
+  launch_pdl(k_lincomb, blas_blocks(L), IRK_BLAS_THREADS, 0, st, x, Z, ldz, k, c, L);
 }
 
 __global__ void k_norm2(const double* __restrict__ x, long long L, double* __restrict__ partials) {
+  pdl_entry();
   __shared__ double sh[kChunk * 32];
   double v[kChunk];
 #pragma unroll
@@ -275,28 +283,30 @@ __global__ void k_norm2(const double* __restrict__ x, long long L, double* __res
 }
 
 void launch_norm2(const double* x, long long L, double* partials, cudaStream_t st) {
-  k_norm2<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(x, L, partials);
+  launch_pdl(k_norm2, blas_blocks(L), IRK_BLAS_THREADS, 0, st, x, L, partials);
 }
 
 __global__ void k_axpby(double* __restrict__ y, double a, const double* __restrict__ x, double b,
                         long long L) {
+  pdl_entry();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
        p += (long long)gridDim.x * blockDim.x)
     y[p] = (b == 0.0) ? a * x[p] : fma(a, x[p], b * y[p]);
 }
 
 void launch_axpby(double* y, double a, const double* x, double b, long long L, cudaStream_t st) {
-  k_axpby<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(y, a, x, b, L);
+  launch_pdl(k_axpby, blas_blocks(L), IRK_BLAS_THREADS, 0, st, y, a, x, b, L);
 }
 
 #ifdef IRK_BOUNDS
 static __device__ double g_selftest_slot[1];
 
 __global__ void k_bounds_selftest(long long index, long long extent) {
+  pdl_entry();
   g_selftest_slot[IRK_IDX(index, extent)] = 1.0;
 }
 
-void launch_bounds_selftest(cudaStream_t st) { k_bounds_selftest<<<1, 1, 0, st>>>(1, 1); }
+void launch_bounds_selftest(cudaStream_t st) { launch_pdl(k_bounds_selftest, 1, 1, 0, st, 1, 1); }
 #endif
 
 }  // namespace irk

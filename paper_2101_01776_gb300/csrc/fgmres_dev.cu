@@ -96,6 +96,7 @@ __device__ void dev_update_dot_any(const double* __restrict__ V, long long ldv, 
 // loop before it starts.
 __global__ void k_fg_init(FGState* s, const double* __restrict__ nrm2, const double* __restrict__ rtol,
                           cudaGraphConditionalHandle cond) {
+  pdl_entry();
   const double beta = isfinite(nrm2[0]) ? sqrt(fmax(nrm2[0], 0.0)) : nrm2[0];
   s->j = 0;
   s->k = 0;
@@ -124,6 +125,7 @@ __global__ void k_fg_init(FGState* s, const double* __restrict__ nrm2, const dou
 __global__ void k_fg_scale(const double* __restrict__ w, const FGState* __restrict__ s,
                            double* __restrict__ V, long long ldv, double* __restrict__ prec_in,
                            long long L) {
+  pdl_entry();
   const double sc = s->inv_scale;
   IRK_CHECK(s->j, IRK_FG_MAXM + 1);
   double* vj = V + (long long)s->j * ldv;
@@ -137,6 +139,7 @@ __global__ void k_fg_scale(const double* __restrict__ w, const FGState* __restri
 
 // y = R^{-1} g on the leading k x k triangle
 __global__ void k_fg_solve(FGState* s) {
+  pdl_entry();
   const int k = s->k;
   IRK_CHECK(k, IRK_FG_MAXM + 1);
   for (int i = k - 1; i >= 0; --i) {
@@ -149,6 +152,7 @@ __global__ void k_fg_solve(FGState* s) {
 // x += sum_{j<k} y_j Z_j
 __global__ void k_fg_lincomb(double* __restrict__ x, const double* __restrict__ Z, long long ldz,
                              const FGState* __restrict__ s, long long L) {
+  pdl_entry();
   __shared__ double ys[IRK_FG_MAXM];
   const int k = s->k;
   IRK_CHECK(k, IRK_FG_MAXM + 1);
@@ -213,6 +217,7 @@ __device__ __forceinline__ void gs1_body(const double* __restrict__ V, long long
 __global__ void __launch_bounds__(IRK_BLAS_THREADS)
 k_fg_gs1(const double* __restrict__ V, long long ldv, FGState* s, const double* __restrict__ w,
          long long L, double* __restrict__ partials, double* __restrict__ h1) {
+  pdl_entry();
   __shared__ double sh[17 * 8];
   const int nv = s->j + 1;
   IRK_CHECK(s->j, IRK_FG_MAXM);
@@ -307,6 +312,7 @@ __global__ void __launch_bounds__(IRK_BLAS_THREADS)
 k_fg_gs2(const double* __restrict__ V, long long ldv, FGState* s, const double* __restrict__ h1,
          double* __restrict__ w, long long L, double* __restrict__ partials, double* __restrict__ h2,
          int m, int maxit, double* its_total, cudaGraphConditionalHandle cond) {
+  pdl_entry();
   __shared__ double sh[17 * 8];
   const int nv = s->j + 1;
   IRK_CHECK(s->j, IRK_FG_MAXM);
@@ -353,6 +359,7 @@ k_fg_next(const double* __restrict__ V, long long ldv, FGState* s,
           const double* __restrict__ h2, const double* __restrict__ w, double* Vout,
           double* __restrict__ prec_in, long long L, int guard_limit,
           cudaGraphConditionalHandle cond) {
+  pdl_entry();
   // independent bound on the loop: whatever the Arnoldi step decided, the
   // body runs at most guard_limit times per cycle
   if (blockIdx.x == 0 && threadIdx.x == 0 && !s->stopped) {
@@ -385,18 +392,18 @@ k_fg_next(const double* __restrict__ V, long long ldv, FGState* s,
 
 void launch_fg_gs1(const double* V, long long ldv, FGState* s, const double* w, long long L,
                    double* partials, double* h1, cudaStream_t st) {
-  k_fg_gs1<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V, ldv, s, w, L, partials, h1);
+  launch_pdl(k_fg_gs1, blas_blocks(L), IRK_BLAS_THREADS, 0, st, V, ldv, s, w, L, partials, h1);
 }
 void launch_fg_gs2(const double* V, long long ldv, FGState* s, const double* h1, double* w,
                    long long L, double* partials, double* h2, int m, int maxit, double* its_total,
                    cudaGraphConditionalHandle cond, cudaStream_t st) {
-  k_fg_gs2<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V, ldv, s, h1, w, L, partials, h2, m, maxit,
+  launch_pdl(k_fg_gs2, blas_blocks(L), IRK_BLAS_THREADS, 0, st, V, ldv, s, h1, w, L, partials, h2, m, maxit,
                                                         its_total, cond);
 }
 void launch_fg_next(const double* V_, long long ldv, FGState* s, const double* h2,
                     const double* w, double* V, double* prec_in, long long L, int guard_limit,
                     cudaGraphConditionalHandle cond, cudaStream_t st) {
-  k_fg_next<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(V_, ldv, s, h2, w, V, prec_in, L,
+  launch_pdl(k_fg_next, blas_blocks(L), IRK_BLAS_THREADS, 0, st, V_, ldv, s, h2, w, V, prec_in, L,
                                                         guard_limit, cond);
 }
 
@@ -425,6 +432,7 @@ __device__ double forcing_term(double rel, double prev_rel, double fn, double pr
 __global__ void k_newton_first(double* nw, const double* __restrict__ f2, double f2_scale,
                                double* rtol_slot, double newton_rtol, double krylov_rtol,
                                cudaGraphConditionalHandle cond) {
+  pdl_entry();
   // f2 is tested before any clamp: fmax(NaN, 0) would read as zero; f2_scale
   // = s when f2 holds one of s equal stage residuals
   const double f0 = isfinite(f2[0]) ? sqrt(fmax(f2_scale * f2[0], 0.0)) : f2[0];
@@ -450,6 +458,7 @@ __global__ void k_newton_first(double* nw, const double* __restrict__ f2, double
 __global__ void k_newton_ctl(double* nw, const double* __restrict__ f2, double* rtol_slot,
                              double newton_rtol, int maxit, double krylov_rtol, int count,
                              cudaGraphConditionalHandle cond) {
+  pdl_entry();
   if (nw[5] != 0.0) return;  // already failed (non-finite ||F(0)||)
   const double fn = isfinite(f2[0]) ? sqrt(fmax(f2[0], 0.0)) : f2[0];
   const int it = (int)nw[4] + count;
@@ -477,6 +486,7 @@ __global__ void k_newton_ctl(double* nw, const double* __restrict__ f2, double* 
 // guess is then replaced by zero stages.
 __global__ void k_zero_if_unforced(const double* __restrict__ nw, double* __restrict__ K,
                                    long long len) {
+  pdl_entry();
   if (nw[0] != 0.0) return;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < len;
        p += (long long)gridDim.x * blockDim.x)
@@ -484,34 +494,34 @@ __global__ void k_zero_if_unforced(const double* __restrict__ nw, double* __rest
 }
 
 void launch_zero_if_unforced(const double* nw, double* K, long long len, cudaStream_t st) {
-  k_zero_if_unforced<<<blas_blocks(len), IRK_BLAS_THREADS, 0, st>>>(nw, K, len);
+  launch_pdl(k_zero_if_unforced, blas_blocks(len), IRK_BLAS_THREADS, 0, st, nw, K, len);
 }
 
 void launch_newton_first(double* nw, const double* f2, double f2_scale, double* rtol_slot,
                          double newton_rtol, double krylov_rtol, cudaGraphConditionalHandle cond,
                          cudaStream_t st) {
-  k_newton_first<<<1, 1, 0, st>>>(nw, f2, f2_scale, rtol_slot, newton_rtol, krylov_rtol, cond);
+  launch_pdl(k_newton_first, 1, 1, 0, st, nw, f2, f2_scale, rtol_slot, newton_rtol, krylov_rtol, cond);
 }
 
 void launch_newton_ctl(double* nw, const double* f2, double* rtol_slot, double newton_rtol,
                        int maxit, double krylov_rtol, cudaGraphConditionalHandle cond, int count,
                        cudaStream_t st) {
-  k_newton_ctl<<<1, 1, 0, st>>>(nw, f2, rtol_slot, newton_rtol, maxit, krylov_rtol, count, cond);
+  launch_pdl(k_newton_ctl, 1, 1, 0, st, nw, f2, rtol_slot, newton_rtol, maxit, krylov_rtol, count, cond);
 }
 
 // ---------------------------------------------------------------------------
 void launch_fg_init(FGState* s, const double* nrm2, const double* rtol,
                     cudaGraphConditionalHandle cond, cudaStream_t st) {
-  k_fg_init<<<1, 1, 0, st>>>(s, nrm2, rtol, cond);
+  launch_pdl(k_fg_init, 1, 1, 0, st, s, nrm2, rtol, cond);
 }
 void launch_fg_scale(const double* w, const FGState* s, double* V, long long ldv, double* prec_in,
                      long long L, cudaStream_t st) {
-  k_fg_scale<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(w, s, V, ldv, prec_in, L);
+  launch_pdl(k_fg_scale, blas_blocks(L), IRK_BLAS_THREADS, 0, st, w, s, V, ldv, prec_in, L);
 }
-void launch_fg_solve(FGState* s, cudaStream_t st) { k_fg_solve<<<1, 1, 0, st>>>(s); }
+void launch_fg_solve(FGState* s, cudaStream_t st) { launch_pdl(k_fg_solve, 1, 1, 0, st, s); }
 void launch_fg_lincomb(double* x, const double* Z, long long ldz, const FGState* s, long long L,
                        cudaStream_t st) {
-  k_fg_lincomb<<<blas_blocks(L), IRK_BLAS_THREADS, 0, st>>>(x, Z, ldz, s, L);
+  launch_pdl(k_fg_lincomb, blas_blocks(L), IRK_BLAS_THREADS, 0, st, x, Z, ldz, s, L);
 }
 
 }  // namespace irk

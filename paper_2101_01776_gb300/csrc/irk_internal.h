@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 
 #include "../../include/irk.h"
 #include "bounds.h"
@@ -19,6 +20,38 @@
 #define IRK_FG_MAXM 64
 
 namespace irk {
+
+// Programmatic dependent launch.  The solver's kernels are launched with
+// launch_pdl: a kernel may be scheduled while its predecessor on the stream
+// (or in the captured graph) is still draining, so its launch latency hides
+// behind that kernel's tail.  Every such kernel begins with pdl_entry(): it
+// waits until the predecessor grid has completed and its writes are visible
+// (so no global access of the kernel can race with it) and then lets its own
+// successor be scheduled.  For a kernel launched without the attribute both
+// instructions return at once.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+#endif
+
+// The error of the launch is left for the caller's cudaGetLastError, as with
+// the <<<>>> syntax.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 #ifdef IRK_BOUNDS
 // per-translation-unit records of the bounds-checked build (bounds.h)

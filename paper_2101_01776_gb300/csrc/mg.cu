@@ -111,6 +111,7 @@ __device__ __forceinline__ Coef4<typename Cmp<TS>::T> stencil_coef(
 template <typename TS>
 __global__ void __launch_bounds__(256) k_mg_coef(MGLevelDesc lv, double alpha64, double beta64,
                                                  const TS* __restrict__ vel, TS* __restrict__ coef) {
+  pdl_entry();
   typedef typename Cmp<TS>::T TC;
   const TC alpha = TC(alpha64), beta = TC(beta64);
   const int npts = lv.npts;
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(256) k_mg_smooth(MGLevelDesc lv, int ncomp, MG
                                                    double epi_coef, double epi_bcoef,
                                                    const double* __restrict__ b64,
                                                    double* __restrict__ out64) {
+  pdl_entry();
   typedef typename Cmp<TS>::T TC;
   const TC alpha = TC(k.alpha), beta = TC(k.beta);
   const TC dinv = TC(k.dinv), keep = TC(k.keep);
@@ -231,6 +233,7 @@ __global__ void __launch_bounds__(256) k_mg_residual(MGLevelDesc lv, int ncomp, 
                                                      const TV* __restrict__ vel,
                                                      const TS* __restrict__ b,
                                                      const TS* __restrict__ w, TS* __restrict__ r) {
+  pdl_entry();
   typedef typename Cmp<TS>::T TC;
   const TC D = TC(k.D);
   const TC alpha = TC(k.alpha), beta = TC(k.beta);
@@ -253,6 +256,7 @@ __global__ void __launch_bounds__(256) k_mg_residual0(MGLevelDesc lv, int ncomp,
                                                       const TV* __restrict__ vel,
                                                       const TS* __restrict__ b, TS* __restrict__ r,
                                                       const double* __restrict__ b64) {
+  pdl_entry();
   typedef typename Cmp<TS>::T TC;
   const TC alpha = TC(k.alpha), beta = TC(k.beta);
   const TC dinv = TC(k.dinv), keep = TC(k.keep);
@@ -299,6 +303,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
                                                         const TS* __restrict__ w_prev,
                                                         TS* __restrict__ w_mid, double wa64,
                                                         double wb64) {
+  pdl_entry();
   typedef typename Cmp<TS>::T TC;
   constexpr int WX = kTX + 2, WY = kTY + 2, NW = WX * WY;  // the halo-1 window
   __shared__ TC s_in[kTY + 4][kTX + 4];
@@ -402,6 +407,7 @@ __global__ void __launch_bounds__(kTX * TY) k_mg_smooth3(MGLevelDesc lv, int nco
                                                         const TS* __restrict__ b,
                                                         const TS* __restrict__ w_in,
                                                         TS* __restrict__ w_out, int first) {
+  pdl_entry();
   typedef typename Cmp<TS>::T TC;
   constexpr int X3 = kTX + 6, Y3 = TY + 6;  // halo-3 window
   constexpr int X2 = kTX + 4, Y2 = TY + 4;  // halo-2 window (b, coefficients)
@@ -499,6 +505,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_rbgs(MGLevelDesc lv, int ncomp
                                                      const TS* __restrict__ b,
                                                      const TS* __restrict__ w_in,
                                                      TS* __restrict__ w_out, int first) {
+  pdl_entry();
   typedef typename Cmp<TS>::T TC;
   __shared__ TC s_w[kTY + 4][kTX + 4];
   const TC alpha = TC(k.alpha), beta = TC(k.beta), dinv = TC(k.dinv);
@@ -592,6 +599,7 @@ __global__ void __launch_bounds__(kBotThreads) k_mg_bottom(BottomConst K, int pr
                                                           const double* __restrict__ pinv,
                                                           const TS* __restrict__ b_in,
                                                           TS* __restrict__ w_out) {
+  pdl_entry();
   typedef typename Cmp<TS>::T TC;
   extern __shared__ unsigned char smem_raw[];
   TC* base = reinterpret_cast<TC*>(smem_raw);
@@ -698,6 +706,7 @@ template <typename TS, int DIM>
 __global__ void __launch_bounds__(256) k_mg_restrict(MGLevelDesc fine, int ncomp,
                                                      const TS* __restrict__ rf,
                                                      TS* __restrict__ bc) {
+  pdl_entry();
   typedef typename Cmp<TS>::T TC;
   const int nc = fine.n >> 1, logc = fine.logn - 1, m = fine.n - 1;
   const int ncpts = (DIM == 1) ? nc : nc * nc;
@@ -742,6 +751,7 @@ __global__ void __launch_bounds__(256) k_mg_resid0_restrict(MGLevelDesc fine, in
                                                             const TS* __restrict__ b,
                                                             const double* __restrict__ b64,
                                                             TS* __restrict__ bc) {
+  pdl_entry();
   typedef typename Cmp<TS>::T TC;
   constexpr int BX = 2 * kRCX + 3, BY = 2 * kRCY + 3;  // b window: r window + stencil halo
   constexpr int RX = 2 * kRCX + 1, RY = 2 * kRCY + 1;  // r window: owned points + weight halo
@@ -800,6 +810,7 @@ __global__ void __launch_bounds__(256) k_mg_prolong_add(MGLevelDesc fine, int nc
                                                         TS* __restrict__ wf,
                                                         const TS* __restrict__ bf, double dinv64,
                                                         const double* __restrict__ b64) {
+  pdl_entry();
   // SET: w_f = dinv b_f + P e (the fine iterate was one sweep from zero and
   // was never stored); otherwise w_f += P e
   typedef typename Cmp<TS>::T TC;
@@ -842,6 +853,7 @@ __global__ void k_mg_coarse(MGLevelDesc lv, int ncomp, double sigma_, double cad
                             double omega_, int sweeps, int project_mean,
                             const TV* __restrict__ vel, const TS* __restrict__ b,
                             TS* __restrict__ w) {
+  pdl_entry();
   typedef typename Cmp<TS>::T TC;
   extern __shared__ unsigned char smem_raw[];
   TC* sw = reinterpret_cast<TC*>(smem_raw);          // ncomp * npts
@@ -902,6 +914,7 @@ __global__ void k_mg_coarse(MGLevelDesc lv, int ncomp, double sigma_, double cad
 
 template <typename TS>
 __global__ void k_convert_in(const double* __restrict__ src, TS* __restrict__ dst, long long n) {
+  pdl_entry();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x)
     stv<TS, typename Cmp<TS>::T>(dst + p, (typename Cmp<TS>::T)src[p]);
@@ -909,6 +922,7 @@ __global__ void k_convert_in(const double* __restrict__ src, TS* __restrict__ ds
 
 template <typename TS>
 __global__ void k_convert_out(const TS* __restrict__ src, double* __restrict__ dst, long long n) {
+  pdl_entry();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x)
     dst[p] = (double)ldv(src + p);
@@ -974,11 +988,11 @@ void launch_mg_smooth(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
   if (prec != IRK_MG_FP64 && !wide) epi_out = nullptr;  // the epilogue reads the FP64 result
   IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, {
     if (wide)
-      k_mg_smooth<TS, DIM, KIND, true, TV><<<grid_for(lv.npts), 256, 0, st>>>(
+      launch_pdl(k_mg_smooth<TS, DIM, KIND, true, TV>, grid_for(lv.npts), 256, 0, st, 
           lv, ncomp, k, (const TV*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, epi_out,
           epi_base, epi_coef, epi_bcoef, b64, out64);
     else
-      k_mg_smooth<TS, DIM, KIND, false, TV><<<grid_for(lv.npts), 256, 0, st>>>(
+      launch_pdl(k_mg_smooth<TS, DIM, KIND, false, TV>, grid_for(lv.npts), 256, 0, st, 
           lv, ncomp, k, (const TV*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, epi_out,
           epi_base, epi_coef, epi_bcoef, nullptr, nullptr);
   }));
@@ -1016,13 +1030,13 @@ void launch_mg_smooth2(int prec, int kind, const MGLevelDesc& lv, int ncomp, dou
   const dim3 grid(lv.n / kTX, lv.n / kTY, zsplit), block(kTX, kTY);
   IRK_DISPATCH_PREC(prec, {
     if (kind == MG_ADVECTIVE)
-      k_mg_smooth2<TS, MG_ADVECTIVE, false, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
+      launch_pdl(k_mg_smooth2<TS, MG_ADVECTIVE, false, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first, nullptr, nullptr, 1.0, 1.0);
     else if (kind == MG_ADVECTIVE_PRE)
-      k_mg_smooth2<TS, MG_ADVECTIVE_PRE, false, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
+      launch_pdl(k_mg_smooth2<TS, MG_ADVECTIVE_PRE, false, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first, nullptr, nullptr, 1.0, 1.0);
     else
-      k_mg_smooth2<TS, MG_DIFFUSION, false, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
+      launch_pdl(k_mg_smooth2<TS, MG_DIFFUSION, false, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first, nullptr, nullptr, 1.0, 1.0);
   });
 }
@@ -1035,13 +1049,13 @@ void launch_mg_rbgs(int prec, int kind, const MGLevelDesc& lv, int ncomp, double
   const dim3 grid(lv.n / kTX, lv.n / kTY, zsplit), block(kTX, kTY);
   IRK_DISPATCH_PREC(prec, {
     if (kind == MG_ADVECTIVE)
-      k_mg_rbgs<TS, MG_ADVECTIVE, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
+      launch_pdl(k_mg_rbgs<TS, MG_ADVECTIVE, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
     else if (kind == MG_ADVECTIVE_PRE)
-      k_mg_rbgs<TS, MG_ADVECTIVE_PRE, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
+      launch_pdl(k_mg_rbgs<TS, MG_ADVECTIVE_PRE, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
     else
-      k_mg_rbgs<TS, MG_DIFFUSION, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
+      launch_pdl(k_mg_rbgs<TS, MG_DIFFUSION, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first);
   });
 }
@@ -1060,13 +1074,13 @@ void launch_mg_smooth3(int prec, int kind, const MGLevelDesc& lv, int ncomp, dou
 #define IRK_S3(TY_)                                                                               \
   do {                                                                                            \
     if (kind == MG_ADVECTIVE)                                                                     \
-      k_mg_smooth3<TS, MG_ADVECTIVE, TY_, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,   \
+      launch_pdl(k_mg_smooth3<TS, MG_ADVECTIVE, TY_, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,   \
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                                      \
     else if (kind == MG_ADVECTIVE_PRE)                                                            \
-      k_mg_smooth3<TS, MG_ADVECTIVE_PRE, TY_, TV><<<grid, block, 0, st>>>(lv, ncomp, k,               \
+      launch_pdl(k_mg_smooth3<TS, MG_ADVECTIVE_PRE, TY_, TV>, grid, block, 0, st, lv, ncomp, k,               \
           (const TV*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                      \
     else                                                                                          \
-      k_mg_smooth3<TS, MG_DIFFUSION, TY_, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,   \
+      launch_pdl(k_mg_smooth3<TS, MG_DIFFUSION, TY_, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,   \
           (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                                      \
   } while (0)
   IRK_DISPATCH_PREC(prec, {
@@ -1085,13 +1099,13 @@ void launch_mg_cheb2(int prec, int kind, const MGLevelDesc& lv, int ncomp, doubl
   const dim3 grid(lv.n / kTX, lv.n / kTY, zsplit), block(kTX, kTY);
   IRK_DISPATCH_PREC(prec, {
     if (kind == MG_ADVECTIVE)
-      k_mg_smooth2<TS, MG_ADVECTIVE, true, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
+      launch_pdl(k_mg_smooth2<TS, MG_ADVECTIVE, true, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)x_cur, (TS*)x_out, first, (const TS*)x_prev, (TS*)x_mid, wa, wb);
     else if (kind == MG_ADVECTIVE_PRE)
-      k_mg_smooth2<TS, MG_ADVECTIVE_PRE, true, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
+      launch_pdl(k_mg_smooth2<TS, MG_ADVECTIVE_PRE, true, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)x_cur, (TS*)x_out, first, (const TS*)x_prev, (TS*)x_mid, wa, wb);
     else
-      k_mg_smooth2<TS, MG_DIFFUSION, true, TV><<<grid, block, 0, st>>>(lv, ncomp, k, (const TV*)vel,
+      launch_pdl(k_mg_smooth2<TS, MG_DIFFUSION, true, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,
           (const TS*)b, (const TS*)x_cur, (TS*)x_out, first, (const TS*)x_prev, (TS*)x_mid, wa, wb);
   });
 }
@@ -1100,7 +1114,7 @@ void launch_mg_residual(int prec, int dim, int kind, const MGLevelDesc& lv, int 
                         double sigma, double cadv, double cdiff, const void* vel, const void* b,
                         const void* w, void* r, cudaStream_t st) {
   const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, 1.0);
-  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_residual<TS, DIM, KIND, TV><<<grid_for(lv.npts), 256, 0, st>>>(
+  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (launch_pdl(k_mg_residual<TS, DIM, KIND, TV>, grid_for(lv.npts), 256, 0, st, 
       lv, ncomp, k, (const TV*)vel, (const TS*)b, (const TS*)w, (TS*)r))));
 }
 
@@ -1109,9 +1123,9 @@ void launch_mg_restrict(int prec, int dim, const MGLevelDesc& fine, int ncomp, c
   const long long nc = dim == 1 ? fine.n / 2 : (long long)(fine.n / 2) * (fine.n / 2);
   IRK_DISPATCH_PREC(prec, {
     if (dim == 1)
-      k_mg_restrict<TS, 1><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)rf, (TS*)bc);
+      launch_pdl(k_mg_restrict<TS, 1>, grid_for(nc), 256, 0, st, fine, ncomp, (const TS*)rf, (TS*)bc);
     else
-      k_mg_restrict<TS, 2><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)rf, (TS*)bc);
+      launch_pdl(k_mg_restrict<TS, 2>, grid_for(nc), 256, 0, st, fine, ncomp, (const TS*)rf, (TS*)bc);
   });
 }
 
@@ -1120,9 +1134,9 @@ void launch_mg_restrict_vel(int prec, int dim, const MGLevelDesc& fine, int ncom
   const long long nc = dim == 1 ? fine.n / 2 : (long long)(fine.n / 2) * (fine.n / 2);
   IRK_DISPATCH_PREC(prec, {
     if (dim == 1)
-      k_mg_restrict<TV, 1><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TV*)vf, (TV*)vc);
+      launch_pdl(k_mg_restrict<TV, 1>, grid_for(nc), 256, 0, st, fine, ncomp, (const TV*)vf, (TV*)vc);
     else
-      k_mg_restrict<TV, 2><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TV*)vf, (TV*)vc);
+      launch_pdl(k_mg_restrict<TV, 2>, grid_for(nc), 256, 0, st, fine, ncomp, (const TV*)vf, (TV*)vc);
   });
 }
 
@@ -1135,10 +1149,10 @@ void launch_mg_prolong_add(int prec, int dim, const MGLevelDesc& fine, int ncomp
   const long long nc = dim == 1 ? fine.n / 2 : (long long)(fine.n / 2) * (fine.n / 2);
   IRK_DISPATCH_PREC(prec, {
     if (dim == 1)
-      k_mg_prolong_add<TS, 1, false><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc,
+      launch_pdl(k_mg_prolong_add<TS, 1, false>, grid_for(nc), 256, 0, st, fine, ncomp, (const TS*)wc,
                                                                    (TS*)wf, nullptr, 0.0, nullptr);
     else
-      k_mg_prolong_add<TS, 2, false><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc,
+      launch_pdl(k_mg_prolong_add<TS, 2, false>, grid_for(nc), 256, 0, st, fine, ncomp, (const TS*)wc,
                                                                    (TS*)wf, nullptr, 0.0, nullptr);
   });
 }
@@ -1151,10 +1165,10 @@ void launch_mg_prolong_set(int prec, int dim, const MGLevelDesc& fine, int ncomp
   const long long nc = dim == 1 ? fine.n / 2 : (long long)(fine.n / 2) * (fine.n / 2);
   IRK_DISPATCH_PREC(prec, {
     if (dim == 1)
-      k_mg_prolong_add<TS, 1, true><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc,
+      launch_pdl(k_mg_prolong_add<TS, 1, true>, grid_for(nc), 256, 0, st, fine, ncomp, (const TS*)wc,
                                                                   (TS*)wf, (const TS*)bf, k.dinv, b64);
     else
-      k_mg_prolong_add<TS, 2, true><<<grid_for(nc), 256, 0, st>>>(fine, ncomp, (const TS*)wc,
+      launch_pdl(k_mg_prolong_add<TS, 2, true>, grid_for(nc), 256, 0, st, fine, ncomp, (const TS*)wc,
                                                                   (TS*)wf, (const TS*)bf, k.dinv, b64);
   });
 }
@@ -1171,6 +1185,7 @@ __global__ void __launch_bounds__(256) k_mg_setup2(MGLevelDesc fine, const doubl
                                                    double* __restrict__ vel1,
                                                    double* __restrict__ coef1, double a0, double b0,
                                                    double a1, double b1) {
+  pdl_entry();
   const int nc = fine.n >> 1, logc = fine.logn - 1, m = fine.n - 1, lf = fine.logn;
   const int ncpts = nc * nc, npts = fine.npts;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < ncpts; p += gridDim.x * blockDim.x) {
@@ -1209,7 +1224,7 @@ void launch_mg_setup2(const MGLevelDesc& fine, const MGLevelDesc& coarse, double
   const MGConst k0 = mg_const(fine, 2, 0.0, cadv, cdiff, 1.0);
   const MGConst k1 = mg_const(coarse, 2, 0.0, cadv, cdiff, 1.0);
   const long long nc = (long long)(fine.n / 2) * (fine.n / 2);
-  k_mg_setup2<<<grid_for(nc), 256, 0, st>>>(fine, combo, (double*)vel0, (double*)coef0,
+  launch_pdl(k_mg_setup2, grid_for(nc), 256, 0, st, fine, combo, (double*)vel0, (double*)coef0,
                                             (double*)vel1, (double*)coef1, k0.alpha, k0.beta,
                                             k1.alpha, k1.beta);
 }
@@ -1219,7 +1234,7 @@ void launch_mg_coef(int prec, const MGLevelDesc& lv, double cadv, double cdiff, 
   const MGConst k = mg_const(lv, 2, 0.0, cadv, cdiff, 1.0);
   // the precomputed-coefficient form serves FP64 storage only
   if (prec != IRK_MG_FP64) return;
-  k_mg_coef<double><<<grid_for(lv.npts), 256, 0, st>>>(lv, k.alpha, k.beta, (const double*)vel,
+  launch_pdl(k_mg_coef<double>, grid_for(lv.npts), 256, 0, st, lv, k.alpha, k.beta, (const double*)vel,
                                                       (double*)coef);
 }
 
@@ -1228,7 +1243,7 @@ void launch_mg_residual0(int prec, int dim, int kind, const MGLevelDesc& lv, int
                          const void* b, void* r, cudaStream_t st, const double* b64) {
   const MGConst k = mg_const(lv, dim, sigma, cadv, cdiff, omega);
   if (prec == IRK_MG_FP64) b64 = nullptr;
-  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (k_mg_residual0<TS, DIM, KIND, TV><<<grid_for(lv.npts), 256, 0, st>>>(
+  IRK_DISPATCH_PREC(prec, IRK_DISPATCH_DK(dim, kind, (launch_pdl(k_mg_residual0<TS, DIM, KIND, TV>, grid_for(lv.npts), 256, 0, st, 
       lv, ncomp, k, (const TV*)vel, (const TS*)b, (TS*)r, b64))));
 }
 
@@ -1241,13 +1256,13 @@ void launch_mg_resid0_restrict(int prec, int kind, const MGLevelDesc& fine, int 
   const dim3 grid((fine.n / 2) / kRCX, (fine.n / 2) / kRCY);
   IRK_DISPATCH_PREC(prec, {
     if (kind == MG_ADVECTIVE)
-      k_mg_resid0_restrict<TS, MG_ADVECTIVE, TV><<<grid, 256, 0, st>>>(fine, ncomp, k, (const TV*)vel,
+      launch_pdl(k_mg_resid0_restrict<TS, MG_ADVECTIVE, TV>, grid, 256, 0, st, fine, ncomp, k, (const TV*)vel,
                                                                   (const TS*)b, b64, (TS*)bc);
     else if (kind == MG_ADVECTIVE_PRE)
-      k_mg_resid0_restrict<TS, MG_ADVECTIVE_PRE, TV><<<grid, 256, 0, st>>>(
+      launch_pdl(k_mg_resid0_restrict<TS, MG_ADVECTIVE_PRE, TV>, grid, 256, 0, st, 
           fine, ncomp, k, (const TV*)vel, (const TS*)b, b64, (TS*)bc);
     else
-      k_mg_resid0_restrict<TS, MG_DIFFUSION, TV><<<grid, 256, 0, st>>>(fine, ncomp, k, (const TV*)vel,
+      launch_pdl(k_mg_resid0_restrict<TS, MG_DIFFUSION, TV>, grid, 256, 0, st, fine, ncomp, k, (const TV*)vel,
                                                                   (const TS*)b, b64, (TS*)bc);
   });
 }
@@ -1271,7 +1286,7 @@ void launch_mg_bottom(int prec, const MGLevelDesc& lv, double cdiff, double omeg
   K.inv_cdiff = 1.0 / cdiff;
   IRK_DISPATCH_PREC(prec, {
     typedef typename Cmp<TS>::T TC;
-    k_mg_bottom<TS><<<1, kBotThreads, sizeof(TC) * words, st>>>(K, pre, post, pinv,
+    launch_pdl(k_mg_bottom<TS>, 1, kBotThreads, sizeof(TC) * words, st, K, pre, post, pinv,
         (const TS*)b, (TS*)w);
   });
 }
@@ -1283,19 +1298,19 @@ void launch_mg_coarse(int prec, int dim, int kind, const MGLevelDesc& lv, int nc
     typedef typename Cmp<TS>::T TC;
     const size_t smem = sizeof(TC) * ((size_t)3 * ncomp * lv.npts + (size_t)dim * lv.npts);
     // the one-CTA kernel takes the velocity (MG_ADVECTIVE), never precomputed coefficients
-    IRK_DISPATCH_DK_VEL(dim, kind, (k_mg_coarse<TS, DIM, KIND, TV><<<1, 256, smem, st>>>(
+    IRK_DISPATCH_DK_VEL(dim, kind, (launch_pdl(k_mg_coarse<TS, DIM, KIND, TV>, 1, 256, smem, st, 
         lv, ncomp, sigma, cadv, cdiff, omega, sweeps, project_mean, (const TV*)vel,
         (const TS*)b, (TS*)w)));
   });
 }
 
 void launch_mg_convert_in(int prec, const double* src, void* dst, long long len, cudaStream_t st) {
-  IRK_DISPATCH_PREC(prec, (k_convert_in<TS><<<grid_for(len), 256, 0, st>>>(src, (TS*)dst, len)));
+  IRK_DISPATCH_PREC(prec, (launch_pdl(k_convert_in<TS>, grid_for(len), 256, 0, st, src, (TS*)dst, len)));
 }
 
 void launch_mg_convert_out(int prec, const void* src, double* dst, long long len,
                            cudaStream_t st) {
-  IRK_DISPATCH_PREC(prec, (k_convert_out<TS><<<grid_for(len), 256, 0, st>>>((const TS*)src, dst, len)));
+  IRK_DISPATCH_PREC(prec, (launch_pdl(k_convert_out<TS>, grid_for(len), 256, 0, st, (const TS*)src, dst, len)));
 }
 
 }  // namespace irk

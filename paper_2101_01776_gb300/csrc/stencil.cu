@@ -32,6 +32,7 @@ __device__ __forceinline__ int wrapn(int i, int n) { return i & (n - 1); }
 // ---------------------------------------------------------------------------
 template <int S>
 __global__ void __launch_bounds__(256) k_stage_states(StageStateArgs a) {
+  pdl_entry();
   const long long L = a.L;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
        p += (long long)gridDim.x * blockDim.x) {
@@ -66,11 +67,11 @@ void launch_stage_states(const GridDesc& g, const StageStateArgs& a, cudaStream_
   int blocks = (int)((L + 255) / 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
   switch (a.s) {
-    case 1: k_stage_states<1><<<blocks, 256, 0, st>>>(a); break;
-    case 2: k_stage_states<2><<<blocks, 256, 0, st>>>(a); break;
-    case 3: k_stage_states<3><<<blocks, 256, 0, st>>>(a); break;
-    case 4: k_stage_states<4><<<blocks, 256, 0, st>>>(a); break;
-    case 5: k_stage_states<5><<<blocks, 256, 0, st>>>(a); break;
+    case 1: launch_pdl(k_stage_states<1>, blocks, 256, 0, st, a); break;
+    case 2: launch_pdl(k_stage_states<2>, blocks, 256, 0, st, a); break;
+    case 3: launch_pdl(k_stage_states<3>, blocks, 256, 0, st, a); break;
+    case 4: launch_pdl(k_stage_states<4>, blocks, 256, 0, st, a); break;
+    case 5: launch_pdl(k_stage_states<5>, blocks, 256, 0, st, a); break;
   }
 }
 
@@ -195,6 +196,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 template <int OP, int S>
 __global__ void __launch_bounds__(256) k_residual(GridDesc g, ResidualArgs a) {
+  pdl_entry();
   __shared__ double sh[32];
   constexpr int C = (OP == IRK_OP_BURGERS_2D || OP == IRK_OP_VSF_2D) ? 2 : 1;
   const long long L = (long long)C * g.npts;
@@ -244,6 +246,7 @@ __global__ void __launch_bounds__(256) k_residual(GridDesc g, ResidualArgs a) {
 // Work item q in [0, 2 npts): component q / npts, point q % npts.
 template <int S>
 __global__ void __launch_bounds__(256) k_residual_b2d(GridDesc g, ResidualArgs a) {
+  pdl_entry();
   __shared__ double sh[32];
   const int npts = g.npts;
   const long long L = 2LL * npts;
@@ -292,6 +295,7 @@ __global__ void __launch_bounds__(256) k_residual_b2d(GridDesc g, ResidualArgs a
 // item the constraint row -L psi - w (M = 0).
 template <int S>
 __global__ void __launch_bounds__(256) k_residual_vsf(GridDesc g, ResidualArgs a) {
+  pdl_entry();
   __shared__ double sh[32];
   const int npts = g.npts;
   const long long L = 2LL * npts;
@@ -351,30 +355,30 @@ static void launch_residual_op(const GridDesc& g, const ResidualArgs& a, cudaStr
   const int blocks = residual_blocks(g);
   if (OP == IRK_OP_BURGERS_2D && !a.forcing) {
     switch (a.s) {
-      case 1: k_residual_b2d<1><<<blocks, 256, 0, st>>>(g, a); break;
-      case 2: k_residual_b2d<2><<<blocks, 256, 0, st>>>(g, a); break;
-      case 3: k_residual_b2d<3><<<blocks, 256, 0, st>>>(g, a); break;
-      case 4: k_residual_b2d<4><<<blocks, 256, 0, st>>>(g, a); break;
-      case 5: k_residual_b2d<5><<<blocks, 256, 0, st>>>(g, a); break;
+      case 1: launch_pdl(k_residual_b2d<1>, blocks, 256, 0, st, g, a); break;
+      case 2: launch_pdl(k_residual_b2d<2>, blocks, 256, 0, st, g, a); break;
+      case 3: launch_pdl(k_residual_b2d<3>, blocks, 256, 0, st, g, a); break;
+      case 4: launch_pdl(k_residual_b2d<4>, blocks, 256, 0, st, g, a); break;
+      case 5: launch_pdl(k_residual_b2d<5>, blocks, 256, 0, st, g, a); break;
     }
     return;
   }
   if (OP == IRK_OP_VSF_2D && !a.forcing) {
     switch (a.s) {
-      case 1: k_residual_vsf<1><<<blocks, 256, 0, st>>>(g, a); break;
-      case 2: k_residual_vsf<2><<<blocks, 256, 0, st>>>(g, a); break;
-      case 3: k_residual_vsf<3><<<blocks, 256, 0, st>>>(g, a); break;
-      case 4: k_residual_vsf<4><<<blocks, 256, 0, st>>>(g, a); break;
-      case 5: k_residual_vsf<5><<<blocks, 256, 0, st>>>(g, a); break;
+      case 1: launch_pdl(k_residual_vsf<1>, blocks, 256, 0, st, g, a); break;
+      case 2: launch_pdl(k_residual_vsf<2>, blocks, 256, 0, st, g, a); break;
+      case 3: launch_pdl(k_residual_vsf<3>, blocks, 256, 0, st, g, a); break;
+      case 4: launch_pdl(k_residual_vsf<4>, blocks, 256, 0, st, g, a); break;
+      case 5: launch_pdl(k_residual_vsf<5>, blocks, 256, 0, st, g, a); break;
     }
     return;
   }
   switch (a.s) {
-    case 1: k_residual<OP, 1><<<blocks, 256, 0, st>>>(g, a); break;
-    case 2: k_residual<OP, 2><<<blocks, 256, 0, st>>>(g, a); break;
-    case 3: k_residual<OP, 3><<<blocks, 256, 0, st>>>(g, a); break;
-    case 4: k_residual<OP, 4><<<blocks, 256, 0, st>>>(g, a); break;
-    case 5: k_residual<OP, 5><<<blocks, 256, 0, st>>>(g, a); break;
+    case 1: launch_pdl(k_residual<OP, 1>, blocks, 256, 0, st, g, a); break;
+    case 2: launch_pdl(k_residual<OP, 2>, blocks, 256, 0, st, g, a); break;
+    case 3: launch_pdl(k_residual<OP, 3>, blocks, 256, 0, st, g, a); break;
+    case 4: launch_pdl(k_residual<OP, 4>, blocks, 256, 0, st, g, a); break;
+    case 5: launch_pdl(k_residual<OP, 5>, blocks, 256, 0, st, g, a); break;
   }
 }
 
@@ -559,6 +563,7 @@ __device__ __forceinline__ void term_apply(const GridDesc& g, const OpTerm& t, c
 
 template <int OP, bool WONLY = false>
 __global__ void __launch_bounds__(256) k_stage_op(GridDesc g, StageOpArgs a) {
+  pdl_entry();
   constexpr int C = WONLY ? 1 : (OP == IRK_OP_BURGERS_2D || OP == IRK_OP_VSF_2D) ? 2 : 1;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npts; p += gridDim.x * blockDim.x) {
     const Nbr nb = neighbours(g, p);
@@ -584,6 +589,7 @@ __global__ void __launch_bounds__(256) k_stage_op(GridDesc g, StageOpArgs a) {
 
 __global__ void __launch_bounds__(256) k_combo_coef(GridDesc g, const double* __restrict__ combos,
                                                     ComboList list, double dt, double* __restrict__ coef) {
+  pdl_entry();
   const int ncombo = list.n;
   const int npts = g.npts;
   const double dth = dt * g.inv2h;
@@ -629,6 +635,7 @@ __device__ __forceinline__ void arakawa_weights(const double a[3][3], double wgt
 // half 1 forms Q from wbar (write-bound: 64 bytes per item).
 __global__ void __launch_bounds__(256) k_combo_coef_vsf(GridDesc g, const double* __restrict__ combos,
                                                         ComboList list, double dt, double* __restrict__ coef) {
+  pdl_entry();
   const int npts = g.npts, ncombo = list.n;
   const double sc = dt * g.inv12h2;
   const long long items = 2LL * ncombo * npts;
@@ -659,9 +666,9 @@ void launch_combo_coef(const GridDesc& g, const double* combos, const ComboList&
   int blocks = (g.npts + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (g.op == IRK_OP_VSF_2D)
-    k_combo_coef_vsf<<<152 * 8, 256, 0, st>>>(g, combos, list, dt, coef);
+    launch_pdl(k_combo_coef_vsf, 152 * 8, 256, 0, st, g, combos, list, dt, coef);
   else
-    k_combo_coef<<<blocks, 256, 0, st>>>(g, combos, list, dt, coef);
+    launch_pdl(k_combo_coef, blocks, 256, 0, st, g, combos, list, dt, coef);
 }
 
 void launch_stage_op(const GridDesc& g, const StageOpArgs& a_in, cudaStream_t st) {
@@ -675,12 +682,12 @@ void launch_stage_op(const GridDesc& g, const StageOpArgs& a_in, cudaStream_t st
   int blocks = (g.npts + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   switch (g.op) {
-    case IRK_OP_DIFFUSION_1D: k_stage_op<IRK_OP_DIFFUSION_1D><<<blocks, 256, 0, st>>>(g, a); break;
-    case IRK_OP_BURGERS_1D: k_stage_op<IRK_OP_BURGERS_1D><<<blocks, 256, 0, st>>>(g, a); break;
-    case IRK_OP_BURGERS_2D: k_stage_op<IRK_OP_BURGERS_2D><<<blocks, 256, 0, st>>>(g, a); break;
+    case IRK_OP_DIFFUSION_1D: launch_pdl(k_stage_op<IRK_OP_DIFFUSION_1D>, blocks, 256, 0, st, g, a); break;
+    case IRK_OP_BURGERS_1D: launch_pdl(k_stage_op<IRK_OP_BURGERS_1D>, blocks, 256, 0, st, g, a); break;
+    case IRK_OP_BURGERS_2D: launch_pdl(k_stage_op<IRK_OP_BURGERS_2D>, blocks, 256, 0, st, g, a); break;
     case IRK_OP_VSF_2D:
-      if (a.vsf_omega_only) k_stage_op<IRK_OP_VSF_2D, true><<<blocks, 256, 0, st>>>(g, a);
-      else k_stage_op<IRK_OP_VSF_2D><<<blocks, 256, 0, st>>>(g, a);
+      if (a.vsf_omega_only) launch_pdl(k_stage_op<IRK_OP_VSF_2D, true>, blocks, 256, 0, st, g, a);
+      else launch_pdl(k_stage_op<IRK_OP_VSF_2D>, blocks, 256, 0, st, g, a);
       break;
   }
 }
@@ -689,6 +696,7 @@ void launch_stage_op(const GridDesc& g, const StageOpArgs& a_in, cudaStream_t st
 // vsf-system-2 divided by -dt, for the Poisson FGMRES of the forward solve.
 __global__ void __launch_bounds__(256) k_neg_laplacian_2d(GridDesc g, const double* __restrict__ x,
                                                           double* __restrict__ y) {
+  pdl_entry();
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npts; p += gridDim.x * blockDim.x) {
     const Nbr nb = neighbours(g, p);
     y[p] = (4.0 * __ldg(x + nb.c) - __ldg(x + nb.e) - __ldg(x + nb.w) - __ldg(x + nb.n) -
@@ -699,7 +707,7 @@ __global__ void __launch_bounds__(256) k_neg_laplacian_2d(GridDesc g, const doub
 void launch_neg_laplacian(const GridDesc& g, const double* x, double* y, cudaStream_t st) {
   int blocks = (g.npts + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_neg_laplacian_2d<<<blocks, 256, 0, st>>>(g, x, y);
+  launch_pdl(k_neg_laplacian_2d, blocks, 256, 0, st, g, x, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -710,6 +718,7 @@ struct SmallMat {
 template <int S>
 __global__ void __launch_bounds__(256) k_stage_update(long long L, SmallMat T, const double* __restrict__ yhat,
                                                       double* __restrict__ K) {
+  pdl_entry();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
        p += (long long)gridDim.x * blockDim.x) {
     double y[S];
@@ -730,6 +739,7 @@ __global__ void __launch_bounds__(256) k_stage_update(long long L, SmallMat T, c
 template <int S>
 __global__ void __launch_bounds__(256) k_stage_extrapolate(long long L, const double* __restrict__ E,
                                                            double* __restrict__ K) {
+  pdl_entry();
   __shared__ double e[S * S];
   for (int i = threadIdx.x; i < S * S; i += blockDim.x) e[i] = E[i];
   __syncthreads();
@@ -752,11 +762,11 @@ void launch_stage_extrapolate(long long L, int s, const double* E, double* K, cu
   int blocks = (int)((L + 255) / 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
   switch (s) {
-    case 1: k_stage_extrapolate<1><<<blocks, 256, 0, st>>>(L, E, K); break;
-    case 2: k_stage_extrapolate<2><<<blocks, 256, 0, st>>>(L, E, K); break;
-    case 3: k_stage_extrapolate<3><<<blocks, 256, 0, st>>>(L, E, K); break;
-    case 4: k_stage_extrapolate<4><<<blocks, 256, 0, st>>>(L, E, K); break;
-    case 5: k_stage_extrapolate<5><<<blocks, 256, 0, st>>>(L, E, K); break;
+    case 1: launch_pdl(k_stage_extrapolate<1>, blocks, 256, 0, st, L, E, K); break;
+    case 2: launch_pdl(k_stage_extrapolate<2>, blocks, 256, 0, st, L, E, K); break;
+    case 3: launch_pdl(k_stage_extrapolate<3>, blocks, 256, 0, st, L, E, K); break;
+    case 4: launch_pdl(k_stage_extrapolate<4>, blocks, 256, 0, st, L, E, K); break;
+    case 5: launch_pdl(k_stage_extrapolate<5>, blocks, 256, 0, st, L, E, K); break;
   }
 }
 
@@ -767,17 +777,18 @@ void launch_stage_update(long long L, int s, const double* QR, const double* yha
   int blocks = (int)((L + 255) / 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
   switch (s) {
-    case 1: k_stage_update<1><<<blocks, 256, 0, st>>>(L, T, yhat, K); break;
-    case 2: k_stage_update<2><<<blocks, 256, 0, st>>>(L, T, yhat, K); break;
-    case 3: k_stage_update<3><<<blocks, 256, 0, st>>>(L, T, yhat, K); break;
-    case 4: k_stage_update<4><<<blocks, 256, 0, st>>>(L, T, yhat, K); break;
-    case 5: k_stage_update<5><<<blocks, 256, 0, st>>>(L, T, yhat, K); break;
+    case 1: launch_pdl(k_stage_update<1>, blocks, 256, 0, st, L, T, yhat, K); break;
+    case 2: launch_pdl(k_stage_update<2>, blocks, 256, 0, st, L, T, yhat, K); break;
+    case 3: launch_pdl(k_stage_update<3>, blocks, 256, 0, st, L, T, yhat, K); break;
+    case 4: launch_pdl(k_stage_update<4>, blocks, 256, 0, st, L, T, yhat, K); break;
+    case 5: launch_pdl(k_stage_update<5>, blocks, 256, 0, st, L, T, yhat, K); break;
   }
 }
 
 template <int S>
 __global__ void __launch_bounds__(256) k_u_update(long long L, SmallMat bw, const double* __restrict__ K,
                                                   double* __restrict__ u) {
+  pdl_entry();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
        p += (long long)gridDim.x * blockDim.x) {
     double acc = 0.0;
@@ -795,11 +806,11 @@ void launch_u_update(long long L, int s, const double* b, double dt, const doubl
   int blocks = (int)((L + 255) / 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
   switch (s) {
-    case 1: k_u_update<1><<<blocks, 256, 0, st>>>(L, bw, K, u); break;
-    case 2: k_u_update<2><<<blocks, 256, 0, st>>>(L, bw, K, u); break;
-    case 3: k_u_update<3><<<blocks, 256, 0, st>>>(L, bw, K, u); break;
-    case 4: k_u_update<4><<<blocks, 256, 0, st>>>(L, bw, K, u); break;
-    case 5: k_u_update<5><<<blocks, 256, 0, st>>>(L, bw, K, u); break;
+    case 1: launch_pdl(k_u_update<1>, blocks, 256, 0, st, L, bw, K, u); break;
+    case 2: launch_pdl(k_u_update<2>, blocks, 256, 0, st, L, bw, K, u); break;
+    case 3: launch_pdl(k_u_update<3>, blocks, 256, 0, st, L, bw, K, u); break;
+    case 4: launch_pdl(k_u_update<4>, blocks, 256, 0, st, L, bw, K, u); break;
+    case 5: launch_pdl(k_u_update<5>, blocks, 256, 0, st, L, bw, K, u); break;
   }
 }
 
@@ -820,6 +831,7 @@ __device__ __forceinline__ void store_as<__nv_bfloat16>(__nv_bfloat16* p, double
 
 template <typename T>
 __global__ void k_velocity(GridDesc g, const double* __restrict__ combo, T* __restrict__ vel) {
+  pdl_entry();
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npts; p += gridDim.x * blockDim.x) {
     if (g.op == IRK_OP_VSF_2D) {
       const Nbr nb = neighbours(g, p);
@@ -842,17 +854,18 @@ void launch_velocity_from_combo(const GridDesc& g, const double* combo, void* ve
   int blocks = (g.npts + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (prec == IRK_MG_FP64)
-    k_velocity<double><<<blocks, 256, 0, st>>>(g, combo, (double*)vel);
+    launch_pdl(k_velocity<double>, blocks, 256, 0, st, g, combo, (double*)vel);
   else if (prec == IRK_MG_FP32)
-    k_velocity<float><<<blocks, 256, 0, st>>>(g, combo, (float*)vel);
+    launch_pdl(k_velocity<float>, blocks, 256, 0, st, g, combo, (float*)vel);
   else
-    k_velocity<__nv_bfloat16><<<blocks, 256, 0, st>>>(g, combo, (__nv_bfloat16*)vel);
+    launch_pdl(k_velocity<__nv_bfloat16>, blocks, 256, 0, st, g, combo, (__nv_bfloat16*)vel);
 }
 
 // ---------------------------------------------------------------------------
 // Zero-mean projection of periodic fields (the psi null space of the DAE).
 __global__ void k_field_sums(long long npts, long long stride, const double* __restrict__ x,
                              double* __restrict__ partials) {
+  pdl_entry();
   __shared__ double sh[32];
   const double* f = x + blockIdx.y * stride;
   double acc = 0.0;
@@ -865,6 +878,7 @@ __global__ void k_field_sums(long long npts, long long stride, const double* __r
 
 __global__ void k_field_sub_mean(long long npts, long long stride, int nblk,
                                  const double* __restrict__ partials, double* __restrict__ x) {
+  pdl_entry();
   __shared__ double mean;
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -883,8 +897,8 @@ void launch_remove_mean(long long npts, int nfields, long long stride, double* x
   int nblk = (int)((npts + 255) / 256);
   if (nblk > 152) nblk = 152;
   dim3 grid(nblk, nfields);
-  k_field_sums<<<grid, 256, 0, st>>>(npts, stride, x, scratch);
-  k_field_sub_mean<<<grid, 256, 0, st>>>(npts, stride, nblk, scratch, x);
+  launch_pdl(k_field_sums, grid, 256, 0, st, npts, stride, x, scratch);
+  launch_pdl(k_field_sub_mean, grid, 256, 0, st, npts, stride, nblk, scratch, x);
 }
 
 }  // namespace irk
