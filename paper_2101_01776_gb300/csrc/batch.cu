@@ -56,7 +56,10 @@ struct Task {
   int pbase;           // first partial slot block (per chunk) of this task
   int inst, sys;       // owner instance / block solve (-1: none)
   int flag;            // Flag
-  int first;           // sweep from w = 0
+  const int* flagp;    // the flag word (set by the host from flag): the task
+  int on_nonzero;      // runs when (*flagp != 0) == on_nonzero
+  int first;           // sweep from w = 0 (residual: of the folded sweep; prolongation: set)
+  int nsw;             // damped-Jacobi sweeps of a k_bsweep task (1..3)
   int p2base, n2chunk; // Newton: the ||F(0)|| partials
   double c[6];
   const double* in[4];
@@ -99,6 +102,7 @@ struct Dev {
   const Plan* plans;
   const Task* tasks;
   const int* cs;
+  const int* ctask;  // per plan and CTA: the task of chunk blockIdx.x (-1: none)
   const Inst* inst;
   Newton* nw;
   Sys* sys;
@@ -107,33 +111,18 @@ struct Dev {
 };
 
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int find_task(const Dev& D, const Plan& P, int c) {
-  int lo = 0, hi = P.ntask - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (D.cs[P.cs0 + mid] <= c) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ bool task_on(const Dev& D, const Task& t) {
-  switch (t.flag) {
-    case F_INST: return D.nw[t.inst].active != 0;
-    case F_SYS: return D.sys[t.sys].fs->stopped == 0;
-    case F_REJ: return D.nw[t.inst].rejected != 0;
-    default: return true;
-  }
-}
-
 // Walk the chunks of plan pi; f(task, local chunk) runs with the whole CTA.
+// The task of this CTA's first chunk comes from a per-plan table (one load,
+// issued together with the plan header); later chunks belong to the same or
+// later tasks, found by stepping forward through the chunk starts.
 template <class F>
 __device__ __forceinline__ void for_chunks(const Dev& D, int pi, F f) {
   const Plan P = D.plans[pi];
+  int t = D.ctask[pi * kGrid + blockIdx.x];
   for (int c = blockIdx.x; c < P.nchunk; c += gridDim.x) {
-    const int t = find_task(D, P, c);
+    while (D.cs[P.cs0 + t + 1] <= c) ++t;
     const Task& tk = D.tasks[P.task0 + t];
-    if (!task_on(D, tk)) continue;
+    if (tk.flagp && ((*(volatile const int*)tk.flagp != 0) != (tk.on_nonzero != 0))) continue;
     f(tk, c - D.cs[P.cs0 + t]);
   }
 }
@@ -218,7 +207,93 @@ __device__ __forceinline__ double burgers_n(const double* __restrict__ Y, int np
 }
 
 // ---------------------------------------------------------------------------
-// Newton-level kernels (tasks: instances)
+// Newton-level kernels (tasks: instances).  The stage count is a template
+// parameter of the per-point bodies (registers, not local memory); a chunk
+// belongs to one instance, so the switch on its s is uniform in the CTA.
+#define IRK_BAT_STAGES(s_, CALL)          \
+  switch (s_) {                           \
+    case 1: { constexpr int S = 1; CALL; } break; \
+    case 2: { constexpr int S = 2; CALL; } break; \
+    case 3: { constexpr int S = 3; CALL; } break; \
+    case 4: { constexpr int S = 4; CALL; } break; \
+    default: { constexpr int S = 5; CALL; } break; \
+  }
+
+template <int S>
+__device__ __forceinline__ void begin_point(const Inst& I, long long p, bool extrapolate) {
+  I.u_save[p] = I.u[p];
+  double k[S];
+#pragma unroll
+  for (int i = 0; i < S; ++i) k[i] = I.K[i * I.L + p];
+#pragma unroll
+  for (int j = 0; j < S; ++j) {
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < S; ++i) acc = fma(I.E[j * S + i], k[i], acc);
+    I.K[j * I.L + p] = extrapolate ? acc : 0.0;
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void states_point(const Inst& I, long long p) {
+  const long long L = I.L;
+  double k[S], y[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) k[j] = I.K[j * L + p];
+  const double u = I.u[p];
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) acc = fma(I.A[i * S + j], k[j], acc);
+    y[i] = fma(I.dt, acc, u);
+    I.Y[i * L + p] = y[i];
+  }
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < S; ++m) acc = fma(I.Dd[q * S + m], y[m], acc);
+    I.combos[q * L + p] = acc;
+  }
+}
+
+// F_i = k_i - N(Y_i) at item q (component c, point p); rhs; returns sum F_i^2
+template <int S>
+__device__ __forceinline__ double resid_point(const Inst& I, int q) {
+  const int c = q >= I.npts ? 1 : 0, p = q - c * I.npts;
+  const P5 nb = nbr(p, I.n, I.logn);
+  const long long L = I.L;
+  double F[S], sq = 0.0;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    const double nv = burgers_n(I.Y + i * L, I.npts, c, nb, I.nu * I.invh2, -I.inv2h);
+    F[i] = __ldg(I.K + i * L + q) - nv;
+    sq = fma(F[i], F[i], sq);
+  }
+#pragma unroll
+  for (int k = 0; k < S; ++k) {
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < S; ++i) acc = fma(-I.Tinv[k * S + i], F[i], acc);
+    I.rhs[k * L + q] = acc;
+  }
+  return sq;
+}
+
+template <int S>
+__device__ __forceinline__ void update_point(const Inst& I, long long p) {
+  double y[S];
+#pragma unroll
+  for (int k = 0; k < S; ++k) y[k] = I.yhat[k * I.L + p];
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    double acc = I.K[i * I.L + p];
+#pragma unroll
+    for (int k = 0; k < S; ++k) acc = fma(I.TR[i * S + k], y[k], acc);
+    I.K[i * I.L + p] = acc;
+  }
+}
 
 // u_save = u; K <- E K (c[0] = 1) or 0
 __global__ void __launch_bounds__(kThreads) k_begin(Dev D, int pi) {
@@ -226,15 +301,7 @@ __global__ void __launch_bounds__(kThreads) k_begin(Dev D, int pi) {
     const Inst& I = D.inst[t.inst];
     const long long p = (long long)lc * kThreads + threadIdx.x;
     if (p >= t.count) return;
-    I.u_save[p] = I.u[p];
-    const int s = I.s;
-    double k[IRK_MAXS];
-    for (int i = 0; i < s; ++i) k[i] = I.K[i * I.L + p];
-    for (int j = 0; j < s; ++j) {
-      double acc = 0.0;
-      for (int i = 0; i < s; ++i) acc = fma(I.E[j * s + i], k[i], acc);
-      I.K[j * I.L + p] = t.c[0] != 0.0 ? acc : 0.0;
-    }
+    IRK_BAT_STAGES(I.s, begin_point<S>(I, p, t.c[0] != 0.0));
   });
 }
 
@@ -261,22 +328,7 @@ __global__ void __launch_bounds__(kThreads) k_states(Dev D, int pi) {
     const Inst& I = D.inst[t.inst];
     const long long p = (long long)lc * kThreads + threadIdx.x;
     if (p >= t.count) return;
-    const int s = I.s;
-    const long long L = I.L;
-    double k[IRK_MAXS], y[IRK_MAXS];
-    for (int j = 0; j < s; ++j) k[j] = I.K[j * L + p];
-    const double u = I.u[p];
-    for (int i = 0; i < s; ++i) {
-      double acc = 0.0;
-      for (int j = 0; j < s; ++j) acc = fma(I.A[i * s + j], k[j], acc);
-      y[i] = fma(I.dt, acc, u);
-      I.Y[i * L + p] = y[i];
-    }
-    for (int q = 0; q < s; ++q) {
-      double acc = 0.0;
-      for (int m = 0; m < s; ++m) acc = fma(I.Dd[q * s + m], y[m], acc);
-      I.combos[q * L + p] = acc;
-    }
+    IRK_BAT_STAGES(I.s, states_point<S>(I, p));
   });
 }
 
@@ -311,23 +363,7 @@ __global__ void __launch_bounds__(kThreads) k_resid(Dev D, int pi) {
     const Inst& I = D.inst[t.inst];
     const int q = lc * kThreads + threadIdx.x;
     double sq = 0.0;
-    if (q < t.count) {
-      const int c = q >= I.npts ? 1 : 0, p = q - c * I.npts;
-      const P5 nb = nbr(p, I.n, I.logn);
-      const int s = I.s;
-      const long long L = I.L;
-      double F[IRK_MAXS];
-      for (int i = 0; i < s; ++i) {
-        const double nv = burgers_n(I.Y + i * L, I.npts, c, nb, I.nu * I.invh2, -I.inv2h);
-        F[i] = __ldg(I.K + i * L + q) - nv;
-        sq = fma(F[i], F[i], sq);
-      }
-      for (int k = 0; k < s; ++k) {
-        double acc = 0.0;
-        for (int i = 0; i < s; ++i) acc = fma(-I.Tinv[k * s + i], F[i], acc);
-        I.rhs[k * L + q] = acc;
-      }
-    }
+    if (q < t.count) IRK_BAT_STAGES(I.s, sq = resid_point<S>(I, q));
     const double tot = cta_sum(sq, sh);
     if (threadIdx.x == 0) D.partials[(long long)(t.pbase + lc) * kPS] = tot;
   });
@@ -442,14 +478,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev D, int pi) {
     const Inst& I = D.inst[t.inst];
     const long long p = (long long)lc * kThreads + threadIdx.x;
     if (p >= t.count) return;
-    const int s = I.s;
-    double y[IRK_MAXS];
-    for (int k = 0; k < s; ++k) y[k] = I.yhat[k * I.L + p];
-    for (int i = 0; i < s; ++i) {
-      double acc = I.K[i * I.L + p];
-      for (int k = 0; k < s; ++k) acc = fma(I.TR[i * s + k], y[k], acc);
-      I.K[i * I.L + p] = acc;
-    }
+    IRK_BAT_STAGES(I.s, update_point<S>(I, p));
   });
 }
 
@@ -516,39 +545,128 @@ __global__ void __launch_bounds__(kThreads) k_mgcoef(Dev D, int pi) {
   });
 }
 
-// one damped-Jacobi sweep: in[0] = b, in[1] = w (unused when first), in[2] =
-// coefficients; out[0] = new w; c[0] = omega/D, c[1] = 1 - omega
-__global__ void __launch_bounds__(kThreads) k_smooth(Dev D, int pi) {
+// One to three damped-Jacobi sweeps (t.nsw) of a multigrid row on one level.
+// A chunk is a 32 x 8 tile (n >= 32), staged with a halo of nsw points: b,
+// the iterate and the four coefficients go to shared memory once, and the
+// sweeps run out of it on windows that shrink by one point per sweep; the
+// last one writes the tile.  A level of n <= 16 is one chunk, held whole
+// (periodic wrap in shared memory).  in[0] = b, in[1] = w (unused when
+// first), in[2] = coefficients; out[0] = the new w; c[0] = omega/D,
+// c[1] = 1 - omega.  Epilogue when out[1] is set (the L_P coupling row of a
+// 2x2 block): out[1] = in[3] + c[2] w on the last sweep.
+constexpr int kBX = 32, kBY = 8, kBH = 3;
+constexpr int kBW = kBX + 2 * kBH, kBHt = kBY + 2 * kBH;
+__global__ void __launch_bounds__(kThreads) k_bsweep(Dev D, int pi) {
+  __shared__ double sw[2][kBHt * kBW];
+  __shared__ double sb[kBHt * kBW];
+  __shared__ double sc[4][kBHt * kBW];
   for_chunks(D, pi, [&](const Task& t, int lc) {
-    const int p = lc * kThreads + threadIdx.x;
-    if (p >= t.count) return;
+    const int n = t.n, m = n - 1, ln = t.logn, np = t.npts, h = t.nsw;
     const double dinv = t.c[0], keep = t.c[1];
-    const int np = t.npts;
     const double* b = t.in[0];
-    double* wo = t.out[0];
-    if (t.first) {
-      wo[p] = dinv * b[p];
-      wo[np + p] = dinv * b[np + p];
-      return;
-    }
-    const P5 q = nbr(p, t.n, t.logn);
-    const double* cf = t.in[2];
-    const double ce = cf[p], cw = cf[np + p], cn = cf[2 * np + p], cs = cf[3 * np + p];
     const double* w = t.in[1];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const double* wc = w + c * np;
-      double s = b[c * np + p];
-      s = fma(-ce, wc[q.e], s);
-      s = fma(-cw, wc[q.w], s);
-      s = fma(-cn, wc[q.n], s);
-      s = fma(-cs, wc[q.s], s);
-      wo[c * np + p] = fma(dinv, s, keep * wc[p]);
+    const double* cf = t.in[2];
+    double* wo = t.out[0];
+    double* eo = t.out[1];
+    const double* eb = t.in[3];
+    if (n >= kBX) {
+      const int tpr = n / kBX;
+      const int x0 = (lc % tpr) * kBX - h, y0 = (lc / tpr) * kBY - h;
+      const int W = kBX + 2 * h, H = kBY + 2 * h;
+      for (int c = 0; c < 2; ++c) {
+        for (int q = threadIdx.x; q < W * H; q += kThreads) {
+          const int ly = q / W, lx = q - ly * W;
+          const int gp = (((y0 + ly) & m) << ln) + ((x0 + lx) & m);
+          sb[q] = b[c * np + gp];
+          if (!t.first) sw[0][q] = w[c * np + gp];
+          if (c == 0) {
+            sc[0][q] = cf[gp];
+            sc[1][q] = cf[np + gp];
+            sc[2][q] = cf[2 * np + gp];
+            sc[3][q] = cf[3 * np + gp];
+          }
+        }
+        __syncthreads();
+        int src = 0;
+        for (int k = 1; k <= h; ++k) {
+          const int rw = W - 2 * k, rh = H - 2 * k;
+          const double* s0 = sw[src];
+          for (int q = threadIdx.x; q < rw * rh; q += kThreads) {
+            const int ry = q / rw, rx = q - ry * rw;
+            const int wq = (ry + k) * W + rx + k;
+            double v;
+            if (t.first && k == 1) {
+              v = dinv * sb[wq];
+            } else {
+              double u = sb[wq];
+              u = fma(-sc[0][wq], s0[wq + 1], u);
+              u = fma(-sc[1][wq], s0[wq - 1], u);
+              u = fma(-sc[2][wq], s0[wq + W], u);
+              u = fma(-sc[3][wq], s0[wq - W], u);
+              v = fma(dinv, u, keep * s0[wq]);
+            }
+            if (k == h) {
+              const int gp = (((y0 + ry + k) & m) << ln) + ((x0 + rx + k) & m);
+              wo[c * np + gp] = v;
+              if (eo) eo[c * np + gp] = fma(t.c[2], v, eb[c * np + gp]);
+            } else {
+              sw[src ^ 1][wq] = v;
+            }
+          }
+          __syncthreads();
+          src ^= 1;
+        }
+      }
+    } else {
+      const int p = threadIdx.x;
+      const int i = p & m, j = p >> ln;
+      const int pe = (j << ln) + ((i + 1) & m), pw = (j << ln) + ((i - 1) & m);
+      const int pn = (((j + 1) & m) << ln) + i, ps = (((j - 1) & m) << ln) + i;
+      for (int c = 0; c < 2; ++c) {
+        if (p < np) {
+          sb[p] = b[c * np + p];
+          sw[0][p] = t.first ? 0.0 : w[c * np + p];
+          if (c == 0) {
+            sc[0][p] = cf[p];
+            sc[1][p] = cf[np + p];
+            sc[2][p] = cf[2 * np + p];
+            sc[3][p] = cf[3 * np + p];
+          }
+        }
+        __syncthreads();
+        int src = 0;
+        for (int k = 1; k <= h; ++k) {
+          if (p < np) {
+            const double* s0 = sw[src];
+            double v;
+            if (t.first && k == 1) {
+              v = dinv * sb[p];
+            } else {
+              double u = sb[p];
+              u = fma(-sc[0][p], s0[pe], u);
+              u = fma(-sc[1][p], s0[pw], u);
+              u = fma(-sc[2][p], s0[pn], u);
+              u = fma(-sc[3][p], s0[ps], u);
+              v = fma(dinv, u, keep * s0[p]);
+            }
+            if (k == h) {
+              wo[c * np + p] = v;
+              if (eo) eo[c * np + p] = fma(t.c[2], v, eb[c * np + p]);
+            } else {
+              sw[src ^ 1][p] = v;
+            }
+          }
+          __syncthreads();
+          src ^= 1;
+        }
+      }
     }
   });
 }
 
-// r = b - A w: in[0] = b, in[1] = w, in[2] = coefficients; c[0] = D
+// r = b - A w: in[0] = b, in[1] = w, in[2] = coefficients; c[0] = D.  first:
+// the residual after one sweep from zero, which is never stored: w = dinv b
+// gives r = (1 - omega) b - dinv sum_k c_k b_k (c[1] = 1 - omega, c[2] = dinv)
 __global__ void __launch_bounds__(kThreads) k_mgresid(Dev D, int pi) {
   for_chunks(D, pi, [&](const Task& t, int lc) {
     const int p = lc * kThreads + threadIdx.x;
@@ -559,20 +677,33 @@ __global__ void __launch_bounds__(kThreads) k_mgresid(Dev D, int pi) {
     const double ce = cf[p], cw = cf[np + p], cn = cf[2 * np + p], cs = cf[3 * np + p];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      const double* wc = t.in[1] + c * np;
-      double s = t.in[0][c * np + p];
-      s = fma(-t.c[0], wc[p], s);
-      s = fma(-ce, wc[q.e], s);
-      s = fma(-cw, wc[q.w], s);
-      s = fma(-cn, wc[q.n], s);
-      s = fma(-cs, wc[q.s], s);
-      t.out[0][c * np + p] = s;
+      const double* bc = t.in[0] + c * np;
+      double r;
+      if (t.first) {
+        double sum = ce * bc[q.e];
+        sum = fma(cw, bc[q.w], sum);
+        sum = fma(cn, bc[q.n], sum);
+        sum = fma(cs, bc[q.s], sum);
+        r = fma(-t.c[2], sum, t.c[1] * bc[p]);
+      } else {
+        const double* wc = t.in[1] + c * np;
+        double u = bc[p];
+        u = fma(-t.c[0], wc[p], u);
+        u = fma(-ce, wc[q.e], u);
+        u = fma(-cw, wc[q.w], u);
+        u = fma(-cn, wc[q.n], u);
+        u = fma(-cs, wc[q.s], u);
+        r = u;
+      }
+      t.out[0][c * np + p] = r;
     }
   });
 }
 
 // w_f += P w_c (bilinear): one item per coarse point, the four fine points it
-// owns; in[0] = coarse correction, out[0] = fine iterate, t.n = fine grid
+// owns; in[0] = coarse correction, out[0] = fine iterate, t.n = fine grid.
+// first: w_f = dinv b_f + P w_c (the folded pre-sweep's iterate, never
+// stored), with in[1] = b_f and c[0] = dinv
 __global__ void __launch_bounds__(kThreads) k_prolong(Dev D, int pi) {
   for_chunks(D, pi, [&](const Task& t, int lc) {
     const int p = lc * kThreads + threadIdx.x;
@@ -583,31 +714,21 @@ __global__ void __launch_bounds__(kThreads) k_prolong(Dev D, int pi) {
     for (int c = 0; c < 2; ++c) {
       const double* g = t.in[0] + (long long)c * t.count;
       double* f = t.out[0] + (long long)c * t.npts;
+      const double* bf = t.first ? t.in[1] + (long long)c * t.npts : nullptr;
       const double c00 = g[p], c10 = g[(J0 << logc) + I1];
       const double c01 = g[(J1 << logc) + I0], c11 = g[(J1 << logc) + I1];
       const long long o0 = ((long long)(2 * J0) << lf) + 2 * I0, o1 = o0 + t.n;
-      f[o0] += c00;
-      f[o0 + 1] += 0.5 * (c00 + c10);
-      f[o1] += 0.5 * (c00 + c01);
-      f[o1 + 1] += 0.25 * ((c00 + c10) + (c01 + c11));
+      auto base = [&](long long o) { return t.first ? t.c[0] * bf[o] : f[o]; };
+      f[o0] = base(o0) + c00;
+      f[o0 + 1] = base(o0 + 1) + 0.5 * (c00 + c10);
+      f[o1] = base(o1) + 0.5 * (c00 + c01);
+      f[o1 + 1] = base(o1 + 1) + 0.25 * ((c00 + c10) + (c01 + c11));
     }
   });
 }
 
 // ---------------------------------------------------------------------------
 // Block-solve kernels (tasks: block solves)
-
-// L_P coupling row (Eq. Lprec; mass only in the block-diagonal iteration):
-// tmpb = pin_b - R_ba pout_a
-__global__ void __launch_bounds__(kThreads) k_couple(Dev D, int pi) {
-  for_chunks(D, pi, [&](const Task& t, int lc) {
-    const Sys& S = D.sys[t.sys];
-    const long long p = (long long)lc * kThreads + threadIdx.x;
-    if (p >= t.count) return;
-    const long long L = S.Lb / 2;
-    S.tmpb[p] = fma(-t.c[0], S.pout[p], S.pin[L + p]);
-  });
-}
 
 // z = rhs_blk - sum_{later rows l} R_rl yhat_l (Eq. D+U, mass coupling),
 // stored in w; per-chunk ||z||^2; the last chunk starts the FGMRES cycle
@@ -747,20 +868,24 @@ __global__ void __launch_bounds__(kThreads) k_matvec(Dev D, int pi) {
 // the Arnoldi/Givens step of the block solve; next forms V_{j+1} = (w - V h2)
 // / h_{j+1,j} (the second update is never stored: ||w''||^2 = ||w'||^2 -
 // ||h2||^2).  kGsItems items per thread per chunk; partials per chunk and value.
-__device__ void chunk_sums(double* vals, int nv, double* sh, double* dst) {
-  // vals[v] of every thread summed over the CTA; thread 0 writes dst[v]
+template <int N>
+__device__ __forceinline__ void chunk_sums(const double (&vals)[N], int nv, double* sh,
+                                           double* dst) {
+  // vals[v] (v < nv <= N) of every thread summed over the CTA into dst[v]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int v = 0; v < nv; ++v) {
+#pragma unroll
+  for (int v = 0; v < N; ++v) {
+    if (v >= nv) break;
     double x = vals[v];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     if (lane == 0) sh[v * (kThreads / 32) + wid] = x;
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+  if (threadIdx.x < nv) {
     double r = 0.0;
-    for (int k = 0; k < kThreads / 32; ++k) r += sh[v * (kThreads / 32) + k];
-    dst[v] = r;
+    for (int k = 0; k < kThreads / 32; ++k) r += sh[threadIdx.x * (kThreads / 32) + k];
+    dst[threadIdx.x] = r;
   }
   __syncthreads();
 }
@@ -770,15 +895,27 @@ __global__ void __launch_bounds__(kThreads) k_gs1(Dev D, int pi) {
   for_chunks(D, pi, [&](const Task& t, int lc) {
     Sys& S = D.sys[t.sys];
     const int nv = S.fs->j + 1;
-    double acc[kPS];
-    for (int v = 0; v < nv; ++v) acc[v] = 0.0;
+    const long long q0 = (long long)lc * kGsItems * kThreads + threadIdx.x;
+    double wv[kGsItems];
+#pragma unroll
     for (int it = 0; it < kGsItems; ++it) {
-      const long long q = ((long long)lc * kGsItems + it) * kThreads + threadIdx.x;
-      if (q >= t.count) break;
-      const double wv = S.w[q];
-      for (int v = 0; v < nv; ++v) acc[v] = fma(S.V[v * S.Lb + q], wv, acc[v]);
+      const long long q = q0 + (long long)it * kThreads;
+      wv[it] = q < t.count ? S.w[q] : 0.0;
     }
-    chunk_sums(acc, nv, sh, D.partials + (long long)(t.pbase + lc) * kPS);
+    double* dst = D.partials + (long long)(t.pbase + lc) * kPS;
+    // four basis vectors at a time: the accumulators stay in registers
+    for (int k0 = 0; k0 < nv; k0 += 4) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int it = 0; it < kGsItems; ++it) {
+        const long long q = q0 + (long long)it * kThreads;
+        if (q >= t.count) break;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          if (k0 + kk < nv) acc[kk] = fma(S.V[(k0 + kk) * S.Lb + q], wv[it], acc[kk]);
+      }
+      chunk_sums(acc, min(4, nv - k0), sh, dst + k0);
+    }
     if (arrive_last(&S.ctr1, t.nchunk)) {
       reduce_partials(D.partials, t.pbase, t.nchunk, nv, S.h1);
       __syncthreads();
@@ -833,18 +970,35 @@ __global__ void __launch_bounds__(kThreads) k_gs2(Dev D, int pi) {
   for_chunks(D, pi, [&](const Task& t, int lc) {
     Sys& S = D.sys[t.sys];
     const int nv = S.fs->j + 1;
-    double acc[kPS];
-    for (int v = 0; v <= nv; ++v) acc[v] = 0.0;
+    const long long q0 = (long long)lc * kGsItems * kThreads + threadIdx.x;
+    double x[kGsItems];
+    double sq = 0.0;
+#pragma unroll
     for (int it = 0; it < kGsItems; ++it) {
-      const long long q = ((long long)lc * kGsItems + it) * kThreads + threadIdx.x;
-      if (q >= t.count) break;
-      double x = S.w[q];
-      for (int v = 0; v < nv; ++v) x = fma(-__ldcg(S.h1 + v), S.V[v * S.Lb + q], x);
-      S.w[q] = x;
-      for (int v = 0; v < nv; ++v) acc[v] = fma(S.V[v * S.Lb + q], x, acc[v]);
-      acc[nv] = fma(x, x, acc[nv]);
+      const long long q = q0 + (long long)it * kThreads;
+      x[it] = 0.0;
+      if (q >= t.count) continue;
+      double v = S.w[q];
+      for (int k = 0; k < nv; ++k) v = fma(-__ldcg(S.h1 + k), S.V[k * S.Lb + q], v);
+      S.w[q] = v;
+      x[it] = v;
+      sq = fma(v, v, sq);
     }
-    chunk_sums(acc, nv + 1, sh, D.partials + (long long)(t.pbase + lc) * kPS);
+    double* dst = D.partials + (long long)(t.pbase + lc) * kPS;
+    for (int k0 = 0; k0 < nv; k0 += 4) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int it = 0; it < kGsItems; ++it) {
+        const long long q = q0 + (long long)it * kThreads;
+        if (q >= t.count) break;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          if (k0 + kk < nv) acc[kk] = fma(S.V[(k0 + kk) * S.Lb + q], x[it], acc[kk]);
+      }
+      chunk_sums(acc, min(4, nv - k0), sh, dst + k0);
+    }
+    const double sqv[1] = {sq};
+    chunk_sums(sqv, 1, sh, dst + nv);
     if (arrive_last(&S.ctr2, t.nchunk)) {
       reduce_partials(D.partials, t.pbase, t.nchunk, nv + 1, S.h2);
       __syncthreads();
@@ -933,8 +1087,8 @@ __global__ void __launch_bounds__(kThreads) k_lincomb(Dev D, int pi) {
 // ---------------------------------------------------------------------------
 // Host side
 enum OpType {
-  O_BEGIN, O_F0, O_STATES, O_CCOEF, O_RESID, O_NEWTON, O_REJECT, O_RESTRICT, O_MGCOEF, O_SMOOTH,
-  O_MGRESID, O_PROLONG, O_COUPLE, O_FGINIT, O_KCOND, O_FGSCALE, O_MATVEC, O_GS1, O_GS2, O_NEXT,
+  O_BEGIN, O_F0, O_STATES, O_CCOEF, O_RESID, O_NEWTON, O_REJECT, O_RESTRICT, O_MGCOEF, O_BSWEEP,
+  O_MGRESID, O_PROLONG, O_FGINIT, O_KCOND, O_FGSCALE, O_MATVEC, O_GS1, O_GS2, O_NEXT,
   O_FGSOLVE, O_LINCOMB, O_UPDATE, O_FINISH,
   O_NEWTON_BEGIN, O_NEWTON_END, O_KRYLOV_BEGIN, O_KRYLOV_END
 };
@@ -1010,6 +1164,9 @@ struct irk_batch {
   std::vector<Plan> plans;
   std::vector<Task> tasks;
   std::vector<int> cs;
+  std::vector<int> ctask;
+  int* dctask = nullptr;
+  size_t cap_ctask = 0;
   int npart = 0;
   std::vector<Op> prog, captured;
   bool dirty = true;
@@ -1199,6 +1356,26 @@ bool setup_rows(InstHost& H, double dt, std::string& err) {
 }
 
 // ---- program construction --------------------------------------------------
+// The device word a task's flag tests, and the sense of the test.
+void set_flag(irk_batch* b, Task& t) {
+  t.flagp = nullptr;
+  t.on_nonzero = 1;
+  switch (t.flag) {
+    case F_INST:
+      t.flagp = &b->dnw[t.inst].active;
+      break;
+    case F_REJ:
+      t.flagp = &b->dnw[t.inst].rejected;
+      break;
+    case F_SYS:
+      t.flagp = &b->inst[t.sys / kMaxBlk].sys[t.sys % kMaxBlk].fs->stopped;
+      t.on_nonzero = 0;
+      break;
+    default:
+      break;
+  }
+}
+
 struct Builder {
   irk_batch* b;
   int addplan(const std::vector<Task>& ts, int ipc, bool reduce) {
@@ -1213,6 +1390,7 @@ struct Builder {
         t.pbase = b->npart;
         b->npart += t.nchunk;
       }
+      set_flag(b, t);
       b->cs.push_back(c);
       c += t.nchunk;
       b->tasks.push_back(t);
@@ -1220,6 +1398,16 @@ struct Builder {
     b->cs.push_back(c);
     P.nchunk = c;
     b->plans.push_back(P);
+    // task of chunk k for CTA k (chunks of a task are consecutive)
+    int ti = 0;
+    for (int k = 0; k < kGrid; ++k) {
+      if (k >= c) {
+        b->ctask.push_back(0);
+        continue;
+      }
+      while (b->cs[P.cs0 + ti + 1] <= k) ++ti;
+      b->ctask.push_back(ti);
+    }
     return (int)b->plans.size() - 1;
   }
   void op(int type, int plan, int mode = 0, int round = 0) { b->prog.push_back({type, plan, mode, round}); }
@@ -1261,82 +1449,112 @@ void mg_consts(const InstHost& H, const RowMG& R, int l, double omega, double* D
 }
 
 // One V-cycle phase: the rows `rows` (instance slot, block index, row in
-// block), each from its level-0 input to its output, in lock step.
+// block), each from its level-0 input to its output, in lock step.  On level
+// l a row going deeper takes its pre-sweeps (a single pre-sweep from zero is
+// folded into the residual and the prolongation, as in the single-instance
+// solver) and a row whose coarsest level is l takes its coarse sweeps, both
+// in the same k_bsweep launches of up to three sweeps each.  epi_out: the
+// pointwise L_P coupling row written by the row's last sweep.
 struct PhaseRow {
   int slot, blk, rr;
   const double* in;
   double* out;
+  double* epi_out;
+  const double* epi_base;
+  double epi_coef;
 };
 
 void emit_vcycle(irk_batch* b, Builder& B, const std::vector<PhaseRow>& rows) {
   if (rows.empty()) return;
-  int Dmax = 0;
-  for (auto& pr : rows) Dmax = std::max(Dmax, b->inst[pr.slot].row[b->inst[pr.slot].sys[pr.blk].a + pr.rr].depth);
   const size_t nr = rows.size();
-  std::vector<const double*> cur(nr * kMaxLev, nullptr);
-  std::vector<int> which(nr * kMaxLev, 0);  // 0: mw holds the iterate next, 1: mw2
   auto Rof = [&](size_t i) -> RowMG& {
     InstHost& H = b->inst[rows[i].slot];
     return H.row[H.sys[rows[i].blk].a + rows[i].rr];
   };
+  auto Hof = [&](size_t i) -> InstHost& { return b->inst[rows[i].slot]; };
   auto Sof = [&](size_t i) -> SysHost& { return b->inst[rows[i].slot].sys[rows[i].blk]; };
+  auto sysi = [&](size_t i) { return rows[i].slot * kMaxBlk + rows[i].blk; };
   auto bl = [&](size_t i, int l) -> const double* { return l == 0 ? rows[i].in : Sof(i).mb[l]; };
-  // next output buffer of row i on level l (ping-pong)
+  int Dmax = 0;
+  for (size_t i = 0; i < nr; ++i) Dmax = std::max(Dmax, Rof(i).depth);
+  std::vector<const double*> cur(nr * kMaxLev, nullptr);
+  std::vector<int> which(nr * kMaxLev, 0);
   auto nextbuf = [&](size_t i, int l) -> double* {
     SysHost& S = Sof(i);
     double* o = which[i * kMaxLev + l] == 0 ? S.mw[l] : S.mw2[l];
     which[i * kMaxLev + l] ^= 1;
     return o;
   };
-  for (int l = 0; l < Dmax; ++l) {
-    int S_l = 0;
-    for (size_t i = 0; i < nr; ++i) {
-      RowMG& R = Rof(i);
-      if (R.depth - 1 > l) S_l = std::max(S_l, R.npre);
-      else if (R.depth - 1 == l) S_l = std::max(S_l, R.ncs);
+  auto folded = [&](size_t i) { return Rof(i).npre == 1; };
+  auto points = [&](size_t i, int l) { return (long long)(Hof(i).n >> l) * (Hof(i).n >> l); };
+  auto tiles = [&](size_t i, int l) {
+    const int nl = Hof(i).n >> l;
+    return nl >= kBX ? (long long)(nl / kBX) * (nl / kBY) : 1LL;
+  };
+  // sweeps of row i on level l on the way down
+  auto down_sweeps = [&](size_t i, int l) {
+    const RowMG& R = Rof(i);
+    if (R.depth - 1 > l) return folded(i) ? 0 : R.npre;
+    if (R.depth - 1 == l) return R.ncs;
+    return 0;
+  };
+  auto sweep_task = [&](size_t i, int l, int nsw, bool first, double omega, double* out,
+                        bool epi) {
+    InstHost& H = Hof(i);
+    RowMG& R = Rof(i);
+    Task t = lev_task(H, rows[i].slot, sysi(i), l, tiles(i, l), F_SYS);
+    double Dg, dinv, keep;
+    mg_consts(H, R, l, omega, &Dg, &dinv, &keep);
+    t.c[0] = dinv;
+    t.c[1] = keep;
+    t.first = first;
+    t.nsw = nsw;
+    t.in[0] = bl(i, l);
+    t.in[1] = cur[i * kMaxLev + l];
+    t.in[2] = R.coef[l];
+    t.out[0] = out;
+    if (epi && rows[i].epi_out) {
+      t.out[1] = rows[i].epi_out;
+      t.in[3] = rows[i].epi_base;
+      t.c[2] = rows[i].epi_coef;
     }
-    for (int k = 0; k < S_l; ++k) {
+    return t;
+  };
+  for (int l = 0; l < Dmax; ++l) {
+    int nlaunch = 0;
+    for (size_t i = 0; i < nr; ++i) nlaunch = std::max(nlaunch, (down_sweeps(i, l) + 2) / 3);
+    for (int k = 0; k < nlaunch; ++k) {
       std::vector<Task> ts;
       for (size_t i = 0; i < nr; ++i) {
-        RowMG& R = Rof(i);
-        const bool pre = R.depth - 1 > l && k < R.npre;
-        const bool coarse = R.depth - 1 == l && k < R.ncs;
-        if (!pre && !coarse) continue;
-        InstHost& H = b->inst[rows[i].slot];
-        Task t = lev_task(H, rows[i].slot, rows[i].slot * kMaxBlk + rows[i].blk, l,
-                          (long long)(H.n >> l) * (H.n >> l), F_SYS);
-        double Dg, dinv, keep;
-        mg_consts(H, R, l, coarse ? R.omc : R.omega, &Dg, &dinv, &keep);
-        t.c[0] = dinv;
-        t.c[1] = keep;
-        t.first = (k == 0);
-        t.in[0] = bl(i, l);
-        t.in[1] = cur[i * kMaxLev + l];
-        t.in[2] = R.coef[l];
+        const int S = down_sweeps(i, l);
+        if (3 * k >= S) continue;
+        const RowMG& R = Rof(i);
+        const double om = (R.depth - 1 == l) ? R.omc : R.omega;
         double* o = nextbuf(i, l);
-        t.out[0] = o;
+        ts.push_back(sweep_task(i, l, std::min(3, S - 3 * k), k == 0, om, o, false));
         cur[i * kMaxLev + l] = o;
-        ts.push_back(t);
       }
-      B.op(O_SMOOTH, B.addplan(ts, kThreads, false));
+      B.op(O_BSWEEP, B.addplan(ts, 1, false));
     }
     std::vector<Task> tr, trs;
     for (size_t i = 0; i < nr; ++i) {
       RowMG& R = Rof(i);
       if (R.depth - 1 <= l) continue;
-      InstHost& H = b->inst[rows[i].slot];
+      InstHost& H = Hof(i);
       SysHost& S = Sof(i);
-      const int sysi = rows[i].slot * kMaxBlk + rows[i].blk;
-      Task t = lev_task(H, rows[i].slot, sysi, l, (long long)(H.n >> l) * (H.n >> l), F_SYS);
+      Task t = lev_task(H, rows[i].slot, sysi(i), l, points(i, l), F_SYS);
       double Dg, dinv, keep;
       mg_consts(H, R, l, R.omega, &Dg, &dinv, &keep);
       t.c[0] = Dg;
+      t.c[1] = keep;
+      t.c[2] = dinv;
+      t.first = folded(i);
       t.in[0] = bl(i, l);
       t.in[1] = cur[i * kMaxLev + l];
       t.in[2] = R.coef[l];
       t.out[0] = S.mr[l];
       tr.push_back(t);
-      Task u = lev_task(H, rows[i].slot, sysi, l, (long long)(H.n >> (l + 1)) * (H.n >> (l + 1)), F_SYS);
+      Task u = lev_task(H, rows[i].slot, sysi(i), l, points(i, l + 1), F_SYS);
       u.in[0] = S.mr[l];
       u.out[0] = S.mb[l + 1];
       trs.push_back(u);
@@ -1348,42 +1566,42 @@ void emit_vcycle(irk_batch* b, Builder& B, const std::vector<PhaseRow>& rows) {
   }
   for (int l = Dmax - 2; l >= 0; --l) {
     std::vector<Task> tp;
-    int post = 0;
+    int nlaunch = 0;
     for (size_t i = 0; i < nr; ++i) {
       RowMG& R = Rof(i);
       if (R.depth - 1 <= l) continue;
-      InstHost& H = b->inst[rows[i].slot];
-      Task t = lev_task(H, rows[i].slot, rows[i].slot * kMaxBlk + rows[i].blk, l,
-                        (long long)(H.n >> (l + 1)) * (H.n >> (l + 1)), F_SYS);
+      InstHost& H = Hof(i);
+      Task t = lev_task(H, rows[i].slot, sysi(i), l, points(i, l + 1), F_SYS);
       t.in[0] = cur[i * kMaxLev + l + 1];
-      t.out[0] = const_cast<double*>(cur[i * kMaxLev + l]);
+      if (folded(i)) {
+        double Dg, dinv, keep;
+        mg_consts(H, R, l, R.omega, &Dg, &dinv, &keep);
+        t.first = 1;
+        t.c[0] = dinv;
+        t.in[1] = bl(i, l);
+        double* o = nextbuf(i, l);
+        t.out[0] = o;
+        cur[i * kMaxLev + l] = o;
+      } else {
+        t.out[0] = const_cast<double*>(cur[i * kMaxLev + l]);
+      }
       tp.push_back(t);
-      post = std::max(post, R.npre);
+      nlaunch = std::max(nlaunch, (R.npre + 2) / 3);
     }
     if (tp.empty()) continue;
     B.op(O_PROLONG, B.addplan(tp, kThreads, false));
-    for (int k = 0; k < post; ++k) {
+    for (int k = 0; k < nlaunch; ++k) {
       std::vector<Task> ts;
       for (size_t i = 0; i < nr; ++i) {
         RowMG& R = Rof(i);
-        if (R.depth - 1 <= l || k >= R.npre) continue;
-        InstHost& H = b->inst[rows[i].slot];
-        Task t = lev_task(H, rows[i].slot, rows[i].slot * kMaxBlk + rows[i].blk, l,
-                          (long long)(H.n >> l) * (H.n >> l), F_SYS);
-        double Dg, dinv, keep;
-        mg_consts(H, R, l, R.omega, &Dg, &dinv, &keep);
-        t.c[0] = dinv;
-        t.c[1] = keep;
-        t.first = 0;
-        t.in[0] = bl(i, l);
-        t.in[1] = cur[i * kMaxLev + l];
-        t.in[2] = R.coef[l];
-        double* o = (l == 0 && k + 1 == R.npre) ? rows[i].out : nextbuf(i, l);
-        t.out[0] = o;
+        if (R.depth - 1 <= l || 3 * k >= R.npre) continue;
+        const int nsw = std::min(3, R.npre - 3 * k);
+        const bool last = (3 * k + nsw == R.npre);
+        double* o = (l == 0 && last) ? rows[i].out : nextbuf(i, l);
+        ts.push_back(sweep_task(i, l, nsw, false, R.omega, o, l == 0 && last));
         cur[i * kMaxLev + l] = o;
-        ts.push_back(t);
       }
-      B.op(O_SMOOTH, B.addplan(ts, kThreads, false));
+      B.op(O_BSWEEP, B.addplan(ts, 1, false));
     }
   }
 }
@@ -1393,6 +1611,7 @@ void build_program(irk_batch* b) {
   b->plans.clear();
   b->tasks.clear();
   b->cs.clear();
+  b->ctask.clear();
   b->prog.clear();
   b->npart = 0;
   Builder B{b};
@@ -1446,6 +1665,7 @@ void build_program(irk_batch* b) {
     }
     b->cs.push_back(0);
     b->plans.push_back(P);
+    for (int k = 0; k < kGrid; ++k) b->ctask.push_back(0);
     return (int)b->plans.size() - 1;
   };
   B.op(O_NEWTON, newton_plan(pr0), N_FIRST);
@@ -1495,7 +1715,7 @@ void build_program(irk_batch* b) {
     int rounds = 0;
     for (int k : slots) rounds = std::max(rounds, b->inst[k].tab.nblk);
     for (int rd = 0; rd < rounds; ++rd) {
-      std::vector<Task> sysT, sysG, sysC;
+      std::vector<Task> sysT, sysG;
       std::vector<PhaseRow> ra, rb;
       for (int k : slots) {
         InstHost& H = b->inst[k];
@@ -1508,13 +1728,13 @@ void build_program(irk_batch* b) {
         sysT.push_back(t);
         Task g = t;
         sysG.push_back(g);
-        ra.push_back({k, blk, 0, S.pin, S.pout});
         if (S.bs == 2) {
-          Task c = inst_task(H, k, H.L, F_SYS);
-          c.sys = sysi;
-          c.c[0] = H.tab.R[(S.a + 1) * H.s + S.a];
-          sysC.push_back(c);
-          rb.push_back({k, blk, 1, S.tmpb, S.pout + H.L});
+          // r_b' = v_b - R_ba z_a, written by the last sweep of row a's V-cycle
+          ra.push_back({k, blk, 0, S.pin, S.pout, S.tmpb, S.pin + H.L,
+                        -H.tab.R[(S.a + 1) * H.s + S.a]});
+          rb.push_back({k, blk, 1, S.tmpb, S.pout + H.L, nullptr, nullptr, 0.0});
+        } else {
+          ra.push_back({k, blk, 0, S.pin, S.pout, nullptr, nullptr, 0.0});
         }
       }
       std::vector<Task> sysInit = sysT;
@@ -1525,7 +1745,6 @@ void build_program(irk_batch* b) {
       B.op(O_FGSCALE, B.addplan(sysT, kThreads, false));
       B.op(O_KRYLOV_BEGIN, -1, 0, rd);
       emit_vcycle(b, B, ra);
-      if (!sysC.empty()) B.op(O_COUPLE, B.addplan(sysC, kThreads, false));
       emit_vcycle(b, B, rb);
       std::vector<Task> mv;
       for (auto& t : sysT) {
@@ -1569,6 +1788,7 @@ irk_status upload(irk_batch* b, bool* realloc_done) {
   BCK(grow((void**)&b->dplans, &b->cap_plans, b->plans.size() * sizeof(Plan)));
   BCK(grow((void**)&b->dtasks, &b->cap_tasks, b->tasks.size() * sizeof(Task)));
   BCK(grow((void**)&b->dcs, &b->cap_cs, b->cs.size() * sizeof(int)));
+  BCK(grow((void**)&b->dctask, &b->cap_ctask, b->ctask.size() * sizeof(int)));
   BCK(grow((void**)&b->dpart, &b->cap_part, (size_t)std::max(b->npart, 1) * kPS * sizeof(double)));
   BCK(cudaMemcpyAsync(b->dplans, b->plans.data(), b->plans.size() * sizeof(Plan),
                       cudaMemcpyHostToDevice, b->st));
@@ -1576,6 +1796,8 @@ irk_status upload(irk_batch* b, bool* realloc_done) {
                       cudaMemcpyHostToDevice, b->st));
   BCK(cudaMemcpyAsync(b->dcs, b->cs.data(), b->cs.size() * sizeof(int), cudaMemcpyHostToDevice,
                       b->st));
+  BCK(cudaMemcpyAsync(b->dctask, b->ctask.data(), b->ctask.size() * sizeof(int),
+                      cudaMemcpyHostToDevice, b->st));
   BCK(cudaStreamSynchronize(b->st));  // the host vectors may change before the next step
   return IRK_OK;
 }
@@ -1590,6 +1812,7 @@ irk_status capture(irk_batch* b) {
   D.plans = b->dplans;
   D.tasks = b->dtasks;
   D.cs = b->dcs;
+  D.ctask = b->dctask;
   D.inst = b->dinst;
   D.nw = b->dnw;
   D.sys = b->dsys;
@@ -1634,10 +1857,9 @@ irk_status capture(irk_batch* b) {
       case O_REJECT: k_reject<<<kGrid, kThreads, 0, cur>>>(D, pi); break;
       case O_RESTRICT: k_restrict<<<kGrid, kThreads, 0, cur>>>(D, pi); break;
       case O_MGCOEF: k_mgcoef<<<kGrid, kThreads, 0, cur>>>(D, pi); break;
-      case O_SMOOTH: k_smooth<<<kGrid, kThreads, 0, cur>>>(D, pi); break;
+      case O_BSWEEP: k_bsweep<<<kGrid, kThreads, 0, cur>>>(D, pi); break;
       case O_MGRESID: k_mgresid<<<kGrid, kThreads, 0, cur>>>(D, pi); break;
       case O_PROLONG: k_prolong<<<kGrid, kThreads, 0, cur>>>(D, pi); break;
-      case O_COUPLE: k_couple<<<kGrid, kThreads, 0, cur>>>(D, pi); break;
       case O_FGINIT: k_fginit<<<kGrid, kThreads, 0, cur>>>(D, pi); break;
       case O_KCOND: k_kcond<<<1, 256, 0, cur>>>(D, pi, o.round, kcond[o.round]); break;
       case O_FGSCALE: k_fgscale<<<kGrid, kThreads, 0, cur>>>(D, pi); break;
@@ -1979,6 +2201,7 @@ void irk_batch_destroy(irk_batch* b) {
   cudaFree(b->dplans);
   cudaFree(b->dtasks);
   cudaFree(b->dcs);
+  cudaFree(b->dctask);
   cudaFree(b->dpart);
   if (b->hnw) cudaFreeHost(b->hnw);
   if (b->aux) cudaStreamDestroy(b->aux);
