@@ -294,7 +294,7 @@ constexpr int kTX = 32, kTY = 8;
 // becomes x_new = x_prev + omega (J(x) - x_prev), with x_prev the iterate
 // before x; the pair reads x_{k-1} (w_prev) and x_k (w_in) and writes x_{k+1}
 // (w_mid) and x_{k+2} (w_out).  `first`: x_0 = 0 (then w_in, w_prev unused).
-template <typename TS, int KIND, bool CHEB, typename TV = TS>
+template <typename TS, int KIND, bool CHEB, typename TV = TS, bool ZK = false>
 __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int ncomp, MGConst k,
                                                         const TV* __restrict__ vel,
                                                         const TS* __restrict__ b,
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
         t = fma(-s_c[1][q], s_in[sy][sx - 1], t);
         t = fma(-s_c[2][q], s_in[sy + 1][sx], t);
         t = fma(-s_c[3][q], s_in[sy - 1][sx], t);
-        v = fma(dinv, t, keep * s_in[sy][sx]);
+        v = ZK ? dinv * t : fma(dinv, t, keep * s_in[sy][sx]);
         if (CHEB) {
           const TC xp = s_p[q];
           v = fma(wa, v - xp, xp);
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
       t = fma(-s_c[1][q], s_w1[sy][sx - 1], t);
       t = fma(-s_c[2][q], s_w1[sy + 1][sx], t);
       t = fma(-s_c[3][q], s_w1[sy - 1][sx], t);
-      TC v = fma(dinv, t, keep * s_w1[sy][sx]);
+      TC v = ZK ? dinv * t : fma(dinv, t, keep * s_w1[sy][sx]);
       if (CHEB) {
         const TC xp = first ? TC(0) : s_in[sy + 1][sx + 1];  // x_k at this point
         v = fma(wb, v - xp, xp);
@@ -400,8 +400,9 @@ __global__ void __launch_bounds__(kTX * kTY) k_mg_smooth2(MGLevelDesc lv, int nc
 // window, then sweeps the halo-2 window, the halo-1 window and the tile out
 // of shared memory (TY = 8: 1028 point updates for 768 useful ones; TY = 16:
 // 1844 for 1536).  Intermediate sweeps are rounded to the storage type: three
-// single sweeps bit for bit.
-template <typename TS, int KIND, int TY, typename TV = TS>
+// single sweeps bit for bit.  ZK: undamped sweeps (1 - omega = 0, the
+// shift-dominated coarsest levels), w = dinv t without the zero term.
+template <typename TS, int KIND, int TY, typename TV = TS, bool ZK = false>
 __global__ void __launch_bounds__(kTX * TY) k_mg_smooth3(MGLevelDesc lv, int ncomp, MGConst k,
                                                         const TV* __restrict__ vel,
                                                         const TS* __restrict__ b,
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(kTX * TY) k_mg_smooth3(MGLevelDesc lv, int nco
         t = fma(-s_c[1][q], s_w0[sy][sx - 1], t);
         t = fma(-s_c[2][q], s_w0[sy + 1][sx], t);
         t = fma(-s_c[3][q], s_w0[sy - 1][sx], t);
-        v = fma(dinv, t, keep * s_w0[sy][sx]);
+        v = ZK ? dinv * t : fma(dinv, t, keep * s_w0[sy][sx]);
       }
       s_w1[ly][lx] = round_to_storage<TS>(v);
     }
@@ -473,7 +474,7 @@ __global__ void __launch_bounds__(kTX * TY) k_mg_smooth3(MGLevelDesc lv, int nco
       t = fma(-s_c[1][cq], s_w1[sy][sx - 1], t);
       t = fma(-s_c[2][cq], s_w1[sy + 1][sx], t);
       t = fma(-s_c[3][cq], s_w1[sy - 1][sx], t);
-      s_w0[ly][lx] = round_to_storage<TS>(fma(dinv, t, keep * s_w1[sy][sx]));
+      s_w0[ly][lx] = round_to_storage<TS>(ZK ? dinv * t : fma(dinv, t, keep * s_w1[sy][sx]));
     }
     __syncthreads();
     // sweep 3 on the tile: s_w0 (halo-1 window at [0..TY+1][0..kTX+1]) -> global
@@ -486,7 +487,8 @@ __global__ void __launch_bounds__(kTX * TY) k_mg_smooth3(MGLevelDesc lv, int nco
       t = fma(-s_c[1][cq], s_w0[sy][sx - 1], t);
       t = fma(-s_c[2][cq], s_w0[sy + 1][sx], t);
       t = fma(-s_c[3][cq], s_w0[sy - 1][sx], t);
-      stv<TS, TC>(w_out + off + tile_pt(x0 + lx, y0 + ly, ln, n), fma(dinv, t, keep * s_w0[sy][sx]));
+      stv<TS, TC>(w_out + off + tile_pt(x0 + lx, y0 + ly, ln, n),
+                  ZK ? dinv * t : fma(dinv, t, keep * s_w0[sy][sx]));
     }
     __syncthreads();
   }
@@ -1028,6 +1030,23 @@ void launch_mg_smooth2(int prec, int kind, const MGLevelDesc& lv, int ncomp, dou
   // component); larger levels loop over the components in one CTA
   const int zsplit = (lv.n <= 256) ? ncomp : 1;
   const dim3 grid(lv.n / kTX, lv.n / kTY, zsplit), block(kTX, kTY);
+  if (k.keep == 0.0) {
+    IRK_DISPATCH_PREC(prec, {
+      if (kind == MG_ADVECTIVE)
+        launch_pdl(k_mg_smooth2<TS, MG_ADVECTIVE, false, TV, true>, grid, block, 0, st, lv, ncomp, k,
+                   (const TV*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, nullptr,
+                   nullptr, 1.0, 1.0);
+      else if (kind == MG_ADVECTIVE_PRE)
+        launch_pdl(k_mg_smooth2<TS, MG_ADVECTIVE_PRE, false, TV, true>, grid, block, 0, st, lv,
+                   ncomp, k, (const TV*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first,
+                   nullptr, nullptr, 1.0, 1.0);
+      else
+        launch_pdl(k_mg_smooth2<TS, MG_DIFFUSION, false, TV, true>, grid, block, 0, st, lv, ncomp, k,
+                   (const TV*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first, nullptr,
+                   nullptr, 1.0, 1.0);
+    });
+    return;
+  }
   IRK_DISPATCH_PREC(prec, {
     if (kind == MG_ADVECTIVE)
       launch_pdl(k_mg_smooth2<TS, MG_ADVECTIVE, false, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,
@@ -1071,21 +1090,25 @@ void launch_mg_smooth3(int prec, int kind, const MGLevelDesc& lv, int ncomp, dou
   const bool tall = tile_rows == 16 || (tile_rows == 0 && prec == IRK_MG_FP64);
   const int ty = tall ? 16 : kTY;
   const dim3 grid(lv.n / kTX, lv.n / ty, zsplit), block(kTX, ty);
-#define IRK_S3(TY_)                                                                               \
+#define IRK_S3(TY_, ZK_)                                                                          \
   do {                                                                                            \
     if (kind == MG_ADVECTIVE)                                                                     \
-      launch_pdl(k_mg_smooth3<TS, MG_ADVECTIVE, TY_, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,   \
-          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                                      \
-    else if (kind == MG_ADVECTIVE_PRE)                                                            \
-      launch_pdl(k_mg_smooth3<TS, MG_ADVECTIVE_PRE, TY_, TV>, grid, block, 0, st, lv, ncomp, k,               \
+      launch_pdl(k_mg_smooth3<TS, MG_ADVECTIVE, TY_, TV, ZK_>, grid, block, 0, st, lv, ncomp, k,  \
           (const TV*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                      \
+    else if (kind == MG_ADVECTIVE_PRE)                                                            \
+      launch_pdl(k_mg_smooth3<TS, MG_ADVECTIVE_PRE, TY_, TV, ZK_>, grid, block, 0, st, lv, ncomp, \
+          k, (const TV*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                   \
     else                                                                                          \
-      launch_pdl(k_mg_smooth3<TS, MG_DIFFUSION, TY_, TV>, grid, block, 0, st, lv, ncomp, k, (const TV*)vel,   \
-          (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                                      \
+      launch_pdl(k_mg_smooth3<TS, MG_DIFFUSION, TY_, TV, ZK_>, grid, block, 0, st, lv, ncomp, k,  \
+          (const TV*)vel, (const TS*)b, (const TS*)w_in, (TS*)w_out, first);                      \
   } while (0)
+  // undamped sweeps (1 - omega = 0) drop the zero term
+  const bool zk = (k.keep == 0.0);
   IRK_DISPATCH_PREC(prec, {
-    if (tall) IRK_S3(16);
-    else IRK_S3(kTY);
+    if (tall && zk) IRK_S3(16, true);
+    else if (tall) IRK_S3(16, false);
+    else if (zk) IRK_S3(kTY, true);
+    else IRK_S3(kTY, false);
   });
 #undef IRK_S3
 }

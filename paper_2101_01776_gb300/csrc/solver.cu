@@ -504,7 +504,10 @@ bool jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, doub
   const double velf = ((kind == MG_DIFFUSION) ? 0
                        : (kind == MG_ADVECTIVE_PRE) ? 4 : (kind == MG_CONSERVATIVE_1D ? 1 : dim)) *
                       (kind == MG_ADVECTIVE_PRE ? 1.0 : (double)mg_vel_size(prec) / h->esz);
-  const double fsw = mg_sweep_flops(kind, dim, ncomp) * d.npts;  // one sweep
+  // one sweep; the tile kernels' undamped sweeps (1 - omega = 0) skip the
+  // damping product and the add of the diagonal FMA: 2 flops less per value
+  const double fsw = mg_sweep_flops(kind, dim, ncomp) * d.npts;
+  const double fsw_tile = (om == 1.0 ? fsw - 2.0 * ncomp * d.npts : fsw);
   const double f0 = (double)ncomp * d.npts;                       // a sweep from zero
   const double pts = (double)ncomp * d.npts;
   int sw = 0;
@@ -518,14 +521,14 @@ bool jacobi_sweeps(irk_handle* h, int l, int kind, int ncomp, double sigma, doub
     if (rem >= 3 && rem != 4 && mg_smooth3_pays(prec, dim, d) && !(rem == 3 && last == b)) {
       if (rem == 3 && last) dst = last;
       ProfScope ps(h, P_MG_SMOOTH2, mg_level_bytes(h, l, (first ? 2.0 : 3.0) * ncomp + velf),
-                   first ? f0 + 2.0 * fsw : 3.0 * fsw);
+                   first ? f0 + 2.0 * fsw_tile : 3.0 * fsw_tile);
       launch_mg_smooth3(prec, kind, d, ncomp, sigma, cadv, cdiff, om, vel, b, cur, dst, first,
                         h->st, h->cfg.mg_tile_rows);
       sw += 3;
     } else if (sw + 1 < sweeps && mg_smooth2_pays(prec, dim, kind, d, first) && !(ends_pair && last == b)) {
       if (ends_pair && last) dst = last;
       ProfScope ps(h, P_MG_SMOOTH2, mg_level_bytes(h, l, (first ? 2.0 : 3.0) * ncomp + velf),
-                   first ? f0 + fsw : 2.0 * fsw);
+                   first ? f0 + fsw_tile : 2.0 * fsw_tile);
       launch_mg_smooth2(prec, kind, d, ncomp, sigma, cadv, cdiff, om, vel, b, cur, dst, first,
                         h->st);
       sw += 2;
