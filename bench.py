@@ -411,6 +411,8 @@ def run_ours(args, rank, world):
         nbytes = u0.size * 8
         line["e2e"] = {"value": e2e_n / t_e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes}
+        # ---- what one copy launch of a given size reaches (the HBM floor) ----
+        line["copy_floor"] = copy_floor_leg(torch, dev, stream, flush, hbm_peak)
         # ---- the other stage count and the FP32 V-cycle, same workload ------
         extra = {}
         # (the *_transfer runs: the residual-restriction fusion against the
@@ -554,13 +556,41 @@ def run_ours(args, rank, world):
     if rank == 0:
         # the side results go last, the most read last of all, rounded to
         # four significant digits (the tail of the line is what logs keep)
-        for k in ("kernels", "roofline_next", "variants", "solver_comparison", "gauss_vs_sdirk",
+        for k in ("copy_floor", "kernels", "roofline_next", "variants", "solver_comparison", "gauss_vs_sdirk",
                   "vsf_dae_solvers", "autotuned", "serving_32_slots", "serving",
                   "serving_small_grids", "batched_serving", "precision"):
             if k in line:
                 line[k] = _round(line.pop(k))
         print(json.dumps(line), flush=True)
     return 0
+
+
+def copy_floor_leg(torch, dev, stream, flush, hbm_peak):
+    """Device-to-device copies of 1 to 512 MB, one launch each after an L2
+    flush (CUDA events on the stream): the bandwidth a single launch of that
+    many bytes reaches, against which the 1-40 MB kernels of the V-cycle and
+    the Krylov loop are read."""
+    out = []
+    for mb in (1, 4, 16, 64, 512):
+        n = mb * 1024 * 1024 // 8
+        src = torch.ones(n, dtype=torch.float64, device=dev)
+        dst = torch.empty_like(src)
+        for _ in range(3):
+            dst.copy_(src)
+        reps, tot = 10, 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dst.copy_(src)
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        us = 1e3 * tot / reps
+        gbs = 2.0 * n * 8 / (us * 1e-6) / 1e9  # bytes read + written
+        out.append({"MB": mb, "us": us, "GBps": gbs, "frac_of_peak": gbs / hbm_peak})
+        del src, dst
+    return {"what": "one copy launch (read + write) after an L2 flush, mean of 10", "sizes": out}
 
 
 def _round(x):

@@ -12,6 +12,9 @@
 // substitution), in FP64.  Outside a graph (the solver's per-kernel timing
 // mode launches these kernels one by one) the handle is zero and the loop
 // state lives only in the FGState block.
+#include <cstdint>
+#include <initializer_list>
+
 #include "irk_internal.h"
 
 namespace irk {
@@ -122,15 +125,29 @@ __global__ void k_fg_init(FGState* s, const double* __restrict__ nrm2, const dou
 }
 
 // v = w * s->inv_scale written to V_j (j from s) and to prec_in
+// (vec: the 16-byte form, two points per access; same arithmetic per point)
 __global__ void k_fg_scale(const double* __restrict__ w, const FGState* __restrict__ s,
                            double* __restrict__ V, long long ldv, double* __restrict__ prec_in,
-                           long long L) {
+                           long long L, int vec) {
   pdl_entry();
   const double sc = s->inv_scale;
   IRK_CHECK(s->j, IRK_FG_MAXM + 1);
   double* vj = V + (long long)s->j * ldv;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
-       p += (long long)gridDim.x * blockDim.x) {
+  const long long S = (long long)gridDim.x * blockDim.x;
+  if (vec) {
+    const double2* __restrict__ w2 = reinterpret_cast<const double2*>(w);
+    double2* __restrict__ v2 = reinterpret_cast<double2*>(vj);
+    double2* __restrict__ p2 = reinterpret_cast<double2*>(prec_in);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (L >> 1); q += S) {
+      double2 x = w2[q];
+      x.x *= sc;
+      x.y *= sc;
+      v2[q] = x;
+      p2[q] = x;
+    }
+    return;
+  }
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L; p += S) {
     const double x = w[p] * sc;
     vj[p] = x;
     prec_in[p] = x;
@@ -149,18 +166,35 @@ __global__ void k_fg_solve(FGState* s) {
   }
 }
 
-// x += sum_{j<k} y_j Z_j
+// x += sum_{j<k} y_j Z_j (vec: the 16-byte form; the same order over j per point)
 __global__ void k_fg_lincomb(double* __restrict__ x, const double* __restrict__ Z, long long ldz,
-                             const FGState* __restrict__ s, long long L) {
+                             const FGState* __restrict__ s, long long L, int vec) {
   pdl_entry();
   __shared__ double ys[IRK_FG_MAXM];
   const int k = s->k;
   IRK_CHECK(k, IRK_FG_MAXM + 1);
   for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = s->y[j];
   __syncthreads();
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L;
-       p += (long long)gridDim.x * blockDim.x) {
+  const long long S = (long long)gridDim.x * blockDim.x;
+  if (vec) {
+    const double2* __restrict__ Z2 = reinterpret_cast<const double2*>(Z);
+    double2* __restrict__ x2 = reinterpret_cast<double2*>(x);
+    const long long ld2 = ldz >> 1;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (L >> 1); q += S) {
+      double2 acc = x2[q];
+#pragma unroll 4
+      for (int j = 0; j < k; ++j) {
+        const double2 z = Z2[j * ld2 + q];
+        acc.x = fma(ys[j], z.x, acc.x);
+        acc.y = fma(ys[j], z.y, acc.y);
+      }
+      x2[q] = acc;
+    }
+    return;
+  }
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L; p += S) {
     double acc = x[p];
+#pragma unroll 4
     for (int j = 0; j < k; ++j) acc = fma(ys[j], Z[j * ldz + p], acc);
     x[p] = acc;
   }
@@ -175,27 +209,87 @@ __global__ void k_fg_lincomb(double* __restrict__ x, const double* __restrict__ 
 // entry, and w'' = w' - V h2 is formed inside the normalisation kernel.
 
 // Sum `count` values (stride `stride`) of the partials of all blocks; called by
-// the whole last block; out[v] = sum_b partials[b*stride + v].
+// the whole last block; out[v] = sum_b partials[b*stride + v] (in b order),
+// also copied to the shared array sout when given.
 __device__ void last_block_reduce(const double* partials, int nblk, int stride, int count,
-                                  double* out) {
+                                  double* out, double* sout = nullptr) {
+  constexpr int R = 10;  // loads in flight per lane (304 blocks = 9.5 per lane)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int v = wid; v < count; v += nw) {
     double acc = 0.0;
-    for (int b = lane; b < nblk; b += 32) acc += __ldcg(partials + (long long)b * stride + v);
+    for (int b0 = lane; b0 < nblk; b0 += 32 * R) {
+      double t[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int b = b0 + 32 * r;
+        t[r] = b < nblk ? __ldcg(partials + (long long)b * stride + v) : 0.0;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc += t[r];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) out[v] = acc;
+    if (lane == 0) {
+      out[v] = acc;
+      if (sout) sout[v] = acc;
+    }
   }
 }
 
 __device__ bool arrive_last(unsigned int* ctr) {
   __shared__ bool last;
-  __threadfence();
+  // every partial of a block is stored by threads of warp 0 (fewer than 32
+  // values, or chunks of 4): their fence publishes them before the count
+  if (threadIdx.x < 32) __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(ctr, 1u) == gridDim.x - 1);
   __syncthreads();
   if (last) __threadfence();
   return last;
+}
+
+// 16-byte form of the first projection: two consecutive points per load and U
+// such pairs per thread and pass, so that a warp keeps (nv + 1) U loads of 16
+// bytes in flight (U = 2 up to four basis vectors, 1 up to eight; the scalar
+// form below otherwise).  Used when L and ldv are even and every vector starts
+// on 16 bytes (the launcher checks).  Out-of-range pairs of the last pass load
+// zeros, which add nothing to the sums.  (The same form measured slower for
+// the update kernels k_fg_gs2 and k_fg_next, which keep the scalar bodies.)
+template <int NV>
+struct PairsPerPass {
+  static constexpr int U = NV <= 4 ? 2 : 1;
+};
+
+template <int NV, int U>
+__device__ __forceinline__ void gs1_body2(const double* __restrict__ V, long long ldv,
+                                          const double* __restrict__ w, long long L,
+                                          double* __restrict__ partials, double* sh) {
+  const double2* __restrict__ V2 = reinterpret_cast<const double2*>(V);
+  const double2* __restrict__ w2 = reinterpret_cast<const double2*>(w);
+  const long long L2 = L >> 1, ld2 = ldv >> 1, S = (long long)gridDim.x * blockDim.x;
+  const double2 zero = make_double2(0.0, 0.0);
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < L2; q += U * S) {
+    double2 wv[U], v[NV][U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long qu = q + u * S;
+      const bool in = qu < L2;
+      wv[u] = in ? w2[qu] : zero;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) v[k][u] = in ? V2[k * ld2 + qu] : zero;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        acc[k] = fma(v[k][u].x, wv[u].x, acc[k]);
+        acc[k] = fma(v[k][u].y, wv[u].y, acc[k]);
+      }
+  }
+  dev_block_sum<NV>(acc, sh, partials + (long long)blockIdx.x * NV);
 }
 
 template <int NV>
@@ -216,13 +310,22 @@ __device__ __forceinline__ void gs1_body(const double* __restrict__ V, long long
 
 __global__ void __launch_bounds__(IRK_BLAS_THREADS)
 k_fg_gs1(const double* __restrict__ V, long long ldv, FGState* s, const double* __restrict__ w,
-         long long L, double* __restrict__ partials, double* __restrict__ h1) {
+         long long L, double* __restrict__ partials, double* __restrict__ h1, int vec) {
   pdl_entry();
   __shared__ double sh[17 * 8];
   const int nv = s->j + 1;
   IRK_CHECK(s->j, IRK_FG_MAXM);
   switch (nv) {
-#define IRK_C(N) case N: gs1_body<N>(V, ldv, w, L, partials, sh); break;
+#define IRK_C(N)                                                                   \
+  case N:                                                                          \
+    if constexpr (N <= 8) {                                                        \
+      if (vec) {                                                                   \
+        gs1_body2<N, PairsPerPass<N>::U>(V, ldv, w, L, partials, sh);              \
+        break;                                                                     \
+      }                                                                            \
+    }                                                                              \
+    gs1_body<N>(V, ldv, w, L, partials, sh);                                       \
+    break;
     IRK_DEV_NV_CASES(IRK_C)
 #undef IRK_C
     default: dev_multi_dot_any(V, ldv, nv, w, L, partials, sh);
@@ -233,51 +336,82 @@ k_fg_gs1(const double* __restrict__ V, long long ldv, FGState* s, const double* 
   }
 }
 
-// Arnoldi/Givens step of iteration j from h1, h2 (= h2[0..nv)) and ||w'||^2 = h2[nv].
-__device__ void arnoldi_step(FGState* s, const double* h1, const double* h2, int m, int maxit,
-                             double* its_total, cudaGraphConditionalHandle cond) {
+// Arnoldi/Givens step of iteration j from h1, h2 (= h2[0..nv)) and ||w'||^2 =
+// h2[nv], run by the whole last block of k_fg_gs2.  The operands (h1, the
+// rotations so far, g_j) are staged in shared memory by many threads first,
+// so that the serial recurrence of thread 0 waits on no global-memory round
+// trip; the new column and rotation are stored back the same way.
+struct ArnoldiShared {
+  double hc[IRK_FG_MAXM + 2];  // column j of the Hessenberg matrix
+  double h2[IRK_FG_MAXM + 2];  // second projection and ||w'||^2
+  double cs[IRK_FG_MAXM], sn[IRK_FG_MAXM];
+  double g[2];                 // g_j, g_{j+1}
+};
+
+__device__ void arnoldi_step(FGState* s, const double* __restrict__ h1, ArnoldiShared& A, int m,
+                             int maxit, double* its_total, cudaGraphConditionalHandle cond) {
   const int j = s->j;
   const int nv = j + 1;
   IRK_CHECK(j, m);
   IRK_CHECK(m - 1, IRK_FG_MAXM);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    A.hc[i] = __ldcg(h1 + i) + A.h2[i];
+    if (i < j) {
+      A.cs[i] = s->cs[i];
+      A.sn[i] = s->sn[i];
+    }
+  }
+  if (threadIdx.x == 0) A.g[0] = s->g[j];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double h2sq = 0.0;
+    for (int i = 0; i <= j; ++i) h2sq = fma(A.h2[i], A.h2[i], h2sq);
+    const double rem = A.h2[nv] - h2sq;
+    const double hn = rem > 0.0 ? sqrt(rem) : 0.0;
+    // previous rotations applied to the new column, top to bottom
+    double lo = A.hc[0];
+    for (int i = 0; i < j; ++i) {
+      const double c = A.cs[i], sg = A.sn[i], hi = A.hc[i + 1];
+      A.hc[i] = c * lo + sg * hi;
+      lo = -sg * lo + c * hi;
+    }
+    const double hjj = lo;
+    const double den = hypot(hjj, hn);
+    const double cj = den > 0.0 ? hjj / den : 1.0;
+    const double sj = den > 0.0 ? hn / den : 0.0;
+    A.cs[j] = cj;
+    A.sn[j] = sj;
+    A.hc[j] = den;
+    A.hc[j + 1] = 0.0;
+    const double gj = A.g[0];
+    A.g[1] = -sj * gj;
+    A.g[0] = cj * gj;
+    const double res = fabs(A.g[1]);
+    s->res = res;
+    s->its += 1;
+    its_total[0] += 1.0;
+    const bool finite = isfinite(hn) && isfinite(res) && isfinite(A.h2[nv]);
+    if (!finite) {
+      s->status = 2;
+      its_total[1] = 1.0;
+    }
+    if (!finite || res <= s->target || hn <= 1e-300 || j + 1 >= m || s->its >= maxit) {
+      s->k = finite ? j + 1 : 0;
+      s->stopped = 1;
+      if (cond) cudaGraphSetConditional(cond, 0);
+    } else {
+      s->j = j + 1;
+      s->inv_scale = 1.0 / hn;
+    }
+  }
+  __syncthreads();
   double* Hc = s->H + j * (IRK_FG_MAXM + 1);
-  double h2sq = 0.0;
-  for (int i = 0; i <= j; ++i) {
-    Hc[i] = h1[i] + h2[i];
-    h2sq = fma(h2[i], h2[i], h2sq);
-  }
-  const double rem = h2[nv] - h2sq;
-  const double hn = rem > 0.0 ? sqrt(rem) : 0.0;
-  for (int i = 0; i < j; ++i) {
-    const double t0 = s->cs[i] * Hc[i] + s->sn[i] * Hc[i + 1];
-    const double t1 = -s->sn[i] * Hc[i] + s->cs[i] * Hc[i + 1];
-    Hc[i] = t0;
-    Hc[i + 1] = t1;
-  }
-  const double hjj = Hc[j];
-  const double den = hypot(hjj, hn);
-  s->cs[j] = den > 0.0 ? hjj / den : 1.0;
-  s->sn[j] = den > 0.0 ? hn / den : 0.0;
-  Hc[j] = den;
-  Hc[j + 1] = 0.0;
-  s->g[j + 1] = -s->sn[j] * s->g[j];
-  s->g[j] = s->cs[j] * s->g[j];
-  const double res = fabs(s->g[j + 1]);
-  s->res = res;
-  s->its += 1;
-  its_total[0] += 1.0;
-  const bool finite = isfinite(hn) && isfinite(res) && isfinite(h2[nv]);
-  if (!finite) {
-    s->status = 2;
-    its_total[1] = 1.0;
-  }
-  if (!finite || res <= s->target || hn <= 1e-300 || j + 1 >= m || s->its >= maxit) {
-    s->k = finite ? j + 1 : 0;
-    s->stopped = 1;
-    if (cond) cudaGraphSetConditional(cond, 0);
-  } else {
-    s->j = j + 1;
-    s->inv_scale = 1.0 / hn;
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hc[i] = A.hc[i];
+  if (threadIdx.x == 0) {
+    s->cs[j] = A.cs[j];
+    s->sn[j] = A.sn[j];
+    s->g[j] = A.g[0];
+    s->g[j + 1] = A.g[1];
   }
 }
 
@@ -323,13 +457,11 @@ k_fg_gs2(const double* __restrict__ V, long long ldv, FGState* s, const double* 
     default: dev_update_dot_any(V, ldv, nv, h1, w, L, 1, partials, sh);
   }
   if (arrive_last(&s->ctr2)) {
-    last_block_reduce(partials, gridDim.x, nv + 1, nv + 1, h2);
+    __shared__ ArnoldiShared A;
+    last_block_reduce(partials, gridDim.x, nv + 1, nv + 1, h2, A.h2);
+    if (threadIdx.x == 0) s->ctr2 = 0u;
     __syncthreads();
-    __threadfence_block();
-    if (threadIdx.x == 0) {
-      s->ctr2 = 0u;
-      arnoldi_step(s, h1, h2, m, maxit, its_total, cond);
-    }
+    arnoldi_step(s, h1, A, m, maxit, its_total, cond);
   }
 }
 
@@ -390,21 +522,31 @@ k_fg_next(const double* __restrict__ V, long long ldv, FGState* s,
   }
 }
 
+// 1 when the 16-byte forms apply: L and the leading dimension even, every
+// vector on a 16-byte boundary.
+static int pairs_ok(long long L, long long ld, std::initializer_list<const void*> ptrs) {
+  if ((L & 1) || (ld & 1)) return 0;
+  for (const void* p : ptrs)
+    if (reinterpret_cast<uintptr_t>(p) & 15u) return 0;
+  return 1;
+}
+
 void launch_fg_gs1(const double* V, long long ldv, FGState* s, const double* w, long long L,
                    double* partials, double* h1, cudaStream_t st) {
-  launch_pdl(k_fg_gs1, blas_blocks(L), IRK_BLAS_THREADS, 0, st, V, ldv, s, w, L, partials, h1);
+  launch_pdl(k_fg_gs1, blas_blocks(L), IRK_BLAS_THREADS, 0, st, V, ldv, s, w, L, partials, h1,
+             pairs_ok(L, ldv, {V, w}));
 }
 void launch_fg_gs2(const double* V, long long ldv, FGState* s, const double* h1, double* w,
                    long long L, double* partials, double* h2, int m, int maxit, double* its_total,
                    cudaGraphConditionalHandle cond, cudaStream_t st) {
   launch_pdl(k_fg_gs2, blas_blocks(L), IRK_BLAS_THREADS, 0, st, V, ldv, s, h1, w, L, partials, h2, m, maxit,
-                                                        its_total, cond);
+             its_total, cond);
 }
 void launch_fg_next(const double* V_, long long ldv, FGState* s, const double* h2,
                     const double* w, double* V, double* prec_in, long long L, int guard_limit,
                     cudaGraphConditionalHandle cond, cudaStream_t st) {
   launch_pdl(k_fg_next, blas_blocks(L), IRK_BLAS_THREADS, 0, st, V_, ldv, s, h2, w, V, prec_in, L,
-                                                        guard_limit, cond);
+             guard_limit, cond);
 }
 
 // ---------------------------------------------------------------------------
@@ -516,12 +658,14 @@ void launch_fg_init(FGState* s, const double* nrm2, const double* rtol,
 }
 void launch_fg_scale(const double* w, const FGState* s, double* V, long long ldv, double* prec_in,
                      long long L, cudaStream_t st) {
-  launch_pdl(k_fg_scale, blas_blocks(L), IRK_BLAS_THREADS, 0, st, w, s, V, ldv, prec_in, L);
+  launch_pdl(k_fg_scale, blas_blocks(L), IRK_BLAS_THREADS, 0, st, w, s, V, ldv, prec_in, L,
+             pairs_ok(L, ldv, {w, V, prec_in}));
 }
 void launch_fg_solve(FGState* s, cudaStream_t st) { launch_pdl(k_fg_solve, 1, 1, 0, st, s); }
 void launch_fg_lincomb(double* x, const double* Z, long long ldz, const FGState* s, long long L,
                        cudaStream_t st) {
-  launch_pdl(k_fg_lincomb, blas_blocks(L), IRK_BLAS_THREADS, 0, st, x, Z, ldz, s, L);
+  launch_pdl(k_fg_lincomb, blas_blocks(L), IRK_BLAS_THREADS, 0, st, x, Z, ldz, s, L,
+             pairs_ok(L, ldz, {x, Z}));
 }
 
 }  // namespace irk
