@@ -15,6 +15,7 @@
 #include <cstdint>
 #include <initializer_list>
 
+#include "dev_reduce.cuh"
 #include "irk_internal.h"
 
 namespace irk {
@@ -208,45 +209,9 @@ __global__ void k_fg_lincomb(double* __restrict__ x, const double* __restrict__ 
 // ||w''||^2 = ||w'||^2 - ||h2||^2 (V orthonormal) gives the new Hessenberg
 // entry, and w'' = w' - V h2 is formed inside the normalisation kernel.
 
-// Sum `count` values (stride `stride`) of the partials of all blocks; called by
-// the whole last block; out[v] = sum_b partials[b*stride + v] (in b order),
-// also copied to the shared array sout when given.
-__device__ void last_block_reduce(const double* partials, int nblk, int stride, int count,
-                                  double* out, double* sout = nullptr) {
-  constexpr int R = 10;  // loads in flight per lane (304 blocks = 9.5 per lane)
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int v = wid; v < count; v += nw) {
-    double acc = 0.0;
-    for (int b0 = lane; b0 < nblk; b0 += 32 * R) {
-      double t[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int b = b0 + 32 * r;
-        t[r] = b < nblk ? __ldcg(partials + (long long)b * stride + v) : 0.0;
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc += t[r];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      out[v] = acc;
-      if (sout) sout[v] = acc;
-    }
-  }
-}
-
-__device__ bool arrive_last(unsigned int* ctr) {
-  __shared__ bool last;
-  // every partial of a block is stored by threads of warp 0 (fewer than 32
-  // values, or chunks of 4): their fence publishes them before the count
-  if (threadIdx.x < 32) __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(ctr, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (last) __threadfence();
-  return last;
-}
+// The last-block reductions (last_block_reduce, arrive_last) are in
+// dev_reduce.cuh.  Every partial of a block here is stored by threads of
+// warp 0 (fewer than 32 values, or chunks of 4), so warp 0 alone fences.
 
 // 16-byte form of the first projection: two consecutive points per load and U
 // such pairs per thread and pass, so that a warp keeps (nv + 1) U loads of 16
@@ -330,7 +295,7 @@ k_fg_gs1(const double* __restrict__ V, long long ldv, FGState* s, const double* 
 #undef IRK_C
     default: dev_multi_dot_any(V, ldv, nv, w, L, partials, sh);
   }
-  if (arrive_last(&s->ctr1)) {
+  if (arrive_last(&s->ctr1, 32)) {
     last_block_reduce(partials, gridDim.x, nv, nv, h1);
     if (threadIdx.x == 0) s->ctr1 = 0u;
   }
@@ -456,7 +421,7 @@ k_fg_gs2(const double* __restrict__ V, long long ldv, FGState* s, const double* 
 #undef IRK_C
     default: dev_update_dot_any(V, ldv, nv, h1, w, L, 1, partials, sh);
   }
-  if (arrive_last(&s->ctr2)) {
+  if (arrive_last(&s->ctr2, 32)) {
     __shared__ ArnoldiShared A;
     last_block_reduce(partials, gridDim.x, nv + 1, nv + 1, h2, A.h2);
     if (threadIdx.x == 0) s->ctr2 = 0u;
