@@ -13,7 +13,10 @@ path.  Each case writes `traj_<case>.npz` beside this file with
 * `u_step1`      the state after the first step (VSF only, omega),
 * `norms`        ||u_n||_2 for n = 0..nsteps,
 * `newton_its`   oracle Newton iterations per step,
-* `n, nu, dt, stages, seed, nsteps` the workload.
+* `n, nu, dt, stages, seed` the workload, `nsteps` the steps written.
+
+The file is rewritten after every step, so an interrupted run leaves a valid
+shorter trajectory (its `nsteps` says how many steps it holds).
 
 Cases (the full-size workloads: Sec. 1.1 Eq. stages/update; Sec. 6
 Eq. dae_stage for the DAE):
@@ -82,15 +85,24 @@ def run(case: str) -> None:
             u1 = u.copy()
         print(f"{case}: step {k + 1}/{c['nsteps']} newton {info.iterations} "
               f"gmres {info.linear_iterations} {time.perf_counter() - t0:.1f} s", flush=True)
+        save(case, c, k + 1, norms, its, u, u1)
+    print(f"wrote {path(case)}", flush=True)
+
+
+def save(case: str, c: dict, done: int, norms, its, u, u1) -> None:
+    """Write the trajectory so far (after every step, so that an interrupted
+    run leaves a valid shorter trajectory: `nsteps` is the steps done)."""
     out = dict(norms=np.array(norms), newton_its=np.array(its),
-               **{k: np.array(v) for k, v in c.items() if k != "op"})
+               **{k: np.array(v) for k, v in c.items() if k not in ("op", "nsteps")})
+    out["nsteps"] = np.array(done)
     if c["op"] == "vsf":
         out["u_final"] = u[0]
         out["u_step1"] = u1[0]
     else:
         out["u_final"] = u
-    np.savez(path(case), **out)
-    print(f"wrote {path(case)}", flush=True)
+    tmp = path(case) + ".tmp.npz"
+    np.savez(tmp, **out)
+    os.replace(tmp, path(case))
 
 
 if __name__ == "__main__":
