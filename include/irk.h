@@ -26,6 +26,9 @@
  *    stage-major.
  *  - `*_on_device` = 1 means the pointer is CUDA device memory on the current
  *    device (e.g. a torch tensor's data_ptr()); 0 means host memory.
+ *  - A handle lives on the device that was current at irk_create.  Every call
+ *    on it makes that device current while it runs and gives the caller's
+ *    current device back on return.
  *  - The caller owns every buffer it passes; the library copies in and out.
  *    The handle owns all device memory it allocates (one arena, sized at
  *    irk_create) and releases it in irk_destroy.

@@ -55,7 +55,9 @@ extern "C" {
 typedef struct irk_batch irk_batch;
 
 /* A batch of up to `capacity` (1..64) instances on the current device; work
- * goes to cuda_stream (NULL: a stream the batch creates). */
+ * goes to cuda_stream (NULL: a stream the batch creates).  Every later call
+ * on the batch makes that device current while it runs and gives the
+ * caller's current device back on return. */
 irk_status irk_batch_create(int capacity, void* cuda_stream, irk_batch** out);
 
 /* Device bytes of one instance's arena for cfg (host-only); 0 if cfg is not

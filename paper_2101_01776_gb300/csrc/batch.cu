@@ -2040,8 +2040,9 @@ size_t irk_batch_instance_bytes(const irk_config* cfg) {
 irk_status irk_batch_add(irk_batch* b, const irk_config* cfg, const double* u0, int u0_on_device,
                          double dt, void* arena, size_t arena_bytes, int* slot) {
   if (!b) return IRK_ERR_INVALID;
-  if (!u0 || !slot || !(dt > 0) || !std::isfinite(dt)) {
-    set_err(b, "u0, slot and dt > 0 are required");
+  DeviceScope ds(b->device);
+  if (!cfg || !u0 || !slot || !(dt > 0) || !std::isfinite(dt)) {
+    set_err(b, "cfg, u0, slot and dt > 0 are required");
     return IRK_ERR_INVALID;
   }
   Layout lo = layout(cfg, 0, nullptr, nullptr);
@@ -2112,6 +2113,7 @@ irk_status irk_batch_add(irk_batch* b, const irk_config* cfg, const double* u0, 
 
 irk_status irk_batch_step(irk_batch* b, irk_stats* stats, irk_status* status) {
   if (!b) return IRK_ERR_INVALID;
+  DeviceScope ds(b->device);
   TraceRange tr("batch_step");
   int nres = 0;
   for (auto& H : b->inst) nres += H.used ? 1 : 0;
@@ -2153,6 +2155,7 @@ irk_status irk_batch_step(irk_batch* b, irk_stats* stats, irk_status* status) {
 
 irk_status irk_batch_get_state(irk_batch* b, int slot, double* dst, int dst_on_device) {
   if (!b || slot < 0 || slot >= b->capacity || !b->inst[slot].used || !dst) return IRK_ERR_INVALID;
+  DeviceScope ds(b->device);
   const InstHost& H = b->inst[slot];
   BCK(cudaMemcpyAsync(dst, H.d.u, sizeof(double) * H.L,
                       dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->st));
@@ -2162,6 +2165,7 @@ irk_status irk_batch_get_state(irk_batch* b, int slot, double* dst, int dst_on_d
 
 irk_status irk_batch_get_stages(irk_batch* b, int slot, double* dst, int dst_on_device) {
   if (!b || slot < 0 || slot >= b->capacity || !b->inst[slot].used || !dst) return IRK_ERR_INVALID;
+  DeviceScope ds(b->device);
   const InstHost& H = b->inst[slot];
   BCK(cudaMemcpyAsync(dst, H.d.K, sizeof(double) * H.s * H.L,
                       dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->st));
@@ -2171,6 +2175,7 @@ irk_status irk_batch_get_stages(irk_batch* b, int slot, double* dst, int dst_on_
 
 irk_status irk_batch_remove(irk_batch* b, int slot) {
   if (!b || slot < 0 || slot >= b->capacity || !b->inst[slot].used) return IRK_ERR_INVALID;
+  DeviceScope ds(b->device);
   InstHost& H = b->inst[slot];
   cudaStreamSynchronize(b->st);
   if (H.own_arena) cudaFree(H.arena);
@@ -2190,6 +2195,7 @@ const char* irk_batch_last_error(const irk_batch* b) { return b ? b->err.c_str()
 
 void irk_batch_destroy(irk_batch* b) {
   if (!b) return;
+  DeviceScope ds(b->device);
   if (b->st) cudaStreamSynchronize(b->st);
   for (auto& H : b->inst)
     if (H.used && H.own_arena) cudaFree(H.arena);

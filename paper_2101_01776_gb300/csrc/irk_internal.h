@@ -35,6 +35,28 @@ __device__ __forceinline__ void pdl_entry() {
 }
 #endif
 
+// Makes `dev` (a handle's device) current for the scope of an API call and
+// gives the caller's current device back on return, so that a call made while
+// another device is current allocates, copies and launches on the handle's
+// device and not on that one.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+      return;
+    }
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+};
+
 // The error of the launch is left for the caller's cudaGetLastError, as with
 // the <<<>>> syntax.
 template <typename... KArgs, typename... Args>

@@ -2672,6 +2672,7 @@ size_t irk_config_device_bytes(const irk_config* cfg) {
 
 irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats* stats) {
   if (!h) return IRK_ERR_INVALID;
+  DeviceScope ds(h->device);
   if (!(dt > 0) || !std::isfinite(dt) || nsteps < 0 || !std::isfinite(t_n)) {
     h->err = "dt must be positive and finite, nsteps >= 0";
     return IRK_ERR_INVALID;
@@ -2721,6 +2722,7 @@ irk_status irk_step(irk_handle* h, double t_n, double dt, int nsteps, irk_stats*
 
 irk_status irk_get_state(irk_handle* h, double* dst, int dst_on_device) {
   if (!h || !dst) return IRK_ERR_INVALID;
+  DeviceScope ds(h->device);
   CK(cudaMemcpyAsync(dst, h->u, sizeof(double) * h->L,
                      dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
@@ -2729,6 +2731,7 @@ irk_status irk_get_state(irk_handle* h, double* dst, int dst_on_device) {
 
 irk_status irk_set_state(irk_handle* h, const double* src, int src_on_device) {
   if (!h || !src) return IRK_ERR_INVALID;
+  DeviceScope ds(h->device);
   CK(cudaMemcpyAsync(h->u, src, sizeof(double) * h->L,
                      src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
   // a new state starts Newton from zero stages
@@ -2740,6 +2743,7 @@ irk_status irk_set_state(irk_handle* h, const double* src, int src_on_device) {
 
 irk_status irk_set_state_keep_stages(irk_handle* h, const double* src, int src_on_device) {
   if (!h || !src) return IRK_ERR_INVALID;
+  DeviceScope ds(h->device);
   CK(cudaMemcpyAsync(h->u, src, sizeof(double) * h->L,
                      src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
   CK(cudaStreamSynchronize(h->st));
@@ -2748,6 +2752,7 @@ irk_status irk_set_state_keep_stages(irk_handle* h, const double* src, int src_o
 
 irk_status irk_set_stages(irk_handle* h, const double* src, int src_on_device) {
   if (!h || !src) return IRK_ERR_INVALID;
+  DeviceScope ds(h->device);
   CK(cudaMemcpyAsync(h->K, src, sizeof(double) * h->L * h->s,
                      src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
   h->last_dt = -1.0;  // the caller's stages: taken as from a step of the next step's dt
@@ -2757,6 +2762,7 @@ irk_status irk_set_stages(irk_handle* h, const double* src, int src_on_device) {
 
 irk_status irk_get_stages(irk_handle* h, double* dst, int dst_on_device) {
   if (!h || !dst) return IRK_ERR_INVALID;
+  DeviceScope ds(h->device);
   CK(cudaMemcpyAsync(dst, h->K, sizeof(double) * h->L * h->s,
                      dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
@@ -2766,6 +2772,7 @@ irk_status irk_get_stages(irk_handle* h, double* dst, int dst_on_device) {
 irk_status irk_stage_residual(irk_handle* h, double t_n, double dt, const double* K, double* F,
                               int on_device) {
   if (!h || !K || !F) return IRK_ERR_INVALID;
+  DeviceScope ds(h->device);
   TraceRange tr("irk_stage_residual");
   const size_t bytes = sizeof(double) * h->L * h->s;
   // stage the input in yhat (free between steps) and the output in rhs
@@ -2784,6 +2791,7 @@ irk_status irk_stage_residual(irk_handle* h, double t_n, double dt, const double
 irk_status irk_stage_jacobian_apply(irk_handle* h, double dt, const double* K, const double* V,
                                     double* JV, int on_device) {
   if (!h || !K || !V || !JV) return IRK_ERR_INVALID;
+  DeviceScope ds(h->device);
   TraceRange tr("irk_stage_jacobian_apply");
   const int s = h->s;
   const size_t bytes = sizeof(double) * h->L * s;
@@ -2835,6 +2843,7 @@ irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_con
     if (h) h->err = "autotune: dt must be positive, 1 <= steps <= 100";
     return IRK_ERR_INVALID;
   }
+  DeviceScope ds(h->device);
   TraceRange tr("irk_autotune");
   const size_t ub = sizeof(double) * h->L, kb = sizeof(double) * h->L * h->s;
   double *u0 = nullptr, *k0 = nullptr;
@@ -2945,6 +2954,7 @@ irk_status irk_autotune(irk_handle* h, double t_n, double dt, int steps, irk_con
 
 irk_status irk_kernel_stats(irk_handle* h, irk_kernel_stat* out, int max, int* count) {
   if (!h || !out || !count) return IRK_ERR_INVALID;
+  DeviceScope ds(h->device);
   prof_harvest(h);
   if (h->inner) prof_harvest(h->inner);
   int n = 0;
@@ -2965,6 +2975,7 @@ irk_status irk_kernel_stats(irk_handle* h, irk_kernel_stat* out, int max, int* c
 
 irk_status irk_reset_kernel_stats(irk_handle* h) {
   if (!h) return IRK_ERR_INVALID;
+  DeviceScope ds(h->device);
   prof_harvest(h);
   for (int k = 0; k < P_NCLASS; ++k) {
     h->prof[k].launches = 0;
@@ -2983,6 +2994,7 @@ const char* irk_last_error(const irk_handle* h) {
 
 void irk_destroy(irk_handle* h) {
   if (!h) return;
+  DeviceScope ds(h->device);
   if (h->inner) irk_destroy(h->inner);
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& ev : h->evpool) cudaEventDestroy(ev);
