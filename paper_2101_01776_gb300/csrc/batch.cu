@@ -1835,6 +1835,7 @@ irk_status capture(irk_batch* b) {
     size_t ndeps = 0;
     cudaError_t r = cudaStreamGetCaptureInfo(s, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
     if (r != cudaSuccess) return r;
+    if (cst != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = h;

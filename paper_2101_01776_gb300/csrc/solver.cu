@@ -1189,6 +1189,8 @@ cudaError_t capture_block_solve(irk_handle* h, double dt, int blk, cudaStream_t 
   cudaStreamCaptureStatus cst;
   cudaGraph_t G = nullptr;
   cudaError_t e = cudaStreamGetCaptureInfo(outer, &cst, nullptr, &G, nullptr, nullptr, nullptr);
+  // (an invalidated capture has no usable graph or dependency list)
+  if (e == cudaSuccess && cst != cudaStreamCaptureStatusActive) e = cudaErrorStreamCaptureInvalidated;
   cudaGraphConditionalHandle cond = 0;
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, G, 1, cudaGraphCondAssignDefault);
   if (e != cudaSuccess) { h->st = saved_st; return e; }
@@ -1218,6 +1220,7 @@ cudaError_t capture_block_solve(irk_handle* h, double dt, int blk, cudaStream_t 
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
   e = cudaStreamGetCaptureInfo(outer, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+  if (e == cudaSuccess && cst != cudaStreamCaptureStatusActive) e = cudaErrorStreamCaptureInvalidated;
   cudaGraphNode_t wnode = nullptr;
   cudaGraph_t body = nullptr;
   if (e == cudaSuccess) {
@@ -1533,6 +1536,7 @@ irk_status build_step_graph(irk_handle* h, double dt) {
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
     e = cudaStreamGetCaptureInfo(h->st, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+    if (e == cudaSuccess && cst != cudaStreamCaptureStatusActive) e = cudaErrorStreamCaptureInvalidated;
     cudaGraphNode_t wnode = nullptr;
     cudaGraph_t body = nullptr;
     if (e == cudaSuccess) {
