@@ -29,6 +29,22 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# The reference arm times the oracle on one host thread (reported as cores =
+# 1): the BLAS thread pools read these when numpy is first imported, so they
+# are set here, before any import that loads numpy.
+def _impl_arg(argv):
+    for i, a in enumerate(argv):
+        if a == "--impl" and i + 1 < len(argv):
+            return argv[i + 1]
+        if a.startswith("--impl="):
+            return a.split("=", 1)[1]
+    return "ours"
+
+
+if _impl_arg(sys.argv) == "reference":
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
 N = 512
 NU = 5e-3
 DT = 2e-3
@@ -187,7 +203,6 @@ def run_reference(args, rank, world):
     import workloads
     from oracle import irk
     from oracle.operators import Problem
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     p = Problem("burgers2d", N, NU)
     u = workloads.random_fourier_2d(N, seed=SEED)
     # the requested warm-up steps run in full; the timed steps stop once
@@ -214,7 +229,7 @@ def run_reference(args, rank, world):
         "steps": len(times), "warmup": warm, "ms_per_step": 1e3 * sec, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args, 1),
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", "1")),
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1,
                          "kind": "oracle",
                          "sample": f"{len(times)} timed IRK steps (of {args.steps} requested, "
                                    f"{budget:.0f} s budget) after {warm} warm-up, FP64 exact Newton "
